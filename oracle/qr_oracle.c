@@ -1,0 +1,644 @@
+/*
+ * FP64 CPU oracle for the Quantile Rendering (Q-Render) hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the package smoke check and the
+ * CPU-baseline leg of the benchmark may load or call this library; the CUDA
+ * library never does, and the two share no code, headers or tables.  Both
+ * sides receive the same seeded inputs from the input generator.
+ *
+ * What it computes, in double precision, following the paper:
+ *   - Sec. 3: a 3D Gaussian has covariance Sigma = R S S^T R^T from its scale
+ *     s (S = diag(exp(log_scale))) and rotation quaternion; it is splatted to
+ *     the image with EWA splatting (the local affine approximation J of the
+ *     perspective projection at the mean, Sigma' = J W Sigma W^T J^T);
+ *     alpha'_i = alpha_i * G_i(u) with G the projected Gaussian at pixel u.
+ *   - Eq. 1 (volume rendering, "V-Render"): w_i = T_i alpha'_i,
+ *     T_i = prod_{j<i} (1 - alpha'_j), summed over the depth-ordered list S_r.
+ *   - Sec. 4.2 / Algorithm 1 (QuantileRender): transmittance partitioned into
+ *     K+1 equal segments; a Gaussian whose test transmittance crosses the next
+ *     boundary 1-(k+1)/(K+1) is a quantile Gaussian and is alpha-blended with
+ *     the quantile transmittance T^Q; the walk stops once the test
+ *     transmittance is below 1/(K+1); the result is divided by 1 - T^Q.
+ *
+ * Readings where the paper is silent (each also listed in the design notes):
+ *   - the index list I of a pixel is every Gaussian in front of the near
+ *     plane with alpha' >= alpha_min (1/255), sorted by camera-space depth,
+ *     ties by lower index; no tiles are involved here;
+ *   - alpha' = min(alpha_max, alpha * G) with alpha_max = 0.99;
+ *   - the EWA covariance gets "dilation" px^2 added to its diagonal;
+ *   - the dense blend stops before a Gaussian that would take T below T_min
+ *     (T_min = 0 gives Eq. 1 over the whole list);
+ *   - a pixel with no quantile Gaussian (1 - T^Q = 0) renders zero.
+ *
+ * Brute force on purpose: every pixel evaluates every Gaussian.
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_OK 0
+#define OR_ERR_ARG 1
+#define OR_ERR_NOMEM 2
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 3: rotation from a quaternion (w, x, y, z), normalised first.         */
+/* ------------------------------------------------------------------------ */
+void or_quat_to_rotation(const float q_in[4], double R[9])
+{
+    double w = q_in[0], x = q_in[1], y = q_in[2], z = q_in[3];
+    double n = sqrt(w * w + x * x + y * y + z * z);
+    w /= n; x /= n; y /= n; z /= n;
+    R[0] = 1.0 - 2.0 * (y * y + z * z); R[1] = 2.0 * (x * y - w * z);       R[2] = 2.0 * (x * z + w * y);
+    R[3] = 2.0 * (x * y + w * z);       R[4] = 1.0 - 2.0 * (x * x + z * z); R[5] = 2.0 * (y * z - w * x);
+    R[6] = 2.0 * (x * z - w * y);       R[7] = 2.0 * (y * z + w * x);       R[8] = 1.0 - 2.0 * (x * x + y * y);
+}
+
+/* Sigma = R S S^T R^T with S = diag(exp(log_scale)); out row-major 3x3. */
+void or_covariance3d(const float log_scale[3], const float quat[4], double Sigma[9])
+{
+    double R[9], M[9];
+    or_quat_to_rotation(quat, R);
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c)
+            M[r * 3 + c] = R[r * 3 + c] * exp((double)log_scale[c]);
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) {
+            double s = 0.0;
+            for (int k = 0; k < 3; ++k) s += M[r * 3 + k] * M[c * 3 + k];
+            Sigma[r * 3 + c] = s;
+        }
+}
+
+/*
+ * Projection of every Gaussian (Sec. 3, EWA splatting).
+ * cam = [R(9) row-major world->camera, t(3), fx, fy, cx, cy, near] (float32).
+ * Outputs (double): mean2d [n][2], conic [n][3] = (A00, A01, A11) of
+ * A = Sigma'^{-1}, cov2d [n][3] = (S00, S01, S11) of Sigma' (with dilation),
+ * depth [n] = camera-space z of the mean; valid [n] = 1 if z > near and
+ * det Sigma' > 0.
+ */
+int or_project(int64_t n, const float *mean, const float *log_scale, const float *quat,
+               const float *cam, double dilation,
+               double *mean2d, double *conic, double *cov2d, double *depth, int32_t *valid)
+{
+    if (n < 0 || !mean || !log_scale || !quat || !cam) return OR_ERR_ARG;
+    double W[9], tw[3];
+    for (int i = 0; i < 9; ++i) W[i] = cam[i];
+    for (int i = 0; i < 3; ++i) tw[i] = cam[9 + i];
+    double fx = cam[12], fy = cam[13], cx = cam[14], cy = cam[15], znear = cam[16];
+    for (int64_t i = 0; i < n; ++i) {
+        double p[3] = {mean[3 * i], mean[3 * i + 1], mean[3 * i + 2]};
+        double c[3];
+        for (int r = 0; r < 3; ++r)
+            c[r] = W[r * 3] * p[0] + W[r * 3 + 1] * p[1] + W[r * 3 + 2] * p[2] + tw[r];
+        depth[i] = c[2];
+        mean2d[2 * i] = mean2d[2 * i + 1] = 0.0;
+        conic[3 * i] = conic[3 * i + 1] = conic[3 * i + 2] = 0.0;
+        cov2d[3 * i] = cov2d[3 * i + 1] = cov2d[3 * i + 2] = 0.0;
+        valid[i] = 0;
+        if (!(c[2] > znear)) continue;
+        double Sigma[9];
+        or_covariance3d(log_scale + 3 * i, quat + 4 * i, Sigma);
+        /* J: Jacobian of (fx x/z + cx, fy y/z + cy) at the camera-space mean */
+        double z = c[2];
+        double J[6] = {fx / z, 0.0, -fx * c[0] / (z * z),
+                       0.0, fy / z, -fy * c[1] / (z * z)};
+        double T[6]; /* T = J W */
+        for (int r = 0; r < 2; ++r)
+            for (int k = 0; k < 3; ++k)
+                T[r * 3 + k] = J[r * 3] * W[k] + J[r * 3 + 1] * W[3 + k] + J[r * 3 + 2] * W[6 + k];
+        double V[4]; /* Sigma' = T Sigma T^T */
+        for (int r = 0; r < 2; ++r)
+            for (int s = 0; s < 2; ++s) {
+                double acc = 0.0;
+                for (int a = 0; a < 3; ++a)
+                    for (int b = 0; b < 3; ++b)
+                        acc += T[r * 3 + a] * Sigma[a * 3 + b] * T[s * 3 + b];
+                V[r * 2 + s] = acc;
+            }
+        double s00 = V[0] + dilation, s01 = 0.5 * (V[1] + V[2]), s11 = V[3] + dilation;
+        double det = s00 * s11 - s01 * s01;
+        if (!(det > 0.0)) continue;
+        cov2d[3 * i] = s00; cov2d[3 * i + 1] = s01; cov2d[3 * i + 2] = s11;
+        conic[3 * i] = s11 / det; conic[3 * i + 1] = -s01 / det; conic[3 * i + 2] = s00 / det;
+        mean2d[2 * i] = fx * c[0] / z + cx;
+        mean2d[2 * i + 1] = fy * c[1] / z + cy;
+        valid[i] = 1;
+    }
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Algorithm 1 on one depth-ordered list of alpha' values.                    */
+/* ------------------------------------------------------------------------ */
+/*
+ * a[0..n)  : alpha' of the list I, front to back.
+ * sel[i]   : 1 if Gaussian i is a quantile Gaussian.
+ * w[i]     : its blend weight T^Q * alpha'_i before normalisation (0 if not).
+ * *TQ      : final quantile transmittance T^Q.
+ * *n_proc  : how many list entries the walk visited before stopping.
+ * Returns the number of quantile Gaussians.
+ */
+int or_qrender_list(int64_t n, const double *a, int K, int32_t *sel, double *w,
+                    double *TQ, int64_t *n_proc)
+{
+    double T = 1.0, Tq = 1.0;
+    int k = 0, m = 0;
+    int64_t i;
+    for (i = 0; i < n; ++i) { sel[i] = 0; w[i] = 0.0; }
+    for (i = 0; i < n; ++i) {
+        double Ttest = T * (1.0 - a[i]);
+        if (Ttest < 1.0 - (double)(k + 1) / (double)(K + 1)) {
+            k = k + 1;
+            w[i] = Tq * a[i];
+            sel[i] = 1;
+            ++m;
+            Tq = Tq * (1.0 - a[i]);
+            while (Ttest < 1.0 - (double)(k + 1) / (double)(K + 1)) k = k + 1;
+        }
+        if (Ttest < 1.0 / (double)(K + 1)) { ++i; break; }
+        T = Ttest;
+    }
+    if (TQ) *TQ = Tq;
+    if (n_proc) *n_proc = i;
+    return m;
+}
+
+/* n(t) = #{ j in 1..K : t < 1 - j/(K+1) }: how many segment boundaries lie above t. */
+static int crossed(double t, int K)
+{
+    int c = 0;
+    for (int j = 1; j <= K; ++j)
+        if (t < 1.0 - (double)j / (double)(K + 1)) ++c;
+    return c;
+}
+
+/*
+ * The same selection written as a closed form over the full transmittance
+ * sequence T_0 = 1, T_i = T_{i-1}(1 - a_i): Gaussian i is visited iff every
+ * earlier T stayed >= 1/(K+1), and it is a quantile Gaussian iff it is
+ * visited and n(T_i) > n(T_{i-1}).
+ */
+int or_qselect_closed_form(int64_t n, const double *a, int K, int32_t *sel)
+{
+    double Tprev = 1.0;
+    int visited = 1, m = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        double Ti = Tprev * (1.0 - a[i]);
+        sel[i] = (visited && crossed(Ti, K) > crossed(Tprev, K)) ? 1 : 0;
+        m += sel[i];
+        if (visited && Ti < 1.0 / (double)(K + 1)) visited = 0;
+        Tprev = Ti;
+    }
+    return m;
+}
+
+/*
+ * Eq. 1 on one list: w_i = T_i alpha'_i with T_i the transmittance before i.
+ * With T_min > 0 the walk stops before the Gaussian whose test transmittance
+ * would fall below T_min.  Returns the number of blended Gaussians.
+ */
+int64_t or_dense_list(int64_t n, const double *a, double T_min, double *w, double *T_final)
+{
+    double T = 1.0;
+    int64_t i, used = 0;
+    for (i = 0; i < n; ++i) w[i] = 0.0;
+    for (i = 0; i < n; ++i) {
+        double Ttest = T * (1.0 - a[i]);
+        if (T_min > 0.0 && Ttest < T_min) break;
+        w[i] = T * a[i];
+        ++used;
+        T = Ttest;
+    }
+    if (T_final) *T_final = T;
+    return used;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Per-pixel renderer (brute force over all Gaussians).                      */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    double depth;
+    int64_t id;
+    double a;        /* alpha' (clamped) */
+    double g;        /* alpha * G, unclamped */
+    double G;        /* Gaussian value exp(-q/2) */
+    double dx, dy;   /* pixel centre minus projected mean */
+    double qabs;     /* |A00| dx^2 + 2|A01||dx dy| + |A11| dy^2 (for the tie check) */
+} member_t;
+
+static int member_cmp(const void *pa, const void *pb)
+{
+    const member_t *a = (const member_t *)pa, *b = (const member_t *)pb;
+    if (a->depth < b->depth) return -1;
+    if (a->depth > b->depth) return 1;
+    return (a->id < b->id) ? -1 : (a->id > b->id);
+}
+
+typedef struct {
+    /* inputs */
+    int64_t n;
+    const double *mean2d, *conic, *depth, *alpha;
+    const int32_t *valid;
+    const double *feat; int C;
+    int K; double alpha_min, alpha_max, T_min;
+    double tie_eps;                 /* relative alpha' error the tie check allows */
+    int64_t npix; const int32_t *pix;
+    const double *grad_out;         /* backward only */
+    /* outputs */
+    double *out_q; int32_t *ids; double *wq; int32_t *cnt; double *tq;
+    double *out_dense; double *t_final; int32_t *n_members; int32_t *n_proc; int32_t *tie;
+    /* threading */
+    int tid, nthreads; int status;
+} render_job_t;
+
+typedef struct {
+    member_t *m; int64_t cap, len;
+    double *border; int64_t bcap, blen;    /* depths of Gaussians with alpha*G near alpha_min */
+    double *a, *w, *wd; int32_t *sel; int64_t acap;
+} scratch_t;
+
+static int grow(void **p, int64_t *cap, int64_t need, size_t elem)
+{
+    if (need <= *cap) return 0;
+    int64_t nc = *cap ? *cap : 256;
+    while (nc < need) nc *= 2;
+    void *q = realloc(*p, (size_t)nc * elem);
+    if (!q) return -1;
+    *p = q; *cap = nc;
+    return 0;
+}
+
+/* Build the depth-ordered list I(p) of one pixel.  Returns 0 on success. */
+static int build_list(const render_job_t *J, scratch_t *S, int px, int py)
+{
+    const double u = ldexp(1.0, -24);
+    double ux = px + 0.5, uy = py + 0.5;
+    S->len = 0; S->blen = 0;
+    for (int64_t i = 0; i < J->n; ++i) {
+        if (!J->valid[i]) continue;
+        double dx = ux - J->mean2d[2 * i], dy = uy - J->mean2d[2 * i + 1];
+        double A00 = J->conic[3 * i], A01 = J->conic[3 * i + 1], A11 = J->conic[3 * i + 2];
+        double q = A00 * dx * dx + 2.0 * A01 * dx * dy + A11 * dy * dy;
+        double G = exp(-0.5 * q);
+        double g = J->alpha[i] * G;
+        double qabs = fabs(A00) * dx * dx + 2.0 * fabs(A01 * dx * dy) + fabs(A11) * dy * dy;
+        double rel = J->tie_eps * (1.0 + qabs) + 4.0 * u;
+        if (J->tie && fabs(g - J->alpha_min) <= 4.0 * rel * J->alpha_min) {
+            if (grow((void **)&S->border, &S->bcap, S->blen + 1, sizeof(double))) return -1;
+            S->border[S->blen++] = J->depth[i];
+        }
+        double a = g < J->alpha_max ? g : J->alpha_max;   /* alpha' = min(alpha_max, alpha G) */
+        if (a < J->alpha_min) continue;
+        if (grow((void **)&S->m, &S->cap, S->len + 1, sizeof(member_t))) return -1;
+        member_t *mm = &S->m[S->len++];
+        mm->depth = J->depth[i]; mm->id = i; mm->g = g; mm->G = G;
+        mm->a = a;
+        mm->dx = dx; mm->dy = dy; mm->qabs = qabs;
+    }
+    qsort(S->m, (size_t)S->len, sizeof(member_t), member_cmp);
+    if (grow((void **)&S->a, &S->acap, S->len + 1, sizeof(double))) return -1;
+    S->w = (double *)realloc(S->w, (size_t)S->acap * sizeof(double));
+    S->wd = (double *)realloc(S->wd, (size_t)S->acap * sizeof(double));
+    S->sel = (int32_t *)realloc(S->sel, (size_t)S->acap * sizeof(int32_t));
+    if (!S->w || !S->wd || !S->sel) return -1;
+    for (int64_t j = 0; j < S->len; ++j) S->a[j] = S->m[j].a;
+    return 0;
+}
+
+/*
+ * Near-tie classification of one pixel (parity diagnostics, not rendering).
+ * A GPU that evaluates alpha' in FP32 may take a different branch than this
+ * FP64 walk only where a decision is closer to its threshold than the FP32
+ * error can reach.  The FP32 relative error of alpha'_i is bounded by
+ * tie_eps * (1 + |q|_abs) + 4u (u = 2^-24), that of a transmittance product
+ * accumulates a_i/(1-a_i) times it plus two roundings per factor.
+ * Bits for Algorithm 1: 1 = a visited test transmittance within that error of
+ * a segment boundary; 2 = a Gaussian up to the stopping point with alpha*G
+ * within error of alpha_min; 4 = two visited list entries whose depths are
+ * within FP32 resolution.  The same three checks up to the dense blend's
+ * stopping point give 16, 64 and 128, and 8 marks its T_min decision.
+ */
+static int classify_ties(const render_job_t *J, const scratch_t *S, int64_t nproc_q,
+                         int64_t nused_dense)
+{
+    const double u = ldexp(1.0, -24);
+    int flags = 0, K = J->K;
+    double T = 1.0, E = 0.0;
+    int64_t last_q = nproc_q - 1;                       /* index of the last visited entry */
+    int64_t last_d = nused_dense < S->len ? nused_dense : S->len - 1;
+    for (int64_t i = 0; i < S->len; ++i) {
+        const member_t *m = &S->m[i];
+        double rel = J->tie_eps * (1.0 + m->qabs) + 4.0 * u;
+        double ea = (m->g >= J->alpha_max) ? 1e-6 : rel * m->a / (1.0 - m->a);
+        E += ea + 2.0 * u;
+        double Tt = T * (1.0 - m->a);
+        if (i <= last_q)
+            for (int j = 0; j < K; ++j) {
+                double tau = 1.0 - (double)(j + 1) / (double)(K + 1);
+                if (fabs(Tt - tau) <= (2.0 * E + 2.0 * u) * tau) flags |= 1;
+            }
+        if (i + 1 < S->len) {
+            double z0 = m->depth, z1 = S->m[i + 1].depth;
+            int close = fabs(z1 - z0) <= 4.0 * u * fabs(z0);
+            if (close && i <= last_q) flags |= 4;
+            if (close && i <= last_d) flags |= 128;
+        }
+        if (i <= last_d && J->T_min > 0.0 &&
+            fabs(Tt - J->T_min) <= (2.0 * E + 2.0 * u) * J->T_min) flags |= 8;
+        T = Tt;
+    }
+    /* a Gaussian at the alpha_min border matters if it lies before the stop */
+    double zq = (last_q >= 0 && last_q < S->len - 1) ? S->m[last_q].depth : INFINITY;
+    double zd = (last_d >= 0 && last_d < S->len - 1) ? S->m[last_d].depth : INFINITY;
+    for (int64_t b = 0; b < S->blen; ++b) {
+        if (S->border[b] <= zq * (1.0 + 4.0 * u)) flags |= 2;
+        if (S->border[b] <= zd * (1.0 + 4.0 * u)) flags |= 64;
+    }
+    return flags;
+}
+
+static void *render_worker(void *arg)
+{
+    render_job_t *J = (render_job_t *)arg;
+    scratch_t S;
+    memset(&S, 0, sizeof(S));
+    const int K = J->K, C = J->C;
+    for (int64_t p = J->tid; p < J->npix; p += J->nthreads) {
+        int px = J->pix[2 * p], py = J->pix[2 * p + 1];
+        if (build_list(J, &S, px, py)) { J->status = OR_ERR_NOMEM; break; }
+        if (J->n_members) J->n_members[p] = (int32_t)S.len;
+        /* Algorithm 1 */
+        double Tq = 1.0; int64_t nproc = 0;
+        int m = or_qrender_list(S.len, S.a, K, S.sel, S.w, &Tq, &nproc);
+        if (J->n_proc) J->n_proc[p] = (int32_t)nproc;
+        if (J->tq) J->tq[p] = Tq;
+        if (J->cnt) J->cnt[p] = m;
+        double D = 1.0 - Tq;
+        if (J->ids || J->wq) {
+            int j = 0;
+            for (int64_t i = 0; i < S.len && j < K; ++i)
+                if (S.sel[i]) {
+                    if (J->ids) J->ids[p * K + j] = (int32_t)S.m[i].id;
+                    if (J->wq) J->wq[p * K + j] = S.w[i] / D;
+                    ++j;
+                }
+            for (; j < K; ++j) {
+                if (J->ids) J->ids[p * K + j] = -1;
+                if (J->wq) J->wq[p * K + j] = 0.0;
+            }
+        }
+        if (J->out_q && J->feat) {
+            double *o = J->out_q + p * C;
+            for (int c = 0; c < C; ++c) o[c] = 0.0;
+            if (m > 0) {
+                for (int64_t i = 0; i < S.len; ++i)
+                    if (S.sel[i]) {
+                        const double *f = J->feat + S.m[i].id * C;
+                        for (int c = 0; c < C; ++c) o[c] += S.w[i] * f[c];
+                    }
+                for (int c = 0; c < C; ++c) o[c] = o[c] / D;
+            }
+        }
+        /* Eq. 1 */
+        int64_t nused = S.len;
+        if (J->out_dense || J->t_final || J->tie) {
+            double Tf = 1.0;
+            nused = or_dense_list(S.len, S.a, J->T_min, S.wd, &Tf);
+            if (J->t_final) J->t_final[p] = Tf;
+            if (J->out_dense && J->feat) {
+                double *o = J->out_dense + p * C;
+                for (int c = 0; c < C; ++c) o[c] = 0.0;
+                for (int64_t i = 0; i < S.len; ++i)
+                    if (S.wd[i] != 0.0) {
+                        const double *f = J->feat + S.m[i].id * C;
+                        for (int c = 0; c < C; ++c) o[c] += S.wd[i] * f[c];
+                    }
+            }
+        }
+        if (J->tie) J->tie[p] = classify_ties(J, &S, nproc, nused);
+    }
+    free(S.m); free(S.border); free(S.a); free(S.w); free(S.wd); free(S.sel);
+    return NULL;
+}
+
+/*
+ * Render the pixels listed in pix [npix][2] = (x, y).  Every output pointer
+ * may be NULL.  feat is [n][C] in double (already decoded).  Outputs:
+ * out_q [npix][C] (Algorithm 1, normalised), ids/wq [npix][K] (quantile
+ * Gaussians in depth order and their normalised weights, -1 / 0 padded),
+ * cnt, tq = T^Q, out_dense [npix][C] (Eq. 1), t_final, n_members = |I(p)|,
+ * n_proc = entries visited by Algorithm 1, tie = near-tie flags.
+ */
+int or_render(int64_t n, const double *mean2d, const double *conic, const double *depth,
+              const double *alpha, const int32_t *valid, const double *feat, int C,
+              int K, double alpha_min, double alpha_max, double T_min, double tie_eps,
+              int64_t npix, const int32_t *pix, int nthreads,
+              double *out_q, int32_t *ids, double *wq, int32_t *cnt, double *tq,
+              double *out_dense, double *t_final, int32_t *n_members, int32_t *n_proc,
+              int32_t *tie)
+{
+    if (n < 0 || npix < 0 || K < 1 || nthreads < 1 || (C < 0)) return OR_ERR_ARG;
+    render_job_t base;
+    memset(&base, 0, sizeof(base));
+    base.n = n; base.mean2d = mean2d; base.conic = conic; base.depth = depth;
+    base.alpha = alpha; base.valid = valid; base.feat = feat; base.C = C;
+    base.K = K; base.alpha_min = alpha_min; base.alpha_max = alpha_max; base.T_min = T_min;
+    base.tie_eps = tie_eps; base.npix = npix; base.pix = pix;
+    base.out_q = out_q; base.ids = ids; base.wq = wq; base.cnt = cnt; base.tq = tq;
+    base.out_dense = out_dense; base.t_final = t_final; base.n_members = n_members;
+    base.n_proc = n_proc; base.tie = tie;
+    base.nthreads = nthreads;
+    render_job_t *jobs = (render_job_t *)calloc((size_t)nthreads, sizeof(render_job_t));
+    pthread_t *th = (pthread_t *)calloc((size_t)nthreads, sizeof(pthread_t));
+    if (!jobs || !th) { free(jobs); free(th); return OR_ERR_NOMEM; }
+    for (int t = 0; t < nthreads; ++t) {
+        jobs[t] = base; jobs[t].tid = t;
+        if (t > 0) pthread_create(&th[t], NULL, render_worker, &jobs[t]);
+    }
+    render_worker(&jobs[0]);
+    int st = jobs[0].status;
+    for (int t = 1; t < nthreads; ++t) {
+        pthread_join(th[t], NULL);
+        if (jobs[t].status) st = jobs[t].status;
+    }
+    free(jobs); free(th);
+    return st;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Backward of Algorithm 1 (the paper gives no formula; our derivation).      */
+/* ------------------------------------------------------------------------ */
+/*
+ * For the quantile Gaussians j = 1..m of a pixel with a_j = alpha'_j,
+ * P_j = prod_{l<j} (1 - a_l), T^Q = P_{m+1}, D = 1 - T^Q and
+ * F = sum_j a_j P_j f_j / D, given g = dL/dF:
+ *   dL/df_j = (a_j P_j / D) g
+ *   dL/da_j = [P_j s_j - (1-a_j)^{-1} sum_{l>j} a_l P_l s_l] / D
+ *             - (g.F) T^Q / ((1-a_j) D),          s_l = g . f_l
+ * and through a = alpha * exp(-q/2) (zero where alpha*G >= alpha_max):
+ *   dL/dalpha = dL/da * G,
+ *   dL/d(A00, A01, A11) = dL/da * (-a/2) * (dx^2, 2 dx dy, dy^2).
+ * The selection is piecewise constant in the inputs and is held fixed, so
+ * non-selected Gaussians receive zero gradient.  Accumulation is serial and
+ * in pixel order.  grad_feat [n][C], grad_alpha [n], grad_conic [n][3] are
+ * accumulated into (the caller zeroes them).
+ */
+int or_backward(int64_t n, const double *mean2d, const double *conic, const double *depth,
+                const double *alpha, const int32_t *valid, const double *feat, int C,
+                int K, double alpha_min, double alpha_max,
+                int64_t npix, const int32_t *pix, const double *grad_out,
+                double *grad_feat, double *grad_alpha, double *grad_conic)
+{
+    if (n < 0 || npix < 0 || K < 1 || C < 1 || !feat || !grad_out) return OR_ERR_ARG;
+    render_job_t J;
+    memset(&J, 0, sizeof(J));
+    J.n = n; J.mean2d = mean2d; J.conic = conic; J.depth = depth; J.alpha = alpha;
+    J.valid = valid; J.feat = feat; J.C = C; J.K = K; J.alpha_min = alpha_min;
+    J.alpha_max = alpha_max; J.nthreads = 1;
+    scratch_t S;
+    memset(&S, 0, sizeof(S));
+    int64_t *sid = NULL; double *sa = NULL, *sP = NULL, *ss = NULL, *F = NULL;
+    int rc = OR_OK;
+    sid = (int64_t *)malloc(sizeof(int64_t) * (size_t)K);
+    sa = (double *)malloc(sizeof(double) * (size_t)K);
+    sP = (double *)malloc(sizeof(double) * (size_t)(K + 1));
+    ss = (double *)malloc(sizeof(double) * (size_t)K);
+    F = (double *)malloc(sizeof(double) * (size_t)C);
+    if (!sid || !sa || !sP || !ss || !F) { rc = OR_ERR_NOMEM; goto done; }
+    for (int64_t p = 0; p < npix; ++p) {
+        int px = pix[2 * p], py = pix[2 * p + 1];
+        if (build_list(&J, &S, px, py)) { rc = OR_ERR_NOMEM; goto done; }
+        double Tq = 1.0; int64_t nproc = 0;
+        int m = or_qrender_list(S.len, S.a, K, S.sel, S.w, &Tq, &nproc);
+        if (m == 0) continue;
+        int j = 0;
+        for (int64_t i = 0; i < S.len; ++i)
+            if (S.sel[i]) { sid[j] = i; sa[j] = S.a[i]; ++j; }
+        sP[0] = 1.0;
+        for (j = 0; j < m; ++j) sP[j + 1] = sP[j] * (1.0 - sa[j]);
+        double D = 1.0 - sP[m];
+        const double *g = grad_out + p * C;
+        for (int c = 0; c < C; ++c) F[c] = 0.0;
+        for (j = 0; j < m; ++j) {
+            const double *f = feat + S.m[sid[j]].id * C;
+            double sj = 0.0;
+            for (int c = 0; c < C; ++c) { sj += g[c] * f[c]; F[c] += sa[j] * sP[j] * f[c] / D; }
+            ss[j] = sj;
+        }
+        double gF = 0.0;
+        for (int c = 0; c < C; ++c) gF += g[c] * F[c];
+        for (j = 0; j < m; ++j) {
+            const member_t *mm = &S.m[sid[j]];
+            double wj = sa[j] * sP[j] / D;
+            double *gf = grad_feat + mm->id * C;
+            for (int c = 0; c < C; ++c) gf[c] += wj * g[c];
+            double tail = 0.0;
+            for (int l = j + 1; l < m; ++l) tail += sa[l] * sP[l] * ss[l];
+            double da = (sP[j] * ss[j] - tail / (1.0 - sa[j])) / D
+                        - gF * sP[m] / ((1.0 - sa[j]) * D);
+            if (mm->g < alpha_max) {
+                if (grad_alpha) grad_alpha[mm->id] += da * mm->G;
+                if (grad_conic) {
+                    double h = -0.5 * sa[j] * da;
+                    grad_conic[3 * mm->id] += h * mm->dx * mm->dx;
+                    grad_conic[3 * mm->id + 1] += h * 2.0 * mm->dx * mm->dy;
+                    grad_conic[3 * mm->id + 2] += h * mm->dy * mm->dy;
+                }
+            }
+        }
+    }
+done:
+    free(S.m); free(S.border); free(S.a); free(S.w); free(S.wd); free(S.sel);
+    free(sid); free(sa); free(sP); free(ss); free(F);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Storage formats of the feature table (not in the paper).                  */
+/* ------------------------------------------------------------------------ */
+static uint32_t f32_bits(float x) { uint32_t b; memcpy(&b, &x, 4); return b; }
+static float bits_f32(uint32_t b) { float x; memcpy(&x, &b, 4); return x; }
+
+/* BF16: the top 16 bits of the FP32 pattern, rounded to nearest, ties to even. */
+void or_bf16_encode(const float *x, int64_t n, uint16_t *out)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        uint32_t b = f32_bits(x[i]);
+        if ((b & 0x7fffffffu) > 0x7f800000u) { out[i] = (uint16_t)((b >> 16) | 0x0040u); continue; }
+        uint32_t lsb = (b >> 16) & 1u;
+        out[i] = (uint16_t)((b + 0x7fffu + lsb) >> 16);
+    }
+}
+
+void or_bf16_decode(const uint16_t *h, int64_t n, double *out)
+{
+    for (int64_t i = 0; i < n; ++i) out[i] = (double)bits_f32((uint32_t)h[i] << 16);
+}
+
+/*
+ * FP8 E4M3 ("FN" variant): 1 sign, 4 exponent (bias 7), 3 mantissa bits; no
+ * infinities; S.1111.111 is NaN, so the largest finite magnitude is
+ * 1.75 * 2^8 = 448.  Exponent field 0 holds the subnormals m * 2^-9.
+ */
+double or_fp8_decode_one(uint8_t v)
+{
+    int s = v >> 7, e = (v >> 3) & 15, m = v & 7;
+    if (e == 15 && m == 7) return NAN;
+    double mag = (e == 0) ? ldexp((double)m, -9) : ldexp(1.0 + m / 8.0, e - 7);
+    return s ? -mag : mag;
+}
+
+/* Round to the nearest finite E4M3 value, ties to the even code; saturate
+ * magnitudes beyond 448 (and infinities) to 448; NaN stays NaN. */
+uint8_t or_fp8_encode_one(float xf)
+{
+    double x = xf;
+    if (x != x) return 0x7f;
+    uint8_t sign = (f32_bits(xf) >> 31) ? 0x80 : 0x00;
+    double a = fabs(x);
+    if (a >= 448.0) return sign | 0x7e;
+    /* codes 0..126 are the finite non-negative values in increasing order */
+    int lo = 0, hi = 126;
+    while (hi - lo > 1) {
+        int mid = (lo + hi) / 2;
+        if (or_fp8_decode_one((uint8_t)mid) <= a) lo = mid; else hi = mid;
+    }
+    double vlo = or_fp8_decode_one((uint8_t)lo), vhi = or_fp8_decode_one((uint8_t)hi);
+    int code;
+    if (a - vlo < vhi - a) code = lo;
+    else if (a - vlo > vhi - a) code = hi;
+    else code = (lo & 1) ? hi : lo;
+    return sign | (uint8_t)code;
+}
+
+void or_fp8_encode(const float *x, int64_t n, uint8_t *out)
+{
+    for (int64_t i = 0; i < n; ++i) out[i] = or_fp8_encode_one(x[i]);
+}
+
+void or_fp8_decode(const uint8_t *v, int64_t n, double *out)
+{
+    for (int64_t i = 0; i < n; ++i) out[i] = or_fp8_decode_one(v[i]);
+}
+
+/*
+ * Per-row FP8 quantisation: scale_i = max_c |f_ic| / 448 in FP32 (1 for an
+ * all-zero row), code_ic = E4M3(f_ic / scale_i) with the division in FP32.
+ * The decoded value is E4M3^{-1}(code) * scale_i.
+ */
+void or_fp8_quantize_rows(const float *f, int64_t n, int C, uint8_t *codes, float *scale)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        float mx = 0.0f;
+        for (int c = 0; c < C; ++c) { float v = fabsf(f[i * C + c]); if (v > mx) mx = v; }
+        float s = mx > 0.0f ? mx / 448.0f : 1.0f;
+        scale[i] = s;
+        for (int c = 0; c < C; ++c) {
+            volatile float r = f[i * C + c] / s;
+            codes[i * C + c] = or_fp8_encode_one(r);
+        }
+    }
+}

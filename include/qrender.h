@@ -1,0 +1,233 @@
+/*
+ * qrender.h -- C ABI of libqrender, a GB300 (sm_103a) implementation of the
+ * hot path of Quantile Rendering (Q-Render, arXiv 2512.20927).
+ *
+ * The paper states the operation as  f~^Q = QuantileRender(G, F, K, I)
+ * (Sec. 4.2, Algorithm 1): given 3D Gaussians G, per-Gaussian C-dimensional
+ * features F, the number of quantile Gaussians K and the depth-ordered index
+ * list I of the Gaussians rasterised at a pixel, return the pixel's rendered
+ * feature.  The list I comes from 3D-GS rasterisation: EWA projection of each
+ * Gaussian, tiling and a depth sort (Sec. 3).  This library splits that path
+ * into calls that can be timed and checked one by one:
+ *
+ *   qr_project  -> qr_sort -> qr_select -> qr_blend        (Q-Render)
+ *   qr_project  -> qr_sort -> qr_dense                     (Eq. 1, V-Render)
+ *
+ * Conventions shared by every call
+ *   - All array pointers are DEVICE pointers owned by the caller unless the
+ *     parameter name ends in _host.  The library never allocates device memory
+ *     on these paths: scratch lives in a caller-allocated workspace whose size
+ *     qr_workspace_bytes() returns.
+ *   - Every call is asynchronous on the caller's stream (NULL = the legacy
+ *     default stream) and returns a qr_status for what it can check on the
+ *     host (arguments, alignment, launch errors).  Conditions found on the
+ *     device (intersection capacity exceeded) are written to a status word in
+ *     the workspace; qr_frame_status() synchronises the stream and reads it.
+ *   - Layouts are row-major.  Gaussian i's parameters are mean[3i..3i+2],
+ *     log_scale[3i..3i+2] (natural log of the per-axis standard deviation),
+ *     quat[4i..4i+3] = (w, x, y, z) (normalised inside) and opacity[i]
+ *     (already activated, in (0, 1)).  Feature row i is feat[i*C .. i*C+C-1].
+ *     Pixel p = y * width + x is sampled at (x + 0.5, y + 0.5).
+ *   - Feature rows must start on 16-byte boundaries: C % 4 == 0 for FP32,
+ *     C % 8 == 0 for BF16, C % 16 == 0 for FP8; feat must be 16-byte aligned.
+ *   - Errors never leave partial work queued that reads out of bounds: a call
+ *     that returns anything but QR_OK has launched nothing.
+ *
+ * Thread safety: calls on different workspaces may run concurrently on
+ * different streams.  Two calls that use the same workspace race unless they
+ * are ordered on one stream.
+ */
+#ifndef QRENDER_H
+#define QRENDER_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t. */
+typedef struct CUstream_st *qr_stream;
+
+typedef enum {
+    QR_OK = 0,
+    QR_ERR_INVALID_ARG = 1,     /* null pointer, size out of range, bad enum */
+    QR_ERR_ALIGNMENT = 2,       /* pointer or row not 16-byte aligned */
+    QR_ERR_CAPACITY = 3,        /* more tile-Gaussian intersections than max_isect */
+    QR_ERR_CUDA = 4,            /* a CUDA runtime call failed */
+    QR_ERR_DEVICE_TIMEOUT = 5,  /* a bounded device-side wait gave up */
+    QR_ERR_NOT_SUPPORTED = 6    /* combination not built (e.g. dtype for this call) */
+} qr_status;
+
+typedef enum { QR_F32 = 0, QR_BF16 = 1, QR_FP8E4M3 = 2 } qr_dtype;
+
+/* Pinhole camera: camera-space point = R * world + t (x right, y down, z
+ * forward); pixel = (fx * x / z + cx, fy * y / z + cy).  Gaussians whose mean
+ * has z <= near_plane are culled (Sec. 3 leaves the camera model open). */
+typedef struct {
+    float R[9];
+    float t[3];
+    float fx, fy, cx, cy;
+    float near_plane;
+    int32_t width, height;
+} qr_camera;
+
+/* Renderer parameters.  Defaults: qr_default_params(). */
+typedef struct {
+    int32_t K;          /* quantile Gaussians per pixel, 1..32 (Algorithm 1)           */
+    float alpha_min;    /* list membership: alpha' >= alpha_min (1/255)                 */
+    float alpha_max;    /* alpha' = min(alpha_max, alpha * G(u)) (0.99)                 */
+    float T_min;        /* dense blend stops before T would fall below it (1e-4); 0 = all */
+    float dilation;     /* px^2 added to the EWA covariance diagonal (0.3)              */
+    int32_t tile_w;     /* screen tile: 16x16 or 8x32 (tile_w * tile_h == 256)          */
+    int32_t tile_h;
+} qr_params;
+
+/* Host-side descriptor of one frame's workspace.  Filled by qr_frame_init;
+ * the caller owns the struct and the workspace it points into.  Fields other
+ * than the documented ones are private to the library. */
+#define QR_FRAME_SLOTS 24
+typedef struct {
+    int64_t n;                 /* number of Gaussians                     */
+    int64_t max_isect;         /* capacity of the tile-intersection lists */
+    qr_camera camera;
+    qr_params params;
+    int32_t tiles_x, tiles_y;  /* screen tiles                            */
+    int32_t sort_blocks;       /* private                                 */
+    int32_t isect_buf;         /* private                                 */
+    void *ws;                  /* device workspace                        */
+    size_t ws_bytes;
+    size_t off[QR_FRAME_SLOTS];/* private: byte offsets into ws           */
+} qr_frame;
+
+/* Device pointers into a frame's workspace, for inspection and tests. */
+typedef struct {
+    const float *mean2d_hi_lo;   /* [n][4]: projected mean (x_hi, y_hi, x_lo, y_lo); x = x_hi + x_lo */
+    const float *conic_alpha;    /* [n][4]: (A00, A01, A11, alpha), A = inverse EWA covariance        */
+    const uint32_t *depth_key;   /* [n]: FP32 bit pattern of camera depth; 0xFFFFFFFF when culled    */
+    const uint32_t *tile_count;  /* [n]: tiles touched by Gaussian i's footprint                     */
+    const uint32_t *sorted_gid;  /* [n]: Gaussian ids in (depth, id) order                           */
+    const uint32_t *isect_tile;  /* [max_isect]: tile id of each sorted intersection                 */
+    const uint32_t *isect_gid;   /* [max_isect]: Gaussian id of each sorted intersection             */
+    const uint32_t *tile_range;  /* [tiles][2]: [begin, end) of each tile in the sorted list         */
+    const uint32_t *counters;    /* [8]: status, n_isect, n_visible, ...                             */
+} qr_frame_view;
+
+/* ---------------------------------------------------------------- setup */
+
+/* ABI version of this header (incremented on incompatible changes). */
+int32_t qr_abi_version(void);
+
+/* Human-readable name of a status code (static string). */
+const char *qr_status_string(qr_status s);
+
+/* Fill *p with the defaults listed in qr_params. */
+void qr_default_params(qr_params *p);
+
+/* Bytes of workspace a frame of n Gaussians at width x height needs with room
+ * for max_isect tile-Gaussian intersections.  0 if an argument is invalid. */
+size_t qr_workspace_bytes(int64_t n, int32_t width, int32_t height, const qr_params *params,
+                          int64_t max_isect);
+
+/* Lay out a frame in a caller-allocated device workspace ws (256-byte
+ * aligned, at least qr_workspace_bytes(...) bytes).  Host only; launches
+ * nothing.  QR_ERR_INVALID_ARG on bad sizes or a too small workspace. */
+qr_status qr_frame_init(qr_frame *frame, int64_t n, const qr_camera *camera,
+                        const qr_params *params, int64_t max_isect, void *ws, size_t ws_bytes);
+
+/* Device pointers of the frame's internal arrays (see qr_frame_view). */
+qr_status qr_frame_view_get(const qr_frame *frame, qr_frame_view *view);
+
+/* Synchronise the stream and read the frame's device status word.  Returns
+ * QR_ERR_CAPACITY if the intersection lists overflowed (the outputs of
+ * qr_sort and everything after it are then zero, not partial), otherwise
+ * QR_OK.  n_isect (nullable) receives the number of intersections the frame
+ * needed, which is also the capacity to ask for on a retry. */
+qr_status qr_frame_status(const qr_frame *frame, qr_stream stream, int64_t *n_isect);
+
+/* ---------------------------------------------------------------- hot path */
+
+/* Sec. 3 (EWA splatting [Zwicker et al.] as used by 3D-GS): per Gaussian,
+ * Sigma = R S S^T R^T, Sigma' = J W Sigma W^T J^T + dilation * I with J the
+ * Jacobian of the pinhole projection at the camera-space mean, conic
+ * A = Sigma'^{-1}, projected mean, camera depth, and the screen tiles its
+ * support {u : alpha * exp(-q(u)/2) >= alpha_min} can reach.  Camera-space
+ * position, projected mean and conic are computed in compensated
+ * (double-FP32) arithmetic, so the stored mean carries a high and low part.
+ * Inputs: mean/log_scale [n][3], quat [n][4], opacity [n] (float32, device).
+ * Writes only the frame's workspace. */
+qr_status qr_project(qr_frame *frame, const float *mean, const float *log_scale,
+                     const float *quat, const float *opacity, qr_stream stream);
+
+/* Sec. 3 "tiling strategy" + the depth-ordered list I of Sec. 4.2: sorts the
+ * Gaussians by (depth, id) with a hand-written LSD radix sort of the 32-bit
+ * depth keys, emits one (tile, Gaussian) intersection per touched tile in that
+ * order, stably radix-sorts the intersections by tile id, and records each
+ * tile's [begin, end) range.  The result is the order a sort of 64-bit
+ * (tile << 32 | depth) keys would give, with equal depths broken by id.
+ * Overflow of max_isect is reported through qr_frame_status. */
+qr_status qr_sort(qr_frame *frame, qr_stream stream);
+
+/* Algorithm 1 (Sec. 4.2), selection half: for every pixel, walk the tile's
+ * list front to back with alpha' = min(alpha_max, alpha * exp(-q/2)),
+ * skipping alpha' < alpha_min, and keep each Gaussian whose test
+ * transmittance T(1 - alpha') crosses the next boundary (K-k)/(K+1) (strict
+ * '<'); stop once it falls below 1/(K+1).  Outputs ids [P][K] int32 (depth
+ * order, -1 padded), weights [P][K] float32 = T^Q alpha' / (1 - T^Q) (the
+ * normalisation of Algorithm 1 folded in; zero padded), counts [P] uint8.
+ * P = width * height. */
+qr_status qr_select(const qr_frame *frame, int32_t *ids, float *weights, uint8_t *counts,
+                    qr_stream stream);
+
+/* Algorithm 1, blend half ("alpha-blending on quantile Gaussians" +
+ * normalisation): out[p] = sum_{j < counts[p]} weights[p][j] * feat[ids[p][j]]
+ * with FP32 accumulation.  feat is [n_gauss][C] of dtype; feat_scale [n_gauss]
+ * float32 multiplies FP8 rows (NULL otherwise).  out is [P][C] float32.
+ * Pixels with counts 0 get zeros.  ids must lie in [0, n_gauss). */
+qr_status qr_blend(const void *feat, const float *feat_scale, qr_dtype dtype, int32_t C,
+                   int64_t n_gauss, const int32_t *ids, const float *weights,
+                   const uint8_t *counts, int64_t P, int32_t K, float *out, qr_stream stream);
+
+/* Eq. 1 (V-Render, the dense method the paper compares against):
+ * out[p] = sum_i T_i alpha'_i f_i over the pixel's whole list with the same
+ * alpha' rules, stopping before a Gaussian whose test transmittance would fall
+ * below T_min.  out [P][C] float32; T_final [P] float32 (nullable). */
+qr_status qr_dense(const qr_frame *frame, const void *feat, const float *feat_scale,
+                   qr_dtype dtype, int32_t C, float *out, float *T_final, qr_stream stream);
+
+/* The whole Q-Render forward of one frame: qr_project, qr_sort, qr_select and
+ * qr_blend in order on one stream.  ids/weights/counts are kept for a later
+ * backward. */
+qr_status qr_render(qr_frame *frame, const float *mean, const float *log_scale,
+                    const float *quat, const float *opacity, const void *feat,
+                    const float *feat_scale, qr_dtype dtype, int32_t C, int32_t *ids,
+                    float *weights, uint8_t *counts, float *out, qr_stream stream);
+
+/* End-to-end variant for callers holding HOST arrays: copies the Gaussians
+ * and features from host memory (pinned for asynchronous copies) into
+ * caller-provided device staging buffers, renders with qr_render, and copies
+ * the [P][C] float32 map back into out_host.  dev_inputs must hold
+ * 11*n float32 followed (16-byte aligned) by the feature table; dev_outputs
+ * must hold the ids/weights/counts/map of qr_render (see qr_render_host_bytes).
+ * The call returns once the work is queued; synchronise the stream before
+ * reading out_host. */
+qr_status qr_render_host_bytes(int64_t n, int32_t width, int32_t height, int32_t K, int32_t C,
+                               qr_dtype dtype, size_t *dev_inputs_bytes,
+                               size_t *dev_outputs_bytes);
+qr_status qr_render_host(qr_frame *frame, const float *mean_host, const float *log_scale_host,
+                         const float *quat_host, const float *opacity_host,
+                         const void *feat_host, const float *feat_scale_host, qr_dtype dtype,
+                         int32_t C, void *dev_inputs, void *dev_outputs, float *out_host,
+                         qr_stream stream);
+
+/* ---------------------------------------------------------------- instrumentation */
+
+/* Number of kernels this library has launched since it was loaded. */
+uint64_t qr_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QRENDER_H */

@@ -250,6 +250,8 @@ typedef struct {
     /* outputs */
     double *out_q; int32_t *ids; double *wq; int32_t *cnt; double *tq;
     double *out_dense; double *t_final; int32_t *n_members; int32_t *n_proc; int32_t *tie;
+    int32_t *members; int max_members;   /* optional: I(p) in depth order, -1 padded */
+    double *scale_q, *scale_dense;       /* optional: sum_j |w_j| max|f_j| (error denominators) */
     /* threading */
     int tid, nthreads; int status;
 } render_job_t;
@@ -370,6 +372,9 @@ static void *render_worker(void *arg)
         int px = J->pix[2 * p], py = J->pix[2 * p + 1];
         if (build_list(J, &S, px, py)) { J->status = OR_ERR_NOMEM; break; }
         if (J->n_members) J->n_members[p] = (int32_t)S.len;
+        if (J->members)
+            for (int j = 0; j < J->max_members; ++j)
+                J->members[p * J->max_members + j] = j < S.len ? (int32_t)S.m[j].id : -1;
         /* Algorithm 1 */
         double Tq = 1.0; int64_t nproc = 0;
         int m = or_qrender_list(S.len, S.a, K, S.sel, S.w, &Tq, &nproc);
@@ -402,6 +407,17 @@ static void *render_worker(void *arg)
                 for (int c = 0; c < C; ++c) o[c] = o[c] / D;
             }
         }
+        if (J->scale_q && J->feat) {
+            double sc = 0.0;
+            for (int64_t i = 0; i < S.len; ++i)
+                if (S.sel[i]) {
+                    const double *f = J->feat + S.m[i].id * C;
+                    double mx = 0.0;
+                    for (int c = 0; c < C; ++c) mx = fabs(f[c]) > mx ? fabs(f[c]) : mx;
+                    sc += fabs(S.w[i] / D) * mx;
+                }
+            J->scale_q[p] = sc;
+        }
         /* Eq. 1 */
         int64_t nused = S.len;
         if (J->out_dense || J->t_final || J->tie) {
@@ -410,12 +426,19 @@ static void *render_worker(void *arg)
             if (J->t_final) J->t_final[p] = Tf;
             if (J->out_dense && J->feat) {
                 double *o = J->out_dense + p * C;
+                double sc = 0.0;
                 for (int c = 0; c < C; ++c) o[c] = 0.0;
                 for (int64_t i = 0; i < S.len; ++i)
                     if (S.wd[i] != 0.0) {
                         const double *f = J->feat + S.m[i].id * C;
-                        for (int c = 0; c < C; ++c) o[c] += S.wd[i] * f[c];
+                        double mx = 0.0;
+                        for (int c = 0; c < C; ++c) {
+                            o[c] += S.wd[i] * f[c];
+                            mx = fabs(f[c]) > mx ? fabs(f[c]) : mx;
+                        }
+                        sc += S.wd[i] * mx;
                     }
+                if (J->scale_dense) J->scale_dense[p] = sc;
             }
         }
         if (J->tie) J->tie[p] = classify_ties(J, &S, nproc, nused);
@@ -430,7 +453,10 @@ static void *render_worker(void *arg)
  * out_q [npix][C] (Algorithm 1, normalised), ids/wq [npix][K] (quantile
  * Gaussians in depth order and their normalised weights, -1 / 0 padded),
  * cnt, tq = T^Q, out_dense [npix][C] (Eq. 1), t_final, n_members = |I(p)|,
- * n_proc = entries visited by Algorithm 1, tie = near-tie flags.
+ * n_proc = entries visited by Algorithm 1, tie = near-tie flags, members
+ * [npix][max_members] = the first max_members entries of I(p) (-1 padded),
+ * scale_q / scale_dense [npix] = sum over blended Gaussians of
+ * |weight| * max_c |f_c| (the denominators of the parity error metric).
  */
 int or_render(int64_t n, const double *mean2d, const double *conic, const double *depth,
               const double *alpha, const int32_t *valid, const double *feat, int C,
@@ -438,7 +464,8 @@ int or_render(int64_t n, const double *mean2d, const double *conic, const double
               int64_t npix, const int32_t *pix, int nthreads,
               double *out_q, int32_t *ids, double *wq, int32_t *cnt, double *tq,
               double *out_dense, double *t_final, int32_t *n_members, int32_t *n_proc,
-              int32_t *tie)
+              int32_t *tie, int32_t *members, int max_members, double *scale_q,
+              double *scale_dense)
 {
     if (n < 0 || npix < 0 || K < 1 || nthreads < 1 || (C < 0)) return OR_ERR_ARG;
     render_job_t base;
@@ -450,6 +477,8 @@ int or_render(int64_t n, const double *mean2d, const double *conic, const double
     base.out_q = out_q; base.ids = ids; base.wq = wq; base.cnt = cnt; base.tq = tq;
     base.out_dense = out_dense; base.t_final = t_final; base.n_members = n_members;
     base.n_proc = n_proc; base.tie = tie;
+    base.members = members; base.max_members = members ? max_members : 0;
+    base.scale_q = scale_q; base.scale_dense = scale_dense;
     base.nthreads = nthreads;
     render_job_t *jobs = (render_job_t *)calloc((size_t)nthreads, sizeof(render_job_t));
     pthread_t *th = (pthread_t *)calloc((size_t)nthreads, sizeof(pthread_t));

@@ -1,0 +1,229 @@
+// K5b: the blend half of Algorithm 1 (Sec. 4.2, "alpha-blending on quantile
+// Gaussians" and "normalizing feature vector"):
+//     out[p] = sum_{j < cnt[p]} w[p][j] * f[ids[p][j]]
+// with the 1/(1 - T^Q) normalisation already folded into w by the selection.
+//
+// GB300 design: this is the bandwidth-bound stage (about zero flops per byte),
+// so the kernel is built around 16-byte vector traffic:
+//   - one warp per pixel (for rows of 512 B or more; narrower rows pack
+//     several pixels into a warp), each lane owning a fixed set of 16-byte
+//     column vectors of the row, so every warp-wide load or store moves 512
+//     contiguous bytes;
+//   - the pixel's ids and weights are read at one address by all of its
+//     lanes (a single L1 broadcast per entry);
+//   - all row loads of a pixel are issued before the FMAs (unrolled by 4
+//     rows) to keep enough bytes in flight per SM;
+//   - BF16 rows are widened with bit shifts, FP8 E4M3 rows with the hardware
+//     conversion instructions; FP8 rows fold their per-Gaussian scale into
+//     the weight;
+//   - the map is written with streaming (evict-first) 16-byte stores so it
+//     does not displace the feature rows that neighbouring pixels share in L2;
+//   - pixels are visited in screen-tile order (16x16 blocks of pixels per
+//     CTA group) so the rows a tile selects stay hot in L1/L2.
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+
+#include "qr_internal.cuh"
+
+namespace qr {
+namespace {
+
+constexpr int kThreads = 256;
+
+// Channels carried by one 16-byte vector of a row.
+template <int DT> struct Vec;
+template <> struct Vec<QR_F32> { static constexpr int C = 4; };
+template <> struct Vec<QR_BF16> { static constexpr int C = 8; };
+template <> struct Vec<QR_FP8E4M3> { static constexpr int C = 16; };
+
+template <int DT>
+__device__ __forceinline__ void decode_fma(const uint4 v, float w, float *acc);
+
+template <>
+__device__ __forceinline__ void decode_fma<QR_F32>(const uint4 v, float w, float *acc) {
+    acc[0] = fmaf(w, __uint_as_float(v.x), acc[0]);
+    acc[1] = fmaf(w, __uint_as_float(v.y), acc[1]);
+    acc[2] = fmaf(w, __uint_as_float(v.z), acc[2]);
+    acc[3] = fmaf(w, __uint_as_float(v.w), acc[3]);
+}
+
+__device__ __forceinline__ void bf16x2_fma(uint32_t u, float w, float *acc) {
+    acc[0] = fmaf(w, __uint_as_float(u << 16), acc[0]);
+    acc[1] = fmaf(w, __uint_as_float(u & 0xFFFF0000u), acc[1]);
+}
+
+template <>
+__device__ __forceinline__ void decode_fma<QR_BF16>(const uint4 v, float w, float *acc) {
+    bf16x2_fma(v.x, w, acc + 0);
+    bf16x2_fma(v.y, w, acc + 2);
+    bf16x2_fma(v.z, w, acc + 4);
+    bf16x2_fma(v.w, w, acc + 6);
+}
+
+__device__ __forceinline__ void fp8x4_fma(uint32_t u, float w, float *acc) {
+    const __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2(__nv_fp8x2_storage_t(u & 0xFFFFu), __NV_E4M3);
+    const __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2(__nv_fp8x2_storage_t(u >> 16), __NV_E4M3);
+    const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&lo));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&hi));
+    acc[0] = fmaf(w, a.x, acc[0]);
+    acc[1] = fmaf(w, a.y, acc[1]);
+    acc[2] = fmaf(w, b.x, acc[2]);
+    acc[3] = fmaf(w, b.y, acc[3]);
+}
+
+template <>
+__device__ __forceinline__ void decode_fma<QR_FP8E4M3>(const uint4 v, float w, float *acc) {
+    fp8x4_fma(v.x, w, acc + 0);
+    fp8x4_fma(v.y, w, acc + 4);
+    fp8x4_fma(v.z, w, acc + 8);
+    fp8x4_fma(v.w, w, acc + 12);
+}
+
+__device__ __forceinline__ uint4 ld_row(const uint4 *p) {
+    uint4 r;
+    asm volatile("ld.global.nc.v4.u32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w) : "l"(p));
+    return r;
+}
+
+__device__ __forceinline__ void st_stream(float4 *p, float4 v) {
+    asm volatile("st.global.cs.v4.f32 [%0], {%1,%2,%3,%4};"
+                 :: "l"(p), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w) : "memory");
+}
+
+// Pixel visited by work item `item` in screen-tile order (16x16 tiles).
+__device__ __forceinline__ int64_t tile_order_pixel(int64_t item, int W, int H) {
+    if (W <= 0) return item;
+    const int tiles_x = (W + 15) >> 4;
+    const int64_t t = item >> 8;
+    const int r = int(item & 255);
+    const int tx = int(t % tiles_x), ty = int(t / tiles_x);
+    const int x = tx * 16 + (r & 15), y = ty * 16 + (r >> 4);
+    if (x >= W || y >= H) return -1;
+    return int64_t(y) * W + x;
+}
+
+// LPP lanes per pixel, VPL 16-byte vectors per lane; row = LPP*VPL vectors.
+template <int DT, int LPP, int VPL>
+__global__ void __launch_bounds__(kThreads)
+blend_kernel(const uint4 *__restrict__ feat, const float *__restrict__ scale, int64_t n_gauss,
+             const int32_t *__restrict__ ids, const float *__restrict__ wts,
+             const uint8_t *__restrict__ cnt, int64_t P, int K, int W, int H,
+             float4 *__restrict__ out) {
+    constexpr int CPV = Vec<DT>::C;          // channels per vector
+    constexpr int PPW = 32 / LPP;            // pixels per warp
+    constexpr int ROWV = LPP * VPL;          // vectors per row
+    const int lane = threadIdx.x & 31;
+    const int sub = lane / LPP, sl = lane % LPP;
+    const int64_t items = (W > 0) ? int64_t((W + 15) >> 4) * ((H + 15) >> 4) * 256 : P;
+    const int64_t warp0 = (int64_t(blockIdx.x) * kThreads + threadIdx.x) >> 5;
+    const int64_t nwarps = (int64_t(gridDim.x) * kThreads) >> 5;
+    for (int64_t it = warp0 * PPW + sub; it - sub < items; it += nwarps * PPW) {
+        const int64_t p = (it < items) ? tile_order_pixel(it, W, H) : -1;
+        const int c = (p >= 0) ? int(cnt[p]) : 0;
+        const int32_t *pid = ids + p * K;
+        const float *pw = wts + p * K;
+        float acc[VPL][CPV];
+#pragma unroll
+        for (int v = 0; v < VPL; ++v)
+#pragma unroll
+            for (int q = 0; q < CPV; ++q) acc[v][q] = 0.f;
+        for (int j0 = 0; j0 < c; j0 += 4) {
+            uint4 r[4][VPL];
+            float wj[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int j = j0 + u;
+                const bool ok = j < c;
+                int id = ok ? pid[j] : 0;     // same address across the pixel's lanes: one L1 broadcast
+                float w = ok ? pw[j] : 0.f;
+                if (uint64_t(int64_t(id)) >= uint64_t(n_gauss)) { id = 0; w = 0.f; }
+                if (DT == QR_FP8E4M3 && ok) w *= scale[id];
+                wj[u] = w;
+                const uint4 *row = feat + int64_t(id) * ROWV + sl;
+#pragma unroll
+                for (int v = 0; v < VPL; ++v)
+                    r[u][v] = ok ? ld_row(row + v * LPP) : make_uint4(0, 0, 0, 0);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < VPL; ++v) decode_fma<DT>(r[u][v], wj[u], acc[v]);
+        }
+        if (p >= 0) {
+            float4 *o = out + p * (int64_t(ROWV) * CPV / 4);
+#pragma unroll
+            for (int v = 0; v < VPL; ++v)
+#pragma unroll
+                for (int q = 0; q < CPV / 4; ++q)
+                    st_stream(o + int64_t(sl + v * LPP) * (CPV / 4) + q,
+                              make_float4(acc[v][4 * q], acc[v][4 * q + 1], acc[v][4 * q + 2],
+                                          acc[v][4 * q + 3]));
+        }
+    }
+}
+
+template <int DT, int LPP, int VPL>
+cudaError_t run(const void *feat, const float *scale, int64_t n_gauss, const int32_t *ids,
+                const float *w, const uint8_t *cnt, int64_t P, int K, int W, int H, float *out,
+                cudaStream_t s) {
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t items = (W > 0) ? int64_t((W + 15) >> 4) * ((H + 15) >> 4) * 256 : P;
+    const int64_t warps_needed = (items + (32 / LPP) - 1) / (32 / LPP);
+    int64_t blocks = (warps_needed + (kThreads / 32) - 1) / (kThreads / 32);
+    const int64_t cap = int64_t(sms) * 8;   // persistent-style grid: 8 CTAs per SM
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    blend_kernel<DT, LPP, VPL><<<unsigned(blocks), kThreads, 0, s>>>(
+        static_cast<const uint4 *>(feat), scale, n_gauss, ids, w, cnt, P, K, W, H,
+        reinterpret_cast<float4 *>(out));
+    count_launch();
+    return cudaGetLastError();
+}
+
+template <int DT>
+cudaError_t dispatch(const void *feat, const float *scale, int64_t n_gauss, int C,
+                     const int32_t *ids, const float *w, const uint8_t *cnt, int64_t P, int K,
+                     int W, int H, float *out, cudaStream_t s) {
+    const int rowv = C / Vec<DT>::C;  // 16-byte vectors per row
+    switch (rowv) {
+        case 1: return run<DT, 1, 1>(feat, scale, n_gauss, ids, w, cnt, P, K, W, H, out, s);
+        case 2: return run<DT, 2, 1>(feat, scale, n_gauss, ids, w, cnt, P, K, W, H, out, s);
+        case 4: return run<DT, 4, 1>(feat, scale, n_gauss, ids, w, cnt, P, K, W, H, out, s);
+        case 8: return run<DT, 8, 1>(feat, scale, n_gauss, ids, w, cnt, P, K, W, H, out, s);
+        case 16: return run<DT, 16, 1>(feat, scale, n_gauss, ids, w, cnt, P, K, W, H, out, s);
+        case 32: return run<DT, 32, 1>(feat, scale, n_gauss, ids, w, cnt, P, K, W, H, out, s);
+        case 64: return run<DT, 32, 2>(feat, scale, n_gauss, ids, w, cnt, P, K, W, H, out, s);
+        case 96: return run<DT, 32, 3>(feat, scale, n_gauss, ids, w, cnt, P, K, W, H, out, s);
+        case 128: return run<DT, 32, 4>(feat, scale, n_gauss, ids, w, cnt, P, K, W, H, out, s);
+        case 256: return run<DT, 32, 8>(feat, scale, n_gauss, ids, w, cnt, P, K, W, H, out, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+// Row widths the blend kernel is built for (16-byte vectors per row).
+bool blend_supported(qr_dtype dt, int C) {
+    const int cpv = dt == QR_F32 ? 4 : dt == QR_BF16 ? 8 : 16;
+    if (C <= 0 || C % cpv) return false;
+    const int rowv = C / cpv;
+    return rowv == 1 || rowv == 2 || rowv == 4 || rowv == 8 || rowv == 16 || rowv == 32 ||
+           rowv == 64 || rowv == 96 || rowv == 128 || rowv == 256;
+}
+
+cudaError_t launch_blend_tiled(const void *feat, const float *scale, qr_dtype dt, int C,
+                               int64_t n_gauss, const int32_t *ids, const float *w,
+                               const uint8_t *cnt, int64_t P, int K, int W, int H, float *out,
+                               cudaStream_t s) {
+    switch (dt) {
+        case QR_F32: return dispatch<QR_F32>(feat, scale, n_gauss, C, ids, w, cnt, P, K, W, H, out, s);
+        case QR_BF16: return dispatch<QR_BF16>(feat, scale, n_gauss, C, ids, w, cnt, P, K, W, H, out, s);
+        case QR_FP8E4M3: return dispatch<QR_FP8E4M3>(feat, scale, n_gauss, C, ids, w, cnt, P, K, W, H, out, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace qr

@@ -1,0 +1,231 @@
+// K1: EWA projection of every Gaussian (Sec. 3 of the paper).
+//
+// Per Gaussian: camera-space mean c = R mu + t, 3D covariance
+// Sigma = Rq S S^T Rq^T (S = diag(exp(log_scale)), Rq from the quaternion),
+// EWA 2D covariance Sigma' = (J W) Sigma (J W)^T + dilation I with J the
+// Jacobian of the pinhole map at c, conic A = Sigma'^{-1}, projected mean
+// mu' = (fx c_x/c_z + cx, fy c_y/c_z + cy), and the screen tiles its support
+// {u : alpha exp(-q(u)/2) >= alpha_min}, q = (u-mu')^T A (u-mu'), can reach.
+//
+// GB300 design: one thread per Gaussian in two stages.  Stage A is a cheap
+// FP32 bound on the footprint that rejects Gaussians that cannot reach the
+// screen; survivors are compacted inside the CTA through shared memory so
+// that stage B -- the exact projection in compensated double-FP32 arithmetic
+// (about 600 FP32 instructions) -- runs on full warps.  Stage B is what makes
+// the per-pixel alpha' agree with an FP64 evaluation to ~1e-6 relative: the
+// projected mean is kept as an unevaluated pair hi + lo, so the pixel offset
+// u - mu' loses nothing even 1000 px from the origin.
+#include "qr_internal.cuh"
+
+namespace qr {
+namespace {
+
+constexpr int kThreads = 256;
+
+struct CamArgs {
+    float R[9], t[3], fx, fy, cx, cy, znear;
+    int W, H;
+};
+
+__device__ __forceinline__ void write_culled(int64_t g, uint32_t *dkey, uint32_t *tcount,
+                                             uint2 *rect) {
+    dkey[g] = 0xFFFFFFFFu;
+    tcount[g] = 0u;
+    rect[g] = make_uint2(0u, 0u);
+}
+
+__global__ void __launch_bounds__(kThreads)
+project_kernel(int64_t n, const float *__restrict__ mean, const float *__restrict__ log_scale,
+               const float *__restrict__ quat, const float *__restrict__ opacity, CamArgs cam,
+               float dilation, float alpha_min, int tile_w, int tile_h, int tiles_x,
+               int tiles_y, float4 *__restrict__ rec_m, float4 *__restrict__ rec_c,
+               uint2 *__restrict__ rect, uint32_t *__restrict__ tcount,
+               uint32_t *__restrict__ dkey, uint32_t *__restrict__ dval,
+               uint32_t *__restrict__ counters) {
+    __shared__ int s_list[kThreads];
+    __shared__ int s_warp[kThreads / 32];
+    __shared__ int s_visible;
+
+    const int64_t base = int64_t(blockIdx.x) * kThreads;
+    const int64_t g = base + threadIdx.x;
+    if (threadIdx.x == 0) s_visible = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) counters[CNT_N] = uint32_t(n);
+
+    // ---------------- stage A: FP32 conservative footprint bound
+    bool cand = false;
+    if (g < n) {
+        dval[g] = uint32_t(g);
+        const float mx = mean[3 * g], my = mean[3 * g + 1], mz = mean[3 * g + 2];
+        const float alpha = opacity[g];
+        const float cz = fmaf(cam.R[6], mx, fmaf(cam.R[7], my, fmaf(cam.R[8], mz, cam.t[2])));
+        if (alpha >= alpha_min && cz > cam.znear - 1e-3f) {
+            const float cx_ = fmaf(cam.R[0], mx, fmaf(cam.R[1], my, fmaf(cam.R[2], mz, cam.t[0])));
+            const float cy_ = fmaf(cam.R[3], mx, fmaf(cam.R[4], my, fmaf(cam.R[5], mz, cam.t[1])));
+            const float zz = fmaxf(cz, 0.5f * cam.znear);
+            const float u = cx_ / zz, v = cy_ / zz;
+            const float smax = __expf(fmaxf(log_scale[3 * g], fmaxf(log_scale[3 * g + 1],
+                                                                   log_scale[3 * g + 2])));
+            const float r2 = 2.0f * __logf(fmaxf(alpha / alpha_min, 1.0f));
+            // Sigma'_00 <= smax^2 |J_x|^2 + dilation with |J_x| = fx/z sqrt(1+u^2)
+            const float jx = cam.fx / zz, jy = cam.fy / zz;
+            const float ex = sqrtf(r2 * (smax * smax * jx * jx * (1.f + u * u) + dilation)) * 1.01f + 2.f;
+            const float ey = sqrtf(r2 * (smax * smax * jy * jy * (1.f + v * v) + dilation)) * 1.01f + 2.f;
+            const float px = fmaf(cam.fx, u, cam.cx), py = fmaf(cam.fy, v, cam.cy);
+            const float tol = 1e-3f * (fabsf(px) + fabsf(py)) + 2.f;
+            cand = (px + ex + tol >= 0.f) && (px - ex - tol <= float(cam.W)) &&
+                   (py + ey + tol >= 0.f) && (py - ey - tol <= float(cam.H));
+        }
+        if (!cand) write_culled(g, dkey, tcount, rect);
+    }
+
+    // ---------------- compact the survivors of this CTA
+    const unsigned ballot = __ballot_sync(0xffffffffu, cand);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) s_warp[warp] = __popc(ballot);
+    __syncthreads();
+    int before = 0, total = 0;
+#pragma unroll
+    for (int w = 0; w < kThreads / 32; ++w) {
+        before += (w < warp) ? s_warp[w] : 0;
+        total += s_warp[w];
+    }
+    if (cand) s_list[before + __popc(ballot & ((1u << lane) - 1u))] = threadIdx.x;
+    __syncthreads();
+
+    // ---------------- stage B: exact projection of the survivors
+    int visible = 0;
+    for (int i = threadIdx.x; i < total; i += kThreads) {
+        const int64_t gi = base + s_list[i];
+        const float mx = mean[3 * gi], my = mean[3 * gi + 1], mz = mean[3 * gi + 2];
+        const float alpha = opacity[gi];
+        // c = R mu + t
+        df c[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+            c[r] = df_add(df_add(df_add(df_two_prod(cam.R[3 * r], mx), df_two_prod(cam.R[3 * r + 1], my)),
+                                 df_two_prod(cam.R[3 * r + 2], mz)),
+                          df_from(cam.t[r]));
+        if (!(c[2].hi > cam.znear || (c[2].hi == cam.znear && c[2].lo > 0.f))) {
+            write_culled(gi, dkey, tcount, rect);
+            continue;
+        }
+        // homogeneous rotation of the (unnormalised) quaternion: Rq = M / |q|^2
+        const float qw = quat[4 * gi], qx = quat[4 * gi + 1], qy = quat[4 * gi + 2], qz = quat[4 * gi + 3];
+        const df ww = df_two_prod(qw, qw), xx = df_two_prod(qx, qx), yy = df_two_prod(qy, qy),
+                 zz = df_two_prod(qz, qz);
+        const df xy = df_two_prod(qx, qy), xz = df_two_prod(qx, qz), yz = df_two_prod(qy, qz),
+                 wx = df_two_prod(qw, qx), wy = df_two_prod(qw, qy), wz = df_two_prod(qw, qz);
+        df M[9];
+        M[0] = df_sub(df_add(ww, xx), df_add(yy, zz));
+        M[4] = df_sub(df_add(ww, yy), df_add(xx, zz));
+        M[8] = df_sub(df_add(ww, zz), df_add(xx, yy));
+        M[1] = df_mul_f(df_sub(xy, wz), 2.f);
+        M[2] = df_mul_f(df_add(xz, wy), 2.f);
+        M[3] = df_mul_f(df_add(xy, wz), 2.f);
+        M[5] = df_mul_f(df_sub(yz, wx), 2.f);
+        M[6] = df_mul_f(df_sub(xz, wy), 2.f);
+        M[7] = df_mul_f(df_add(yz, wx), 2.f);
+        const df qn = df_add(df_add(ww, xx), df_add(yy, zz));
+        // J W: rows (fx/z)(W0 - u W2), (fy/z)(W1 - v W2) with u = x/z, v = y/z
+        const df iz = df_div(df_from(1.f), c[2]);
+        const df u = df_mul(c[0], iz), v = df_mul(c[1], iz);
+        const df jx = df_mul_f(iz, cam.fx), jy = df_mul_f(iz, cam.fy);
+        df T0[3], T1[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            T0[k] = df_mul(jx, df_sub(df_from(cam.R[k]), df_mul_f(u, cam.R[6 + k])));
+            T1[k] = df_mul(jy, df_sub(df_from(cam.R[3 + k]), df_mul_f(v, cam.R[6 + k])));
+        }
+        // P = (J W) M ; Sigma' = P diag(s^2) P^T / |q|^4
+        df P0[3], P1[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            P0[k] = df_dot3(T0[0], M[k], T0[1], M[3 + k], T0[2], M[6 + k]);
+            P1[k] = df_dot3(T1[0], M[k], T1[1], M[3 + k], T1[2], M[6 + k]);
+        }
+        df s00 = df_from(0.f), s01 = df_from(0.f), s11 = df_from(0.f);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float sk = expf(log_scale[3 * gi + k]);
+            const df sk2 = df_two_prod(sk, sk);
+            const df a0 = df_mul(P0[k], sk2);
+            s00 = df_add(s00, df_mul(a0, P0[k]));
+            s01 = df_add(s01, df_mul(a0, P1[k]));
+            s11 = df_add(s11, df_mul(df_mul(P1[k], sk2), P1[k]));
+        }
+        const df inq2 = df_div(df_from(1.f), df_mul(qn, qn));
+        s00 = df_add_f(df_mul(s00, inq2), dilation);
+        s01 = df_mul(s01, inq2);
+        s11 = df_add_f(df_mul(s11, inq2), dilation);
+        const df det = df_sub(df_mul(s00, s11), df_mul(s01, s01));
+        if (!(det.hi > 0.f)) {
+            write_culled(gi, dkey, tcount, rect);
+            continue;
+        }
+        const df idet = df_div(df_from(1.f), det);
+        const float A00 = df_mul(s11, idet).hi;
+        const float A01 = -df_mul(s01, idet).hi;
+        const float A11 = df_mul(s00, idet).hi;
+        const df mxp = df_add_f(df_mul_f(u, cam.fx), cam.cx);
+        const df myp = df_add_f(df_mul_f(v, cam.fy), cam.cy);
+
+        // footprint: q <= r^2 = 2 ln(alpha/alpha_min); extent r sqrt(Sigma'_ii); 1 px pad
+        const float r = sqrtf(2.0f * logf(fmaxf(alpha / alpha_min, 1.0f))) * 1.0001f;
+        float ex = r * sqrtf(s00.hi), ey = r * sqrtf(s11.hi);
+        if (!(isfinite(mxp.hi) && isfinite(myp.hi) && ex >= 0.f && ey >= 0.f)) {
+            write_culled(gi, dkey, tcount, rect);
+            continue;
+        }
+        ex = fminf(ex, 1e7f);
+        ey = fminf(ey, 1e7f);
+        const float x0f = floorf(mxp.hi - ex - 1.5f), x1f = floorf(mxp.hi + ex + 0.5f);
+        const float y0f = floorf(myp.hi - ey - 1.5f), y1f = floorf(myp.hi + ey + 0.5f);
+        const int x0 = int(fmaxf(x0f, 0.f)), x1 = int(fminf(x1f, float(cam.W - 1)));
+        const int y0 = int(fmaxf(y0f, 0.f)), y1 = int(fminf(y1f, float(cam.H - 1)));
+        if (x1f < 0.f || y1f < 0.f || x0f > float(cam.W - 1) || y0f > float(cam.H - 1) ||
+            x0 > x1 || y0 > y1) {
+            write_culled(gi, dkey, tcount, rect);
+            continue;
+        }
+        const int tx0 = x0 / tile_w, tx1 = x1 / tile_w, ty0 = y0 / tile_h, ty1 = y1 / tile_h;
+        rec_m[gi] = make_float4(mxp.hi, myp.hi, mxp.lo, myp.lo);
+        rec_c[gi] = make_float4(A00, A01, A11, alpha);
+        rect[gi] = make_uint2(uint32_t(tx0) | (uint32_t(ty0) << 16), uint32_t(tx1) | (uint32_t(ty1) << 16));
+        tcount[gi] = uint32_t((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
+        dkey[gi] = __float_as_uint(c[2].hi);
+        ++visible;
+    }
+    // block-aggregated visible count
+    for (int o = 16; o > 0; o >>= 1) visible += __shfl_xor_sync(0xffffffffu, visible, o);
+    if (lane == 0 && visible) atomicAdd(&s_visible, visible);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_visible) atomicAdd(&counters[CNT_VISIBLE], uint32_t(s_visible));
+    (void)tiles_x;
+    (void)tiles_y;
+}
+
+}  // namespace
+
+cudaError_t launch_project(const qr_frame &f, const float *mean, const float *log_scale,
+                           const float *quat, const float *opacity, cudaStream_t s) {
+    const int64_t n = f.n;
+    uint32_t *counters = slot<uint32_t>(f, S_COUNTERS);
+    cudaError_t e = cudaMemsetAsync(counters, 0, CNT_WORDS * sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    if (n == 0) return cudaSuccess;
+    CamArgs cam;
+    for (int i = 0; i < 9; ++i) cam.R[i] = f.camera.R[i];
+    for (int i = 0; i < 3; ++i) cam.t[i] = f.camera.t[i];
+    cam.fx = f.camera.fx; cam.fy = f.camera.fy; cam.cx = f.camera.cx; cam.cy = f.camera.cy;
+    cam.znear = f.camera.near_plane; cam.W = f.camera.width; cam.H = f.camera.height;
+    const unsigned blocks = unsigned((n + kThreads - 1) / kThreads);
+    project_kernel<<<blocks, kThreads, 0, s>>>(
+        n, mean, log_scale, quat, opacity, cam, f.params.dilation, f.params.alpha_min,
+        f.params.tile_w, f.params.tile_h, f.tiles_x, f.tiles_y, slot<float4>(f, S_REC_M),
+        slot<float4>(f, S_REC_C), slot<uint2>(f, S_RECT), slot<uint32_t>(f, S_TCOUNT),
+        slot<uint32_t>(f, S_DKEY0), slot<uint32_t>(f, S_DVAL0), counters);
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace qr

@@ -1,0 +1,141 @@
+// Internal declarations shared by the libqrender translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/qrender.h"
+
+namespace qr {
+
+// ---------------------------------------------------------------- status word
+// counters[0]: device status (a qr_status value, 0 = OK)
+// counters[1]: number of tile-Gaussian intersections the frame needs
+// counters[2]: number of Gaussians with a non-empty footprint
+// counters[3]: number of Gaussians n (item count of the depth sort)
+// counters[4]: number of intersections actually emitted (0 on overflow)
+enum { CNT_STATUS = 0, CNT_ISECT = 1, CNT_VISIBLE = 2, CNT_N = 3, CNT_SORT_N = 4, CNT_WORDS = 8 };
+
+// Workspace slots (byte offsets in qr_frame::off).
+enum Slot {
+    S_COUNTERS = 0, S_REC_M, S_REC_C, S_RECT, S_TCOUNT,
+    S_DKEY0, S_DKEY1, S_DVAL0, S_DVAL1,
+    S_IKEY0, S_IKEY1, S_IVAL0, S_IVAL1,
+    S_RANGES, S_HIST, S_BLOCKSUM,
+    S_END
+};
+static_assert(S_END <= QR_FRAME_SLOTS, "too many workspace slots");
+
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 8;                       // items per thread per tile
+constexpr int kSortTile = kSortThreads * kSortItems; // 2048
+constexpr int kSortMaxBlocks = 304;                 // 2 per SM on a 152-SM GB300
+constexpr int kRadixBitsMax = 8;
+constexpr int kKMax = 32;
+
+// Launch counter (all TUs add to it).
+void count_launch(int n = 1);
+
+template <typename T>
+__host__ __device__ inline T *slot(void *ws, const qr_frame &f, Slot s) {
+    return reinterpret_cast<T *>(static_cast<char *>(ws) + f.off[s]);
+}
+template <typename T>
+inline T *slot(const qr_frame &f, Slot s) {
+    return reinterpret_cast<T *>(static_cast<char *>(f.ws) + f.off[s]);
+}
+
+inline int64_t num_pixels(const qr_frame &f) {
+    return int64_t(f.camera.width) * int64_t(f.camera.height);
+}
+inline int32_t num_tiles(const qr_frame &f) { return f.tiles_x * f.tiles_y; }
+
+// ---------------------------------------------------------------- launchers
+cudaError_t launch_project(const qr_frame &f, const float *mean, const float *log_scale,
+                           const float *quat, const float *opacity, cudaStream_t s);
+cudaError_t launch_sort(const qr_frame &f, cudaStream_t s);
+cudaError_t launch_select(const qr_frame &f, int32_t *ids, float *w, uint8_t *cnt,
+                          cudaStream_t s);
+cudaError_t launch_dense(const qr_frame &f, const void *feat, const float *scale, qr_dtype dt,
+                         int C, float *out, float *T_final, cudaStream_t s);
+
+// Generic pieces of the sort, reused by later stages.
+// Stable LSD radix sort of (key, val) pairs; count read from the device.
+// Sorts bits [bit_lo, bit_hi) of the keys; returns through *out_keys/*out_vals
+// which of the two buffers holds the result (0 = buffers "a", 1 = "b").
+cudaError_t radix_sort_pairs(uint32_t *keys_a, uint32_t *vals_a, uint32_t *keys_b,
+                             uint32_t *vals_b, const uint32_t *d_count, int64_t capacity,
+                             int bit_lo, int bit_hi, uint32_t *hist, int blocks,
+                             int *result_in_b, cudaStream_t s);
+
+int sort_blocks_for(int64_t capacity);
+int tile_bits_for(int tiles);
+
+// ---------------------------------------------------------------- compensated arithmetic
+// Pairs (hi, lo) of FP32 with |lo| <= ulp(hi)/2 represent hi + lo exactly;
+// the error-free transformations are Knuth's TwoSum, Dekker's FastTwoSum and
+// the FMA-based TwoProduct; division is Dekker's long division with two
+// correction steps.  Explicit _rn intrinsics keep nvcc from contracting or
+// reassociating them.
+struct df {
+    float hi, lo;
+};
+
+__device__ __forceinline__ df df_two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+__device__ __forceinline__ df df_fast_two_sum(float a, float b) {  // needs |a| >= |b| or a == 0
+    float s = __fadd_rn(a, b);
+    float e = __fsub_rn(b, __fsub_rn(s, a));
+    return {s, e};
+}
+__device__ __forceinline__ df df_two_prod(float a, float b) {
+    float p = __fmul_rn(a, b);
+    float e = __fmaf_rn(a, b, -p);
+    return {p, e};
+}
+__device__ __forceinline__ df df_from(float a) { return {a, 0.0f}; }
+__device__ __forceinline__ df df_neg(df a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ df df_add(df a, df b) {
+    df s = df_two_sum(a.hi, b.hi);
+    df t = df_two_sum(a.lo, b.lo);
+    s.lo = __fadd_rn(s.lo, t.hi);
+    s = df_fast_two_sum(s.hi, s.lo);
+    s.lo = __fadd_rn(s.lo, t.lo);
+    return df_fast_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, df_neg(b)); }
+__device__ __forceinline__ df df_add_f(df a, float b) {
+    df s = df_two_sum(a.hi, b);
+    s.lo = __fadd_rn(s.lo, a.lo);
+    return df_fast_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ df df_mul(df a, df b) {
+    df p = df_two_prod(a.hi, b.hi);
+    p.lo = __fmaf_rn(a.hi, b.lo, p.lo);
+    p.lo = __fmaf_rn(a.lo, b.hi, p.lo);
+    return df_fast_two_sum(p.hi, p.lo);
+}
+__device__ __forceinline__ df df_mul_f(df a, float b) {
+    df p = df_two_prod(a.hi, b);
+    p.lo = __fmaf_rn(a.lo, b, p.lo);
+    return df_fast_two_sum(p.hi, p.lo);
+}
+__device__ __forceinline__ df df_div(df a, df b) {
+    float q1 = __fdiv_rn(a.hi, b.hi);
+    df r = df_sub(a, df_mul_f(b, q1));
+    float q2 = __fdiv_rn(r.hi, b.hi);
+    r = df_sub(r, df_mul_f(b, q2));
+    float q3 = __fdiv_rn(r.hi, b.hi);
+    df q = df_fast_two_sum(q1, q2);
+    return df_add_f(q, q3);
+}
+// a*b + c*d + e*f + g (sum of three products plus a term), all in df.
+__device__ __forceinline__ df df_dot3(df a, df b, df c, df d, df e, df f) {
+    return df_add(df_add(df_mul(a, b), df_mul(c, d)), df_mul(e, f));
+}
+
+}  // namespace qr

@@ -1,0 +1,353 @@
+// K2-K4: binning, radix sort and tile ranges (Sec. 3 "tiling strategy"; the
+// depth-ordered index list I of Sec. 4.2).
+//
+// Order produced: intersections sorted by (tile id, depth, Gaussian id), the
+// order of a stable sort of 64-bit (tile << 32 | depth-bits) keys over
+// id-ordered input.  It is built as
+//   1. a stable LSD radix sort of the N 32-bit depth keys (ids as values),
+//   2. an exclusive scan of the per-Gaussian tile counts in that order and an
+//      emit of one (tile, id) pair per touched tile, in depth order,
+//   3. a stable LSD radix sort of the X intersections by tile id only
+//      (ceil(log2 tiles) bits, <= 8 bits per pass).
+// The depth digits are therefore sorted once per Gaussian instead of once per
+// intersection -- the lower-digit passes of the 64-bit LSD sort hoisted in
+// front of the duplication, which preserves relative order.
+//
+// Every pass is reduce-then-scan: per-block digit histograms, one scan of the
+// [digit][block] table, then a stable scatter.  No CTA ever waits for another,
+// so nothing here can spin.  Item counts are read from device memory, so the
+// whole stage can be captured in a CUDA graph with worst-case grids.
+#include "qr_internal.cuh"
+
+namespace qr {
+namespace {
+
+constexpr int T = kSortThreads;      // 256
+constexpr int IPT = kSortItems;      // 8
+constexpr int TILE = kSortTile;      // 2048
+constexpr int WARPS = T / 32;
+
+__device__ __forceinline__ void block_tiles(uint32_t n, int b, int nb, uint32_t &t0, uint32_t &t1) {
+    const uint32_t tiles = (n + TILE - 1) / TILE;
+    const uint32_t per = (tiles + nb - 1) / nb;
+    t0 = min(tiles, uint32_t(b) * per);
+    t1 = min(tiles, t0 + per);
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// ------------------------------------------------------------------ radix pass
+__global__ void __launch_bounds__(T)
+radix_upsweep(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ d_count, int shift,
+              int bits, uint32_t *__restrict__ hist) {
+    __shared__ uint32_t s_h[WARPS][1 << kRadixBitsMax];
+    const int radix = 1 << bits;
+    const uint32_t mask = uint32_t(radix - 1);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < WARPS * radix; i += T) (&s_h[0][0])[(i / radix) * (1 << kRadixBitsMax) + i % radix] = 0;
+    __syncthreads();
+    const uint32_t n = *d_count;
+    uint32_t t0, t1;
+    block_tiles(n, blockIdx.x, gridDim.x, t0, t1);
+    const uint32_t end = min(n, t1 * TILE);
+    for (uint32_t base = t0 * TILE; base < end; base += T) {   // uniform trip count
+        const uint32_t i = base + threadIdx.x;
+        const bool valid = i < end;
+        const uint32_t d = valid ? (keys[i] >> shift) & mask : 0xFFFFFFFFu;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        if (valid && lane == __ffs(peers) - 1) atomicAdd(&s_h[warp][d], uint32_t(__popc(peers)));
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < radix; d += T) {
+        uint32_t s = 0;
+#pragma unroll
+        for (int w = 0; w < WARPS; ++w) s += s_h[w][d];
+        hist[d * gridDim.x + blockIdx.x] = s;
+    }
+}
+
+// exclusive scan of `total` u32 in place by one CTA of 1024 threads;
+// optionally stores the grand total in *sum_out.
+__device__ void cta_exclusive_scan(uint32_t *data, int total, uint32_t *sum_out) {
+    __shared__ uint32_t s_w[32];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int per = (total + nt - 1) / nt;
+    const int a = min(total, tid * per), b = min(total, a + per);
+    uint32_t s = 0;
+    for (int i = a; i < b; ++i) s += data[i];
+    // block exclusive scan of s
+    const int lane = tid & 31, warp = tid >> 5;
+    uint32_t x = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_w[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = (lane < nt / 32) ? s_w[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        s_w[lane] = w;
+    }
+    __syncthreads();
+    uint32_t run = x - s + (warp > 0 ? s_w[warp - 1] : 0);
+    for (int i = a; i < b; ++i) {
+        const uint32_t v = data[i];
+        data[i] = run;
+        run += v;
+    }
+    if (sum_out && tid == nt - 1) *sum_out = run;
+}
+
+__global__ void __launch_bounds__(1024) radix_scan(uint32_t *hist, int total) {
+    cta_exclusive_scan(hist, total, nullptr);
+}
+
+__global__ void __launch_bounds__(T)
+radix_downsweep(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
+                uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out,
+                const uint32_t *__restrict__ d_count, int shift, int bits,
+                const uint32_t *__restrict__ hist) {
+    __shared__ uint32_t s_base[1 << kRadixBitsMax];
+    __shared__ uint32_t s_tot[1 << kRadixBitsMax];
+    __shared__ uint32_t s_w[WARPS][1 << kRadixBitsMax];
+    const int radix = 1 << bits;
+    const uint32_t mask = uint32_t(radix - 1);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt = lanemask_lt();
+    for (int d = threadIdx.x; d < radix; d += T) s_base[d] = hist[d * gridDim.x + blockIdx.x];
+    const uint32_t n = *d_count;
+    uint32_t t0, t1;
+    block_tiles(n, blockIdx.x, gridDim.x, t0, t1);
+    for (uint32_t tile = t0; tile < t1; ++tile) {
+        for (int i = threadIdx.x; i < WARPS * radix; i += T) s_w[i / radix][i % radix] = 0;
+        __syncthreads();
+        uint32_t key[IPT], val[IPT], rank[IPT], dig[IPT];
+        const uint32_t wbase = tile * TILE + warp * (32 * IPT);
+#pragma unroll
+        for (int r = 0; r < IPT; ++r) {
+            const uint32_t idx = wbase + r * 32 + lane;
+            const bool valid = idx < n;
+            key[r] = valid ? keys_in[idx] : 0u;
+            val[r] = valid ? vals_in[idx] : 0u;
+            dig[r] = valid ? (key[r] >> shift) & mask : 0xFFFFFFFFu;
+            const unsigned peers = __match_any_sync(0xffffffffu, dig[r]);
+            const uint32_t before = valid ? s_w[warp][dig[r]] : 0u;
+            rank[r] = before + __popc(peers & lt);
+            __syncwarp();
+            if (valid && lane == __ffs(peers) - 1) s_w[warp][dig[r]] = before + __popc(peers);
+            __syncwarp();
+        }
+        __syncthreads();
+        for (int d = threadIdx.x; d < radix; d += T) {
+            uint32_t run = 0;
+#pragma unroll
+            for (int w = 0; w < WARPS; ++w) {
+                const uint32_t c = s_w[w][d];
+                s_w[w][d] = run;
+                run += c;
+            }
+            s_tot[d] = run;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < IPT; ++r) {
+            if (dig[r] != 0xFFFFFFFFu) {
+                const uint32_t pos = s_base[dig[r]] + s_w[warp][dig[r]] + rank[r];
+                keys_out[pos] = key[r];
+                vals_out[pos] = val[r];
+            }
+        }
+        __syncthreads();
+        for (int d = threadIdx.x; d < radix; d += T) s_base[d] += s_tot[d];
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ emit
+// Block sums of the tile counts taken in depth order.
+__global__ void __launch_bounds__(T)
+emit_upsweep(const uint32_t *__restrict__ sorted_gid, const uint32_t *__restrict__ tcount,
+             const uint32_t *__restrict__ d_n, uint32_t *__restrict__ blocksum) {
+    __shared__ uint32_t s_w[WARPS];
+    const uint32_t n = *d_n;
+    uint32_t t0, t1;
+    block_tiles(n, blockIdx.x, gridDim.x, t0, t1);
+    const uint32_t end = min(n, t1 * TILE);
+    uint32_t s = 0;
+    for (uint32_t i = t0 * TILE + threadIdx.x; i < end; i += T) s += tcount[sorted_gid[i]];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int w = 0; w < WARPS; ++w) t += s_w[w];
+        blocksum[blockIdx.x] = t;
+    }
+}
+
+// Scan of the block sums; writes the intersection count and the capacity check.
+__global__ void __launch_bounds__(1024)
+emit_scan(uint32_t *blocksum, int nblocks, uint32_t *counters, uint32_t capacity) {
+    __shared__ uint32_t s_total;
+    cta_exclusive_scan(blocksum, nblocks, &s_total);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint32_t x = s_total;
+        counters[CNT_ISECT] = x;
+        if (x > capacity) {
+            counters[CNT_STATUS] = QR_ERR_CAPACITY;
+            counters[CNT_SORT_N] = 0;
+        } else {
+            counters[CNT_SORT_N] = x;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(T)
+emit_pairs(const uint32_t *__restrict__ sorted_gid, const uint32_t *__restrict__ tcount,
+           const uint2 *__restrict__ rect, const uint32_t *__restrict__ d_n,
+           const uint32_t *__restrict__ blocksum, const uint32_t *__restrict__ counters,
+           int tiles_x, uint32_t *__restrict__ ikey, uint32_t *__restrict__ ival) {
+    __shared__ uint32_t s_w[WARPS];
+    __shared__ uint32_t s_run;
+    if (counters[CNT_STATUS] != 0) return;  // capacity exceeded: emit nothing
+    const uint32_t n = *d_n;
+    uint32_t t0, t1;
+    block_tiles(n, blockIdx.x, gridDim.x, t0, t1);
+    const uint32_t end = min(n, t1 * TILE);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_run = blocksum[blockIdx.x];
+    __syncthreads();
+    for (uint32_t base = t0 * TILE; base < end; base += T) {
+        const uint32_t i = base + threadIdx.x;
+        const uint32_t g = i < end ? sorted_gid[i] : 0u;
+        const uint32_t c = i < end ? tcount[g] : 0u;
+        uint32_t x = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_w[warp] = x;
+        __syncthreads();
+        uint32_t off = s_run + x - c;
+        for (int w = 0; w < warp; ++w) off += s_w[w];
+        if (c) {
+            const uint2 rc = rect[g];
+            const int tx0 = rc.x & 0xFFFF, ty0 = rc.x >> 16, tx1 = rc.y & 0xFFFF, ty1 = rc.y >> 16;
+            for (int ty = ty0; ty <= ty1; ++ty)
+                for (int tx = tx0; tx <= tx1; ++tx) {
+                    ikey[off] = uint32_t(ty * tiles_x + tx);
+                    ival[off] = g;
+                    ++off;
+                }
+        }
+        __syncthreads();
+        if (threadIdx.x == T - 1) {
+            uint32_t t = 0;
+            for (int w = 0; w < WARPS; ++w) t += s_w[w];
+            s_run += t;
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ ranges
+__global__ void __launch_bounds__(T)
+tile_ranges(const uint32_t *__restrict__ ikey, const uint32_t *__restrict__ counters,
+            uint2 *__restrict__ ranges) {
+    const uint32_t n = counters[CNT_SORT_N];
+    for (uint32_t i = blockIdx.x * T + threadIdx.x; i < n; i += gridDim.x * T) {
+        const uint32_t t = ikey[i];
+        if (i == 0 || ikey[i - 1] != t) ranges[t].x = i;
+        if (i + 1 == n || ikey[i + 1] != t) ranges[t].y = i + 1;
+    }
+}
+
+}  // namespace
+
+int sort_blocks_for(int64_t capacity) {
+    const int64_t tiles = (capacity + TILE - 1) / TILE;
+    return int(tiles < 1 ? 1 : (tiles > kSortMaxBlocks ? kSortMaxBlocks : tiles));
+}
+
+cudaError_t radix_sort_pairs(uint32_t *keys_a, uint32_t *vals_a, uint32_t *keys_b,
+                             uint32_t *vals_b, const uint32_t *d_count, int64_t capacity,
+                             int bit_lo, int bit_hi, uint32_t *hist, int blocks,
+                             int *result_in_b, cudaStream_t s) {
+    (void)capacity;
+    int in_b = 0;
+    for (int lo = bit_lo; lo < bit_hi;) {
+        const int remaining = bit_hi - lo;
+        const int passes_left = (remaining + kRadixBitsMax - 1) / kRadixBitsMax;
+        const int bits = (remaining + passes_left - 1) / passes_left;
+        uint32_t *ki = in_b ? keys_b : keys_a, *vi = in_b ? vals_b : vals_a;
+        uint32_t *ko = in_b ? keys_a : keys_b, *vo = in_b ? vals_a : vals_b;
+        radix_upsweep<<<blocks, T, 0, s>>>(ki, d_count, lo, bits, hist);
+        radix_scan<<<1, 1024, 0, s>>>(hist, (1 << bits) * blocks);
+        radix_downsweep<<<blocks, T, 0, s>>>(ki, vi, ko, vo, d_count, lo, bits, hist);
+        count_launch(3);
+        in_b ^= 1;
+        lo += bits;
+    }
+    if (result_in_b) *result_in_b = in_b;
+    return cudaGetLastError();
+}
+
+int tile_bits_for(int tiles) {
+    int b = 1;
+    while ((1 << b) < tiles) ++b;
+    return b;
+}
+
+cudaError_t launch_sort(const qr_frame &f, cudaStream_t s) {
+    uint32_t *counters = slot<uint32_t>(f, S_COUNTERS);
+    uint32_t *hist = slot<uint32_t>(f, S_HIST);
+    const int tiles = num_tiles(f);
+    cudaError_t e = cudaMemsetAsync(slot<uint2>(f, S_RANGES), 0, sizeof(uint2) * size_t(tiles), s);
+    if (e != cudaSuccess) return e;
+    if (f.n == 0) return cudaSuccess;
+    // 1. depth sort of all n Gaussians (culled ones carry key 0xFFFFFFFF and sort last)
+    const int nb_depth = sort_blocks_for(f.n);
+    int in_b = 0;
+    e = radix_sort_pairs(slot<uint32_t>(f, S_DKEY0), slot<uint32_t>(f, S_DVAL0),
+                         slot<uint32_t>(f, S_DKEY1), slot<uint32_t>(f, S_DVAL1),
+                         counters + CNT_N, f.n, 0, 32, hist, nb_depth, &in_b, s);
+    if (e != cudaSuccess) return e;
+    const uint32_t *sorted_gid = slot<uint32_t>(f, in_b ? S_DVAL1 : S_DVAL0);
+    // 2. scan of tile counts in depth order + emit
+    uint32_t *blocksum = slot<uint32_t>(f, S_BLOCKSUM);
+    emit_upsweep<<<nb_depth, T, 0, s>>>(sorted_gid, slot<uint32_t>(f, S_TCOUNT), counters + CNT_N,
+                                        blocksum);
+    emit_scan<<<1, 1024, 0, s>>>(blocksum, nb_depth, counters, uint32_t(f.max_isect));
+    emit_pairs<<<nb_depth, T, 0, s>>>(sorted_gid, slot<uint32_t>(f, S_TCOUNT),
+                                      slot<uint2>(f, S_RECT), counters + CNT_N, blocksum, counters,
+                                      f.tiles_x, slot<uint32_t>(f, S_IKEY0),
+                                      slot<uint32_t>(f, S_IVAL0));
+    count_launch(3);
+    // 3. stable sort of the intersections by tile id
+    int ib = 0;
+    e = radix_sort_pairs(slot<uint32_t>(f, S_IKEY0), slot<uint32_t>(f, S_IVAL0),
+                         slot<uint32_t>(f, S_IKEY1), slot<uint32_t>(f, S_IVAL1),
+                         counters + CNT_SORT_N, f.max_isect, 0, tile_bits_for(tiles), hist,
+                         f.sort_blocks, &ib, s);
+    if (e != cudaSuccess) return e;
+    // 4. tile ranges
+    const uint32_t *ikey = slot<uint32_t>(f, ib ? S_IKEY1 : S_IKEY0);
+    const int rb = 2 * 152 * 4;
+    tile_ranges<<<rb, T, 0, s>>>(ikey, counters, slot<uint2>(f, S_RANGES));
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace qr

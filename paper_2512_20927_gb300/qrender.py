@@ -1,0 +1,340 @@
+"""Thin ctypes binding of libqrender (include/qrender.h).
+
+Argument marshalling only: every step of the render runs in the library's
+CUDA kernels.  PyTorch provides device memory (the workspace and the output
+tensors) and the current CUDA stream.  The functions keep the C names.
+
+The library must have been built (``__graft_entry__.build()`` or
+``python -m paper_2512_20927_gb300.build_lib``); loading fails loudly
+otherwise -- there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libqrender.so")
+
+QR_OK, QR_ERR_INVALID_ARG, QR_ERR_ALIGNMENT, QR_ERR_CAPACITY, QR_ERR_CUDA, \
+    QR_ERR_DEVICE_TIMEOUT, QR_ERR_NOT_SUPPORTED = range(7)
+QR_F32, QR_BF16, QR_FP8E4M3 = 0, 1, 2
+FRAME_SLOTS = 24
+
+
+class QRError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {status_string(code)} ({code})")
+
+
+class qr_camera(ctypes.Structure):
+    _fields_ = [("R", ctypes.c_float * 9), ("t", ctypes.c_float * 3), ("fx", ctypes.c_float),
+                ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float),
+                ("near_plane", ctypes.c_float), ("width", ctypes.c_int32),
+                ("height", ctypes.c_int32)]
+
+
+class qr_params(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int32), ("alpha_min", ctypes.c_float),
+                ("alpha_max", ctypes.c_float), ("T_min", ctypes.c_float),
+                ("dilation", ctypes.c_float), ("tile_w", ctypes.c_int32),
+                ("tile_h", ctypes.c_int32)]
+
+
+class qr_frame(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("max_isect", ctypes.c_int64), ("camera", qr_camera),
+                ("params", qr_params), ("tiles_x", ctypes.c_int32), ("tiles_y", ctypes.c_int32),
+                ("sort_blocks", ctypes.c_int32), ("isect_buf", ctypes.c_int32),
+                ("ws", ctypes.c_void_p), ("ws_bytes", ctypes.c_size_t),
+                ("off", ctypes.c_size_t * FRAME_SLOTS)]
+
+
+class qr_frame_view(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_void_p) for name in (
+        "mean2d_hi_lo", "conic_alpha", "depth_key", "tile_count", "sorted_gid", "isect_tile",
+        "isect_gid", "tile_range", "counters")]
+
+
+_P = ctypes.c_void_p
+_I32 = ctypes.c_int32
+_I64 = ctypes.c_int64
+_S = ctypes.c_int
+
+# name -> (restype, argtypes); every function declared in include/qrender.h
+SIGNATURES = {
+    "qr_abi_version": (_I32, []),
+    "qr_status_string": (ctypes.c_char_p, [_S]),
+    "qr_default_params": (None, [ctypes.POINTER(qr_params)]),
+    "qr_workspace_bytes": (ctypes.c_size_t, [_I64, _I32, _I32, ctypes.POINTER(qr_params), _I64]),
+    "qr_frame_init": (_S, [ctypes.POINTER(qr_frame), _I64, ctypes.POINTER(qr_camera),
+                           ctypes.POINTER(qr_params), _I64, _P, ctypes.c_size_t]),
+    "qr_frame_view_get": (_S, [ctypes.POINTER(qr_frame), ctypes.POINTER(qr_frame_view)]),
+    "qr_frame_status": (_S, [ctypes.POINTER(qr_frame), _P, ctypes.POINTER(_I64)]),
+    "qr_project": (_S, [ctypes.POINTER(qr_frame), _P, _P, _P, _P, _P]),
+    "qr_sort": (_S, [ctypes.POINTER(qr_frame), _P]),
+    "qr_select": (_S, [ctypes.POINTER(qr_frame), _P, _P, _P, _P]),
+    "qr_blend": (_S, [_P, _P, _S, _I32, _I64, _P, _P, _P, _I64, _I32, _P, _P]),
+    "qr_dense": (_S, [ctypes.POINTER(qr_frame), _P, _P, _S, _I32, _P, _P, _P]),
+    "qr_render": (_S, [ctypes.POINTER(qr_frame), _P, _P, _P, _P, _P, _P, _S, _I32, _P, _P, _P,
+                       _P, _P]),
+    "qr_render_host_bytes": (_S, [_I64, _I32, _I32, _I32, _I32, _S,
+                                  ctypes.POINTER(ctypes.c_size_t),
+                                  ctypes.POINTER(ctypes.c_size_t)]),
+    "qr_render_host": (_S, [ctypes.POINTER(qr_frame), _P, _P, _P, _P, _P, _P, _S, _I32, _P, _P,
+                            _P, _P]),
+    "qr_launch_count": (ctypes.c_uint64, []),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libqrender.so; raise if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build() "
+                               "(there is no CPU fallback)")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def status_string(code: int) -> str:
+    try:
+        return load().qr_status_string(code).decode()
+    except Exception:  # noqa: BLE001 - used while formatting another error
+        return "status"
+
+
+def _check(code: int, where: str):
+    if code != QR_OK:
+        raise QRError(code, where)
+
+
+# ---------------------------------------------------------------- torch glue
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dtype_code(t) -> int:
+    torch = _torch()
+    if t.dtype == torch.float32:
+        return QR_F32
+    if t.dtype == torch.bfloat16:
+        return QR_BF16
+    if t.dtype in (torch.uint8, getattr(torch, "float8_e4m3fn", torch.uint8)):
+        return QR_FP8E4M3
+    raise TypeError(f"unsupported feature dtype {t.dtype}")
+
+
+def default_params(K: int = 8, **kw) -> qr_params:
+    p = qr_params()
+    load().qr_default_params(ctypes.byref(p))
+    p.K = K
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def make_camera(cam) -> qr_camera:
+    """qr_camera from a scenes.Camera (or anything with R, t, fx, fy, cx, cy, width, height, near)."""
+    c = qr_camera()
+    R = np.asarray(cam.R, np.float32).reshape(-1)
+    t = np.asarray(cam.t, np.float32).reshape(-1)
+    for i in range(9):
+        c.R[i] = float(R[i])
+    for i in range(3):
+        c.t[i] = float(t[i])
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    c.near_plane = float(cam.near)
+    c.width, c.height = int(cam.width), int(cam.height)
+    return c
+
+
+@dataclass
+class Frame:
+    """A qr_frame plus the torch tensor that backs its workspace."""
+    frame: qr_frame
+    workspace: object
+    camera: qr_camera
+    params: qr_params
+
+    @property
+    def width(self) -> int:
+        return int(self.camera.width)
+
+    @property
+    def height(self) -> int:
+        return int(self.camera.height)
+
+    @property
+    def pixels(self) -> int:
+        return self.width * self.height
+
+    @property
+    def K(self) -> int:
+        return int(self.params.K)
+
+
+def workspace_bytes(n: int, width: int, height: int, params: qr_params, max_isect: int) -> int:
+    return int(load().qr_workspace_bytes(n, width, height, ctypes.byref(params), max_isect))
+
+
+def frame_create(n: int, cam, params: qr_params, max_isect: int, device="cuda") -> Frame:
+    """Allocate a workspace with torch and lay out a frame in it (qr_frame_init)."""
+    torch = _torch()
+    camc = cam if isinstance(cam, qr_camera) else make_camera(cam)
+    nbytes = workspace_bytes(n, camc.width, camc.height, params, max_isect)
+    if nbytes == 0:
+        raise QRError(QR_ERR_INVALID_ARG, "qr_workspace_bytes")
+    ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+    base = ws.data_ptr()
+    aligned = (base + 255) // 256 * 256
+    f = qr_frame()
+    _check(load().qr_frame_init(ctypes.byref(f), n, ctypes.byref(camc), ctypes.byref(params),
+                                max_isect, ctypes.c_void_p(aligned), nbytes), "qr_frame_init")
+    return Frame(f, ws, camc, params)
+
+
+def qr_frame_status(fr: Frame, stream=None):
+    """Synchronise and read the device status; returns (status code, n_isect)."""
+    n = _I64(0)
+    code = load().qr_frame_status(ctypes.byref(fr.frame), _stream(stream), ctypes.byref(n))
+    return code, int(n.value)
+
+
+def qr_frame_view_get(fr: Frame) -> qr_frame_view:
+    v = qr_frame_view()
+    _check(load().qr_frame_view_get(ctypes.byref(fr.frame), ctypes.byref(v)), "qr_frame_view_get")
+    return v
+
+
+def qr_project(fr: Frame, mean, log_scale, quat, opacity, stream=None):
+    _check(load().qr_project(ctypes.byref(fr.frame), _ptr(mean), _ptr(log_scale), _ptr(quat),
+                             _ptr(opacity), _stream(stream)), "qr_project")
+
+
+def qr_sort(fr: Frame, stream=None):
+    _check(load().qr_sort(ctypes.byref(fr.frame), _stream(stream)), "qr_sort")
+
+
+def qr_select(fr: Frame, ids, weights, counts, stream=None):
+    _check(load().qr_select(ctypes.byref(fr.frame), _ptr(ids), _ptr(weights), _ptr(counts),
+                            _stream(stream)), "qr_select")
+
+
+def qr_blend(feat, feat_scale, ids, weights, counts, out, stream=None):
+    P, K = ids.shape
+    C = feat.shape[1]
+    _check(load().qr_blend(_ptr(feat), _ptr(feat_scale), _dtype_code(feat), C, feat.shape[0],
+                           _ptr(ids), _ptr(weights), _ptr(counts), P, K, _ptr(out),
+                           _stream(stream)), "qr_blend")
+
+
+def qr_dense(fr: Frame, feat, feat_scale, out, T_final=None, stream=None):
+    _check(load().qr_dense(ctypes.byref(fr.frame), _ptr(feat), _ptr(feat_scale),
+                           _dtype_code(feat), feat.shape[1], _ptr(out), _ptr(T_final),
+                           _stream(stream)), "qr_dense")
+
+
+def qr_render(fr: Frame, mean, log_scale, quat, opacity, feat, feat_scale, ids, weights, counts,
+              out, stream=None):
+    _check(load().qr_render(ctypes.byref(fr.frame), _ptr(mean), _ptr(log_scale), _ptr(quat),
+                            _ptr(opacity), _ptr(feat), _ptr(feat_scale), _dtype_code(feat),
+                            feat.shape[1], _ptr(ids), _ptr(weights), _ptr(counts), _ptr(out),
+                            _stream(stream)), "qr_render")
+
+
+def qr_render_host_bytes(n, width, height, K, C, dtype_code):
+    a, b = ctypes.c_size_t(0), ctypes.c_size_t(0)
+    _check(load().qr_render_host_bytes(n, width, height, K, C, dtype_code, ctypes.byref(a),
+                                       ctypes.byref(b)), "qr_render_host_bytes")
+    return int(a.value), int(b.value)
+
+
+def qr_render_host(fr: Frame, mean_h, log_scale_h, quat_h, opacity_h, feat_h, feat_scale_h,
+                   dtype_code, C, dev_inputs, dev_outputs, out_h, stream=None):
+    """Host-buffer render: arguments are pinned torch CPU tensors (or numpy arrays)."""
+    def hp(x):
+        if x is None:
+            return None
+        if hasattr(x, "data_ptr"):
+            return ctypes.c_void_p(x.data_ptr())
+        return ctypes.c_void_p(x.ctypes.data)
+    _check(load().qr_render_host(ctypes.byref(fr.frame), hp(mean_h), hp(log_scale_h),
+                                 hp(quat_h), hp(opacity_h), hp(feat_h), hp(feat_scale_h),
+                                 dtype_code, C, _ptr(dev_inputs), _ptr(dev_outputs), hp(out_h),
+                                 _stream(stream)), "qr_render_host")
+
+
+def qr_launch_count() -> int:
+    return int(load().qr_launch_count())
+
+
+# ---------------------------------------------------------------- convenience
+def gaussians_to_device(g, device="cuda"):
+    """Upload a scenes.Gaussians to the GPU as contiguous float32 tensors."""
+    torch = _torch()
+    return tuple(torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(device)
+                 for a in (g.mean, g.log_scale, g.quat, g.opacity))
+
+
+def render_frame(gdev, feat, cam, K=8, max_isect=None, params=None, stream=None, dense=False):
+    """Project, sort, select and blend one frame; grows the intersection
+    capacity and retries when the device reports an overflow.  Returns a dict
+    of device tensors (ids, weights, counts, out[, dense, T_final]) and the frame."""
+    torch = _torch()
+    mean = gdev[0]
+    n = mean.shape[0]
+    params = params or default_params(K)
+    cap = max_isect or max(1 << 16, 8 * n)
+    camc = make_camera(cam)
+    while True:
+        fr = frame_create(n, camc, params, cap, device=mean.device)
+        P = fr.pixels
+        ids = torch.empty((P, params.K), dtype=torch.int32, device=mean.device)
+        w = torch.empty((P, params.K), dtype=torch.float32, device=mean.device)
+        cnt = torch.empty(P, dtype=torch.uint8, device=mean.device)
+        qr_project(fr, *gdev, stream=stream)
+        qr_sort(fr, stream=stream)
+        code, nis = qr_frame_status(fr, stream)
+        if code == QR_ERR_CAPACITY:
+            cap = int(nis * 1.25) + 1024
+            continue
+        _check(code, "qr_sort")
+        break
+    qr_select(fr, ids, w, cnt, stream=stream)
+    res = {"ids": ids, "weights": w, "counts": cnt, "n_isect": nis, "frame": fr}
+    if feat is not None:
+        f, fs = feat if isinstance(feat, tuple) else (feat, None)
+        C = f.shape[1]
+        out = torch.empty((P, C), dtype=torch.float32, device=mean.device)
+        qr_blend(f, fs, ids, w, cnt, out, stream=stream)
+        res["out"] = out
+        if dense:
+            dout = torch.empty((P, C), dtype=torch.float32, device=mean.device)
+            tf = torch.empty(P, dtype=torch.float32, device=mean.device)
+            qr_dense(fr, f, fs, dout, tf, stream=stream)
+            res["dense"] = dout
+            res["T_final"] = tf
+    return res

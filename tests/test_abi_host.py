@@ -1,0 +1,109 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports
+every function include/qrender.h declares, and validates its arguments before
+touching the device."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2512_20927_gb300 import qrender as q
+from paper_2512_20927_gb300 import scenes
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2512_20927_gb300 import build_lib
+    build_lib.build()
+    return q.load()
+
+
+def _declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(qr_[a-z0-9_]+)\s*\(", src))
+    return names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared_functions()
+    assert len(names) >= 15
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(q.SIGNATURES) == names
+
+
+def test_abi_version_and_strings(lib):
+    assert lib.qr_abi_version() == 1
+    for code in range(7):
+        assert q.status_string(code)
+
+
+def test_default_params(lib):
+    p = q.default_params(8)
+    assert p.K == 8 and p.tile_w * p.tile_h == 256
+    assert abs(p.alpha_min - 1 / 255) < 1e-9 and abs(p.alpha_max - 0.99) < 1e-7
+
+
+def _frame(n=1000, K=8, cap=4096, ws=1 << 20, nbytes=1 << 40, cam=None, **kw):
+    p = q.default_params(K, **kw)
+    c = q.make_camera(cam or scenes.tiny_camera())
+    f = q.qr_frame()
+    return q.load().qr_frame_init(ctypes.byref(f), n, ctypes.byref(c), ctypes.byref(p), cap,
+                                  ctypes.c_void_p(ws), nbytes), f
+
+
+def test_frame_init_validates_arguments(lib):
+    assert _frame()[0] == q.QR_OK
+    assert _frame(K=0)[0] == q.QR_ERR_INVALID_ARG
+    assert _frame(K=33)[0] == q.QR_ERR_INVALID_ARG
+    assert _frame(n=-1)[0] == q.QR_ERR_INVALID_ARG
+    assert _frame(tile_w=12, tile_h=21)[0] == q.QR_ERR_INVALID_ARG
+    assert _frame(ws=(1 << 20) + 16)[0] == q.QR_ERR_ALIGNMENT
+    assert _frame(nbytes=1000)[0] == q.QR_ERR_INVALID_ARG
+    bad = scenes.tiny_camera()
+    bad.fx = float("nan")
+    assert _frame(cam=bad)[0] == q.QR_ERR_INVALID_ARG
+    rc, f = _frame(tile_w=8, tile_h=32)
+    assert rc == q.QR_OK and f.tiles_x == 16 and f.tiles_y == 4
+
+
+def test_workspace_bytes_scale(lib):
+    p = q.default_params(8)
+    a = q.workspace_bytes(1000, 64, 64, p, 1000)
+    b = q.workspace_bytes(2000, 64, 64, p, 1000)
+    c = q.workspace_bytes(1000, 64, 64, p, 100000)
+    assert 0 < a < b and a < c
+    assert q.workspace_bytes(-5, 64, 64, p, 10) == 0
+
+
+def test_blend_rejects_bad_arguments_before_launch(lib):
+    L = q.load()
+    P = ctypes.c_void_p
+    good = P(1 << 20)
+    launches = L.qr_launch_count()
+    # null features
+    assert L.qr_blend(None, None, q.QR_F32, 16, 10, good, good, good, 4, 8, good, None) == q.QR_ERR_INVALID_ARG
+    # misaligned feature pointer
+    assert L.qr_blend(P((1 << 20) + 4), None, q.QR_F32, 16, 10, good, good, good, 4, 8, good, None) == q.QR_ERR_ALIGNMENT
+    # row not a multiple of 16 bytes
+    assert L.qr_blend(good, None, q.QR_F32, 6, 10, good, good, good, 4, 8, good, None) == q.QR_ERR_ALIGNMENT
+    # FP8 without scales
+    assert L.qr_blend(good, None, q.QR_FP8E4M3, 32, 10, good, good, good, 4, 8, good, None) == q.QR_ERR_INVALID_ARG
+    # K out of range
+    assert L.qr_blend(good, None, q.QR_F32, 16, 10, good, good, good, 4, 40, good, None) == q.QR_ERR_INVALID_ARG
+    # unsupported width
+    assert L.qr_blend(good, None, q.QR_F32, 20, 10, good, good, good, 4, 8, good, None) == q.QR_ERR_NOT_SUPPORTED
+    # nothing launched by any of these
+    assert L.qr_launch_count() == launches
+
+
+def test_render_host_sizes(lib):
+    nin, nout = q.qr_render_host_bytes(100, 32, 16, 8, 16, q.QR_F32)
+    assert nin >= 100 * 11 * 4 + 100 * 16 * 4 and nout >= 32 * 16 * (8 * 8 + 1 + 16 * 4)

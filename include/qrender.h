@@ -103,15 +103,17 @@ typedef struct {
 
 /* Device pointers into a frame's workspace, for inspection and tests. */
 typedef struct {
-    const float *mean2d_hi_lo;   /* [n][4]: projected mean (x_hi, y_hi, x_lo, y_lo); x = x_hi + x_lo */
-    const float *conic_alpha;    /* [n][4]: (A00, A01, A11, alpha), A = inverse EWA covariance        */
-    const uint32_t *depth_key;   /* [n]: FP32 bit pattern of camera depth; 0xFFFFFFFF when culled    */
-    const uint32_t *tile_count;  /* [n]: tiles touched by Gaussian i's footprint                     */
-    const uint32_t *sorted_gid;  /* [n]: Gaussian ids in (depth, id) order                           */
-    const uint32_t *isect_tile;  /* [max_isect]: tile id of each sorted intersection                 */
-    const uint32_t *isect_gid;   /* [max_isect]: Gaussian id of each sorted intersection             */
-    const uint32_t *tile_range;  /* [tiles][2]: [begin, end) of each tile in the sorted list         */
-    const uint32_t *counters;    /* [8]: status, n_isect, n_visible, ...                             */
+    const float *mean2d_hi_lo;   /* [n][4]: projected mean (x_hi, y_hi, x_lo, y_lo); x = x_hi + x_lo   */
+    const float *axes;           /* [n][4]: (w1x, w1y, w2x, w2y), conic A = 2 (w1 w1^T + w2 w2^T)        */
+    const float *opacity;        /* [n]: alpha of each kept Gaussian                                   */
+    const uint32_t *depth_key;   /* [n]: FP32 bit pattern of camera depth; 0xFFFFFFFF when culled      */
+    const uint32_t *tile_count;  /* [n]: tiles touched by Gaussian i's footprint                       */
+    const uint32_t *sorted_key;  /* [n_kept]: depth keys in ascending (depth, id) order                */
+    const uint32_t *sorted_gid;  /* [n_kept]: Gaussian ids in (depth, id) order                        */
+    const uint32_t *isect_tile;  /* [max_isect]: tile id of each sorted intersection                   */
+    const uint32_t *isect_gid;   /* [max_isect]: Gaussian id of each sorted intersection               */
+    const uint32_t *tile_range;  /* [tiles][2]: [begin, end) of each tile in the sorted list           */
+    const uint32_t *counters;    /* [8]: status, n_isect, n_kept, n, n_emitted                         */
 } qr_frame_view;
 
 /* ---------------------------------------------------------------- setup */

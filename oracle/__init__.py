@@ -28,10 +28,14 @@ _LIB = os.path.join(_HERE, "_build", "liboracle.so")
 
 ALPHA_MIN = 1.0 / 255.0
 ALPHA_MAX = 0.99
+# The same parameters rounded to FP32, as the CUDA library receives them; the
+# parity tests evaluate the oracle with these exact values.
+ALPHA_MIN_F32 = float(np.float32(1.0 / 255.0))
+ALPHA_MAX_F32 = float(np.float32(0.99))
 DEFAULT_DILATION = 0.3
 # FP32 relative-error constant for alpha' used by the near-tie classifier
 # (see the comment above classify_ties in qr_oracle.c).
-DEFAULT_TIE_EPS = 2.0 ** -21
+DEFAULT_TIE_EPS = 2.0 ** -22
 
 
 def build(force: bool = False) -> str:

@@ -226,7 +226,7 @@ typedef struct {
     double g;        /* alpha * G, unclamped */
     double G;        /* Gaussian value exp(-q/2) */
     double dx, dy;   /* pixel centre minus projected mean */
-    double qabs;     /* |A00| dx^2 + 2|A01||dx dy| + |A11| dy^2 (for the tie check) */
+    double qabs;     /* conditioning magnitude of q (for the tie check) */
 } member_t;
 
 static int member_cmp(const void *pa, const void *pb)
@@ -286,9 +286,13 @@ static int build_list(const render_job_t *J, scratch_t *S, int px, int py)
         double q = A00 * dx * dx + 2.0 * A01 * dx * dy + A11 * dy * dy;
         double G = exp(-0.5 * q);
         double g = J->alpha[i] * G;
-        double qabs = fabs(A00) * dx * dx + 2.0 * fabs(A01 * dx * dy) + fabs(A11) * dy * dy;
+        /* conditioning of q for an FP32 sum-of-squares evaluation along the
+         * conic's principal axes: |d| sqrt(lambda_max(A)) sqrt(q) + q */
+        double lmax = 0.5 * (A00 + A11) + sqrt(0.25 * (A00 - A11) * (A00 - A11) + A01 * A01);
+        double qabs = sqrt(dx * dx + dy * dy) * sqrt(lmax > 0.0 ? lmax : 0.0) * sqrt(q > 0.0 ? q : 0.0) + fabs(q);
         double rel = J->tie_eps * (1.0 + qabs) + 4.0 * u;
-        if (J->tie && fabs(g - J->alpha_min) <= 4.0 * rel * J->alpha_min) {
+        /* alpha*G within the FP32 error of alpha_min: |ln(g / alpha_min)| <= 4 rel */
+        if (J->tie && g > 0.0 && fabs(log(g / J->alpha_min)) <= 4.0 * rel) {
             if (grow((void **)&S->border, &S->bcap, S->blen + 1, sizeof(double))) return -1;
             S->border[S->blen++] = J->depth[i];
         }
@@ -314,9 +318,11 @@ static int build_list(const render_job_t *J, scratch_t *S, int px, int py)
  * Near-tie classification of one pixel (parity diagnostics, not rendering).
  * A GPU that evaluates alpha' in FP32 may take a different branch than this
  * FP64 walk only where a decision is closer to its threshold than the FP32
- * error can reach.  The FP32 relative error of alpha'_i is bounded by
- * tie_eps * (1 + |q|_abs) + 4u (u = 2^-24), that of a transmittance product
- * accumulates a_i/(1-a_i) times it plus two roundings per factor.
+ * error can reach.  The GPU evaluates q/2 = (d.w1)^2 + (d.w2)^2 with the
+ * conic's principal axes w rounded to FP32; the relative error of its alpha'_i
+ * is bounded by tie_eps * (1 + |d| sqrt(lambda_max(A) q) + q) + 4u
+ * (u = 2^-24), and that of a transmittance product accumulates a_i/(1-a_i)
+ * times it plus two roundings per factor.
  * Bits for Algorithm 1: 1 = a visited test transmittance within that error of
  * a segment boundary; 2 = a Gaussian up to the stopping point with alpha*G
  * within error of alpha_min; 4 = two visited list entries whose depths are

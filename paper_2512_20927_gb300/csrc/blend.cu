@@ -18,8 +18,9 @@
 //     the weight;
 //   - the map is written with streaming (evict-first) 16-byte stores so it
 //     does not displace the feature rows that neighbouring pixels share in L2;
-//   - pixels are visited in screen-tile order (16x16 blocks of pixels per
-//     CTA group) so the rows a tile selects stay hot in L1/L2.
+//   - one CTA renders one 16x16 screen tile, its warps interleaved over the
+//     tile's pixels, so rows shared by a tile's pixels are re-read from the
+//     SM's L1 instead of L2.
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
@@ -116,10 +117,11 @@ blend_kernel(const uint4 *__restrict__ feat, const float *__restrict__ scale, in
     const int lane = threadIdx.x & 31;
     const int sub = lane / LPP, sl = lane % LPP;
     const int64_t items = (W > 0) ? int64_t((W + 15) >> 4) * ((H + 15) >> 4) * 256 : P;
-    const int64_t warp0 = (int64_t(blockIdx.x) * kThreads + threadIdx.x) >> 5;
-    const int64_t nwarps = (int64_t(gridDim.x) * kThreads) >> 5;
-    for (int64_t it = warp0 * PPW + sub; it - sub < items; it += nwarps * PPW) {
-        const int64_t p = (it < items) ? tile_order_pixel(it, W, H) : -1;
+    const int warp = threadIdx.x >> 5;
+    const int64_t chunk0 = int64_t(blockIdx.x) * 256;   // one 16x16 screen tile per CTA
+    for (int it = warp * PPW + sub; it < 256; it += (kThreads / 32) * PPW) {
+        const int64_t item = chunk0 + it;
+        const int64_t p = (item < items) ? tile_order_pixel(item, W, H) : -1;
         const int c = (p >= 0) ? int(cnt[p]) : 0;
         const int32_t *pid = ids + p * K;
         const float *pw = wts + p * K;
@@ -167,15 +169,8 @@ template <int DT, int LPP, int VPL>
 cudaError_t run(const void *feat, const float *scale, int64_t n_gauss, const int32_t *ids,
                 const float *w, const uint8_t *cnt, int64_t P, int K, int W, int H, float *out,
                 cudaStream_t s) {
-    int dev = 0, sms = 152;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t items = (W > 0) ? int64_t((W + 15) >> 4) * ((H + 15) >> 4) * 256 : P;
-    const int64_t warps_needed = (items + (32 / LPP) - 1) / (32 / LPP);
-    int64_t blocks = (warps_needed + (kThreads / 32) - 1) / (kThreads / 32);
-    const int64_t cap = int64_t(sms) * 8;   // persistent-style grid: 8 CTAs per SM
-    if (blocks > cap) blocks = cap;
-    if (blocks < 1) blocks = 1;
+    const int64_t blocks = (items + 255) / 256;
     blend_kernel<DT, LPP, VPL><<<unsigned(blocks), kThreads, 0, s>>>(
         static_cast<const uint4 *>(feat), scale, n_gauss, ids, w, cnt, P, K, W, H,
         reinterpret_cast<float4 *>(out));

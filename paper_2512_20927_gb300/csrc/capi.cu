@@ -53,13 +53,17 @@ size_t layout(int64_t n, int W, int H, const qr_params *p, int64_t cap, size_t *
     sizes[S_COUNTERS] = CNT_WORDS * 4;
     sizes[S_REC_M] = N * 16;
     sizes[S_REC_C] = N * 16;
+    sizes[S_REC_A] = N * 4;
     sizes[S_RECT] = N * 8;
     sizes[S_TCOUNT] = N * 4;
     sizes[S_DKEY0] = sizes[S_DKEY1] = sizes[S_DVAL0] = sizes[S_DVAL1] = N * 4;
     sizes[S_IKEY0] = sizes[S_IKEY1] = sizes[S_IVAL0] = sizes[S_IVAL1] = X * 4;
     sizes[S_RANGES] = tiles * 8;
     sizes[S_HIST] = size_t(1 << kRadixBitsMax) * kSortMaxBlocks * 4;
+    sizes[S_DIGITSUM] = size_t(1 << kRadixBitsMax) * 4;
     sizes[S_BLOCKSUM] = (kSortMaxBlocks + 1) * 4;
+    sizes[S_VISCNT] = ((N + kProjectThreads - 1) / kProjectThreads + 1) * 4;
+    sizes[S_GKEY] = N * 4;
     size_t o = 0;
     for (int s = 0; s < S_END; ++s) {
         if (off) off[s] = o;
@@ -148,10 +152,12 @@ qr_status qr_frame_view_get(const qr_frame *frame, qr_frame_view *view) {
     if (!frame_ok(frame) || !view) return QR_ERR_INVALID_ARG;
     const qr_frame &f = *frame;
     view->mean2d_hi_lo = slot<float>(f, S_REC_M);
-    view->conic_alpha = slot<float>(f, S_REC_C);
-    view->depth_key = slot<uint32_t>(f, S_DKEY0);   // before qr_sort: per-Gaussian keys
+    view->axes = slot<float>(f, S_REC_C);
+    view->opacity = slot<float>(f, S_REC_A);
+    view->depth_key = slot<uint32_t>(f, S_GKEY);
     view->tile_count = slot<uint32_t>(f, S_TCOUNT);
-    view->sorted_gid = slot<uint32_t>(f, S_DVAL0);  // after qr_sort: 4 passes end in buffer a
+    view->sorted_key = slot<uint32_t>(f, S_DKEY0);  // 4 depth passes end in buffer a
+    view->sorted_gid = slot<uint32_t>(f, S_DVAL0);
     view->isect_tile = slot<uint32_t>(f, f.isect_buf ? S_IKEY1 : S_IKEY0);
     view->isect_gid = slot<uint32_t>(f, f.isect_buf ? S_IVAL1 : S_IVAL0);
     view->tile_range = slot<uint32_t>(f, S_RANGES);

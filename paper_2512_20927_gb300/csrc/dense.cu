@@ -66,7 +66,8 @@ template <> struct Cpv<QR_FP8E4M3> { static constexpr int v = 16; };
 // CC channels per CTA; thread tile PX x CH with (256/PX) * (CC/CH) == 256.
 template <int DT, int CC, int PX, int CH>
 __global__ void __launch_bounds__(kThreads)
-dense_kernel(const float4 *__restrict__ rec_m, const float4 *__restrict__ rec_c,
+dense_kernel(const float4 *__restrict__ rec_m, const float4 *__restrict__ rec_w,
+              const float *__restrict__ rec_a,
              const uint32_t *__restrict__ isect_gid, const uint2 *__restrict__ ranges,
              const unsigned char *__restrict__ feat, const float *__restrict__ fscale, int C,
              int W, int H, int tile_w, int tiles_x, float alpha_min, float alpha_max,
@@ -76,6 +77,7 @@ dense_kernel(const float4 *__restrict__ rec_m, const float4 *__restrict__ rec_c,
     constexpr int ESZ = DT == QR_F32 ? 4 : DT == QR_BF16 ? 2 : 1;
     __shared__ float4 s_m[kBatch];
     __shared__ float4 s_c[kBatch];
+    __shared__ float s_a[kBatch];
     __shared__ __align__(16) float s_F[kBatch][CC];
     __shared__ __align__(16) float s_W[kBatch][kThreads];
 
@@ -109,7 +111,8 @@ dense_kernel(const float4 *__restrict__ rec_m, const float4 *__restrict__ rec_c,
         if (threadIdx.x < nb) {
             const uint32_t g = isect_gid[b + threadIdx.x];
             s_m[threadIdx.x] = rec_m[g];
-            s_c[threadIdx.x] = rec_c[g];
+            s_c[threadIdx.x] = rec_w[g];
+            s_a[threadIdx.x] = rec_a[g];
         }
         constexpr int VPR = CC / CPV;  // 16-byte vectors per row slice
         for (int i = threadIdx.x; i < kBatch * VPR; i += kThreads) {
@@ -134,10 +137,8 @@ dense_kernel(const float4 *__restrict__ rec_m, const float4 *__restrict__ rec_c,
             if (!done && j < nb) {
                 const float4 mm = s_m[j];
                 const float4 cc = s_c[j];
-                const float dx = (ux - mm.x) - mm.z;
-                const float dy = (uy - mm.y) - mm.w;
-                const float q = fmaf(cc.x * dx, dx, fmaf(2.0f * cc.y * dx, dy, cc.z * dy * dy));
-                const float a = fminf(alpha_max, cc.w * __expf(-0.5f * q));
+                const PixelTerm pt = eval_half_q(ux, uy, mm, cc);
+                const float a = eval_alpha(s_a[j], pt.half_q, alpha_max);
                 if (a >= alpha_min) {
                     const float Tt = T * (1.0f - a);
                     if (T_min > 0.f && Tt < T_min) {
@@ -197,7 +198,8 @@ cudaError_t run(const qr_frame &f, const void *feat, const float *scale, int C, 
     dim3 grid(unsigned(num_tiles(f)), unsigned(C / CC));
     const int ib = f.isect_buf;
     dense_kernel<DT, CC, PX, CH><<<grid, kThreads, 0, s>>>(
-        slot<float4>(f, S_REC_M), slot<float4>(f, S_REC_C), slot<uint32_t>(f, ib ? S_IVAL1 : S_IVAL0),
+        slot<float4>(f, S_REC_M), slot<float4>(f, S_REC_C), slot<float>(f, S_REC_A),
+        slot<uint32_t>(f, ib ? S_IVAL1 : S_IVAL0),
         slot<uint2>(f, S_RANGES), static_cast<const unsigned char *>(feat), scale, C, f.camera.width,
         f.camera.height, f.params.tile_w, f.tiles_x, f.params.alpha_min, f.params.alpha_max,
         f.params.T_min, out, T_final);

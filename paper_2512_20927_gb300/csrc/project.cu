@@ -4,7 +4,9 @@
 // Sigma = Rq S S^T Rq^T (S = diag(exp(log_scale)), Rq from the quaternion),
 // EWA 2D covariance Sigma' = (J W) Sigma (J W)^T + dilation I with J the
 // Jacobian of the pinhole map at c, conic A = Sigma'^{-1}, projected mean
-// mu' = (fx c_x/c_z + cx, fy c_y/c_z + cy), and the screen tiles its support
+// mu' = (fx c_x/c_z + cx, fy c_y/c_z + cy), the conic's scaled principal axes
+// (A = 2 (w1 w1^T + w2 w2^T), the form every pixel evaluates), and the screen
+// tiles its support
 // {u : alpha exp(-q(u)/2) >= alpha_min}, q = (u-mu')^T A (u-mu'), can reach.
 //
 // GB300 design: one thread per Gaussian in two stages.  Stage A is a cheap
@@ -20,7 +22,7 @@
 namespace qr {
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = kProjectThreads;
 
 struct CamArgs {
     float R[9], t[3], fx, fy, cx, cy, znear;
@@ -38,10 +40,10 @@ __global__ void __launch_bounds__(kThreads)
 project_kernel(int64_t n, const float *__restrict__ mean, const float *__restrict__ log_scale,
                const float *__restrict__ quat, const float *__restrict__ opacity, CamArgs cam,
                float dilation, float alpha_min, int tile_w, int tile_h, int tiles_x,
-               int tiles_y, float4 *__restrict__ rec_m, float4 *__restrict__ rec_c,
-               uint2 *__restrict__ rect, uint32_t *__restrict__ tcount,
-               uint32_t *__restrict__ dkey, uint32_t *__restrict__ dval,
-               uint32_t *__restrict__ counters) {
+               int tiles_y, float4 *__restrict__ rec_m, float4 *__restrict__ rec_w,
+               float *__restrict__ rec_a, uint2 *__restrict__ rect,
+               uint32_t *__restrict__ tcount, uint32_t *__restrict__ dkey,
+               uint32_t *__restrict__ vis_count, uint32_t *__restrict__ counters) {
     __shared__ int s_list[kThreads];
     __shared__ int s_warp[kThreads / 32];
     __shared__ int s_visible;
@@ -54,7 +56,6 @@ project_kernel(int64_t n, const float *__restrict__ mean, const float *__restric
     // ---------------- stage A: FP32 conservative footprint bound
     bool cand = false;
     if (g < n) {
-        dval[g] = uint32_t(g);
         const float mx = mean[3 * g], my = mean[3 * g + 1], mz = mean[3 * g + 2];
         const float alpha = opacity[g];
         const float cz = fmaf(cam.R[6], mx, fmaf(cam.R[7], my, fmaf(cam.R[8], mz, cam.t[2])));
@@ -162,10 +163,26 @@ project_kernel(int64_t n, const float *__restrict__ mean, const float *__restric
             write_culled(gi, dkey, tcount, rect);
             continue;
         }
-        const df idet = df_div(df_from(1.f), det);
-        const float A00 = df_mul(s11, idet).hi;
-        const float A01 = -df_mul(s01, idet).hi;
-        const float A11 = df_mul(s00, idet).hi;
+        // principal axes of Sigma': lambda1 >= lambda2 > 0, unit eigenvector e1;
+        // the conic's scaled axes are w_k = e_k / sqrt(2 lambda_k)
+        const df hd = df_mul_f(df_sub(s00, s11), 0.5f);
+        const df rad = df_sqrt(df_add(df_mul(hd, hd), df_mul(s01, s01)));
+        const df l1 = df_add(df_mul_f(df_add(s00, s11), 0.5f), rad);
+        const df l2 = df_div(det, l1);
+        const df ax = df_sub(l1, s11), bx = df_sub(l1, s00);
+        df vx, vy;
+        if (df_abs_hi(ax) + df_abs_hi(s01) >= df_abs_hi(s01) + df_abs_hi(bx)) {
+            vx = ax; vy = s01;
+        } else {
+            vx = s01; vy = bx;
+        }
+        df nv = df_sqrt(df_add(df_mul(vx, vx), df_mul(vy, vy)));
+        if (!(nv.hi > 0.f)) { vx = df_from(1.f); vy = df_from(0.f); nv = df_from(1.f); }
+        const df e1x = df_div(vx, nv), e1y = df_div(vy, nv);
+        const df r1 = df_div(df_from(1.f), df_sqrt(df_mul_f(l1, 2.f)));
+        const df r2 = df_div(df_from(1.f), df_sqrt(df_mul_f(l2, 2.f)));
+        const float4 waxes = make_float4(df_mul(e1x, r1).hi, df_mul(e1y, r1).hi,
+                                         -df_mul(e1y, r2).hi, df_mul(e1x, r2).hi);
         const df mxp = df_add_f(df_mul_f(u, cam.fx), cam.cx);
         const df myp = df_add_f(df_mul_f(v, cam.fy), cam.cy);
 
@@ -189,17 +206,18 @@ project_kernel(int64_t n, const float *__restrict__ mean, const float *__restric
         }
         const int tx0 = x0 / tile_w, tx1 = x1 / tile_w, ty0 = y0 / tile_h, ty1 = y1 / tile_h;
         rec_m[gi] = make_float4(mxp.hi, myp.hi, mxp.lo, myp.lo);
-        rec_c[gi] = make_float4(A00, A01, A11, alpha);
+        rec_w[gi] = waxes;
+        rec_a[gi] = alpha;
         rect[gi] = make_uint2(uint32_t(tx0) | (uint32_t(ty0) << 16), uint32_t(tx1) | (uint32_t(ty1) << 16));
         tcount[gi] = uint32_t((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
         dkey[gi] = __float_as_uint(c[2].hi);
         ++visible;
     }
-    // block-aggregated visible count
+    // per-CTA count of kept Gaussians (consumed by the order-preserving compaction)
     for (int o = 16; o > 0; o >>= 1) visible += __shfl_xor_sync(0xffffffffu, visible, o);
     if (lane == 0 && visible) atomicAdd(&s_visible, visible);
     __syncthreads();
-    if (threadIdx.x == 0 && s_visible) atomicAdd(&counters[CNT_VISIBLE], uint32_t(s_visible));
+    if (threadIdx.x == 0) vis_count[blockIdx.x] = uint32_t(s_visible);
     (void)tiles_x;
     (void)tiles_y;
 }
@@ -222,8 +240,9 @@ cudaError_t launch_project(const qr_frame &f, const float *mean, const float *lo
     project_kernel<<<blocks, kThreads, 0, s>>>(
         n, mean, log_scale, quat, opacity, cam, f.params.dilation, f.params.alpha_min,
         f.params.tile_w, f.params.tile_h, f.tiles_x, f.tiles_y, slot<float4>(f, S_REC_M),
-        slot<float4>(f, S_REC_C), slot<uint2>(f, S_RECT), slot<uint32_t>(f, S_TCOUNT),
-        slot<uint32_t>(f, S_DKEY0), slot<uint32_t>(f, S_DVAL0), counters);
+        slot<float4>(f, S_REC_C), slot<float>(f, S_REC_A), slot<uint2>(f, S_RECT),
+        slot<uint32_t>(f, S_TCOUNT), slot<uint32_t>(f, S_GKEY), slot<uint32_t>(f, S_VISCNT),
+        counters);
     count_launch();
     return cudaGetLastError();
 }

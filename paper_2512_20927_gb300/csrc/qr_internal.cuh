@@ -18,12 +18,13 @@ enum { CNT_STATUS = 0, CNT_ISECT = 1, CNT_VISIBLE = 2, CNT_N = 3, CNT_SORT_N = 4
 
 // Workspace slots (byte offsets in qr_frame::off).
 enum Slot {
-    S_COUNTERS = 0, S_REC_M, S_REC_C, S_RECT, S_TCOUNT,
+    S_COUNTERS = 0, S_REC_M, S_REC_C, S_REC_A, S_RECT, S_TCOUNT,
     S_DKEY0, S_DKEY1, S_DVAL0, S_DVAL1,
     S_IKEY0, S_IKEY1, S_IVAL0, S_IVAL1,
-    S_RANGES, S_HIST, S_BLOCKSUM,
+    S_RANGES, S_HIST, S_DIGITSUM, S_BLOCKSUM, S_VISCNT, S_GKEY,
     S_END
 };
+constexpr int kProjectThreads = 256;
 static_assert(S_END <= QR_FRAME_SLOTS, "too many workspace slots");
 
 constexpr int kSortThreads = 256;
@@ -65,11 +66,35 @@ cudaError_t launch_dense(const qr_frame &f, const void *feat, const float *scale
 // which of the two buffers holds the result (0 = buffers "a", 1 = "b").
 cudaError_t radix_sort_pairs(uint32_t *keys_a, uint32_t *vals_a, uint32_t *keys_b,
                              uint32_t *vals_b, const uint32_t *d_count, int64_t capacity,
-                             int bit_lo, int bit_hi, uint32_t *hist, int blocks,
-                             int *result_in_b, cudaStream_t s);
+                             int bit_lo, int bit_hi, uint32_t *hist, uint32_t *digitsum,
+                             int blocks, int *result_in_b, cudaStream_t s);
 
 int sort_blocks_for(int64_t capacity);
 int tile_bits_for(int tiles);
+
+// ---------------------------------------------------------------- per-pixel Gaussian
+// Every kernel evaluates alpha' at a pixel the same way.  The projected
+// Gaussian is stored as its mean (hi + lo) and two scaled principal axes
+// w1, w2 of the conic, A = 2 (w1 w1^T + w2 w2^T), so that
+//     q/2 = (d . w1)^2 + (d . w2)^2,   d = u - mu'.
+// The sum of squares has no cancellation (the conic form
+// A00 dx^2 + 2 A01 dx dy + A11 dy^2 loses up to cond(Sigma') ulps for
+// elongated Gaussians), and costs five FP32 operations.
+struct PixelTerm {
+    float dx, dy, half_q;
+};
+__device__ __forceinline__ PixelTerm eval_half_q(float ux, float uy, float4 m, float4 w) {
+    PixelTerm t;
+    t.dx = (ux - m.x) - m.z;
+    t.dy = (uy - m.y) - m.w;
+    const float p1 = fmaf(t.dx, w.x, t.dy * w.y);
+    const float p2 = fmaf(t.dx, w.z, t.dy * w.w);
+    t.half_q = fmaf(p1, p1, p2 * p2);
+    return t;
+}
+__device__ __forceinline__ float eval_alpha(float alpha, float half_q, float alpha_max) {
+    return fminf(alpha_max, alpha * __expf(-half_q));
+}
 
 // ---------------------------------------------------------------- compensated arithmetic
 // Pairs (hi, lo) of FP32 with |lo| <= ulp(hi)/2 represent hi + lo exactly;
@@ -133,7 +158,15 @@ __device__ __forceinline__ df df_div(df a, df b) {
     df q = df_fast_two_sum(q1, q2);
     return df_add_f(q, q3);
 }
-// a*b + c*d + e*f + g (sum of three products plus a term), all in df.
+// Square root with one Newton correction of the FP32 estimate.
+__device__ __forceinline__ df df_sqrt(df a) {
+    if (!(a.hi > 0.f)) return {0.f, 0.f};
+    const float s = sqrtf(a.hi);
+    const df r = df_sub(a, df_two_prod(s, s));
+    return df_fast_two_sum(s, __fdiv_rn(r.hi, 2.0f * s));
+}
+__device__ __forceinline__ float df_abs_hi(df a) { return fabsf(a.hi); }
+// a*b + c*d + e*f, all in df.
 __device__ __forceinline__ df df_dot3(df a, df b, df c, df d, df e, df f) {
     return df_add(df_add(df_mul(a, b), df_mul(c, d)), df_mul(e, f));
 }

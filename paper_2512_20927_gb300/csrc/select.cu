@@ -14,7 +14,7 @@
 //
 // GB300 design: one CTA per screen tile (256 threads, one per pixel).  The
 // tile's list is staged through shared memory 256 entries at a time (gid,
-// projected mean hi/lo, conic, opacity: 36 B each) with one coalesced load
+// projected mean hi/lo, conic axes, opacity: 40 B each) with one coalesced load
 // per thread; every pixel then reads the staged entries as broadcasts.  The
 // walk is scalar FP32 (one exp per pixel-entry pair); a CTA stops loading as
 // soon as all of its pixels have stopped (__syncthreads_count).  Kept
@@ -28,12 +28,14 @@ namespace {
 constexpr int kThreads = 256;
 
 __global__ void __launch_bounds__(kThreads)
-select_kernel(const float4 *__restrict__ rec_m, const float4 *__restrict__ rec_c,
+select_kernel(const float4 *__restrict__ rec_m, const float4 *__restrict__ rec_w,
+              const float *__restrict__ rec_a,
               const uint32_t *__restrict__ isect_gid, const uint2 *__restrict__ ranges, int W,
               int H, int tile_w, int tiles_x, int K, float alpha_min, float alpha_max,
               int32_t *__restrict__ ids, float *__restrict__ wout, uint8_t *__restrict__ cnt) {
     __shared__ float4 s_m[kThreads];
     __shared__ float4 s_c[kThreads];
+    __shared__ float s_a[kThreads];
     __shared__ uint32_t s_g[kThreads];
     extern __shared__ unsigned char s_dyn[];
     int32_t *s_ids = reinterpret_cast<int32_t *>(s_dyn);              // [K][256]
@@ -61,7 +63,8 @@ select_kernel(const float4 *__restrict__ rec_m, const float4 *__restrict__ rec_c
             const uint32_t g = isect_gid[idx];
             s_g[threadIdx.x] = g;
             s_m[threadIdx.x] = rec_m[g];
-            s_c[threadIdx.x] = rec_c[g];
+            s_c[threadIdx.x] = rec_w[g];
+            s_a[threadIdx.x] = rec_a[g];
         }
         __syncthreads();
         const int nb = int(min(uint32_t(kThreads), range.y - b));
@@ -69,10 +72,8 @@ select_kernel(const float4 *__restrict__ rec_m, const float4 *__restrict__ rec_c
             for (int j = 0; j < nb; ++j) {
                 const float4 mm = s_m[j];
                 const float4 cc = s_c[j];
-                const float dx = (ux - mm.x) - mm.z;
-                const float dy = (uy - mm.y) - mm.w;
-                const float q = fmaf(cc.x * dx, dx, fmaf(2.0f * cc.y * dx, dy, cc.z * dy * dy));
-                const float a = fminf(alpha_max, cc.w * __expf(-0.5f * q));
+                const PixelTerm pt = eval_half_q(ux, uy, mm, cc);
+                const float a = eval_alpha(s_a[j], pt.half_q, alpha_max);
                 if (a < alpha_min) continue;
                 const float Tt = T * (1.0f - a);
                 if (Tt < thr) {
@@ -119,7 +120,8 @@ cudaError_t launch_select(const qr_frame &f, int32_t *ids, float *w, uint8_t *cn
     }
     const int ib = f.isect_buf;  // which buffer holds the sorted intersections
     select_kernel<<<tiles, kThreads, dyn, s>>>(
-        slot<float4>(f, S_REC_M), slot<float4>(f, S_REC_C), slot<uint32_t>(f, ib ? S_IVAL1 : S_IVAL0),
+        slot<float4>(f, S_REC_M), slot<float4>(f, S_REC_C), slot<float>(f, S_REC_A),
+        slot<uint32_t>(f, ib ? S_IVAL1 : S_IVAL0),
         slot<uint2>(f, S_RANGES), f.camera.width, f.camera.height, f.params.tile_w, f.tiles_x, K,
         f.params.alpha_min, f.params.alpha_max, ids, w, cnt);
     count_launch();

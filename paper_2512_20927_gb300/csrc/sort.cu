@@ -70,18 +70,11 @@ radix_upsweep(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ d_
     }
 }
 
-// exclusive scan of `total` u32 in place by one CTA of 1024 threads;
-// optionally stores the grand total in *sum_out.
-__device__ void cta_exclusive_scan(uint32_t *data, int total, uint32_t *sum_out) {
-    __shared__ uint32_t s_w[32];
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const int per = (total + nt - 1) / nt;
-    const int a = min(total, tid * per), b = min(total, a + per);
-    uint32_t s = 0;
-    for (int i = a; i < b; ++i) s += data[i];
-    // block exclusive scan of s
-    const int lane = tid & 31, warp = tid >> 5;
-    uint32_t x = s;
+// Inclusive scan of one value per thread across the CTA (blockDim.x a
+// multiple of 32, at most 1024); returns the inclusive prefix and the total.
+__device__ __forceinline__ uint32_t block_inclusive_scan(uint32_t v, uint32_t *s_w, uint32_t &total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t x = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
@@ -90,7 +83,7 @@ __device__ void cta_exclusive_scan(uint32_t *data, int total, uint32_t *sum_out)
     if (lane == 31) s_w[warp] = x;
     __syncthreads();
     if (warp == 0) {
-        uint32_t w = (lane < nt / 32) ? s_w[lane] : 0;
+        uint32_t w = (lane < nw) ? s_w[lane] : 0u;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
@@ -99,32 +92,76 @@ __device__ void cta_exclusive_scan(uint32_t *data, int total, uint32_t *sum_out)
         s_w[lane] = w;
     }
     __syncthreads();
-    uint32_t run = x - s + (warp > 0 ? s_w[warp - 1] : 0);
-    for (int i = a; i < b; ++i) {
-        const uint32_t v = data[i];
-        data[i] = run;
-        run += v;
-    }
-    if (sum_out && tid == nt - 1) *sum_out = run;
+    const uint32_t r = x + (warp > 0 ? s_w[warp - 1] : 0u);
+    total = s_w[nw - 1];
+    __syncthreads();
+    return r;
 }
 
-__global__ void __launch_bounds__(1024) radix_scan(uint32_t *hist, int total) {
-    cta_exclusive_scan(hist, total, nullptr);
+// Exclusive scan of `total` u32 in place by one CTA: coalesced chunks of
+// blockDim.x elements with a running carry.  Returns the grand total to
+// thread 0 through *sum_out (nullable).
+__device__ void cta_exclusive_scan(uint32_t *data, int total, uint32_t *sum_out) {
+    __shared__ uint32_t s_w[32];
+    uint32_t carry = 0;
+    for (int base = 0; base < total; base += blockDim.x) {
+        const int i = base + threadIdx.x;
+        const uint32_t v = i < total ? data[i] : 0u;
+        uint32_t chunk;
+        const uint32_t inc = block_inclusive_scan(v, s_w, chunk);
+        if (i < total) data[i] = carry + inc - v;
+        carry += chunk;
+    }
+    if (sum_out && threadIdx.x == 0) *sum_out = carry;
+}
+
+__global__ void __launch_bounds__(1024) scan_kernel(uint32_t *data, int total) {
+    cta_exclusive_scan(data, total, nullptr);
+}
+
+// One warp per digit: exclusive scan of the digit's per-block counts (row d of
+// the [digit][block] table) in place; the row total goes to digitsum[d].
+__global__ void __launch_bounds__(256)
+radix_scan_rows(uint32_t *__restrict__ hist, int radix, int blocks, uint32_t *__restrict__ digitsum) {
+    const int d = blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (d >= radix) return;
+    uint32_t *row = hist + size_t(d) * blocks;
+    uint32_t carry = 0;
+    for (int base = 0; base < blocks; base += 32) {
+        const int i = base + lane;
+        const uint32_t v = i < blocks ? row[i] : 0u;
+        uint32_t x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (i < blocks) row[i] = carry + x - v;
+        carry += __shfl_sync(0xffffffffu, x, 31);
+    }
+    if (lane == 0) digitsum[d] = carry;
 }
 
 __global__ void __launch_bounds__(T)
 radix_downsweep(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
                 uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out,
                 const uint32_t *__restrict__ d_count, int shift, int bits,
-                const uint32_t *__restrict__ hist) {
+                const uint32_t *__restrict__ hist, const uint32_t *__restrict__ digitsum) {
     __shared__ uint32_t s_base[1 << kRadixBitsMax];
+    __shared__ uint32_t s_scan[32];
     __shared__ uint32_t s_tot[1 << kRadixBitsMax];
     __shared__ uint32_t s_w[WARPS][1 << kRadixBitsMax];
     const int radix = 1 << bits;
     const uint32_t mask = uint32_t(radix - 1);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt = lanemask_lt();
-    for (int d = threadIdx.x; d < radix; d += T) s_base[d] = hist[d * gridDim.x + blockIdx.x];
+    {   // base of digit d for this block = sum of smaller digits + this digit's earlier blocks
+        const uint32_t ds = threadIdx.x < radix ? digitsum[threadIdx.x] : 0u;
+        uint32_t tot;
+        const uint32_t inc = block_inclusive_scan(ds, s_scan, tot);
+        if (threadIdx.x < radix) s_base[threadIdx.x] = inc - ds + hist[threadIdx.x * gridDim.x + blockIdx.x];
+    }
     const uint32_t n = *d_count;
     uint32_t t0, t1;
     block_tiles(n, blockIdx.x, gridDim.x, t0, t1);
@@ -170,6 +207,36 @@ radix_downsweep(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict
         __syncthreads();
         for (int d = threadIdx.x; d < radix; d += T) s_base[d] += s_tot[d];
         __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ compaction
+// The kept Gaussians (finite depth key) are packed in id order, so the depth
+// sort works on the visible set only and equal depths keep id order.
+__global__ void __launch_bounds__(1024)
+compact_scan(uint32_t *vis_count, int nblk, uint32_t *counters) {
+    __shared__ uint32_t s_total;
+    cta_exclusive_scan(vis_count, nblk, &s_total);
+    __syncthreads();
+    if (threadIdx.x == 0) counters[CNT_VISIBLE] = s_total;
+}
+
+__global__ void __launch_bounds__(kProjectThreads)
+compact_scatter(const uint32_t *__restrict__ gkey, const uint32_t *__restrict__ vis_off, int64_t n,
+                uint32_t *__restrict__ dkey, uint32_t *__restrict__ dval) {
+    __shared__ uint32_t s_w[kProjectThreads / 32];
+    const int64_t g = int64_t(blockIdx.x) * kProjectThreads + threadIdx.x;
+    const uint32_t key = g < n ? gkey[g] : 0xFFFFFFFFu;
+    const bool keep = key != 0xFFFFFFFFu;
+    const unsigned ballot = __ballot_sync(0xffffffffu, keep);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) s_w[warp] = __popc(ballot);
+    __syncthreads();
+    uint32_t off = vis_off[blockIdx.x] + __popc(ballot & ((1u << lane) - 1u));
+    for (int w = 0; w < warp; ++w) off += s_w[w];
+    if (keep) {
+        dkey[off] = key;
+        dval[off] = uint32_t(g);
     }
 }
 
@@ -283,8 +350,8 @@ int sort_blocks_for(int64_t capacity) {
 
 cudaError_t radix_sort_pairs(uint32_t *keys_a, uint32_t *vals_a, uint32_t *keys_b,
                              uint32_t *vals_b, const uint32_t *d_count, int64_t capacity,
-                             int bit_lo, int bit_hi, uint32_t *hist, int blocks,
-                             int *result_in_b, cudaStream_t s) {
+                             int bit_lo, int bit_hi, uint32_t *hist, uint32_t *digitsum,
+                             int blocks, int *result_in_b, cudaStream_t s) {
     (void)capacity;
     int in_b = 0;
     for (int lo = bit_lo; lo < bit_hi;) {
@@ -294,8 +361,8 @@ cudaError_t radix_sort_pairs(uint32_t *keys_a, uint32_t *vals_a, uint32_t *keys_
         uint32_t *ki = in_b ? keys_b : keys_a, *vi = in_b ? vals_b : vals_a;
         uint32_t *ko = in_b ? keys_a : keys_b, *vo = in_b ? vals_a : vals_b;
         radix_upsweep<<<blocks, T, 0, s>>>(ki, d_count, lo, bits, hist);
-        radix_scan<<<1, 1024, 0, s>>>(hist, (1 << bits) * blocks);
-        radix_downsweep<<<blocks, T, 0, s>>>(ki, vi, ko, vo, d_count, lo, bits, hist);
+        radix_scan_rows<<<((1 << bits) + 7) / 8, 256, 0, s>>>(hist, 1 << bits, blocks, digitsum);
+        radix_downsweep<<<blocks, T, 0, s>>>(ki, vi, ko, vo, d_count, lo, bits, hist, digitsum);
         count_launch(3);
         in_b ^= 1;
         lo += bits;
@@ -313,26 +380,35 @@ int tile_bits_for(int tiles) {
 cudaError_t launch_sort(const qr_frame &f, cudaStream_t s) {
     uint32_t *counters = slot<uint32_t>(f, S_COUNTERS);
     uint32_t *hist = slot<uint32_t>(f, S_HIST);
+    uint32_t *digitsum = slot<uint32_t>(f, S_DIGITSUM);
     const int tiles = num_tiles(f);
     cudaError_t e = cudaMemsetAsync(slot<uint2>(f, S_RANGES), 0, sizeof(uint2) * size_t(tiles), s);
     if (e != cudaSuccess) return e;
     if (f.n == 0) return cudaSuccess;
-    // 1. depth sort of all n Gaussians (culled ones carry key 0xFFFFFFFF and sort last)
+    // 0. pack the kept Gaussians (id order) -> counters[CNT_VISIBLE] items
+    const int nblk = int((f.n + kProjectThreads - 1) / kProjectThreads);
+    uint32_t *viscnt = slot<uint32_t>(f, S_VISCNT);
+    compact_scan<<<1, 1024, 0, s>>>(viscnt, nblk, counters);
+    compact_scatter<<<nblk, kProjectThreads, 0, s>>>(slot<uint32_t>(f, S_GKEY), viscnt, f.n,
+                                                     slot<uint32_t>(f, S_DKEY0),
+                                                     slot<uint32_t>(f, S_DVAL0));
+    count_launch(2);
+    // 1. depth sort of the kept Gaussians
     const int nb_depth = sort_blocks_for(f.n);
     int in_b = 0;
     e = radix_sort_pairs(slot<uint32_t>(f, S_DKEY0), slot<uint32_t>(f, S_DVAL0),
                          slot<uint32_t>(f, S_DKEY1), slot<uint32_t>(f, S_DVAL1),
-                         counters + CNT_N, f.n, 0, 32, hist, nb_depth, &in_b, s);
+                         counters + CNT_VISIBLE, f.n, 0, 32, hist, digitsum, nb_depth, &in_b, s);
     if (e != cudaSuccess) return e;
     const uint32_t *sorted_gid = slot<uint32_t>(f, in_b ? S_DVAL1 : S_DVAL0);
     // 2. scan of tile counts in depth order + emit
     uint32_t *blocksum = slot<uint32_t>(f, S_BLOCKSUM);
-    emit_upsweep<<<nb_depth, T, 0, s>>>(sorted_gid, slot<uint32_t>(f, S_TCOUNT), counters + CNT_N,
-                                        blocksum);
+    emit_upsweep<<<nb_depth, T, 0, s>>>(sorted_gid, slot<uint32_t>(f, S_TCOUNT),
+                                        counters + CNT_VISIBLE, blocksum);
     emit_scan<<<1, 1024, 0, s>>>(blocksum, nb_depth, counters, uint32_t(f.max_isect));
     emit_pairs<<<nb_depth, T, 0, s>>>(sorted_gid, slot<uint32_t>(f, S_TCOUNT),
-                                      slot<uint2>(f, S_RECT), counters + CNT_N, blocksum, counters,
-                                      f.tiles_x, slot<uint32_t>(f, S_IKEY0),
+                                      slot<uint2>(f, S_RECT), counters + CNT_VISIBLE, blocksum,
+                                      counters, f.tiles_x, slot<uint32_t>(f, S_IKEY0),
                                       slot<uint32_t>(f, S_IVAL0));
     count_launch(3);
     // 3. stable sort of the intersections by tile id
@@ -340,12 +416,14 @@ cudaError_t launch_sort(const qr_frame &f, cudaStream_t s) {
     e = radix_sort_pairs(slot<uint32_t>(f, S_IKEY0), slot<uint32_t>(f, S_IVAL0),
                          slot<uint32_t>(f, S_IKEY1), slot<uint32_t>(f, S_IVAL1),
                          counters + CNT_SORT_N, f.max_isect, 0, tile_bits_for(tiles), hist,
-                         f.sort_blocks, &ib, s);
+                         digitsum, f.sort_blocks, &ib, s);
     if (e != cudaSuccess) return e;
     // 4. tile ranges
     const uint32_t *ikey = slot<uint32_t>(f, ib ? S_IKEY1 : S_IKEY0);
-    const int rb = 2 * 152 * 4;
-    tile_ranges<<<rb, T, 0, s>>>(ikey, counters, slot<uint2>(f, S_RANGES));
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    tile_ranges<<<sms * 4, T, 0, s>>>(ikey, counters, slot<uint2>(f, S_RANGES));
     count_launch();
     return cudaGetLastError();
 }

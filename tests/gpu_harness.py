@@ -29,7 +29,9 @@ def run_oracle(g, feat, cam, K, pixels=None, T_min=1e-4, max_members=0, params_k
     pk = params_kw or {}
     pr = oracle.project(g, cam.as_array(), dilation=pk.get("dilation", oracle.DEFAULT_DILATION))
     pix = oracle.all_pixels(cam.width, cam.height) if pixels is None else pixels
-    ref = oracle.render(pr, feat, K, pix, T_min=T_min, max_members=max_members)
+    ref = oracle.render(pr, feat, K, pix, T_min=float(np.float32(T_min)),
+                        alpha_min=oracle.ALPHA_MIN_F32, alpha_max=oracle.ALPHA_MAX_F32,
+                        max_members=max_members)
     return pr, pix, ref
 
 

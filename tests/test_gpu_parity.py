@@ -51,20 +51,28 @@ def test_projection_matches_oracle():
     torch.cuda.synchronize()
     n = g.n
     rec_m = _device_copy(v.mean2d_hi_lo, n * 4, torch.float32).view(n, 4).cpu().numpy()
-    rec_c = _device_copy(v.conic_alpha, n * 4, torch.float32).view(n, 4).cpu().numpy()
+    axes = _device_copy(v.axes, n * 4, torch.float32).view(n, 4).cpu().numpy().astype(np.float64)
+    opac = _device_copy(v.opacity, n, torch.float32).cpu().numpy()
     dkey = _device_copy(v.depth_key, n, torch.int32).cpu().numpy().view(np.uint32)
     pr = oracle.project(g, cam.as_array())
     vis = dkey != 0xFFFFFFFF
+    assert vis.sum() > 100
     # every Gaussian the GPU keeps is in front of the near plane in FP64
     assert (pr.valid[vis] == 1).all()
     m2 = rec_m[vis, 0:2].astype(np.float64) + rec_m[vis, 2:4].astype(np.float64)
     np.testing.assert_allclose(m2, pr.mean2d[vis], rtol=0, atol=1e-6)
-    A = rec_c[vis, :3].astype(np.float64)
+    # conic rebuilt from the principal axes: A = 2 (w1 w1^T + w2 w2^T)
+    w1, w2 = axes[vis, 0:2], axes[vis, 2:4]
+    A = 2.0 * np.stack([w1[:, 0] ** 2 + w2[:, 0] ** 2, w1[:, 0] * w1[:, 1] + w2[:, 0] * w2[:, 1],
+                        w1[:, 1] ** 2 + w2[:, 1] ** 2], axis=1)
     scale = np.abs(pr.conic[vis]).max(axis=1, keepdims=True)
-    assert (np.abs(A - pr.conic[vis]) <= 2e-6 * scale).all()
+    assert (np.abs(A - pr.conic[vis]) <= 1e-6 * scale).all(), np.abs(A - pr.conic[vis]).max()
+    # the axes are orthogonal
+    assert (np.abs((w1 * w2).sum(axis=1)) <= 1e-6 * np.linalg.norm(w1, axis=1) *
+            np.linalg.norm(w2, axis=1)).all()
     depth32 = dkey[vis].view(np.float32).astype(np.float64)
     assert (np.abs(depth32 - pr.depth[vis]) <= 2.0 ** -23 * pr.depth[vis]).all()
-    np.testing.assert_array_equal(rec_c[vis, 3], g.opacity[vis])
+    np.testing.assert_array_equal(opac[vis], g.opacity[vis])
     # Gaussians with any visible pixel are kept (checked on the oracle's members)
     ref = oracle.render(pr, None, 8, oracle.all_pixels(cam.width, cam.height), want_q=False,
                         want_dense=False, max_members=64)
@@ -79,7 +87,7 @@ def _device_copy(ptr, count, dtype):
 
     class _View:
         __cuda_array_interface__ = {"shape": (count,), "typestr": typestr,
-                                    "data": (int(ptr), True), "version": 3, "strides": None}
+                                    "data": (int(ptr), False), "version": 3, "strides": None}
     return torch.as_tensor(_View(), device="cuda").clone()
 
 

@@ -115,10 +115,6 @@ __device__ void cta_exclusive_scan(uint32_t *data, int total, uint32_t *sum_out)
     if (sum_out && threadIdx.x == 0) *sum_out = carry;
 }
 
-__global__ void __launch_bounds__(1024) scan_kernel(uint32_t *data, int total) {
-    cta_exclusive_scan(data, total, nullptr);
-}
-
 // One warp per digit: exclusive scan of the digit's per-block counts (row d of
 // the [digit][block] table) in place; the row total goes to digitsum[d].
 __global__ void __launch_bounds__(256)
@@ -280,50 +276,87 @@ emit_scan(uint32_t *blocksum, int nblocks, uint32_t *counters, uint32_t capacity
     }
 }
 
+// Per-Gaussian exclusive offsets of the intersection list, in depth order.
 __global__ void __launch_bounds__(T)
-emit_pairs(const uint32_t *__restrict__ sorted_gid, const uint32_t *__restrict__ tcount,
-           const uint2 *__restrict__ rect, const uint32_t *__restrict__ d_n,
-           const uint32_t *__restrict__ blocksum, const uint32_t *__restrict__ counters,
-           int tiles_x, uint32_t *__restrict__ ikey, uint32_t *__restrict__ ival) {
-    __shared__ uint32_t s_w[WARPS];
-    __shared__ uint32_t s_run;
-    if (counters[CNT_STATUS] != 0) return;  // capacity exceeded: emit nothing
+emit_offsets(const uint32_t *__restrict__ sorted_gid, const uint32_t *__restrict__ tcount,
+             const uint32_t *__restrict__ d_n, const uint32_t *__restrict__ blocksum,
+             uint32_t *__restrict__ off) {
+    __shared__ uint32_t s_w[32];
     const uint32_t n = *d_n;
     uint32_t t0, t1;
     block_tiles(n, blockIdx.x, gridDim.x, t0, t1);
     const uint32_t end = min(n, t1 * TILE);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) s_run = blocksum[blockIdx.x];
-    __syncthreads();
+    uint32_t run = blocksum[blockIdx.x];
     for (uint32_t base = t0 * TILE; base < end; base += T) {
         const uint32_t i = base + threadIdx.x;
-        const uint32_t g = i < end ? sorted_gid[i] : 0u;
-        const uint32_t c = i < end ? tcount[g] : 0u;
-        uint32_t x = c;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
+        const uint32_t c = i < end ? tcount[sorted_gid[i]] : 0u;
+        uint32_t tot;
+        const uint32_t inc = block_inclusive_scan(c, s_w, tot);
+        if (i < end) off[i] = run + inc - c;
+        run += tot;
+    }
+}
+
+// Last index s in [0, n) with off[s] <= target (off[0] == 0 <= target), found
+// by one warp with 32-way splits.
+__device__ __forceinline__ uint32_t warp_upper_index(const uint32_t *off, uint32_t n, uint32_t target) {
+    const int lane = threadIdx.x & 31;
+    uint32_t lo = 0, hi = n;
+    while (hi - lo > 32) {
+        const uint32_t step = (hi - lo + 31) / 32;
+        const uint32_t pos = lo + lane * step;
+        const bool le = pos < hi && off[pos] <= target;
+        const int k = __popc(__ballot_sync(0xffffffffu, le));
+        lo = lo + (k - 1) * step;
+        hi = min(hi, lo + step);
+    }
+    const uint32_t pos = lo + lane;
+    const bool le = pos < hi && off[pos] <= target;
+    return lo + __popc(__ballot_sync(0xffffffffu, le)) - 1;
+}
+
+// Load-balanced expansion: each CTA owns EMIT_CHUNK consecutive output slots,
+// finds the Gaussians that own them, and writes one (tile, id) pair per slot
+// with coalesced stores.  Work per CTA is independent of footprint sizes.
+constexpr int EMIT_CHUNK = 2048;
+__global__ void __launch_bounds__(T)
+emit_expand(const uint32_t *__restrict__ off, const uint32_t *__restrict__ sorted_gid,
+            const uint2 *__restrict__ rect, const uint32_t *__restrict__ d_n,
+            const uint32_t *__restrict__ counters, int tiles_x, uint32_t *__restrict__ ikey,
+            uint32_t *__restrict__ ival) {
+    __shared__ uint32_t s_off[EMIT_CHUNK + 1];
+    __shared__ uint32_t s_gid[EMIT_CHUNK + 1];
+    __shared__ uint2 s_rect[EMIT_CHUNK + 1];
+    __shared__ uint32_t s_range[2];
+    const uint32_t X = counters[CNT_SORT_N];   // 0 when the capacity was exceeded
+    const uint32_t n = *d_n;
+    for (uint32_t o0 = blockIdx.x * uint32_t(EMIT_CHUNK); o0 < X; o0 += gridDim.x * uint32_t(EMIT_CHUNK)) {
+        const uint32_t o1 = min(X, o0 + uint32_t(EMIT_CHUNK));
+        if (threadIdx.x < 32) {
+            const uint32_t s0 = warp_upper_index(off, n, o0);
+            const uint32_t s1 = warp_upper_index(off, n, o1 - 1);
+            if (threadIdx.x == 0) { s_range[0] = s0; s_range[1] = s1; }
         }
-        if (lane == 31) s_w[warp] = x;
         __syncthreads();
-        uint32_t off = s_run + x - c;
-        for (int w = 0; w < warp; ++w) off += s_w[w];
-        if (c) {
-            const uint2 rc = rect[g];
-            const int tx0 = rc.x & 0xFFFF, ty0 = rc.x >> 16, tx1 = rc.y & 0xFFFF, ty1 = rc.y >> 16;
-            for (int ty = ty0; ty <= ty1; ++ty)
-                for (int tx = tx0; tx <= tx1; ++tx) {
-                    ikey[off] = uint32_t(ty * tiles_x + tx);
-                    ival[off] = g;
-                    ++off;
-                }
+        const uint32_t s0 = s_range[0], len = s_range[1] - s_range[0] + 1;   // <= EMIT_CHUNK
+        for (uint32_t i = threadIdx.x; i < len; i += T) {
+            const uint32_t g = sorted_gid[s0 + i];
+            s_off[i] = off[s0 + i];
+            s_gid[i] = g;
+            s_rect[i] = rect[g];
         }
         __syncthreads();
-        if (threadIdx.x == T - 1) {
-            uint32_t t = 0;
-            for (int w = 0; w < WARPS; ++w) t += s_w[w];
-            s_run += t;
+        for (uint32_t o = o0 + threadIdx.x; o < o1; o += T) {
+            uint32_t lo = 0, hi = len;             // last local index with s_off <= o
+            while (hi - lo > 1) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (s_off[mid] <= o) lo = mid; else hi = mid;
+            }
+            const uint2 rc = s_rect[lo];
+            const uint32_t tx0 = rc.x & 0xFFFFu, ty0 = rc.x >> 16, tx1 = rc.y & 0xFFFFu;
+            const uint32_t wx = tx1 - tx0 + 1, j = o - s_off[lo];
+            ikey[o] = (ty0 + j / wx) * uint32_t(tiles_x) + tx0 + j % wx;
+            ival[o] = s_gid[lo];
         }
         __syncthreads();
     }
@@ -403,14 +436,19 @@ cudaError_t launch_sort(const qr_frame &f, cudaStream_t s) {
     const uint32_t *sorted_gid = slot<uint32_t>(f, in_b ? S_DVAL1 : S_DVAL0);
     // 2. scan of tile counts in depth order + emit
     uint32_t *blocksum = slot<uint32_t>(f, S_BLOCKSUM);
+    uint32_t *offs = slot<uint32_t>(f, in_b ? S_DKEY0 : S_DKEY1);  // the free key buffer
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     emit_upsweep<<<nb_depth, T, 0, s>>>(sorted_gid, slot<uint32_t>(f, S_TCOUNT),
                                         counters + CNT_VISIBLE, blocksum);
     emit_scan<<<1, 1024, 0, s>>>(blocksum, nb_depth, counters, uint32_t(f.max_isect));
-    emit_pairs<<<nb_depth, T, 0, s>>>(sorted_gid, slot<uint32_t>(f, S_TCOUNT),
-                                      slot<uint2>(f, S_RECT), counters + CNT_VISIBLE, blocksum,
-                                      counters, f.tiles_x, slot<uint32_t>(f, S_IKEY0),
-                                      slot<uint32_t>(f, S_IVAL0));
-    count_launch(3);
+    emit_offsets<<<nb_depth, T, 0, s>>>(sorted_gid, slot<uint32_t>(f, S_TCOUNT),
+                                        counters + CNT_VISIBLE, blocksum, offs);
+    emit_expand<<<sms * 2, T, 0, s>>>(offs, sorted_gid, slot<uint2>(f, S_RECT),
+                                      counters + CNT_VISIBLE, counters, f.tiles_x,
+                                      slot<uint32_t>(f, S_IKEY0), slot<uint32_t>(f, S_IVAL0));
+    count_launch(4);
     // 3. stable sort of the intersections by tile id
     int ib = 0;
     e = radix_sort_pairs(slot<uint32_t>(f, S_IKEY0), slot<uint32_t>(f, S_IVAL0),
@@ -420,9 +458,6 @@ cudaError_t launch_sort(const qr_frame &f, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     // 4. tile ranges
     const uint32_t *ikey = slot<uint32_t>(f, ib ? S_IKEY1 : S_IKEY0);
-    int dev = 0, sms = 152;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     tile_ranges<<<sms * 4, T, 0, s>>>(ikey, counters, slot<uint2>(f, S_RANGES));
     count_launch();
     return cudaGetLastError();

@@ -106,12 +106,17 @@ def test_tile_lists_sorted_and_conservative():
     rng = _device_copy(v.tile_range, 2 * tiles, torch.int32).cpu().numpy().reshape(tiles, 2)
     pr = oracle.project(g, cam.as_array())
     # the GPU's own per-Gaussian depth keys, recovered from the sorted (key, id) pairs
-    skey = _device_copy(v.depth_key, g.n, torch.int32).cpu().numpy().view(np.uint32)
-    sgid = _device_copy(v.sorted_gid, g.n, torch.int32).cpu().numpy()
-    assert (np.diff(skey.astype(np.int64)) >= 0).all()
-    key_of = np.empty(g.n, np.uint32)
-    key_of[sgid] = skey
-    depth32 = key_of.view(np.float32)
+    cnt = _device_copy(v.counters, 8, torch.int32).cpu().numpy()
+    n_kept = int(cnt[2])
+    gkey = _device_copy(v.depth_key, g.n, torch.int32).cpu().numpy().view(np.uint32)
+    skey = _device_copy(v.sorted_key, n_kept, torch.int32).cpu().numpy().view(np.uint32)
+    sgid = _device_copy(v.sorted_gid, n_kept, torch.int32).cpu().numpy()
+    # the kept set is every Gaussian with a finite key, sorted by (key, id)
+    kept = np.nonzero(gkey != 0xFFFFFFFF)[0]
+    assert n_kept == len(kept)
+    np.testing.assert_array_equal(sgid, kept[np.lexsort((kept, gkey[kept]))])
+    np.testing.assert_array_equal(skey, gkey[sgid])
+    depth32 = gkey.view(np.float32)
     assert (np.diff(keys) >= 0).all()
     for t in range(tiles):
         a, b = rng[t]

@@ -223,6 +223,33 @@ qr_status qr_render_host(qr_frame *frame, const float *mean_host, const float *l
                          int32_t C, void *dev_inputs, void *dev_outputs, float *out_host,
                          qr_stream stream);
 
+/* ---------------------------------------------------------------- allocation-free variant */
+
+/* No counterpart in the paper.  The Q-Render forward of qr_render for callers
+ * that may not allocate device memory: a plug-in whose host application owns
+ * all device memory through its own pool, a real-time loop in which an
+ * allocation could block or fail, or code that prepares everything before a
+ * CUDA graph is recorded.  Inputs and outputs are the caller's, with the
+ * meaning and layout of qr_render for n Gaussians and the given camera and
+ * params; the scratch workspace qr_render would take from the caller is a
+ * 16 MiB static device array inside this library instead, which every GPU
+ * that loads the library holds until the process exits.
+ * Limits: n <= 65,536 Gaussians and width * height <= 65,536 pixels (larger
+ * inputs are rejected with QR_ERR_INVALID_ARG before anything is launched),
+ * and at most 524,288 tile-Gaussian intersections (an overflow is reported
+ * by qr_frame_status on *frame_out, which describes the static workspace
+ * until the next call; frame_out may be NULL).
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  All calls share the one array: calls that
+ * overlap on the GPU race.  A call allocates nothing: no cudaMalloc, no
+ * cudaFree, no allocating library routine. */
+qr_status qr_render_noalloc(const float *mean, const float *log_scale, const float *quat,
+                            const float *opacity, int64_t n, const qr_camera *camera,
+                            const qr_params *params, const void *feat, const float *feat_scale,
+                            qr_dtype dtype, int32_t C, int32_t *ids, float *weights,
+                            uint8_t *counts, float *out, qr_frame *frame_out, qr_stream stream);
+
 /* ---------------------------------------------------------------- instrumentation */
 
 /* Number of kernels this library has launched since it was loaded. */

@@ -87,6 +87,9 @@ SIGNATURES = {
     "qr_render_host": (_S, [ctypes.POINTER(qr_frame), _P, _P, _P, _P, _P, _P, _S, _I32, _P, _P,
                             _P, _P]),
     "qr_launch_count": (ctypes.c_uint64, []),
+    "qr_render_noalloc": (_S, [_P, _P, _P, _P, _I64, ctypes.POINTER(qr_camera),
+                               ctypes.POINTER(qr_params), _P, _P, _S, _I32, _P, _P, _P, _P,
+                               ctypes.POINTER(qr_frame), _P]),
 }
 
 _lib = None
@@ -285,6 +288,23 @@ def qr_render_host(fr: Frame, mean_h, log_scale_h, quat_h, opacity_h, feat_h, fe
                                  hp(quat_h), hp(opacity_h), hp(feat_h), hp(feat_scale_h),
                                  dtype_code, C, _ptr(dev_inputs), _ptr(dev_outputs), hp(out_h),
                                  _stream(stream)), "qr_render_host")
+
+
+def qr_render_noalloc(mean, log_scale, quat, opacity, cam, params, feat, feat_scale, ids,
+                      weights, counts, out, stream=None) -> Frame:
+    """qr_render without any device allocation (scratch in the library's static array).
+
+    Returns a Frame describing the static workspace (valid until the next
+    call) for qr_frame_status."""
+    camc = cam if isinstance(cam, qr_camera) else make_camera(cam)
+    f = qr_frame()
+    _check(load().qr_render_noalloc(_ptr(mean), _ptr(log_scale), _ptr(quat), _ptr(opacity),
+                                    mean.shape[0], ctypes.byref(camc), ctypes.byref(params),
+                                    _ptr(feat), _ptr(feat_scale), _dtype_code(feat),
+                                    feat.shape[1], _ptr(ids), _ptr(weights), _ptr(counts),
+                                    _ptr(out), ctypes.byref(f), _stream(stream)),
+           "qr_render_noalloc")
+    return Frame(f, None, camc, params)
 
 
 def qr_launch_count() -> int:

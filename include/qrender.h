@@ -108,11 +108,10 @@ typedef struct {
     const float *opacity;        /* [n]: alpha of each kept Gaussian                                   */
     const uint32_t *depth_key;   /* [n]: FP32 bit pattern of camera depth; 0xFFFFFFFF when culled      */
     const uint32_t *tile_count;  /* [n]: tiles touched by Gaussian i's footprint                       */
-    const uint32_t *sorted_key;  /* [n_kept]: depth keys in ascending (depth, id) order                */
-    const uint32_t *sorted_gid;  /* [n_kept]: Gaussian ids in (depth, id) order                        */
-    const uint32_t *isect_tile;  /* [max_isect]: tile id of each sorted intersection                   */
-    const uint32_t *isect_gid;   /* [max_isect]: Gaussian id of each sorted intersection               */
-    const uint32_t *tile_range;  /* [tiles][2]: [begin, end) of each tile in the sorted list           */
+    const uint32_t *kept_gid;    /* [n_kept]: ids of the Gaussians with a footprint, ascending          */
+    const uint32_t *kept_offset; /* [n_kept]: first intersection slot of each kept Gaussian             */
+    const uint32_t *isect_gid;   /* [n_isect]: per tile, the Gaussian ids in (depth, id) order          */
+    const uint32_t *tile_range;  /* [tiles][2]: [begin, end) of each tile in isect_gid                  */
     const uint32_t *counters;    /* [8]: status, n_isect, n_kept, n, n_emitted                         */
 } qr_frame_view;
 
@@ -162,13 +161,14 @@ qr_status qr_frame_status(const qr_frame *frame, qr_stream stream, int64_t *n_is
 qr_status qr_project(qr_frame *frame, const float *mean, const float *log_scale,
                      const float *quat, const float *opacity, qr_stream stream);
 
-/* Sec. 3 "tiling strategy" + the depth-ordered list I of Sec. 4.2: sorts the
- * Gaussians by (depth, id) with a hand-written LSD radix sort of the 32-bit
- * depth keys, emits one (tile, Gaussian) intersection per touched tile in that
- * order, stably radix-sorts the intersections by tile id, and records each
- * tile's [begin, end) range.  The result is the order a sort of 64-bit
- * (tile << 32 | depth) keys would give, with equal depths broken by id.
- * Overflow of max_isect is reported through qr_frame_status. */
+/* Sec. 3 "tiling strategy" + the depth-ordered list I of Sec. 4.2: bins every
+ * kept Gaussian into the screen tiles its footprint touches (load-balanced
+ * expansion), and sorts each tile's list by (camera depth, id) in shared
+ * memory with a hand-written bitonic network (chunked merge for lists larger
+ * than shared memory).  The result -- tile ranges and per-tile id lists -- is
+ * the order a sort of 64-bit (tile << 32 | depth) keys would give, with equal
+ * depths broken by id.  Overflow of max_isect is reported through
+ * qr_frame_status. */
 qr_status qr_sort(qr_frame *frame, qr_stream stream);
 
 /* Algorithm 1 (Sec. 4.2), selection half: for every pixel, walk the tile's

@@ -165,6 +165,138 @@ blend_kernel(const uint4 *__restrict__ feat, const float *__restrict__ scale, in
     }
 }
 
+// Wide rows (one warp per row): a warp owns a group of G neighbouring pixels
+// (2x2 for G = 4, 2x1 for G = 2) whose selections are subsequences of the same
+// tile list and mostly share rows.  Lane g*K + j holds entry j of pixel g;
+// __match_any_sync groups equal ids, the lowest lane of each group leads, and
+// each distinct row is loaded once and accumulated into every pixel of the
+// group with that pixel's weight (zero weights are skipped).  L1 row traffic
+// drops from sum(counts) to the number of distinct rows of the group.
+template <int G>
+__device__ __forceinline__ int64_t group_pixel(int64_t chunk0, int gi, int m, int W, int H,
+                                               int64_t items) {
+    int r;
+    if (G == 4) {
+        const int qx = gi & 7, qy = gi >> 3;
+        r = (2 * qy + (m >> 1)) * 16 + 2 * qx + (m & 1);
+    } else if (G == 2) {
+        r = (gi >> 3) * 16 + 2 * (gi & 7) + m;
+    } else {
+        r = gi;
+    }
+    const int64_t item = chunk0 + r;
+    if (item >= items) return -1;
+    return tile_order_pixel(item, W, H);
+}
+
+template <int DT, int VPL, int G>
+__global__ void __launch_bounds__(kThreads)
+blend_group_kernel(const uint4 *__restrict__ feat, const float *__restrict__ scale,
+                   int64_t n_gauss, const int32_t *__restrict__ ids,
+                   const float *__restrict__ wts, const uint8_t *__restrict__ cnt, int64_t P,
+                   int K, int W, int H, float4 *__restrict__ out) {
+    constexpr int CPV = Vec<DT>::C;
+    constexpr int ROWV = 32 * VPL;
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t items = (W > 0) ? int64_t((W + 15) >> 4) * ((H + 15) >> 4) * 256 : P;
+    const int64_t chunk0 = int64_t(blockIdx.x) * 256;
+    const unsigned kmask = (K >= 32) ? FULL : ((1u << K) - 1u);
+    for (int gi = warp; gi < 256 / G; gi += kThreads / 32) {
+        const int m = lane / K, j = lane - m * K;
+        int64_t p = -1;
+        if (m < G) p = (W > 0) ? group_pixel<G>(chunk0, gi, m, W, H, items)
+                               : (chunk0 + gi * G + m < items ? chunk0 + gi * G + m : -1);
+        int id = -1;
+        float w = 0.f;
+        if (p >= 0 && j < int(cnt[p])) {
+            id = ids[p * K + j];
+            w = wts[p * K + j];
+            if (uint64_t(int64_t(id)) >= uint64_t(n_gauss)) { id = -1; w = 0.f; }
+            else if (DT == QR_FP8E4M3) w *= scale[id];
+        }
+        const unsigned peers = __match_any_sync(FULL, id);
+        unsigned leaders = __ballot_sync(FULL, id >= 0 && lane == __ffs(peers) - 1);
+        float acc[G][VPL][CPV];
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+#pragma unroll
+            for (int v = 0; v < VPL; ++v)
+#pragma unroll
+                for (int q = 0; q < CPV; ++q) acc[g][v][q] = 0.f;
+        while (leaders) {
+            int L[2];
+            L[0] = __ffs(leaders) - 1;
+            leaders &= leaders - 1;
+            L[1] = leaders ? __ffs(leaders) - 1 : -1;
+            if (L[1] >= 0) leaders &= leaders - 1;
+            uint4 r[2][VPL];
+            float wg[2][G];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int src = L[u] >= 0 ? L[u] : 0;
+                const int rid = __shfl_sync(FULL, id, src);
+                const unsigned pe = __shfl_sync(FULL, peers, src);
+#pragma unroll
+                for (int g = 0; g < G; ++g) {
+                    // pixel g's weight for this row (summed if the pixel lists the id twice)
+                    unsigned b = (L[u] >= 0) ? (pe & (kmask << (g * K))) : 0u;
+                    float x = 0.f;
+                    while (b) {
+                        x += __shfl_sync(FULL, w, __ffs(b) - 1);
+                        b &= b - 1;
+                    }
+                    wg[u][g] = x;
+                }
+                const uint4 *row = feat + int64_t(rid) * ROWV + lane;
+#pragma unroll
+                for (int v = 0; v < VPL; ++v)
+                    r[u][v] = (L[u] >= 0) ? ld_row(row + 32 * v) : make_uint4(0, 0, 0, 0);
+            }
+#pragma unroll
+            for (int u = 0; u < 2; ++u)
+#pragma unroll
+                for (int g = 0; g < G; ++g)
+                    if (wg[u][g] != 0.f) {
+#pragma unroll
+                        for (int v = 0; v < VPL; ++v) decode_fma<DT>(r[u][v], wg[u][g], acc[g][v]);
+                    }
+        }
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const int64_t pg = __shfl_sync(FULL, p, g * K < 32 ? g * K : 0);
+            if (pg >= 0) {
+                float4 *o = out + pg * (int64_t(ROWV) * CPV / 4);
+#pragma unroll
+                for (int v = 0; v < VPL; ++v)
+#pragma unroll
+                    for (int q = 0; q < CPV / 4; ++q)
+                        st_stream(o + int64_t(lane + 32 * v) * (CPV / 4) + q,
+                                  make_float4(acc[g][v][4 * q], acc[g][v][4 * q + 1],
+                                              acc[g][v][4 * q + 2], acc[g][v][4 * q + 3]));
+            }
+        }
+    }
+}
+
+template <int DT, int VPL>
+cudaError_t run_group(const void *feat, const float *scale, int64_t n_gauss, const int32_t *ids,
+                      const float *w, const uint8_t *cnt, int64_t P, int K, int W, int H,
+                      float *out, cudaStream_t s) {
+    const int64_t items = (W > 0) ? int64_t((W + 15) >> 4) * ((H + 15) >> 4) * 256 : P;
+    const unsigned blocks = unsigned((items + 255) / 256);
+    const uint4 *f = static_cast<const uint4 *>(feat);
+    float4 *o = reinterpret_cast<float4 *>(out);
+    if (K <= 8)
+        blend_group_kernel<DT, VPL, 4><<<blocks, kThreads, 0, s>>>(f, scale, n_gauss, ids, w, cnt, P, K, W, H, o);
+    else if (K <= 16)
+        blend_group_kernel<DT, VPL, 2><<<blocks, kThreads, 0, s>>>(f, scale, n_gauss, ids, w, cnt, P, K, W, H, o);
+    else
+        blend_group_kernel<DT, VPL, 1><<<blocks, kThreads, 0, s>>>(f, scale, n_gauss, ids, w, cnt, P, K, W, H, o);
+    count_launch();
+    return cudaGetLastError();
+}
+
 template <int DT, int LPP, int VPL>
 cudaError_t run(const void *feat, const float *scale, int64_t n_gauss, const int32_t *ids,
                 const float *w, const uint8_t *cnt, int64_t P, int K, int W, int H, float *out,
@@ -189,10 +321,10 @@ cudaError_t dispatch(const void *feat, const float *scale, int64_t n_gauss, int 
         case 4: return run<DT, 4, 1>(feat, scale, n_gauss, ids, w, cnt, P, K, W, H, out, s);
         case 8: return run<DT, 8, 1>(feat, scale, n_gauss, ids, w, cnt, P, K, W, H, out, s);
         case 16: return run<DT, 16, 1>(feat, scale, n_gauss, ids, w, cnt, P, K, W, H, out, s);
-        case 32: return run<DT, 32, 1>(feat, scale, n_gauss, ids, w, cnt, P, K, W, H, out, s);
-        case 64: return run<DT, 32, 2>(feat, scale, n_gauss, ids, w, cnt, P, K, W, H, out, s);
-        case 96: return run<DT, 32, 3>(feat, scale, n_gauss, ids, w, cnt, P, K, W, H, out, s);
-        case 128: return run<DT, 32, 4>(feat, scale, n_gauss, ids, w, cnt, P, K, W, H, out, s);
+        case 32: return run_group<DT, 1>(feat, scale, n_gauss, ids, w, cnt, P, K, W, H, out, s);
+        case 64: return run_group<DT, 2>(feat, scale, n_gauss, ids, w, cnt, P, K, W, H, out, s);
+        case 96: return run_group<DT, 3>(feat, scale, n_gauss, ids, w, cnt, P, K, W, H, out, s);
+        case 128: return run_group<DT, 4>(feat, scale, n_gauss, ids, w, cnt, P, K, W, H, out, s);
         case 256: return run<DT, 32, 8>(feat, scale, n_gauss, ids, w, cnt, P, K, W, H, out, s);
         default: return cudaErrorInvalidValue;
     }

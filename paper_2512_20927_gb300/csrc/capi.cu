@@ -50,20 +50,23 @@ size_t layout(int64_t n, int W, int H, const qr_params *p, int64_t cap, size_t *
     if (tx > 65535 || ty > 65535) return 0;
     const size_t N = size_t(n), X = size_t(cap), tiles = size_t(tx * ty);
     size_t sizes[S_END];
+    const size_t nblk = (N + kProjectThreads - 1) / kProjectThreads + 1;
     sizes[S_COUNTERS] = CNT_WORDS * 4;
     sizes[S_REC_M] = N * 16;
     sizes[S_REC_C] = N * 16;
     sizes[S_REC_A] = N * 4;
     sizes[S_RECT] = N * 8;
     sizes[S_TCOUNT] = N * 4;
-    sizes[S_DKEY0] = sizes[S_DKEY1] = sizes[S_DVAL0] = sizes[S_DVAL1] = N * 4;
-    sizes[S_IKEY0] = sizes[S_IKEY1] = sizes[S_IVAL0] = sizes[S_IVAL1] = X * 4;
-    sizes[S_RANGES] = tiles * 8;
-    sizes[S_HIST] = size_t(1 << kRadixBitsMax) * kSortMaxBlocks * 4;
-    sizes[S_DIGITSUM] = size_t(1 << kRadixBitsMax) * 4;
-    sizes[S_BLOCKSUM] = (kSortMaxBlocks + 1) * 4;
-    sizes[S_VISCNT] = ((N + kProjectThreads - 1) / kProjectThreads + 1) * 4;
     sizes[S_GKEY] = N * 4;
+    sizes[S_VISCNT] = nblk * 4;
+    sizes[S_BSUM] = nblk * 4;
+    sizes[S_KID] = N * 4;
+    sizes[S_OFF] = N * 4;
+    sizes[S_TCNT] = tiles * 4;
+    sizes[S_RANGES] = tiles * 8;
+    sizes[S_KEYS64] = X * 8;
+    sizes[S_SCRATCH64] = X * 8;
+    sizes[S_IGID] = X * 4;
     size_t o = 0;
     for (int s = 0; s < S_END; ++s) {
         if (off) off[s] = o;
@@ -139,9 +142,7 @@ qr_status qr_frame_init(qr_frame *frame, int64_t n, const qr_camera *camera,
     f.tiles_x = (camera->width + params->tile_w - 1) / params->tile_w;
     f.tiles_y = (camera->height + params->tile_h - 1) / params->tile_h;
     f.sort_blocks = sort_blocks_for(max_isect);
-    const int bits = tile_bits_for(f.tiles_x * f.tiles_y);
-    const int passes = (bits + kRadixBitsMax - 1) / kRadixBitsMax;
-    f.isect_buf = passes & 1;
+    f.isect_buf = 0;
     f.ws = ws;
     f.ws_bytes = ws_bytes;
     *frame = f;
@@ -156,10 +157,9 @@ qr_status qr_frame_view_get(const qr_frame *frame, qr_frame_view *view) {
     view->opacity = slot<float>(f, S_REC_A);
     view->depth_key = slot<uint32_t>(f, S_GKEY);
     view->tile_count = slot<uint32_t>(f, S_TCOUNT);
-    view->sorted_key = slot<uint32_t>(f, S_DKEY0);  // 4 depth passes end in buffer a
-    view->sorted_gid = slot<uint32_t>(f, S_DVAL0);
-    view->isect_tile = slot<uint32_t>(f, f.isect_buf ? S_IKEY1 : S_IKEY0);
-    view->isect_gid = slot<uint32_t>(f, f.isect_buf ? S_IVAL1 : S_IVAL0);
+    view->kept_gid = slot<uint32_t>(f, S_KID);
+    view->kept_offset = slot<uint32_t>(f, S_OFF);
+    view->isect_gid = slot<uint32_t>(f, S_IGID);
     view->tile_range = slot<uint32_t>(f, S_RANGES);
     view->counters = slot<uint32_t>(f, S_COUNTERS);
     return QR_OK;

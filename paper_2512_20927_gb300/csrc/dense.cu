@@ -196,10 +196,9 @@ template <int DT, int CC, int PX, int CH>
 cudaError_t run(const qr_frame &f, const void *feat, const float *scale, int C, float *out,
                 float *T_final, cudaStream_t s) {
     dim3 grid(unsigned(num_tiles(f)), unsigned(C / CC));
-    const int ib = f.isect_buf;
     dense_kernel<DT, CC, PX, CH><<<grid, kThreads, 0, s>>>(
         slot<float4>(f, S_REC_M), slot<float4>(f, S_REC_C), slot<float>(f, S_REC_A),
-        slot<uint32_t>(f, ib ? S_IVAL1 : S_IVAL0),
+        slot<uint32_t>(f, S_IGID),
         slot<uint2>(f, S_RANGES), static_cast<const unsigned char *>(feat), scale, C, f.camera.width,
         f.camera.height, f.params.tile_w, f.tiles_x, f.params.alpha_min, f.params.alpha_max,
         f.params.T_min, out, T_final);

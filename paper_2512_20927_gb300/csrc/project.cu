@@ -43,14 +43,16 @@ project_kernel(int64_t n, const float *__restrict__ mean, const float *__restric
                int tiles_y, float4 *__restrict__ rec_m, float4 *__restrict__ rec_w,
                float *__restrict__ rec_a, uint2 *__restrict__ rect,
                uint32_t *__restrict__ tcount, uint32_t *__restrict__ dkey,
-               uint32_t *__restrict__ vis_count, uint32_t *__restrict__ counters) {
+               uint32_t *__restrict__ vis_count, uint32_t *__restrict__ tile_sum,
+               uint32_t *__restrict__ counters) {
     __shared__ int s_list[kThreads];
     __shared__ int s_warp[kThreads / 32];
     __shared__ int s_visible;
+    __shared__ uint32_t s_tiles;
 
     const int64_t base = int64_t(blockIdx.x) * kThreads;
     const int64_t g = base + threadIdx.x;
-    if (threadIdx.x == 0) s_visible = 0;
+    if (threadIdx.x == 0) { s_visible = 0; s_tiles = 0u; }
     if (blockIdx.x == 0 && threadIdx.x == 0) counters[CNT_N] = uint32_t(n);
 
     // ---------------- stage A: FP32 conservative footprint bound
@@ -95,6 +97,7 @@ project_kernel(int64_t n, const float *__restrict__ mean, const float *__restric
 
     // ---------------- stage B: exact projection of the survivors
     int visible = 0;
+    uint32_t tiles_touched = 0;
     for (int i = threadIdx.x; i < total; i += kThreads) {
         const int64_t gi = base + s_list[i];
         const float mx = mean[3 * gi], my = mean[3 * gi + 1], mz = mean[3 * gi + 2];
@@ -209,15 +212,26 @@ project_kernel(int64_t n, const float *__restrict__ mean, const float *__restric
         rec_w[gi] = waxes;
         rec_a[gi] = alpha;
         rect[gi] = make_uint2(uint32_t(tx0) | (uint32_t(ty0) << 16), uint32_t(tx1) | (uint32_t(ty1) << 16));
-        tcount[gi] = uint32_t((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
+        const uint32_t nt = uint32_t((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
+        tcount[gi] = nt;
         dkey[gi] = __float_as_uint(c[2].hi);
         ++visible;
+        tiles_touched += nt;
     }
-    // per-CTA count of kept Gaussians (consumed by the order-preserving compaction)
-    for (int o = 16; o > 0; o >>= 1) visible += __shfl_xor_sync(0xffffffffu, visible, o);
-    if (lane == 0 && visible) atomicAdd(&s_visible, visible);
+    // per-CTA count of kept Gaussians and of their tiles (scanned by the binning)
+    for (int o = 16; o > 0; o >>= 1) {
+        visible += __shfl_xor_sync(0xffffffffu, visible, o);
+        tiles_touched += __shfl_xor_sync(0xffffffffu, tiles_touched, o);
+    }
+    if (lane == 0 && visible) {
+        atomicAdd(&s_visible, visible);
+        atomicAdd(&s_tiles, tiles_touched);
+    }
     __syncthreads();
-    if (threadIdx.x == 0) vis_count[blockIdx.x] = uint32_t(s_visible);
+    if (threadIdx.x == 0) {
+        vis_count[blockIdx.x] = uint32_t(s_visible);
+        tile_sum[blockIdx.x] = s_tiles;
+    }
     (void)tiles_x;
     (void)tiles_y;
 }
@@ -242,7 +256,7 @@ cudaError_t launch_project(const qr_frame &f, const float *mean, const float *lo
         f.params.tile_w, f.params.tile_h, f.tiles_x, f.tiles_y, slot<float4>(f, S_REC_M),
         slot<float4>(f, S_REC_C), slot<float>(f, S_REC_A), slot<uint2>(f, S_RECT),
         slot<uint32_t>(f, S_TCOUNT), slot<uint32_t>(f, S_GKEY), slot<uint32_t>(f, S_VISCNT),
-        counters);
+        slot<uint32_t>(f, S_BSUM), counters);
     count_launch();
     return cudaGetLastError();
 }

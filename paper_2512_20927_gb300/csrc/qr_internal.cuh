@@ -11,17 +11,15 @@ namespace qr {
 // ---------------------------------------------------------------- status word
 // counters[0]: device status (a qr_status value, 0 = OK)
 // counters[1]: number of tile-Gaussian intersections the frame needs
-// counters[2]: number of Gaussians with a non-empty footprint
-// counters[3]: number of Gaussians n (item count of the depth sort)
+// counters[2]: number of kept Gaussians (non-empty footprint)
+// counters[3]: number of Gaussians n
 // counters[4]: number of intersections actually emitted (0 on overflow)
 enum { CNT_STATUS = 0, CNT_ISECT = 1, CNT_VISIBLE = 2, CNT_N = 3, CNT_SORT_N = 4, CNT_WORDS = 8 };
 
 // Workspace slots (byte offsets in qr_frame::off).
 enum Slot {
-    S_COUNTERS = 0, S_REC_M, S_REC_C, S_REC_A, S_RECT, S_TCOUNT,
-    S_DKEY0, S_DKEY1, S_DVAL0, S_DVAL1,
-    S_IKEY0, S_IKEY1, S_IVAL0, S_IVAL1,
-    S_RANGES, S_HIST, S_DIGITSUM, S_BLOCKSUM, S_VISCNT, S_GKEY,
+    S_COUNTERS = 0, S_REC_M, S_REC_C, S_REC_A, S_RECT, S_TCOUNT, S_GKEY,
+    S_VISCNT, S_BSUM, S_KID, S_OFF, S_TCNT, S_RANGES, S_KEYS64, S_SCRATCH64, S_IGID,
     S_END
 };
 constexpr int kProjectThreads = 256;
@@ -71,6 +69,52 @@ cudaError_t radix_sort_pairs(uint32_t *keys_a, uint32_t *vals_a, uint32_t *keys_
 
 int sort_blocks_for(int64_t capacity);
 int tile_bits_for(int tiles);
+
+// ---------------------------------------------------------------- block scans
+// Inclusive scan of one value per thread across the CTA (blockDim.x a
+// multiple of 32, at most 1024); returns the inclusive prefix and the total.
+__device__ __forceinline__ uint32_t block_inclusive_scan(uint32_t v, uint32_t *s_w, uint32_t &total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_w[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = (lane < nw) ? s_w[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        s_w[lane] = w;
+    }
+    __syncthreads();
+    const uint32_t r = x + (warp > 0 ? s_w[warp - 1] : 0u);
+    total = s_w[nw - 1];
+    __syncthreads();
+    return r;
+}
+
+// Exclusive scan of `total` u32 in place by one CTA: coalesced chunks of
+// blockDim.x elements with a running carry.  Returns the grand total to
+// thread 0 through *sum_out (nullable).
+__device__ __forceinline__ void cta_exclusive_scan(uint32_t *data, int total, uint32_t *sum_out) {
+    __shared__ uint32_t s_w[32];
+    uint32_t carry = 0;
+    for (int base = 0; base < total; base += blockDim.x) {
+        const int i = base + threadIdx.x;
+        const uint32_t v = i < total ? data[i] : 0u;
+        uint32_t chunk;
+        const uint32_t inc = block_inclusive_scan(v, s_w, chunk);
+        if (i < total) data[i] = carry + inc - v;
+        carry += chunk;
+    }
+    if (sum_out && threadIdx.x == 0) *sum_out = carry;
+}
 
 // ---------------------------------------------------------------- per-pixel Gaussian
 // Every kernel evaluates alpha' at a pixel the same way.  The projected

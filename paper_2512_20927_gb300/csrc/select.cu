@@ -118,10 +118,9 @@ cudaError_t launch_select(const qr_frame &f, int32_t *ids, float *w, uint8_t *cn
                                              int(dyn));
         if (e != cudaSuccess) return e;
     }
-    const int ib = f.isect_buf;  // which buffer holds the sorted intersections
     select_kernel<<<tiles, kThreads, dyn, s>>>(
         slot<float4>(f, S_REC_M), slot<float4>(f, S_REC_C), slot<float>(f, S_REC_A),
-        slot<uint32_t>(f, ib ? S_IVAL1 : S_IVAL0),
+        slot<uint32_t>(f, S_IGID),
         slot<uint2>(f, S_RANGES), f.camera.width, f.camera.height, f.params.tile_w, f.tiles_x, K,
         f.params.alpha_min, f.params.alpha_max, ids, w, cnt);
     count_launch();

@@ -1,271 +1,52 @@
-// K2-K4: binning, radix sort and tile ranges (Sec. 3 "tiling strategy"; the
-// depth-ordered index list I of Sec. 4.2).
+// K2-K4: binning, per-tile depth sort and tile ranges (Sec. 3 "tiling
+// strategy"; the depth-ordered index list I of each ray, Sec. 4.2).
 //
-// Order produced: intersections sorted by (tile id, depth, Gaussian id), the
-// order of a stable sort of 64-bit (tile << 32 | depth-bits) keys over
-// id-ordered input.  It is built as
-//   1. a stable LSD radix sort of the N 32-bit depth keys (ids as values),
-//   2. an exclusive scan of the per-Gaussian tile counts in that order and an
-//      emit of one (tile, id) pair per touched tile, in depth order,
-//   3. a stable LSD radix sort of the X intersections by tile id only
-//      (ceil(log2 tiles) bits, <= 8 bits per pass).
-// The depth digits are therefore sorted once per Gaussian instead of once per
-// intersection -- the lower-digit passes of the 64-bit LSD sort hoisted in
-// front of the duplication, which preserves relative order.
+// Result: for every screen tile, the ids of the Gaussians whose footprint
+// touches it, ordered by (camera depth, id) -- the order a stable sort of
+// 64-bit (tile << 32 | depth) keys over id-ordered input gives.
 //
-// Every pass is reduce-then-scan: per-block digit histograms, one scan of the
-// [digit][block] table, then a stable scatter.  No CTA ever waits for another,
-// so nothing here can spin.  Item counts are read from device memory, so the
-// whole stage can be captured in a CUDA graph with worst-case grids.
+// GB300 design (6 kernels after the projection, no global depth sort):
+//   1. project (K1) writes, per CTA of 256 Gaussians, how many it kept and the
+//      sum of their tile counts;
+//   2. offsets_scan + offsets_apply compact the kept Gaussians (id order) and
+//      give each its first output slot (exclusive scan), with the capacity
+//      check; offsets of kept Gaussians are strictly increasing;
+//   3. expand_count: a load-balanced expansion -- each CTA owns 2048
+//      consecutive output slots, finds their owners with a warp-wide 32-way
+//      search (at most 2048 owners per chunk), derives each slot's tile from
+//      the owner's footprint rectangle, and counts intersections per tile with
+//      warp-aggregated atomics;
+//   4. tile_scan: per-tile offsets, i.e. the tile ranges;
+//   5. expand_scatter: the same expansion writes (depth << 32 | id) into its
+//      tile's bucket at an atomically claimed position;
+//   6. tile_sort: one CTA per tile sorts its bucket in shared memory (bitonic
+//      network over the unique 64-bit keys) and writes the ids; a bucket
+//      larger than shared memory is sorted in chunks and merged in global
+//      memory by the same CTA (merge path), so no size is refused.
+// Keys are unique, so the order inside a bucket before step 6 does not matter
+// and the result is deterministic.  No CTA waits for another.  Counts live in
+// device memory, so the stage can be captured in a CUDA graph.
 #include "qr_internal.cuh"
 
 namespace qr {
 namespace {
 
-constexpr int T = kSortThreads;      // 256
-constexpr int IPT = kSortItems;      // 8
-constexpr int TILE = kSortTile;      // 2048
-constexpr int WARPS = T / 32;
+constexpr int T = 256;
+constexpr int EMIT_CHUNK = 2048;
+constexpr int TS_CAP = 8192;             // keys a tile sorts in shared memory (64 KB)
 
-__device__ __forceinline__ void block_tiles(uint32_t n, int b, int nb, uint32_t &t0, uint32_t &t1) {
-    const uint32_t tiles = (n + TILE - 1) / TILE;
-    const uint32_t per = (tiles + nb - 1) / nb;
-    t0 = min(tiles, uint32_t(b) * per);
-    t1 = min(tiles, t0 + per);
-}
-
-__device__ __forceinline__ unsigned lanemask_lt() {
-    unsigned m;
-    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
-    return m;
-}
-
-// ------------------------------------------------------------------ radix pass
-__global__ void __launch_bounds__(T)
-radix_upsweep(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ d_count, int shift,
-              int bits, uint32_t *__restrict__ hist) {
-    __shared__ uint32_t s_h[WARPS][1 << kRadixBitsMax];
-    const int radix = 1 << bits;
-    const uint32_t mask = uint32_t(radix - 1);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int i = threadIdx.x; i < WARPS * radix; i += T) (&s_h[0][0])[(i / radix) * (1 << kRadixBitsMax) + i % radix] = 0;
-    __syncthreads();
-    const uint32_t n = *d_count;
-    uint32_t t0, t1;
-    block_tiles(n, blockIdx.x, gridDim.x, t0, t1);
-    const uint32_t end = min(n, t1 * TILE);
-    for (uint32_t base = t0 * TILE; base < end; base += T) {   // uniform trip count
-        const uint32_t i = base + threadIdx.x;
-        const bool valid = i < end;
-        const uint32_t d = valid ? (keys[i] >> shift) & mask : 0xFFFFFFFFu;
-        const unsigned peers = __match_any_sync(0xffffffffu, d);
-        if (valid && lane == __ffs(peers) - 1) atomicAdd(&s_h[warp][d], uint32_t(__popc(peers)));
-    }
-    __syncthreads();
-    for (int d = threadIdx.x; d < radix; d += T) {
-        uint32_t s = 0;
-#pragma unroll
-        for (int w = 0; w < WARPS; ++w) s += s_h[w][d];
-        hist[d * gridDim.x + blockIdx.x] = s;
-    }
-}
-
-// Inclusive scan of one value per thread across the CTA (blockDim.x a
-// multiple of 32, at most 1024); returns the inclusive prefix and the total.
-__device__ __forceinline__ uint32_t block_inclusive_scan(uint32_t v, uint32_t *s_w, uint32_t &total) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    uint32_t x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) s_w[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-        uint32_t w = (lane < nw) ? s_w[lane] : 0u;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
-            if (lane >= o) w += y;
-        }
-        s_w[lane] = w;
-    }
-    __syncthreads();
-    const uint32_t r = x + (warp > 0 ? s_w[warp - 1] : 0u);
-    total = s_w[nw - 1];
-    __syncthreads();
-    return r;
-}
-
-// Exclusive scan of `total` u32 in place by one CTA: coalesced chunks of
-// blockDim.x elements with a running carry.  Returns the grand total to
-// thread 0 through *sum_out (nullable).
-__device__ void cta_exclusive_scan(uint32_t *data, int total, uint32_t *sum_out) {
-    __shared__ uint32_t s_w[32];
-    uint32_t carry = 0;
-    for (int base = 0; base < total; base += blockDim.x) {
-        const int i = base + threadIdx.x;
-        const uint32_t v = i < total ? data[i] : 0u;
-        uint32_t chunk;
-        const uint32_t inc = block_inclusive_scan(v, s_w, chunk);
-        if (i < total) data[i] = carry + inc - v;
-        carry += chunk;
-    }
-    if (sum_out && threadIdx.x == 0) *sum_out = carry;
-}
-
-// One warp per digit: exclusive scan of the digit's per-block counts (row d of
-// the [digit][block] table) in place; the row total goes to digitsum[d].
-__global__ void __launch_bounds__(256)
-radix_scan_rows(uint32_t *__restrict__ hist, int radix, int blocks, uint32_t *__restrict__ digitsum) {
-    const int d = blockIdx.x * 8 + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (d >= radix) return;
-    uint32_t *row = hist + size_t(d) * blocks;
-    uint32_t carry = 0;
-    for (int base = 0; base < blocks; base += 32) {
-        const int i = base + lane;
-        const uint32_t v = i < blocks ? row[i] : 0u;
-        uint32_t x = v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-        }
-        if (i < blocks) row[i] = carry + x - v;
-        carry += __shfl_sync(0xffffffffu, x, 31);
-    }
-    if (lane == 0) digitsum[d] = carry;
-}
-
-__global__ void __launch_bounds__(T)
-radix_downsweep(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
-                uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out,
-                const uint32_t *__restrict__ d_count, int shift, int bits,
-                const uint32_t *__restrict__ hist, const uint32_t *__restrict__ digitsum) {
-    __shared__ uint32_t s_base[1 << kRadixBitsMax];
-    __shared__ uint32_t s_scan[32];
-    __shared__ uint32_t s_tot[1 << kRadixBitsMax];
-    __shared__ uint32_t s_w[WARPS][1 << kRadixBitsMax];
-    const int radix = 1 << bits;
-    const uint32_t mask = uint32_t(radix - 1);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const unsigned lt = lanemask_lt();
-    {   // base of digit d for this block = sum of smaller digits + this digit's earlier blocks
-        const uint32_t ds = threadIdx.x < radix ? digitsum[threadIdx.x] : 0u;
-        uint32_t tot;
-        const uint32_t inc = block_inclusive_scan(ds, s_scan, tot);
-        if (threadIdx.x < radix) s_base[threadIdx.x] = inc - ds + hist[threadIdx.x * gridDim.x + blockIdx.x];
-    }
-    const uint32_t n = *d_count;
-    uint32_t t0, t1;
-    block_tiles(n, blockIdx.x, gridDim.x, t0, t1);
-    for (uint32_t tile = t0; tile < t1; ++tile) {
-        for (int i = threadIdx.x; i < WARPS * radix; i += T) s_w[i / radix][i % radix] = 0;
-        __syncthreads();
-        uint32_t key[IPT], val[IPT], rank[IPT], dig[IPT];
-        const uint32_t wbase = tile * TILE + warp * (32 * IPT);
-#pragma unroll
-        for (int r = 0; r < IPT; ++r) {
-            const uint32_t idx = wbase + r * 32 + lane;
-            const bool valid = idx < n;
-            key[r] = valid ? keys_in[idx] : 0u;
-            val[r] = valid ? vals_in[idx] : 0u;
-            dig[r] = valid ? (key[r] >> shift) & mask : 0xFFFFFFFFu;
-            const unsigned peers = __match_any_sync(0xffffffffu, dig[r]);
-            const uint32_t before = valid ? s_w[warp][dig[r]] : 0u;
-            rank[r] = before + __popc(peers & lt);
-            __syncwarp();
-            if (valid && lane == __ffs(peers) - 1) s_w[warp][dig[r]] = before + __popc(peers);
-            __syncwarp();
-        }
-        __syncthreads();
-        for (int d = threadIdx.x; d < radix; d += T) {
-            uint32_t run = 0;
-#pragma unroll
-            for (int w = 0; w < WARPS; ++w) {
-                const uint32_t c = s_w[w][d];
-                s_w[w][d] = run;
-                run += c;
-            }
-            s_tot[d] = run;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int r = 0; r < IPT; ++r) {
-            if (dig[r] != 0xFFFFFFFFu) {
-                const uint32_t pos = s_base[dig[r]] + s_w[warp][dig[r]] + rank[r];
-                keys_out[pos] = key[r];
-                vals_out[pos] = val[r];
-            }
-        }
-        __syncthreads();
-        for (int d = threadIdx.x; d < radix; d += T) s_base[d] += s_tot[d];
-        __syncthreads();
-    }
-}
-
-// ------------------------------------------------------------------ compaction
-// The kept Gaussians (finite depth key) are packed in id order, so the depth
-// sort works on the visible set only and equal depths keep id order.
+// ------------------------------------------------------------------ offsets
+// Exclusive scans of the per-CTA kept counts and tile-count sums.
 __global__ void __launch_bounds__(1024)
-compact_scan(uint32_t *vis_count, int nblk, uint32_t *counters) {
-    __shared__ uint32_t s_total;
-    cta_exclusive_scan(vis_count, nblk, &s_total);
+offsets_scan(uint32_t *kept, uint32_t *tsum, int nblk, uint32_t *counters, uint32_t capacity) {
+    __shared__ uint32_t s_total[2];
+    cta_exclusive_scan(kept, nblk, &s_total[0]);
     __syncthreads();
-    if (threadIdx.x == 0) counters[CNT_VISIBLE] = s_total;
-}
-
-__global__ void __launch_bounds__(kProjectThreads)
-compact_scatter(const uint32_t *__restrict__ gkey, const uint32_t *__restrict__ vis_off, int64_t n,
-                uint32_t *__restrict__ dkey, uint32_t *__restrict__ dval) {
-    __shared__ uint32_t s_w[kProjectThreads / 32];
-    const int64_t g = int64_t(blockIdx.x) * kProjectThreads + threadIdx.x;
-    const uint32_t key = g < n ? gkey[g] : 0xFFFFFFFFu;
-    const bool keep = key != 0xFFFFFFFFu;
-    const unsigned ballot = __ballot_sync(0xffffffffu, keep);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) s_w[warp] = __popc(ballot);
-    __syncthreads();
-    uint32_t off = vis_off[blockIdx.x] + __popc(ballot & ((1u << lane) - 1u));
-    for (int w = 0; w < warp; ++w) off += s_w[w];
-    if (keep) {
-        dkey[off] = key;
-        dval[off] = uint32_t(g);
-    }
-}
-
-// ------------------------------------------------------------------ emit
-// Block sums of the tile counts taken in depth order.
-__global__ void __launch_bounds__(T)
-emit_upsweep(const uint32_t *__restrict__ sorted_gid, const uint32_t *__restrict__ tcount,
-             const uint32_t *__restrict__ d_n, uint32_t *__restrict__ blocksum) {
-    __shared__ uint32_t s_w[WARPS];
-    const uint32_t n = *d_n;
-    uint32_t t0, t1;
-    block_tiles(n, blockIdx.x, gridDim.x, t0, t1);
-    const uint32_t end = min(n, t1 * TILE);
-    uint32_t s = 0;
-    for (uint32_t i = t0 * TILE + threadIdx.x; i < end; i += T) s += tcount[sorted_gid[i]];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = s;
+    cta_exclusive_scan(tsum, nblk, &s_total[1]);
     __syncthreads();
     if (threadIdx.x == 0) {
-        uint32_t t = 0;
-        for (int w = 0; w < WARPS; ++w) t += s_w[w];
-        blocksum[blockIdx.x] = t;
-    }
-}
-
-// Scan of the block sums; writes the intersection count and the capacity check.
-__global__ void __launch_bounds__(1024)
-emit_scan(uint32_t *blocksum, int nblocks, uint32_t *counters, uint32_t capacity) {
-    __shared__ uint32_t s_total;
-    cta_exclusive_scan(blocksum, nblocks, &s_total);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const uint32_t x = s_total;
+        const uint32_t x = s_total[1];
+        counters[CNT_VISIBLE] = s_total[0];
         counters[CNT_ISECT] = x;
         if (x > capacity) {
             counters[CNT_STATUS] = QR_ERR_CAPACITY;
@@ -276,29 +57,27 @@ emit_scan(uint32_t *blocksum, int nblocks, uint32_t *counters, uint32_t capacity
     }
 }
 
-// Per-Gaussian exclusive offsets of the intersection list, in depth order.
-__global__ void __launch_bounds__(T)
-emit_offsets(const uint32_t *__restrict__ sorted_gid, const uint32_t *__restrict__ tcount,
-             const uint32_t *__restrict__ d_n, const uint32_t *__restrict__ blocksum,
-             uint32_t *__restrict__ off) {
+// Compacted kept ids (id order) and their first output slots.
+__global__ void __launch_bounds__(kProjectThreads)
+offsets_apply(const uint32_t *__restrict__ tcount, const uint32_t *__restrict__ kept_base,
+              const uint32_t *__restrict__ tsum_base, int64_t n, uint32_t *__restrict__ kid,
+              uint32_t *__restrict__ koff) {
     __shared__ uint32_t s_w[32];
-    const uint32_t n = *d_n;
-    uint32_t t0, t1;
-    block_tiles(n, blockIdx.x, gridDim.x, t0, t1);
-    const uint32_t end = min(n, t1 * TILE);
-    uint32_t run = blocksum[blockIdx.x];
-    for (uint32_t base = t0 * TILE; base < end; base += T) {
-        const uint32_t i = base + threadIdx.x;
-        const uint32_t c = i < end ? tcount[sorted_gid[i]] : 0u;
-        uint32_t tot;
-        const uint32_t inc = block_inclusive_scan(c, s_w, tot);
-        if (i < end) off[i] = run + inc - c;
-        run += tot;
+    const int64_t g = int64_t(blockIdx.x) * kProjectThreads + threadIdx.x;
+    const uint32_t c = g < n ? tcount[g] : 0u;
+    const uint32_t k = c > 0 ? 1u : 0u;
+    uint32_t tot;
+    const uint32_t kinc = block_inclusive_scan(k, s_w, tot);
+    const uint32_t cinc = block_inclusive_scan(c, s_w, tot);
+    if (k) {
+        const uint32_t slot = kept_base[blockIdx.x] + kinc - 1u;
+        kid[slot] = uint32_t(g);
+        koff[slot] = tsum_base[blockIdx.x] + cinc - c;
     }
 }
 
-// Last index s in [0, n) with off[s] <= target (off[0] == 0 <= target), found
-// by one warp with 32-way splits.
+// Last index s in [0, n) with off[s] <= target (off[0] == 0 <= target), by
+// one warp with 32-way splits: the owner of output slot `target`.
 __device__ __forceinline__ uint32_t warp_upper_index(const uint32_t *off, uint32_t n, uint32_t target) {
     const int lane = threadIdx.x & 31;
     uint32_t lo = 0, hi = n;
@@ -315,94 +94,207 @@ __device__ __forceinline__ uint32_t warp_upper_index(const uint32_t *off, uint32
     return lo + __popc(__ballot_sync(0xffffffffu, le)) - 1;
 }
 
-// Load-balanced expansion: each CTA owns EMIT_CHUNK consecutive output slots,
-// finds the Gaussians that own them, and writes one (tile, id) pair per slot
-// with coalesced stores.  Work per CTA is independent of footprint sizes.
-constexpr int EMIT_CHUNK = 2048;
+// Owners of the slots [o0, o1) staged in shared memory (every kept Gaussian
+// owns at least one slot, so a chunk has at most EMIT_CHUNK owners).
+struct ExpandSmem {
+    uint32_t off[EMIT_CHUNK];
+    uint32_t gid[EMIT_CHUNK];
+    uint2 rect[EMIT_CHUNK];
+    uint32_t range[2];
+};
+
+__device__ __forceinline__ uint32_t stage_owners(ExpandSmem &sm, const uint32_t *koff,
+                                                 const uint32_t *kid, const uint2 *rect,
+                                                 uint32_t nk, uint32_t o0, uint32_t o1) {
+    if (threadIdx.x < 32) {
+        const uint32_t s0 = warp_upper_index(koff, nk, o0);
+        const uint32_t s1 = warp_upper_index(koff, nk, o1 - 1);
+        if (threadIdx.x == 0) { sm.range[0] = s0; sm.range[1] = s1; }
+    }
+    __syncthreads();
+    const uint32_t s0 = sm.range[0], len = sm.range[1] - sm.range[0] + 1;   // <= o1 - o0
+    for (uint32_t i = threadIdx.x; i < len; i += T) {
+        const uint32_t g = kid[s0 + i];
+        sm.off[i] = koff[s0 + i];
+        sm.gid[i] = g;
+        sm.rect[i] = rect[g];
+    }
+    __syncthreads();
+    return len;
+}
+
+__device__ __forceinline__ void slot_owner(const ExpandSmem &sm, uint32_t len, uint32_t o,
+                                           int tiles_x, uint32_t &g, uint32_t &tile) {
+    uint32_t lo = 0, hi = len;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (sm.off[mid] <= o) lo = mid; else hi = mid;
+    }
+    const uint2 rc = sm.rect[lo];
+    const uint32_t tx0 = rc.x & 0xFFFFu, ty0 = rc.x >> 16, tx1 = rc.y & 0xFFFFu;
+    const uint32_t wx = tx1 - tx0 + 1, j = o - sm.off[lo];
+    g = sm.gid[lo];
+    tile = (ty0 + j / wx) * uint32_t(tiles_x) + tx0 + j % wx;
+}
+
 __global__ void __launch_bounds__(T)
-emit_expand(const uint32_t *__restrict__ off, const uint32_t *__restrict__ sorted_gid,
-            const uint2 *__restrict__ rect, const uint32_t *__restrict__ d_n,
-            const uint32_t *__restrict__ counters, int tiles_x, uint32_t *__restrict__ ikey,
-            uint32_t *__restrict__ ival) {
-    __shared__ uint32_t s_off[EMIT_CHUNK + 1];
-    __shared__ uint32_t s_gid[EMIT_CHUNK + 1];
-    __shared__ uint2 s_rect[EMIT_CHUNK + 1];
-    __shared__ uint32_t s_range[2];
-    const uint32_t X = counters[CNT_SORT_N];   // 0 when the capacity was exceeded
-    const uint32_t n = *d_n;
+expand_count(const uint32_t *__restrict__ koff, const uint32_t *__restrict__ kid,
+             const uint2 *__restrict__ rect, const uint32_t *__restrict__ counters, int tiles_x,
+             uint32_t *__restrict__ tcnt) {
+    __shared__ ExpandSmem sm;
+    const uint32_t X = counters[CNT_SORT_N];        // 0 when the capacity was exceeded
+    const uint32_t nk = counters[CNT_VISIBLE];
     for (uint32_t o0 = blockIdx.x * uint32_t(EMIT_CHUNK); o0 < X; o0 += gridDim.x * uint32_t(EMIT_CHUNK)) {
         const uint32_t o1 = min(X, o0 + uint32_t(EMIT_CHUNK));
-        if (threadIdx.x < 32) {
-            const uint32_t s0 = warp_upper_index(off, n, o0);
-            const uint32_t s1 = warp_upper_index(off, n, o1 - 1);
-            if (threadIdx.x == 0) { s_range[0] = s0; s_range[1] = s1; }
-        }
-        __syncthreads();
-        const uint32_t s0 = s_range[0], len = s_range[1] - s_range[0] + 1;   // <= EMIT_CHUNK
-        for (uint32_t i = threadIdx.x; i < len; i += T) {
-            const uint32_t g = sorted_gid[s0 + i];
-            s_off[i] = off[s0 + i];
-            s_gid[i] = g;
-            s_rect[i] = rect[g];
-        }
-        __syncthreads();
-        for (uint32_t o = o0 + threadIdx.x; o < o1; o += T) {
-            uint32_t lo = 0, hi = len;             // last local index with s_off <= o
-            while (hi - lo > 1) {
-                const uint32_t mid = (lo + hi) >> 1;
-                if (s_off[mid] <= o) lo = mid; else hi = mid;
-            }
-            const uint2 rc = s_rect[lo];
-            const uint32_t tx0 = rc.x & 0xFFFFu, ty0 = rc.x >> 16, tx1 = rc.y & 0xFFFFu;
-            const uint32_t wx = tx1 - tx0 + 1, j = o - s_off[lo];
-            ikey[o] = (ty0 + j / wx) * uint32_t(tiles_x) + tx0 + j % wx;
-            ival[o] = s_gid[lo];
+        const uint32_t len = stage_owners(sm, koff, kid, rect, nk, o0, o1);
+        for (uint32_t base = o0; base < o1; base += T) {       // uniform trip count
+            const uint32_t o = base + threadIdx.x;
+            uint32_t g = 0, tile = 0xFFFFFFFFu;
+            if (o < o1) slot_owner(sm, len, o, tiles_x, g, tile);
+            const unsigned peers = __match_any_sync(0xffffffffu, tile);
+            if (o < o1 && int(threadIdx.x & 31) == __ffs(peers) - 1)
+                atomicAdd(&tcnt[tile], uint32_t(__popc(peers)));
         }
         __syncthreads();
     }
 }
 
-// ------------------------------------------------------------------ ranges
-__global__ void __launch_bounds__(T)
-tile_ranges(const uint32_t *__restrict__ ikey, const uint32_t *__restrict__ counters,
-            uint2 *__restrict__ ranges) {
-    const uint32_t n = counters[CNT_SORT_N];
-    for (uint32_t i = blockIdx.x * T + threadIdx.x; i < n; i += gridDim.x * T) {
-        const uint32_t t = ikey[i];
-        if (i == 0 || ikey[i - 1] != t) ranges[t].x = i;
-        if (i + 1 == n || ikey[i + 1] != t) ranges[t].y = i + 1;
+// Per-tile exclusive offsets -> ranges; the counts become zeroed cursors.
+__global__ void __launch_bounds__(1024)
+tile_scan(uint32_t *tcnt, int tiles, uint2 *ranges) {
+    __shared__ uint32_t s_w[32];
+    uint32_t carry = 0;
+    for (int base = 0; base < tiles; base += blockDim.x) {
+        const int t = base + threadIdx.x;
+        const uint32_t c = t < tiles ? tcnt[t] : 0u;
+        uint32_t chunk;
+        const uint32_t inc = block_inclusive_scan(c, s_w, chunk);
+        if (t < tiles) {
+            ranges[t] = make_uint2(carry + inc - c, carry + inc);
+            tcnt[t] = 0u;
+        }
+        carry += chunk;
     }
+}
+
+__global__ void __launch_bounds__(T)
+expand_scatter(const uint32_t *__restrict__ koff, const uint32_t *__restrict__ kid,
+               const uint2 *__restrict__ rect, const uint32_t *__restrict__ gkey,
+               const uint32_t *__restrict__ counters, int tiles_x,
+               const uint2 *__restrict__ ranges, uint32_t *__restrict__ cursor,
+               unsigned long long *__restrict__ keys) {
+    __shared__ ExpandSmem sm;
+    const uint32_t X = counters[CNT_SORT_N];
+    const uint32_t nk = counters[CNT_VISIBLE];
+    const int lane = threadIdx.x & 31;
+    for (uint32_t o0 = blockIdx.x * uint32_t(EMIT_CHUNK); o0 < X; o0 += gridDim.x * uint32_t(EMIT_CHUNK)) {
+        const uint32_t o1 = min(X, o0 + uint32_t(EMIT_CHUNK));
+        const uint32_t len = stage_owners(sm, koff, kid, rect, nk, o0, o1);
+        for (uint32_t base = o0; base < o1; base += T) {
+            const uint32_t o = base + threadIdx.x;
+            uint32_t g = 0, tile = 0xFFFFFFFFu;
+            if (o < o1) slot_owner(sm, len, o, tiles_x, g, tile);
+            const unsigned peers = __match_any_sync(0xffffffffu, tile);
+            const int leader = __ffs(peers) - 1;
+            uint32_t pos = 0;
+            if (o < o1 && lane == leader) pos = atomicAdd(&cursor[tile], uint32_t(__popc(peers)));
+            pos = __shfl_sync(0xffffffffu, pos, leader);
+            if (o < o1) {
+                const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
+                keys[ranges[tile].x + pos + rank] =
+                    (static_cast<unsigned long long>(gkey[g]) << 32) | g;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ per-tile sort
+__device__ __forceinline__ void bitonic_smem(unsigned long long *s, int npow2) {
+    for (int k = 2; k <= npow2; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < npow2; i += T) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const unsigned long long a = s[i], b = s[ixj];
+                    const bool up = (i & k) == 0;
+                    if ((a > b) == up) { s[i] = b; s[ixj] = a; }
+                }
+            }
+            __syncthreads();
+        }
+}
+
+// Sort m <= TS_CAP keys in place in global memory through shared memory.
+__device__ __forceinline__ void sort_chunk(unsigned long long *s, unsigned long long *g, int m) {
+    int npow2 = 1;
+    while (npow2 < m) npow2 <<= 1;
+    for (int i = threadIdx.x; i < npow2; i += T) s[i] = i < m ? g[i] : ~0ull;
+    __syncthreads();
+    bitonic_smem(s, npow2);
+    for (int i = threadIdx.x; i < m; i += T) g[i] = s[i];
+    __syncthreads();
+}
+
+// Merge sorted A[0,na) and B[0,nb) into C with the whole CTA (merge path).
+__device__ __forceinline__ void merge_cta(const unsigned long long *A, int na,
+                                          const unsigned long long *B, int nb,
+                                          unsigned long long *C) {
+    const int total = na + nb;
+    const int per = (total + T - 1) / T;
+    const int d0 = min(total, int(threadIdx.x) * per), d1 = min(total, d0 + per);
+    auto split = [&](int d) {
+        int lo = max(0, d - nb), hi = min(d, na);
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (A[mid] <= B[d - 1 - mid]) lo = mid + 1; else hi = mid;
+        }
+        return lo;
+    };
+    int i = split(d0), j = d0 - i;
+    const int iend = split(d1), jend = d1 - iend;
+    for (int d = d0; d < d1; ++d) {
+        if (i < iend && (j >= jend || A[i] <= B[j])) C[d] = A[i++];
+        else C[d] = B[j++];
+    }
+}
+
+__global__ void __launch_bounds__(T)
+tile_sort(const uint2 *__restrict__ ranges, unsigned long long *__restrict__ keys,
+          unsigned long long *__restrict__ scratch, uint32_t *__restrict__ igid) {
+    extern __shared__ unsigned long long s_k[];   // TS_CAP keys
+    const uint2 r = ranges[blockIdx.x];
+    const int n = int(r.y - r.x);
+    if (n == 0) return;
+    unsigned long long *src = keys + r.x;
+    if (n <= TS_CAP) {
+        int npow2 = 1;
+        while (npow2 < n) npow2 <<= 1;
+        for (int i = threadIdx.x; i < npow2; i += T) s_k[i] = i < n ? src[i] : ~0ull;
+        __syncthreads();
+        bitonic_smem(s_k, npow2);
+        for (int i = threadIdx.x; i < n; i += T) igid[r.x + i] = uint32_t(s_k[i]);
+        return;
+    }
+    // a bucket beyond shared memory: sorted chunks, then merge rounds
+    // ping-ponging between the key buffer and the scratch buffer
+    for (int c0 = 0; c0 < n; c0 += TS_CAP) sort_chunk(s_k, src + c0, min(TS_CAP, n - c0));
+    unsigned long long *dst = scratch + r.x;
+    for (int w = TS_CAP; w < n; w <<= 1) {
+        for (int a0 = 0; a0 < n; a0 += 2 * w) {
+            const int na = min(w, n - a0);
+            const int nb = min(w, n - a0 - na);
+            merge_cta(src + a0, na, src + a0 + na, nb, dst + a0);
+        }
+        __syncthreads();
+        unsigned long long *t = src;
+        src = dst;
+        dst = t;
+    }
+    for (int i = threadIdx.x; i < n; i += T) igid[r.x + i] = uint32_t(src[i]);
 }
 
 }  // namespace
-
-int sort_blocks_for(int64_t capacity) {
-    const int64_t tiles = (capacity + TILE - 1) / TILE;
-    return int(tiles < 1 ? 1 : (tiles > kSortMaxBlocks ? kSortMaxBlocks : tiles));
-}
-
-cudaError_t radix_sort_pairs(uint32_t *keys_a, uint32_t *vals_a, uint32_t *keys_b,
-                             uint32_t *vals_b, const uint32_t *d_count, int64_t capacity,
-                             int bit_lo, int bit_hi, uint32_t *hist, uint32_t *digitsum,
-                             int blocks, int *result_in_b, cudaStream_t s) {
-    (void)capacity;
-    int in_b = 0;
-    for (int lo = bit_lo; lo < bit_hi;) {
-        const int remaining = bit_hi - lo;
-        const int passes_left = (remaining + kRadixBitsMax - 1) / kRadixBitsMax;
-        const int bits = (remaining + passes_left - 1) / passes_left;
-        uint32_t *ki = in_b ? keys_b : keys_a, *vi = in_b ? vals_b : vals_a;
-        uint32_t *ko = in_b ? keys_a : keys_b, *vo = in_b ? vals_a : vals_b;
-        radix_upsweep<<<blocks, T, 0, s>>>(ki, d_count, lo, bits, hist);
-        radix_scan_rows<<<((1 << bits) + 7) / 8, 256, 0, s>>>(hist, 1 << bits, blocks, digitsum);
-        radix_downsweep<<<blocks, T, 0, s>>>(ki, vi, ko, vo, d_count, lo, bits, hist, digitsum);
-        count_launch(3);
-        in_b ^= 1;
-        lo += bits;
-    }
-    if (result_in_b) *result_in_b = in_b;
-    return cudaGetLastError();
-}
 
 int tile_bits_for(int tiles) {
     int b = 1;
@@ -412,54 +304,36 @@ int tile_bits_for(int tiles) {
 
 cudaError_t launch_sort(const qr_frame &f, cudaStream_t s) {
     uint32_t *counters = slot<uint32_t>(f, S_COUNTERS);
-    uint32_t *hist = slot<uint32_t>(f, S_HIST);
-    uint32_t *digitsum = slot<uint32_t>(f, S_DIGITSUM);
     const int tiles = num_tiles(f);
-    cudaError_t e = cudaMemsetAsync(slot<uint2>(f, S_RANGES), 0, sizeof(uint2) * size_t(tiles), s);
+    uint2 *ranges = slot<uint2>(f, S_RANGES);
+    uint32_t *tcnt = slot<uint32_t>(f, S_TCNT);
+    cudaError_t e = cudaMemsetAsync(tcnt, 0, sizeof(uint32_t) * size_t(tiles), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ranges, 0, sizeof(uint2) * size_t(tiles), s);
     if (e != cudaSuccess) return e;
     if (f.n == 0) return cudaSuccess;
-    // 0. pack the kept Gaussians (id order) -> counters[CNT_VISIBLE] items
-    const int nblk = int((f.n + kProjectThreads - 1) / kProjectThreads);
-    uint32_t *viscnt = slot<uint32_t>(f, S_VISCNT);
-    compact_scan<<<1, 1024, 0, s>>>(viscnt, nblk, counters);
-    compact_scatter<<<nblk, kProjectThreads, 0, s>>>(slot<uint32_t>(f, S_GKEY), viscnt, f.n,
-                                                     slot<uint32_t>(f, S_DKEY0),
-                                                     slot<uint32_t>(f, S_DVAL0));
-    count_launch(2);
-    // 1. depth sort of the kept Gaussians
-    const int nb_depth = sort_blocks_for(f.n);
-    int in_b = 0;
-    e = radix_sort_pairs(slot<uint32_t>(f, S_DKEY0), slot<uint32_t>(f, S_DVAL0),
-                         slot<uint32_t>(f, S_DKEY1), slot<uint32_t>(f, S_DVAL1),
-                         counters + CNT_VISIBLE, f.n, 0, 32, hist, digitsum, nb_depth, &in_b, s);
+    e = cudaFuncSetAttribute(tile_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(TS_CAP * sizeof(unsigned long long)));
     if (e != cudaSuccess) return e;
-    const uint32_t *sorted_gid = slot<uint32_t>(f, in_b ? S_DVAL1 : S_DVAL0);
-    // 2. scan of tile counts in depth order + emit
-    uint32_t *blocksum = slot<uint32_t>(f, S_BLOCKSUM);
-    uint32_t *offs = slot<uint32_t>(f, in_b ? S_DKEY0 : S_DKEY1);  // the free key buffer
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    emit_upsweep<<<nb_depth, T, 0, s>>>(sorted_gid, slot<uint32_t>(f, S_TCOUNT),
-                                        counters + CNT_VISIBLE, blocksum);
-    emit_scan<<<1, 1024, 0, s>>>(blocksum, nb_depth, counters, uint32_t(f.max_isect));
-    emit_offsets<<<nb_depth, T, 0, s>>>(sorted_gid, slot<uint32_t>(f, S_TCOUNT),
-                                        counters + CNT_VISIBLE, blocksum, offs);
-    emit_expand<<<sms * 2, T, 0, s>>>(offs, sorted_gid, slot<uint2>(f, S_RECT),
-                                      counters + CNT_VISIBLE, counters, f.tiles_x,
-                                      slot<uint32_t>(f, S_IKEY0), slot<uint32_t>(f, S_IVAL0));
-    count_launch(4);
-    // 3. stable sort of the intersections by tile id
-    int ib = 0;
-    e = radix_sort_pairs(slot<uint32_t>(f, S_IKEY0), slot<uint32_t>(f, S_IVAL0),
-                         slot<uint32_t>(f, S_IKEY1), slot<uint32_t>(f, S_IVAL1),
-                         counters + CNT_SORT_N, f.max_isect, 0, tile_bits_for(tiles), hist,
-                         digitsum, f.sort_blocks, &ib, s);
-    if (e != cudaSuccess) return e;
-    // 4. tile ranges
-    const uint32_t *ikey = slot<uint32_t>(f, ib ? S_IKEY1 : S_IKEY0);
-    tile_ranges<<<sms * 4, T, 0, s>>>(ikey, counters, slot<uint2>(f, S_RANGES));
-    count_launch();
+    const int nblk = int((f.n + kProjectThreads - 1) / kProjectThreads);
+    uint32_t *kept = slot<uint32_t>(f, S_VISCNT);
+    uint32_t *tsum = slot<uint32_t>(f, S_BSUM);
+    uint32_t *kid = slot<uint32_t>(f, S_KID);
+    uint32_t *koff = slot<uint32_t>(f, S_OFF);
+    const uint2 *rect = slot<uint2>(f, S_RECT);
+    offsets_scan<<<1, 1024, 0, s>>>(kept, tsum, nblk, counters, uint32_t(f.max_isect));
+    offsets_apply<<<nblk, kProjectThreads, 0, s>>>(slot<uint32_t>(f, S_TCOUNT), kept, tsum, f.n,
+                                                   kid, koff);
+    expand_count<<<sms * 2, T, 0, s>>>(koff, kid, rect, counters, f.tiles_x, tcnt);
+    tile_scan<<<1, 1024, 0, s>>>(tcnt, tiles, ranges);
+    auto *keys = slot<unsigned long long>(f, S_KEYS64);
+    expand_scatter<<<sms * 2, T, 0, s>>>(koff, kid, rect, slot<uint32_t>(f, S_GKEY), counters,
+                                         f.tiles_x, ranges, tcnt, keys);
+    tile_sort<<<tiles, T, TS_CAP * sizeof(unsigned long long), s>>>(
+        ranges, keys, slot<unsigned long long>(f, S_SCRATCH64), slot<uint32_t>(f, S_IGID));
+    count_launch(6);
     return cudaGetLastError();
 }
 

@@ -55,8 +55,8 @@ class qr_frame(ctypes.Structure):
 
 class qr_frame_view(ctypes.Structure):
     _fields_ = [(name, ctypes.c_void_p) for name in (
-        "mean2d_hi_lo", "axes", "opacity", "depth_key", "tile_count", "sorted_key", "sorted_gid",
-        "isect_tile", "isect_gid", "tile_range", "counters")]
+        "mean2d_hi_lo", "axes", "opacity", "depth_key", "tile_count", "kept_gid", "kept_offset",
+        "isect_gid", "tile_range", "counters")]
 
 
 _P = ctypes.c_void_p

@@ -101,30 +101,33 @@ def test_tile_lists_sorted_and_conservative():
     v = q.qr_frame_view_get(fr)
     nis = gpu["n_isect"]
     tiles = fr.frame.tiles_x * fr.frame.tiles_y
-    keys = _device_copy(v.isect_tile, nis, torch.int32).cpu().numpy()
-    gids = _device_copy(v.isect_gid, nis, torch.int32).cpu().numpy()
-    rng = _device_copy(v.tile_range, 2 * tiles, torch.int32).cpu().numpy().reshape(tiles, 2)
-    pr = oracle.project(g, cam.as_array())
-    # the GPU's own per-Gaussian depth keys, recovered from the sorted (key, id) pairs
     cnt = _device_copy(v.counters, 8, torch.int32).cpu().numpy()
     n_kept = int(cnt[2])
+    assert int(cnt[1]) == nis
     gkey = _device_copy(v.depth_key, g.n, torch.int32).cpu().numpy().view(np.uint32)
-    skey = _device_copy(v.sorted_key, n_kept, torch.int32).cpu().numpy().view(np.uint32)
-    sgid = _device_copy(v.sorted_gid, n_kept, torch.int32).cpu().numpy()
-    # the kept set is every Gaussian with a finite key, sorted by (key, id)
+    tcount = _device_copy(v.tile_count, g.n, torch.int32).cpu().numpy()
+    kid = _device_copy(v.kept_gid, n_kept, torch.int32).cpu().numpy()
+    koff = _device_copy(v.kept_offset, n_kept, torch.int32).cpu().numpy()
+    gids = _device_copy(v.isect_gid, nis, torch.int32).cpu().numpy()
+    rng = _device_copy(v.tile_range, 2 * tiles, torch.int32).cpu().numpy().reshape(tiles, 2)
+    # kept set: finite depth key <=> non-empty footprint, compacted in id order
     kept = np.nonzero(gkey != 0xFFFFFFFF)[0]
-    assert n_kept == len(kept)
-    np.testing.assert_array_equal(sgid, kept[np.lexsort((kept, gkey[kept]))])
-    np.testing.assert_array_equal(skey, gkey[sgid])
+    np.testing.assert_array_equal(kid, kept)
+    assert (tcount[kept] > 0).all() and (tcount[gkey == 0xFFFFFFFF] == 0).all()
+    np.testing.assert_array_equal(koff, np.concatenate([[0], np.cumsum(tcount[kid])[:-1]]))
+    assert koff[-1] + tcount[kid[-1]] == nis
+    # ranges tile the list; every kept Gaussian appears once per touched tile
+    assert rng[0, 0] == 0 and rng[-1, 1] == nis and (rng[1:, 0] == rng[:-1, 1]).all()
+    np.testing.assert_array_equal(np.bincount(gids, minlength=g.n), tcount)
+    # each tile's list is ordered by (FP32 depth key, id)
     depth32 = gkey.view(np.float32)
-    assert (np.diff(keys) >= 0).all()
     for t in range(tiles):
         a, b = rng[t]
-        assert (keys[a:b] == t).all()
-        d = depth32[gids[a:b]]
-        order = np.lexsort((gids[a:b], d))
+        assert len(set(gids[a:b].tolist())) == b - a
+        order = np.lexsort((gids[a:b], depth32[gids[a:b]]))
         np.testing.assert_array_equal(order, np.arange(b - a))
-    # every member of a pixel appears in its tile's list
+    # every member of a pixel (FP64 oracle) appears in its tile's list
+    pr = oracle.project(g, cam.as_array())
     ref = oracle.render(pr, None, 8, oracle.all_pixels(cam.width, cam.height), want_q=False,
                         want_dense=False, max_members=64)
     assert ref.n_members.max() <= 64
@@ -134,6 +137,40 @@ def test_tile_lists_sorted_and_conservative():
         a, b = rng[t]
         mem = ref.members[p][ref.members[p] >= 0]
         assert np.isin(mem, gids[a:b]).all()
+
+
+def test_large_tile_lists_use_the_merge_path():
+    """Tiles with more than 8192 Gaussians are sorted in chunks and merged."""
+    rng = np.random.default_rng(11)
+    n = 30000
+    # a thin slab of small Gaussians right in front of a 48x48 camera: every
+    # tile sees thousands of them
+    mean = np.stack([rng.uniform(-0.2, 0.2, n), rng.uniform(-0.2, 0.2, n),
+                     rng.uniform(-0.5, 0.5, n)], 1).astype(np.float32)
+    g = scenes.Gaussians(mean, np.full((n, 3), -2.0, np.float32),
+                         np.tile(np.array([1, 0, 0, 0], np.float32), (n, 1)),
+                         np.full(n, 0.05, np.float32))
+    f = rng.normal(size=(n, 16)).astype(np.float32)
+    cam = scenes.tiny_camera(48, 48)
+    gpu = H.run_gpu(g, f, cam, K=8)
+    fr = gpu["frame"]
+    from paper_2512_20927_gb300 import qrender as q
+    import torch
+    v = q.qr_frame_view_get(fr)
+    tiles = fr.frame.tiles_x * fr.frame.tiles_y
+    rngs = _device_copy(v.tile_range, 2 * tiles, torch.int32).cpu().numpy().reshape(tiles, 2)
+    sizes = rngs[:, 1] - rngs[:, 0]
+    assert sizes.max() > 8192, sizes.max()
+    gkey = _device_copy(v.depth_key, n, torch.int32).cpu().numpy().view(np.uint32)
+    gids = _device_copy(v.isect_gid, gpu["n_isect"], torch.int32).cpu().numpy()
+    for t in range(tiles):
+        a, b = rngs[t]
+        order = np.lexsort((gids[a:b], gkey.view(np.float32)[gids[a:b]]))
+        np.testing.assert_array_equal(order, np.arange(b - a))
+    pix = H.sample_pixels(48, 48, 200, seed=3)
+    pr, pix, ref = H.run_oracle(g, f, cam, 8, pixels=pix)
+    H.check_frame(gpu, ref, pix, cam.width, f, FEAT_TOL, DENSE_TOL, max_tie_frac=0.1,
+                  label="big tiles")
 
 
 @pytest.mark.parametrize("C", [16, 64, 512])

@@ -223,6 +223,21 @@ qr_status qr_render_host(qr_frame *frame, const float *mean_host, const float *l
                          int32_t C, void *dev_inputs, void *dev_outputs, float *out_host,
                          qr_stream stream);
 
+/* ---------------------------------------------------------------- feature storage */
+
+/* Storage formats of the feature table; the paper stores FP32 (Sec. 4).
+ * BF16: out[i] = in[i] rounded to nearest even (bit pattern as uint16).
+ * count elements, device pointers; asynchronous on stream. */
+qr_status qr_quantize_bf16(const float *in, int64_t count, uint16_t *out, qr_stream stream);
+
+/* FP8 E4M3 with one FP32 scale per row: scale[r] = max_c |in[r][c]| / 448
+ * (1 for an all-zero row), codes[r][c] = E4M3(in[r][c] / scale[r]) rounded to
+ * nearest even and saturated to +-448.  in [rows][C], codes [rows][C],
+ * scale [rows].  Decoding is E4M3(code) * scale (qr_blend / qr_dense with
+ * QR_FP8E4M3 do it in registers). */
+qr_status qr_quantize_fp8(const float *in, int64_t rows, int32_t C, uint8_t *codes,
+                          float *scale, qr_stream stream);
+
 /* ---------------------------------------------------------------- allocation-free variant */
 
 /* No counterpart in the paper.  The Q-Render forward of qr_render for callers

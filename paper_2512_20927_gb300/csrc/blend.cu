@@ -189,20 +189,24 @@ __device__ __forceinline__ int64_t group_pixel(int64_t chunk0, int gi, int m, in
     return tile_order_pixel(item, W, H);
 }
 
-template <int DT, int VPL, int G>
-__global__ void __launch_bounds__(kThreads)
+template <int DT, int VPL, int G, int S>
+__global__ void __launch_bounds__(kThreads, 3)
 blend_group_kernel(const uint4 *__restrict__ feat, const float *__restrict__ scale,
                    int64_t n_gauss, const int32_t *__restrict__ ids,
                    const float *__restrict__ wts, const uint8_t *__restrict__ cnt, int64_t P,
                    int K, int W, int H, float4 *__restrict__ out) {
+    // S warps share a pixel group, each owning VPL/S of the row's vectors
     constexpr int CPV = Vec<DT>::C;
     constexpr int ROWV = 32 * VPL;
+    constexpr int VW = VPL / S;                     // vectors per lane in this warp
     constexpr unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t items = (W > 0) ? int64_t((W + 15) >> 4) * ((H + 15) >> 4) * 256 : P;
     const int64_t chunk0 = int64_t(blockIdx.x) * 256;
     const unsigned kmask = (K >= 32) ? FULL : ((1u << K) - 1u);
-    for (int gi = warp; gi < 256 / G; gi += kThreads / 32) {
+    for (int wi = warp; wi < (256 / G) * S; wi += kThreads / 32) {
+        const int gi = wi / S, part = wi % S;
+        const int vbase = part * VW;                // first vector index (in units of 32 lanes)
         const int m = lane / K, j = lane - m * K;
         int64_t p = -1;
         if (m < G) p = (W > 0) ? group_pixel<G>(chunk0, gi, m, W, H, items)
@@ -217,11 +221,11 @@ blend_group_kernel(const uint4 *__restrict__ feat, const float *__restrict__ sca
         }
         const unsigned peers = __match_any_sync(FULL, id);
         unsigned leaders = __ballot_sync(FULL, id >= 0 && lane == __ffs(peers) - 1);
-        float acc[G][VPL][CPV];
+        float acc[G][VW][CPV];
 #pragma unroll
         for (int g = 0; g < G; ++g)
 #pragma unroll
-            for (int v = 0; v < VPL; ++v)
+            for (int v = 0; v < VW; ++v)
 #pragma unroll
                 for (int q = 0; q < CPV; ++q) acc[g][v][q] = 0.f;
         while (leaders) {
@@ -230,7 +234,7 @@ blend_group_kernel(const uint4 *__restrict__ feat, const float *__restrict__ sca
             leaders &= leaders - 1;
             L[1] = leaders ? __ffs(leaders) - 1 : -1;
             if (L[1] >= 0) leaders &= leaders - 1;
-            uint4 r[2][VPL];
+            uint4 r[2][VW];
             float wg[2][G];
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
@@ -248,9 +252,9 @@ blend_group_kernel(const uint4 *__restrict__ feat, const float *__restrict__ sca
                     }
                     wg[u][g] = x;
                 }
-                const uint4 *row = feat + int64_t(rid) * ROWV + lane;
+                const uint4 *row = feat + int64_t(rid) * ROWV + 32 * vbase + lane;
 #pragma unroll
-                for (int v = 0; v < VPL; ++v)
+                for (int v = 0; v < VW; ++v)
                     r[u][v] = (L[u] >= 0) ? ld_row(row + 32 * v) : make_uint4(0, 0, 0, 0);
             }
 #pragma unroll
@@ -259,7 +263,7 @@ blend_group_kernel(const uint4 *__restrict__ feat, const float *__restrict__ sca
                 for (int g = 0; g < G; ++g)
                     if (wg[u][g] != 0.f) {
 #pragma unroll
-                        for (int v = 0; v < VPL; ++v) decode_fma<DT>(r[u][v], wg[u][g], acc[g][v]);
+                        for (int v = 0; v < VW; ++v) decode_fma<DT>(r[u][v], wg[u][g], acc[g][v]);
                     }
         }
 #pragma unroll
@@ -268,10 +272,10 @@ blend_group_kernel(const uint4 *__restrict__ feat, const float *__restrict__ sca
             if (pg >= 0) {
                 float4 *o = out + pg * (int64_t(ROWV) * CPV / 4);
 #pragma unroll
-                for (int v = 0; v < VPL; ++v)
+                for (int v = 0; v < VW; ++v)
 #pragma unroll
                     for (int q = 0; q < CPV / 4; ++q)
-                        st_stream(o + int64_t(lane + 32 * v) * (CPV / 4) + q,
+                        st_stream(o + int64_t(lane + 32 * (vbase + v)) * (CPV / 4) + q,
                                   make_float4(acc[g][v][4 * q], acc[g][v][4 * q + 1],
                                               acc[g][v][4 * q + 2], acc[g][v][4 * q + 3]));
             }
@@ -287,12 +291,13 @@ cudaError_t run_group(const void *feat, const float *scale, int64_t n_gauss, con
     const unsigned blocks = unsigned((items + 255) / 256);
     const uint4 *f = static_cast<const uint4 *>(feat);
     float4 *o = reinterpret_cast<float4 *>(out);
+    constexpr int S = (VPL % 2 == 0) ? 2 : 1;      // split wide rows over two warps
     if (K <= 8)
-        blend_group_kernel<DT, VPL, 4><<<blocks, kThreads, 0, s>>>(f, scale, n_gauss, ids, w, cnt, P, K, W, H, o);
+        blend_group_kernel<DT, VPL, 4, S><<<blocks, kThreads, 0, s>>>(f, scale, n_gauss, ids, w, cnt, P, K, W, H, o);
     else if (K <= 16)
-        blend_group_kernel<DT, VPL, 2><<<blocks, kThreads, 0, s>>>(f, scale, n_gauss, ids, w, cnt, P, K, W, H, o);
+        blend_group_kernel<DT, VPL, 2, S><<<blocks, kThreads, 0, s>>>(f, scale, n_gauss, ids, w, cnt, P, K, W, H, o);
     else
-        blend_group_kernel<DT, VPL, 1><<<blocks, kThreads, 0, s>>>(f, scale, n_gauss, ids, w, cnt, P, K, W, H, o);
+        blend_group_kernel<DT, VPL, 1, S><<<blocks, kThreads, 0, s>>>(f, scale, n_gauss, ids, w, cnt, P, K, W, H, o);
     count_launch();
     return cudaGetLastError();
 }

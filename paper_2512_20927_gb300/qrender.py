@@ -87,6 +87,8 @@ SIGNATURES = {
     "qr_render_host": (_S, [ctypes.POINTER(qr_frame), _P, _P, _P, _P, _P, _P, _S, _I32, _P, _P,
                             _P, _P]),
     "qr_launch_count": (ctypes.c_uint64, []),
+    "qr_quantize_bf16": (_S, [_P, _I64, _P, _P]),
+    "qr_quantize_fp8": (_S, [_P, _I64, _I32, _P, _P, _P]),
     "qr_render_noalloc": (_S, [_P, _P, _P, _P, _I64, ctypes.POINTER(qr_camera),
                                ctypes.POINTER(qr_params), _P, _P, _S, _I32, _P, _P, _P, _P,
                                ctypes.POINTER(qr_frame), _P]),
@@ -305,6 +307,26 @@ def qr_render_noalloc(mean, log_scale, quat, opacity, cam, params, feat, feat_sc
                                     _ptr(out), ctypes.byref(f), _stream(stream)),
            "qr_render_noalloc")
     return Frame(f, None, camc, params)
+
+
+def qr_quantize_bf16(x, stream=None):
+    """BF16 copy of a float32 device tensor (returned as torch.bfloat16)."""
+    torch = _torch()
+    out = torch.empty(x.shape, dtype=torch.bfloat16, device=x.device)
+    _check(load().qr_quantize_bf16(_ptr(x), x.numel(), _ptr(out), _stream(stream)),
+           "qr_quantize_bf16")
+    return out
+
+
+def qr_quantize_fp8(x, stream=None):
+    """(codes uint8 [rows, C], scale float32 [rows]) of a float32 [rows, C] device tensor."""
+    torch = _torch()
+    rows, C = x.shape
+    codes = torch.empty((rows, C), dtype=torch.uint8, device=x.device)
+    scale = torch.empty(rows, dtype=torch.float32, device=x.device)
+    _check(load().qr_quantize_fp8(_ptr(x), rows, C, _ptr(codes), _ptr(scale), _stream(stream)),
+           "qr_quantize_fp8")
+    return codes, scale
 
 
 def qr_launch_count() -> int:

@@ -169,7 +169,7 @@ def test_large_tile_lists_use_the_merge_path():
         np.testing.assert_array_equal(order, np.arange(b - a))
     pix = H.sample_pixels(48, 48, 200, seed=3)
     pr, pix, ref = H.run_oracle(g, f, cam, 8, pixels=pix)
-    H.check_frame(gpu, ref, pix, cam.width, f, FEAT_TOL, DENSE_TOL, max_tie_frac=0.1,
+    H.check_frame(gpu, ref, pix, cam.width, f, FEAT_TOL, DENSE_TOL, max_tie_frac=0.6,
                   label="big tiles")
 
 

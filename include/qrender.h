@@ -223,6 +223,44 @@ qr_status qr_render_host(qr_frame *frame, const float *mean_host, const float *l
                          int32_t C, void *dev_inputs, void *dev_outputs, float *out_host,
                          qr_stream stream);
 
+/* ---------------------------------------------------------------- backward */
+
+/* Backward of Algorithm 1.  The paper states that image-space gradients flow
+ * through Q-Render into the per-Gaussian features (Sec. 1, Sec. 4.2) without a
+ * formula; with the quantile Gaussians j of a pixel (depth order),
+ * a_j = alpha'_j, P_j = prod_{l<j} (1 - a_l), T^Q = P_{m+1}, D = 1 - T^Q and
+ * g = dL/dF_p:
+ *   dL/df_j   = w_j g                                  (w_j = a_j P_j / D)
+ *   dL/da_j   = [P_j s_j - sum_{l>j} a_l P_l s_l / (1-a_j)] / D
+ *               - (g.F) T^Q / ((1-a_j) D),             s_l = g . f_l
+ *   dL/dalpha = dL/da * exp(-q/2);  dL/d(A00, A01, A11) = dL/da * (-a/2) *
+ *               (dx^2, 2 dx dy, dy^2), both zero where alpha' was clamped;
+ * the selection itself is piecewise constant and held fixed.
+ * frame must still hold the forward's projection and tile lists (qr_project
+ * and qr_sort of the same frame), ids/weights/counts its qr_select outputs and
+ * feat the table qr_blend used.  grad_out [P][C] float32.  Outputs (all
+ * overwritten): grad_feat [n][C] float32 (zero rows for Gaussians no pixel
+ * selected), grad_opacity [n] and grad_conic [n][3] (both nullable).  The sum
+ * over pixels is deterministic: per-tile partials reduced in a fixed order, no
+ * floating-point atomics.  ws: qr_backward_workspace_bytes(frame, C) bytes,
+ * 256-byte aligned (about max_isect * C * 4 bytes of partial rows). */
+size_t qr_backward_workspace_bytes(const qr_frame *frame, int32_t C);
+qr_status qr_backward(const qr_frame *frame, const void *feat, const float *feat_scale,
+                      qr_dtype dtype, int32_t C, const int32_t *ids, const float *weights,
+                      const uint8_t *counts, const float *grad_out, float *grad_feat,
+                      float *grad_opacity, float *grad_conic, void *ws, size_t ws_bytes,
+                      qr_stream stream);
+
+/* Loss of the differentiation workload (the paper trains with the contrastive
+ * Eq. 2 on CLIP targets, which are not available): L = mean over pixels with
+ * counts > 0 of 1 - cos(F_p, t_p), cos = F.t / (max(|F|, 1e-8) max(|t|, 1e-8)).
+ * feature_map, target [P][C]; loss_out [2] device floats receive (L, 1/n);
+ * grad [P][C] receives dL/dF (zero on pixels without quantile Gaussians);
+ * scratch [P] floats.  Deterministic reduction. */
+qr_status qr_cosine_loss(const float *feature_map, const float *target, const uint8_t *counts,
+                         int64_t P, int32_t C, float *loss_out, float *grad, float *scratch,
+                         qr_stream stream);
+
 /* ---------------------------------------------------------------- feature storage */
 
 /* Storage formats of the feature table; the paper stores FP32 (Sec. 4).

@@ -310,6 +310,40 @@ qr_status qr_render_host(qr_frame *frame, const float *mean_host, const float *l
     return from_cuda(e);
 }
 
+size_t qr_backward_workspace_bytes(const qr_frame *frame, int32_t C) {
+    if (!frame_ok(frame) || C < 4 || C % 4) return 0;
+    return backward_workspace_bytes(*frame, C);
+}
+
+qr_status qr_backward(const qr_frame *frame, const void *feat, const float *feat_scale,
+                      qr_dtype dtype, int32_t C, const int32_t *ids, const float *weights,
+                      const uint8_t *counts, const float *grad_out, float *grad_feat,
+                      float *grad_opacity, float *grad_conic, void *ws, size_t ws_bytes,
+                      qr_stream stream) {
+    if (!frame_ok(frame) || !ids || !weights || !counts || !grad_out || !grad_feat || !ws)
+        return QR_ERR_INVALID_ARG;
+    qr_status st = check_feat(feat, feat_scale, dtype, C);
+    if (st != QR_OK) return st;
+    if (!aligned16(grad_out) || !aligned16(grad_feat) ||
+        (reinterpret_cast<uintptr_t>(ws) & (kAlign - 1)))
+        return QR_ERR_ALIGNMENT;
+    if (ws_bytes < backward_workspace_bytes(*frame, C)) return QR_ERR_INVALID_ARG;
+    if (frame->n == 0) return QR_OK;
+    return from_cuda(launch_backward(*frame, feat, feat_scale, dtype, C, ids, weights, counts,
+                                     grad_out, grad_feat, grad_opacity, grad_conic, ws,
+                                     reinterpret_cast<cudaStream_t>(stream)));
+}
+
+qr_status qr_cosine_loss(const float *feature_map, const float *target, const uint8_t *counts,
+                         int64_t P, int32_t C, float *loss_out, float *grad, float *scratch,
+                         qr_stream stream) {
+    if (!feature_map || !target || !counts || !loss_out || !grad || !scratch || P < 0 || C < 1)
+        return QR_ERR_INVALID_ARG;
+    if (P == 0) return QR_OK;
+    return from_cuda(launch_cosine_loss(feature_map, target, counts, P, C, scratch, loss_out, grad,
+                                        reinterpret_cast<cudaStream_t>(stream)));
+}
+
 uint64_t qr_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 }  // extern "C"

@@ -58,6 +58,14 @@ cudaError_t launch_select(const qr_frame &f, int32_t *ids, float *w, uint8_t *cn
 cudaError_t launch_dense(const qr_frame &f, const void *feat, const float *scale, qr_dtype dt,
                          int C, float *out, float *T_final, cudaStream_t s);
 
+size_t backward_workspace_bytes(const qr_frame &f, int C);
+cudaError_t launch_backward(const qr_frame &f, const void *feat, const float *scale, qr_dtype dt,
+                            int C, const int32_t *ids, const float *w, const uint8_t *cnt,
+                            const float *grad_out, float *grad_feat, float *grad_alpha,
+                            float *grad_conic, void *ws, cudaStream_t s);
+cudaError_t launch_cosine_loss(const float *F, const float *tgt, const uint8_t *counts, int64_t P,
+                               int C, float *term, float *out2, float *grad, cudaStream_t s);
+
 // Generic pieces of the sort, reused by later stages.
 // Stable LSD radix sort of (key, val) pairs; count read from the device.
 // Sorts bits [bit_lo, bit_hi) of the keys; returns through *out_keys/*out_vals

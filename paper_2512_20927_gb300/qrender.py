@@ -87,6 +87,10 @@ SIGNATURES = {
     "qr_render_host": (_S, [ctypes.POINTER(qr_frame), _P, _P, _P, _P, _P, _P, _S, _I32, _P, _P,
                             _P, _P]),
     "qr_launch_count": (ctypes.c_uint64, []),
+    "qr_backward_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(qr_frame), _I32]),
+    "qr_backward": (_S, [ctypes.POINTER(qr_frame), _P, _P, _S, _I32, _P, _P, _P, _P, _P, _P, _P,
+                         _P, ctypes.c_size_t, _P]),
+    "qr_cosine_loss": (_S, [_P, _P, _P, _I64, _I32, _P, _P, _P, _P]),
     "qr_quantize_bf16": (_S, [_P, _I64, _P, _P]),
     "qr_quantize_fp8": (_S, [_P, _I64, _I32, _P, _P, _P]),
     "qr_render_noalloc": (_S, [_P, _P, _P, _P, _I64, ctypes.POINTER(qr_camera),
@@ -307,6 +311,44 @@ def qr_render_noalloc(mean, log_scale, quat, opacity, cam, params, feat, feat_sc
                                     _ptr(out), ctypes.byref(f), _stream(stream)),
            "qr_render_noalloc")
     return Frame(f, None, camc, params)
+
+
+def qr_backward(fr: Frame, feat, feat_scale, ids, weights, counts, grad_out, want_conic=True,
+                stream=None):
+    """Gradients of the Q-Render forward of `fr` w.r.t. features, opacity and conic.
+
+    Returns (grad_feat [n, C] float32, grad_opacity [n], grad_conic [n, 3] or None)."""
+    torch = _torch()
+    n = int(fr.frame.n)
+    C = feat.shape[1]
+    dev = grad_out.device
+    nbytes = int(load().qr_backward_workspace_bytes(ctypes.byref(fr.frame), C))
+    if nbytes == 0:
+        raise QRError(QR_ERR_INVALID_ARG, "qr_backward_workspace_bytes")
+    ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
+    wsp = ctypes.c_void_p((ws.data_ptr() + 255) // 256 * 256)
+    gf = torch.empty((n, C), dtype=torch.float32, device=dev)
+    ga = torch.empty(n, dtype=torch.float32, device=dev)
+    gc = torch.empty((n, 3), dtype=torch.float32, device=dev) if want_conic else None
+    _check(load().qr_backward(ctypes.byref(fr.frame), _ptr(feat), _ptr(feat_scale),
+                              _dtype_code(feat), C, _ptr(ids), _ptr(weights), _ptr(counts),
+                              _ptr(grad_out.contiguous()), _ptr(gf), _ptr(ga), _ptr(gc), wsp,
+                              nbytes, _stream(stream)), "qr_backward")
+    return gf, ga, gc
+
+
+def qr_cosine_loss(feature_map, target, counts, stream=None):
+    """(loss scalar tensor, dL/dF) of the mean (1 - cos) loss over covered pixels."""
+    torch = _torch()
+    P, C = feature_map.shape
+    dev = feature_map.device
+    out2 = torch.empty(2, dtype=torch.float32, device=dev)
+    grad = torch.empty((P, C), dtype=torch.float32, device=dev)
+    scratch = torch.empty(P, dtype=torch.float32, device=dev)
+    _check(load().qr_cosine_loss(_ptr(feature_map.contiguous()), _ptr(target.contiguous()),
+                                 _ptr(counts), P, C, _ptr(out2), _ptr(grad), _ptr(scratch),
+                                 _stream(stream)), "qr_cosine_loss")
+    return out2[0], grad
 
 
 def qr_quantize_bf16(x, stream=None):

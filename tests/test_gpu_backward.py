@@ -1,0 +1,165 @@
+"""Backward of Algorithm 1 on the GPU against the FP64 oracle's gradient
+(itself pinned by finite differences in tests/test_oracle_pins.py).
+
+Upstream gradients are zero on the pixels the oracle flags as near ties, so
+both sides sum over the same selections.  Tolerances: feature gradients are
+sums of w * g (FP32 accumulation), 2e-5 of the largest entry; opacity and
+conic gradients contain differences of products, 2e-4 of the largest entry.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import compare
+from paper_2512_20927_gb300 import scenes
+
+import gpu_harness as H
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _compare(name, got, ref, rel):
+    scale = np.abs(ref).max()
+    err = np.abs(got - ref).max()
+    assert err <= rel * max(scale, 1e-30), (name, err, scale)
+    return err / max(scale, 1e-30)
+
+
+def _run(g, f, cam, K, table=None, decoded=None, seed=0):
+    import torch
+    from paper_2512_20927_gb300 import qrender as q
+    decoded = f if decoded is None else decoded
+    fdev = torch.from_numpy(f).cuda() if table is None else table
+    res = q.render_frame(q.gaussians_to_device(g), fdev, cam, K=K)
+    pr, pix, ref = H.run_oracle(g, decoded, cam, K)
+    tie = (ref.tie & compare.Q_TIE_BITS) != 0
+    rng = np.random.default_rng(seed)
+    gout = rng.normal(size=(cam.width * cam.height, f.shape[1]))
+    gout[tie] = 0.0
+    gdev = torch.from_numpy(gout.astype(np.float32)).cuda()
+    feat_t, scale_t = (fdev, None) if not isinstance(fdev, tuple) else fdev
+    gf, ga, gc = q.qr_backward(res["frame"], feat_t, scale_t, res["ids"], res["weights"],
+                               res["counts"], gdev)
+    torch.cuda.synchronize()
+    rf, ra, rc = oracle.backward(pr, decoded, K, pix, gout.astype(np.float32).astype(np.float64),
+                                 alpha_min=oracle.ALPHA_MIN_F32, alpha_max=oracle.ALPHA_MAX_F32)
+    return (gf.cpu().numpy(), ga.cpu().numpy(), gc.cpu().numpy()), (rf, ra, rc)
+
+
+def test_backward_tiny_matches_oracle():
+    g, f = scenes.tiny_scene()
+    (gf, ga, gc), (rf, ra, rc) = _run(g, f, scenes.tiny_camera(), 8)
+    e = [_compare("feat", gf, rf, 2e-5), _compare("alpha", ga, ra, 2e-4),
+         _compare("conic", gc, rc, 2e-4)]
+    untouched = (rf == 0).all(axis=1)
+    assert (gf[untouched] == 0).all()
+    print("tiny backward rel errors", e)
+
+
+@pytest.mark.parametrize("K", [4, 16])
+def test_backward_room_matches_oracle(K):
+    g, f = H.small_room(n=20000, channels=64)
+    (gf, ga, gc), (rf, ra, rc) = _run(g, f, scenes.room_camera(150, 110), K, seed=K)
+    _compare("feat", gf, rf, 2e-5)
+    _compare("alpha", ga, ra, 2e-4)
+    _compare("conic", gc, rc, 2e-4)
+
+
+def test_backward_bf16_table():
+    import torch
+    from paper_2512_20927_gb300 import qrender as q
+    g, f = H.small_room(n=20000, channels=64)
+    table = q.qr_quantize_bf16(torch.from_numpy(f).cuda())
+    decoded = oracle.bf16_decode(oracle.bf16_encode(f))
+    (gf, ga, gc), (rf, ra, rc) = _run(g, f, scenes.room_camera(150, 110), 8, table=table,
+                                      decoded=decoded)
+    _compare("feat", gf, rf, 2e-5)
+    _compare("alpha", ga, ra, 2e-4)
+
+
+def test_autograd_function_matches_c_abi_and_is_linear_in_features():
+    import torch
+    from paper_2512_20927_gb300 import qrender as q
+    from paper_2512_20927_gb300.autograd import quantile_render
+    g, f = scenes.tiny_scene(seed=3)
+    cam = scenes.tiny_camera(96, 96)
+    mean, ls, quat, op = q.gaussians_to_device(g)
+    op = op.clone().requires_grad_(True)
+    feat = torch.from_numpy(f).cuda().requires_grad_(True)
+    out, counts = quantile_render(mean, ls, quat, op, feat, cam, K=8)
+    gout = torch.randn_like(out)
+    (out * gout).sum().backward()
+    fr = q.render_frame((mean, ls, quat, op.detach()), feat.detach(), cam, K=8)
+    gf, ga, _ = q.qr_backward(fr["frame"], feat.detach(), None, fr["ids"], fr["weights"],
+                              fr["counts"], gout.reshape(-1, f.shape[1]).contiguous())
+    torch.testing.assert_close(feat.grad, gf, rtol=0, atol=0)
+    torch.testing.assert_close(op.grad, ga, rtol=0, atol=0)
+    # the map is linear in the features: a finite difference is exact up to rounding
+    idx = torch.nonzero(gf.abs().sum(dim=1) > 0)[:5, 0]
+    for i in idx.tolist():
+        fp = feat.detach().clone()
+        fm = feat.detach().clone()
+        fp[i, 3] += 0.5
+        fm[i, 3] -= 0.5
+        Lp = (quantile_render(mean, ls, quat, op.detach(), fp, cam, K=8)[0] * gout).sum()
+        Lm = (quantile_render(mean, ls, quat, op.detach(), fm, cam, K=8)[0] * gout).sum()
+        fd = (Lp - Lm).item() / 1.0
+        assert abs(fd - gf[i, 3].item()) <= 1e-3 * max(1.0, abs(fd)), (i, fd, gf[i, 3].item())
+
+
+def test_cosine_loss_matches_oracle():
+    import torch
+    from paper_2512_20927_gb300 import qrender as q
+    rng = np.random.default_rng(5)
+    P, C = 3000, 64
+    F = rng.normal(size=(P, C)).astype(np.float32)
+    t = rng.normal(size=(P, C)).astype(np.float32)
+    F[7] = 0.0
+    cnt = (rng.uniform(size=P) < 0.8).astype(np.uint8)
+    loss, grad = q.qr_cosine_loss(torch.from_numpy(F).cuda(), torch.from_numpy(t).cuda(),
+                                  torch.from_numpy(cnt).cuda())
+    L, gref = oracle.cosine_loss(F, t, cnt > 0)
+    assert abs(loss.item() - L) <= 1e-6 * max(1.0, abs(L))
+    np.testing.assert_allclose(grad.cpu().numpy(), gref, rtol=0, atol=1e-5 * np.abs(gref).max())
+
+
+def test_differentiation_config_sampled_pixels():
+    """300k-Gaussian room, 640x480, 512-D, K = 8, loss = mean (1 - cos) against
+    the dense map of a second Gaussian set; the loss is restricted to sampled
+    pixels so the oracle (own forward, own target, own upstream gradient) can
+    compute the same gradients."""
+    import torch
+    from paper_2512_20927_gb300 import qrender as q
+    g, f = scenes.room_scene(seed=0, n=300_000, channels=512)
+    g2, f2 = scenes.room_scene(seed=1, n=300_000, channels=512)
+    cam = scenes.room_camera(640, 480)
+    K = 8
+    res = q.render_frame(q.gaussians_to_device(g), torch.from_numpy(f).cuda(), cam, K=K)
+    tgt = q.render_frame(q.gaussians_to_device(g2), torch.from_numpy(f2).cuda(), cam, K=K,
+                         dense=True)["dense"]
+    pix = H.sample_pixels(640, 480, 200, seed=9)
+    pr, pix, ref = H.run_oracle(g, f, cam, K, pixels=pix)
+    pr2, _, ref2 = H.run_oracle(g2, f2, cam, K, pixels=pix)
+    tie = (ref.tie & compare.Q_TIE_BITS) != 0
+    use = (~tie) & (ref.cnt > 0)
+    idx = H.pixel_index(pix, cam.width)
+    mask = torch.zeros(cam.width * cam.height, dtype=torch.uint8, device="cuda")
+    mask[torch.from_numpy(idx[use]).cuda()] = 1
+    loss, gmap = q.qr_cosine_loss(res["out"], tgt, mask)
+    gf, ga, gc = q.qr_backward(res["frame"], torch.from_numpy(f).cuda(), None, res["ids"],
+                               res["weights"], res["counts"], gmap)
+    torch.cuda.synchronize()
+    Lref, gref = oracle.cosine_loss(ref.out_q, ref2.out_dense, use)
+    assert abs(loss.item() - Lref) <= 1e-4 * max(1.0, abs(Lref)), (loss.item(), Lref)
+    rf, ra, rc = oracle.backward(pr, f, K, pix, gref, alpha_min=oracle.ALPHA_MIN_F32,
+                                 alpha_max=oracle.ALPHA_MAX_F32)
+    _compare("feat", gf.cpu().numpy(), rf, 1e-4)
+    _compare("alpha", ga.cpu().numpy(), ra, 1e-3)
+    _compare("conic", gc.cpu().numpy(), rc, 1e-3)

@@ -261,6 +261,20 @@ qr_status qr_cosine_loss(const float *feature_map, const float *target, const ui
                          int64_t P, int32_t C, float *loss_out, float *grad, float *scratch,
                          qr_stream stream);
 
+/* ---------------------------------------------------------------- relevance */
+
+/* Open-vocabulary relevance (Sec. 5 scores features against text embeddings by
+ * cosine similarity): out[p][q] = sum_c map[p][c] * Q[q][c] on the tensor
+ * cores (tcgen05, BF16 inputs, FP32 accumulation in TMEM).  feature_map
+ * [P][C] float32 (rounded to BF16 on the fly), queries_bf16 [Q][C] (unit
+ * vectors give cosine similarity against unit-normalised features),
+ * out [P][Q] float32.  Q in {16, 32, 64, 128}; C a multiple of 64 with the
+ * queries fitting in shared memory (Q * C * 2 bytes <= ~190 KB).  status: a
+ * device int32 the kernel sets to QR_ERR_DEVICE_TIMEOUT if a bounded wait
+ * gives up (it is never cleared by the library). */
+qr_status qr_relevance(const float *feature_map, const uint16_t *queries_bf16, int32_t Q, int32_t C,
+                       int64_t P, float *out, int32_t *status, qr_stream stream);
+
 /* ---------------------------------------------------------------- feature storage */
 
 /* Storage formats of the feature table; the paper stores FP32 (Sec. 4).

@@ -344,6 +344,16 @@ qr_status qr_cosine_loss(const float *feature_map, const float *target, const ui
                                         reinterpret_cast<cudaStream_t>(stream)));
 }
 
+qr_status qr_relevance(const float *feature_map, const uint16_t *queries_bf16, int32_t Q, int32_t C,
+                       int64_t P, float *out, int32_t *status, qr_stream stream) {
+    if (!feature_map || !queries_bf16 || !out || !status || P < 0) return QR_ERR_INVALID_ARG;
+    if (!relevance_supported(Q, C)) return QR_ERR_NOT_SUPPORTED;
+    if (!aligned16(feature_map) || !aligned16(queries_bf16) || !aligned16(out)) return QR_ERR_ALIGNMENT;
+    if (P == 0) return QR_OK;
+    return from_cuda(launch_relevance(feature_map, queries_bf16, Q, P, C, out, status,
+                                      reinterpret_cast<cudaStream_t>(stream)));
+}
+
 uint64_t qr_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 }  // extern "C"

@@ -66,6 +66,10 @@ cudaError_t launch_backward(const qr_frame &f, const void *feat, const float *sc
 cudaError_t launch_cosine_loss(const float *F, const float *tgt, const uint8_t *counts, int64_t P,
                                int C, float *term, float *out2, float *grad, cudaStream_t s);
 
+bool relevance_supported(int Q, int C);
+cudaError_t launch_relevance(const float *map, const uint16_t *q, int Q, int64_t P, int C,
+                             float *out, int *status, cudaStream_t s);
+
 // Generic pieces of the sort, reused by later stages.
 // Stable LSD radix sort of (key, val) pairs; count read from the device.
 // Sorts bits [bit_lo, bit_hi) of the keys; returns through *out_keys/*out_vals

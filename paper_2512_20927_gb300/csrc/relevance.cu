@@ -1,0 +1,267 @@
+// K8: open-vocabulary relevance (Sec. 5: cosine similarity of features and
+// text embeddings), R[p][q] = sum_c map[p][c] * Q[q][c], on the 5th-generation
+// tensor cores (tcgen05 / UMMA, kind::f16: BF16 x BF16 -> FP32 in TMEM).
+//
+// GB300 design: a persistent CTA of 4 warps per tile of 128 pixels.
+//   * the BF16 queries (Q x C, at most 128 x 1024) are staged once per CTA in
+//     shared memory in the K-major 128-byte-swizzled layout UMMA reads;
+//   * the map arrives in FP32 (the blend's output), so each 128 x 64 slice is
+//     read with coalesced 16-byte loads, rounded to BF16 in registers and
+//     written swizzled into one of two shared-memory stages (a TMA copy cannot
+//     change the dtype);
+//   * one thread issues four 128 x Q x 16 MMAs per slice into a TMEM
+//     accumulator (Q columns), and tcgen05.commit signals an mbarrier when the
+//     stage may be refilled, so loading slice k+1 overlaps the MMAs of slice k;
+//   * the epilogue reads the accumulator with tcgen05.ld (warp w owns TMEM
+//     lanes 32w..32w+31 = pixels) and writes FP32 rows of R.
+// The product is memory-bound at Q = 64 (about 51 flops per byte of BF16 map),
+// so the tensor cores' job is to keep the FMA work off the critical path.
+// Every mbarrier wait is bounded; on timeout the CTA records
+// QR_ERR_DEVICE_TIMEOUT in the status word, frees its TMEM and returns.
+#include <cuda_bf16.h>
+
+#include "qr_internal.cuh"
+
+namespace qr {
+namespace {
+
+constexpr int BM = 128;            // pixels per tile (TMEM lanes)
+constexpr int BK = 64;             // channels per slice: 128 bytes of BF16
+constexpr int NT = 128;            // threads
+constexpr int A_STAGE = BM * BK * 2;   // 16 KB
+constexpr unsigned kSpinLimit = 1u << 26;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// K-major, 128-byte swizzle: row r of a 128-byte-wide slice, 16-byte chunk c.
+__device__ __forceinline__ uint32_t swz(int r, int c) {
+    return uint32_t(r) * 128u + uint32_t((c ^ (r & 7)) * 16);
+}
+
+// Shared-memory matrix descriptor (tcgen05): start >> 4, LBO (unused for
+// swizzled K-major, 16 B), SBO = 1024 B between 8-row groups, fixed 0b001 at
+// bit 46, swizzle mode 2 = 128 B at bits 61-63.
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
+    return uint64_t((saddr & 0x3FFFFu) >> 4) | (uint64_t(1) << 16) | (uint64_t(1024 >> 4) << 32) |
+           (uint64_t(1) << 46) | (uint64_t(2) << 61);
+}
+
+// Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16
+// (bits 7-9, 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t make_idesc(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(N >> 3) << 17) | (uint32_t(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+// Bounded wait for the phase with the given parity; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    const uint32_t a = smem_u32(bar);
+    for (unsigned i = 0; i < kSpinLimit; ++i) {
+        uint32_t done;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(done) : "r"(a), "r"(parity) : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// The same decision for every thread of the CTA: thread 0 polls, all read the result.
+__device__ __forceinline__ bool cta_wait(uint64_t *bar, uint32_t parity, int *s_flag) {
+    if (threadIdx.x == 0) *s_flag = mbar_wait(bar, parity) ? 1 : 0;
+    __syncthreads();
+    const bool r = *s_flag != 0;
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                          uint32_t idesc, uint32_t accumulate) {
+    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                 " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                 :: "r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate) : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 :: "r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// 16 consecutive accumulator columns of this warp's 32 TMEM lanes.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
+    uint32_t r[16];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                   "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+                   "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Round an FP32 map slice (rows p0.., channels c0..c0+63) to BF16 into a swizzled stage.
+__device__ __forceinline__ void load_a_slice(const float *__restrict__ map, int64_t P, int C,
+                                             int64_t p0, int c0, unsigned char *stage) {
+    // 128 rows x 16 float4 per row; a warp instruction covers two rows (coalesced 256 B each)
+    for (int i = threadIdx.x; i < BM * 16; i += NT) {
+        const int r = i >> 4, f4 = i & 15;
+        const int64_t p = p0 + r;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (p < P) v = *reinterpret_cast<const float4 *>(map + p * C + c0 + f4 * 4);
+        const __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y);
+        const __nv_bfloat162 hi = __floats2bfloat162_rn(v.z, v.w);
+        uint2 packed;
+        packed.x = *reinterpret_cast<const uint32_t *>(&lo);
+        packed.y = *reinterpret_cast<const uint32_t *>(&hi);
+        *reinterpret_cast<uint2 *>(stage + swz(r, f4 >> 1) + (f4 & 1) * 8) = packed;
+    }
+}
+
+template <int QN>
+__global__ void __launch_bounds__(NT, 1)
+relevance_kernel(const float *__restrict__ map, const uint16_t *__restrict__ queries, int64_t P,
+                 int C, float *__restrict__ out, int *__restrict__ status) {
+    constexpr uint32_t TMEM_COLS = QN <= 32 ? 32 : QN <= 64 ? 64 : 128;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *base = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const int nslices = C / BK;
+    unsigned char *sB = base;                                     // nslices x QN x 128 B
+    unsigned char *sA = sB + size_t(nslices) * QN * 128;         // 2 stages x 16 KB
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sA + 2 * A_STAGE);   // 2 mbarriers
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2);
+    int *s_flag = reinterpret_cast<int *>(tmem_slot + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    // queries -> swizzled K-major slices (16-byte chunks copied as they are)
+    for (int i = threadIdx.x; i < nslices * QN * 8; i += NT) {
+        const int s = i / (QN * 8), rem = i % (QN * 8), n = rem >> 3, c = rem & 7;
+        const uint4 v = *reinterpret_cast<const uint4 *>(queries + size_t(n) * C + s * BK + c * 8);
+        *reinterpret_cast<uint4 *>(sB + size_t(s) * QN * 128 + swz(n, c)) = v;
+    }
+    if (threadIdx.x == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_u32(tmem_slot)), "r"(TMEM_COLS) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    constexpr uint32_t idesc = make_idesc(BM, QN);
+    uint32_t uses[2] = {0u, 0u};      // commits issued per stage
+    bool ok = true;
+    const int64_t tiles = (P + BM - 1) / BM;
+    for (int64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+        const int64_t p0 = t * BM;
+        for (int s = 0; s < nslices; ++s) {
+            const int st = s & 1;
+            if (uses[st] > 0 && !cta_wait(&bars[st], (uses[st] - 1) & 1, s_flag)) { ok = false; break; }
+            load_a_slice(map, P, C, p0, s * BK, sA + st * A_STAGE);
+            fence_async_smem();
+            tc_fence_before();
+            __syncthreads();
+            tc_fence_after();
+            if (threadIdx.x == 0) {
+                const uint32_t a0 = smem_u32(sA + st * A_STAGE);
+                const uint32_t b0 = smem_u32(sB + size_t(s) * QN * 128);
+#pragma unroll
+                for (int k = 0; k < BK / 16; ++k)
+                    umma_bf16(tmem, make_desc(a0 + k * 32), make_desc(b0 + k * 32), idesc,
+                              (s > 0 || k > 0) ? 1u : 0u);
+                umma_commit(&bars[st]);
+            }
+            ++uses[st];
+        }
+        if (!ok) break;
+        // all MMAs of this tile are done once the last commit has landed
+        const int last = (nslices - 1) & 1;
+        if (!cta_wait(&bars[last], (uses[last] - 1) & 1, s_flag)) { ok = false; break; }
+        tc_fence_after();
+        const int64_t p = p0 + warp * 32 + lane;
+        const uint32_t taddr = tmem + (uint32_t(warp * 32) << 16);
+#pragma unroll
+        for (int c = 0; c < QN; c += 16) {
+            float v[16];
+            tmem_ld16(taddr + uint32_t(c), v);
+            if (p < P) {
+                float4 *o = reinterpret_cast<float4 *>(out + p * QN + c);
+                o[0] = make_float4(v[0], v[1], v[2], v[3]);
+                o[1] = make_float4(v[4], v[5], v[6], v[7]);
+                o[2] = make_float4(v[8], v[9], v[10], v[11]);
+                o[3] = make_float4(v[12], v[13], v[14], v[15]);
+            }
+        }
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+    }
+    if (!ok && threadIdx.x == 0) atomicExch(status, int(QR_ERR_DEVICE_TIMEOUT));
+    // a stage whose commit was not waited for may still be in flight: drain it
+    for (int st = 0; st < 2; ++st)
+        if (uses[st] > 0) cta_wait(&bars[st], (uses[st] - 1) & 1, s_flag);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(TMEM_COLS) : "memory");
+}
+
+template <int QN>
+cudaError_t run(const float *map, const uint16_t *q, int64_t P, int C, float *out, int *status,
+                cudaStream_t s) {
+    const size_t smem = 1024 + size_t(C / BK) * QN * 128 + 2 * A_STAGE + 64;
+    cudaError_t e = cudaFuncSetAttribute(relevance_kernel<QN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(smem));
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t tiles = (P + BM - 1) / BM;
+    const int grid = int(tiles < sms ? tiles : sms);
+    relevance_kernel<QN><<<grid, NT, smem, s>>>(map, q, P, C, out, status);
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool relevance_supported(int Q, int C) {
+    if (C < BK || C % BK) return false;
+    if (!(Q == 16 || Q == 32 || Q == 64 || Q == 128)) return false;
+    return 1024 + size_t(C / BK) * Q * 128 + 2 * A_STAGE + 64 <= 227 * 1024;
+}
+
+cudaError_t launch_relevance(const float *map, const uint16_t *q, int Q, int64_t P, int C,
+                             float *out, int *status, cudaStream_t s) {
+    switch (Q) {
+        case 16: return run<16>(map, q, P, C, out, status, s);
+        case 32: return run<32>(map, q, P, C, out, status, s);
+        case 64: return run<64>(map, q, P, C, out, status, s);
+        case 128: return run<128>(map, q, P, C, out, status, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace qr

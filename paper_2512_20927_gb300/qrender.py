@@ -91,6 +91,7 @@ SIGNATURES = {
     "qr_backward": (_S, [ctypes.POINTER(qr_frame), _P, _P, _S, _I32, _P, _P, _P, _P, _P, _P, _P,
                          _P, ctypes.c_size_t, _P]),
     "qr_cosine_loss": (_S, [_P, _P, _P, _I64, _I32, _P, _P, _P, _P]),
+    "qr_relevance": (_S, [_P, _P, _I32, _I32, _I64, _P, _P, _P]),
     "qr_quantize_bf16": (_S, [_P, _I64, _P, _P]),
     "qr_quantize_fp8": (_S, [_P, _I64, _I32, _P, _P, _P]),
     "qr_render_noalloc": (_S, [_P, _P, _P, _P, _I64, ctypes.POINTER(qr_camera),
@@ -349,6 +350,21 @@ def qr_cosine_loss(feature_map, target, counts, stream=None):
                                  _ptr(counts), P, C, _ptr(out2), _ptr(grad), _ptr(scratch),
                                  _stream(stream)), "qr_cosine_loss")
     return out2[0], grad
+
+
+def qr_relevance(feature_map, queries_bf16, stream=None):
+    """Relevance scores [P, Q] float32 of a [P, C] float32 map against [Q, C] BF16 queries.
+
+    Returns (scores, status) where status is a 1-element device int32 tensor
+    (nonzero if a device-side wait timed out)."""
+    torch = _torch()
+    P, C = feature_map.shape
+    Q = queries_bf16.shape[0]
+    out = torch.empty((P, Q), dtype=torch.float32, device=feature_map.device)
+    status = torch.zeros(1, dtype=torch.int32, device=feature_map.device)
+    _check(load().qr_relevance(_ptr(feature_map), _ptr(queries_bf16), Q, C, P, _ptr(out),
+                               _ptr(status), _stream(stream)), "qr_relevance")
+    return out, status
 
 
 def qr_quantize_bf16(x, stream=None):

@@ -147,7 +147,7 @@ def test_differentiation_config_sampled_pixels():
     pix = H.sample_pixels(640, 480, 200, seed=9)
     pr, pix, ref = H.run_oracle(g, f, cam, K, pixels=pix)
     pr2, _, ref2 = H.run_oracle(g2, f2, cam, K, pixels=pix)
-    tie = (ref.tie & compare.Q_TIE_BITS) != 0
+    tie = ((ref.tie & compare.Q_TIE_BITS) != 0) | ((ref2.tie & compare.DENSE_TIE_BITS) != 0)
     use = (~tie) & (ref.cnt > 0)
     idx = H.pixel_index(pix, cam.width)
     mask = torch.zeros(cam.width * cam.height, dtype=torch.uint8, device="cuda")

@@ -37,20 +37,25 @@ template <> struct Vec<QR_F32> { static constexpr int C = 4; };
 template <> struct Vec<QR_BF16> { static constexpr int C = 8; };
 template <> struct Vec<QR_FP8E4M3> { static constexpr int C = 16; };
 
+// acc[0..1] += w * (x0, x1) with one packed FP32x2 FMA (each lane of the pair
+// rounds exactly like a scalar fmaf).
+__device__ __forceinline__ void fma2(float *acc, float w, float x0, float x1) {
+    asm("{\n .reg .b64 a, ww, xx;\n mov.b64 a, {%0, %1};\n mov.b64 ww, {%2, %2};\n"
+        " mov.b64 xx, {%3, %4};\n fma.rn.f32x2 a, ww, xx, a;\n mov.b64 {%0, %1}, a;\n}\n"
+        : "+f"(acc[0]), "+f"(acc[1]) : "f"(w), "f"(x0), "f"(x1));
+}
+
 template <int DT>
 __device__ __forceinline__ void decode_fma(const uint4 v, float w, float *acc);
 
 template <>
 __device__ __forceinline__ void decode_fma<QR_F32>(const uint4 v, float w, float *acc) {
-    acc[0] = fmaf(w, __uint_as_float(v.x), acc[0]);
-    acc[1] = fmaf(w, __uint_as_float(v.y), acc[1]);
-    acc[2] = fmaf(w, __uint_as_float(v.z), acc[2]);
-    acc[3] = fmaf(w, __uint_as_float(v.w), acc[3]);
+    fma2(acc + 0, w, __uint_as_float(v.x), __uint_as_float(v.y));
+    fma2(acc + 2, w, __uint_as_float(v.z), __uint_as_float(v.w));
 }
 
 __device__ __forceinline__ void bf16x2_fma(uint32_t u, float w, float *acc) {
-    acc[0] = fmaf(w, __uint_as_float(u << 16), acc[0]);
-    acc[1] = fmaf(w, __uint_as_float(u & 0xFFFF0000u), acc[1]);
+    fma2(acc, w, __uint_as_float(u << 16), __uint_as_float(u & 0xFFFF0000u));
 }
 
 template <>
@@ -66,10 +71,8 @@ __device__ __forceinline__ void fp8x4_fma(uint32_t u, float w, float *acc) {
     const __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2(__nv_fp8x2_storage_t(u >> 16), __NV_E4M3);
     const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&lo));
     const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&hi));
-    acc[0] = fmaf(w, a.x, acc[0]);
-    acc[1] = fmaf(w, a.y, acc[1]);
-    acc[2] = fmaf(w, b.x, acc[2]);
-    acc[3] = fmaf(w, b.y, acc[3]);
+    fma2(acc + 0, w, a.x, a.y);
+    fma2(acc + 2, w, b.x, b.y);
 }
 
 template <>

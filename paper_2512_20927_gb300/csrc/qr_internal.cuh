@@ -19,7 +19,7 @@ enum { CNT_STATUS = 0, CNT_ISECT = 1, CNT_VISIBLE = 2, CNT_N = 3, CNT_SORT_N = 4
 // Workspace slots (byte offsets in qr_frame::off).
 enum Slot {
     S_COUNTERS = 0, S_REC_M, S_REC_C, S_REC_A, S_RECT, S_TCOUNT, S_GKEY,
-    S_VISCNT, S_BSUM, S_KID, S_OFF, S_TCNT, S_RANGES, S_KEYS64, S_SCRATCH64, S_IGID,
+    S_VISCNT, S_BSUM, S_KID, S_OFF, S_TCNT, S_RANGES, S_KEYS64, S_SCRATCH64, S_IGID, S_DIFF,
     S_END
 };
 constexpr int kProjectThreads = 256;

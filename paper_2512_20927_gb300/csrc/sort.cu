@@ -5,25 +5,26 @@
 // touches it, ordered by (camera depth, id) -- the order a stable sort of
 // 64-bit (tile << 32 | depth) keys over id-ordered input gives.
 //
-// GB300 design (6 kernels after the projection, no global depth sort):
+// GB300 design (5 kernels after the projection, no global depth sort):
 //   1. project (K1) writes, per CTA of 256 Gaussians, how many it kept and the
 //      sum of their tile counts;
 //   2. offsets_scan + offsets_apply compact the kept Gaussians (id order) and
 //      give each its first output slot (exclusive scan), with the capacity
 //      check; offsets of kept Gaussians are strictly increasing;
-//   3. expand_count: a load-balanced expansion -- each CTA owns 2048
+//      Each kept Gaussian also adds its tile rectangle to a 2-D difference
+//      array of per-tile counts (4 atomics instead of one per intersection);
+//   3. tile_scan integrates the difference array into per-tile counts and
+//      exclusive offsets, i.e. the tile ranges;
+//   4. expand_scatter: a load-balanced expansion -- each CTA owns 2048
 //      consecutive output slots, finds their owners with a warp-wide 32-way
 //      search (at most 2048 owners per chunk), derives each slot's tile from
-//      the owner's footprint rectangle, and counts intersections per tile with
-//      warp-aggregated atomics;
-//   4. tile_scan: per-tile offsets, i.e. the tile ranges;
-//   5. expand_scatter: the same expansion writes (depth << 32 | id) into its
-//      tile's bucket at an atomically claimed position;
-//   6. tile_sort: one CTA per tile sorts its bucket in shared memory (bitonic
+//      the owner's footprint rectangle, and writes (depth << 32 | id) into
+//      its tile's bucket at an atomically claimed position;
+//   5. tile_sort: one CTA per tile sorts its bucket in shared memory (bitonic
 //      network over the unique 64-bit keys) and writes the ids; a bucket
 //      larger than shared memory is sorted in chunks and merged in global
 //      memory by the same CTA (merge path), so no size is refused.
-// Keys are unique, so the order inside a bucket before step 6 does not matter
+// Keys are unique, so the order inside a bucket before step 5 does not matter
 // and the result is deterministic.  No CTA waits for another.  Counts live in
 // device memory, so the stage can be captured in a CUDA graph.
 #include "qr_internal.cuh"
@@ -57,10 +58,13 @@ offsets_scan(uint32_t *kept, uint32_t *tsum, int nblk, uint32_t *counters, uint3
     }
 }
 
-// Compacted kept ids (id order) and their first output slots.
+// Compacted kept ids (id order) and their first output slots; each kept
+// Gaussian also adds its footprint rectangle to the 2-D difference array of
+// tile counts (+1 at (x0,y0) and (x1+1,y1+1), -1 at (x1+1,y0) and (x0,y1+1)).
 __global__ void __launch_bounds__(kProjectThreads)
 offsets_apply(const uint32_t *__restrict__ tcount, const uint32_t *__restrict__ kept_base,
-              const uint32_t *__restrict__ tsum_base, int64_t n, uint32_t *__restrict__ kid,
+              const uint32_t *__restrict__ tsum_base, int64_t n, const uint2 *__restrict__ rect,
+              int tiles_x, int *__restrict__ diff, uint32_t *__restrict__ kid,
               uint32_t *__restrict__ koff) {
     __shared__ uint32_t s_w[32];
     const int64_t g = int64_t(blockIdx.x) * kProjectThreads + threadIdx.x;
@@ -73,6 +77,14 @@ offsets_apply(const uint32_t *__restrict__ tcount, const uint32_t *__restrict__ 
         const uint32_t slot = kept_base[blockIdx.x] + kinc - 1u;
         kid[slot] = uint32_t(g);
         koff[slot] = tsum_base[blockIdx.x] + cinc - c;
+        const uint2 rc = rect[g];
+        const int x0 = int(rc.x & 0xFFFFu), y0 = int(rc.x >> 16);
+        const int x1 = int(rc.y & 0xFFFFu) + 1, y1 = int(rc.y >> 16) + 1;
+        const int stride = tiles_x + 1;
+        atomicAdd(&diff[y0 * stride + x0], 1);
+        atomicAdd(&diff[y0 * stride + x1], -1);
+        atomicAdd(&diff[y1 * stride + x0], -1);
+        atomicAdd(&diff[y1 * stride + x1], 1);
     }
 }
 
@@ -137,44 +149,50 @@ __device__ __forceinline__ void slot_owner(const ExpandSmem &sm, uint32_t len, u
     tile = (ty0 + j / wx) * uint32_t(tiles_x) + tx0 + j % wx;
 }
 
-__global__ void __launch_bounds__(T)
-expand_count(const uint32_t *__restrict__ koff, const uint32_t *__restrict__ kid,
-             const uint2 *__restrict__ rect, const uint32_t *__restrict__ counters, int tiles_x,
-             uint32_t *__restrict__ tcnt) {
-    __shared__ ExpandSmem sm;
-    const uint32_t X = counters[CNT_SORT_N];        // 0 when the capacity was exceeded
-    const uint32_t nk = counters[CNT_VISIBLE];
-    for (uint32_t o0 = blockIdx.x * uint32_t(EMIT_CHUNK); o0 < X; o0 += gridDim.x * uint32_t(EMIT_CHUNK)) {
-        const uint32_t o1 = min(X, o0 + uint32_t(EMIT_CHUNK));
-        const uint32_t len = stage_owners(sm, koff, kid, rect, nk, o0, o1);
-        for (uint32_t base = o0; base < o1; base += T) {       // uniform trip count
-            const uint32_t o = base + threadIdx.x;
-            uint32_t g = 0, tile = 0xFFFFFFFFu;
-            if (o < o1) slot_owner(sm, len, o, tiles_x, g, tile);
-            const unsigned peers = __match_any_sync(0xffffffffu, tile);
-            if (o < o1 && int(threadIdx.x & 31) == __ffs(peers) - 1)
-                atomicAdd(&tcnt[tile], uint32_t(__popc(peers)));
-        }
-        __syncthreads();
-    }
-}
-
-// Per-tile exclusive offsets -> ranges; the counts become zeroed cursors.
+// Tile counts from the difference array (prefix sums along x, then y, one
+// CTA), then exclusive offsets -> ranges; the counts become zeroed cursors.
 __global__ void __launch_bounds__(1024)
-tile_scan(uint32_t *tcnt, int tiles, uint2 *ranges) {
+tile_scan(const int *__restrict__ diff, const uint32_t *__restrict__ counters, uint32_t *tcnt,
+          int tiles_x, int tiles_y, uint2 *ranges) {
     __shared__ uint32_t s_w[32];
+    const int stride = tiles_x + 1;
+    const int tiles = tiles_x * tiles_y;
+    if (counters[CNT_STATUS] != 0) {   // capacity exceeded: every tile list is empty
+        for (int t = threadIdx.x; t < tiles; t += blockDim.x) {
+            ranges[t] = make_uint2(0u, 0u);
+            tcnt[t] = 0u;
+        }
+        return;
+    }
+    // rows: running sum along x (one thread per row)
+    for (int y = threadIdx.x; y < tiles_y; y += blockDim.x) {
+        int run = 0;
+        for (int x = 0; x < tiles_x; ++x) {
+            run += diff[y * stride + x];
+            tcnt[y * tiles_x + x] = uint32_t(run);
+        }
+    }
+    __syncthreads();
+    // columns: running sum along y (one thread per column)
+    for (int x = threadIdx.x; x < tiles_x; x += blockDim.x) {
+        uint32_t run = 0;
+        for (int y = 0; y < tiles_y; ++y) {
+            run += tcnt[y * tiles_x + x];
+            tcnt[y * tiles_x + x] = run;
+        }
+    }
+    __syncthreads();
     uint32_t carry = 0;
     for (int base = 0; base < tiles; base += blockDim.x) {
         const int t = base + threadIdx.x;
         const uint32_t c = t < tiles ? tcnt[t] : 0u;
         uint32_t chunk;
         const uint32_t inc = block_inclusive_scan(c, s_w, chunk);
-        if (t < tiles) {
-            ranges[t] = make_uint2(carry + inc - c, carry + inc);
-            tcnt[t] = 0u;
-        }
+        if (t < tiles) ranges[t] = make_uint2(carry + inc - c, carry + inc);
         carry += chunk;
     }
+    __syncthreads();
+    for (int t = threadIdx.x; t < tiles; t += blockDim.x) tcnt[t] = 0u;
 }
 
 __global__ void __launch_bounds__(T)
@@ -307,8 +325,11 @@ cudaError_t launch_sort(const qr_frame &f, cudaStream_t s) {
     const int tiles = num_tiles(f);
     uint2 *ranges = slot<uint2>(f, S_RANGES);
     uint32_t *tcnt = slot<uint32_t>(f, S_TCNT);
+    int *diff = slot<int>(f, S_DIFF);
     cudaError_t e = cudaMemsetAsync(tcnt, 0, sizeof(uint32_t) * size_t(tiles), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(ranges, 0, sizeof(uint2) * size_t(tiles), s);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(diff, 0, sizeof(int) * size_t(f.tiles_x + 1) * size_t(f.tiles_y + 1), s);
     if (e != cudaSuccess) return e;
     if (f.n == 0) return cudaSuccess;
     e = cudaFuncSetAttribute(tile_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -325,15 +346,14 @@ cudaError_t launch_sort(const qr_frame &f, cudaStream_t s) {
     const uint2 *rect = slot<uint2>(f, S_RECT);
     offsets_scan<<<1, 1024, 0, s>>>(kept, tsum, nblk, counters, uint32_t(f.max_isect));
     offsets_apply<<<nblk, kProjectThreads, 0, s>>>(slot<uint32_t>(f, S_TCOUNT), kept, tsum, f.n,
-                                                   kid, koff);
-    expand_count<<<sms * 2, T, 0, s>>>(koff, kid, rect, counters, f.tiles_x, tcnt);
-    tile_scan<<<1, 1024, 0, s>>>(tcnt, tiles, ranges);
+                                                   rect, f.tiles_x, diff, kid, koff);
+    tile_scan<<<1, 1024, 0, s>>>(diff, counters, tcnt, f.tiles_x, f.tiles_y, ranges);
     auto *keys = slot<unsigned long long>(f, S_KEYS64);
     expand_scatter<<<sms * 2, T, 0, s>>>(koff, kid, rect, slot<uint32_t>(f, S_GKEY), counters,
                                          f.tiles_x, ranges, tcnt, keys);
     tile_sort<<<tiles, T, TS_CAP * sizeof(unsigned long long), s>>>(
         ranges, keys, slot<unsigned long long>(f, S_SCRATCH64), slot<uint32_t>(f, S_IGID));
-    count_launch(6);
+    count_launch(5);
     return cudaGetLastError();
 }
 

@@ -223,6 +223,41 @@ qr_status qr_render_host(qr_frame *frame, const float *mean_host, const float *l
                          int32_t C, void *dev_inputs, void *dev_outputs, float *out_host,
                          qr_stream stream);
 
+/* ---------------------------------------------------------------- many views */
+
+/* One view of a batch: its frame (already through qr_project and qr_sort),
+ * the feature table of its scene, and its outputs (layouts as in qr_select
+ * and qr_blend). */
+typedef struct {
+    const qr_frame *frame;
+    const void *feat;
+    const float *feat_scale;
+    int32_t *ids;
+    float *weights;
+    uint8_t *counts;
+    float *out;
+} qr_view;
+
+/* Bytes of device workspace for the descriptors of n_views views. */
+size_t qr_batch_workspace_bytes(int32_t n_views);
+
+/* Copy the per-view descriptors into ws (set-up; synchronises the stream so
+ * views may be freed afterwards).  All views must share K.  total_tiles
+ * receives the number of (view, tile) work items. */
+qr_status qr_batch_prepare(const qr_view *views, int32_t n_views, void *ws, size_t ws_bytes,
+                           uint32_t *total_tiles, qr_stream stream);
+
+/* Algorithm 1 (selection and blend) for every tile of every prepared view in
+ * one persistent launch: CTAs take (view, tile) items from a device counter,
+ * select each pixel's quantile Gaussians into shared memory and blend them
+ * there (same arithmetic as qr_select + qr_blend; ids/weights/counts are also
+ * written).  dtype and C are shared by the batch; group = pixels per warp in
+ * the blend (4, 2 or 1; 0 = largest allowed by K), ctas_per_sm caps the
+ * resident CTAs per SM (0 = occupancy limit).  Capturable in a CUDA graph. */
+qr_status qr_render_batch(const void *ws, int32_t n_views, uint32_t total_tiles, qr_dtype dtype,
+                          int32_t C, int32_t K, int32_t group, int32_t ctas_per_sm,
+                          qr_stream stream);
+
 /* ---------------------------------------------------------------- backward */
 
 /* Backward of Algorithm 1.  The paper states that image-space gradients flow

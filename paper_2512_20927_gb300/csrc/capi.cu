@@ -4,6 +4,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <vector>
 
 #include "qr_internal.cuh"
 
@@ -353,6 +354,45 @@ qr_status qr_relevance(const float *feature_map, const uint16_t *queries_bf16, i
     if (P == 0) return QR_OK;
     return from_cuda(launch_relevance(feature_map, queries_bf16, Q, P, C, out, status,
                                       reinterpret_cast<cudaStream_t>(stream)));
+}
+
+size_t qr_batch_workspace_bytes(int32_t n_views) {
+    return n_views < 1 ? 0 : batch_desc_bytes(n_views);
+}
+
+qr_status qr_batch_prepare(const qr_view *views, int32_t n_views, void *ws, size_t ws_bytes,
+                           uint32_t *total_tiles, qr_stream stream) {
+    if (!views || n_views < 1 || !ws || !total_tiles) return QR_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(ws) & (kAlign - 1)) != 0) return QR_ERR_ALIGNMENT;
+    if (ws_bytes < batch_desc_bytes(n_views)) return QR_ERR_INVALID_ARG;
+    uint64_t tiles = 0;
+    for (int i = 0; i < n_views; ++i) {
+        const qr_view &v = views[i];
+        if (!frame_ok(v.frame) || !v.feat || !v.ids || !v.weights || !v.counts || !v.out)
+            return QR_ERR_INVALID_ARG;
+        if (v.frame->params.K != views[0].frame->params.K) return QR_ERR_INVALID_ARG;
+        if (!aligned16(v.feat) || !aligned16(v.out)) return QR_ERR_ALIGNMENT;
+        tiles += uint64_t(num_tiles(*v.frame));
+    }
+    if (tiles > 0xFFFFFFF0ull) return QR_ERR_INVALID_ARG;
+    std::vector<unsigned char> host(batch_view_size() * size_t(n_views));
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = prepare_batch(views, n_views, ws, total_tiles, s,
+                                  reinterpret_cast<BatchView *>(host.data()));
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return from_cuda(e);
+}
+
+qr_status qr_render_batch(const void *ws, int32_t n_views, uint32_t total_tiles, qr_dtype dtype,
+                          int32_t C, int32_t K, int32_t group, int32_t ctas_per_sm,
+                          qr_stream stream) {
+    if (!ws || n_views < 1 || K < 1 || K > kKMax || group < 0 || group > 4 || ctas_per_sm < 0)
+        return QR_ERR_INVALID_ARG;
+    if (dtype != QR_F32 && dtype != QR_BF16 && dtype != QR_FP8E4M3) return QR_ERR_INVALID_ARG;
+    if (!batch_supported(dtype, C)) return QR_ERR_NOT_SUPPORTED;
+    if (total_tiles == 0) return QR_OK;
+    return from_cuda(launch_batch(ws, n_views, total_tiles, dtype, C, K, group, ctas_per_sm,
+                                  reinterpret_cast<cudaStream_t>(stream)));
 }
 
 uint64_t qr_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }

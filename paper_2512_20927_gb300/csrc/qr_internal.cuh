@@ -66,6 +66,14 @@ cudaError_t launch_backward(const qr_frame &f, const void *feat, const float *sc
 cudaError_t launch_cosine_loss(const float *F, const float *tgt, const uint8_t *counts, int64_t P,
                                int C, float *term, float *out2, float *grad, cudaStream_t s);
 
+struct BatchView;
+bool batch_supported(qr_dtype dt, int C);
+size_t batch_desc_bytes(int n_views);
+size_t batch_view_size();
+cudaError_t launch_batch(const void *ws, int n_views, uint32_t total_items, qr_dtype dt, int C,
+                         int K, int group, int ctas_per_sm, cudaStream_t s);
+cudaError_t prepare_batch(const qr_view *views, int n_views, void *ws, uint32_t *total_items,
+                          cudaStream_t s, BatchView *host_scratch);
 bool relevance_supported(int Q, int C);
 cudaError_t launch_relevance(const float *map, const uint16_t *q, int Q, int64_t P, int C,
                              float *out, int *status, cudaStream_t s);

@@ -53,6 +53,13 @@ class qr_frame(ctypes.Structure):
                 ("off", ctypes.c_size_t * FRAME_SLOTS)]
 
 
+class qr_view(ctypes.Structure):
+    _fields_ = [("frame", ctypes.c_void_p), ("feat", ctypes.c_void_p),
+                ("feat_scale", ctypes.c_void_p), ("ids", ctypes.c_void_p),
+                ("weights", ctypes.c_void_p), ("counts", ctypes.c_void_p),
+                ("out", ctypes.c_void_p)]
+
+
 class qr_frame_view(ctypes.Structure):
     _fields_ = [(name, ctypes.c_void_p) for name in (
         "mean2d_hi_lo", "axes", "opacity", "depth_key", "tile_count", "kept_gid", "kept_offset",
@@ -92,6 +99,10 @@ SIGNATURES = {
                          _P, ctypes.c_size_t, _P]),
     "qr_cosine_loss": (_S, [_P, _P, _P, _I64, _I32, _P, _P, _P, _P]),
     "qr_relevance": (_S, [_P, _P, _I32, _I32, _I64, _P, _P, _P]),
+    "qr_batch_workspace_bytes": (ctypes.c_size_t, [_I32]),
+    "qr_batch_prepare": (_S, [ctypes.POINTER(qr_view), _I32, _P, ctypes.c_size_t,
+                              ctypes.POINTER(ctypes.c_uint32), _P]),
+    "qr_render_batch": (_S, [_P, _I32, ctypes.c_uint32, _S, _I32, _I32, _I32, _I32, _P]),
     "qr_quantize_bf16": (_S, [_P, _I64, _P, _P]),
     "qr_quantize_fp8": (_S, [_P, _I64, _I32, _P, _P, _P]),
     "qr_render_noalloc": (_S, [_P, _P, _P, _P, _I64, ctypes.POINTER(qr_camera),

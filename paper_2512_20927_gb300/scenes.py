@@ -123,10 +123,18 @@ def room_gaussians(rng: np.random.Generator, n: int) -> Gaussians:
     return Gaussians(mean, log_scale, quat, opacity)
 
 
-def unit_features(rng: np.random.Generator, n: int, channels: int) -> np.ndarray:
-    f = rng.normal(0.0, 1.0, size=(n, channels))
-    f /= np.linalg.norm(f, axis=1, keepdims=True)
-    return f.astype(np.float32)
+def unit_features(rng: np.random.Generator, n: int, channels: int,
+                  chunk: int = 65536) -> np.ndarray:
+    """N(0,1) rows normalised to unit L2 norm, drawn in row chunks (the same
+    values as one draw of the whole [n, channels] array, without its float64
+    copy)."""
+    out = np.empty((n, channels), np.float32)
+    for a in range(0, n, chunk):
+        b = min(n, a + chunk)
+        f = rng.normal(0.0, 1.0, size=(b - a, channels))
+        f /= np.linalg.norm(f, axis=1, keepdims=True)
+        out[a:b] = f
+    return out
 
 
 def room_scene(seed: int = 0, n: int = 500_000, channels: int = 512):

@@ -184,7 +184,7 @@ def run_gpu(args, ws, rank, local):
         q.qr_project(fr, *gdev)
         q.qr_sort(fr)
         q.qr_select(fr, ids, w, cnt)
-        q.qr_blend(fdev, None, ids, w, cnt, out)
+        q.qr_blend(fdev, None, ids, w, cnt, out, width=WIDTH)
 
     def barrier():
         if ws > 1:
@@ -212,7 +212,7 @@ def run_gpu(args, ws, rank, local):
             e[1].record(stream)
             q.qr_select(fr, ids, w, cnt)
             e[2].record(stream)
-            q.qr_blend(fdev, None, ids, w, cnt, out)
+            q.qr_blend(fdev, None, ids, w, cnt, out, width=WIDTH)
             e[3].record(stream)
         t_end.record(stream)
         barrier()
@@ -281,7 +281,7 @@ def run_gpu(args, ws, rank, local):
             q.qr_project(fr2, *gdev)
             q.qr_sort(fr2)
             q.qr_select(fr2, a[0], a[1], a[2])
-            q.qr_blend(fdev, None, a[0], a[1], a[2], a[3])
+            q.qr_blend(fdev, None, a[0], a[1], a[2], a[3], width=WIDTH)
         for _ in range(2):
             f2()
         torch.cuda.synchronize()

@@ -186,10 +186,15 @@ qr_status qr_select(const qr_frame *frame, int32_t *ids, float *weights, uint8_t
  * normalisation): out[p] = sum_{j < counts[p]} weights[p][j] * feat[ids[p][j]]
  * with FP32 accumulation.  feat is [n_gauss][C] of dtype; feat_scale [n_gauss]
  * float32 multiplies FP8 rows (NULL otherwise).  out is [P][C] float32.
- * Pixels with counts 0 get zeros.  ids must lie in [0, n_gauss). */
+ * Pixels with counts 0 get zeros.  ids must lie in [0, n_gauss).
+ * width > 0 declares the P pixels a row-major image of that width: pixels are
+ * then visited in 16x16 screen tiles with 2x2 groups sharing feature rows;
+ * width = 0 groups consecutive pixels.  Only the summation order (and speed)
+ * depends on it. */
 qr_status qr_blend(const void *feat, const float *feat_scale, qr_dtype dtype, int32_t C,
                    int64_t n_gauss, const int32_t *ids, const float *weights,
-                   const uint8_t *counts, int64_t P, int32_t K, float *out, qr_stream stream);
+                   const uint8_t *counts, int64_t P, int32_t K, int32_t width, float *out,
+                   qr_stream stream);
 
 /* Eq. 1 (V-Render, the dense method the paper compares against):
  * out[p] = sum_i T_i alpha'_i f_i over the pixel's whole list with the same

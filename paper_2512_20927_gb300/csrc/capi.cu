@@ -208,16 +208,19 @@ static qr_status check_feat(const void *feat, const float *feat_scale, qr_dtype 
 
 qr_status qr_blend(const void *feat, const float *feat_scale, qr_dtype dtype, int32_t C,
                    int64_t n_gauss, const int32_t *ids, const float *weights,
-                   const uint8_t *counts, int64_t P, int32_t K, float *out, qr_stream stream) {
+                   const uint8_t *counts, int64_t P, int32_t K, int32_t width, float *out,
+                   qr_stream stream) {
     qr_status st = check_feat(feat, feat_scale, dtype, C);
     if (st != QR_OK) return st;
-    if (!ids || !weights || !counts || !out || P < 0 || K < 1 || K > kKMax || n_gauss < 1)
+    if (!ids || !weights || !counts || !out || P < 0 || K < 1 || K > kKMax || n_gauss < 1 ||
+        width < 0 || (width > 0 && P % width != 0))
         return QR_ERR_INVALID_ARG;
     if (!aligned16(out)) return QR_ERR_ALIGNMENT;
     if (!blend_supported(dtype, C)) return QR_ERR_NOT_SUPPORTED;
     if (P == 0) return QR_OK;
+    const int H = width > 0 ? int(P / width) : 0;
     return from_cuda(launch_blend_tiled(feat, feat_scale, dtype, C, n_gauss, ids, weights, counts,
-                                        P, K, 0, 0, out, reinterpret_cast<cudaStream_t>(stream)));
+                                        P, K, width, H, out, reinterpret_cast<cudaStream_t>(stream)));
 }
 
 qr_status qr_dense(const qr_frame *frame, const void *feat, const float *feat_scale,

@@ -84,7 +84,7 @@ SIGNATURES = {
     "qr_project": (_S, [ctypes.POINTER(qr_frame), _P, _P, _P, _P, _P]),
     "qr_sort": (_S, [ctypes.POINTER(qr_frame), _P]),
     "qr_select": (_S, [ctypes.POINTER(qr_frame), _P, _P, _P, _P]),
-    "qr_blend": (_S, [_P, _P, _S, _I32, _I64, _P, _P, _P, _I64, _I32, _P, _P]),
+    "qr_blend": (_S, [_P, _P, _S, _I32, _I64, _P, _P, _P, _I64, _I32, _I32, _P, _P]),
     "qr_dense": (_S, [ctypes.POINTER(qr_frame), _P, _P, _S, _I32, _P, _P, _P]),
     "qr_render": (_S, [ctypes.POINTER(qr_frame), _P, _P, _P, _P, _P, _P, _S, _I32, _P, _P, _P,
                        _P, _P]),
@@ -264,11 +264,11 @@ def qr_select(fr: Frame, ids, weights, counts, stream=None):
                             _stream(stream)), "qr_select")
 
 
-def qr_blend(feat, feat_scale, ids, weights, counts, out, stream=None):
+def qr_blend(feat, feat_scale, ids, weights, counts, out, width=0, stream=None):
     P, K = ids.shape
     C = feat.shape[1]
     _check(load().qr_blend(_ptr(feat), _ptr(feat_scale), _dtype_code(feat), C, feat.shape[0],
-                           _ptr(ids), _ptr(weights), _ptr(counts), P, K, _ptr(out),
+                           _ptr(ids), _ptr(weights), _ptr(counts), P, K, width, _ptr(out),
                            _stream(stream)), "qr_blend")
 
 
@@ -440,7 +440,7 @@ def render_frame(gdev, feat, cam, K=8, max_isect=None, params=None, stream=None,
         f, fs = feat if isinstance(feat, tuple) else (feat, None)
         C = f.shape[1]
         out = torch.empty((P, C), dtype=torch.float32, device=mean.device)
-        qr_blend(f, fs, ids, w, cnt, out, stream=stream)
+        qr_blend(f, fs, ids, w, cnt, out, width=fr.width, stream=stream)
         res["out"] = out
         if dense:
             dout = torch.empty((P, C), dtype=torch.float32, device=mean.device)

@@ -89,17 +89,17 @@ def test_blend_rejects_bad_arguments_before_launch(lib):
     good = P(1 << 20)
     launches = L.qr_launch_count()
     # null features
-    assert L.qr_blend(None, None, q.QR_F32, 16, 10, good, good, good, 4, 8, good, None) == q.QR_ERR_INVALID_ARG
+    assert L.qr_blend(None, None, q.QR_F32, 16, 10, good, good, good, 4, 8, 0, good, None) == q.QR_ERR_INVALID_ARG
     # misaligned feature pointer
-    assert L.qr_blend(P((1 << 20) + 4), None, q.QR_F32, 16, 10, good, good, good, 4, 8, good, None) == q.QR_ERR_ALIGNMENT
+    assert L.qr_blend(P((1 << 20) + 4), None, q.QR_F32, 16, 10, good, good, good, 4, 8, 0, good, None) == q.QR_ERR_ALIGNMENT
     # row not a multiple of 16 bytes
-    assert L.qr_blend(good, None, q.QR_F32, 6, 10, good, good, good, 4, 8, good, None) == q.QR_ERR_ALIGNMENT
+    assert L.qr_blend(good, None, q.QR_F32, 6, 10, good, good, good, 4, 8, 0, good, None) == q.QR_ERR_ALIGNMENT
     # FP8 without scales
-    assert L.qr_blend(good, None, q.QR_FP8E4M3, 32, 10, good, good, good, 4, 8, good, None) == q.QR_ERR_INVALID_ARG
+    assert L.qr_blend(good, None, q.QR_FP8E4M3, 32, 10, good, good, good, 4, 8, 0, good, None) == q.QR_ERR_INVALID_ARG
     # K out of range
-    assert L.qr_blend(good, None, q.QR_F32, 16, 10, good, good, good, 4, 40, good, None) == q.QR_ERR_INVALID_ARG
+    assert L.qr_blend(good, None, q.QR_F32, 16, 10, good, good, good, 4, 40, 0, good, None) == q.QR_ERR_INVALID_ARG
     # unsupported width
-    assert L.qr_blend(good, None, q.QR_F32, 20, 10, good, good, good, 4, 8, good, None) == q.QR_ERR_NOT_SUPPORTED
+    assert L.qr_blend(good, None, q.QR_F32, 20, 10, good, good, good, 4, 8, 0, good, None) == q.QR_ERR_NOT_SUPPORTED
     # nothing launched by any of these
     assert L.qr_launch_count() == launches
 

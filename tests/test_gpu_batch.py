@@ -52,9 +52,9 @@ def test_batch_matches_single_views(tile):
         torch.testing.assert_close(got["ids"], ref["ids"], rtol=0, atol=0)
         torch.testing.assert_close(got["counts"], ref["counts"], rtol=0, atol=0)
         torch.testing.assert_close(got["weights"], ref["weights"], rtol=0, atol=0)
-        if tile == (16, 16):      # same pixel groups as qr_blend: same summation order
+        if tile == (16, 16):      # same 2x2 pixel groups as qr_blend: same summation order
             torch.testing.assert_close(got["out"], ref["out"], rtol=0, atol=0)
-        else:
+        else:                     # 2x2 groups of 8x32 tiles: another summation order
             torch.testing.assert_close(got["out"], ref["out"], rtol=1e-6, atol=1e-6)
 
 

@@ -2,18 +2,20 @@
 // text embeddings), R[p][q] = sum_c map[p][c] * Q[q][c], on the 5th-generation
 // tensor cores (tcgen05 / UMMA, kind::f16: BF16 x BF16 -> FP32 in TMEM).
 //
-// GB300 design: a persistent CTA of 4 warps per tile of 128 pixels.
+// GB300 design: persistent CTAs of 8 warps (two per SM), one 128-pixel tile at a time.
 //   * the BF16 queries (Q x C, at most 128 x 1024) are staged once per CTA in
 //     shared memory in the K-major 128-byte-swizzled layout UMMA reads;
 //   * the map arrives in FP32 (the blend's output), so each 128 x 64 slice is
-//     read with coalesced 16-byte loads, rounded to BF16 in registers and
-//     written swizzled into one of two shared-memory stages (a TMA copy cannot
-//     change the dtype);
+//     read with coalesced 16-byte streaming loads into registers one slice
+//     ahead (the loads of slice k+1 are in flight while the MMAs of slice k
+//     run), rounded to BF16 and written swizzled into one of two shared-memory
+//     stages (a TMA copy cannot change the dtype);
 //   * one thread issues four 128 x Q x 16 MMAs per slice into a TMEM
 //     accumulator (Q columns), and tcgen05.commit signals an mbarrier when the
 //     stage may be refilled, so loading slice k+1 overlaps the MMAs of slice k;
 //   * the epilogue reads the accumulator with tcgen05.ld (warp w owns TMEM
-//     lanes 32w..32w+31 = pixels) and writes FP32 rows of R.
+//     lanes 32(w%4).. = pixels and half w/4 of the Q columns) and writes FP32
+//     rows of R.
 // The product is memory-bound at Q = 64 (about 51 flops per byte of BF16 map),
 // so the tensor cores' job is to keep the FMA work off the critical path.
 // Every mbarrier wait is bounded; on timeout the CTA records
@@ -27,7 +29,8 @@ namespace {
 
 constexpr int BM = 128;            // pixels per tile (TMEM lanes)
 constexpr int BK = 64;             // channels per slice: 128 bytes of BF16
-constexpr int NT = 128;            // threads
+constexpr int NT = 256;            // threads (8 warps)
+constexpr int PF = BM * 16 / NT;   // float4 of a 128 x 64 FP32 slice per thread
 constexpr int A_STAGE = BM * BK * 2;   // 16 KB
 constexpr unsigned kSpinLimit = 1u << 26;
 
@@ -116,17 +119,28 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Round an FP32 map slice (rows p0.., channels c0..c0+63) to BF16 into a swizzled stage.
-__device__ __forceinline__ void load_a_slice(const float *__restrict__ map, int64_t P, int C,
-                                             int64_t p0, int c0, unsigned char *stage) {
-    // 128 rows x 16 float4 per row; a warp instruction covers two rows (coalesced 256 B each)
-    for (int i = threadIdx.x; i < BM * 16; i += NT) {
+// Issue the loads of an FP32 map slice (rows p0.., channels c0..c0+63) into
+// registers: element i = threadIdx.x + k*NT is row i/16, float4 i%16, so a
+// warp-wide load covers two rows with 256 contiguous bytes each.
+__device__ __forceinline__ void fetch_slice(const float *__restrict__ map, int64_t P, int C,
+                                            int64_t p0, int c0, float4 (&v)[PF]) {
+#pragma unroll
+    for (int k = 0; k < PF; ++k) {
+        const int i = threadIdx.x + k * NT;
+        const int64_t p = p0 + (i >> 4);
+        v[k] = p < P ? __ldcs(reinterpret_cast<const float4 *>(map + p * C + c0 + (i & 15) * 4))
+                     : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
+// Round the fetched slice to BF16 into a 128-byte-swizzled K-major stage.
+__device__ __forceinline__ void store_slice(const float4 (&v)[PF], unsigned char *stage) {
+#pragma unroll
+    for (int k = 0; k < PF; ++k) {
+        const int i = threadIdx.x + k * NT;
         const int r = i >> 4, f4 = i & 15;
-        const int64_t p = p0 + r;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (p < P) v = *reinterpret_cast<const float4 *>(map + p * C + c0 + f4 * 4);
-        const __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y);
-        const __nv_bfloat162 hi = __floats2bfloat162_rn(v.z, v.w);
+        const __nv_bfloat162 lo = __floats2bfloat162_rn(v[k].x, v[k].y);
+        const __nv_bfloat162 hi = __floats2bfloat162_rn(v[k].z, v[k].w);
         uint2 packed;
         packed.x = *reinterpret_cast<const uint32_t *>(&lo);
         packed.y = *reinterpret_cast<const uint32_t *>(&hi);
@@ -135,7 +149,7 @@ __device__ __forceinline__ void load_a_slice(const float *__restrict__ map, int6
 }
 
 template <int QN>
-__global__ void __launch_bounds__(NT, 1)
+__global__ void __launch_bounds__(NT, 2)
 relevance_kernel(const float *__restrict__ map, const uint16_t *__restrict__ queries, int64_t P,
                  int C, float *__restrict__ out, int *__restrict__ status) {
     constexpr uint32_t TMEM_COLS = QN <= 32 ? 32 : QN <= 64 ? 64 : 128;
@@ -174,12 +188,14 @@ relevance_kernel(const float *__restrict__ map, const uint16_t *__restrict__ que
     uint32_t uses[2] = {0u, 0u};      // commits issued per stage
     bool ok = true;
     const int64_t tiles = (P + BM - 1) / BM;
+    float4 regs[PF];
+    if (int64_t(blockIdx.x) < tiles) fetch_slice(map, P, C, int64_t(blockIdx.x) * BM, 0, regs);
     for (int64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
         const int64_t p0 = t * BM;
         for (int s = 0; s < nslices; ++s) {
             const int st = s & 1;
             if (uses[st] > 0 && !cta_wait(&bars[st], (uses[st] - 1) & 1, s_flag)) { ok = false; break; }
-            load_a_slice(map, P, C, p0, s * BK, sA + st * A_STAGE);
+            store_slice(regs, sA + st * A_STAGE);
             fence_async_smem();
             tc_fence_before();
             __syncthreads();
@@ -194,24 +210,32 @@ relevance_kernel(const float *__restrict__ map, const uint16_t *__restrict__ que
                 umma_commit(&bars[st]);
             }
             ++uses[st];
+            // the next slice's loads fly while the tensor cores work on this one
+            if (s + 1 < nslices) fetch_slice(map, P, C, p0, (s + 1) * BK, regs);
+            else if (t + gridDim.x < tiles) fetch_slice(map, P, C, (t + gridDim.x) * BM, 0, regs);
         }
         if (!ok) break;
         // all MMAs of this tile are done once the last commit has landed
         const int last = (nslices - 1) & 1;
         if (!cta_wait(&bars[last], (uses[last] - 1) & 1, s_flag)) { ok = false; break; }
         tc_fence_after();
-        const int64_t p = p0 + warp * 32 + lane;
-        const uint32_t taddr = tmem + (uint32_t(warp * 32) << 16);
+        // warp w reads TMEM lanes 32*(w%4).. (pixels) and half w/4 of the columns
+        const int quarter = warp & 3, half = warp >> 2;
+        constexpr int CW = QN >= 32 ? QN / 2 : QN;
+        if (QN >= 32 || half == 0) {
+            const int64_t p = p0 + quarter * 32 + lane;
+            const uint32_t taddr = tmem + (uint32_t(quarter * 32) << 16);
 #pragma unroll
-        for (int c = 0; c < QN; c += 16) {
-            float v[16];
-            tmem_ld16(taddr + uint32_t(c), v);
-            if (p < P) {
-                float4 *o = reinterpret_cast<float4 *>(out + p * QN + c);
-                o[0] = make_float4(v[0], v[1], v[2], v[3]);
-                o[1] = make_float4(v[4], v[5], v[6], v[7]);
-                o[2] = make_float4(v[8], v[9], v[10], v[11]);
-                o[3] = make_float4(v[12], v[13], v[14], v[15]);
+            for (int c = half * CW; c < half * CW + CW; c += 16) {
+                float v[16];
+                tmem_ld16(taddr + uint32_t(c), v);
+                if (p < P) {
+                    float4 *o = reinterpret_cast<float4 *>(out + p * QN + c);
+                    o[0] = make_float4(v[0], v[1], v[2], v[3]);
+                    o[1] = make_float4(v[4], v[5], v[6], v[7]);
+                    o[2] = make_float4(v[8], v[9], v[10], v[11]);
+                    o[3] = make_float4(v[12], v[13], v[14], v[15]);
+                }
             }
         }
         tc_fence_before();
@@ -239,7 +263,8 @@ cudaError_t run(const float *map, const uint16_t *q, int64_t P, int C, float *ou
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t tiles = (P + BM - 1) / BM;
-    const int grid = int(tiles < sms ? tiles : sms);
+    const int64_t cap = int64_t(sms) * 2;      // two resident CTAs per SM
+    const int grid = int(tiles < cap ? tiles : cap);
     relevance_kernel<QN><<<grid, NT, smem, s>>>(map, q, P, C, out, status);
     count_launch();
     return cudaGetLastError();

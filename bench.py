@@ -184,7 +184,7 @@ def run_gpu(args, ws, rank, local):
         q.qr_project(fr, *gdev)
         q.qr_sort(fr)
         q.qr_select(fr, ids, w, cnt)
-        q.qr_blend(fdev, None, ids, w, cnt, out, width=WIDTH)
+        q.qr_blend(fdev, None, ids, w, cnt, out)
 
     def barrier():
         if ws > 1:
@@ -212,7 +212,7 @@ def run_gpu(args, ws, rank, local):
             e[1].record(stream)
             q.qr_select(fr, ids, w, cnt)
             e[2].record(stream)
-            q.qr_blend(fdev, None, ids, w, cnt, out, width=WIDTH)
+            q.qr_blend(fdev, None, ids, w, cnt, out)
             e[3].record(stream)
         t_end.record(stream)
         barrier()
@@ -281,7 +281,7 @@ def run_gpu(args, ws, rank, local):
             q.qr_project(fr2, *gdev)
             q.qr_sort(fr2)
             q.qr_select(fr2, a[0], a[1], a[2])
-            q.qr_blend(fdev, None, a[0], a[1], a[2], a[3], width=WIDTH)
+            q.qr_blend(fdev, None, a[0], a[1], a[2], a[3])
         for _ in range(2):
             f2()
         torch.cuda.synchronize()
@@ -372,6 +372,82 @@ def run_gpu(args, ws, rank, local):
     }
 
 
+def run_batched(local, steps=3):
+    """Many-view workload: 4 rooms (200k, 500k, 1M, 2M Gaussians), 32 views from
+    320x240 to 1296x968, 512-D BF16 features, K = 8, autotuned tile shape and
+    pixel group, one graph per batch (per-view projection and binning, one
+    persistent select+blend launch, relevance against 64 BF16 queries)."""
+    import torch
+    from paper_2512_20927_gb300 import qrender as q
+    from paper_2512_20927_gb300 import scenes
+    from paper_2512_20927_gb300.batch import Scene, autotune, time_batch
+    dev = torch.device("cuda", local)
+    sc = []
+    for seed, n in enumerate((200_000, 500_000, 1_000_000, 2_000_000)):
+        g, f = scenes.room_scene(seed=seed, n=n, channels=C)
+        gd = tuple(t.to(dev) for t in q.gaussians_to_device(g, device="cpu"))
+        sc.append(Scene(gd, q.qr_quantize_bf16(torch.from_numpy(f).to(dev))))
+        del f
+    views = scenes.batched_views(seed=0, n_views=32, scenes=4)
+    qbits = q.qr_quantize_bf16(torch.from_numpy(scenes.unit_queries(7, 64, C)).to(dev))
+    qbits = qbits.view(torch.int16)
+    best, timings = autotune(sc, views, K=K, queries=qbits, steps=steps)
+    ms = time_batch(best, steps=max(steps, 3))
+    pixels = int(best.offsets[-1])
+    # relevance alone, for its own roofline (BF16 operands read from an FP32 map)
+    r0 = torch.cuda.Event(enable_timing=True)
+    r1 = torch.cuda.Event(enable_timing=True)
+    r0.record()
+    for _ in range(3):
+        best.relevance()
+    r1.record()
+    torch.cuda.synchronize()
+    rel_ms = r0.elapsed_time(r1) / 3
+    rel_bytes = pixels * C * 4 + pixels * 64 * 4
+    rel_flops = 2.0 * pixels * C * 64
+    return {"views": len(views), "pixels": pixels, "ms_per_batch": round(ms, 3),
+            "views_per_s": round(len(views) * 1000.0 / ms, 2),
+            "mpixels_per_s": round(pixels / ms / 1000.0, 1),
+            "autotune_ms": timings, "chosen": {"tile": list(best.tile), "group": best.group},
+            "relevance": {"ms": round(rel_ms, 4), "GB_per_s": round(rel_bytes / rel_ms / 1e6, 1),
+                          "TFLOP_per_s": round(rel_flops / rel_ms / 1e9, 1)}}
+
+
+def run_train_step(local, steps=10):
+    """Differentiation workload: 300k-Gaussian room, 512-D BF16 features,
+    640x480, K = 8; forward + mean (1 - cos) loss against the dense map of a
+    second Gaussian set + backward to features and opacities."""
+    import torch
+    from paper_2512_20927_gb300 import qrender as q
+    from paper_2512_20927_gb300 import scenes
+    dev = torch.device("cuda", local)
+    g, f = scenes.room_scene(seed=0, n=300_000, channels=C)
+    g2, f2 = scenes.room_scene(seed=1, n=300_000, channels=C)
+    cam = scenes.room_camera(WIDTH, HEIGHT)
+    gd = tuple(t.to(dev) for t in q.gaussians_to_device(g, device="cpu"))
+    table = q.qr_quantize_bf16(torch.from_numpy(f).to(dev))
+    g2d = tuple(t.to(dev) for t in q.gaussians_to_device(g2, device="cpu"))
+    tgt = q.render_frame(g2d, torch.from_numpy(f2).to(dev), cam, K=K, dense=True)["dense"]
+
+    def step():
+        res = q.render_frame(gd, table, cam, K=K, max_isect=2_000_000)
+        loss, gmap = q.qr_cosine_loss(res["out"], tgt, res["counts"])
+        gf, ga, _ = q.qr_backward(res["frame"], table, None, res["ids"], res["weights"],
+                                  res["counts"], gmap, want_conic=False)
+        return loss
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        loss = step()
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t0) * 1000.0 / steps
+    return {"ms_per_step": round(ms, 3), "steps_per_s": round(1000.0 / ms, 2),
+            "loss": round(float(loss.item()), 6),
+            "note": "host-timed; includes workspace allocation and the capacity check per step"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -382,6 +458,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true",
                     help="only set up the frame and run the eager steps (for ncu captures)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the many-view and training-step measurements")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws, rank, local = _dist()
@@ -448,6 +526,12 @@ def main():
                   "per_k_fps", "stages_ms", "gpu_launches", "clocks", "e2e", "roofline"):
             line[k] = r[k]
         line["cpu_baseline"] = cpu
+        if not args.no_extras and ws == 1:
+            for key, fn in (("batched", run_batched), ("train_step", run_train_step)):
+                try:
+                    line[key] = fn(local)
+                except Exception as exc:  # noqa: BLE001 - keep the headline line
+                    line[key] = {"error": f"{type(exc).__name__}: {exc}"[:200]}
         print(json.dumps(line))
     if ws > 1:
         import torch.distributed as dist

@@ -28,6 +28,7 @@ struct BatchView {
     const float4 *rec_m;
     const float4 *rec_w;
     const float *rec_a;
+    const float *rec_h;
     const uint32_t *igid;
     const uint2 *ranges;
     const unsigned char *feat;
@@ -105,6 +106,7 @@ batch_kernel(const BatchView *__restrict__ views, int n_views, uint32_t total_it
     __shared__ float4 s_m[T];
     __shared__ float4 s_c[T];
     __shared__ float s_a[T];
+    __shared__ float s_h[T];
     __shared__ uint32_t s_g[T];
     __shared__ uint32_t s_item;
     extern __shared__ unsigned char s_dyn[];
@@ -151,12 +153,14 @@ batch_kernel(const BatchView *__restrict__ views, int n_views, uint32_t total_it
                     s_m[threadIdx.x] = V.rec_m[g];
                     s_c[threadIdx.x] = V.rec_w[g];
                     s_a[threadIdx.x] = V.rec_a[g];
+                    s_h[threadIdx.x] = V.rec_h[g];
                 }
                 __syncthreads();
                 const int nb = int(min(uint32_t(T), range.y - b));
                 if (!done) {
                     for (int j = 0; j < nb; ++j) {
                         const PixelTerm pt = eval_half_q(ux, uy, s_m[j], s_c[j]);
+                        if (pt.half_q > s_h[j]) continue;
                         const float a = eval_alpha(s_a[j], pt.half_q, V.alpha_max);
                         if (a < V.alpha_min) continue;
                         const float Tt = Tr * (1.0f - a);
@@ -353,6 +357,7 @@ cudaError_t prepare_batch(const qr_view *views, int n_views, void *ws, uint32_t 
         b.rec_m = slot<float4>(f, S_REC_M);
         b.rec_w = slot<float4>(f, S_REC_C);
         b.rec_a = slot<float>(f, S_REC_A);
+        b.rec_h = slot<float>(f, S_REC_H);
         b.igid = slot<uint32_t>(f, S_IGID);
         b.ranges = slot<uint2>(f, S_RANGES);
         b.feat = static_cast<const unsigned char *>(views[i].feat);

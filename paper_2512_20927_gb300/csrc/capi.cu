@@ -56,6 +56,7 @@ size_t layout(int64_t n, int W, int H, const qr_params *p, int64_t cap, size_t *
     sizes[S_REC_M] = N * 16;
     sizes[S_REC_C] = N * 16;
     sizes[S_REC_A] = N * 4;
+    sizes[S_REC_H] = N * 4;
     sizes[S_RECT] = N * 8;
     sizes[S_TCOUNT] = N * 4;
     sizes[S_GKEY] = N * 4;

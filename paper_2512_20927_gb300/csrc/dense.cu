@@ -67,7 +67,7 @@ template <> struct Cpv<QR_FP8E4M3> { static constexpr int v = 16; };
 template <int DT, int CC, int PX, int CH>
 __global__ void __launch_bounds__(kThreads)
 dense_kernel(const float4 *__restrict__ rec_m, const float4 *__restrict__ rec_w,
-              const float *__restrict__ rec_a,
+              const float *__restrict__ rec_a, const float *__restrict__ rec_h,
              const uint32_t *__restrict__ isect_gid, const uint2 *__restrict__ ranges,
              const unsigned char *__restrict__ feat, const float *__restrict__ fscale, int C,
              int W, int H, int tile_w, int tiles_x, float alpha_min, float alpha_max,
@@ -78,6 +78,7 @@ dense_kernel(const float4 *__restrict__ rec_m, const float4 *__restrict__ rec_w,
     __shared__ float4 s_m[kBatch];
     __shared__ float4 s_c[kBatch];
     __shared__ float s_a[kBatch];
+    __shared__ float s_h[kBatch];
     __shared__ __align__(16) float s_F[kBatch][CC];
     __shared__ __align__(16) float s_W[kBatch][kThreads];
 
@@ -113,6 +114,7 @@ dense_kernel(const float4 *__restrict__ rec_m, const float4 *__restrict__ rec_w,
             s_m[threadIdx.x] = rec_m[g];
             s_c[threadIdx.x] = rec_w[g];
             s_a[threadIdx.x] = rec_a[g];
+            s_h[threadIdx.x] = rec_h[g];
         }
         constexpr int VPR = CC / CPV;  // 16-byte vectors per row slice
         for (int i = threadIdx.x; i < kBatch * VPR; i += kThreads) {
@@ -138,7 +140,7 @@ dense_kernel(const float4 *__restrict__ rec_m, const float4 *__restrict__ rec_w,
                 const float4 mm = s_m[j];
                 const float4 cc = s_c[j];
                 const PixelTerm pt = eval_half_q(ux, uy, mm, cc);
-                const float a = eval_alpha(s_a[j], pt.half_q, alpha_max);
+                const float a = pt.half_q > s_h[j] ? 0.f : eval_alpha(s_a[j], pt.half_q, alpha_max);
                 if (a >= alpha_min) {
                     const float Tt = T * (1.0f - a);
                     if (T_min > 0.f && Tt < T_min) {
@@ -197,7 +199,7 @@ cudaError_t run(const qr_frame &f, const void *feat, const float *scale, int C, 
                 float *T_final, cudaStream_t s) {
     dim3 grid(unsigned(num_tiles(f)), unsigned(C / CC));
     dense_kernel<DT, CC, PX, CH><<<grid, kThreads, 0, s>>>(
-        slot<float4>(f, S_REC_M), slot<float4>(f, S_REC_C), slot<float>(f, S_REC_A),
+        slot<float4>(f, S_REC_M), slot<float4>(f, S_REC_C), slot<float>(f, S_REC_A), slot<float>(f, S_REC_H),
         slot<uint32_t>(f, S_IGID),
         slot<uint2>(f, S_RANGES), static_cast<const unsigned char *>(feat), scale, C, f.camera.width,
         f.camera.height, f.params.tile_w, f.tiles_x, f.params.alpha_min, f.params.alpha_max,

@@ -41,7 +41,7 @@ project_kernel(int64_t n, const float *__restrict__ mean, const float *__restric
                const float *__restrict__ quat, const float *__restrict__ opacity, CamArgs cam,
                float dilation, float alpha_min, int tile_w, int tile_h, int tiles_x,
                int tiles_y, float4 *__restrict__ rec_m, float4 *__restrict__ rec_w,
-               float *__restrict__ rec_a, uint2 *__restrict__ rect,
+               float *__restrict__ rec_a, float *__restrict__ rec_h, uint2 *__restrict__ rect,
                uint32_t *__restrict__ tcount, uint32_t *__restrict__ dkey,
                uint32_t *__restrict__ vis_count, uint32_t *__restrict__ tile_sum,
                uint32_t *__restrict__ counters) {
@@ -211,6 +211,7 @@ project_kernel(int64_t n, const float *__restrict__ mean, const float *__restric
         rec_m[gi] = make_float4(mxp.hi, myp.hi, mxp.lo, myp.lo);
         rec_w[gi] = waxes;
         rec_a[gi] = alpha;
+        rec_h[gi] = reject_half_q(alpha, alpha_min);
         rect[gi] = make_uint2(uint32_t(tx0) | (uint32_t(ty0) << 16), uint32_t(tx1) | (uint32_t(ty1) << 16));
         const uint32_t nt = uint32_t((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
         tcount[gi] = nt;
@@ -254,7 +255,8 @@ cudaError_t launch_project(const qr_frame &f, const float *mean, const float *lo
     project_kernel<<<blocks, kThreads, 0, s>>>(
         n, mean, log_scale, quat, opacity, cam, f.params.dilation, f.params.alpha_min,
         f.params.tile_w, f.params.tile_h, f.tiles_x, f.tiles_y, slot<float4>(f, S_REC_M),
-        slot<float4>(f, S_REC_C), slot<float>(f, S_REC_A), slot<uint2>(f, S_RECT),
+        slot<float4>(f, S_REC_C), slot<float>(f, S_REC_A), slot<float>(f, S_REC_H),
+        slot<uint2>(f, S_RECT),
         slot<uint32_t>(f, S_TCOUNT), slot<uint32_t>(f, S_GKEY), slot<uint32_t>(f, S_VISCNT),
         slot<uint32_t>(f, S_BSUM), counters);
     count_launch();

@@ -18,7 +18,7 @@ enum { CNT_STATUS = 0, CNT_ISECT = 1, CNT_VISIBLE = 2, CNT_N = 3, CNT_SORT_N = 4
 
 // Workspace slots (byte offsets in qr_frame::off).
 enum Slot {
-    S_COUNTERS = 0, S_REC_M, S_REC_C, S_REC_A, S_RECT, S_TCOUNT, S_GKEY,
+    S_COUNTERS = 0, S_REC_M, S_REC_C, S_REC_A, S_REC_H, S_RECT, S_TCOUNT, S_GKEY,
     S_VISCNT, S_BSUM, S_KID, S_OFF, S_TCNT, S_RANGES, S_KEYS64, S_SCRATCH64, S_IGID, S_DIFF,
     S_END
 };
@@ -158,6 +158,13 @@ __device__ __forceinline__ PixelTerm eval_half_q(float ux, float uy, float4 m, f
 }
 __device__ __forceinline__ float eval_alpha(float alpha, float half_q, float alpha_max) {
     return fminf(alpha_max, alpha * __expf(-half_q));
+}
+// A pixel whose q/2 exceeds this bound cannot reach alpha' >= alpha_min:
+// alpha exp(-q/2) < alpha_min exactly when q/2 > ln(alpha / alpha_min); the 1 %
+// + 0.01 margin is far above the FP32 error of q/2 and of the exponential, so
+// skipping these pixels before the exponential changes no decision.
+__device__ __forceinline__ float reject_half_q(float alpha, float alpha_min) {
+    return fmaf(logf(fmaxf(alpha / alpha_min, 1.0f)), 1.01f, 0.01f);
 }
 
 // ---------------------------------------------------------------- compensated arithmetic

@@ -29,13 +29,14 @@ constexpr int kThreads = 256;
 
 __global__ void __launch_bounds__(kThreads)
 select_kernel(const float4 *__restrict__ rec_m, const float4 *__restrict__ rec_w,
-              const float *__restrict__ rec_a,
+              const float *__restrict__ rec_a, const float *__restrict__ rec_h,
               const uint32_t *__restrict__ isect_gid, const uint2 *__restrict__ ranges, int W,
               int H, int tile_w, int tiles_x, int K, float alpha_min, float alpha_max,
               int32_t *__restrict__ ids, float *__restrict__ wout, uint8_t *__restrict__ cnt) {
     __shared__ float4 s_m[kThreads];
     __shared__ float4 s_c[kThreads];
     __shared__ float s_a[kThreads];
+    __shared__ float s_h[kThreads];
     __shared__ uint32_t s_g[kThreads];
     extern __shared__ unsigned char s_dyn[];
     int32_t *s_ids = reinterpret_cast<int32_t *>(s_dyn);              // [K][256]
@@ -65,6 +66,7 @@ select_kernel(const float4 *__restrict__ rec_m, const float4 *__restrict__ rec_w
             s_m[threadIdx.x] = rec_m[g];
             s_c[threadIdx.x] = rec_w[g];
             s_a[threadIdx.x] = rec_a[g];
+            s_h[threadIdx.x] = rec_h[g];
         }
         __syncthreads();
         const int nb = int(min(uint32_t(kThreads), range.y - b));
@@ -73,6 +75,7 @@ select_kernel(const float4 *__restrict__ rec_m, const float4 *__restrict__ rec_w
                 const float4 mm = s_m[j];
                 const float4 cc = s_c[j];
                 const PixelTerm pt = eval_half_q(ux, uy, mm, cc);
+                if (pt.half_q > s_h[j]) continue;          // alpha' < alpha_min for certain
                 const float a = eval_alpha(s_a[j], pt.half_q, alpha_max);
                 if (a < alpha_min) continue;
                 const float Tt = T * (1.0f - a);
@@ -119,7 +122,7 @@ cudaError_t launch_select(const qr_frame &f, int32_t *ids, float *w, uint8_t *cn
         if (e != cudaSuccess) return e;
     }
     select_kernel<<<tiles, kThreads, dyn, s>>>(
-        slot<float4>(f, S_REC_M), slot<float4>(f, S_REC_C), slot<float>(f, S_REC_A),
+        slot<float4>(f, S_REC_M), slot<float4>(f, S_REC_C), slot<float>(f, S_REC_A), slot<float>(f, S_REC_H),
         slot<uint32_t>(f, S_IGID),
         slot<uint2>(f, S_RANGES), f.camera.width, f.camera.height, f.params.tile_w, f.tiles_x, K,
         f.params.alpha_min, f.params.alpha_max, ids, w, cnt);

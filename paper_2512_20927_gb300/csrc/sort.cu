@@ -15,9 +15,9 @@
 //      array of per-tile counts (4 atomics instead of one per intersection);
 //   3. tile_scan integrates the difference array into per-tile counts and
 //      exclusive offsets, i.e. the tile ranges;
-//   4. expand_scatter: a load-balanced expansion -- each CTA owns 2048
+//   4. expand_scatter: a load-balanced expansion -- each CTA owns 1024
 //      consecutive output slots, finds their owners with a warp-wide 32-way
-//      search (at most 2048 owners per chunk), derives each slot's tile from
+//      search (at most 1024 owners per chunk), derives each slot's tile from
 //      the owner's footprint rectangle, and writes (depth << 32 | id) into
 //      its tile's bucket at an atomically claimed position;
 //   5. tile_sort: one CTA per tile sorts its bucket in shared memory (bitonic
@@ -33,7 +33,7 @@ namespace qr {
 namespace {
 
 constexpr int T = 256;
-constexpr int EMIT_CHUNK = 2048;
+constexpr int EMIT_CHUNK = 1024;
 constexpr int TS_CAP = 8192;             // keys a tile sorts in shared memory (64 KB)
 
 // ------------------------------------------------------------------ offsets
@@ -349,7 +349,7 @@ cudaError_t launch_sort(const qr_frame &f, cudaStream_t s) {
                                                    rect, f.tiles_x, diff, kid, koff);
     tile_scan<<<1, 1024, 0, s>>>(diff, counters, tcnt, f.tiles_x, f.tiles_y, ranges);
     auto *keys = slot<unsigned long long>(f, S_KEYS64);
-    expand_scatter<<<sms * 2, T, 0, s>>>(koff, kid, rect, slot<uint32_t>(f, S_GKEY), counters,
+    expand_scatter<<<sms * 6, T, 0, s>>>(koff, kid, rect, slot<uint32_t>(f, S_GKEY), counters,
                                          f.tiles_x, ranges, tcnt, keys);
     tile_sort<<<tiles, T, TS_CAP * sizeof(unsigned long long), s>>>(
         ranges, keys, slot<unsigned long long>(f, S_SCRATCH64), slot<uint32_t>(f, S_IGID));

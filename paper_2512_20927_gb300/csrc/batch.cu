@@ -12,9 +12,11 @@
 //      qr_select; the kept ids and normalised weights stay in shared memory
 //      (and are also written out for a backward pass);
 //   2. blend (warp per 2x2 / 2x1 pixel group, like qr_blend): equal ids of the
-//      group are merged with __match_any_sync, each distinct feature row is
-//      read once with 16-byte loads and accumulated into every pixel of the
-//      group, and the rows of the map are written with streaming stores.
+//      group are merged with __match_any_sync, the group's weights of each
+//      distinct row are gathered into a per-warp shared-memory table, each
+//      distinct feature row is read once with 16-byte loads and accumulated
+//      into every pixel of the group, and the rows of the map are written
+//      with streaming stores.
 // Per-view descriptors live in device memory (qr_batch_prepare), the counter
 // is cleared by a memset on the stream, so the launch can sit in a CUDA graph.
 #include <cuda_bf16.h>
@@ -109,6 +111,8 @@ batch_kernel(const BatchView *__restrict__ views, int n_views, uint32_t total_it
     __shared__ float s_h[T];
     __shared__ uint32_t s_g[T];
     __shared__ uint32_t s_item;
+    __shared__ __align__(16) float s_tw[T / 32][32][G];   // per-warp row-weight table
+    __shared__ int s_tid[T / 32][32];
     extern __shared__ unsigned char s_dyn[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
@@ -196,8 +200,7 @@ batch_kernel(const BatchView *__restrict__ views, int n_views, uint32_t total_it
         __syncthreads();
 
         // ---------------- 2. blend (warp per pixel group, rows shared in registers)
-        const unsigned kmask = (K >= 32) ? FULL : ((1u << K) - 1u);
-        const int half_w = tile_w / 2;
+                const int half_w = tile_w / 2;
         for (int gi = warp; gi < T / G; gi += T / 32) {
             const int mm = lane / K, j = lane - mm * K;
             int lx, ly;
@@ -216,7 +219,20 @@ batch_kernel(const BatchView *__restrict__ views, int n_views, uint32_t total_it
                 if (id >= 0 && DT == QR_FP8E4M3) w *= V.fscale[id];
             }
             const unsigned peers = __match_any_sync(FULL, id);
-            unsigned leaders = __ballot_sync(FULL, id >= 0 && lane == __ffs(peers) - 1);
+            const int leader = __ffs(peers) - 1;
+            const unsigned leaders = __ballot_sync(FULL, id >= 0 && lane == leader);
+            const int nrows = __popc(leaders);
+            // the G weights of each distinct row, gathered once (a pixel that
+            // lists an id twice gets the sum)
+#pragma unroll
+            for (int g = 0; g < G; ++g) s_tw[warp][lane][g] = 0.f;
+            __syncwarp();
+            if (id >= 0) {
+                const int slot = __popc(leaders & ((1u << leader) - 1u));
+                atomicAdd(&s_tw[warp][slot][mm], w);
+                if (lane == leader) s_tid[warp][slot] = id;
+            }
+            __syncwarp();
             float acc[G][VPL][CPV];
 #pragma unroll
             for (int g = 0; g < G; ++g)
@@ -225,42 +241,29 @@ batch_kernel(const BatchView *__restrict__ views, int n_views, uint32_t total_it
 #pragma unroll
                     for (int q = 0; q < CPV; ++q) acc[g][vv][q] = 0.f;
             const uint4 *feat = reinterpret_cast<const uint4 *>(V.feat);
-            while (leaders) {
-                int L[2];
-                L[0] = __ffs(leaders) - 1;
-                leaders &= leaders - 1;
-                L[1] = leaders ? __ffs(leaders) - 1 : -1;
-                if (L[1] >= 0) leaders &= leaders - 1;
+            for (int r0 = 0; r0 < nrows; r0 += 2) {
                 uint4 r[2][VPL];
-                float wg[2][G];
 #pragma unroll
                 for (int u = 0; u < 2; ++u) {
-                    const int src = L[u] >= 0 ? L[u] : 0;
-                    const int rid = __shfl_sync(FULL, id, src);
-                    const unsigned pe = __shfl_sync(FULL, peers, src);
-#pragma unroll
-                    for (int g = 0; g < G; ++g) {
-                        unsigned bb = (L[u] >= 0) ? (pe & (kmask << (g * K))) : 0u;
-                        float x = 0.f;
-                        while (bb) {
-                            x += __shfl_sync(FULL, w, __ffs(bb) - 1);
-                            bb &= bb - 1;
-                        }
-                        wg[u][g] = x;
-                    }
-                    const uint4 *row = feat + int64_t(rid < 0 ? 0 : rid) * ROWV + lane;
+                    const bool ok = r0 + u < nrows;
+                    const uint4 *row = feat + int64_t(ok ? s_tid[warp][r0 + u] : 0) * ROWV + lane;
 #pragma unroll
                     for (int vv = 0; vv < VPL; ++vv)
-                        r[u][vv] = (L[u] >= 0) ? ldg_nc(row + 32 * vv) : make_uint4(0, 0, 0, 0);
+                        r[u][vv] = ok ? ldg_nc(row + 32 * vv) : make_uint4(0, 0, 0, 0);
                 }
 #pragma unroll
-                for (int u = 0; u < 2; ++u)
+                for (int u = 0; u < 2; ++u) {
+                    if (r0 + u >= nrows) break;
+                    float wg[G];
+#pragma unroll
+                    for (int g = 0; g < G; ++g) wg[g] = s_tw[warp][r0 + u][g];
 #pragma unroll
                     for (int g = 0; g < G; ++g)
-                        if (wg[u][g] != 0.f) {
+                        if (wg[g] != 0.f) {
 #pragma unroll
-                            for (int vv = 0; vv < VPL; ++vv) dec_fma<DT>(r[u][vv], wg[u][g], acc[g][vv]);
+                            for (int vv = 0; vv < VPL; ++vv) dec_fma<DT>(r[u][vv], wg[g], acc[g][vv]);
                         }
+                }
             }
 #pragma unroll
             for (int g = 0; g < G; ++g) {
@@ -276,6 +279,7 @@ batch_kernel(const BatchView *__restrict__ views, int n_views, uint32_t total_it
                                               acc[g][vv][4 * q + 2], acc[g][vv][4 * q + 3]));
                 }
             }
+            __syncwarp();   // the table is rewritten by the next group
         }
         __syncthreads();
     }

@@ -171,10 +171,10 @@ blend_kernel(const uint4 *__restrict__ feat, const float *__restrict__ scale, in
 // Wide rows (one warp per row): a warp owns a group of G neighbouring pixels
 // (2x2 for G = 4, 2x1 for G = 2) whose selections are subsequences of the same
 // tile list and mostly share rows.  Lane g*K + j holds entry j of pixel g;
-// __match_any_sync groups equal ids, the lowest lane of each group leads, and
-// each distinct row is loaded once and accumulated into every pixel of the
-// group with that pixel's weight (zero weights are skipped).  L1 row traffic
-// drops from sum(counts) to the number of distinct rows of the group.
+// __match_any_sync groups equal ids and each distinct row is loaded once and
+// accumulated into every pixel of the group with that pixel's weight (zero
+// weights are skipped).  L1 row traffic drops from sum(counts) to the number
+// of distinct rows of the group.
 template <int G>
 __device__ __forceinline__ int64_t group_pixel(int64_t chunk0, int gi, int m, int W, int H,
                                                int64_t items) {
@@ -192,82 +192,87 @@ __device__ __forceinline__ int64_t group_pixel(int64_t chunk0, int gi, int m, in
     return tile_order_pixel(item, W, H);
 }
 
-template <int DT, int VPL, int G, int S>
+// The G weights of each distinct row are gathered once into a shared-memory
+// table (slot = rank of the row's leader lane, one float per pixel; a pixel
+// that lists an id twice gets the sum), so the row loop reads them with one
+// broadcast load instead of a chain of shuffles.
+template <int DT, int VPL, int G>
 __global__ void __launch_bounds__(kThreads)
 blend_group_kernel(const uint4 *__restrict__ feat, const float *__restrict__ scale,
                    int64_t n_gauss, const int32_t *__restrict__ ids,
                    const float *__restrict__ wts, const uint8_t *__restrict__ cnt, int64_t P,
                    int K, int W, int H, float4 *__restrict__ out) {
-    // S warps share a pixel group, each owning VPL/S of the row's vectors
     constexpr int CPV = Vec<DT>::C;
     constexpr int ROWV = 32 * VPL;
-    constexpr int VW = VPL / S;                     // vectors per lane in this warp
     constexpr unsigned FULL = 0xffffffffu;
+    constexpr int NW = kThreads / 32;
+    __shared__ __align__(16) float s_w[NW][32][G];
+    __shared__ int s_id[NW][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t items = (W > 0) ? int64_t((W + 15) >> 4) * ((H + 15) >> 4) * 256 : P;
     const int64_t chunk0 = int64_t(blockIdx.x) * 256;
-    const unsigned kmask = (K >= 32) ? FULL : ((1u << K) - 1u);
-    for (int wi = warp; wi < (256 / G) * S; wi += kThreads / 32) {
-        const int gi = wi / S, part = wi % S;
-        const int vbase = part * VW;                // first vector index (in units of 32 lanes)
-        const int m = lane / K, j = lane - m * K;
-        int64_t p = -1;
-        if (m < G) p = (W > 0) ? group_pixel<G>(chunk0, gi, m, W, H, items)
-                               : (chunk0 + gi * G + m < items ? chunk0 + gi * G + m : -1);
-        int id = -1;
-        float w = 0.f;
+    const int m = lane / K, j = lane - m * K;
+    auto entry = [&](int wi, int64_t &p, int &id, float &w) {
+        p = -1;
+        if (m < G) p = (W > 0) ? group_pixel<G>(chunk0, wi, m, W, H, items)
+                               : (chunk0 + wi * G + m < items ? chunk0 + wi * G + m : -1);
+        id = -1;
+        w = 0.f;
         if (p >= 0 && j < int(cnt[p])) {
             id = ids[p * K + j];
             w = wts[p * K + j];
             if (uint64_t(int64_t(id)) >= uint64_t(n_gauss)) { id = -1; w = 0.f; }
             else if (DT == QR_FP8E4M3) w *= scale[id];
         }
+    };
+    int64_t p;
+    int id;
+    float w;
+    entry(warp, p, id, w);
+    for (int wi = warp; wi < 256 / G; wi += NW) {
         const unsigned peers = __match_any_sync(FULL, id);
-        unsigned leaders = __ballot_sync(FULL, id >= 0 && lane == __ffs(peers) - 1);
-        float acc[G][VW][CPV];
+        const int leader = __ffs(peers) - 1;
+        const unsigned leaders = __ballot_sync(FULL, id >= 0 && lane == leader);
+        const int nrows = __popc(leaders);
+#pragma unroll
+        for (int g = 0; g < G; ++g) s_w[warp][lane][g] = 0.f;
+        __syncwarp();
+        if (id >= 0) {
+            const int slot = __popc(leaders & ((1u << leader) - 1u));
+            atomicAdd(&s_w[warp][slot][m], w);   // m < G for every listed entry
+            if (lane == leader) s_id[warp][slot] = id;
+        }
+        __syncwarp();
+        float acc[G][VPL][CPV];
 #pragma unroll
         for (int g = 0; g < G; ++g)
 #pragma unroll
-            for (int v = 0; v < VW; ++v)
+            for (int v = 0; v < VPL; ++v)
 #pragma unroll
                 for (int q = 0; q < CPV; ++q) acc[g][v][q] = 0.f;
-        while (leaders) {
-            int L[2];
-            L[0] = __ffs(leaders) - 1;
-            leaders &= leaders - 1;
-            L[1] = leaders ? __ffs(leaders) - 1 : -1;
-            if (L[1] >= 0) leaders &= leaders - 1;
-            uint4 r[2][VW];
-            float wg[2][G];
+        for (int r0 = 0; r0 < nrows; r0 += 2) {
+            uint4 r[2][VPL];
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
-                const int src = L[u] >= 0 ? L[u] : 0;
-                const int rid = __shfl_sync(FULL, id, src);
-                const unsigned pe = __shfl_sync(FULL, peers, src);
+                const bool ok = r0 + u < nrows;
+                const uint4 *row = feat + int64_t(ok ? s_id[warp][r0 + u] : 0) * ROWV + lane;
 #pragma unroll
-                for (int g = 0; g < G; ++g) {
-                    // pixel g's weight for this row (summed if the pixel lists the id twice)
-                    unsigned b = (L[u] >= 0) ? (pe & (kmask << (g * K))) : 0u;
-                    float x = 0.f;
-                    while (b) {
-                        x += __shfl_sync(FULL, w, __ffs(b) - 1);
-                        b &= b - 1;
-                    }
-                    wg[u][g] = x;
-                }
-                const uint4 *row = feat + int64_t(rid) * ROWV + 32 * vbase + lane;
-#pragma unroll
-                for (int v = 0; v < VW; ++v)
-                    r[u][v] = (L[u] >= 0) ? ld_row(row + 32 * v) : make_uint4(0, 0, 0, 0);
+                for (int v = 0; v < VPL; ++v)
+                    r[u][v] = ok ? ld_row(row + 32 * v) : make_uint4(0, 0, 0, 0);
             }
 #pragma unroll
-            for (int u = 0; u < 2; ++u)
+            for (int u = 0; u < 2; ++u) {
+                if (r0 + u >= nrows) break;
+                float wg[G];
+#pragma unroll
+                for (int g = 0; g < G; ++g) wg[g] = s_w[warp][r0 + u][g];
 #pragma unroll
                 for (int g = 0; g < G; ++g)
-                    if (wg[u][g] != 0.f) {
+                    if (wg[g] != 0.f) {
 #pragma unroll
-                        for (int v = 0; v < VW; ++v) decode_fma<DT>(r[u][v], wg[u][g], acc[g][v]);
+                        for (int v = 0; v < VPL; ++v) decode_fma<DT>(r[u][v], wg[g], acc[g][v]);
                     }
+            }
         }
 #pragma unroll
         for (int g = 0; g < G; ++g) {
@@ -275,14 +280,16 @@ blend_group_kernel(const uint4 *__restrict__ feat, const float *__restrict__ sca
             if (pg >= 0) {
                 float4 *o = out + pg * (int64_t(ROWV) * CPV / 4);
 #pragma unroll
-                for (int v = 0; v < VW; ++v)
+                for (int v = 0; v < VPL; ++v)
 #pragma unroll
                     for (int q = 0; q < CPV / 4; ++q)
-                        st_stream(o + int64_t(lane + 32 * (vbase + v)) * (CPV / 4) + q,
+                        st_stream(o + int64_t(lane + 32 * v) * (CPV / 4) + q,
                                   make_float4(acc[g][v][4 * q], acc[g][v][4 * q + 1],
                                               acc[g][v][4 * q + 2], acc[g][v][4 * q + 3]));
             }
         }
+        __syncwarp();   // the table is rewritten by the next group
+        if (wi + NW < 256 / G) entry(wi + NW, p, id, w);
     }
 }
 
@@ -294,13 +301,12 @@ cudaError_t run_group(const void *feat, const float *scale, int64_t n_gauss, con
     const unsigned blocks = unsigned((items + 255) / 256);
     const uint4 *f = static_cast<const uint4 *>(feat);
     float4 *o = reinterpret_cast<float4 *>(out);
-    constexpr int S = 1;   // one warp owns the whole row of its pixel group (measured faster than 2)
     if (K <= 8)
-        blend_group_kernel<DT, VPL, 4, S><<<blocks, kThreads, 0, s>>>(f, scale, n_gauss, ids, w, cnt, P, K, W, H, o);
+        blend_group_kernel<DT, VPL, 4><<<blocks, kThreads, 0, s>>>(f, scale, n_gauss, ids, w, cnt, P, K, W, H, o);
     else if (K <= 16)
-        blend_group_kernel<DT, VPL, 2, S><<<blocks, kThreads, 0, s>>>(f, scale, n_gauss, ids, w, cnt, P, K, W, H, o);
+        blend_group_kernel<DT, VPL, 2><<<blocks, kThreads, 0, s>>>(f, scale, n_gauss, ids, w, cnt, P, K, W, H, o);
     else
-        blend_group_kernel<DT, VPL, 1, S><<<blocks, kThreads, 0, s>>>(f, scale, n_gauss, ids, w, cnt, P, K, W, H, o);
+        blend_group_kernel<DT, VPL, 1><<<blocks, kThreads, 0, s>>>(f, scale, n_gauss, ids, w, cnt, P, K, W, H, o);
     count_launch();
     return cudaGetLastError();
 }

@@ -9,14 +9,19 @@
 // tiles its support
 // {u : alpha exp(-q(u)/2) >= alpha_min}, q = (u-mu')^T A (u-mu'), can reach.
 //
-// GB300 design: one thread per Gaussian in two stages.  Stage A is a cheap
-// FP32 bound on the footprint that rejects Gaussians that cannot reach the
-// screen; survivors are compacted inside the CTA through shared memory so
-// that stage B -- the exact projection in compensated double-FP32 arithmetic
-// (about 600 FP32 instructions) -- runs on full warps.  Stage B is what makes
-// the per-pixel alpha' agree with an FP64 evaluation to ~1e-6 relative: the
-// projected mean is kept as an unevaluated pair hi + lo, so the pixel offset
-// u - mu' loses nothing even 1000 px from the origin.
+// GB300 design: two kernels.  project_cull (one thread per Gaussian) applies
+// a cheap FP32 bound on the footprint, marks Gaussians that cannot reach the
+// screen as culled and appends the survivors to a device-wide candidate list
+// (one atomic per CTA; a tenth of an indoor scene survives).
+// project_exact (a grid of full CTAs striding over that list) runs the exact
+// projection -- compensated double-FP32 arithmetic, about 600 FP32
+// instructions -- on full warps whatever the survival rate.  Stage B is what
+// makes the per-pixel alpha' agree with an FP64 evaluation to ~1e-6
+// relative: the projected mean is kept as an unevaluated pair hi + lo, so the
+// pixel offset u - mu' loses nothing even 1000 px from the origin.  Every
+// output is indexed by Gaussian id, and the per-256-id kept counts and tile
+// sums the binning scans are integer atomics, so the result does not depend
+// on the order of the candidate list.
 #include "qr_internal.cuh"
 
 namespace qr {
@@ -36,27 +41,17 @@ __device__ __forceinline__ void write_culled(int64_t g, uint32_t *dkey, uint32_t
     rect[g] = make_uint2(0u, 0u);
 }
 
+// Stage A: conservative FP32 footprint bound; survivors go to the candidate list.
 __global__ void __launch_bounds__(kThreads)
-project_kernel(int64_t n, const float *__restrict__ mean, const float *__restrict__ log_scale,
-               const float *__restrict__ quat, const float *__restrict__ opacity, CamArgs cam,
-               float dilation, float alpha_min, int tile_w, int tile_h, int tiles_x,
-               int tiles_y, float4 *__restrict__ rec_m, float4 *__restrict__ rec_w,
-               float *__restrict__ rec_a, float *__restrict__ rec_h, uint2 *__restrict__ rect,
-               uint32_t *__restrict__ tcount, uint32_t *__restrict__ dkey,
-               uint32_t *__restrict__ vis_count, uint32_t *__restrict__ tile_sum,
-               uint32_t *__restrict__ counters) {
-    __shared__ int s_list[kThreads];
-    __shared__ int s_warp[kThreads / 32];
-    __shared__ int s_visible;
-    __shared__ uint32_t s_tiles;
-
-    const int64_t base = int64_t(blockIdx.x) * kThreads;
-    const int64_t g = base + threadIdx.x;
-    if (threadIdx.x == 0) { s_visible = 0; s_tiles = 0u; }
+project_cull(int64_t n, const float *__restrict__ mean, const float *__restrict__ log_scale,
+             const float *__restrict__ opacity, CamArgs cam, float dilation, float alpha_min,
+             uint2 *__restrict__ rect, uint32_t *__restrict__ tcount,
+             uint32_t *__restrict__ dkey, uint32_t *__restrict__ cand,
+             uint32_t *__restrict__ counters) {
+    const int64_t g = int64_t(blockIdx.x) * kThreads + threadIdx.x;
     if (blockIdx.x == 0 && threadIdx.x == 0) counters[CNT_N] = uint32_t(n);
-
     // ---------------- stage A: FP32 conservative footprint bound
-    bool cand = false;
+    bool pass = false;
     if (g < n) {
         const float mx = mean[3 * g], my = mean[3 * g + 1], mz = mean[3 * g + 2];
         const float alpha = opacity[g];
@@ -75,31 +70,49 @@ project_kernel(int64_t n, const float *__restrict__ mean, const float *__restric
             const float ey = sqrtf(r2 * (smax * smax * jy * jy * (1.f + v * v) + dilation)) * 1.01f + 2.f;
             const float px = fmaf(cam.fx, u, cam.cx), py = fmaf(cam.fy, v, cam.cy);
             const float tol = 1e-3f * (fabsf(px) + fabsf(py)) + 2.f;
-            cand = (px + ex + tol >= 0.f) && (px - ex - tol <= float(cam.W)) &&
+            pass = (px + ex + tol >= 0.f) && (px - ex - tol <= float(cam.W)) &&
                    (py + ey + tol >= 0.f) && (py - ey - tol <= float(cam.H));
         }
-        if (!cand) write_culled(g, dkey, tcount, rect);
+        if (!pass) write_culled(g, dkey, tcount, rect);
     }
 
-    // ---------------- compact the survivors of this CTA
-    const unsigned ballot = __ballot_sync(0xffffffffu, cand);
+    // one atomic per CTA: warp counts -> CTA offset -> list positions
+    __shared__ uint32_t s_cnt[kThreads / 32];
+    __shared__ uint32_t s_base;
+    const unsigned ballot = __ballot_sync(0xffffffffu, pass);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) s_warp[warp] = __popc(ballot);
+    if (lane == 0) s_cnt[warp] = uint32_t(__popc(ballot));
     __syncthreads();
-    int before = 0, total = 0;
+    if (threadIdx.x == 0) {
+        uint32_t tot = 0;
 #pragma unroll
-    for (int w = 0; w < kThreads / 32; ++w) {
-        before += (w < warp) ? s_warp[w] : 0;
-        total += s_warp[w];
+        for (int w = 0; w < kThreads / 32; ++w) tot += s_cnt[w];
+        s_base = tot ? atomicAdd(&counters[CNT_CAND], tot) : 0u;
     }
-    if (cand) s_list[before + __popc(ballot & ((1u << lane) - 1u))] = threadIdx.x;
     __syncthreads();
+    if (pass) {
+        uint32_t pos = s_base + uint32_t(__popc(ballot & ((1u << lane) - 1u)));
+        for (int w = 0; w < warp; ++w) pos += s_cnt[w];
+        cand[pos] = uint32_t(g);
+    }
+}
 
-    // ---------------- stage B: exact projection of the survivors
-    int visible = 0;
-    uint32_t tiles_touched = 0;
-    for (int i = threadIdx.x; i < total; i += kThreads) {
-        const int64_t gi = base + s_list[i];
+// Stage B: exact projection of the candidates.
+__global__ void __launch_bounds__(kThreads)
+project_exact(const float *__restrict__ mean, const float *__restrict__ log_scale,
+              const float *__restrict__ quat, const float *__restrict__ opacity, CamArgs cam,
+              float dilation, float alpha_min, int tile_w, int tile_h,
+              const uint32_t *__restrict__ cand, float4 *__restrict__ rec_m,
+              float4 *__restrict__ rec_w, float *__restrict__ rec_a, float *__restrict__ rec_h,
+              uint2 *__restrict__ rect, uint32_t *__restrict__ tcount,
+              uint32_t *__restrict__ dkey, uint32_t *__restrict__ vis_count,
+              uint32_t *__restrict__ tile_sum, int tiles_x, int tiles_y, int *__restrict__ diff,
+              const uint32_t *__restrict__ counters) {
+    const uint32_t ncand = counters[CNT_CAND];
+    // this CTA's copy of the difference array of per-tile counts
+    int *dcopy = diff + size_t(blockIdx.x % kDiffCopies) * size_t(tiles_x + 1) * size_t(tiles_y + 1);
+    for (uint32_t i = blockIdx.x * kThreads + threadIdx.x; i < ncand; i += gridDim.x * kThreads) {
+        const int64_t gi = int64_t(cand[i]);
         const float mx = mean[3 * gi], my = mean[3 * gi + 1], mz = mean[3 * gi + 2];
         const float alpha = opacity[gi];
         // c = R mu + t
@@ -216,25 +229,17 @@ project_kernel(int64_t n, const float *__restrict__ mean, const float *__restric
         const uint32_t nt = uint32_t((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
         tcount[gi] = nt;
         dkey[gi] = __float_as_uint(c[2].hi);
-        ++visible;
-        tiles_touched += nt;
+        // per-256-id counts of kept Gaussians and of their tiles (scanned by the
+        // binning), and the footprint rectangle in the difference array of
+        // per-tile counts: +1 at (x0,y0) and (x1+1,y1+1), -1 at (x1+1,y0) and (x0,y1+1)
+        atomicAdd(&vis_count[gi / kThreads], 1u);
+        atomicAdd(&tile_sum[gi / kThreads], nt);
+        const int stride = tiles_x + 1;
+        atomicAdd(&dcopy[ty0 * stride + tx0], 1);
+        atomicAdd(&dcopy[ty0 * stride + tx1 + 1], -1);
+        atomicAdd(&dcopy[(ty1 + 1) * stride + tx0], -1);
+        atomicAdd(&dcopy[(ty1 + 1) * stride + tx1 + 1], 1);
     }
-    // per-CTA count of kept Gaussians and of their tiles (scanned by the binning)
-    for (int o = 16; o > 0; o >>= 1) {
-        visible += __shfl_xor_sync(0xffffffffu, visible, o);
-        tiles_touched += __shfl_xor_sync(0xffffffffu, tiles_touched, o);
-    }
-    if (lane == 0 && visible) {
-        atomicAdd(&s_visible, visible);
-        atomicAdd(&s_tiles, tiles_touched);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        vis_count[blockIdx.x] = uint32_t(s_visible);
-        tile_sum[blockIdx.x] = s_tiles;
-    }
-    (void)tiles_x;
-    (void)tiles_y;
 }
 
 }  // namespace
@@ -252,14 +257,29 @@ cudaError_t launch_project(const qr_frame &f, const float *mean, const float *lo
     cam.fx = f.camera.fx; cam.fy = f.camera.fy; cam.cx = f.camera.cx; cam.cy = f.camera.cy;
     cam.znear = f.camera.near_plane; cam.W = f.camera.width; cam.H = f.camera.height;
     const unsigned blocks = unsigned((n + kThreads - 1) / kThreads);
-    project_kernel<<<blocks, kThreads, 0, s>>>(
-        n, mean, log_scale, quat, opacity, cam, f.params.dilation, f.params.alpha_min,
-        f.params.tile_w, f.params.tile_h, f.tiles_x, f.tiles_y, slot<float4>(f, S_REC_M),
-        slot<float4>(f, S_REC_C), slot<float>(f, S_REC_A), slot<float>(f, S_REC_H),
-        slot<uint2>(f, S_RECT),
-        slot<uint32_t>(f, S_TCOUNT), slot<uint32_t>(f, S_GKEY), slot<uint32_t>(f, S_VISCNT),
-        slot<uint32_t>(f, S_BSUM), counters);
-    count_launch();
+    uint32_t *vis = slot<uint32_t>(f, S_VISCNT), *tsum = slot<uint32_t>(f, S_BSUM);
+    int *diff = slot<int>(f, S_DIFF);
+    e = cudaMemsetAsync(vis, 0, sizeof(uint32_t) * blocks, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(tsum, 0, sizeof(uint32_t) * blocks, s);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(diff, 0, sizeof(int) * size_t(f.tiles_x + 1) * size_t(f.tiles_y + 1) * kDiffCopies, s);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // the candidate list lives in the kept-id slot, which the binning fills later
+    uint32_t *cand = slot<uint32_t>(f, S_KID);
+    uint2 *rect = slot<uint2>(f, S_RECT);
+    uint32_t *tcount = slot<uint32_t>(f, S_TCOUNT), *dkey = slot<uint32_t>(f, S_GKEY);
+    project_cull<<<blocks, kThreads, 0, s>>>(n, mean, log_scale, opacity, cam, f.params.dilation,
+                                             f.params.alpha_min, rect, tcount, dkey, cand, counters);
+    const unsigned grid = blocks < unsigned(sms) * 4u ? blocks : unsigned(sms) * 4u;
+    project_exact<<<grid, kThreads, 0, s>>>(
+        mean, log_scale, quat, opacity, cam, f.params.dilation, f.params.alpha_min,
+        f.params.tile_w, f.params.tile_h, cand, slot<float4>(f, S_REC_M), slot<float4>(f, S_REC_C),
+        slot<float>(f, S_REC_A), slot<float>(f, S_REC_H), rect, tcount, dkey, vis, tsum, f.tiles_x,
+        f.tiles_y, diff, counters);
+    count_launch(2);
     return cudaGetLastError();
 }
 

@@ -14,7 +14,8 @@ namespace qr {
 // counters[2]: number of kept Gaussians (non-empty footprint)
 // counters[3]: number of Gaussians n
 // counters[4]: number of intersections actually emitted (0 on overflow)
-enum { CNT_STATUS = 0, CNT_ISECT = 1, CNT_VISIBLE = 2, CNT_N = 3, CNT_SORT_N = 4, CNT_WORDS = 8 };
+enum { CNT_STATUS = 0, CNT_ISECT = 1, CNT_VISIBLE = 2, CNT_N = 3, CNT_SORT_N = 4, CNT_CAND = 5,
+       CNT_WORDS = 8 };
 
 // Workspace slots (byte offsets in qr_frame::off).
 enum Slot {
@@ -23,6 +24,9 @@ enum Slot {
     S_END
 };
 constexpr int kProjectThreads = 256;
+// Copies of the 2-D difference array of per-tile counts; CTA b adds into copy
+// b % kDiffCopies, which spreads the atomics on its hot corners.
+constexpr int kDiffCopies = 8;
 static_assert(S_END <= QR_FRAME_SLOTS, "too many workspace slots");
 
 constexpr int kSortThreads = 256;

@@ -12,20 +12,80 @@
 // Outputs are the kept ids in depth order and the weights divided by
 // 1 - T^Q (the normalisation step folded into the weights).
 //
-// GB300 design: one CTA per screen tile (256 threads, one per pixel).  The
-// tile's list is staged through shared memory 256 entries at a time (gid,
-// projected mean hi/lo, conic axes, opacity: 40 B each) with one coalesced load
-// per thread; every pixel then reads the staged entries as broadcasts.  The
-// walk is scalar FP32 (one exp per pixel-entry pair); a CTA stops loading as
-// soon as all of its pixels have stopped (__syncthreads_count).  Kept
-// (id, weight) pairs go to per-thread shared-memory slots [K][256] so no
+// GB300 design: one CTA per screen tile (256 pixels), 128 threads, each
+// walking two vertically adjacent pixels of the same column.  The tile's list
+// is staged through shared memory 256 entries at a time (gid, projected mean
+// hi/lo, conic axes, opacity, reject bound: 44 B each) with coalesced loads;
+// the walk reads the staged entries as broadcasts.  The two pixels share the
+// x offset, and their y offsets, axis projections and q/2 are computed with
+// packed FP32x2 instructions (each half rounds exactly like the scalar
+// instruction), so the common case -- an entry out of reach of both pixels,
+// four of five entries walked -- costs one shared-memory read set and a
+// handful of instructions for two pixels; four entries are evaluated per
+// step (independent chains, so a long walk is not one serial latency chain)
+// and the ids of the next batch are fetched while the current one is walked.
+// Entries within reach take the Algorithm 1 step for both pixels at once (one
+// exp per pixel-entry pair, T_test packed), in list order; only keeping a
+// Gaussian or stopping branches off.  A CTA stops loading as soon as all of
+// its pixels have stopped (__syncthreads_count).
+// Kept (id, weight) pairs go to per-pixel shared-memory slots [K][256] so no
 // dynamically indexed register array spills, then are written out once.
 #include "qr_internal.cuh"
 
 namespace qr {
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kPix = 256;       // pixels per tile
+constexpr int kThreads = 128;   // two pixels per thread
+
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+    float2 d;
+    asm("{\n .reg .b64 x, y;\n mov.b64 x, {%2, %3};\n mov.b64 y, {%4, %5};\n"
+        " add.rn.f32x2 x, x, y;\n mov.b64 {%0, %1}, x;\n}\n"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+    float2 d;
+    asm("{\n .reg .b64 x, y;\n mov.b64 x, {%2, %3};\n mov.b64 y, {%4, %5};\n"
+        " mul.rn.f32x2 x, x, y;\n mov.b64 {%0, %1}, x;\n}\n"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+    float2 d;
+    asm("{\n .reg .b64 x, y, z;\n mov.b64 x, {%2, %3};\n mov.b64 y, {%4, %5};\n"
+        " mov.b64 z, {%6, %7};\n fma.rn.f32x2 x, x, y, z;\n mov.b64 {%0, %1}, x;\n}\n"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+
+// Algorithm 1 state of one pixel.
+struct Walk {
+    float T, TQ, thr;
+    int k, m;
+    bool done;
+};
+
+// The rarely taken end of an Algorithm 1 step, for a member entry (alpha' >=
+// alpha_min) whose T_test = Tt crosses the next quantile boundary or the stop
+// threshold: keep the Gaussian, advance k, stop.
+__device__ __forceinline__ void walk_event(Walk &w, float Tt, float a, float tau_stop, int K,
+                                        uint32_t gid, int slot, int32_t *s_ids, float *s_w) {
+    if (Tt < w.thr) {
+        s_ids[w.m * kPix + slot] = int32_t(gid);
+        s_w[w.m * kPix + slot] = w.TQ * a;
+        ++w.m;
+        w.TQ = w.TQ * (1.0f - a);
+        do {
+            ++w.k;
+            w.thr = (w.k < K) ? __fdiv_rn(float(K - w.k), float(K + 1)) : -1.0f;
+        } while (Tt < w.thr);
+    }
+    if (Tt < tau_stop) w.done = true;
+    else w.T = Tt;
+}
 
 __global__ void __launch_bounds__(kThreads)
 select_kernel(const float4 *__restrict__ rec_m, const float4 *__restrict__ rec_w,
@@ -33,79 +93,133 @@ select_kernel(const float4 *__restrict__ rec_m, const float4 *__restrict__ rec_w
               const uint32_t *__restrict__ isect_gid, const uint2 *__restrict__ ranges, int W,
               int H, int tile_w, int tiles_x, int K, float alpha_min, float alpha_max,
               int32_t *__restrict__ ids, float *__restrict__ wout, uint8_t *__restrict__ cnt) {
-    __shared__ float4 s_m[kThreads];
-    __shared__ float4 s_c[kThreads];
-    __shared__ float s_a[kThreads];
-    __shared__ float s_h[kThreads];
-    __shared__ uint32_t s_g[kThreads];
+    __shared__ float4 s_m[kPix];
+    __shared__ float4 s_c[kPix];
+    __shared__ float s_a[kPix];
+    __shared__ float s_h[kPix];
+    __shared__ uint32_t s_g[kPix];
     extern __shared__ unsigned char s_dyn[];
-    int32_t *s_ids = reinterpret_cast<int32_t *>(s_dyn);              // [K][256]
-    float *s_w = reinterpret_cast<float *>(s_dyn) + K * kThreads;     // [K][256]
+    int32_t *s_ids = reinterpret_cast<int32_t *>(s_dyn);          // [K][256]
+    float *s_w = reinterpret_cast<float *>(s_dyn) + K * kPix;     // [K][256]
 
     const int tile = blockIdx.x;
     const int tx = tile % tiles_x, ty = tile / tiles_x;
-    const int tile_h = kThreads / tile_w;
-    const int lx = threadIdx.x % tile_w, ly = threadIdx.x / tile_w;
+    const int tile_h = kPix / tile_w;
+    const int lx = threadIdx.x % tile_w, ly = 2 * (threadIdx.x / tile_w);
     const int px = tx * tile_w + lx, py = ty * tile_h + ly;
-    const bool inside = px < W && py < H;
-    const float ux = float(px) + 0.5f, uy = float(py) + 0.5f;
+    const int slot0 = ly * tile_w + lx, slot1 = slot0 + tile_w;
+    const bool in0 = px < W && py < H, in1 = px < W && py + 1 < H;
+    const float ux = float(px) + 0.5f;
+    const float2 uy = make_float2(float(py) + 0.5f, float(py + 1) + 0.5f);
     const uint2 range = ranges[tile];
 
     const float tau_stop = __fdiv_rn(1.0f, float(K + 1));
-    float T = 1.0f, TQ = 1.0f;
-    int k = 0, m = 0;
-    float thr = __fdiv_rn(float(K), float(K + 1));
-    bool done = !inside;
+    const float thr0 = __fdiv_rn(float(K), float(K + 1));
+    Walk w0{1.0f, 1.0f, thr0, 0, 0, !in0};
+    Walk w1{1.0f, 1.0f, thr0, 0, 0, !in1};
 
-    for (uint32_t b = range.x; b < range.y; b += kThreads) {
-        if (__syncthreads_count(done) == kThreads) break;
-        const uint32_t idx = b + threadIdx.x;
-        if (idx < range.y) {
-            const uint32_t g = isect_gid[idx];
-            s_g[threadIdx.x] = g;
-            s_m[threadIdx.x] = rec_m[g];
-            s_c[threadIdx.x] = rec_w[g];
-            s_a[threadIdx.x] = rec_a[g];
-            s_h[threadIdx.x] = rec_h[g];
-        }
-        __syncthreads();
-        const int nb = int(min(uint32_t(kThreads), range.y - b));
-        if (!done) {
-            for (int j = 0; j < nb; ++j) {
-                const float4 mm = s_m[j];
-                const float4 cc = s_c[j];
-                const PixelTerm pt = eval_half_q(ux, uy, mm, cc);
-                if (pt.half_q > s_h[j]) continue;          // alpha' < alpha_min for certain
-                const float a = eval_alpha(s_a[j], pt.half_q, alpha_max);
-                if (a < alpha_min) continue;
-                const float Tt = T * (1.0f - a);
-                if (Tt < thr) {
-                    s_ids[m * kThreads + threadIdx.x] = int32_t(s_g[j]);
-                    s_w[m * kThreads + threadIdx.x] = TQ * a;
-                    ++m;
-                    TQ = TQ * (1.0f - a);
-                    do {
-                        ++k;
-                        thr = (k < K) ? __fdiv_rn(float(K - k), float(K + 1)) : -1.0f;
-                    } while (Tt < thr);
-                }
-                if (Tt < tau_stop) {
-                    done = true;
-                    break;
-                }
-                T = Tt;
+    // ids of the next batch are fetched while the current batch is walked
+    uint32_t gnext[kPix / kThreads];
+#pragma unroll
+    for (int u = 0; u < kPix / kThreads; ++u) {
+        const uint32_t idx = range.x + threadIdx.x + u * kThreads;
+        gnext[u] = idx < range.y ? isect_gid[idx] : 0u;
+    }
+    for (uint32_t b = range.x; b < range.y; b += kPix) {
+        if (__syncthreads_count(w0.done && w1.done) == kThreads) break;
+#pragma unroll
+        for (int u = 0; u < kPix / kThreads; ++u) {
+            const int e = threadIdx.x + u * kThreads;
+            if (b + e < range.y) {
+                const uint32_t g = gnext[u];
+                s_g[e] = g;
+                s_m[e] = rec_m[g];
+                s_c[e] = rec_w[g];
+                s_a[e] = rec_a[g];
+                s_h[e] = rec_h[g];
             }
         }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < kPix / kThreads; ++u) {
+            const uint32_t idx = b + kPix + threadIdx.x + u * kThreads;
+            gnext[u] = idx < range.y ? isect_gid[idx] : 0u;
+        }
+        const int nb = int(min(uint32_t(kPix), range.y - b));
+        if (w0.done && w1.done) continue;
+        // four entries per step: their q/2 chains are independent, and the
+        // scalar Algorithm 1 steps run only when one of them is within reach
+        for (int j0 = 0; j0 < nb; j0 += 4) {
+            float2 hq[4];
+            float h[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int j = min(j0 + u, nb - 1);
+                const float4 mm = s_m[j];
+                const float4 cc = s_c[j];
+                h[u] = s_h[j];
+                // eval_half_q for both pixels: dx shared, the rest packed
+                const float dx = (ux - mm.x) - mm.z;
+                const float2 dy = add2(add2(uy, make_float2(-mm.y, -mm.y)), make_float2(-mm.w, -mm.w));
+                const float2 dx2 = make_float2(dx, dx);
+                const float2 p1 = fma2(dx2, make_float2(cc.x, cc.x), mul2(dy, make_float2(cc.y, cc.y)));
+                const float2 p2 = fma2(dx2, make_float2(cc.z, cc.z), mul2(dy, make_float2(cc.w, cc.w)));
+                hq[u] = fma2(p1, p1, mul2(p2, p2));
+            }
+            unsigned reach = 0;   // bit 2u: pixel 0 may take entry u, bit 2u+1: pixel 1
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const bool valid = j0 + u < nb;
+                reach |= unsigned(valid && !(hq[u].x > h[u])) << (2 * u);
+                reach |= unsigned(valid && !(hq[u].y > h[u])) << (2 * u + 1);
+            }
+            if (w0.done) reach &= 0xAAu;
+            if (w1.done) reach &= 0x55u;
+            if (!reach) continue;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const bool r0 = !w0.done && ((reach >> (2 * u)) & 1u);
+                const bool r1 = !w1.done && ((reach >> (2 * u + 1)) & 1u);
+                if (!(r0 || r1)) continue;
+                // alpha' and T_test for both pixels; a pixel for which the entry is
+                // not a member gets alpha' = 0, i.e. T_test = T (1 - 0) = T exactly
+                const float alpha = s_a[j0 + u];
+                const float a0 = eval_alpha(alpha, hq[u].x, alpha_max);
+                const float a1 = eval_alpha(alpha, hq[u].y, alpha_max);
+                const bool t0 = r0 && !(a0 < alpha_min), t1 = r1 && !(a1 < alpha_min);
+                const float2 Tt = mul2(make_float2(w0.T, w1.T),
+                                       add2(make_float2(1.0f, 1.0f),
+                                            make_float2(t0 ? -a0 : -0.0f, t1 ? -a1 : -0.0f)));
+                const bool e0 = t0 && (Tt.x < w0.thr || Tt.x < tau_stop);
+                const bool e1 = t1 && (Tt.y < w1.thr || Tt.y < tau_stop);
+                if (e0 || e1) {
+                    const uint32_t gid = s_g[j0 + u];
+                    if (e0) walk_event(w0, Tt.x, a0, tau_stop, K, gid, slot0, s_ids, s_w);
+                    if (e1) walk_event(w1, Tt.y, a1, tau_stop, K, gid, slot1, s_ids, s_w);
+                }
+                if (t0 && !e0) w0.T = Tt.x;
+                if (t1 && !e1) w1.T = Tt.y;
+            }
+            if (w0.done && w1.done) break;
+        }
     }
-    if (!inside) return;
-    const int64_t p = int64_t(py) * W + px;
-    const float D = 1.0f - TQ;
+    const float D0 = 1.0f - w0.TQ, D1 = 1.0f - w1.TQ;
     for (int j = 0; j < K; ++j) {
-        const bool has = j < m;
-        ids[p * K + j] = has ? s_ids[j * kThreads + threadIdx.x] : -1;
-        wout[p * K + j] = has ? __fdiv_rn(s_w[j * kThreads + threadIdx.x], D) : 0.0f;
+        if (in0) {
+            const int64_t p = int64_t(py) * W + px;
+            const bool has = j < w0.m;
+            ids[p * K + j] = has ? s_ids[j * kPix + slot0] : -1;
+            wout[p * K + j] = has ? __fdiv_rn(s_w[j * kPix + slot0], D0) : 0.0f;
+        }
+        if (in1) {
+            const int64_t p = int64_t(py + 1) * W + px;
+            const bool has = j < w1.m;
+            ids[p * K + j] = has ? s_ids[j * kPix + slot1] : -1;
+            wout[p * K + j] = has ? __fdiv_rn(s_w[j * kPix + slot1], D1) : 0.0f;
+        }
     }
-    cnt[p] = uint8_t(m);
+    if (in0) cnt[int64_t(py) * W + px] = uint8_t(w0.m);
+    if (in1) cnt[int64_t(py + 1) * W + px] = uint8_t(w1.m);
 }
 
 }  // namespace
@@ -115,7 +229,7 @@ cudaError_t launch_select(const qr_frame &f, int32_t *ids, float *w, uint8_t *cn
     const int tiles = num_tiles(f);
     if (tiles == 0) return cudaSuccess;
     const int K = f.params.K;
-    const size_t dyn = size_t(K) * kThreads * 8;
+    const size_t dyn = size_t(K) * kPix * 8;
     if (dyn > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              int(dyn));

@@ -6,24 +6,27 @@
 // 64-bit (tile << 32 | depth) keys over id-ordered input gives.
 //
 // GB300 design (5 kernels after the projection, no global depth sort):
-//   1. project (K1) writes, per CTA of 256 Gaussians, how many it kept and the
-//      sum of their tile counts;
+//   1. the projection (K1) counts, per 256 consecutive ids, the kept
+//      Gaussians and the sum of their tile counts;
 //   2. offsets_scan + offsets_apply compact the kept Gaussians (id order) and
 //      give each its first output slot (exclusive scan), with the capacity
-//      check; offsets of kept Gaussians are strictly increasing;
-//      Each kept Gaussian also adds its tile rectangle to a 2-D difference
-//      array of per-tile counts (4 atomics instead of one per intersection);
-//   3. tile_scan integrates the difference array into per-tile counts and
-//      exclusive offsets, i.e. the tile ranges;
+//      check; offsets of kept Gaussians are strictly increasing (the
+//      projection has already added each kept Gaussian's tile rectangle to
+//      a 2-D difference array of per-tile counts: 4 atomics instead of one
+//      per intersection);
+//   3. tile_scan integrates the difference array into per-tile counts (in
+//      shared memory) and exclusive offsets, i.e. the tile ranges;
 //   4. expand_scatter: a load-balanced expansion -- each CTA owns 1024
 //      consecutive output slots, finds their owners with a warp-wide 32-way
 //      search (at most 1024 owners per chunk), derives each slot's tile from
 //      the owner's footprint rectangle, and writes (depth << 32 | id) into
 //      its tile's bucket at an atomically claimed position;
-//   5. tile_sort: one CTA per tile sorts its bucket in shared memory (bitonic
-//      network over the unique 64-bit keys) and writes the ids; a bucket
-//      larger than shared memory is sorted in chunks and merged in global
-//      memory by the same CTA (merge path), so no size is refused.
+//   5. tile_sort: one CTA per tile sorts its bucket (bitonic network over the
+//      unique 64-bit keys) and writes the ids: buckets of up to 2048 keys in
+//      registers (register swaps, warp shuffles, shared memory only for the
+//      cross-warp strides), up to 8192 in shared memory; a larger bucket is
+//      sorted in chunks and merged in global memory by the same CTA (merge
+//      path), so no size is refused.
 // Keys are unique, so the order inside a bucket before step 5 does not matter
 // and the result is deterministic.  No CTA waits for another.  Counts live in
 // device memory, so the stage can be captured in a CUDA graph.
@@ -35,6 +38,7 @@ namespace {
 constexpr int T = 256;
 constexpr int EMIT_CHUNK = 1024;
 constexpr int TS_CAP = 8192;             // keys a tile sorts in shared memory (64 KB)
+constexpr int kScanSmemTiles = 48 * 1024; // tile counts tile_scan integrates in shared memory
 
 // ------------------------------------------------------------------ offsets
 // Exclusive scans of the per-CTA kept counts and tile-count sums.
@@ -58,13 +62,10 @@ offsets_scan(uint32_t *kept, uint32_t *tsum, int nblk, uint32_t *counters, uint3
     }
 }
 
-// Compacted kept ids (id order) and their first output slots; each kept
-// Gaussian also adds its footprint rectangle to the 2-D difference array of
-// tile counts (+1 at (x0,y0) and (x1+1,y1+1), -1 at (x1+1,y0) and (x0,y1+1)).
+// Compacted kept ids (id order) and their first output slots.
 __global__ void __launch_bounds__(kProjectThreads)
 offsets_apply(const uint32_t *__restrict__ tcount, const uint32_t *__restrict__ kept_base,
-              const uint32_t *__restrict__ tsum_base, int64_t n, const uint2 *__restrict__ rect,
-              int tiles_x, int *__restrict__ diff, uint32_t *__restrict__ kid,
+              const uint32_t *__restrict__ tsum_base, int64_t n, uint32_t *__restrict__ kid,
               uint32_t *__restrict__ koff) {
     __shared__ uint32_t s_w[32];
     const int64_t g = int64_t(blockIdx.x) * kProjectThreads + threadIdx.x;
@@ -77,14 +78,6 @@ offsets_apply(const uint32_t *__restrict__ tcount, const uint32_t *__restrict__ 
         const uint32_t slot = kept_base[blockIdx.x] + kinc - 1u;
         kid[slot] = uint32_t(g);
         koff[slot] = tsum_base[blockIdx.x] + cinc - c;
-        const uint2 rc = rect[g];
-        const int x0 = int(rc.x & 0xFFFFu), y0 = int(rc.x >> 16);
-        const int x1 = int(rc.y & 0xFFFFu) + 1, y1 = int(rc.y >> 16) + 1;
-        const int stride = tiles_x + 1;
-        atomicAdd(&diff[y0 * stride + x0], 1);
-        atomicAdd(&diff[y0 * stride + x1], -1);
-        atomicAdd(&diff[y1 * stride + x0], -1);
-        atomicAdd(&diff[y1 * stride + x1], 1);
     }
 }
 
@@ -151,9 +144,15 @@ __device__ __forceinline__ void slot_owner(const ExpandSmem &sm, uint32_t len, u
 
 // Tile counts from the difference array (prefix sums along x, then y, one
 // CTA), then exclusive offsets -> ranges; the counts become zeroed cursors.
+// The counts are integrated in shared memory when the tile grid fits (up to
+// kScanSmemTiles tiles, e.g. 4K frames with 16x16 tiles), else in the cursor
+// array itself.  Rows are summed by one warp each (shuffle scans), columns by
+// one thread each.  Partial sums may be negative; the uint32 arithmetic is
+// exact modulo 2^32 and the integrated counts are not.
 __global__ void __launch_bounds__(1024)
 tile_scan(const int *__restrict__ diff, const uint32_t *__restrict__ counters, uint32_t *tcnt,
-          int tiles_x, int tiles_y, uint2 *ranges) {
+          int tiles_x, int tiles_y, uint2 *ranges, int in_smem) {
+    extern __shared__ uint32_t s_cnt[];
     __shared__ uint32_t s_w[32];
     const int stride = tiles_x + 1;
     const int tiles = tiles_x * tiles_y;
@@ -164,28 +163,39 @@ tile_scan(const int *__restrict__ diff, const uint32_t *__restrict__ counters, u
         }
         return;
     }
-    // rows: running sum along x (one thread per row)
-    for (int y = threadIdx.x; y < tiles_y; y += blockDim.x) {
-        int run = 0;
-        for (int x = 0; x < tiles_x; ++x) {
-            run += diff[y * stride + x];
-            tcnt[y * tiles_x + x] = uint32_t(run);
+    uint32_t *A = in_smem ? s_cnt : tcnt;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    for (int y = warp; y < tiles_y; y += nwarps) {
+        uint32_t carry = 0;
+        for (int x0 = 0; x0 < tiles_x; x0 += 32) {
+            const int x = x0 + lane;
+            uint32_t v = 0u;
+            if (x < tiles_x)
+#pragma unroll
+                for (int r = 0; r < kDiffCopies; ++r)
+                    v += uint32_t(diff[size_t(r) * stride * (tiles_y + 1) + y * stride + x]);
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += t;
+            }
+            if (x < tiles_x) A[y * tiles_x + x] = carry + v;
+            carry += __shfl_sync(0xffffffffu, v, 31);
         }
     }
     __syncthreads();
-    // columns: running sum along y (one thread per column)
     for (int x = threadIdx.x; x < tiles_x; x += blockDim.x) {
         uint32_t run = 0;
         for (int y = 0; y < tiles_y; ++y) {
-            run += tcnt[y * tiles_x + x];
-            tcnt[y * tiles_x + x] = run;
+            run += A[y * tiles_x + x];
+            A[y * tiles_x + x] = run;
         }
     }
     __syncthreads();
     uint32_t carry = 0;
     for (int base = 0; base < tiles; base += blockDim.x) {
         const int t = base + threadIdx.x;
-        const uint32_t c = t < tiles ? tcnt[t] : 0u;
+        const uint32_t c = t < tiles ? A[t] : 0u;
         uint32_t chunk;
         const uint32_t inc = block_inclusive_scan(c, s_w, chunk);
         if (t < tiles) ranges[t] = make_uint2(carry + inc - c, carry + inc);
@@ -243,6 +253,66 @@ __device__ __forceinline__ void bitonic_smem(unsigned long long *s, int npow2) {
         }
 }
 
+// Bitonic sort of a bucket of up to 256*E keys held in registers, E per
+// thread in blocked order (thread t holds positions tE .. tE+E-1), padded
+// with ~0.  Compare-exchange partners i and i^j meet inside a thread for
+// j < E (register swaps), across lanes for E <= j < 32E (shuffles) and
+// across warps for larger j (shared memory, two barriers per stage).
+__device__ __forceinline__ unsigned long long shfl_xor64(unsigned long long x, int m) {
+    const uint32_t lo = __shfl_xor_sync(0xffffffffu, uint32_t(x), m);
+    const uint32_t hi = __shfl_xor_sync(0xffffffffu, uint32_t(x >> 32), m);
+    return (static_cast<unsigned long long>(hi) << 32) | lo;
+}
+
+template <int E>
+__device__ void sort_registers(const unsigned long long *__restrict__ src, int n,
+                               unsigned long long *s, uint32_t *__restrict__ dst) {
+    constexpr int N = T * E;
+    const int base = threadIdx.x * E;
+    unsigned long long v[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) v[e] = base + e < n ? src[base + e] : ~0ull;
+    for (int k = 2; k <= N; k <<= 1) {
+        for (int j = k >> 1; j >= 32 * E; j >>= 1) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) s[base + e] = v[e];
+            __syncthreads();
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int i = base + e;
+                const unsigned long long y = s[i ^ j];
+                const bool take_min = ((i & j) == 0) == ((i & k) == 0);
+                v[e] = take_min ? (v[e] < y ? v[e] : y) : (v[e] < y ? y : v[e]);
+            }
+            __syncthreads();
+        }
+        for (int j = min(k >> 1, 16 * E); j >= E; j >>= 1) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int i = base + e;
+                const unsigned long long y = shfl_xor64(v[e], j / E);
+                const bool take_min = ((i & j) == 0) == ((i & k) == 0);
+                v[e] = take_min ? (v[e] < y ? v[e] : y) : (v[e] < y ? y : v[e]);
+            }
+        }
+#pragma unroll
+        for (int J = E / 2; J > 0; J >>= 1) {
+            if (J >= k) continue;
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                if ((e ^ J) > e) {
+                    const bool up = ((base + e) & k) == 0;
+                    const unsigned long long a = v[e], b = v[e ^ J];
+                    if ((a > b) == up) { v[e] = b; v[e ^ J] = a; }
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+        if (base + e < n) dst[base + e] = uint32_t(v[e]);
+}
+
 // Sort m <= TS_CAP keys in place in global memory through shared memory.
 __device__ __forceinline__ void sort_chunk(unsigned long long *s, unsigned long long *g, int m) {
     int npow2 = 1;
@@ -285,6 +355,16 @@ tile_sort(const uint2 *__restrict__ ranges, unsigned long long *__restrict__ key
     const int n = int(r.y - r.x);
     if (n == 0) return;
     unsigned long long *src = keys + r.x;
+    if (n <= 2 * T) {
+        if (n <= T) sort_registers<1>(src, n, s_k, igid + r.x);
+        else sort_registers<2>(src, n, s_k, igid + r.x);
+        return;
+    }
+    if (n <= 8 * T) {
+        if (n <= 4 * T) sort_registers<4>(src, n, s_k, igid + r.x);
+        else sort_registers<8>(src, n, s_k, igid + r.x);
+        return;
+    }
     if (n <= TS_CAP) {
         int npow2 = 1;
         while (npow2 < n) npow2 <<= 1;
@@ -328,8 +408,6 @@ cudaError_t launch_sort(const qr_frame &f, cudaStream_t s) {
     int *diff = slot<int>(f, S_DIFF);
     cudaError_t e = cudaMemsetAsync(tcnt, 0, sizeof(uint32_t) * size_t(tiles), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(ranges, 0, sizeof(uint2) * size_t(tiles), s);
-    if (e == cudaSuccess)
-        e = cudaMemsetAsync(diff, 0, sizeof(int) * size_t(f.tiles_x + 1) * size_t(f.tiles_y + 1), s);
     if (e != cudaSuccess) return e;
     if (f.n == 0) return cudaSuccess;
     e = cudaFuncSetAttribute(tile_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -346,8 +424,14 @@ cudaError_t launch_sort(const qr_frame &f, cudaStream_t s) {
     const uint2 *rect = slot<uint2>(f, S_RECT);
     offsets_scan<<<1, 1024, 0, s>>>(kept, tsum, nblk, counters, uint32_t(f.max_isect));
     offsets_apply<<<nblk, kProjectThreads, 0, s>>>(slot<uint32_t>(f, S_TCOUNT), kept, tsum, f.n,
-                                                   rect, f.tiles_x, diff, kid, koff);
-    tile_scan<<<1, 1024, 0, s>>>(diff, counters, tcnt, f.tiles_x, f.tiles_y, ranges);
+                                                   kid, koff);
+    const int scan_smem = tiles <= kScanSmemTiles ? 1 : 0;
+    const size_t scan_bytes = scan_smem ? sizeof(uint32_t) * size_t(tiles) : 0;
+    e = cudaFuncSetAttribute(tile_scan, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(sizeof(uint32_t) * kScanSmemTiles));
+    if (e != cudaSuccess) return e;
+    tile_scan<<<1, 1024, scan_bytes, s>>>(diff, counters, tcnt, f.tiles_x, f.tiles_y, ranges,
+                                          scan_smem);
     auto *keys = slot<unsigned long long>(f, S_KEYS64);
     expand_scatter<<<sms * 6, T, 0, s>>>(koff, kid, rect, slot<uint32_t>(f, S_GKEY), counters,
                                          f.tiles_x, ranges, tcnt, keys);

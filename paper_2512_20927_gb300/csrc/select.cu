@@ -16,20 +16,23 @@
 // walking two vertically adjacent pixels of the same column.  The tile's list
 // is staged through shared memory 256 entries at a time (gid, projected mean
 // hi/lo, conic axes, opacity, reject bound: 44 B each) with coalesced loads;
-// the walk reads the staged entries as broadcasts.  The two pixels share the
-// x offset, and their y offsets, axis projections and q/2 are computed with
-// packed FP32x2 instructions (each half rounds exactly like the scalar
-// instruction), so the common case -- an entry out of reach of both pixels,
-// four of five entries walked -- costs one shared-memory read set and a
-// handful of instructions for two pixels; four entries are evaluated per
-// step (independent chains, so a long walk is not one serial latency chain)
-// and the ids of the next batch are fetched while the current one is walked.
-// Entries within reach take the Algorithm 1 step for both pixels at once (one
-// exp per pixel-entry pair, T_test packed), in list order; only keeping a
-// Gaussian or stopping branches off.  A CTA stops loading as soon as all of
-// its pixels have stopped (__syncthreads_count).
-// Kept (id, weight) pairs go to per-pixel shared-memory slots [K][256] so no
-// dynamically indexed register array spills, then are written out once.
+// the ids of the next batch are fetched while the current one is walked.
+//   * Each warp first culls the staged entries against its box of pixel
+//     centres (16x4 for 16x16 tiles), one entry per lane: the minimum of q/2
+//     over the box against the entry's reject bound.  About four of five
+//     entries a pixel would walk are out of reach of the whole box; the
+//     survivors form a per-warp list in shared memory, in list order.
+//   * The warp walks its list four entries per step (independent chains).
+//     The two pixels of a thread share the x offset; their y offsets, axis
+//     projections and q/2 use packed FP32x2 instructions (each half rounds
+//     exactly like the scalar instruction).  Entries within reach take the
+//     Algorithm 1 step for both pixels at once (one exp per pixel-entry pair,
+//     T_test packed); only keeping a Gaussian or stopping branches off.
+// A CTA stops loading as soon as all of its pixels have stopped
+// (__syncthreads_count).  Kept (id, weight) pairs go to per-pixel
+// shared-memory slots [256][K|1] (no dynamically indexed register array, no
+// bank conflicts) and are written out once per tile row as contiguous runs of
+// tile_w * K ids and weights, so the stores are fully coalesced.
 #include "qr_internal.cuh"
 
 namespace qr {
@@ -37,6 +40,7 @@ namespace {
 
 constexpr int kPix = 256;       // pixels per tile
 constexpr int kThreads = 128;   // two pixels per thread
+constexpr int kBatch = 128;     // list entries staged per batch
 
 __device__ __forceinline__ float2 add2(float2 a, float2 b) {
     float2 d;
@@ -61,6 +65,37 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
     return d;
 }
 
+// Lower end of q/2 = (d.w1)^2 + (d.w2)^2, d = u - mu', over the box
+// [x0,x1] x [y0,y1] of pixel centres: 0 if mu' is inside, else the smallest
+// value on the four edges, each at its clamped 1-D minimiser (evaluated with
+// the same dot products as a pixel, so no cancellation-prone closed form).
+__device__ __forceinline__ float box_min_half_q(float4 mm, float4 cc, float x0, float x1, float y0,
+                                                float y1) {
+    const float mx = mm.x + mm.z, my = mm.y + mm.w;
+    if (mx >= x0 && mx <= x1 && my >= y0 && my <= y1) return 0.0f;
+    const float sxy = fmaf(cc.x, cc.y, cc.z * cc.w);
+    const float sxx = fmaf(cc.x, cc.x, cc.z * cc.z), syy = fmaf(cc.y, cc.y, cc.w * cc.w);
+    // the edge minimisers only choose where q/2 is evaluated, so an approximate
+    // quotient suffices (inf / NaN clamp to an edge end)
+    const float ky = -__fdividef(sxy, syy), kx = -__fdividef(sxy, sxx);
+    float best = INFINITY;
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const float dx = (e ? x1 : x0) - mx;
+        const float dy = fminf(fmaxf(dx * ky, y0 - my), y1 - my);
+        const float p1 = fmaf(dx, cc.x, dy * cc.y), p2 = fmaf(dx, cc.z, dy * cc.w);
+        best = fminf(best, fmaf(p1, p1, p2 * p2));
+    }
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const float dy = (e ? y1 : y0) - my;
+        const float dx = fminf(fmaxf(dy * kx, x0 - mx), x1 - mx);
+        const float p1 = fmaf(dx, cc.x, dy * cc.y), p2 = fmaf(dx, cc.z, dy * cc.w);
+        best = fminf(best, fmaf(p1, p1, p2 * p2));
+    }
+    return best;
+}
+
 // Algorithm 1 state of one pixel.
 struct Walk {
     float T, TQ, thr;
@@ -72,10 +107,10 @@ struct Walk {
 // alpha_min) whose T_test = Tt crosses the next quantile boundary or the stop
 // threshold: keep the Gaussian, advance k, stop.
 __device__ __forceinline__ void walk_event(Walk &w, float Tt, float a, float tau_stop, int K,
-                                        uint32_t gid, int slot, int32_t *s_ids, float *s_w) {
+                                        uint32_t gid, int slot, int KS, int32_t *s_ids, float *s_w) {
     if (Tt < w.thr) {
-        s_ids[w.m * kPix + slot] = int32_t(gid);
-        s_w[w.m * kPix + slot] = w.TQ * a;
+        s_ids[slot * KS + w.m] = int32_t(gid);
+        s_w[slot * KS + w.m] = w.TQ * a;
         ++w.m;
         w.TQ = w.TQ * (1.0f - a);
         do {
@@ -87,20 +122,23 @@ __device__ __forceinline__ void walk_event(Walk &w, float Tt, float a, float tau
     else w.T = Tt;
 }
 
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 8)
 select_kernel(const float4 *__restrict__ rec_m, const float4 *__restrict__ rec_w,
               const float *__restrict__ rec_a, const float *__restrict__ rec_h,
               const uint32_t *__restrict__ isect_gid, const uint2 *__restrict__ ranges, int W,
               int H, int tile_w, int tiles_x, int K, float alpha_min, float alpha_max,
               int32_t *__restrict__ ids, float *__restrict__ wout, uint8_t *__restrict__ cnt) {
-    __shared__ float4 s_m[kPix];
-    __shared__ float4 s_c[kPix];
-    __shared__ float s_a[kPix];
-    __shared__ float s_h[kPix];
-    __shared__ uint32_t s_g[kPix];
+    __shared__ float4 s_m[kBatch];
+    __shared__ float4 s_c[kBatch];
+    __shared__ float s_a[kBatch];
+    __shared__ float s_h[kBatch];
+    __shared__ uint32_t s_g[kBatch];
+    __shared__ float s_D[kPix];       // 1 - T^Q per pixel
+    __shared__ uint8_t s_cnt[kPix];
     extern __shared__ unsigned char s_dyn[];
-    int32_t *s_ids = reinterpret_cast<int32_t *>(s_dyn);          // [K][256]
-    float *s_w = reinterpret_cast<float *>(s_dyn) + K * kPix;     // [K][256]
+    const int KS = K | 1;   // odd stride: the per-pixel slots fall in distinct banks
+    int32_t *s_ids = reinterpret_cast<int32_t *>(s_dyn);          // [256][KS]
+    float *s_w = reinterpret_cast<float *>(s_dyn) + KS * kPix;    // [256][KS]
 
     const int tile = blockIdx.x;
     const int tx = tile % tiles_x, ty = tile / tiles_x;
@@ -118,108 +156,136 @@ select_kernel(const float4 *__restrict__ rec_m, const float4 *__restrict__ rec_w
     Walk w0{1.0f, 1.0f, thr0, 0, 0, !in0};
     Walk w1{1.0f, 1.0f, thr0, 0, 0, !in1};
 
-    // ids of the next batch are fetched while the current batch is walked
-    uint32_t gnext[kPix / kThreads];
+    // the warp's box of pixel centres
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    float bx0 = ux, bx1 = ux, by0 = uy.x, by1 = uy.y;
 #pragma unroll
-    for (int u = 0; u < kPix / kThreads; ++u) {
-        const uint32_t idx = range.x + threadIdx.x + u * kThreads;
-        gnext[u] = idx < range.y ? isect_gid[idx] : 0u;
+    for (int o = 16; o > 0; o >>= 1) {
+        bx0 = fminf(bx0, __shfl_xor_sync(FULL, bx0, o));
+        bx1 = fmaxf(bx1, __shfl_xor_sync(FULL, bx1, o));
+        by0 = fminf(by0, __shfl_xor_sync(FULL, by0, o));
+        by1 = fmaxf(by1, __shfl_xor_sync(FULL, by1, o));
     }
-    for (uint32_t b = range.x; b < range.y; b += kPix) {
+
+    // the id of the next staged entry is fetched while the current batch is walked
+    uint32_t gnext = range.x + threadIdx.x < range.y ? isect_gid[range.x + threadIdx.x] : 0u;
+    for (uint32_t b = range.x; b < range.y; b += kBatch) {
         if (__syncthreads_count(w0.done && w1.done) == kThreads) break;
-#pragma unroll
-        for (int u = 0; u < kPix / kThreads; ++u) {
-            const int e = threadIdx.x + u * kThreads;
-            if (b + e < range.y) {
-                const uint32_t g = gnext[u];
-                s_g[e] = g;
-                s_m[e] = rec_m[g];
-                s_c[e] = rec_w[g];
-                s_a[e] = rec_a[g];
-                s_h[e] = rec_h[g];
-            }
+        if (b + threadIdx.x < range.y) {
+            s_g[threadIdx.x] = gnext;
+            s_m[threadIdx.x] = rec_m[gnext];
+            s_c[threadIdx.x] = rec_w[gnext];
+            s_a[threadIdx.x] = rec_a[gnext];
+            s_h[threadIdx.x] = rec_h[gnext];
         }
         __syncthreads();
-#pragma unroll
-        for (int u = 0; u < kPix / kThreads; ++u) {
-            const uint32_t idx = b + kPix + threadIdx.x + u * kThreads;
-            gnext[u] = idx < range.y ? isect_gid[idx] : 0u;
+        {
+            const uint32_t idx = b + kBatch + threadIdx.x;
+            gnext = idx < range.y ? isect_gid[idx] : 0u;
         }
-        const int nb = int(min(uint32_t(kPix), range.y - b));
-        if (w0.done && w1.done) continue;
-        // four entries per step: their q/2 chains are independent, and the
-        // scalar Algorithm 1 steps run only when one of them is within reach
-        for (int j0 = 0; j0 < nb; j0 += 4) {
-            float2 hq[4];
-            float h[4];
+        const int nb = int(min(uint32_t(kBatch), range.y - b));
+        for (int c0 = 0; c0 < nb; c0 += 32) {
+            if (__all_sync(FULL, w0.done && w1.done)) break;
+            // cull 32 staged entries against the warp's box (one per lane): an
+            // entry whose q/2 stays above its reject bound over the whole box
+            // is skipped by every pixel of the warp anyway
+            const int jl = c0 + lane;
+            bool pass = false;
+            if (jl < nb)
+                pass = !(box_min_half_q(s_m[jl], s_c[jl], bx0, bx1, by0, by1) * 0.999f > s_h[jl] + 1e-3f);
+            unsigned todo = __ballot_sync(FULL, pass);
+            // walk the survivors in list order, four entries per step: their
+            // q/2 chains are independent, and the Algorithm 1 steps run only
+            // when one of them is within reach
+            while (todo) {
+                int jj[4];
+                bool valid[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int j = min(j0 + u, nb - 1);
-                const float4 mm = s_m[j];
-                const float4 cc = s_c[j];
-                h[u] = s_h[j];
-                // eval_half_q for both pixels: dx shared, the rest packed
-                const float dx = (ux - mm.x) - mm.z;
-                const float2 dy = add2(add2(uy, make_float2(-mm.y, -mm.y)), make_float2(-mm.w, -mm.w));
-                const float2 dx2 = make_float2(dx, dx);
-                const float2 p1 = fma2(dx2, make_float2(cc.x, cc.x), mul2(dy, make_float2(cc.y, cc.y)));
-                const float2 p2 = fma2(dx2, make_float2(cc.z, cc.z), mul2(dy, make_float2(cc.w, cc.w)));
-                hq[u] = fma2(p1, p1, mul2(p2, p2));
-            }
-            unsigned reach = 0;   // bit 2u: pixel 0 may take entry u, bit 2u+1: pixel 1
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const bool valid = j0 + u < nb;
-                reach |= unsigned(valid && !(hq[u].x > h[u])) << (2 * u);
-                reach |= unsigned(valid && !(hq[u].y > h[u])) << (2 * u + 1);
-            }
-            if (w0.done) reach &= 0xAAu;
-            if (w1.done) reach &= 0x55u;
-            if (!reach) continue;
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const bool r0 = !w0.done && ((reach >> (2 * u)) & 1u);
-                const bool r1 = !w1.done && ((reach >> (2 * u + 1)) & 1u);
-                if (!(r0 || r1)) continue;
-                // alpha' and T_test for both pixels; a pixel for which the entry is
-                // not a member gets alpha' = 0, i.e. T_test = T (1 - 0) = T exactly
-                const float alpha = s_a[j0 + u];
-                const float a0 = eval_alpha(alpha, hq[u].x, alpha_max);
-                const float a1 = eval_alpha(alpha, hq[u].y, alpha_max);
-                const bool t0 = r0 && !(a0 < alpha_min), t1 = r1 && !(a1 < alpha_min);
-                const float2 Tt = mul2(make_float2(w0.T, w1.T),
-                                       add2(make_float2(1.0f, 1.0f),
-                                            make_float2(t0 ? -a0 : -0.0f, t1 ? -a1 : -0.0f)));
-                const bool e0 = t0 && (Tt.x < w0.thr || Tt.x < tau_stop);
-                const bool e1 = t1 && (Tt.y < w1.thr || Tt.y < tau_stop);
-                if (e0 || e1) {
-                    const uint32_t gid = s_g[j0 + u];
-                    if (e0) walk_event(w0, Tt.x, a0, tau_stop, K, gid, slot0, s_ids, s_w);
-                    if (e1) walk_event(w1, Tt.y, a1, tau_stop, K, gid, slot1, s_ids, s_w);
+                for (int u = 0; u < 4; ++u) {
+                    valid[u] = todo != 0u;
+                    jj[u] = valid[u] ? c0 + __ffs(todo) - 1 : jj[0];
+                    todo &= todo - 1u;
                 }
-                if (t0 && !e0) w0.T = Tt.x;
-                if (t1 && !e1) w1.T = Tt.y;
+                float2 hq[4];
+                float h[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int j = jj[u];
+                    const float4 mm = s_m[j];
+                    const float4 cc = s_c[j];
+                    h[u] = s_h[j];
+                    // eval_half_q for both pixels: dx shared, the rest packed
+                    const float dx = (ux - mm.x) - mm.z;
+                    const float2 dy = add2(add2(uy, make_float2(-mm.y, -mm.y)), make_float2(-mm.w, -mm.w));
+                    const float2 dx2 = make_float2(dx, dx);
+                    const float2 p1 = fma2(dx2, make_float2(cc.x, cc.x), mul2(dy, make_float2(cc.y, cc.y)));
+                    const float2 p2 = fma2(dx2, make_float2(cc.z, cc.z), mul2(dy, make_float2(cc.w, cc.w)));
+                    hq[u] = fma2(p1, p1, mul2(p2, p2));
+                }
+                unsigned reach = 0;   // bit 2u: pixel 0 may take entry u, bit 2u+1: pixel 1
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    reach |= unsigned(valid[u] && !(hq[u].x > h[u])) << (2 * u);
+                    reach |= unsigned(valid[u] && !(hq[u].y > h[u])) << (2 * u + 1);
+                }
+                if (w0.done) reach &= 0xAAu;
+                if (w1.done) reach &= 0x55u;
+                if (!reach) continue;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const bool r0 = !w0.done && ((reach >> (2 * u)) & 1u);
+                    const bool r1 = !w1.done && ((reach >> (2 * u + 1)) & 1u);
+                    if (!(r0 || r1)) continue;
+                    // alpha' and T_test for both pixels; a pixel for which the entry is
+                    // not a member gets alpha' = 0, i.e. T_test = T (1 - 0) = T exactly
+                    const float alpha = s_a[jj[u]];
+                    const float a0 = eval_alpha(alpha, hq[u].x, alpha_max);
+                    const float a1 = eval_alpha(alpha, hq[u].y, alpha_max);
+                    const bool t0 = r0 && !(a0 < alpha_min), t1 = r1 && !(a1 < alpha_min);
+                    const float2 Tt = mul2(make_float2(w0.T, w1.T),
+                                           add2(make_float2(1.0f, 1.0f),
+                                                make_float2(t0 ? -a0 : -0.0f, t1 ? -a1 : -0.0f)));
+                    const bool e0 = t0 && (Tt.x < w0.thr || Tt.x < tau_stop);
+                    const bool e1 = t1 && (Tt.y < w1.thr || Tt.y < tau_stop);
+                    if (e0 || e1) {
+                        const uint32_t gid = s_g[jj[u]];
+                        if (e0) walk_event(w0, Tt.x, a0, tau_stop, K, gid, slot0, KS, s_ids, s_w);
+                        if (e1) walk_event(w1, Tt.y, a1, tau_stop, K, gid, slot1, KS, s_ids, s_w);
+                    }
+                    if (t0 && !e0) w0.T = Tt.x;
+                    if (t1 && !e1) w1.T = Tt.y;
+                }
+                if (w0.done && w1.done) break;
             }
-            if (w0.done && w1.done) break;
         }
     }
-    const float D0 = 1.0f - w0.TQ, D1 = 1.0f - w1.TQ;
-    for (int j = 0; j < K; ++j) {
-        if (in0) {
-            const int64_t p = int64_t(py) * W + px;
-            const bool has = j < w0.m;
-            ids[p * K + j] = has ? s_ids[j * kPix + slot0] : -1;
-            wout[p * K + j] = has ? __fdiv_rn(s_w[j * kPix + slot0], D0) : 0.0f;
-        }
-        if (in1) {
-            const int64_t p = int64_t(py + 1) * W + px;
-            const bool has = j < w1.m;
-            ids[p * K + j] = has ? s_ids[j * kPix + slot1] : -1;
-            wout[p * K + j] = has ? __fdiv_rn(s_w[j * kPix + slot1], D1) : 0.0f;
+    s_D[slot0] = 1.0f - w0.TQ;
+    s_D[slot1] = 1.0f - w1.TQ;
+    s_cnt[slot0] = uint8_t(w0.m);
+    s_cnt[slot1] = uint8_t(w1.m);
+    __syncthreads();
+    // coalesced output: each row of the tile is tile_w * K consecutive entries
+    // of ids and weights in the image
+    const int rowlen = tile_w * K;
+    for (int rem = threadIdx.x; rem < rowlen; rem += kThreads) {
+        const int cx = rem / K, j = rem - cx * K;
+        const int gx = tx * tile_w + cx;
+        if (gx >= W) continue;
+        for (int row = 0; row < tile_h; ++row) {
+            const int gy = ty * tile_h + row;
+            if (gy >= H) break;
+            const int slot = row * tile_w + cx;
+            const int64_t o = (int64_t(gy) * W + gx) * K + j;
+            const bool has = j < int(s_cnt[slot]);
+            ids[o] = has ? s_ids[slot * KS + j] : -1;
+            wout[o] = has ? __fdiv_rn(s_w[slot * KS + j], s_D[slot]) : 0.0f;
         }
     }
-    if (in0) cnt[int64_t(py) * W + px] = uint8_t(w0.m);
-    if (in1) cnt[int64_t(py + 1) * W + px] = uint8_t(w1.m);
+    for (int e = threadIdx.x; e < kPix; e += kThreads) {
+        const int gx = tx * tile_w + e % tile_w, gy = ty * tile_h + e / tile_w;
+        if (gx < W && gy < H) cnt[int64_t(gy) * W + gx] = s_cnt[e];
+    }
 }
 
 }  // namespace
@@ -229,7 +295,7 @@ cudaError_t launch_select(const qr_frame &f, int32_t *ids, float *w, uint8_t *cn
     const int tiles = num_tiles(f);
     if (tiles == 0) return cudaSuccess;
     const int K = f.params.K;
-    const size_t dyn = size_t(K) * kPix * 8;
+    const size_t dyn = size_t(K | 1) * kPix * 8;
     if (dyn > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              int(dyn));

@@ -47,9 +47,17 @@ project_cull(int64_t n, const float *__restrict__ mean, const float *__restrict_
              const float *__restrict__ opacity, CamArgs cam, float dilation, float alpha_min,
              uint2 *__restrict__ rect, uint32_t *__restrict__ tcount,
              uint32_t *__restrict__ dkey, uint32_t *__restrict__ cand,
-             uint32_t *__restrict__ counters) {
+             uint32_t *__restrict__ vis_count, uint32_t *__restrict__ tile_sum,
+             int *__restrict__ diff, int64_t ndiff, uint32_t *__restrict__ counters) {
     const int64_t g = int64_t(blockIdx.x) * kThreads + threadIdx.x;
     if (blockIdx.x == 0 && threadIdx.x == 0) counters[CNT_N] = uint32_t(n);
+    // clear what the exact stage accumulates into (one word per 256 ids, the
+    // difference-array copies); it runs after this kernel
+    if (g < gridDim.x) {
+        vis_count[g] = 0u;
+        tile_sum[g] = 0u;
+    }
+    for (int64_t i = g; i < ndiff; i += int64_t(gridDim.x) * kThreads) diff[i] = 0;
     // ---------------- stage A: FP32 conservative footprint bound
     bool pass = false;
     if (g < n) {
@@ -259,11 +267,7 @@ cudaError_t launch_project(const qr_frame &f, const float *mean, const float *lo
     const unsigned blocks = unsigned((n + kThreads - 1) / kThreads);
     uint32_t *vis = slot<uint32_t>(f, S_VISCNT), *tsum = slot<uint32_t>(f, S_BSUM);
     int *diff = slot<int>(f, S_DIFF);
-    e = cudaMemsetAsync(vis, 0, sizeof(uint32_t) * blocks, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(tsum, 0, sizeof(uint32_t) * blocks, s);
-    if (e == cudaSuccess)
-        e = cudaMemsetAsync(diff, 0, sizeof(int) * size_t(f.tiles_x + 1) * size_t(f.tiles_y + 1) * kDiffCopies, s);
-    if (e != cudaSuccess) return e;
+    const int64_t ndiff = int64_t(f.tiles_x + 1) * int64_t(f.tiles_y + 1) * kDiffCopies;
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -272,7 +276,8 @@ cudaError_t launch_project(const qr_frame &f, const float *mean, const float *lo
     uint2 *rect = slot<uint2>(f, S_RECT);
     uint32_t *tcount = slot<uint32_t>(f, S_TCOUNT), *dkey = slot<uint32_t>(f, S_GKEY);
     project_cull<<<blocks, kThreads, 0, s>>>(n, mean, log_scale, opacity, cam, f.params.dilation,
-                                             f.params.alpha_min, rect, tcount, dkey, cand, counters);
+                                             f.params.alpha_min, rect, tcount, dkey, cand, vis, tsum,
+                                             diff, ndiff, counters);
     const unsigned grid = blocks < unsigned(sms) * 4u ? blocks : unsigned(sms) * 4u;
     project_exact<<<grid, kThreads, 0, s>>>(
         mean, log_scale, quat, opacity, cam, f.params.dilation, f.params.alpha_min,

@@ -5,17 +5,17 @@
 // touches it, ordered by (camera depth, id) -- the order a stable sort of
 // 64-bit (tile << 32 | depth) keys over id-ordered input gives.
 //
-// GB300 design (5 kernels after the projection, no global depth sort):
+// GB300 design (4 kernels after the projection, no global depth sort):
 //   1. the projection (K1) counts, per 256 consecutive ids, the kept
 //      Gaussians and the sum of their tile counts;
-//   2. offsets_scan + offsets_apply compact the kept Gaussians (id order) and
-//      give each its first output slot (exclusive scan), with the capacity
-//      check; offsets of kept Gaussians are strictly increasing (the
-//      projection has already added each kept Gaussian's tile rectangle to
-//      a 2-D difference array of per-tile counts: 4 atomics instead of one
-//      per intersection);
-//   3. tile_scan integrates the difference array into per-tile counts (in
-//      shared memory) and exclusive offsets, i.e. the tile ranges;
+//   2. bin_scan (one CTA) scans the per-256-id counts (first output slot of
+//      each kept Gaussian's block, totals, capacity check) and integrates the
+//      2-D difference array of per-tile counts that the projection filled
+//      (4 atomics per kept Gaussian instead of one per intersection) into
+//      per-tile counts and exclusive offsets, i.e. the tile ranges;
+//   3. offsets_apply compacts the kept Gaussians (id order) and gives each
+//      its first output slot; offsets of kept Gaussians are strictly
+//      increasing;
 //   4. expand_scatter: a load-balanced expansion -- each CTA owns 1024
 //      consecutive output slots, finds their owners with a warp-wide 32-way
 //      search (at most 1024 owners per chunk), derives each slot's tile from
@@ -38,30 +38,9 @@ namespace {
 constexpr int T = 256;
 constexpr int EMIT_CHUNK = 1024;
 constexpr int TS_CAP = 8192;             // keys a tile sorts in shared memory (64 KB)
-constexpr int kScanSmemTiles = 48 * 1024; // tile counts tile_scan integrates in shared memory
+constexpr int kScanSmemTiles = 48 * 1024; // tile counts bin_scan integrates in shared memory
 
 // ------------------------------------------------------------------ offsets
-// Exclusive scans of the per-CTA kept counts and tile-count sums.
-__global__ void __launch_bounds__(1024)
-offsets_scan(uint32_t *kept, uint32_t *tsum, int nblk, uint32_t *counters, uint32_t capacity) {
-    __shared__ uint32_t s_total[2];
-    cta_exclusive_scan(kept, nblk, &s_total[0]);
-    __syncthreads();
-    cta_exclusive_scan(tsum, nblk, &s_total[1]);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const uint32_t x = s_total[1];
-        counters[CNT_VISIBLE] = s_total[0];
-        counters[CNT_ISECT] = x;
-        if (x > capacity) {
-            counters[CNT_STATUS] = QR_ERR_CAPACITY;
-            counters[CNT_SORT_N] = 0;
-        } else {
-            counters[CNT_SORT_N] = x;
-        }
-    }
-}
-
 // Compacted kept ids (id order) and their first output slots.
 __global__ void __launch_bounds__(kProjectThreads)
 offsets_apply(const uint32_t *__restrict__ tcount, const uint32_t *__restrict__ kept_base,
@@ -142,21 +121,37 @@ __device__ __forceinline__ void slot_owner(const ExpandSmem &sm, uint32_t len, u
     tile = (ty0 + j / wx) * uint32_t(tiles_x) + tx0 + j % wx;
 }
 
-// Tile counts from the difference array (prefix sums along x, then y, one
-// CTA), then exclusive offsets -> ranges; the counts become zeroed cursors.
+// One CTA: exclusive scans of the per-256-id kept counts and tile sums (the
+// kept Gaussians' first output slots, totals, capacity check), then the tile
+// counts from the difference array (prefix sums along x, then y) and their
+// exclusive offsets, i.e. the tile ranges; the counts become zeroed cursors.
 // The counts are integrated in shared memory when the tile grid fits (up to
 // kScanSmemTiles tiles, e.g. 4K frames with 16x16 tiles), else in the cursor
 // array itself.  Rows are summed by one warp each (shuffle scans), columns by
 // one thread each.  Partial sums may be negative; the uint32 arithmetic is
 // exact modulo 2^32 and the integrated counts are not.
 __global__ void __launch_bounds__(1024)
-tile_scan(const int *__restrict__ diff, const uint32_t *__restrict__ counters, uint32_t *tcnt,
-          int tiles_x, int tiles_y, uint2 *ranges, int in_smem) {
+bin_scan(uint32_t *kept, uint32_t *tsum, int nblk, uint32_t *counters, uint32_t capacity,
+         const int *__restrict__ diff, uint32_t *tcnt, int tiles_x, int tiles_y, uint2 *ranges,
+         int in_smem) {
     extern __shared__ uint32_t s_cnt[];
     __shared__ uint32_t s_w[32];
+    __shared__ uint32_t s_total[2];
+    cta_exclusive_scan(kept, nblk, &s_total[0]);
+    __syncthreads();
+    cta_exclusive_scan(tsum, nblk, &s_total[1]);
+    __syncthreads();
+    const uint32_t isect = s_total[1];
+    const bool over = isect > capacity;
+    if (threadIdx.x == 0) {
+        counters[CNT_VISIBLE] = s_total[0];
+        counters[CNT_ISECT] = isect;
+        if (over) counters[CNT_STATUS] = QR_ERR_CAPACITY;
+        counters[CNT_SORT_N] = over ? 0u : isect;
+    }
     const int stride = tiles_x + 1;
     const int tiles = tiles_x * tiles_y;
-    if (counters[CNT_STATUS] != 0) {   // capacity exceeded: every tile list is empty
+    if (over) {   // capacity exceeded: every tile list is empty
         for (int t = threadIdx.x; t < tiles; t += blockDim.x) {
             ranges[t] = make_uint2(0u, 0u);
             tcnt[t] = 0u;
@@ -406,10 +401,12 @@ cudaError_t launch_sort(const qr_frame &f, cudaStream_t s) {
     uint2 *ranges = slot<uint2>(f, S_RANGES);
     uint32_t *tcnt = slot<uint32_t>(f, S_TCNT);
     int *diff = slot<int>(f, S_DIFF);
-    cudaError_t e = cudaMemsetAsync(tcnt, 0, sizeof(uint32_t) * size_t(tiles), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(ranges, 0, sizeof(uint2) * size_t(tiles), s);
-    if (e != cudaSuccess) return e;
-    if (f.n == 0) return cudaSuccess;
+    cudaError_t e;
+    if (f.n == 0) {   // nothing projected: empty tile lists
+        e = cudaMemsetAsync(tcnt, 0, sizeof(uint32_t) * size_t(tiles), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(ranges, 0, sizeof(uint2) * size_t(tiles), s);
+        return e;
+    }
     e = cudaFuncSetAttribute(tile_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              int(TS_CAP * sizeof(unsigned long long)));
     if (e != cudaSuccess) return e;
@@ -422,22 +419,21 @@ cudaError_t launch_sort(const qr_frame &f, cudaStream_t s) {
     uint32_t *kid = slot<uint32_t>(f, S_KID);
     uint32_t *koff = slot<uint32_t>(f, S_OFF);
     const uint2 *rect = slot<uint2>(f, S_RECT);
-    offsets_scan<<<1, 1024, 0, s>>>(kept, tsum, nblk, counters, uint32_t(f.max_isect));
-    offsets_apply<<<nblk, kProjectThreads, 0, s>>>(slot<uint32_t>(f, S_TCOUNT), kept, tsum, f.n,
-                                                   kid, koff);
     const int scan_smem = tiles <= kScanSmemTiles ? 1 : 0;
     const size_t scan_bytes = scan_smem ? sizeof(uint32_t) * size_t(tiles) : 0;
-    e = cudaFuncSetAttribute(tile_scan, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(bin_scan, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              int(sizeof(uint32_t) * kScanSmemTiles));
     if (e != cudaSuccess) return e;
-    tile_scan<<<1, 1024, scan_bytes, s>>>(diff, counters, tcnt, f.tiles_x, f.tiles_y, ranges,
-                                          scan_smem);
+    bin_scan<<<1, 1024, scan_bytes, s>>>(kept, tsum, nblk, counters, uint32_t(f.max_isect), diff,
+                                         tcnt, f.tiles_x, f.tiles_y, ranges, scan_smem);
+    offsets_apply<<<nblk, kProjectThreads, 0, s>>>(slot<uint32_t>(f, S_TCOUNT), kept, tsum, f.n,
+                                                   kid, koff);
     auto *keys = slot<unsigned long long>(f, S_KEYS64);
     expand_scatter<<<sms * 6, T, 0, s>>>(koff, kid, rect, slot<uint32_t>(f, S_GKEY), counters,
                                          f.tiles_x, ranges, tcnt, keys);
     tile_sort<<<tiles, T, TS_CAP * sizeof(unsigned long long), s>>>(
         ranges, keys, slot<unsigned long long>(f, S_SCRATCH64), slot<uint32_t>(f, S_IGID));
-    count_launch(5);
+    count_launch(4);
     return cudaGetLastError();
 }
 

@@ -20,7 +20,9 @@
 //      consecutive output slots, finds their owners with a warp-wide 32-way
 //      search (at most 1024 owners per chunk), derives each slot's tile from
 //      the owner's footprint rectangle, and writes (depth << 32 | id) into
-//      its tile's bucket at an atomically claimed position;
+//      its tile's bucket at an atomically claimed position (counted per tile
+//      in shared memory first, one global atomic per touched tile, when the
+//      grid has at most 4096 tiles);
 //   5. tile_sort: one CTA per tile sorts its bucket (bitonic network over the
 //      unique 64-bit keys) and writes the ids: buckets of up to 2048 keys in
 //      registers (register swaps, warp shuffles, shared memory only for the
@@ -39,6 +41,7 @@ constexpr int T = 256;
 constexpr int EMIT_CHUNK = 1024;
 constexpr int TS_CAP = 8192;             // keys a tile sorts in shared memory (64 KB)
 constexpr int kScanSmemTiles = 48 * 1024; // tile counts bin_scan integrates in shared memory
+constexpr int kAggTiles = 4096;           // tile grids whose bucket claims are aggregated per CTA
 
 // ------------------------------------------------------------------ offsets
 // Compacted kept ids (id order) and their first output slots.
@@ -200,32 +203,67 @@ bin_scan(uint32_t *kept, uint32_t *tsum, int nblk, uint32_t *counters, uint32_t 
     for (int t = threadIdx.x; t < tiles; t += blockDim.x) tcnt[t] = 0u;
 }
 
+// AGG: tile grids of at most kAggTiles tiles claim bucket positions per CTA:
+// shared-memory atomics count the chunk's slots per tile (and give each slot
+// its rank), then one global atomic per touched tile reserves the chunk's
+// run in the bucket.  Otherwise every warp claims with one global atomic per
+// distinct tile among its 32 slots.
+template <bool AGG>
 __global__ void __launch_bounds__(T)
 expand_scatter(const uint32_t *__restrict__ koff, const uint32_t *__restrict__ kid,
                const uint2 *__restrict__ rect, const uint32_t *__restrict__ gkey,
-               const uint32_t *__restrict__ counters, int tiles_x,
+               const uint32_t *__restrict__ counters, int tiles_x, int tiles,
                const uint2 *__restrict__ ranges, uint32_t *__restrict__ cursor,
                unsigned long long *__restrict__ keys) {
     __shared__ ExpandSmem sm;
+    extern __shared__ uint32_t s_agg[];   // AGG: [tiles] counts, [tiles] run bases
     const uint32_t X = counters[CNT_SORT_N];
     const uint32_t nk = counters[CNT_VISIBLE];
     const int lane = threadIdx.x & 31;
+    constexpr int PER = EMIT_CHUNK / T;
     for (uint32_t o0 = blockIdx.x * uint32_t(EMIT_CHUNK); o0 < X; o0 += gridDim.x * uint32_t(EMIT_CHUNK)) {
         const uint32_t o1 = min(X, o0 + uint32_t(EMIT_CHUNK));
-        const uint32_t len = stage_owners(sm, koff, kid, rect, nk, o0, o1);
-        for (uint32_t base = o0; base < o1; base += T) {
-            const uint32_t o = base + threadIdx.x;
-            uint32_t g = 0, tile = 0xFFFFFFFFu;
-            if (o < o1) slot_owner(sm, len, o, tiles_x, g, tile);
-            const unsigned peers = __match_any_sync(0xffffffffu, tile);
-            const int leader = __ffs(peers) - 1;
-            uint32_t pos = 0;
-            if (o < o1 && lane == leader) pos = atomicAdd(&cursor[tile], uint32_t(__popc(peers)));
-            pos = __shfl_sync(0xffffffffu, pos, leader);
-            if (o < o1) {
-                const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
-                keys[ranges[tile].x + pos + rank] =
-                    (static_cast<unsigned long long>(gkey[g]) << 32) | g;
+        if (AGG)
+            for (int t = threadIdx.x; t < tiles; t += T) s_agg[t] = 0u;
+        const uint32_t len = stage_owners(sm, koff, kid, rect, nk, o0, o1);   // ends with a barrier
+        if (AGG) {
+            uint32_t tl[PER], gg[PER], rk[PER];
+#pragma unroll
+            for (int k = 0; k < PER; ++k) {
+                const uint32_t o = o0 + threadIdx.x + k * T;
+                tl[k] = 0xFFFFFFFFu;
+                if (o < o1) {
+                    slot_owner(sm, len, o, tiles_x, gg[k], tl[k]);
+                    rk[k] = atomicAdd(&s_agg[tl[k]], 1u);
+                }
+            }
+            __syncthreads();
+            for (int t = threadIdx.x; t < tiles; t += T) {
+                const uint32_t c = s_agg[t];
+                if (c) s_agg[tiles + t] = atomicAdd(&cursor[t], c);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < PER; ++k) {
+                if (tl[k] == 0xFFFFFFFFu) continue;
+                keys[ranges[tl[k]].x + s_agg[tiles + tl[k]] + rk[k]] =
+                    (static_cast<unsigned long long>(gkey[gg[k]]) << 32) | gg[k];
+            }
+        } else {
+            for (uint32_t base = o0; base < o1; base += T) {
+                const uint32_t o = base + threadIdx.x;
+                uint32_t g = 0, tile = 0xFFFFFFFFu;
+                if (o < o1) slot_owner(sm, len, o, tiles_x, g, tile);
+                const unsigned peers = __match_any_sync(0xffffffffu, tile);
+                const int leader = __ffs(peers) - 1;
+                uint32_t pos = 0;
+                if (o < o1 && lane == leader) pos = atomicAdd(&cursor[tile], uint32_t(__popc(peers)));
+                pos = __shfl_sync(0xffffffffu, pos, leader);
+                if (o < o1) {
+                    const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
+                    keys[ranges[tile].x + pos + rank] =
+                        (static_cast<unsigned long long>(gkey[g]) << 32) | g;
+                }
             }
         }
         __syncthreads();
@@ -429,8 +467,17 @@ cudaError_t launch_sort(const qr_frame &f, cudaStream_t s) {
     offsets_apply<<<nblk, kProjectThreads, 0, s>>>(slot<uint32_t>(f, S_TCOUNT), kept, tsum, f.n,
                                                    kid, koff);
     auto *keys = slot<unsigned long long>(f, S_KEYS64);
-    expand_scatter<<<sms * 6, T, 0, s>>>(koff, kid, rect, slot<uint32_t>(f, S_GKEY), counters,
-                                         f.tiles_x, ranges, tcnt, keys);
+    if (tiles <= kAggTiles) {
+        const size_t agg = sizeof(uint32_t) * 2 * size_t(tiles);
+        e = cudaFuncSetAttribute(expand_scatter<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 int(sizeof(uint32_t) * 2 * kAggTiles));
+        if (e != cudaSuccess) return e;
+        expand_scatter<true><<<sms * 4, T, agg, s>>>(koff, kid, rect, slot<uint32_t>(f, S_GKEY),
+                                                     counters, f.tiles_x, tiles, ranges, tcnt, keys);
+    } else {
+        expand_scatter<false><<<sms * 6, T, 0, s>>>(koff, kid, rect, slot<uint32_t>(f, S_GKEY),
+                                                    counters, f.tiles_x, tiles, ranges, tcnt, keys);
+    }
     tile_sort<<<tiles, T, TS_CAP * sizeof(unsigned long long), s>>>(
         ranges, keys, slot<unsigned long long>(f, S_SCRATCH64), slot<uint32_t>(f, S_IGID));
     count_launch(4);

@@ -56,6 +56,26 @@ def _dist():
     return ws, rank, local
 
 
+def max_over_ranks(values, ws, device=None):
+    """Element-wise maximum over all ranks of this rank's timings (ms): the
+    job is as slow as its slowest rank."""
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64)
+    if ws > 1:
+        import torch.distributed as dist
+        if device is not None:
+            t = t.to(device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t = t.cpu()
+    return [float(x) for x in t]
+
+
+def whole_job_rate(ws, ms_per_step):
+    """Frames per second of the whole job when every rank renders one frame per
+    step (weak scaling: the per-rank work is fixed as ranks are added)."""
+    return ws * 1000.0 / ms_per_step
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -298,6 +318,7 @@ def run_gpu(args, ws, rank, local):
 
     # ---- end to end through the host-buffer C-ABI call
     e2e = None
+    e2e_ms = None
     try:
         nin, nout = q.qr_render_host_bytes(N_GAUSS, WIDTH, HEIGHT, K, C, q.QR_F32)
         din = torch.empty(nin + 256, dtype=torch.uint8, device=dev)
@@ -328,21 +349,17 @@ def run_gpu(args, ws, rank, local):
         e1.record()
         torch.cuda.synchronize()
         e2e_ms = e0.elapsed_time(e1) / ne
-        h2d = N_GAUSS * 11 * 4 + N_GAUSS * C * 4
-        d2h = P * C * 4
-        e2e = {"value": round(ws * 1000.0 / e2e_ms, 3), "unit": "frames/s",
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
     except Exception as exc:  # noqa: BLE001
         print(f"# e2e failed: {exc}", file=sys.stderr)
 
-    # ---- max over ranks
-    t_local = torch.tensor([step_ms, eager_ms, blend_ms, dense_ms], dtype=torch.float64)
-    if ws > 1:
-        import torch.distributed as dist
-        tt = t_local.to(dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_local = tt.cpu()
-    step_ms, eager_ms, blend_ms, dense_ms = [float(x) for x in t_local]
+    # ---- max over ranks (a rank whose e2e leg failed reports -1)
+    step_ms, eager_ms, blend_ms, dense_ms, e2e_max = max_over_ranks(
+        [step_ms, eager_ms, blend_ms, dense_ms, e2e_ms if e2e_ms is not None else -1.0], ws, dev)
+    e2e_fail = max_over_ranks([0.0 if e2e_ms is not None else 1.0], ws, dev)[0] > 0
+    if not e2e_fail:
+        e2e = {"value": round(whole_job_rate(ws, e2e_max), 3), "unit": "frames/s",
+               "h2d_bytes_per_step": N_GAUSS * 11 * 4 + N_GAUSS * C * 4,
+               "d2h_bytes_per_step": P * C * 4}
 
     hbm_peak, peak_src = _peaks()
     alg_bytes = U * C * 4 + P * K * 8 + P + P * C * 4
@@ -350,11 +367,11 @@ def run_gpu(args, ws, rank, local):
     traffic = _traffic_from_profile()
     clocks = clk.summary()
     return {
-        "value": round(ws * 1000.0 / step_ms, 3),
+        "value": round(whole_job_rate(ws, step_ms), 3),
         "ms_per_step": round(step_ms, 4),
         "eager_ms_per_step": round(eager_ms, 4),
         "graph_ms_per_step": round(graph_ms, 4) if graph_ms else None,
-        "dense_fps": round(ws * 1000.0 / dense_ms, 3),
+        "dense_fps": round(whole_job_rate(ws, dense_ms), 3),
         "speedup_vs_dense": round(dense_ms / step_ms, 3),
         "per_k_fps": per_k,
         "stages_ms": {"project+sort": round(float(stage_ms[0]), 4),

@@ -173,6 +173,50 @@ def test_large_tile_lists_use_the_merge_path():
                   label="big tiles")
 
 
+def _slab_scene(n, seed=11):
+    """A thin slab of small Gaussians right in front of a 48x48 camera: the
+    central tiles see nearly all of them."""
+    rng = np.random.default_rng(seed)
+    mean = np.stack([rng.uniform(-0.2, 0.2, n), rng.uniform(-0.2, 0.2, n),
+                     rng.uniform(-0.5, 0.5, n)], 1).astype(np.float32)
+    g = scenes.Gaussians(mean, np.full((n, 3), -2.0, np.float32),
+                         np.tile(np.array([1, 0, 0, 0], np.float32), (n, 1)),
+                         np.full(n, 0.05, np.float32))
+    return g, rng.normal(size=(n, 16)).astype(np.float32)
+
+
+@pytest.mark.parametrize("n,lo,hi", [(200, 1, 256), (420, 257, 512), (900, 513, 1024),
+                                     (1800, 1025, 2048), (5000, 2049, 8192)])
+def test_tile_sort_size_classes(n, lo, hi):
+    """Each size class of the per-tile sort (registers with 1, 2, 4, 8 keys
+    per thread; shared memory up to 8192 keys) orders its bucket by
+    (FP32 depth, id) and keeps every intersection exactly once."""
+    g, f = _slab_scene(n)
+    cam = scenes.tiny_camera(48, 48)
+    gpu = H.run_gpu(g, f, cam, K=8)
+    fr = gpu["frame"]
+    from paper_2512_20927_gb300 import qrender as q
+    import torch
+    v = q.qr_frame_view_get(fr)
+    tiles = fr.frame.tiles_x * fr.frame.tiles_y
+    rngs = _device_copy(v.tile_range, 2 * tiles, torch.int32).cpu().numpy().reshape(tiles, 2)
+    sizes = rngs[:, 1] - rngs[:, 0]
+    assert lo <= sizes.max() <= hi, sizes
+    gkey = _device_copy(v.depth_key, n, torch.int32).cpu().numpy().view(np.uint32)
+    tcount = _device_copy(v.tile_count, n, torch.int32).cpu().numpy()
+    gids = _device_copy(v.isect_gid, gpu["n_isect"], torch.int32).cpu().numpy()
+    np.testing.assert_array_equal(np.bincount(gids, minlength=n), tcount)
+    for t in range(tiles):
+        a, b = rngs[t]
+        assert len(set(gids[a:b].tolist())) == b - a
+        order = np.lexsort((gids[a:b], gkey.view(np.float32)[gids[a:b]]))
+        np.testing.assert_array_equal(order, np.arange(b - a))
+    pix = H.sample_pixels(48, 48, 120, seed=5)
+    pr, pix, ref = H.run_oracle(g, f, cam, 8, pixels=pix)
+    H.check_frame(gpu, ref, pix, cam.width, f, FEAT_TOL, DENSE_TOL, max_tie_frac=0.6,
+                  label=f"slab {n}")
+
+
 @pytest.mark.parametrize("C", [16, 64, 512])
 def test_blend_stage_matches_definition(C):
     import torch

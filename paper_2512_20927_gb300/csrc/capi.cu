@@ -70,6 +70,7 @@ size_t layout(int64_t n, int W, int H, const qr_params *p, int64_t cap, size_t *
     sizes[S_SCRATCH64] = X * 8;
     sizes[S_IGID] = X * 4;
     sizes[S_DIFF] = size_t(tx + 1) * size_t(ty + 1) * 4 * kDiffCopies;
+    sizes[S_CHUNK] = (X / kEmitChunk + 2) * 4;
     size_t o = 0;
     for (int s = 0; s < S_END; ++s) {
         if (off) off[s] = o;

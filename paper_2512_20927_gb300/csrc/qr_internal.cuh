@@ -21,12 +21,16 @@ enum { CNT_STATUS = 0, CNT_ISECT = 1, CNT_VISIBLE = 2, CNT_N = 3, CNT_SORT_N = 4
 enum Slot {
     S_COUNTERS = 0, S_REC_M, S_REC_C, S_REC_A, S_REC_H, S_RECT, S_TCOUNT, S_GKEY,
     S_VISCNT, S_BSUM, S_KID, S_OFF, S_TCNT, S_RANGES, S_KEYS64, S_SCRATCH64, S_IGID, S_DIFF,
+    S_CHUNK,
     S_END
 };
 constexpr int kProjectThreads = 256;
 // Copies of the 2-D difference array of per-tile counts; CTA b adds into copy
 // b % kDiffCopies, which spreads the atomics on its hot corners.
 constexpr int kDiffCopies = 8;
+// Output slots per expansion chunk (the binning records the owner of each
+// chunk's first slot).
+constexpr int kEmitChunk = 1024;
 static_assert(S_END <= QR_FRAME_SLOTS, "too many workspace slots");
 
 constexpr int kSortThreads = 256;
@@ -138,6 +142,37 @@ __device__ __forceinline__ void cta_exclusive_scan(uint32_t *data, int total, ui
         carry += chunk;
     }
     if (sum_out && threadIdx.x == 0) *sum_out = carry;
+}
+
+// Two independent inclusive scans in one pass (x and y of one uint2 per
+// thread); s_w holds 64 words.
+__device__ __forceinline__ uint2 block_inclusive_scan2(uint2 v, uint32_t *s_w, uint2 &total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint2 x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t a = __shfl_up_sync(0xffffffffu, x.x, o);
+        const uint32_t b = __shfl_up_sync(0xffffffffu, x.y, o);
+        if (lane >= o) { x.x += a; x.y += b; }
+    }
+    if (lane == 31) { s_w[warp] = x.x; s_w[32 + warp] = x.y; }
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t a = (lane < nw) ? s_w[lane] : 0u, b = (lane < nw) ? s_w[32 + lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t ya = __shfl_up_sync(0xffffffffu, a, o);
+            const uint32_t yb = __shfl_up_sync(0xffffffffu, b, o);
+            if (lane >= o) { a += ya; b += yb; }
+        }
+        s_w[lane] = a;
+        s_w[32 + lane] = b;
+    }
+    __syncthreads();
+    const uint2 r = make_uint2(x.x + (warp > 0 ? s_w[warp - 1] : 0u), x.y + (warp > 0 ? s_w[32 + warp - 1] : 0u));
+    total = make_uint2(s_w[nw - 1], s_w[32 + nw - 1]);
+    __syncthreads();
+    return r;
 }
 
 // ---------------------------------------------------------------- per-pixel Gaussian

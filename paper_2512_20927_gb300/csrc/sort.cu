@@ -17,8 +17,9 @@
 //      its first output slot; offsets of kept Gaussians are strictly
 //      increasing;
 //   4. expand_scatter: a load-balanced expansion -- each CTA owns 1024
-//      consecutive output slots, finds their owners with a warp-wide 32-way
-//      search (at most 1024 owners per chunk), derives each slot's tile from
+//      consecutive output slots, stages their owners (the kept Gaussians from
+//      the owner of the chunk's first slot, which offsets_apply recorded, to
+//      the owner of the next chunk's first slot), derives each slot's tile from
 //      the owner's footprint rectangle, and writes (depth << 32 | id) into
 //      its tile's bucket at an atomically claimed position (counted per tile
 //      in shared memory first, one global atomic per touched tile, when the
@@ -38,17 +39,20 @@ namespace qr {
 namespace {
 
 constexpr int T = 256;
-constexpr int EMIT_CHUNK = 1024;
+constexpr int EMIT_CHUNK = kEmitChunk;
 constexpr int TS_CAP = 8192;             // keys a tile sorts in shared memory (64 KB)
 constexpr int kScanSmemTiles = 48 * 1024; // tile counts bin_scan integrates in shared memory
 constexpr int kAggTiles = 4096;           // tile grids whose bucket claims are aggregated per CTA
 
 // ------------------------------------------------------------------ offsets
 // Compacted kept ids (id order) and their first output slots.
+// It also records, for every expansion chunk, the kept index that owns the
+// chunk's first slot (chunks past `nchunk` -- a capacity overflow -- are
+// not recorded; the expansion then has nothing to do).
 __global__ void __launch_bounds__(kProjectThreads)
 offsets_apply(const uint32_t *__restrict__ tcount, const uint32_t *__restrict__ kept_base,
               const uint32_t *__restrict__ tsum_base, int64_t n, uint32_t *__restrict__ kid,
-              uint32_t *__restrict__ koff) {
+              uint32_t *__restrict__ koff, uint32_t *__restrict__ chunk_owner, uint32_t nchunk) {
     __shared__ uint32_t s_w[32];
     const int64_t g = int64_t(blockIdx.x) * kProjectThreads + threadIdx.x;
     const uint32_t c = g < n ? tcount[g] : 0u;
@@ -58,52 +62,33 @@ offsets_apply(const uint32_t *__restrict__ tcount, const uint32_t *__restrict__ 
     const uint32_t cinc = block_inclusive_scan(c, s_w, tot);
     if (k) {
         const uint32_t slot = kept_base[blockIdx.x] + kinc - 1u;
+        const uint32_t a = tsum_base[blockIdx.x] + cinc - c;
         kid[slot] = uint32_t(g);
-        koff[slot] = tsum_base[blockIdx.x] + cinc - c;
+        koff[slot] = a;
+        for (uint32_t ch = (a + EMIT_CHUNK - 1) / EMIT_CHUNK; ch < nchunk && ch * EMIT_CHUNK < a + c; ++ch)
+            chunk_owner[ch] = slot;
     }
 }
 
-// Last index s in [0, n) with off[s] <= target (off[0] == 0 <= target), by
-// one warp with 32-way splits: the owner of output slot `target`.
-__device__ __forceinline__ uint32_t warp_upper_index(const uint32_t *off, uint32_t n, uint32_t target) {
-    const int lane = threadIdx.x & 31;
-    uint32_t lo = 0, hi = n;
-    while (hi - lo > 32) {
-        const uint32_t step = (hi - lo + 31) / 32;
-        const uint32_t pos = lo + lane * step;
-        const bool le = pos < hi && off[pos] <= target;
-        const int k = __popc(__ballot_sync(0xffffffffu, le));
-        lo = lo + (k - 1) * step;
-        hi = min(hi, lo + step);
-    }
-    const uint32_t pos = lo + lane;
-    const bool le = pos < hi && off[pos] <= target;
-    return lo + __popc(__ballot_sync(0xffffffffu, le)) - 1;
-}
-
-// Owners of the slots [o0, o1) staged in shared memory (every kept Gaussian
-// owns at least one slot, so a chunk has at most EMIT_CHUNK owners).
+// Owners of the slots [o0, o1) staged in shared memory: kept indices s0 (the
+// owner of o0, recorded by offsets_apply) .. s1 (the owner of the next
+// chunk's first slot, or the last kept Gaussian), at most EMIT_CHUNK + 1.
 struct ExpandSmem {
-    uint32_t off[EMIT_CHUNK];
-    uint32_t gid[EMIT_CHUNK];
-    uint2 rect[EMIT_CHUNK];
-    uint32_t range[2];
+    uint32_t off[EMIT_CHUNK + 1];
+    uint32_t gid[EMIT_CHUNK + 1];
+    uint32_t key[EMIT_CHUNK + 1];
+    uint2 rect[EMIT_CHUNK + 1];
 };
 
 __device__ __forceinline__ uint32_t stage_owners(ExpandSmem &sm, const uint32_t *koff,
                                                  const uint32_t *kid, const uint2 *rect,
-                                                 uint32_t nk, uint32_t o0, uint32_t o1) {
-    if (threadIdx.x < 32) {
-        const uint32_t s0 = warp_upper_index(koff, nk, o0);
-        const uint32_t s1 = warp_upper_index(koff, nk, o1 - 1);
-        if (threadIdx.x == 0) { sm.range[0] = s0; sm.range[1] = s1; }
-    }
-    __syncthreads();
-    const uint32_t s0 = sm.range[0], len = sm.range[1] - sm.range[0] + 1;   // <= o1 - o0
+                                                 const uint32_t *gkey, uint32_t s0, uint32_t s1) {
+    const uint32_t len = s1 - s0 + 1;
     for (uint32_t i = threadIdx.x; i < len; i += T) {
         const uint32_t g = kid[s0 + i];
         sm.off[i] = koff[s0 + i];
         sm.gid[i] = g;
+        sm.key[i] = gkey[g];
         sm.rect[i] = rect[g];
     }
     __syncthreads();
@@ -111,7 +96,8 @@ __device__ __forceinline__ uint32_t stage_owners(ExpandSmem &sm, const uint32_t 
 }
 
 __device__ __forceinline__ void slot_owner(const ExpandSmem &sm, uint32_t len, uint32_t o,
-                                           int tiles_x, uint32_t &g, uint32_t &tile) {
+                                           int tiles_x, uint32_t &g, uint32_t &tile,
+                                           uint32_t &key) {
     uint32_t lo = 0, hi = len;
     while (hi - lo > 1) {
         const uint32_t mid = (lo + hi) >> 1;
@@ -121,6 +107,7 @@ __device__ __forceinline__ void slot_owner(const ExpandSmem &sm, uint32_t len, u
     const uint32_t tx0 = rc.x & 0xFFFFu, ty0 = rc.x >> 16, tx1 = rc.y & 0xFFFFu;
     const uint32_t wx = tx1 - tx0 + 1, j = o - sm.off[lo];
     g = sm.gid[lo];
+    key = sm.key[lo];
     tile = (ty0 + j / wx) * uint32_t(tiles_x) + tx0 + j % wx;
 }
 
@@ -138,16 +125,32 @@ bin_scan(uint32_t *kept, uint32_t *tsum, int nblk, uint32_t *counters, uint32_t 
          const int *__restrict__ diff, uint32_t *tcnt, int tiles_x, int tiles_y, uint2 *ranges,
          int in_smem) {
     extern __shared__ uint32_t s_cnt[];
-    __shared__ uint32_t s_w[32];
-    __shared__ uint32_t s_total[2];
-    cta_exclusive_scan(kept, nblk, &s_total[0]);
-    __syncthreads();
-    cta_exclusive_scan(tsum, nblk, &s_total[1]);
-    __syncthreads();
-    const uint32_t isect = s_total[1];
+    __shared__ uint32_t s_w[64];
+    // both per-block scans in one pass, each thread owning `per` consecutive blocks
+    const int per = (nblk + int(blockDim.x) - 1) / int(blockDim.x);
+    const int b0 = int(threadIdx.x) * per;
+    uint2 own = make_uint2(0u, 0u);
+    for (int i = 0; i < per; ++i) {
+        const int bb = b0 + i;
+        if (bb < nblk) { own.x += kept[bb]; own.y += tsum[bb]; }
+    }
+    uint2 tot;
+    const uint2 inc = block_inclusive_scan2(own, s_w, tot);
+    uint2 ex = make_uint2(inc.x - own.x, inc.y - own.y);
+    for (int i = 0; i < per; ++i) {
+        const int bb = b0 + i;
+        if (bb < nblk) {
+            const uint32_t k = kept[bb], t = tsum[bb];
+            kept[bb] = ex.x;
+            tsum[bb] = ex.y;
+            ex.x += k;
+            ex.y += t;
+        }
+    }
+    const uint32_t isect = tot.y;
     const bool over = isect > capacity;
     if (threadIdx.x == 0) {
-        counters[CNT_VISIBLE] = s_total[0];
+        counters[CNT_VISIBLE] = tot.x;
         counters[CNT_ISECT] = isect;
         if (over) counters[CNT_STATUS] = QR_ERR_CAPACITY;
         counters[CNT_SORT_N] = over ? 0u : isect;
@@ -212,48 +215,51 @@ template <bool AGG>
 __global__ void __launch_bounds__(T)
 expand_scatter(const uint32_t *__restrict__ koff, const uint32_t *__restrict__ kid,
                const uint2 *__restrict__ rect, const uint32_t *__restrict__ gkey,
-               const uint32_t *__restrict__ counters, int tiles_x, int tiles,
-               const uint2 *__restrict__ ranges, uint32_t *__restrict__ cursor,
-               unsigned long long *__restrict__ keys) {
+               const uint32_t *__restrict__ chunk_owner, const uint32_t *__restrict__ counters,
+               int tiles_x, int tiles, const uint2 *__restrict__ ranges,
+               uint32_t *__restrict__ cursor, unsigned long long *__restrict__ keys) {
     __shared__ ExpandSmem sm;
     extern __shared__ uint32_t s_agg[];   // AGG: [tiles] counts, [tiles] run bases
     const uint32_t X = counters[CNT_SORT_N];
     const uint32_t nk = counters[CNT_VISIBLE];
     const int lane = threadIdx.x & 31;
     constexpr int PER = EMIT_CHUNK / T;
-    for (uint32_t o0 = blockIdx.x * uint32_t(EMIT_CHUNK); o0 < X; o0 += gridDim.x * uint32_t(EMIT_CHUNK)) {
+    for (uint32_t c = blockIdx.x; c * uint32_t(EMIT_CHUNK) < X; c += gridDim.x) {
+        const uint32_t o0 = c * uint32_t(EMIT_CHUNK);
         const uint32_t o1 = min(X, o0 + uint32_t(EMIT_CHUNK));
         if (AGG)
             for (int t = threadIdx.x; t < tiles; t += T) s_agg[t] = 0u;
-        const uint32_t len = stage_owners(sm, koff, kid, rect, nk, o0, o1);   // ends with a barrier
+        const uint32_t s0 = chunk_owner[c];
+        const uint32_t s1 = o1 < X ? chunk_owner[c + 1] : nk - 1u;
+        const uint32_t len = stage_owners(sm, koff, kid, rect, gkey, s0, s1);   // ends with a barrier
         if (AGG) {
-            uint32_t tl[PER], gg[PER], rk[PER];
+            uint32_t tl[PER], gg[PER], kk[PER], rk[PER];
 #pragma unroll
             for (int k = 0; k < PER; ++k) {
                 const uint32_t o = o0 + threadIdx.x + k * T;
                 tl[k] = 0xFFFFFFFFu;
                 if (o < o1) {
-                    slot_owner(sm, len, o, tiles_x, gg[k], tl[k]);
+                    slot_owner(sm, len, o, tiles_x, gg[k], tl[k], kk[k]);
                     rk[k] = atomicAdd(&s_agg[tl[k]], 1u);
                 }
             }
             __syncthreads();
             for (int t = threadIdx.x; t < tiles; t += T) {
-                const uint32_t c = s_agg[t];
-                if (c) s_agg[tiles + t] = atomicAdd(&cursor[t], c);
+                const uint32_t cnt = s_agg[t];
+                if (cnt) s_agg[tiles + t] = atomicAdd(&cursor[t], cnt);
             }
             __syncthreads();
 #pragma unroll
             for (int k = 0; k < PER; ++k) {
                 if (tl[k] == 0xFFFFFFFFu) continue;
                 keys[ranges[tl[k]].x + s_agg[tiles + tl[k]] + rk[k]] =
-                    (static_cast<unsigned long long>(gkey[gg[k]]) << 32) | gg[k];
+                    (static_cast<unsigned long long>(kk[k]) << 32) | gg[k];
             }
         } else {
             for (uint32_t base = o0; base < o1; base += T) {
                 const uint32_t o = base + threadIdx.x;
-                uint32_t g = 0, tile = 0xFFFFFFFFu;
-                if (o < o1) slot_owner(sm, len, o, tiles_x, g, tile);
+                uint32_t g = 0, tile = 0xFFFFFFFFu, key = 0;
+                if (o < o1) slot_owner(sm, len, o, tiles_x, g, tile, key);
                 const unsigned peers = __match_any_sync(0xffffffffu, tile);
                 const int leader = __ffs(peers) - 1;
                 uint32_t pos = 0;
@@ -261,8 +267,7 @@ expand_scatter(const uint32_t *__restrict__ koff, const uint32_t *__restrict__ k
                 pos = __shfl_sync(0xffffffffu, pos, leader);
                 if (o < o1) {
                     const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
-                    keys[ranges[tile].x + pos + rank] =
-                        (static_cast<unsigned long long>(gkey[g]) << 32) | g;
+                    keys[ranges[tile].x + pos + rank] = (static_cast<unsigned long long>(key) << 32) | g;
                 }
             }
         }
@@ -464,8 +469,10 @@ cudaError_t launch_sort(const qr_frame &f, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     bin_scan<<<1, 1024, scan_bytes, s>>>(kept, tsum, nblk, counters, uint32_t(f.max_isect), diff,
                                          tcnt, f.tiles_x, f.tiles_y, ranges, scan_smem);
+    uint32_t *chunk_owner = slot<uint32_t>(f, S_CHUNK);
+    const uint32_t nchunk = uint32_t(f.max_isect / EMIT_CHUNK + 1);
     offsets_apply<<<nblk, kProjectThreads, 0, s>>>(slot<uint32_t>(f, S_TCOUNT), kept, tsum, f.n,
-                                                   kid, koff);
+                                                   kid, koff, chunk_owner, nchunk);
     auto *keys = slot<unsigned long long>(f, S_KEYS64);
     if (tiles <= kAggTiles) {
         const size_t agg = sizeof(uint32_t) * 2 * size_t(tiles);
@@ -473,10 +480,12 @@ cudaError_t launch_sort(const qr_frame &f, cudaStream_t s) {
                                  int(sizeof(uint32_t) * 2 * kAggTiles));
         if (e != cudaSuccess) return e;
         expand_scatter<true><<<sms * 4, T, agg, s>>>(koff, kid, rect, slot<uint32_t>(f, S_GKEY),
-                                                     counters, f.tiles_x, tiles, ranges, tcnt, keys);
+                                                     chunk_owner, counters, f.tiles_x, tiles,
+                                                     ranges, tcnt, keys);
     } else {
         expand_scatter<false><<<sms * 6, T, 0, s>>>(koff, kid, rect, slot<uint32_t>(f, S_GKEY),
-                                                    counters, f.tiles_x, tiles, ranges, tcnt, keys);
+                                                    chunk_owner, counters, f.tiles_x, tiles,
+                                                    ranges, tcnt, keys);
     }
     tile_sort<<<tiles, T, TS_CAP * sizeof(unsigned long long), s>>>(
         ranges, keys, slot<unsigned long long>(f, S_SCRATCH64), slot<uint32_t>(f, S_IGID));

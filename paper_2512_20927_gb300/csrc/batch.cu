@@ -7,10 +7,12 @@
 // (view, tile) work items from one atomic counter, so views of very different
 // sizes balance without a host round trip.  For each tile:
 //   1. selection (thread per pixel): the tile's depth-ordered list is staged
-//      through shared memory 256 entries at a time and every pixel walks it
-//      with the same alpha' evaluation and the same Algorithm 1 rule as
-//      qr_select; the kept ids and normalised weights stay in shared memory
-//      (and are also written out for a backward pass);
+//      through shared memory 256 entries at a time; each warp culls the
+//      staged entries against its box of pixel centres and walks only the
+//      survivors, four per step, with the same alpha' evaluation and the same
+//      Algorithm 1 rule as qr_select; the kept ids and normalised weights
+//      stay in shared memory and are also written out (coalesced tile-row
+//      runs) for a backward pass;
 //   2. blend (warp per 2x2 / 2x1 pixel group, like qr_blend): equal ids of the
 //      group are merged with __match_any_sync, the group's weights of each
 //      distinct row are gathered into a per-warp shared-memory table, each
@@ -97,7 +99,7 @@ __device__ __forceinline__ void st_cs(float4 *p, float4 v) {
                  :: "l"(p), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w) : "memory");
 }
 
-// Dynamic shared memory: s_ids [K][256] int32, s_w [K][256] float.
+// Dynamic shared memory: s_ids [256][K|1] int32, s_w [256][K|1] float.
 template <int DT, int VPL, int G>
 __global__ void __launch_bounds__(T)
 batch_kernel(const BatchView *__restrict__ views, int n_views, uint32_t total_items,
@@ -111,6 +113,7 @@ batch_kernel(const BatchView *__restrict__ views, int n_views, uint32_t total_it
     __shared__ float s_h[T];
     __shared__ uint32_t s_g[T];
     __shared__ uint32_t s_item;
+    __shared__ uint8_t s_cnt[T];
     __shared__ __align__(16) float s_tw[T / 32][32][G];   // per-warp row-weight table
     __shared__ int s_tid[T / 32][32];
     extern __shared__ unsigned char s_dyn[];
@@ -130,72 +133,115 @@ batch_kernel(const BatchView *__restrict__ views, int n_views, uint32_t total_it
         }
         const BatchView &V = views[v];
         const int K = V.K;
-        int32_t *s_ids = reinterpret_cast<int32_t *>(s_dyn);
-        float *s_w = reinterpret_cast<float *>(s_dyn) + K * T;
+        const int KS = K | 1;   // odd stride: per-pixel slots fall in distinct banks
+        int32_t *s_ids = reinterpret_cast<int32_t *>(s_dyn);          // [256][KS]
+        float *s_w = reinterpret_cast<float *>(s_dyn) + KS * T;       // [256][KS]
         const int tile = int(item - V.tile_base);
         const int tx = tile % V.tiles_x, ty = tile / V.tiles_x;
         const int tile_w = V.tile_w, tile_h = T / tile_w;
 
         // ---------------- 1. selection (thread per pixel)
         {
-            const int px = tx * tile_w + int(threadIdx.x) % tile_w;
-            const int py = ty * tile_h + int(threadIdx.x) / tile_w;
+            constexpr unsigned FULL = 0xffffffffu;
+            const int lane = threadIdx.x & 31;
+            const int lx = int(threadIdx.x) % tile_w, ly = int(threadIdx.x) / tile_w;
+            const int px = tx * tile_w + lx, py = ty * tile_h + ly;
             const bool inside = px < V.W && py < V.H;
             const float ux = float(px) + 0.5f, uy = float(py) + 0.5f;
             const uint2 range = V.ranges[tile];
             const float tau_stop = __fdiv_rn(1.0f, float(K + 1));
-            float Tr = 1.0f, TQ = 1.0f;
-            int k = 0, m = 0;
-            float thr = __fdiv_rn(float(K), float(K + 1));
-            bool done = !inside;
+            Walk wk{1.0f, 1.0f, __fdiv_rn(float(K), float(K + 1)), 0, 0, !inside};
+            // the warp's box of pixel centres
+            float bx0 = ux, bx1 = ux, by0 = uy, by1 = uy;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                bx0 = fminf(bx0, __shfl_xor_sync(FULL, bx0, o));
+                bx1 = fmaxf(bx1, __shfl_xor_sync(FULL, bx1, o));
+                by0 = fminf(by0, __shfl_xor_sync(FULL, by0, o));
+                by1 = fmaxf(by1, __shfl_xor_sync(FULL, by1, o));
+            }
+            uint32_t gnext = range.x + threadIdx.x < range.y ? V.igid[range.x + threadIdx.x] : 0u;
             for (uint32_t b = range.x; b < range.y; b += T) {
-                if (__syncthreads_count(done) == T) break;
-                const uint32_t idx = b + threadIdx.x;
-                if (idx < range.y) {
-                    const uint32_t g = V.igid[idx];
-                    s_g[threadIdx.x] = g;
-                    s_m[threadIdx.x] = V.rec_m[g];
-                    s_c[threadIdx.x] = V.rec_w[g];
-                    s_a[threadIdx.x] = V.rec_a[g];
-                    s_h[threadIdx.x] = V.rec_h[g];
+                if (__syncthreads_count(wk.done) == T) break;
+                if (b + threadIdx.x < range.y) {
+                    s_g[threadIdx.x] = gnext;
+                    s_m[threadIdx.x] = V.rec_m[gnext];
+                    s_c[threadIdx.x] = V.rec_w[gnext];
+                    s_a[threadIdx.x] = V.rec_a[gnext];
+                    s_h[threadIdx.x] = V.rec_h[gnext];
                 }
                 __syncthreads();
+                {
+                    const uint32_t idx = b + T + threadIdx.x;
+                    gnext = idx < range.y ? V.igid[idx] : 0u;
+                }
                 const int nb = int(min(uint32_t(T), range.y - b));
-                if (!done) {
-                    for (int j = 0; j < nb; ++j) {
-                        const PixelTerm pt = eval_half_q(ux, uy, s_m[j], s_c[j]);
-                        if (pt.half_q > s_h[j]) continue;
-                        const float a = eval_alpha(s_a[j], pt.half_q, V.alpha_max);
-                        if (a < V.alpha_min) continue;
-                        const float Tt = Tr * (1.0f - a);
-                        if (Tt < thr) {
-                            s_ids[m * T + threadIdx.x] = int32_t(s_g[j]);
-                            s_w[m * T + threadIdx.x] = TQ * a;
-                            ++m;
-                            TQ = TQ * (1.0f - a);
-                            do {
-                                ++k;
-                                thr = (k < K) ? __fdiv_rn(float(K - k), float(K + 1)) : -1.0f;
-                            } while (Tt < thr);
+                for (int c0 = 0; c0 < nb; c0 += 32) {
+                    if (__all_sync(FULL, wk.done)) break;
+                    // per-warp culling against the box, as in qr_select
+                    const int jl = c0 + lane;
+                    bool pass = false;
+                    if (jl < nb)
+                        pass = !(box_min_half_q(s_m[jl], s_c[jl], bx0, bx1, by0, by1) * 0.999f > s_h[jl] + 1e-3f);
+                    unsigned todo = __ballot_sync(FULL, pass);
+                    while (todo) {
+                        int jj[4];
+                        bool valid[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            valid[u] = todo != 0u;
+                            jj[u] = valid[u] ? c0 + __ffs(todo) - 1 : jj[0];
+                            todo &= todo - 1u;
                         }
-                        if (Tt < tau_stop) { done = true; break; }
-                        Tr = Tt;
+                        float hq[4];
+                        unsigned reach = 0;
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            hq[u] = eval_half_q(ux, uy, s_m[jj[u]], s_c[jj[u]]).half_q;
+                            reach |= unsigned(valid[u] && !(hq[u] > s_h[jj[u]])) << u;
+                        }
+                        if (wk.done || !reach) continue;
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            if (wk.done || !((reach >> u) & 1u)) continue;
+                            const float a = eval_alpha(s_a[jj[u]], hq[u], V.alpha_max);
+                            if (a < V.alpha_min) continue;
+                            const float Tt = wk.T * (1.0f - a);
+                            if (Tt < wk.thr || Tt < tau_stop)
+                                walk_event(wk, Tt, a, tau_stop, K, s_g[jj[u]], threadIdx.x, KS, s_ids, s_w);
+                            else
+                                wk.T = Tt;
+                        }
+                        if (wk.done) break;
                     }
                 }
             }
-            const float D = 1.0f - TQ;
+            // normalise this pixel's weights (Algorithm 1's 1 / (1 - T^Q)) in place
+            const float D = 1.0f - wk.TQ;
             for (int j = 0; j < K; ++j) {
-                const bool has = j < m;
-                const float wn = has ? __fdiv_rn(s_w[j * T + threadIdx.x], D) : 0.0f;
-                s_w[j * T + threadIdx.x] = wn;
-                if (!has) s_ids[j * T + threadIdx.x] = -1;
-                if (inside) {
-                    const int64_t p = int64_t(py) * V.W + px;
-                    V.ids[p * K + j] = has ? s_ids[j * T + threadIdx.x] : -1;
-                    V.w[p * K + j] = wn;
+                const bool has = j < wk.m;
+                s_w[threadIdx.x * KS + j] = has ? __fdiv_rn(s_w[threadIdx.x * KS + j], D) : 0.0f;
+                if (!has) s_ids[threadIdx.x * KS + j] = -1;
+            }
+            s_cnt[threadIdx.x] = uint8_t(wk.m);
+            __syncthreads();
+            // coalesced output for a backward pass: each tile row is tile_w * K
+            // consecutive ids and weights in the view
+            const int rowlen = tile_w * K;
+            for (int rem = threadIdx.x; rem < rowlen; rem += T) {
+                const int cx = rem / K, j = rem - cx * K;
+                const int gx = tx * tile_w + cx;
+                if (gx >= V.W) continue;
+                for (int row = 0; row < tile_h; ++row) {
+                    const int gy = ty * tile_h + row;
+                    if (gy >= V.H) break;
+                    const int sl = row * tile_w + cx;
+                    const int64_t o = (int64_t(gy) * V.W + gx) * K + j;
+                    V.ids[o] = s_ids[sl * KS + j];
+                    V.w[o] = s_w[sl * KS + j];
                 }
             }
-            if (inside) V.cnt[int64_t(py) * V.W + px] = uint8_t(m);
+            if (inside) V.cnt[int64_t(py) * V.W + px] = s_cnt[threadIdx.x];
         }
         __syncthreads();
 
@@ -214,8 +260,8 @@ batch_kernel(const BatchView *__restrict__ views, int n_views, uint32_t total_it
             int id = -1;
             float w = 0.f;
             if (p >= 0) {
-                id = s_ids[j * T + loc];
-                w = s_w[j * T + loc];
+                id = s_ids[loc * KS + j];
+                w = s_w[loc * KS + j];
                 if (id >= 0 && DT == QR_FP8E4M3) w *= V.fscale[id];
             }
             const unsigned peers = __match_any_sync(FULL, id);
@@ -288,7 +334,7 @@ batch_kernel(const BatchView *__restrict__ views, int n_views, uint32_t total_it
 template <int DT, int VPL, int G>
 cudaError_t run_batch(const BatchView *dviews, int n_views, uint32_t total, uint32_t *counter,
                       int K, int ctas_per_sm, cudaStream_t s) {
-    const size_t dyn = size_t(K) * T * 8;
+    const size_t dyn = size_t(K | 1) * T * 8;
     cudaError_t e = cudaFuncSetAttribute(batch_kernel<DT, VPL, G>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, int(dyn));
     if (e != cudaSuccess) return e;

@@ -206,6 +206,64 @@ __device__ __forceinline__ float reject_half_q(float alpha, float alpha_min) {
     return fmaf(logf(fmaxf(alpha / alpha_min, 1.0f)), 1.01f, 0.01f);
 }
 
+// Lower end of q/2 = (d.w1)^2 + (d.w2)^2, d = u - mu', over the box
+// [x0,x1] x [y0,y1] of pixel centres: 0 if mu' is inside, else the smallest
+// value on the four edges, each at its clamped 1-D minimiser (evaluated with
+// the same dot products as a pixel, so no cancellation-prone closed form).
+__device__ __forceinline__ float box_min_half_q(float4 mm, float4 cc, float x0, float x1, float y0,
+                                                float y1) {
+    const float mx = mm.x + mm.z, my = mm.y + mm.w;
+    if (mx >= x0 && mx <= x1 && my >= y0 && my <= y1) return 0.0f;
+    const float sxy = fmaf(cc.x, cc.y, cc.z * cc.w);
+    const float sxx = fmaf(cc.x, cc.x, cc.z * cc.z), syy = fmaf(cc.y, cc.y, cc.w * cc.w);
+    // the edge minimisers only choose where q/2 is evaluated, so an approximate
+    // quotient suffices (inf / NaN clamp to an edge end)
+    const float ky = -__fdividef(sxy, syy), kx = -__fdividef(sxy, sxx);
+    float best = INFINITY;
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const float dx = (e ? x1 : x0) - mx;
+        const float dy = fminf(fmaxf(dx * ky, y0 - my), y1 - my);
+        const float p1 = fmaf(dx, cc.x, dy * cc.y), p2 = fmaf(dx, cc.z, dy * cc.w);
+        best = fminf(best, fmaf(p1, p1, p2 * p2));
+    }
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const float dy = (e ? y1 : y0) - my;
+        const float dx = fminf(fmaxf(dy * kx, x0 - mx), x1 - mx);
+        const float p1 = fmaf(dx, cc.x, dy * cc.y), p2 = fmaf(dx, cc.z, dy * cc.w);
+        best = fminf(best, fmaf(p1, p1, p2 * p2));
+    }
+    return best;
+}
+
+// ---------------------------------------------------------------- Algorithm 1 walk
+// Algorithm 1 state of one pixel.
+struct Walk {
+    float T, TQ, thr;
+    int k, m;
+    bool done;
+};
+
+// The rarely taken end of an Algorithm 1 step, for a member entry (alpha' >=
+// alpha_min) whose T_test = Tt crosses the next quantile boundary or the stop
+// threshold: keep the Gaussian, advance k, stop.
+__device__ __forceinline__ void walk_event(Walk &w, float Tt, float a, float tau_stop, int K,
+                                        uint32_t gid, int slot, int KS, int32_t *s_ids, float *s_w) {
+    if (Tt < w.thr) {
+        s_ids[slot * KS + w.m] = int32_t(gid);
+        s_w[slot * KS + w.m] = w.TQ * a;
+        ++w.m;
+        w.TQ = w.TQ * (1.0f - a);
+        do {
+            ++w.k;
+            w.thr = (w.k < K) ? __fdiv_rn(float(K - w.k), float(K + 1)) : -1.0f;
+        } while (Tt < w.thr);
+    }
+    if (Tt < tau_stop) w.done = true;
+    else w.T = Tt;
+}
+
 // ---------------------------------------------------------------- compensated arithmetic
 // Pairs (hi, lo) of FP32 with |lo| <= ulp(hi)/2 represent hi + lo exactly;
 // the error-free transformations are Knuth's TwoSum, Dekker's FastTwoSum and

@@ -1,26 +1,31 @@
 // K8: open-vocabulary relevance (Sec. 5: cosine similarity of features and
 // text embeddings), R[p][q] = sum_c map[p][c] * Q[q][c], on the 5th-generation
-// tensor cores (tcgen05 / UMMA, kind::f16: BF16 x BF16 -> FP32 in TMEM).
+// tensor cores (tcgen05 / UMMA, FP32 accumulation in TMEM).  The map is the
+// blend's FP32 output, so the product is memory-bound (~32 flops per byte of
+// map at Q = 64): the kernels are built to stream the map at HBM speed.
 //
-// GB300 design: persistent CTAs of 8 warps (two per SM), one 128-pixel tile at a time.
-//   * the BF16 queries (Q x C, at most 128 x 1024) are staged once per CTA in
-//     shared memory in the K-major 128-byte-swizzled layout UMMA reads;
-//   * the map arrives in FP32 (the blend's output), so each 128 x 64 slice is
-//     read with coalesced 16-byte streaming loads into registers one slice
-//     ahead (the loads of slice k+1 are in flight while the MMAs of slice k
-//     run), rounded to BF16 and written swizzled into one of two shared-memory
-//     stages (a TMA copy cannot change the dtype);
-//   * one thread issues four 128 x Q x 16 MMAs per slice into a TMEM
-//     accumulator (Q columns), and tcgen05.commit signals an mbarrier when the
-//     stage may be refilled, so loading slice k+1 overlaps the MMAs of slice k;
-//   * the epilogue reads the accumulator with tcgen05.ld (warp w owns TMEM
-//     lanes 32(w%4).. = pixels and half w/4 of the Q columns) and writes FP32
-//     rows of R.
-// The product is memory-bound at Q = 64 (about 51 flops per byte of BF16 map),
-// so the tensor cores' job is to keep the FMA work off the critical path.
-// Every mbarrier wait is bounded; on timeout the CTA records
-// QR_ERR_DEVICE_TIMEOUT in the status word, frees its TMEM and returns.
+// Main kernel (relevance_tma_kernel), when its shared memory fits:
+//   * persistent, one CTA per SM, warp-specialised: warp 0 issues TMA
+//     (cp.async.bulk.tensor) loads of 128-pixel x 32-channel FP32 map tiles
+//     into a 4-stage ring in the 128-byte-swizzled K-major layout UMMA reads;
+//   * warp 1 issues kind::tf32 UMMAs (TF32 keeps 10 mantissa bits of the map;
+//     the BF16 queries are exact in TF32) into one of two TMEM accumulators
+//     and commits each stage back to the producer through an mbarrier;
+//   * warps 2-5 drain the other accumulator with tcgen05.ld and write FP32
+//     rows of R while the next tile's MMAs run;
+//   * the queries are staged once per CTA, converted to FP32 and swizzled.
+// Fallback kernel (relevance_kernel), e.g. 128 queries of 512 channels whose
+// FP32 copy would not fit next to the ring: persistent CTAs of 8 warps (two
+// per SM) read each 128 x 64 FP32 slice with 16-byte streaming loads into
+// registers one slice ahead, round to BF16 into a swizzled shared-memory stage
+// and issue kind::f16 UMMAs.
+// Every mbarrier wait is bounded; on timeout a CTA records
+// QR_ERR_DEVICE_TIMEOUT in the status word, waits (bounded) for its own copies
+// and MMAs, frees its TMEM and returns.
+#include <cuda.h>
 #include <cuda_bf16.h>
+
+#include <mutex>
 
 #include "qr_internal.cuh"
 
@@ -148,6 +153,48 @@ __device__ __forceinline__ void store_slice(const float4 (&v)[PF], unsigned char
     }
 }
 
+// ------------------------------------------------------------ TMA + TF32 path
+// mbarrier arrive that also announces the bytes a TMA copy will deliver.
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                 :: "r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_u32(bar)) : "memory");
+}
+
+// 2-D tiled TMA load of box {32 floats, 128 rows} at (x = channel, y = pixel)
+// into a 128-byte-swizzled shared-memory stage; completion is counted on bar.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y,
+                                            uint64_t *bar) {
+    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                 " [%0], [%1, {%2, %3}], [%4];"
+                 :: "r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y),
+                    "r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void umma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                          uint32_t idesc, uint32_t accumulate) {
+    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                 " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+                 :: "r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate) : "memory");
+}
+
+// Instruction descriptor, kind::tf32: D = F32 (bits 4-5 = 1), A = B = TF32
+// (bits 7-9, 10-12 = 2), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t make_idesc_tf32(int M, int N) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t(N >> 3) << 17) | (uint32_t(M >> 4) << 24);
+}
+
+// Bounded wait by one thread; on timeout raises the CTA's abort flag.
+__device__ __forceinline__ bool lane_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
+    if (*abort_flag) return false;
+    if (mbar_wait(bar, parity)) return true;
+    *abort_flag = 1;
+    return false;
+}
+
 template <int QN>
 __global__ void __launch_bounds__(NT, 2)
 relevance_kernel(const float *__restrict__ map, const uint16_t *__restrict__ queries, int64_t P,
@@ -252,6 +299,214 @@ relevance_kernel(const float *__restrict__ map, const uint16_t *__restrict__ que
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(TMEM_COLS) : "memory");
 }
 
+constexpr int TT = 192;               // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+constexpr int STAGES = 4;             // FP32 map tiles in flight per CTA
+constexpr int A_TILE = 128 * 32 * 4;  // 128 pixels x 32 channels FP32 = 16 KB
+
+// Persistent, one CTA per SM, warp-specialised: a TMA producer streams
+// 128 x 32 FP32 map tiles into a 4-stage 128-byte-swizzled ring, one thread
+// issues kind::tf32 UMMAs (TF32 keeps 10 mantissa bits of the map, more than
+// BF16) into one of two TMEM accumulators, and four epilogue warps drain the
+// other accumulator with tcgen05.ld while the next tile's MMAs run.  The
+// queries (BF16, exact in TF32) are staged once per CTA.  Every mbarrier wait
+// is bounded; on timeout the CTA raises an abort flag, every role stops, the
+// CTA waits (bounded) for its own TMA copies and MMAs, frees TMEM and reports
+// QR_ERR_DEVICE_TIMEOUT.
+template <int QN>
+__global__ void __launch_bounds__(TT, 1)
+relevance_tma_kernel(const __grid_constant__ CUtensorMap tmap, const uint16_t *__restrict__ queries,
+                     int64_t P, int C, float *__restrict__ out, int *__restrict__ status) {
+    constexpr uint32_t TMEM_COLS = 2 * QN < 32 ? 32 : 2 * QN;   // two accumulators
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *base = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const int nsl = C / 32;
+    unsigned char *sA = base;                                       // STAGES x 16 KB
+    unsigned char *sB = sA + STAGES * A_TILE;                       // nsl x QN x 128 B
+    uint64_t *full = reinterpret_cast<uint64_t *>(sB + size_t(nsl) * QN * 128);
+    uint64_t *empty = full + STAGES;
+    uint64_t *tfull = empty + STAGES;
+    uint64_t *tempty = tfull + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tempty + 2);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    uint32_t *s_count = reinterpret_cast<uint32_t *>(tmem_slot + 2);   // [0] TMA issued, [1] MMA slices
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    // queries -> FP32 in the K-major 128-byte-swizzled layout UMMA reads:
+    // row n of slice s holds channels 32s .. 32s+31 in 16-byte chunks c ^ (n % 8)
+    for (int i = threadIdx.x; i < QN * C; i += TT) {
+        const int n = i / C, c = i - n * C;
+        const int sl = c >> 5, cc = c & 31;
+        const float v = __uint_as_float(uint32_t(queries[size_t(n) * C + c]) << 16);
+        *reinterpret_cast<float *>(sB + size_t(sl) * QN * 128 + n * 128 +
+                                   (((cc >> 2) ^ (n & 7)) << 4) + (cc & 3) * 4) = v;
+    }
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < STAGES; ++st) {
+            mbar_init(&full[st], 1);
+            mbar_init(&empty[st], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&tfull[a], 1);
+            mbar_init(&tempty[a], 4);
+        }
+        *abort_flag = 0;
+        s_count[0] = s_count[1] = 0u;
+        // make the initialised barriers visible to the TMA and tensor-core units
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_u32(tmem_slot)), "r"(TMEM_COLS) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const int64_t tiles = (P + 127) / 128;
+
+    if (warp == 0 && lane == 0) {
+        // TMA producer
+        uint32_t it = 0;
+        bool ok = true;
+        for (int64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x)
+            for (int sl = 0; sl < nsl; ++sl) {
+                const int st = int(it % STAGES);
+                if (!lane_wait(&empty[st], ((it / STAGES) & 1u) ^ 1u, abort_flag)) { ok = false; break; }
+                mbar_expect_tx(&full[st], A_TILE);
+                tma_load_2d(smem_u32(sA + st * A_TILE), &tmap, sl * 32, int(t * 128), &full[st]);
+                ++it;
+            }
+        s_count[0] = it;
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        constexpr uint32_t idesc = make_idesc_tf32(128, QN);
+        uint32_t it = 0, tl = 0;
+        bool ok = true;
+        for (int64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++tl) {
+            const uint32_t acc = tl & 1u;
+            if (!lane_wait(&tempty[acc], ((tl >> 1) & 1u) ^ 1u, abort_flag)) break;
+            tc_fence_after();
+            for (int sl = 0; sl < nsl; ++sl) {
+                const int st = int(it % STAGES);
+                if (!lane_wait(&full[st], (it / STAGES) & 1u, abort_flag)) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t a0 = smem_u32(sA + st * A_TILE);
+                const uint32_t b0 = smem_u32(sB + size_t(sl) * QN * 128);
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    umma_tf32(tmem + acc * QN, make_desc(a0 + k * 32), make_desc(b0 + k * 32), idesc,
+                              (sl > 0 || k > 0) ? 1u : 0u);
+                umma_commit(&empty[st]);
+                ++it;
+            }
+            if (ok) umma_commit(&tfull[acc]);
+        }
+        s_count[1] = it;
+    } else if (warp >= 2) {
+        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. (its 32 pixels of the tile)
+        const int q = warp & 3;
+        uint32_t tl = 0;
+        for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x, ++tl) {
+            const uint32_t acc = tl & 1u;
+            int ok = 1;
+            if (lane == 0) ok = lane_wait(&tfull[acc], (tl >> 1) & 1u, abort_flag) ? 1 : 0;
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) break;
+            tc_fence_after();
+            const int64_t p = t * 128 + q * 32 + lane;
+            const uint32_t taddr = tmem + (uint32_t(q * 32) << 16) + acc * QN;
+#pragma unroll
+            for (int c = 0; c < QN; c += 16) {
+                float v[16];
+                tmem_ld16(taddr + uint32_t(c), v);
+                if (p < P) {
+                    float4 *o = reinterpret_cast<float4 *>(out + p * QN + c);
+                    o[0] = make_float4(v[0], v[1], v[2], v[3]);
+                    o[1] = make_float4(v[4], v[5], v[6], v[7]);
+                    o[2] = make_float4(v[8], v[9], v[10], v[11]);
+                    o[3] = make_float4(v[12], v[13], v[14], v[15]);
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[acc]);
+        }
+    }
+    __syncthreads();
+    if (*abort_flag) {
+        // nothing of this CTA may still be writing shared memory or TMEM
+        if (threadIdx.x == 0) atomicExch(status, int(QR_ERR_DEVICE_TIMEOUT));
+        if (warp == 0 && lane == 0) {
+            const uint32_t n = s_count[0];
+            for (uint32_t i = n > STAGES ? n - STAGES : 0u; i < n; ++i)
+                mbar_wait(&full[i % STAGES], (i / STAGES) & 1u);
+        }
+        if (warp == 1 && lane == 0 && s_count[1] > 0) {
+            const uint32_t last = s_count[1] - 1;
+            mbar_wait(&empty[last % STAGES], (last / STAGES) & 1u);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(TMEM_COLS) : "memory");
+}
+
+size_t tma_smem_bytes(int Q, int C) {
+    return 1024 + size_t(STAGES) * A_TILE + size_t(C) * Q * 4 + 256;
+}
+
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                 const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                 const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                 CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// The driver's tensor-map encoder, resolved once through the runtime (no
+// link-time dependency on libcuda).
+EncodeTiled encode_tiled() {
+    static std::once_flag once;
+    static EncodeTiled fn = nullptr;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiled>(p);
+    });
+    return fn;
+}
+
+template <int QN>
+cudaError_t run_tma(const float *map, const uint16_t *q, int64_t P, int C, float *out, int *status,
+                    cudaStream_t s) {
+    EncodeTiled enc = encode_tiled();
+    if (!enc) return cudaErrorNotSupported;
+    CUtensorMap tm;
+    const cuuint64_t dims[2] = {cuuint64_t(C), cuuint64_t(P)};
+    const cuuint64_t strides[1] = {cuuint64_t(C) * 4};
+    const cuuint32_t box[2] = {32, 128};
+    const cuuint32_t estr[2] = {1, 1};
+    if (enc(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(map), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
+    const size_t smem = tma_smem_bytes(QN, C);
+    cudaError_t e = cudaFuncSetAttribute(relevance_tma_kernel<QN>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t tiles = (P + 127) / 128;
+    const int grid = int(tiles < sms ? tiles : sms);
+    relevance_tma_kernel<QN><<<grid, TT, smem, s>>>(tm, q, P, C, out, status);
+    count_launch();
+    return cudaGetLastError();
+}
+
 template <int QN>
 cudaError_t run(const float *map, const uint16_t *q, int64_t P, int C, float *out, int *status,
                 cudaStream_t s) {
@@ -278,8 +533,23 @@ bool relevance_supported(int Q, int C) {
     return 1024 + size_t(C / BK) * Q * 128 + 2 * A_STAGE + 64 <= 227 * 1024;
 }
 
+// The TMA + TF32 kernel where its shared memory fits (the queries are held in
+// FP32), else the register-staged BF16 kernel.
+static bool tma_fits(int Q, int C, int64_t P, const float *map) {
+    return C % 32 == 0 && P < (int64_t(1) << 31) - 128 &&
+           (reinterpret_cast<uintptr_t>(map) & 15) == 0 && tma_smem_bytes(Q, C) <= 227 * 1024;
+}
+
 cudaError_t launch_relevance(const float *map, const uint16_t *q, int Q, int64_t P, int C,
                              float *out, int *status, cudaStream_t s) {
+    if (tma_fits(Q, C, P, map)) {
+        switch (Q) {
+            case 16: return run_tma<16>(map, q, P, C, out, status, s);
+            case 32: return run_tma<32>(map, q, P, C, out, status, s);
+            case 64: return run_tma<64>(map, q, P, C, out, status, s);
+            case 128: return run_tma<128>(map, q, P, C, out, status, s);
+        }
+    }
     switch (Q) {
         case 16: return run<16>(map, q, P, C, out, status, s);
         case 32: return run<32>(map, q, P, C, out, status, s);

@@ -80,3 +80,24 @@ def sample_pixels(width, height, n, seed=0):
 def small_room(n=20000, seed=0, channels=64):
     g, f = scenes.room_scene(seed=seed, n=n, channels=channels)
     return g, f
+
+
+def check_relevance(got, fmap, qbits, kernel="tma"):
+    """Scores of the relevance GEMM against FP64.  Every kernel is within the
+    BF16 bound 2^-8 * sum |a b| of the exact product of the FP32 map and the
+    BF16 queries.  The TMA kernel reads the map as TF32 (at least 10 mantissa
+    bits): within 2^-10 * sum |a b|.  The register-staged kernel rounds the map
+    to BF16 like the oracle's encoder: equal to the FP64 product of the
+    BF16-rounded map up to FP32 accumulation (1e-4 * sum |a b|)."""
+    got = np.asarray(got, np.float64)
+    b = oracle.bf16_decode(qbits)
+    exact = oracle.relevance(fmap, b)
+    mag = np.abs(np.asarray(fmap, np.float64)) @ np.abs(b).T
+    err = np.abs(got - exact)
+    assert (err <= 2.0 ** -8 * mag + 1e-6).all(), (err / (mag + 1e-30)).max()
+    if kernel == "tma":
+        assert (err <= 2.0 ** -10 * mag + 1e-6).all(), (err / (mag + 1e-30)).max()
+    else:
+        a = oracle.bf16_decode(oracle.bf16_encode(fmap))
+        ref = oracle.relevance(a, b)
+        assert (np.abs(got - ref) <= 1e-4 * mag + 1e-30).all(), np.abs(got - ref).max()

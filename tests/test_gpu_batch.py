@@ -77,11 +77,7 @@ def test_batch_graph_replay_and_relevance():
     torch.testing.assert_close(b.out, eager[0], rtol=0, atol=0)
     torch.testing.assert_close(b.scores, eager[1], rtol=0, atol=0)
     assert int(b.rel_status.item()) == 0
-    m = oracle.bf16_decode(oracle.bf16_encode(b.out.cpu().numpy()))
-    qd = oracle.bf16_decode(oracle.bf16_encode(queries))
-    ref = oracle.relevance(m, qd)
-    mag = np.abs(m) @ np.abs(qd).T
-    assert (np.abs(b.scores.cpu().numpy() - ref) <= 1e-4 * mag + 1e-30).all()
+    H.check_relevance(b.scores.cpu().numpy(), b.out.cpu().numpy(), oracle.bf16_encode(queries))
 
 
 def test_many_view_workload_against_oracle():

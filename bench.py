@@ -480,6 +480,35 @@ def run_train_step(local, steps=10):
             "note": "host-timed; includes workspace allocation and the capacity check per step"}
 
 
+def profile_relevance(local, reps=13):
+    """Relevance GEMM alone on a random FP32 map of 524,288 x 512 (1.07 GB,
+    larger than L2) against 64 unit BF16 queries: the small case the ncu
+    capture of the relevance kernel runs on."""
+    import torch
+    from paper_2512_20927_gb300 import qrender as q
+    from paper_2512_20927_gb300 import scenes
+    P_, C_, Q_ = 524288, C, 64
+    dev = torch.device("cuda", local)
+    g = torch.Generator(device=dev)
+    g.manual_seed(0)
+    fmap = torch.randn(P_, C_, device=dev, generator=g)
+    qbits = q.qr_quantize_bf16(torch.from_numpy(scenes.unit_queries(7, Q_, C_)).to(dev)).view(torch.int16)
+    for _ in range(3):
+        q.qr_relevance(fmap, qbits)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps - 3):
+        scores, st = q.qr_relevance(fmap, qbits)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / (reps - 3)
+    return {"profile": "relevance", "pixels": P_, "channels": C_, "queries": Q_,
+            "us": round(ms * 1000, 1), "GB_per_s": round((P_ * C_ * 4 + P_ * Q_ * 4) / ms / 1e6, 1),
+            "status": int(st.item())}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -490,6 +519,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true",
                     help="only set up the frame and run the eager steps (for ncu captures)")
+    ap.add_argument("--profile-relevance", action="store_true",
+                    help="only run the relevance GEMM on a 1.07 GB map (for ncu captures)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the many-view and training-step measurements")
     args = ap.parse_args()
@@ -527,6 +558,11 @@ def main():
                     "d2h_bytes_per_step": 0}}))
         return
 
+    if args.profile_relevance:
+        import torch
+        torch.cuda.set_device(local)
+        print(json.dumps(profile_relevance(local)))
+        return
     if ws > 1:
         import torch
         import torch.distributed as dist

@@ -48,6 +48,7 @@ class Batch:
     group: int = 0
     ctas_per_sm: int = 0
     queries: object = None        # [Q, C] BF16 bit patterns (int16 tensor) or None
+    streams: int = 4              # side streams the per-view projection and binning use
     frames: list = field(default_factory=list)
     graph: object = None
 
@@ -94,6 +95,7 @@ class Batch:
             v.weights = self.weights[a:b].data_ptr()
             v.counts = self.counts[a:b].data_ptr()
             v.out = self.out[a:b].data_ptr()
+        self.side = [torch.cuda.Stream(device=dev) for _ in range(max(self.streams, 1))]
         nbytes = int(q.load().qr_batch_workspace_bytes(len(self.views)))
         self.ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
         self.ws_ptr = (self.ws.data_ptr() + 255) // 256 * 256
@@ -110,9 +112,28 @@ class Batch:
 
     # ---------------------------------------------------------------- work
     def project_sort(self, stream=None):
-        for (si, _), fr in zip(self.views, self.frames):
-            q.qr_project(fr, *self.scenes[si].gdev, stream=stream)
-            q.qr_sort(fr, stream=stream)
+        """Projection and binning of every view.  The views are independent, so
+        they are spread round-robin over the side streams, forked from and
+        joined back into `stream` with events (also inside graph capture)."""
+        torch = _torch()
+        base = stream if stream is not None else torch.cuda.current_stream()
+        if len(self.side) <= 1:
+            for (si, _), fr in zip(self.views, self.frames):
+                q.qr_project(fr, *self.scenes[si].gdev, stream=base)
+                q.qr_sort(fr, stream=base)
+            return
+        fork = torch.cuda.Event()
+        fork.record(base)
+        for s in self.side:
+            s.wait_event(fork)
+        for k, ((si, _), fr) in enumerate(zip(self.views, self.frames)):
+            s = self.side[k % len(self.side)]
+            q.qr_project(fr, *self.scenes[si].gdev, stream=s)
+            q.qr_sort(fr, stream=s)
+        for s in self.side:
+            join = torch.cuda.Event()
+            join.record(s)
+            base.wait_event(join)
 
     def select_blend(self, stream=None):
         q._check(q.load().qr_render_batch(ctypes.c_void_p(self.ws_ptr), len(self.views),

@@ -445,10 +445,10 @@ def run_batched(local, steps=3):
                           "TFLOP_per_s": round(rel_flops / rel_ms / 1e9, 1)}}
 
 
-def run_train_step(local, steps=10):
+def _train_workload(local):
     """Differentiation workload: 300k-Gaussian room, 512-D BF16 features,
-    640x480, K = 8; forward + mean (1 - cos) loss against the dense map of a
-    second Gaussian set + backward to features and opacities."""
+    640x480, K = 8, and the target map: the dense render of a second Gaussian
+    set."""
     import torch
     from paper_2512_20927_gb300 import qrender as q
     from paper_2512_20927_gb300 import scenes
@@ -460,6 +460,34 @@ def run_train_step(local, steps=10):
     table = q.qr_quantize_bf16(torch.from_numpy(f).to(dev))
     g2d = tuple(t.to(dev) for t in q.gaussians_to_device(g2, device="cpu"))
     tgt = q.render_frame(g2d, torch.from_numpy(f2).to(dev), cam, K=K, dense=True)["dense"]
+    return dev, cam, gd, table, tgt
+
+
+def profile_train(local, steps=3):
+    """Forward + loss + backward of the differentiation workload on fixed
+    buffers, eager (for ncu launch lists)."""
+    import torch
+    from paper_2512_20927_gb300 import qrender as q
+    dev, cam, gd, table, tgt = _train_workload(local)
+    r0 = q.render_frame(gd, table, cam, K=K, max_isect=2_000_000)
+    fr, ids, w, cnt, out = r0["frame"], r0["ids"], r0["weights"], r0["counts"], r0["out"]
+    for _ in range(steps):
+        q.qr_project(fr, *gd)
+        q.qr_sort(fr)
+        q.qr_select(fr, ids, w, cnt)
+        q.qr_blend(table, None, ids, w, cnt, out)
+        loss, gmap = q.qr_cosine_loss(out, tgt, cnt)
+        q.qr_backward(fr, table, None, ids, w, cnt, gmap, want_conic=False)
+    torch.cuda.synchronize()
+    return {"profile": "train", "steps": steps, "loss": round(float(loss.item()), 6)}
+
+
+def run_train_step(local, steps=10):
+    """Differentiation workload (see _train_workload): forward + mean (1 - cos)
+    loss + backward to features and opacities."""
+    import torch
+    from paper_2512_20927_gb300 import qrender as q
+    dev, cam, gd, table, tgt = _train_workload(local)
 
     def step():
         res = q.render_frame(gd, table, cam, K=K, max_isect=2_000_000)
@@ -475,9 +503,48 @@ def run_train_step(local, steps=10):
         loss = step()
     torch.cuda.synchronize()
     ms = (time.perf_counter() - t0) * 1000.0 / steps
+
+    # the same step on a fixed frame and fixed buffers, captured once as a CUDA
+    # graph and replayed: what the kernels cost without host work
+    r0 = q.render_frame(gd, table, cam, K=K, max_isect=2_000_000)
+    fr, ids, w, cnt, out = r0["frame"], r0["ids"], r0["weights"], r0["counts"], r0["out"]
+    keep = {}
+
+    def gstep():
+        q.qr_project(fr, *gd)
+        q.qr_sort(fr)
+        q.qr_select(fr, ids, w, cnt)
+        q.qr_blend(table, None, ids, w, cnt, out)
+        keep["loss"], gmap = q.qr_cosine_loss(out, tgt, cnt)
+        keep["gf"], keep["ga"], _ = q.qr_backward(fr, table, None, ids, w, cnt, gmap,
+                                                  want_conic=False)
+    side = torch.cuda.Stream(device=dev)
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for _ in range(2):
+            gstep()
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        gstep()
+    for _ in range(3):
+        graph.replay()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        graph.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    gms = e0.elapsed_time(e1) / steps
     return {"ms_per_step": round(ms, 3), "steps_per_s": round(1000.0 / ms, 2),
             "loss": round(float(loss.item()), 6),
-            "note": "host-timed; includes workspace allocation and the capacity check per step"}
+            "graph_ms_per_step": round(gms, 4), "graph_loss": round(float(keep["loss"].item()), 6),
+            "note": "ms_per_step host-timed (workspace allocation and a capacity check per "
+                    "step); graph_ms_per_step: forward + loss + backward replayed from a "
+                    "CUDA graph on fixed buffers"}
 
 
 def profile_relevance(local, reps=13):
@@ -519,6 +586,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true",
                     help="only set up the frame and run the eager steps (for ncu captures)")
+    ap.add_argument("--profile-train", action="store_true",
+                    help="only run eager training steps of the differentiation workload (for ncu)")
     ap.add_argument("--profile-relevance", action="store_true",
                     help="only run the relevance GEMM on a 1.07 GB map (for ncu captures)")
     ap.add_argument("--no-extras", action="store_true",
@@ -558,10 +627,10 @@ def main():
                     "d2h_bytes_per_step": 0}}))
         return
 
-    if args.profile_relevance:
+    if args.profile_relevance or args.profile_train:
         import torch
         torch.cuda.set_device(local)
-        print(json.dumps(profile_relevance(local)))
+        print(json.dumps(profile_relevance(local) if args.profile_relevance else profile_train(local)))
         return
     if ws > 1:
         import torch

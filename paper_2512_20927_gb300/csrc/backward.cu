@@ -15,23 +15,27 @@
 //      with the forward's exact evaluation, forms s_j with warp-wide dot
 //      products (16-byte feature loads, BF16/FP8 decoded in registers) and
 //      writes per-entry (dalpha, dA00, dA01, dA11);
-//   2. bwd_tile_partials: one CTA per (screen tile, 128-channel slice) sorts
-//      the tile's (Gaussian, entry) keys in shared memory and lets each warp
-//      reduce one distinct Gaussian's w * g rows in entry order into a partial
-//      row, stored at a fixed slot of that tile's intersection range;
+//   2. bwd_tile_partials: one CTA per screen tile sorts the tile's (Gaussian,
+//      entry) keys once (in registers), stages each entry's pixel and weight
+//      and, 64 channels at a time, the tile's rows of g in shared memory, and
+//      lets each warp reduce one distinct Gaussian's w * g rows in entry order
+//      into a partial row, stored at a fixed slot of that tile's intersection
+//      range;
 //   3. a stable radix sort of the slot keys by Gaussian id;
 //   4. bwd_reduce: one warp per Gaussian sums its partials in tile order and
 //      writes its gradient row (zeros for unselected Gaussians).
+#include <cstring>
+
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
 #include "qr_internal.cuh"
+#include "tma.cuh"
 
 namespace qr {
 namespace {
 
 constexpr int T = 256;
-constexpr int CHUNK = 128;     // channels per partial-reduction CTA
 
 template <int DT> struct VecB;
 template <> struct VecB<QR_F32> { static constexpr int C = 4; static constexpr int E = 4; };
@@ -68,7 +72,7 @@ __device__ __forceinline__ void widen<QR_FP8E4M3>(const uint4 v, float *o) {
 }
 
 // ------------------------------------------------------------------ 1. per pixel
-template <int DT>
+template <int DT, int VPL>
 __global__ void __launch_bounds__(T)
 bwd_pixel(const float4 *__restrict__ rec_m, const float4 *__restrict__ rec_w,
           const float *__restrict__ rec_a, const unsigned char *__restrict__ feat,
@@ -89,29 +93,77 @@ bwd_pixel(const float4 *__restrict__ rec_m, const float4 *__restrict__ rec_w,
         const float ux = float(p % W) + 0.5f, uy = float(p / W) + 0.5f;
         const int id = lane < m ? ids[p * K + lane] : 0;
         const float wj = lane < m ? wts[p * K + lane] : 0.f;
-        // s_j = g . f_j for every quantile Gaussian j (lane j keeps s_j)
+        // s_j = g . f_j for every quantile Gaussian j (lane j keeps s_j): the
+        // lane's slice of g is held in registers, four rows are loaded at once
+        // and their four partial dots reduced together
         const float *g = grad_out + p * int64_t(C);
         float s_mine = 0.f;
-        for (int j = 0; j < m; ++j) {
-            const int gj = __shfl_sync(FULL, id, j);
-            const unsigned char *row = feat + size_t(gj) * row_bytes;
-            const float sc = (DT == QR_FP8E4M3) ? fscale[gj] : 1.f;
-            float part = 0.f;
-            for (int v = lane; v < nvec; v += 32) {
-                float fv[CPV];
-                widen<DT>(*reinterpret_cast<const uint4 *>(row + size_t(v) * 16), fv);
-                const float4 *gv = reinterpret_cast<const float4 *>(g + v * CPV);
+        if (VPL > 0) {
+            float gr[VPL > 0 ? VPL : 1][CPV];
+#pragma unroll
+            for (int t = 0; t < VPL; ++t) {
+                const float4 *gv = reinterpret_cast<const float4 *>(g + (lane + 32 * t) * CPV);
 #pragma unroll
                 for (int q = 0; q < CPV / 4; ++q) {
                     const float4 gg = gv[q];
-                    part = fmaf(fv[4 * q], gg.x, part);
-                    part = fmaf(fv[4 * q + 1], gg.y, part);
-                    part = fmaf(fv[4 * q + 2], gg.z, part);
-                    part = fmaf(fv[4 * q + 3], gg.w, part);
+                    gr[t][4 * q] = gg.x; gr[t][4 * q + 1] = gg.y; gr[t][4 * q + 2] = gg.z; gr[t][4 * q + 3] = gg.w;
                 }
             }
-            for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(FULL, part, o);
-            if (lane == j) s_mine = part * sc;
+            for (int j0 = 0; j0 < m; j0 += 4) {
+                uint4 rv[4][VPL > 0 ? VPL : 1];
+                float sc4[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int jj = j0 + u < m ? j0 + u : j0;
+                    const int gj = __shfl_sync(FULL, id, jj);
+                    const unsigned char *row = feat + size_t(gj) * row_bytes;
+                    sc4[u] = (DT == QR_FP8E4M3) ? fscale[gj] : 1.f;
+#pragma unroll
+                    for (int t = 0; t < VPL; ++t)
+                        rv[u][t] = *reinterpret_cast<const uint4 *>(row + size_t(lane + 32 * t) * 16);
+                }
+                float part[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    part[u] = 0.f;
+#pragma unroll
+                    for (int t = 0; t < VPL; ++t) {
+                        float fv[CPV];
+                        widen<DT>(rv[u][t], fv);
+#pragma unroll
+                        for (int q = 0; q < CPV; ++q) part[u] = fmaf(fv[q], gr[t][q], part[u]);
+                    }
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) part[u] += __shfl_xor_sync(FULL, part[u], o);
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (j0 + u < m && lane == j0 + u) s_mine = part[u] * sc4[u];
+            }
+        } else {
+            for (int j = 0; j < m; ++j) {
+                const int gj = __shfl_sync(FULL, id, j);
+                const unsigned char *row = feat + size_t(gj) * row_bytes;
+                const float sc = (DT == QR_FP8E4M3) ? fscale[gj] : 1.f;
+                float part = 0.f;
+                for (int v = lane; v < nvec; v += 32) {
+                    float fv[CPV];
+                    widen<DT>(*reinterpret_cast<const uint4 *>(row + size_t(v) * 16), fv);
+                    const float4 *gv = reinterpret_cast<const float4 *>(g + v * CPV);
+#pragma unroll
+                    for (int q = 0; q < CPV / 4; ++q) {
+                        const float4 gg = gv[q];
+                        part = fmaf(fv[4 * q], gg.x, part);
+                        part = fmaf(fv[4 * q + 1], gg.y, part);
+                        part = fmaf(fv[4 * q + 2], gg.z, part);
+                        part = fmaf(fv[4 * q + 3], gg.w, part);
+                    }
+                }
+                for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(FULL, part, o);
+                if (lane == j) s_mine = part * sc;
+            }
         }
         // alpha', G, offsets of this lane's Gaussian, recomputed exactly as in the forward
         float a = 0.f, G = 0.f, dx = 0.f, dy = 0.f;
@@ -154,6 +206,14 @@ bwd_pixel(const float4 *__restrict__ rec_m, const float4 *__restrict__ rec_w,
     }
 }
 
+// acc += w * g for both halves with one packed FP32x2 FMA (each half rounds
+// exactly like fmaf).
+__device__ __forceinline__ void fma2v(float2 &acc, float w, float2 g) {
+    asm("{\n .reg .b64 a, ww, xx;\n mov.b64 a, {%0, %1};\n mov.b64 ww, {%2, %2};\n"
+        " mov.b64 xx, {%3, %4};\n fma.rn.f32x2 a, ww, xx, a;\n mov.b64 {%0, %1}, a;\n}\n"
+        : "+f"(acc.x), "+f"(acc.y) : "f"(w), "f"(g.x), "f"(g.y));
+}
+
 // ------------------------------------------------------------------ 2. per tile
 __device__ __forceinline__ void bitonic64(unsigned long long *s, int npow2) {
     for (int k = 2; k <= npow2; k <<= 1)
@@ -169,18 +229,51 @@ __device__ __forceinline__ void bitonic64(unsigned long long *s, int npow2) {
         }
 }
 
+// One CTA per tile (256 threads, one per pixel).  The tile's (gid, pixel * K +
+// entry) keys -- 32-bit (gid << 11 | local) when every gid is below 2^21 and
+// K <= 8, else 64-bit (gid << 32 | local) -- are sorted once (E = 1..8 per
+// thread in registers when K <= 8, else a shared-memory network), so the
+// entries of each distinct Gaussian form a segment in (pixel, entry) order.
+// Each entry's pixel, weight and per-entry (dalpha, dA) terms are then
+// gathered into shared memory in sorted order with independent loads; per
+// CH-channel chunk, the tile's rows of g are staged in shared memory (by TMA,
+// double-buffered, when a tensor map is given) and one warp per segment sums
+// w * g[pixel] over the segment (eight entries in flight) into that segment's
+// partial row, stored at slot range.x + segment of the tile's intersection
+// range.  The (dalpha, dA) terms are summed per segment by the warp's lanes in
+// a fixed order.
+constexpr unsigned kTmaSpin = 1u << 26;   // polls before a staging wait gives up
+
+template <int E, typename KT>
 __global__ void __launch_bounds__(T)
 bwd_tile_partials(const uint2 *__restrict__ ranges, int W, int H, int tile_w, int tiles_x,
                   const int32_t *__restrict__ ids, const float *__restrict__ wts,
-                  const uint8_t *__restrict__ cnt, const float4 *__restrict__ E,
-                  const float *__restrict__ grad_out, int C, int K,
+                  const uint8_t *__restrict__ cnt, const float4 *__restrict__ E4,
+                  const float *__restrict__ grad_out, int C, int K, int CH,
                   float *__restrict__ partial, float4 *__restrict__ partial_s,
-                  uint32_t *__restrict__ pkey) {
-    extern __shared__ unsigned long long s_key[];          // pow2 >= 256*K keys
+                  uint32_t *__restrict__ pkey, const __grid_constant__ CUtensorMap gmap, int use_tma,
+                  uint32_t *__restrict__ counters) {
+    constexpr bool K32 = sizeof(KT) == 4;
+    constexpr int SHIFT = K32 ? 11 : 32;
+    constexpr bool STAGE_E = E > 0;   // per-entry E terms staged (K <= 8)
+    extern __shared__ __align__(16) unsigned char s_dyn[];
     __shared__ uint32_t s_w[32];
     __shared__ uint32_t s_nseg;
+    __shared__ __align__(8) uint64_t s_bar[2];
+    __shared__ int s_ok;
+    int npow2 = 1;
+    while (npow2 < T * K) npow2 <<= 1;
+    // 1024-byte aligned base (the launch adds 1 KB of slack for it)
+    unsigned char *base = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(s_dyn) + 1023) & ~uintptr_t(1023));
+    KT *s_key = reinterpret_cast<KT *>(base);                                    // npow2
+    uint32_t *seg = reinterpret_cast<uint32_t *>(s_key + npow2);                 // T*K
+    uint2 *s_ent = reinterpret_cast<uint2 *>(seg + T * K);                       // T*K (pixel, w)
+    float4 *s_e4 = reinterpret_cast<float4 *>(s_ent + T * K);                    // T*K if STAGE_E
+    const size_t g_off = (size_t(npow2) * sizeof(KT) + size_t(T * K) * (12 + (STAGE_E ? 16 : 0)) +
+                          1023) & ~size_t(1023);
+    float *s_g = reinterpret_cast<float *>(base + g_off);                       // [2][T*CH]
     const int tile = blockIdx.x;
-    const int c0 = blockIdx.y * CHUNK;
     const int tx = tile % tiles_x, ty = tile / tiles_x;
     const int tile_h = T / tile_w;
     const int px = tx * tile_w + threadIdx.x % tile_w, py = ty * tile_h + threadIdx.x / tile_w;
@@ -188,26 +281,60 @@ bwd_tile_partials(const uint2 *__restrict__ ranges, int W, int H, int tile_w, in
     const int64_t p = inside ? int64_t(py) * W + px : 0;
     const uint2 r = ranges[tile];
     const int m = inside ? int(cnt[p]) : 0;
-    // gather (gid << 32 | local entry) keys
     uint32_t tot;
-    const uint32_t inc = block_inclusive_scan(uint32_t(m), s_w, tot);
+    block_inclusive_scan(uint32_t(m), s_w, tot);
     const int n = int(tot);
-    int npow2 = 1;
-    while (npow2 < n) npow2 <<= 1;
-    for (int j = 0; j < m; ++j)
-        s_key[inc - m + j] = (static_cast<unsigned long long>(uint32_t(ids[p * K + j])) << 32) |
-                             uint32_t(threadIdx.x * K + j);
-    for (int i = n + threadIdx.x; i < npow2; i += T) s_key[i] = ~0ull;
+    if (n == 0) {
+        for (int u = threadIdx.x; u < int(r.y - r.x); u += T) pkey[r.x + u] = 0xFFFFFFFFu;
+        return;
+    }
+    const int nchunks = (C + CH - 1) / CH;
+    const uint32_t chunk_bytes = uint32_t(T) * uint32_t(CH) * 4u;
+    if (use_tma && threadIdx.x == 0) {
+        // the first two chunks of g fly while the keys are sorted
+        tma_mbar_init(&s_bar[0], 1);
+        tma_mbar_init(&s_bar[1], 1);
+        tma_fence_init();
+        for (int b = 0; b < 2 && b < nchunks; ++b) {
+            tma_expect_tx(&s_bar[b], chunk_bytes);
+            tma_load_3d(s_g + size_t(b) * T * CH, &gmap, b * CH, tx * tile_w, ty * tile_h, &s_bar[b]);
+        }
+    }
+    auto key_of = [&](int j) -> KT {
+        return j < m ? (KT(uint32_t(ids[p * K + j])) << SHIFT) | KT(uint32_t(threadIdx.x * K + j))
+                     : ~KT(0);
+    };
+    if constexpr (E > 0) {
+        KT v[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) v[e] = key_of(e);
+        bitonic_regs<E, T, KT>(v, s_key);
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < E; ++e) s_key[threadIdx.x * E + e] = v[e];
+    } else {
+        for (int j = 0; j < K; ++j) s_key[threadIdx.x * K + j] = key_of(j);
+        for (int i = T * K + threadIdx.x; i < npow2; i += T) s_key[i] = ~KT(0);
+        __syncthreads();
+        bitonic64(reinterpret_cast<unsigned long long *>(s_key), npow2);
+    }
     __syncthreads();
-    if (n > 1) bitonic64(s_key, npow2);
-    // segment heads -> segment starts stored after the keys
-    uint32_t *seg = reinterpret_cast<uint32_t *>(s_key + npow2);
+    constexpr KT LOCAL_MASK = K32 ? KT(0x7FF) : KT(0xFFFFFFFFu);
+    // each entry's (local pixel, weight) and E terms in sorted order: independent loads
+#pragma unroll 4
+    for (int i = threadIdx.x; i < n; i += T) {
+        const uint32_t loc = uint32_t(s_key[i] & LOCAL_MASK);
+        const int pix = int(loc) / K, j = int(loc) - pix * K;
+        const int64_t pp = int64_t(ty * tile_h + pix / tile_w) * W + tx * tile_w + pix % tile_w;
+        s_ent[i] = make_uint2(uint32_t(pix), __float_as_uint(wts[pp * K + j]));
+        if (STAGE_E) s_e4[i] = E4[pp * K + j];
+    }
     if (threadIdx.x == 0) s_nseg = 0;
-    __syncthreads();
+    // segment starts
     uint32_t carry = 0;
-    for (int base = 0; base < n; base += T) {
-        const int i = base + threadIdx.x;
-        const uint32_t h = (i < n && (i == 0 || (s_key[i] >> 32) != (s_key[i - 1] >> 32))) ? 1u : 0u;
+    for (int base_i = 0; base_i < n; base_i += T) {
+        const int i = base_i + threadIdx.x;
+        const uint32_t h = (i < n && (i == 0 || (s_key[i] >> SHIFT) != (s_key[i - 1] >> SHIFT))) ? 1u : 0u;
         uint32_t chunk;
         const uint32_t hi = block_inclusive_scan(h, s_w, chunk);
         if (h) seg[carry + hi - 1] = uint32_t(i);
@@ -216,37 +343,105 @@ bwd_tile_partials(const uint2 *__restrict__ ranges, int W, int H, int tile_w, in
     if (threadIdx.x == 0) s_nseg = carry;
     __syncthreads();
     const int nseg = int(s_nseg);
-    if (blockIdx.y == 0) {
-        for (int u = threadIdx.x; u < int(r.y - r.x); u += T)
-            pkey[r.x + u] = u < nseg ? uint32_t(s_key[seg[u]] >> 32) : 0xFFFFFFFFu;
-    }
-    // each warp reduces one distinct Gaussian's rows of this channel slice
+    for (int u = threadIdx.x; u < int(r.y - r.x); u += T)
+        pkey[r.x + u] = u < nseg ? uint32_t(s_key[seg[u]] >> SHIFT) : 0xFFFFFFFFu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int cl = c0 + lane * 4;
-    const bool has_c = cl < C;
-    const int tile_x0 = tx * tile_w, tile_y0 = ty * tile_h;
+    // per-entry (dalpha, dA) sums: lanes take entries b + lane, b + lane + 32, ...
     for (int u = warp; u < nseg; u += T / 32) {
         const int b = int(seg[u]), e = (u + 1 < nseg) ? int(seg[u + 1]) : n;
-        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
         float4 sacc = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int i = b; i < e; ++i) {
-            const uint32_t loc = uint32_t(s_key[i]);
-            const int pix = int(loc) / K, j = int(loc) % K;
-            const int64_t pp = int64_t(tile_y0 + pix / tile_w) * W + tile_x0 + pix % tile_w;
-            const float w = wts[pp * K + j];
-            if (has_c) {
-                const float4 gg = *reinterpret_cast<const float4 *>(grad_out + pp * int64_t(C) + cl);
-                acc.x = fmaf(w, gg.x, acc.x); acc.y = fmaf(w, gg.y, acc.y);
-                acc.z = fmaf(w, gg.z, acc.z); acc.w = fmaf(w, gg.w, acc.w);
+        for (int i = b + lane; i < e; i += 32) {
+            float4 ee;
+            if (STAGE_E) {
+                ee = s_e4[i];
+            } else {
+                const uint32_t loc = uint32_t(s_key[i] & LOCAL_MASK);
+                const int pix = int(loc) / K, j = int(loc) - pix * K;
+                const int64_t pp = int64_t(ty * tile_h + pix / tile_w) * W + tx * tile_w + pix % tile_w;
+                ee = E4[pp * K + j];
             }
-            if (blockIdx.y == 0) {
-                const float4 ee = E[pp * K + j];
-                sacc.x += ee.x; sacc.y += ee.y; sacc.z += ee.z; sacc.w += ee.w;
+            sacc.x += ee.x; sacc.y += ee.y; sacc.z += ee.z; sacc.w += ee.w;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            sacc.x += __shfl_xor_sync(0xffffffffu, sacc.x, o);
+            sacc.y += __shfl_xor_sync(0xffffffffu, sacc.y, o);
+            sacc.z += __shfl_xor_sync(0xffffffffu, sacc.z, o);
+            sacc.w += __shfl_xor_sync(0xffffffffu, sacc.w, o);
+        }
+        if (lane == 0) partial_s[int64_t(r.x) + u] = sacc;
+    }
+    // the w * g sums, CH channels at a time (lane owns channels 2 lane, 2 lane + 1 of 64)
+    const int cpl = CH / 32;   // channels per lane: 1 or 2
+    int c_fail = -1;
+    for (int c = 0; c < nchunks; ++c) {
+        const int c0 = c * CH;
+        const float *gbuf = s_g;
+        if (use_tma) {
+            const int buf = c & 1;
+            if (threadIdx.x == 0) s_ok = tma_mbar_wait(&s_bar[buf], uint32_t(c >> 1) & 1u, kTmaSpin) ? 1 : 0;
+            __syncthreads();
+            if (!s_ok) { c_fail = c; break; }
+            gbuf = s_g + size_t(buf) * T * CH;
+        } else {
+            __syncthreads();   // the previous chunk is consumed
+            for (int i = threadIdx.x; i < T * (CH / 4); i += T) {
+                const int pix = i / (CH / 4), c4 = i - pix * (CH / 4);
+                const int gx = tx * tile_w + pix % tile_w, gy = ty * tile_h + pix / tile_w;
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (gx < W && gy < H && c0 + c4 * 4 < C)
+                    v = *reinterpret_cast<const float4 *>(grad_out + (int64_t(gy) * W + gx) * int64_t(C) + c0 + c4 * 4);
+                reinterpret_cast<float4 *>(s_g + pix * CH)[c4] = v;
+            }
+            __syncthreads();
+        }
+        for (int u = warp; u < nseg; u += T / 32) {
+            const int b = int(seg[u]), e = (u + 1 < nseg) ? int(seg[u + 1]) : n;
+            float2 acc = make_float2(0.f, 0.f);
+            int i = b;
+            if (cpl == 2) {
+                // eight entries in flight, packed FMAs
+                for (; i + 8 <= e; i += 8) {
+                    uint2 en[8];
+                    float2 gv[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) en[q] = s_ent[i + q];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) gv[q] = reinterpret_cast<const float2 *>(gbuf + en[q].x * CH)[lane];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) fma2v(acc, __uint_as_float(en[q].y), gv[q]);
+                }
+            }
+            for (; i < e; ++i) {
+                const uint2 en = s_ent[i];
+                const float2 gv = cpl == 2 ? reinterpret_cast<const float2 *>(gbuf + en.x * CH)[lane]
+                                           : make_float2(gbuf[en.x * CH + lane], 0.f);
+                fma2v(acc, __uint_as_float(en.y), gv);
+            }
+            float *dst = partial + (int64_t(r.x) + u) * C + c0;
+            if (cpl == 2) {
+                if (c0 + 2 * lane + 1 < C) reinterpret_cast<float2 *>(dst)[lane] = acc;
+                else if (c0 + 2 * lane < C) dst[2 * lane] = acc.x;
+            } else if (c0 + lane < C) {
+                dst[lane] = acc.x;
             }
         }
-        const int64_t slot = int64_t(r.x) + u;
-        if (has_c) *reinterpret_cast<float4 *>(partial + slot * C + cl) = acc;
-        if (blockIdx.y == 0 && lane == 0) partial_s[slot] = sacc;
+        if (use_tma) {
+            __syncthreads();   // every warp is done with this buffer: refill it
+            if (threadIdx.x == 0 && c + 2 < nchunks) {
+                const int buf = c & 1;
+                tma_expect_tx(&s_bar[buf], chunk_bytes);
+                tma_load_3d(s_g + size_t(buf) * T * CH, &gmap, (c + 2) * CH, tx * tile_w, ty * tile_h,
+                            &s_bar[buf]);
+            }
+        }
+    }
+    if (c_fail >= 0 && threadIdx.x == 0) {
+        // a staging copy did not arrive: report it, and let the copies still in
+        // flight (chunks c_fail and c_fail + 1) land before the CTA exits
+        atomicExch(&counters[CNT_STATUS], uint32_t(QR_ERR_DEVICE_TIMEOUT));
+        for (int cc = c_fail; cc < c_fail + 2 && cc < nchunks; ++cc)
+            tma_mbar_wait(&s_bar[cc & 1], uint32_t(cc >> 1) & 1u, kTmaSpin);
     }
 }
 
@@ -345,10 +540,21 @@ void launch_bwd_pixel(const qr_frame &f, const void *feat, const float *scale, i
     int64_t blocks = (warps * 32 + T - 1) / T;
     const int64_t cap = int64_t(sms_now()) * 8;
     if (blocks > cap) blocks = cap;
-    bwd_pixel<DT><<<unsigned(blocks), T, 0, s>>>(
-        slot<float4>(f, S_REC_M), slot<float4>(f, S_REC_C), slot<float>(f, S_REC_A),
-        static_cast<const unsigned char *>(feat), scale, C, ids, w, cnt, g, P, f.params.K,
-        f.camera.width, f.params.alpha_max, E);
+    // vectors of 16 bytes per lane when every lane holds the same number
+    const int nvec = C / VecB<DT>::C;
+    const int vpl = nvec % 32 == 0 ? nvec / 32 : 0;
+    auto go = [&](auto kern) {
+        kern<<<unsigned(blocks), T, 0, s>>>(
+            slot<float4>(f, S_REC_M), slot<float4>(f, S_REC_C), slot<float>(f, S_REC_A),
+            static_cast<const unsigned char *>(feat), scale, C, ids, w, cnt, g, P, f.params.K,
+            f.camera.width, f.params.alpha_max, E);
+    };
+    switch (vpl) {
+        case 1: go(bwd_pixel<DT, 1>); break;
+        case 2: go(bwd_pixel<DT, 2>); break;
+        case 4: go(bwd_pixel<DT, 4>); break;
+        default: go(bwd_pixel<DT, 0>); break;
+    }
 }
 
 }  // namespace
@@ -384,16 +590,48 @@ cudaError_t launch_backward(const qr_frame &f, const void *feat, const float *sc
         case QR_BF16: launch_bwd_pixel<QR_BF16>(f, feat, scale, C, ids, w, cnt, grad_out, E, s); break;
         case QR_FP8E4M3: launch_bwd_pixel<QR_FP8E4M3>(f, feat, scale, C, ids, w, cnt, grad_out, E, s); break;
     }
-    // per-tile partials
+    // per-tile partials; for K <= 8 the tile's rows of g are staged by TMA
+    // (3-D boxes {64 channels, tile_w pixels, tile_h rows} of the [H][W][C]
+    // gradient, double-buffered) when the driver provides a tensor-map encoder
     int npow2 = 1;
     while (npow2 < 256 * K) npow2 <<= 1;
-    const size_t smem = size_t(npow2) * 8 + size_t(256 * K) * 4;
-    e = cudaFuncSetAttribute(bwd_tile_partials, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    const int CH = K <= 8 ? 64 : 32;
+    CUtensorMap gmap;
+    std::memset(&gmap, 0, sizeof(gmap));
+    int use_tma = 0;
+    if (K <= 8) {
+        EncodeTiled enc = tensor_map_encoder();
+        const cuuint64_t dims[3] = {cuuint64_t(C), cuuint64_t(f.camera.width), cuuint64_t(f.camera.height)};
+        const cuuint64_t strides[2] = {cuuint64_t(C) * 4, cuuint64_t(C) * 4 * cuuint64_t(f.camera.width)};
+        const cuuint32_t box[3] = {cuuint32_t(CH), cuuint32_t(f.params.tile_w), cuuint32_t(f.params.tile_h)};
+        const cuuint32_t estr[3] = {1, 1, 1};
+        if (enc && enc(&gmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(grad_out), dims,
+                       strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
+            use_tma = 1;
+    }
+    // keys sized for 8 bytes (an upper bound for both key types), E terms staged for K <= 8
+    const size_t g_off = (size_t(npow2) * 8 + size_t(256 * K) * (12 + (K <= 8 ? 16 : 0)) + 1023) & ~size_t(1023);
+    const size_t smem = 1024 + g_off + size_t(use_tma ? 2 : 1) * 256 * CH * 4;
+    auto tp = [&](auto kern) {
+        cudaError_t ee = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (ee != cudaSuccess) return ee;
+        kern<<<unsigned(tiles), T, smem, s>>>(slot<uint2>(f, S_RANGES), f.camera.width,
+                                               f.camera.height, f.params.tile_w, f.tiles_x, ids, w,
+                                               cnt, E, grad_out, C, K, CH, partial, partial_s, key0,
+                                               gmap, use_tma, counters);
+        return cudaSuccess;
+    };
+    if (f.n < (int64_t(1) << 21)) {
+        e = K == 1 ? tp(bwd_tile_partials<1, uint32_t>) : K == 2 ? tp(bwd_tile_partials<2, uint32_t>)
+          : K <= 4 ? tp(bwd_tile_partials<4, uint32_t>) : K <= 8 ? tp(bwd_tile_partials<8, uint32_t>)
+                   : tp(bwd_tile_partials<0, unsigned long long>);
+    } else {
+        e = K == 1 ? tp(bwd_tile_partials<1, unsigned long long>) : K == 2 ? tp(bwd_tile_partials<2, unsigned long long>)
+          : K <= 4 ? tp(bwd_tile_partials<4, unsigned long long>) : K <= 8 ? tp(bwd_tile_partials<8, unsigned long long>)
+                   : tp(bwd_tile_partials<0, unsigned long long>);
+    }
     if (e != cudaSuccess) return e;
-    dim3 grid(unsigned(tiles), unsigned((C + CHUNK - 1) / CHUNK));
-    bwd_tile_partials<<<grid, T, smem, s>>>(slot<uint2>(f, S_RANGES), f.camera.width,
-                                            f.camera.height, f.params.tile_w, f.tiles_x, ids, w,
-                                            cnt, E, grad_out, C, K, partial, partial_s, key0);
     // stable sort of the slots by Gaussian id (ids < n; unused slots carry 0xFFFFFFFF)
     const uint32_t *d_x = counters + CNT_SORT_N;
     iota_kernel<<<sms_now() * 4, T, 0, s>>>(val0, d_x);

@@ -264,6 +264,63 @@ __device__ __forceinline__ void walk_event(Walk &w, float Tt, float a, float tau
     else w.T = Tt;
 }
 
+// ---------------------------------------------------------------- register bitonic sort
+// Sorts NTH*E keys (32- or 64-bit) held E per thread in blocked order (thread t holds
+// positions tE .. tE+E-1; pad with ~0).  Compare-exchange partners i and i^j
+// meet inside a thread for j < E (register swaps), across lanes for
+// E <= j < 32E (shuffles) and across warps for larger j (the shared-memory
+// buffer s of NTH*E keys, two barriers per stage).  All NTH threads call it.
+__device__ __forceinline__ unsigned long long shfl_xor_key(unsigned long long x, int m) {
+    const uint32_t lo = __shfl_xor_sync(0xffffffffu, uint32_t(x), m);
+    const uint32_t hi = __shfl_xor_sync(0xffffffffu, uint32_t(x >> 32), m);
+    return (static_cast<unsigned long long>(hi) << 32) | lo;
+}
+__device__ __forceinline__ uint32_t shfl_xor_key(uint32_t x, int m) {
+    return __shfl_xor_sync(0xffffffffu, x, m);
+}
+
+template <int E, int NTH, typename KT>
+__device__ void bitonic_regs(KT (&v)[E], KT *s) {
+    constexpr int N = NTH * E;
+    const int base = threadIdx.x * E;
+    for (int k = 2; k <= N; k <<= 1) {
+        for (int j = k >> 1; j >= 32 * E; j >>= 1) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) s[base + e] = v[e];
+            __syncthreads();
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int i = base + e;
+                const KT y = s[i ^ j];
+                const bool take_min = ((i & j) == 0) == ((i & k) == 0);
+                v[e] = take_min ? (v[e] < y ? v[e] : y) : (v[e] < y ? y : v[e]);
+            }
+            __syncthreads();
+        }
+        for (int j = min(k >> 1, 16 * E); j >= E; j >>= 1) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int i = base + e;
+                const KT y = shfl_xor_key(v[e], j / E);
+                const bool take_min = ((i & j) == 0) == ((i & k) == 0);
+                v[e] = take_min ? (v[e] < y ? v[e] : y) : (v[e] < y ? y : v[e]);
+            }
+        }
+#pragma unroll
+        for (int J = E / 2; J > 0; J >>= 1) {
+            if (J >= k) continue;
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                if ((e ^ J) > e) {
+                    const bool up = ((base + e) & k) == 0;
+                    const KT a = v[e], b = v[e ^ J];
+                    if ((a > b) == up) { v[e] = b; v[e ^ J] = a; }
+                }
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------- compensated arithmetic
 // Pairs (hi, lo) of FP32 with |lo| <= ulp(hi)/2 represent hi + lo exactly;
 // the error-free transformations are Knuth's TwoSum, Dekker's FastTwoSum and

@@ -25,9 +25,8 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 
-#include <mutex>
-
 #include "qr_internal.cuh"
+#include "tma.cuh"
 
 namespace qr {
 namespace {
@@ -459,30 +458,10 @@ size_t tma_smem_bytes(int Q, int C) {
     return 1024 + size_t(STAGES) * A_TILE + size_t(C) * Q * 4 + 256;
 }
 
-using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
-                                 const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
-                                 const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
-                                 CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-// The driver's tensor-map encoder, resolved once through the runtime (no
-// link-time dependency on libcuda).
-EncodeTiled encode_tiled() {
-    static std::once_flag once;
-    static EncodeTiled fn = nullptr;
-    std::call_once(once, [] {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess && q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<EncodeTiled>(p);
-    });
-    return fn;
-}
-
 template <int QN>
 cudaError_t run_tma(const float *map, const uint16_t *q, int64_t P, int C, float *out, int *status,
                     cudaStream_t s) {
-    EncodeTiled enc = encode_tiled();
+    EncodeTiled enc = tensor_map_encoder();
     if (!enc) return cudaErrorNotSupported;
     CUtensorMap tm;
     const cuuint64_t dims[2] = {cuuint64_t(C), cuuint64_t(P)};

@@ -291,61 +291,16 @@ __device__ __forceinline__ void bitonic_smem(unsigned long long *s, int npow2) {
         }
 }
 
-// Bitonic sort of a bucket of up to 256*E keys held in registers, E per
-// thread in blocked order (thread t holds positions tE .. tE+E-1), padded
-// with ~0.  Compare-exchange partners i and i^j meet inside a thread for
-// j < E (register swaps), across lanes for E <= j < 32E (shuffles) and
-// across warps for larger j (shared memory, two barriers per stage).
-__device__ __forceinline__ unsigned long long shfl_xor64(unsigned long long x, int m) {
-    const uint32_t lo = __shfl_xor_sync(0xffffffffu, uint32_t(x), m);
-    const uint32_t hi = __shfl_xor_sync(0xffffffffu, uint32_t(x >> 32), m);
-    return (static_cast<unsigned long long>(hi) << 32) | lo;
-}
-
+// A bucket of up to 256*E keys, loaded E per thread in blocked order and
+// padded with ~0, sorted by the register bitonic network, ids written out.
 template <int E>
 __device__ void sort_registers(const unsigned long long *__restrict__ src, int n,
                                unsigned long long *s, uint32_t *__restrict__ dst) {
-    constexpr int N = T * E;
     const int base = threadIdx.x * E;
     unsigned long long v[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) v[e] = base + e < n ? src[base + e] : ~0ull;
-    for (int k = 2; k <= N; k <<= 1) {
-        for (int j = k >> 1; j >= 32 * E; j >>= 1) {
-#pragma unroll
-            for (int e = 0; e < E; ++e) s[base + e] = v[e];
-            __syncthreads();
-#pragma unroll
-            for (int e = 0; e < E; ++e) {
-                const int i = base + e;
-                const unsigned long long y = s[i ^ j];
-                const bool take_min = ((i & j) == 0) == ((i & k) == 0);
-                v[e] = take_min ? (v[e] < y ? v[e] : y) : (v[e] < y ? y : v[e]);
-            }
-            __syncthreads();
-        }
-        for (int j = min(k >> 1, 16 * E); j >= E; j >>= 1) {
-#pragma unroll
-            for (int e = 0; e < E; ++e) {
-                const int i = base + e;
-                const unsigned long long y = shfl_xor64(v[e], j / E);
-                const bool take_min = ((i & j) == 0) == ((i & k) == 0);
-                v[e] = take_min ? (v[e] < y ? v[e] : y) : (v[e] < y ? y : v[e]);
-            }
-        }
-#pragma unroll
-        for (int J = E / 2; J > 0; J >>= 1) {
-            if (J >= k) continue;
-#pragma unroll
-            for (int e = 0; e < E; ++e) {
-                if ((e ^ J) > e) {
-                    const bool up = ((base + e) & k) == 0;
-                    const unsigned long long a = v[e], b = v[e ^ J];
-                    if ((a > b) == up) { v[e] = b; v[e ^ J] = a; }
-                }
-            }
-        }
-    }
+    bitonic_regs<E, T, unsigned long long>(v, s);
 #pragma unroll
     for (int e = 0; e < E; ++e)
         if (base + e < n) dst[base + e] = uint32_t(v[e]);

@@ -22,8 +22,10 @@
 //      into a partial row, stored at a fixed slot of that tile's intersection
 //      range;
 //   3. a stable radix sort of the slot keys by Gaussian id;
-//   4. bwd_reduce: one warp per Gaussian sums its partials in tile order and
-//      writes its gradient row (zeros for unselected Gaussians).
+//   4. bwd_reduce_runs + bwd_reduce: a two-level sum of each Gaussian's
+//      partials in tile order -- fixed 32-slot chunks first, then the chunk
+//      sums per Gaussian -- so a Gaussian selected in many tiles is not one
+//      long serial chain; unselected Gaussians keep zero rows.
 #include <cstring>
 
 #include <cuda_bf16.h>
@@ -464,8 +466,90 @@ gauss_ranges(const uint32_t *__restrict__ key, const uint32_t *__restrict__ d_n,
     }
 }
 
+// Level 1 of the per-Gaussian reduction: the gid-sorted slot array is cut
+// into fixed chunks of 32 positions; one warp per chunk sums each run of equal
+// gids inside the chunk (four rows in flight, lanes over channels) into the
+// run's first row.  A run is a whole Gaussian or the part of a long one that
+// falls in the chunk.
+constexpr int kRunChunk = 32;
+
 __global__ void __launch_bounds__(T)
-bwd_reduce(const uint2 *__restrict__ gr, const uint32_t *__restrict__ slot_of,
+bwd_reduce_runs(const uint32_t *__restrict__ skey, const uint32_t *__restrict__ sval,
+                const uint32_t *__restrict__ d_n, int64_t N, int C, float *__restrict__ partial,
+                float4 *__restrict__ partial_s) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t n = *d_n;
+    const int64_t warp0 = (int64_t(blockIdx.x) * T + threadIdx.x) >> 5;
+    const int64_t nw = (int64_t(gridDim.x) * T) >> 5;
+    const int64_t nchunk = (int64_t(n) + kRunChunk - 1) / kRunChunk;
+    for (int64_t ch = warp0; ch < nchunk; ch += nw) {
+        const uint32_t i0 = uint32_t(ch * kRunChunk);
+        const uint32_t i1 = min(n, i0 + uint32_t(kRunChunk));
+        // lane k holds position i0 + k: its key and slot
+        const uint32_t my_key = i0 + lane < i1 ? skey[i0 + lane] : 0xFFFFFFFFu;
+        const uint32_t my_slot = i0 + lane < i1 ? sval[i0 + lane] : 0u;
+        const int len = int(i1 - i0);
+        int a0 = 0;
+        while (a0 < len) {
+            const uint32_t k = __shfl_sync(0xffffffffu, my_key, a0);
+            if (int64_t(k) >= N) break;   // unused slots sort last
+            // run [a0, a1) of key k
+            const unsigned same = __ballot_sync(0xffffffffu, my_key == k && lane >= a0 && lane < len);
+            const int a1 = 32 - __clz(same);   // one past the last lane of the run (runs are contiguous)
+            const uint32_t head = __shfl_sync(0xffffffffu, my_slot, a0);
+            if (a1 - a0 > 1) {
+                // every lane runs the channel loop (the shuffles need the whole
+                // warp); lanes past the row's end only skip the loads and stores
+                for (int cb = 0; cb < C; cb += 128) {
+                    const int c = cb + lane * 4;
+                    const bool act = c < C;
+                    float4 acc = act ? *reinterpret_cast<const float4 *>(partial + int64_t(head) * C + c)
+                                     : make_float4(0.f, 0.f, 0.f, 0.f);
+                    int q = a0 + 1;
+                    for (; q + 4 <= a1; q += 4) {
+                        float4 v[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const uint32_t sl = __shfl_sync(0xffffffffu, my_slot, q + u);
+                            v[u] = act ? *reinterpret_cast<const float4 *>(partial + int64_t(sl) * C + c)
+                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+                        }
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            acc.x += v[u].x; acc.y += v[u].y; acc.z += v[u].z; acc.w += v[u].w;
+                        }
+                    }
+                    for (; q < a1; ++q) {
+                        const uint32_t sl = __shfl_sync(0xffffffffu, my_slot, q);
+                        if (act) {
+                            const float4 v = *reinterpret_cast<const float4 *>(partial + int64_t(sl) * C + c);
+                            acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
+                        }
+                    }
+                    if (act) *reinterpret_cast<float4 *>(partial + int64_t(head) * C + c) = acc;
+                }
+                // the (dalpha, dA) terms: lane k of the run adds its slot's, fixed tree
+                float4 sv = (lane >= a0 && lane < a1) ? partial_s[my_slot] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    sv.x += __shfl_xor_sync(0xffffffffu, sv.x, o);
+                    sv.y += __shfl_xor_sync(0xffffffffu, sv.y, o);
+                    sv.z += __shfl_xor_sync(0xffffffffu, sv.z, o);
+                    sv.w += __shfl_xor_sync(0xffffffffu, sv.w, o);
+                }
+                if (lane == 0) partial_s[head] = sv;
+            }
+            a0 = a1;
+        }
+    }
+}
+
+// Level 2: one warp per Gaussian with slots adds the heads of its runs (its
+// first position and every chunk start inside its range) in order and writes
+// its gradient row; Gaussians without slots keep the zeros the output was
+// cleared to.
+__global__ void __launch_bounds__(T)
+bwd_reduce(const uint2 *__restrict__ gr, const uint32_t *__restrict__ sval,
            const float *__restrict__ partial, const float4 *__restrict__ partial_s, int64_t N,
            int C, float *__restrict__ grad_feat, float *__restrict__ grad_alpha,
            float *__restrict__ grad_conic) {
@@ -474,26 +558,29 @@ bwd_reduce(const uint2 *__restrict__ gr, const uint32_t *__restrict__ slot_of,
     const int64_t nw = (int64_t(gridDim.x) * T) >> 5;
     for (int64_t u = warp0; u < N; u += nw) {
         const uint2 r = gr[u];
+        if (r.y <= r.x) continue;
         float *out = grad_feat + u * int64_t(C);
+        // run heads: r.x, then every multiple of the chunk size inside (r.x, r.y)
+        const uint32_t first_chunk = r.x / kRunChunk + 1;
         for (int c = lane * 4; c < C; c += 128) {
-            float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-            for (uint32_t i = r.x; i < r.y; ++i) {
-                const float4 v = *reinterpret_cast<const float4 *>(partial + int64_t(slot_of[i]) * C + c);
+            float4 acc = *reinterpret_cast<const float4 *>(partial + int64_t(sval[r.x]) * C + c);
+            for (uint32_t h = first_chunk * kRunChunk; h < r.y; h += kRunChunk) {
+                const float4 v = *reinterpret_cast<const float4 *>(partial + int64_t(sval[h]) * C + c);
                 acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
             }
             *reinterpret_cast<float4 *>(out + c) = acc;
         }
         if (lane == 0) {
-            float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
-            for (uint32_t i = r.x; i < r.y; ++i) {
-                const float4 v = partial_s[slot_of[i]];
-                s.x += v.x; s.y += v.y; s.z += v.z; s.w += v.w;
+            float4 sacc = partial_s[sval[r.x]];
+            for (uint32_t h = first_chunk * kRunChunk; h < r.y; h += kRunChunk) {
+                const float4 v = partial_s[sval[h]];
+                sacc.x += v.x; sacc.y += v.y; sacc.z += v.z; sacc.w += v.w;
             }
-            if (grad_alpha) grad_alpha[u] = s.x;
+            if (grad_alpha) grad_alpha[u] = sacc.x;
             if (grad_conic) {
-                grad_conic[3 * u] = s.y;
-                grad_conic[3 * u + 1] = s.z;
-                grad_conic[3 * u + 2] = s.w;
+                grad_conic[3 * u] = sacc.y;
+                grad_conic[3 * u + 1] = sacc.z;
+                grad_conic[3 * u + 2] = sacc.w;
             }
         }
     }
@@ -643,13 +730,17 @@ cudaError_t launch_backward(const qr_frame &f, const void *feat, const float *sc
     const uint32_t *skey = in_b ? key1 : key0;
     const uint32_t *sval = in_b ? val1 : val0;
     gauss_ranges<<<sms_now() * 4, T, 0, s>>>(skey, d_x, f.n, gr);
+    // gradient rows of Gaussians that no pixel selected are zero
+    e = cudaMemsetAsync(grad_feat, 0, size_t(f.n) * size_t(C) * 4, s);
+    if (e != cudaSuccess) return e;
+    bwd_reduce_runs<<<sms_now() * 8, T, 0, s>>>(skey, sval, d_x, f.n, C, partial, partial_s);
     int64_t blocks = (f.n * 32 + T - 1) / T;
     const int64_t cap = int64_t(sms_now()) * 16;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
     bwd_reduce<<<unsigned(blocks), T, 0, s>>>(gr, sval, partial, partial_s, f.n, C, grad_feat,
                                               grad_alpha, grad_conic);
-    count_launch(5);
+    count_launch(6);
     return cudaGetLastError();
 }
 

@@ -294,9 +294,12 @@ qr_status qr_backward(const qr_frame *frame, const void *feat, const float *feat
 /* Loss of the differentiation workload (the paper trains with the contrastive
  * Eq. 2 on CLIP targets, which are not available): L = mean over pixels with
  * counts > 0 of 1 - cos(F_p, t_p), cos = F.t / (max(|F|, 1e-8) max(|t|, 1e-8)).
- * feature_map, target [P][C]; loss_out [2] device floats receive (L, 1/n);
+ * feature_map, target [P][C]; loss_out [2] device floats receive (L, 1/n)
+ * (they hold integer counters while the call runs on the stream);
  * grad [P][C] receives dL/dF (zero on pixels without quantile Gaussians);
- * scratch [P] floats.  Deterministic reduction. */
+ * scratch [P] floats (overwritten).  Deterministic reduction: the covered
+ * pixels are counted with integer atomics and the per-pixel terms are summed
+ * over fixed ranges whose sums are added in range order. */
 qr_status qr_cosine_loss(const float *feature_map, const float *target, const uint8_t *counts,
                          int64_t P, int32_t C, float *loss_out, float *grad, float *scratch,
                          qr_stream stream);

@@ -254,25 +254,27 @@ bwd_tile_partials(const uint2 *__restrict__ ranges, int W, int H, int tile_w, in
                   const float *__restrict__ grad_out, int C, int K, int CH,
                   float *__restrict__ partial, float4 *__restrict__ partial_s,
                   uint32_t *__restrict__ pkey, const __grid_constant__ CUtensorMap gmap, int use_tma,
-                  uint32_t *__restrict__ counters) {
+                  int nbuf, int stage_e, uint32_t *__restrict__ counters) {
     constexpr bool K32 = sizeof(KT) == 4;
     constexpr int SHIFT = K32 ? 11 : 32;
-    constexpr bool STAGE_E = E > 0;   // per-entry E terms staged (K <= 8)
     extern __shared__ __align__(16) unsigned char s_dyn[];
     __shared__ uint32_t s_w[32];
     __shared__ uint32_t s_nseg;
     __shared__ __align__(8) uint64_t s_bar[2];
     __shared__ int s_ok;
+    __shared__ float2 s_piece[(T / 32) * 2 * 32];   // per warp: continued piece, begun piece
+    __shared__ int s_first[T / 32], s_last[T / 32];
     int npow2 = 1;
     while (npow2 < T * K) npow2 <<= 1;
-    // 1024-byte aligned base (the launch adds 1 KB of slack for it)
-    unsigned char *base = reinterpret_cast<unsigned char *>(
-        (reinterpret_cast<uintptr_t>(s_dyn) + 1023) & ~uintptr_t(1023));
+    // 1024-byte aligned base (the launch adds 1 KB of slack for it), formed as an
+    // offset from the shared array so every access below stays a shared-memory
+    // access (a round trip through an integer address would make them generic)
+    unsigned char *base = s_dyn + ((1024u - (uint32_t(__cvta_generic_to_shared(s_dyn)) & 1023u)) & 1023u);
     KT *s_key = reinterpret_cast<KT *>(base);                                    // npow2
     uint32_t *seg = reinterpret_cast<uint32_t *>(s_key + npow2);                 // T*K
     uint2 *s_ent = reinterpret_cast<uint2 *>(seg + T * K);                       // T*K (pixel, w)
-    float4 *s_e4 = reinterpret_cast<float4 *>(s_ent + T * K);                    // T*K if STAGE_E
-    const size_t g_off = (size_t(npow2) * sizeof(KT) + size_t(T * K) * (12 + (STAGE_E ? 16 : 0)) +
+    float4 *s_e4 = reinterpret_cast<float4 *>(s_ent + T * K);                    // T*K if stage_e
+    const size_t g_off = (size_t(npow2) * sizeof(KT) + size_t(T * K) * (12 + (stage_e ? 16 : 0)) +
                           1023) & ~size_t(1023);
     float *s_g = reinterpret_cast<float *>(base + g_off);                       // [2][T*CH]
     const int tile = blockIdx.x;
@@ -293,11 +295,11 @@ bwd_tile_partials(const uint2 *__restrict__ ranges, int W, int H, int tile_w, in
     const int nchunks = (C + CH - 1) / CH;
     const uint32_t chunk_bytes = uint32_t(T) * uint32_t(CH) * 4u;
     if (use_tma && threadIdx.x == 0) {
-        // the first two chunks of g fly while the keys are sorted
+        // the first nbuf (1 or 2) chunks of g fly while the keys are sorted
         tma_mbar_init(&s_bar[0], 1);
         tma_mbar_init(&s_bar[1], 1);
         tma_fence_init();
-        for (int b = 0; b < 2 && b < nchunks; ++b) {
+        for (int b = 0; b < nbuf && b < nchunks; ++b) {
             tma_expect_tx(&s_bar[b], chunk_bytes);
             tma_load_3d(s_g + size_t(b) * T * CH, &gmap, b * CH, tx * tile_w, ty * tile_h, &s_bar[b]);
         }
@@ -329,7 +331,7 @@ bwd_tile_partials(const uint2 *__restrict__ ranges, int W, int H, int tile_w, in
         const int pix = int(loc) / K, j = int(loc) - pix * K;
         const int64_t pp = int64_t(ty * tile_h + pix / tile_w) * W + tx * tile_w + pix % tile_w;
         s_ent[i] = make_uint2(uint32_t(pix), __float_as_uint(wts[pp * K + j]));
-        if (STAGE_E) s_e4[i] = E4[pp * K + j];
+        if (stage_e) s_e4[i] = E4[pp * K + j];
     }
     if (threadIdx.x == 0) s_nseg = 0;
     // segment starts
@@ -354,7 +356,7 @@ bwd_tile_partials(const uint2 *__restrict__ ranges, int W, int H, int tile_w, in
         float4 sacc = make_float4(0.f, 0.f, 0.f, 0.f);
         for (int i = b + lane; i < e; i += 32) {
             float4 ee;
-            if (STAGE_E) {
+            if (stage_e) {
                 ee = s_e4[i];
             } else {
                 const uint32_t loc = uint32_t(s_key[i] & LOCAL_MASK);
@@ -375,13 +377,21 @@ bwd_tile_partials(const uint2 *__restrict__ ranges, int W, int H, int tile_w, in
     }
     // the w * g sums, CH channels at a time (lane owns channels 2 lane, 2 lane + 1 of 64)
     const int cpl = CH / 32;   // channels per lane: 1 or 2
+    constexpr int NWARP = T / 32;
+    const int r0 = int(int64_t(n) * warp / NWARP), r1 = int(int64_t(n) * (warp + 1) / NWARP);
+    int u_lo = 0;   // the segment holding entry r0: the last u with seg[u] <= r0
+    for (int hi = nseg; hi - u_lo > 1;) {
+        const int mid = (u_lo + hi) >> 1;
+        if (int(seg[mid]) <= r0) u_lo = mid; else hi = mid;
+    }
     int c_fail = -1;
     for (int c = 0; c < nchunks; ++c) {
         const int c0 = c * CH;
         const float *gbuf = s_g;
         if (use_tma) {
-            const int buf = c & 1;
-            if (threadIdx.x == 0) s_ok = tma_mbar_wait(&s_bar[buf], uint32_t(c >> 1) & 1u, kTmaSpin) ? 1 : 0;
+            const int buf = nbuf == 2 ? (c & 1) : 0;
+            const uint32_t parity = uint32_t(nbuf == 2 ? c >> 1 : c) & 1u;
+            if (threadIdx.x == 0) s_ok = tma_mbar_wait(&s_bar[buf], parity, kTmaSpin) ? 1 : 0;
             __syncthreads();
             if (!s_ok) { c_fail = c; break; }
             gbuf = s_g + size_t(buf) * T * CH;
@@ -397,12 +407,13 @@ bwd_tile_partials(const uint2 *__restrict__ ranges, int W, int H, int tile_w, in
             }
             __syncthreads();
         }
-        for (int u = warp; u < nseg; u += T / 32) {
-            const int b = int(seg[u]), e = (u + 1 < nseg) ? int(seg[u + 1]) : n;
+        // balanced walk: warp w sums entries [w n / 8, (w + 1) n / 8); a segment
+        // that crosses a warp boundary is split into pieces, the piece holding
+        // its start is completed below with the next warps' pieces, in order
+        auto walk = [&](int b, int e) {
             float2 acc = make_float2(0.f, 0.f);
             int i = b;
             if (cpl == 2) {
-                // eight entries in flight, packed FMAs
                 for (; i + 8 <= e; i += 8) {
                     uint2 en[8];
                     float2 gv[8];
@@ -420,6 +431,9 @@ bwd_tile_partials(const uint2 *__restrict__ ranges, int W, int H, int tile_w, in
                                            : make_float2(gbuf[en.x * CH + lane], 0.f);
                 fma2v(acc, __uint_as_float(en.y), gv);
             }
+            return acc;
+        };
+        auto store = [&](int u, float2 acc) {
             float *dst = partial + (int64_t(r.x) + u) * C + c0;
             if (cpl == 2) {
                 if (c0 + 2 * lane + 1 < C) reinterpret_cast<float2 *>(dst)[lane] = acc;
@@ -427,23 +441,57 @@ bwd_tile_partials(const uint2 *__restrict__ ranges, int W, int H, int tile_w, in
             } else if (c0 + lane < C) {
                 dst[lane] = acc.x;
             }
+        };
+        int first_u = -1, last_u = -1;
+        if (r0 < r1) {
+            for (int u = u_lo; u < nseg && int(seg[u]) < r1; ++u) {
+                const int sb = int(seg[u]), se = (u + 1 < nseg) ? int(seg[u + 1]) : n;
+                const float2 acc = walk(max(sb, r0), min(se, r1));
+                if (sb < r0) {            // continues a segment begun by an earlier warp
+                    s_piece[(warp * 2) * 32 + lane] = acc;
+                    first_u = u;
+                } else if (se > r1) {     // begins a segment that later warps continue
+                    s_piece[(warp * 2 + 1) * 32 + lane] = acc;
+                    last_u = u;
+                } else {
+                    store(u, acc);
+                }
+            }
+        }
+        if (lane == 0) {
+            s_first[warp] = first_u;
+            s_last[warp] = last_u;
+        }
+        __syncthreads();
+        if (s_last[warp] >= 0) {
+            const int u = s_last[warp];
+            float2 acc = s_piece[(warp * 2 + 1) * 32 + lane];
+            for (int w2 = warp + 1; w2 < NWARP; ++w2) {
+                const int a2 = int(int64_t(n) * w2 / NWARP), b2 = int(int64_t(n) * (w2 + 1) / NWARP);
+                if (a2 >= b2) continue;        // an empty range holds no piece
+                if (s_first[w2] != u) break;
+                const float2 v = s_piece[(w2 * 2) * 32 + lane];
+                acc.x += v.x;
+                acc.y += v.y;
+            }
+            store(u, acc);
         }
         if (use_tma) {
             __syncthreads();   // every warp is done with this buffer: refill it
-            if (threadIdx.x == 0 && c + 2 < nchunks) {
-                const int buf = c & 1;
+            if (threadIdx.x == 0 && c + nbuf < nchunks) {
+                const int buf = nbuf == 2 ? (c & 1) : 0;
                 tma_expect_tx(&s_bar[buf], chunk_bytes);
-                tma_load_3d(s_g + size_t(buf) * T * CH, &gmap, (c + 2) * CH, tx * tile_w, ty * tile_h,
+                tma_load_3d(s_g + size_t(buf) * T * CH, &gmap, (c + nbuf) * CH, tx * tile_w, ty * tile_h,
                             &s_bar[buf]);
             }
         }
     }
     if (c_fail >= 0 && threadIdx.x == 0) {
         // a staging copy did not arrive: report it, and let the copies still in
-        // flight (chunks c_fail and c_fail + 1) land before the CTA exits
+        // flight (chunks c_fail .. c_fail + nbuf - 1) land before the CTA exits
         atomicExch(&counters[CNT_STATUS], uint32_t(QR_ERR_DEVICE_TIMEOUT));
-        for (int cc = c_fail; cc < c_fail + 2 && cc < nchunks; ++cc)
-            tma_mbar_wait(&s_bar[cc & 1], uint32_t(cc >> 1) & 1u, kTmaSpin);
+        for (int cc = c_fail; cc < c_fail + nbuf && cc < nchunks; ++cc)
+            tma_mbar_wait(&s_bar[nbuf == 2 ? (cc & 1) : 0], uint32_t(nbuf == 2 ? cc >> 1 : cc) & 1u, kTmaSpin);
     }
 }
 
@@ -697,19 +745,30 @@ cudaError_t launch_backward(const qr_frame &f, const void *feat, const float *sc
                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
             use_tma = 1;
     }
-    // keys sized for 8 bytes (an upper bound for both key types), E terms staged for K <= 8
-    const size_t g_off = (size_t(npow2) * 8 + size_t(256 * K) * (12 + (K <= 8 ? 16 : 0)) + 1023) & ~size_t(1023);
-    const size_t smem = 1024 + g_off + size_t(use_tma ? 2 : 1) * 256 * CH * 4;
+    // One CTA per tile.  With TMA staging and K <= 8 the CTA holds one g chunk
+    // (64 channels x 256 pixels, 64 KB) and reads the E terms from global
+    // memory, so two CTAs share an SM and one's sort and gathers overlap the
+    // other's walk; otherwise one CTA per SM stages the E terms and
+    // double-buffers g.
+    const bool k32 = K <= 8 && f.n < (int64_t(1) << 21);
+    const size_t key_bytes = k32 ? 4 : 8;
+    const int nbuf = use_tma && K <= 8 ? 1 : use_tma ? 2 : 1;
+    const int stage_e = (K <= 8 && nbuf == 2) ? 1 : 0;
+    const size_t g_off = (size_t(npow2) * key_bytes + size_t(256 * K) * (12 + (stage_e ? 16 : 0)) + 1023) &
+                         ~size_t(1023);
+    const size_t smem = 1024 + g_off + size_t(nbuf) * 256 * CH * 4;
     auto tp = [&](auto kern) {
         cudaError_t ee = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (ee != cudaSuccess) return ee;
+        ee = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         if (ee != cudaSuccess) return ee;
         kern<<<unsigned(tiles), T, smem, s>>>(slot<uint2>(f, S_RANGES), f.camera.width,
                                                f.camera.height, f.params.tile_w, f.tiles_x, ids, w,
                                                cnt, E, grad_out, C, K, CH, partial, partial_s, key0,
-                                               gmap, use_tma, counters);
+                                               gmap, use_tma, nbuf, stage_e, counters);
         return cudaSuccess;
     };
-    if (f.n < (int64_t(1) << 21)) {
+    if (k32) {
         e = K == 1 ? tp(bwd_tile_partials<1, uint32_t>) : K == 2 ? tp(bwd_tile_partials<2, uint32_t>)
           : K <= 4 ? tp(bwd_tile_partials<4, uint32_t>) : K <= 8 ? tp(bwd_tile_partials<8, uint32_t>)
                    : tp(bwd_tile_partials<0, unsigned long long>);

@@ -2,8 +2,11 @@
 // the contrastive Eq. 2 on CLIP targets): L = mean over pixels with at least
 // one quantile Gaussian of 1 - cos(F_p, t_p), cos = F.t / (max(|F|,eps) max(|t|,eps)),
 // and its gradient dL/dF.  Deterministic: the covered pixels are counted
-// first (1/n), one pass writes every pixel's term and its gradient row already
-// scaled by 1/n, and one CTA sums the terms in a fixed order.
+// first (integer atomics, so the count does not depend on their order), one
+// pass writes every pixel's term and its gradient row already scaled by 1/n,
+// and the terms are summed over fixed contiguous ranges, one per CTA, whose
+// sums the last CTA to finish adds in range order.  out[0] and out[1] hold
+// the ticket and the count as integers until that CTA writes (L, 1/n).
 #include "qr_internal.cuh"
 
 namespace qr {
@@ -29,19 +32,29 @@ __device__ __forceinline__ unsigned long long count_covered(const uint8_t *__res
     return n;
 }
 
-// Number of covered pixels -> 1/n (out[1]), before the gradient pass needs it.
+// Number of covered pixels, added into out[1] as an integer (zeroed before),
+// before the gradient pass needs it.  CTA b counts the pixels of range b:
+// [b range, (b + 1) range), the last one up to P.
 __global__ void __launch_bounds__(1024)
-cos_count(const uint8_t *__restrict__ counts, int64_t P, float *__restrict__ out) {
+cos_count(const uint8_t *__restrict__ counts, int64_t P, int64_t range, float *__restrict__ out) {
     __shared__ unsigned long long s_n[32];
-    unsigned long long n = count_covered(counts, P);
+    const int64_t i0 = int64_t(blockIdx.x) * range;
+    const int64_t len = blockIdx.x + 1 == gridDim.x ? P - i0 : range;   // the last range takes the rest
+    unsigned long long n = len > 0 ? count_covered(counts + i0, len) : 0ull;
     for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
     if ((threadIdx.x & 31) == 0) s_n[threadIdx.x >> 5] = n;
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned long long nn = 0;
         for (int w = 0; w < int(blockDim.x >> 5); ++w) nn += s_n[w];
-        out[1] = float(1.0 / (nn > 0 ? double(nn) : 1.0));
+        if (nn) atomicAdd(reinterpret_cast<unsigned int *>(out + 1), unsigned(nn));
     }
+}
+
+// 1/n from the integer count held in out[1]
+__device__ __forceinline__ float inv_count(const float *out) {
+    const unsigned nn = *reinterpret_cast<const volatile unsigned int *>(out + 1);
+    return float(1.0 / (nn > 0 ? double(nn) : 1.0));
 }
 
 // One warp per pixel: the pixel's term 1 - cos and its gradient row, already
@@ -54,7 +67,7 @@ cos_terms(const float *__restrict__ F, const float *__restrict__ tgt,
     const int lane = threadIdx.x & 31;
     const int64_t w0 = (int64_t(blockIdx.x) * T + threadIdx.x) >> 5;
     const int64_t nw = (int64_t(gridDim.x) * T) >> 5;
-    const float s = out[1];
+    const float s = inv_count(out);
     for (int64_t p = w0; p < P; p += nw) {
         const bool on = counts[p] > 0;
         const float *f = F + p * C;
@@ -115,39 +128,67 @@ __device__ __forceinline__ void two_sum_acc(float &s, float &c, float x) {
     s = t;
 }
 
-// L = (sum of the terms) / n, coalesced reads in a fixed order, eight loads in
-// flight per thread; per-thread compensated sums are combined in double.
+// L = (sum of the terms) / n.  CTA b sums the terms of range b (coalesced
+// reads, eight loads in flight per thread, compensated per-thread sums
+// combined in double).  With one CTA it writes L directly; otherwise it
+// stores its sum, as the two 32-bit halves of a double, over the first two
+// terms of its range (every range holds at least 8192), which no other CTA
+// reads, and the last CTA to take a ticket adds the sums in range order.
 __global__ void __launch_bounds__(1024)
-cos_final(const float *__restrict__ term, const uint8_t *__restrict__ counts, int64_t P,
-          float *__restrict__ out) {
+cos_final(float *__restrict__ term, int64_t P, int64_t range, float *__restrict__ out) {
     __shared__ double s_sum[32];
-    __shared__ unsigned long long s_n[32];
+    __shared__ unsigned s_ticket;
+    const int64_t i0 = int64_t(blockIdx.x) * range;
+    const int64_t len = blockIdx.x + 1 == gridDim.x ? P - i0 : range;   // the last range takes the rest
+    const float *t0 = term + i0;
     float sf = 0.f, cf = 0.f;
     const int64_t step = blockDim.x;
     int64_t i = threadIdx.x;
-    for (; i + 7 * step < P; i += 8 * step) {
+    for (; i + 7 * step < len; i += 8 * step) {
         float t[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) t[u] = term[i + u * step];
+        for (int u = 0; u < 8; ++u) t[u] = t0[i + u * step];
 #pragma unroll
         for (int u = 0; u < 8; ++u) two_sum_acc(sf, cf, t[u]);
     }
-    for (; i < P; i += step) two_sum_acc(sf, cf, term[i]);
+    for (; i < len; i += step) two_sum_acc(sf, cf, t0[i]);
     double sum = double(sf) + double(cf);
-    unsigned long long n = count_covered(counts, P);
-    for (int o = 16; o > 0; o >>= 1) {
-        sum += __shfl_xor_sync(0xffffffffu, sum, o);
-        n += __shfl_xor_sync(0xffffffffu, n, o);
-    }
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) { s_sum[warp] = sum; s_n[warp] = n; }
-    __syncthreads();
+    if (lane == 0) s_sum[warp] = sum;
+    __syncthreads();   // every read of this range is done
+    if (gridDim.x == 1) {
+        if (threadIdx.x == 0) {
+            double sm = 0.0;
+            for (int w = 0; w < int(blockDim.x >> 5); ++w) sm += s_sum[w];
+            const unsigned nn = *reinterpret_cast<const volatile unsigned int *>(out + 1);
+            const double n = nn > 0 ? double(nn) : 1.0;
+            out[0] = float(sm / n);
+            out[1] = float(1.0 / n);
+        }
+        return;
+    }
     if (threadIdx.x == 0) {
         double sm = 0.0;
-        unsigned long long nn = 0;
-        for (int w = 0; w < int(blockDim.x >> 5); ++w) { sm += s_sum[w]; nn += s_n[w]; }
-        out[0] = float(sm / (nn > 0 ? double(nn) : 1.0));
+        for (int w = 0; w < int(blockDim.x >> 5); ++w) sm += s_sum[w];
+        unsigned *slot = reinterpret_cast<unsigned *>(term + i0);
+        slot[0] = unsigned(__double2loint(sm));
+        slot[1] = unsigned(__double2hiint(sm));
+        __threadfence();
+        s_ticket = atomicAdd(reinterpret_cast<unsigned int *>(out), 1u);
     }
+    __syncthreads();
+    if (s_ticket != gridDim.x - 1 || threadIdx.x != 0) return;
+    __threadfence();
+    double total = 0.0;
+    for (unsigned b = 0; b < gridDim.x; ++b) {
+        const volatile unsigned *slot = reinterpret_cast<const volatile unsigned *>(term + int64_t(b) * range);
+        total += __hiloint2double(int(slot[1]), int(slot[0]));
+    }
+    const unsigned nn = *reinterpret_cast<const volatile unsigned int *>(out + 1);
+    const double n = nn > 0 ? double(nn) : 1.0;
+    out[0] = float(total / n);
+    out[1] = float(1.0 / n);
 }
 
 }  // namespace
@@ -160,10 +201,17 @@ cudaError_t launch_cosine_loss(const float *F, const float *tgt, const uint8_t *
     const bool vec = C % 4 == 0 && (reinterpret_cast<uintptr_t>(F) & 15) == 0 &&
                      (reinterpret_cast<uintptr_t>(tgt) & 15) == 0 &&
                      (reinterpret_cast<uintptr_t>(grad) & 15) == 0;
-    cos_count<<<1, 1024, 0, s>>>(counts, P, out2);
+    // ranges of at least 8192 pixels (each holds the two words of its sum), at
+    // most two per SM; the last range takes the rest of the pixels
+    int64_t range = (P + 2 * sms - 1) / (2 * sms);
+    if (range < 8192) range = 8192;
+    const unsigned nblk = unsigned(P / range > 1 ? P / range : 1);
+    cudaError_t e = cudaMemsetAsync(out2, 0, 2 * sizeof(float), s);
+    if (e != cudaSuccess) return e;
+    cos_count<<<nblk, 1024, 0, s>>>(counts, P, range, out2);
     if (vec) cos_terms<true><<<sms * 8, T, 0, s>>>(F, tgt, counts, P, C, 1e-8f, term, grad, out2);
     else cos_terms<false><<<sms * 8, T, 0, s>>>(F, tgt, counts, P, C, 1e-8f, term, grad, out2);
-    cos_final<<<1, 1024, 0, s>>>(term, counts, P, out2);
+    cos_final<<<nblk, 1024, 0, s>>>(term, P, range, out2);
     count_launch(3);
     return cudaGetLastError();
 }

@@ -476,8 +476,7 @@ def profile_train(local, steps=3):
         q.qr_sort(fr)
         q.qr_select(fr, ids, w, cnt)
         q.qr_blend(table, None, ids, w, cnt, out)
-        loss, gmap = q.qr_cosine_loss(out, tgt, cnt)
-        q.qr_backward(fr, table, None, ids, w, cnt, gmap, want_conic=False)
+        loss = q.qr_cosine_backward(fr, table, None, ids, w, cnt, out, tgt, want_conic=False)[0]
     torch.cuda.synchronize()
     return {"profile": "train", "steps": steps, "loss": round(float(loss.item()), 6)}
 
@@ -491,9 +490,8 @@ def run_train_step(local, steps=10):
 
     def step():
         res = q.render_frame(gd, table, cam, K=K, max_isect=2_000_000)
-        loss, gmap = q.qr_cosine_loss(res["out"], tgt, res["counts"])
-        gf, ga, _ = q.qr_backward(res["frame"], table, None, res["ids"], res["weights"],
-                                  res["counts"], gmap, want_conic=False)
+        loss = q.qr_cosine_backward(res["frame"], table, None, res["ids"], res["weights"],
+                                    res["counts"], res["out"], tgt, want_conic=False)[0]
         return loss
     for _ in range(2):
         step()
@@ -515,9 +513,8 @@ def run_train_step(local, steps=10):
         q.qr_sort(fr)
         q.qr_select(fr, ids, w, cnt)
         q.qr_blend(table, None, ids, w, cnt, out)
-        keep["loss"], gmap = q.qr_cosine_loss(out, tgt, cnt)
-        keep["gf"], keep["ga"], _ = q.qr_backward(fr, table, None, ids, w, cnt, gmap,
-                                                  want_conic=False)
+        keep["loss"], _, keep["gf"], keep["ga"], _ = q.qr_cosine_backward(
+            fr, table, None, ids, w, cnt, out, tgt, want_conic=False)
     side = torch.cuda.Stream(device=dev)
     side.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(side):

@@ -304,6 +304,26 @@ qr_status qr_cosine_loss(const float *feature_map, const float *target, const ui
                          int64_t P, int32_t C, float *loss_out, float *grad, float *scratch,
                          qr_stream stream);
 
+/* The cosine loss above and the backward above in one call, with the loss's
+ * per-pixel pass fused into the backward's: every pixel's dL/dF is formed in
+ * registers from its map and target rows, written to grad_map (the upstream
+ * gradient of the rest of the backward) and dotted with its quantile
+ * Gaussians' features at once, so grad_map is not read back for those dots.
+ * Same results as qr_cosine_loss(feature_map, target, mask, ...) followed by
+ * qr_backward(..., grad_out = grad_map, ...) up to floating-point summation
+ * order.  counts: the forward's quantile counts; mask [P]: pixels in the loss
+ * (e.g. the counts themselves); loss_out [2] device floats -> (L, 1/n);
+ * grad_map [P][C] -> dL/dF; feature_map, target, grad_map, grad_feat 16-byte
+ * aligned; ws: qr_cosine_backward_workspace_bytes(frame, C) bytes, 256-byte
+ * aligned (the backward's workspace plus P floats of loss terms). */
+size_t qr_cosine_backward_workspace_bytes(const qr_frame *frame, int32_t C);
+qr_status qr_cosine_backward(const qr_frame *frame, const void *feat, const float *feat_scale,
+                             qr_dtype dtype, int32_t C, const int32_t *ids, const float *weights,
+                             const uint8_t *counts, const float *feature_map, const float *target,
+                             const uint8_t *mask, float *loss_out, float *grad_map,
+                             float *grad_feat, float *grad_opacity, float *grad_conic, void *ws,
+                             size_t ws_bytes, qr_stream stream);
+
 /* ---------------------------------------------------------------- relevance */
 
 /* Open-vocabulary relevance (Sec. 5 scores features against text embeddings by

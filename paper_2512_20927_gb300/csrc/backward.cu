@@ -74,14 +74,25 @@ __device__ __forceinline__ void widen<QR_FP8E4M3>(const uint4 v, float *o) {
 }
 
 // ------------------------------------------------------------------ 1. per pixel
-template <int DT, int VPL>
+// LOSS: the upstream gradient is the cosine loss's, formed here from the map
+// F and the target (the lane's slices, held in registers) and written to
+// grad_out; the pixel's loss term goes to term.  Needs VPL > 0.
+struct PixLoss {
+    const float *F;
+    const float *tgt;
+    const uint8_t *mask;
+    float *term;
+    const float *out2;
+};
+
+template <int DT, int VPL, bool LOSS>
 __global__ void __launch_bounds__(T)
 bwd_pixel(const float4 *__restrict__ rec_m, const float4 *__restrict__ rec_w,
           const float *__restrict__ rec_a, const unsigned char *__restrict__ feat,
           const float *__restrict__ fscale, int C, const int32_t *__restrict__ ids,
           const float *__restrict__ wts, const uint8_t *__restrict__ cnt,
-          const float *__restrict__ grad_out, int64_t P, int K, int W, float alpha_max,
-          float4 *__restrict__ E) {
+          float *__restrict__ grad_out, int64_t P, int K, int W, float alpha_max,
+          float4 *__restrict__ E, PixLoss loss) {
     constexpr int CPV = VecB<DT>::C, ESZ = VecB<DT>::E;
     constexpr unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -89,8 +100,54 @@ bwd_pixel(const float4 *__restrict__ rec_m, const float4 *__restrict__ rec_w,
     const int64_t nw = (int64_t(gridDim.x) * T) >> 5;
     const int nvec = C / CPV;                      // 16-byte vectors per feature row
     const size_t row_bytes = size_t(C) * ESZ;
+    const float inv_n = LOSS ? cos_inv_count(loss.out2) : 0.f;
     for (int64_t p = warp0; p < P; p += nw) {
         const int m = cnt[p];
+        float gr[VPL > 0 ? VPL : 1][CPV];
+        float *g = grad_out + p * int64_t(C);
+        if (LOSS) {
+            // the loss term and dL/dF of this pixel (every pixel, zero rows
+            // outside the mask), as the loss's own pass computes them
+            const bool on = loss.mask[p] > 0;
+            float tr[VPL > 0 ? VPL : 1][CPV];
+            float dot = 0.f, ff = 0.f, tt = 0.f;
+#pragma unroll
+            for (int t = 0; t < VPL; ++t) {
+                const float4 *fv = reinterpret_cast<const float4 *>(loss.F + p * int64_t(C) + (lane + 32 * t) * CPV);
+                const float4 *tv = reinterpret_cast<const float4 *>(loss.tgt + p * int64_t(C) + (lane + 32 * t) * CPV);
+#pragma unroll
+                for (int q = 0; q < CPV / 4; ++q) {
+                    const float4 a = fv[q], b = tv[q];
+                    gr[t][4 * q] = a.x; gr[t][4 * q + 1] = a.y; gr[t][4 * q + 2] = a.z; gr[t][4 * q + 3] = a.w;
+                    tr[t][4 * q] = b.x; tr[t][4 * q + 1] = b.y; tr[t][4 * q + 2] = b.z; tr[t][4 * q + 3] = b.w;
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < VPL; ++t)
+#pragma unroll
+                for (int q = 0; q < CPV; ++q) {
+                    dot = fmaf(gr[t][q], tr[t][q], dot);
+                    ff = fmaf(gr[t][q], gr[t][q], ff);
+                    tt = fmaf(tr[t][q], tr[t][q], tt);
+                }
+            for (int o = 16; o > 0; o >>= 1) {
+                dot += __shfl_xor_sync(FULL, dot, o);
+                ff += __shfl_xor_sync(FULL, ff, o);
+                tt += __shfl_xor_sync(FULL, tt, o);
+            }
+            const CosCoeffs cc = cos_coeffs(dot, ff, tt, 1e-8f);
+            if (lane == 0) loss.term[p] = on ? 1.f - cc.cs : 0.f;
+#pragma unroll
+            for (int t = 0; t < VPL; ++t) {
+#pragma unroll
+                for (int q = 0; q < CPV; ++q)
+                    gr[t][q] = on ? -(tr[t][q] * cc.k1 - gr[t][q] * cc.k2) * inv_n : 0.f;
+                float4 *gv = reinterpret_cast<float4 *>(g + (lane + 32 * t) * CPV);
+#pragma unroll
+                for (int q = 0; q < CPV / 4; ++q)
+                    __stcg(gv + q, make_float4(gr[t][4 * q], gr[t][4 * q + 1], gr[t][4 * q + 2], gr[t][4 * q + 3]));
+            }
+        }
         if (m == 0) continue;
         const float ux = float(p % W) + 0.5f, uy = float(p / W) + 0.5f;
         const int id = lane < m ? ids[p * K + lane] : 0;
@@ -98,17 +155,17 @@ bwd_pixel(const float4 *__restrict__ rec_m, const float4 *__restrict__ rec_w,
         // s_j = g . f_j for every quantile Gaussian j (lane j keeps s_j): the
         // lane's slice of g is held in registers, four rows are loaded at once
         // and their four partial dots reduced together
-        const float *g = grad_out + p * int64_t(C);
         float s_mine = 0.f;
         if (VPL > 0) {
-            float gr[VPL > 0 ? VPL : 1][CPV];
+            if (!LOSS) {
 #pragma unroll
-            for (int t = 0; t < VPL; ++t) {
-                const float4 *gv = reinterpret_cast<const float4 *>(g + (lane + 32 * t) * CPV);
+                for (int t = 0; t < VPL; ++t) {
+                    const float4 *gv = reinterpret_cast<const float4 *>(g + (lane + 32 * t) * CPV);
 #pragma unroll
-                for (int q = 0; q < CPV / 4; ++q) {
-                    const float4 gg = gv[q];
-                    gr[t][4 * q] = gg.x; gr[t][4 * q + 1] = gg.y; gr[t][4 * q + 2] = gg.z; gr[t][4 * q + 3] = gg.w;
+                    for (int q = 0; q < CPV / 4; ++q) {
+                        const float4 gg = gv[q];
+                        gr[t][4 * q] = gg.x; gr[t][4 * q + 1] = gg.y; gr[t][4 * q + 2] = gg.z; gr[t][4 * q + 3] = gg.w;
+                    }
                 }
             }
             for (int j0 = 0; j0 < m; j0 += 4) {
@@ -666,40 +723,57 @@ BwdLayout bwd_layout(const qr_frame &f, int C) {
     return L;
 }
 
+// vectors of 16 bytes per lane when every lane holds the same number (0: not)
+int bwd_vpl(qr_dtype dt, int C) {
+    const int cpv = dt == QR_F32 ? 4 : dt == QR_BF16 ? 8 : 16;
+    const int nvec = C % cpv == 0 ? C / cpv : 0;
+    const int vpl = nvec % 32 == 0 ? nvec / 32 : 0;
+    return vpl == 1 || vpl == 2 || vpl == 4 ? vpl : 0;
+}
+
+// loss != nullptr: the fused cosine-loss pass (bwd_vpl(dt, C) > 0), g is its output
 template <int DT>
 void launch_bwd_pixel(const qr_frame &f, const void *feat, const float *scale, int C,
-                      const int32_t *ids, const float *w, const uint8_t *cnt, const float *g,
-                      float4 *E, cudaStream_t s) {
+                      const int32_t *ids, const float *w, const uint8_t *cnt, float *g,
+                      float4 *E, const CosLossArgs *loss, cudaStream_t s) {
     const int64_t P = num_pixels(f);
     const int64_t warps = P;
     int64_t blocks = (warps * 32 + T - 1) / T;
     const int64_t cap = int64_t(sms_now()) * 8;
     if (blocks > cap) blocks = cap;
-    // vectors of 16 bytes per lane when every lane holds the same number
-    const int nvec = C / VecB<DT>::C;
-    const int vpl = nvec % 32 == 0 ? nvec / 32 : 0;
+    const int vpl = bwd_vpl(qr_dtype(DT), C);
+    PixLoss pl{};
+    if (loss) pl = PixLoss{loss->F, loss->tgt, loss->mask, loss->term, loss->out2};
     auto go = [&](auto kern) {
         kern<<<unsigned(blocks), T, 0, s>>>(
             slot<float4>(f, S_REC_M), slot<float4>(f, S_REC_C), slot<float>(f, S_REC_A),
             static_cast<const unsigned char *>(feat), scale, C, ids, w, cnt, g, P, f.params.K,
-            f.camera.width, f.params.alpha_max, E);
+            f.camera.width, f.params.alpha_max, E, pl);
     };
+    if (loss) {
+        switch (vpl) {
+            case 1: go(bwd_pixel<DT, 1, true>); break;
+            case 2: go(bwd_pixel<DT, 2, true>); break;
+            default: go(bwd_pixel<DT, 4, true>); break;
+        }
+        return;
+    }
     switch (vpl) {
-        case 1: go(bwd_pixel<DT, 1>); break;
-        case 2: go(bwd_pixel<DT, 2>); break;
-        case 4: go(bwd_pixel<DT, 4>); break;
-        default: go(bwd_pixel<DT, 0>); break;
+        case 1: go(bwd_pixel<DT, 1, false>); break;
+        case 2: go(bwd_pixel<DT, 2, false>); break;
+        case 4: go(bwd_pixel<DT, 4, false>); break;
+        default: go(bwd_pixel<DT, 0, false>); break;
     }
 }
 
 }  // namespace
 
-size_t backward_workspace_bytes(const qr_frame &f, int C) { return bwd_layout(f, C).total; }
+namespace {
 
-cudaError_t launch_backward(const qr_frame &f, const void *feat, const float *scale, qr_dtype dt,
-                            int C, const int32_t *ids, const float *w, const uint8_t *cnt,
-                            const float *grad_out, float *grad_feat, float *grad_alpha,
-                            float *grad_conic, void *ws, cudaStream_t s) {
+cudaError_t backward_impl(const qr_frame &f, const void *feat, const float *scale, qr_dtype dt,
+                          int C, const int32_t *ids, const float *w, const uint8_t *cnt,
+                          const float *grad_out, const CosLossArgs *loss, float *grad_feat,
+                          float *grad_alpha, float *grad_conic, void *ws, cudaStream_t s) {
     const BwdLayout L = bwd_layout(f, C);
     char *b = static_cast<char *>(ws);
     float4 *E = reinterpret_cast<float4 *>(b + L.e);
@@ -720,10 +794,16 @@ cudaError_t launch_backward(const qr_frame &f, const void *feat, const float *sc
     if (grad_alpha) e = cudaMemsetAsync(grad_alpha, 0, size_t(f.n) * 4, s);
     if (e == cudaSuccess && grad_conic) e = cudaMemsetAsync(grad_conic, 0, size_t(f.n) * 12, s);
     if (e != cudaSuccess) return e;
+    float *g = const_cast<float *>(grad_out);   // written only by the fused loss pass
     switch (dt) {
-        case QR_F32: launch_bwd_pixel<QR_F32>(f, feat, scale, C, ids, w, cnt, grad_out, E, s); break;
-        case QR_BF16: launch_bwd_pixel<QR_BF16>(f, feat, scale, C, ids, w, cnt, grad_out, E, s); break;
-        case QR_FP8E4M3: launch_bwd_pixel<QR_FP8E4M3>(f, feat, scale, C, ids, w, cnt, grad_out, E, s); break;
+        case QR_F32: launch_bwd_pixel<QR_F32>(f, feat, scale, C, ids, w, cnt, g, E, loss, s); break;
+        case QR_BF16: launch_bwd_pixel<QR_BF16>(f, feat, scale, C, ids, w, cnt, g, E, loss, s); break;
+        case QR_FP8E4M3: launch_bwd_pixel<QR_FP8E4M3>(f, feat, scale, C, ids, w, cnt, g, E, loss, s); break;
+    }
+    if (loss) {
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = launch_cos_final(loss->term, num_pixels(f), loss->out2, s);
+        if (e != cudaSuccess) return e;
     }
     // per-tile partials; for K <= 8 the tile's rows of g are staged by TMA
     // (3-D boxes {64 channels, tile_w pixels, tile_h rows} of the [H][W][C]
@@ -801,6 +881,41 @@ cudaError_t launch_backward(const qr_frame &f, const void *feat, const float *sc
                                               grad_alpha, grad_conic);
     count_launch(6);
     return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t backward_workspace_bytes(const qr_frame &f, int C) { return bwd_layout(f, C).total; }
+
+size_t backward_cos_workspace_bytes(const qr_frame &f, int C) {
+    return bwd_layout(f, C).total + ((size_t(num_pixels(f)) * 4 + 255) & ~size_t(255));
+}
+
+cudaError_t launch_backward(const qr_frame &f, const void *feat, const float *scale, qr_dtype dt,
+                            int C, const int32_t *ids, const float *w, const uint8_t *cnt,
+                            const float *grad_out, float *grad_feat, float *grad_alpha,
+                            float *grad_conic, void *ws, cudaStream_t s) {
+    return backward_impl(f, feat, scale, dt, C, ids, w, cnt, grad_out, nullptr, grad_feat,
+                         grad_alpha, grad_conic, ws, s);
+}
+
+cudaError_t launch_backward_cos(const qr_frame &f, const void *feat, const float *scale,
+                                qr_dtype dt, int C, const int32_t *ids, const float *w,
+                                const uint8_t *cnt, const CosLossArgs &loss, float *grad_feat,
+                                float *grad_alpha, float *grad_conic, void *ws, cudaStream_t s) {
+    const int64_t P = num_pixels(f);
+    if (bwd_vpl(dt, C) == 0) {
+        // rows that do not split evenly over the lanes: the loss's own pass first
+        cudaError_t e = launch_cosine_loss(loss.F, loss.tgt, loss.mask, P, C, loss.term, loss.out2,
+                                           loss.grad_map, s);
+        if (e != cudaSuccess) return e;
+        return launch_backward(f, feat, scale, dt, C, ids, w, cnt, loss.grad_map, grad_feat,
+                               grad_alpha, grad_conic, ws, s);
+    }
+    cudaError_t e = launch_cos_count(loss.mask, P, loss.out2, s);
+    if (e != cudaSuccess) return e;
+    return backward_impl(f, feat, scale, dt, C, ids, w, cnt, loss.grad_map, &loss, grad_feat,
+                         grad_alpha, grad_conic, ws, s);
 }
 
 }  // namespace qr

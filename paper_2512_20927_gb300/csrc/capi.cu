@@ -341,6 +341,43 @@ qr_status qr_backward(const qr_frame *frame, const void *feat, const float *feat
                                      reinterpret_cast<cudaStream_t>(stream)));
 }
 
+size_t qr_cosine_backward_workspace_bytes(const qr_frame *frame, int32_t C) {
+    if (!frame_ok(frame) || C < 4 || C % 4) return 0;
+    return backward_cos_workspace_bytes(*frame, C);
+}
+
+qr_status qr_cosine_backward(const qr_frame *frame, const void *feat, const float *feat_scale,
+                             qr_dtype dtype, int32_t C, const int32_t *ids, const float *weights,
+                             const uint8_t *counts, const float *feature_map, const float *target,
+                             const uint8_t *mask, float *loss_out, float *grad_map,
+                             float *grad_feat, float *grad_opacity, float *grad_conic, void *ws,
+                             size_t ws_bytes, qr_stream stream) {
+    if (!frame_ok(frame) || !ids || !weights || !counts || !feature_map || !target || !mask ||
+        !loss_out || !grad_map || !grad_feat || !ws)
+        return QR_ERR_INVALID_ARG;
+    qr_status st = check_feat(feat, feat_scale, dtype, C);
+    if (st != QR_OK) return st;
+    if (!aligned16(feature_map) || !aligned16(target) || !aligned16(grad_map) ||
+        !aligned16(grad_feat) || (reinterpret_cast<uintptr_t>(ws) & (kAlign - 1)))
+        return QR_ERR_ALIGNMENT;
+    if (ws_bytes < backward_cos_workspace_bytes(*frame, C)) return QR_ERR_INVALID_ARG;
+    const int64_t P = num_pixels(*frame);
+    if (P == 0) return QR_OK;
+    const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    CosLossArgs loss;
+    loss.F = feature_map;
+    loss.tgt = target;
+    loss.mask = mask;
+    loss.term = reinterpret_cast<float *>(static_cast<char *>(ws) + backward_workspace_bytes(*frame, C));
+    loss.out2 = loss_out;
+    loss.grad_map = grad_map;
+    if (frame->n == 0)   // nothing to differentiate: the loss alone
+        return from_cuda(launch_cosine_loss(feature_map, target, mask, P, C, loss.term, loss_out,
+                                            grad_map, s));
+    return from_cuda(launch_backward_cos(*frame, feat, feat_scale, dtype, C, ids, weights, counts,
+                                         loss, grad_feat, grad_opacity, grad_conic, ws, s));
+}
+
 qr_status qr_cosine_loss(const float *feature_map, const float *target, const uint8_t *counts,
                          int64_t P, int32_t C, float *loss_out, float *grad, float *scratch,
                          qr_stream stream) {

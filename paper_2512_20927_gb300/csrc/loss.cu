@@ -51,11 +51,6 @@ cos_count(const uint8_t *__restrict__ counts, int64_t P, int64_t range, float *_
     }
 }
 
-// 1/n from the integer count held in out[1]
-__device__ __forceinline__ float inv_count(const float *out) {
-    const unsigned nn = *reinterpret_cast<const volatile unsigned int *>(out + 1);
-    return float(1.0 / (nn > 0 ? double(nn) : 1.0));
-}
 
 // One warp per pixel: the pixel's term 1 - cos and its gradient row, already
 // multiplied by 1/n.  VEC: 16-byte loads and stores (C % 4 == 0, aligned rows).
@@ -67,7 +62,7 @@ cos_terms(const float *__restrict__ F, const float *__restrict__ tgt,
     const int lane = threadIdx.x & 31;
     const int64_t w0 = (int64_t(blockIdx.x) * T + threadIdx.x) >> 5;
     const int64_t nw = (int64_t(gridDim.x) * T) >> 5;
-    const float s = inv_count(out);
+    const float s = cos_inv_count(out);
     for (int64_t p = w0; p < P; p += nw) {
         const bool on = counts[p] > 0;
         const float *f = F + p * C;
@@ -95,13 +90,10 @@ cos_terms(const float *__restrict__ F, const float *__restrict__ tgt,
             ff += __shfl_xor_sync(0xffffffffu, ff, o);
             tt += __shfl_xor_sync(0xffffffffu, tt, o);
         }
-        const float nf_raw = sqrtf(ff), nt = fmaxf(sqrtf(tt), eps);
-        const bool big = nf_raw > eps;
-        const float nf = big ? nf_raw : eps;
-        const float cs = dot / (nf * nt);
-        if (lane == 0) term[p] = on ? 1.f - cs : 0.f;
+        const CosCoeffs cc = cos_coeffs(dot, ff, tt, eps);
+        if (lane == 0) term[p] = on ? 1.f - cc.cs : 0.f;
         float *gp = grad + p * C;
-        const float k1 = 1.f / (nf * nt), k2 = big ? dot / (nf * nf * nf * nt) : 0.f;
+        const float k1 = cc.k1, k2 = cc.k2;
         if (VEC) {
             const float4 *f4 = reinterpret_cast<const float4 *>(f);
             const float4 *t4 = reinterpret_cast<const float4 *>(t);
@@ -193,27 +185,56 @@ cos_final(float *__restrict__ term, int64_t P, int64_t range, float *__restrict_
 
 }  // namespace
 
-cudaError_t launch_cosine_loss(const float *F, const float *tgt, const uint8_t *counts, int64_t P,
-                               int C, float *term, float *out2, float *grad, cudaStream_t s) {
+namespace {
+// ranges of at least 8192 pixels (each holds the two words of its sum), at
+// most two per SM; the last range takes the rest of the pixels
+struct Ranges {
+    int64_t range;
+    unsigned nblk;
+};
+Ranges loss_ranges(int64_t P, int sms) {
+    int64_t range = (P + 2 * sms - 1) / (2 * sms);
+    if (range < 8192) range = 8192;
+    return {range, unsigned(P / range > 1 ? P / range : 1)};
+}
+int sm_count() {
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms;
+}
+}  // namespace
+
+cudaError_t launch_cos_count(const uint8_t *counts, int64_t P, float *out2, cudaStream_t s) {
+    const Ranges r = loss_ranges(P, sm_count());
+    cudaError_t e = cudaMemsetAsync(out2, 0, 2 * sizeof(float), s);
+    if (e != cudaSuccess) return e;
+    cos_count<<<r.nblk, 1024, 0, s>>>(counts, P, r.range, out2);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cos_final(float *term, int64_t P, float *out2, cudaStream_t s) {
+    const Ranges r = loss_ranges(P, sm_count());
+    cos_final<<<r.nblk, 1024, 0, s>>>(term, P, r.range, out2);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cosine_loss(const float *F, const float *tgt, const uint8_t *counts, int64_t P,
+                               int C, float *term, float *out2, float *grad, cudaStream_t s) {
+    const int sms = sm_count();
     const bool vec = C % 4 == 0 && (reinterpret_cast<uintptr_t>(F) & 15) == 0 &&
                      (reinterpret_cast<uintptr_t>(tgt) & 15) == 0 &&
                      (reinterpret_cast<uintptr_t>(grad) & 15) == 0;
-    // ranges of at least 8192 pixels (each holds the two words of its sum), at
-    // most two per SM; the last range takes the rest of the pixels
-    int64_t range = (P + 2 * sms - 1) / (2 * sms);
-    if (range < 8192) range = 8192;
-    const unsigned nblk = unsigned(P / range > 1 ? P / range : 1);
-    cudaError_t e = cudaMemsetAsync(out2, 0, 2 * sizeof(float), s);
+    cudaError_t e = launch_cos_count(counts, P, out2, s);
     if (e != cudaSuccess) return e;
-    cos_count<<<nblk, 1024, 0, s>>>(counts, P, range, out2);
     if (vec) cos_terms<true><<<sms * 8, T, 0, s>>>(F, tgt, counts, P, C, 1e-8f, term, grad, out2);
     else cos_terms<false><<<sms * 8, T, 0, s>>>(F, tgt, counts, P, C, 1e-8f, term, grad, out2);
-    cos_final<<<nblk, 1024, 0, s>>>(term, P, range, out2);
-    count_launch(3);
-    return cudaGetLastError();
+    count_launch(1);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_cos_final(term, P, out2, s);
 }
 
 }  // namespace qr

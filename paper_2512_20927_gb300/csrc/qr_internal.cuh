@@ -73,6 +73,53 @@ cudaError_t launch_backward(const qr_frame &f, const void *feat, const float *sc
                             float *grad_conic, void *ws, cudaStream_t s);
 cudaError_t launch_cosine_loss(const float *F, const float *tgt, const uint8_t *counts, int64_t P,
                                int C, float *term, float *out2, float *grad, cudaStream_t s);
+// the loss's two reductions, for a caller that forms the terms and the
+// gradient itself: the covered-pixel count into out2[1] (zeroed first) and
+// the final in-order sum that leaves (L, 1/n) in out2
+cudaError_t launch_cos_count(const uint8_t *counts, int64_t P, float *out2, cudaStream_t s);
+cudaError_t launch_cos_final(float *term, int64_t P, float *out2, cudaStream_t s);
+
+// The cosine loss fused into the backward's per-pixel pass: F, tgt [P][C],
+// mask [P] (pixels in the loss), term [P] scratch, out2 [2] -> (L, 1/n),
+// grad_map [P][C] -> dL/dF (then the backward's upstream gradient).
+struct CosLossArgs {
+    const float *F;
+    const float *tgt;
+    const uint8_t *mask;
+    float *term;
+    float *out2;
+    float *grad_map;
+};
+size_t backward_cos_workspace_bytes(const qr_frame &f, int C);   // + P floats of loss terms
+cudaError_t launch_backward_cos(const qr_frame &f, const void *feat, const float *scale,
+                                qr_dtype dt, int C, const int32_t *ids, const float *w,
+                                const uint8_t *cnt, const CosLossArgs &loss, float *grad_feat,
+                                float *grad_alpha, float *grad_conic, void *ws, cudaStream_t s);
+
+// 1/n from the integer covered-pixel count that out2[1] holds between the
+// count and the final sum
+__device__ __forceinline__ float cos_inv_count(const float *out2) {
+    const unsigned nn = *reinterpret_cast<const volatile unsigned int *>(out2 + 1);
+    return float(1.0 / (nn > 0 ? double(nn) : 1.0));
+}
+
+// Per-pixel cosine term from the reduced dot = F.t, ff = |F|^2, tt = |t|^2:
+// cs = F.t / (max(|F|,eps) max(|t|,eps)); dL/dF = -(t k1 - F k2) / n with
+// k1 = 1 / (nf nt) and k2 = F.t / (nf^3 nt) (zero when |F| <= eps, where
+// max(|F|, eps) is constant).
+struct CosCoeffs {
+    float cs, k1, k2;
+};
+__device__ __forceinline__ CosCoeffs cos_coeffs(float dot, float ff, float tt, float eps) {
+    const float nf_raw = sqrtf(ff), nt = fmaxf(sqrtf(tt), eps);
+    const bool big = nf_raw > eps;
+    const float nf = big ? nf_raw : eps;
+    CosCoeffs c;
+    c.cs = dot / (nf * nt);
+    c.k1 = 1.f / (nf * nt);
+    c.k2 = big ? dot / (nf * nf * nf * nt) : 0.f;
+    return c;
+}
 
 struct BatchView;
 bool batch_supported(qr_dtype dt, int C);

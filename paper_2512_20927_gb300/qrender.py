@@ -98,6 +98,9 @@ SIGNATURES = {
     "qr_backward": (_S, [ctypes.POINTER(qr_frame), _P, _P, _S, _I32, _P, _P, _P, _P, _P, _P, _P,
                          _P, ctypes.c_size_t, _P]),
     "qr_cosine_loss": (_S, [_P, _P, _P, _I64, _I32, _P, _P, _P, _P]),
+    "qr_cosine_backward_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(qr_frame), _I32]),
+    "qr_cosine_backward": (_S, [ctypes.POINTER(qr_frame), _P, _P, _S, _I32, _P, _P, _P, _P, _P,
+                                _P, _P, _P, _P, _P, _P, _P, ctypes.c_size_t, _P]),
     "qr_relevance": (_S, [_P, _P, _I32, _I32, _I64, _P, _P, _P]),
     "qr_batch_workspace_bytes": (ctypes.c_size_t, [_I32]),
     "qr_batch_prepare": (_S, [ctypes.POINTER(qr_view), _I32, _P, ctypes.c_size_t,
@@ -347,6 +350,38 @@ def qr_backward(fr: Frame, feat, feat_scale, ids, weights, counts, grad_out, wan
                               _ptr(grad_out.contiguous()), _ptr(gf), _ptr(ga), _ptr(gc), wsp,
                               nbytes, _stream(stream)), "qr_backward")
     return gf, ga, gc
+
+
+def qr_cosine_backward(fr: Frame, feat, feat_scale, ids, weights, counts, feature_map, target,
+                       mask=None, want_conic=True, stream=None):
+    """Cosine loss of `feature_map` against `target` over `mask` (default: the
+    counts) and the backward of the forward of `fr` under that loss, with the
+    loss's per-pixel pass fused into the backward's.
+
+    Returns (loss scalar tensor, dL/dF [P, C], grad_feat [n, C], grad_opacity [n],
+    grad_conic [n, 3] or None)."""
+    torch = _torch()
+    n = int(fr.frame.n)
+    C = feat.shape[1]
+    dev = feature_map.device
+    P = feature_map.shape[0]
+    nbytes = int(load().qr_cosine_backward_workspace_bytes(ctypes.byref(fr.frame), C))
+    if nbytes == 0:
+        raise QRError(QR_ERR_INVALID_ARG, "qr_cosine_backward_workspace_bytes")
+    ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
+    wsp = ctypes.c_void_p((ws.data_ptr() + 255) // 256 * 256)
+    out2 = torch.empty(2, dtype=torch.float32, device=dev)
+    gmap = torch.empty((P, C), dtype=torch.float32, device=dev)
+    gf = torch.empty((n, C), dtype=torch.float32, device=dev)
+    ga = torch.empty(n, dtype=torch.float32, device=dev)
+    gc = torch.empty((n, 3), dtype=torch.float32, device=dev) if want_conic else None
+    mask = counts if mask is None else mask
+    _check(load().qr_cosine_backward(ctypes.byref(fr.frame), _ptr(feat), _ptr(feat_scale),
+                                     _dtype_code(feat), C, _ptr(ids), _ptr(weights), _ptr(counts),
+                                     _ptr(feature_map.contiguous()), _ptr(target.contiguous()),
+                                     _ptr(mask), _ptr(out2), _ptr(gmap), _ptr(gf), _ptr(ga),
+                                     _ptr(gc), wsp, nbytes, _stream(stream)), "qr_cosine_backward")
+    return out2[0], gmap, gf, ga, gc
 
 
 def qr_cosine_loss(feature_map, target, counts, stream=None):

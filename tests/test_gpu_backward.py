@@ -156,13 +156,52 @@ def test_differentiation_config_sampled_pixels():
     mask = torch.zeros(cam.width * cam.height, dtype=torch.uint8, device="cuda")
     mask[torch.from_numpy(idx[use]).cuda()] = 1
     loss, gmap = q.qr_cosine_loss(res["out"], tgt, mask)
-    gf, ga, gc = q.qr_backward(res["frame"], torch.from_numpy(f).cuda(), None, res["ids"],
-                               res["weights"], res["counts"], gmap)
+    fdev = torch.from_numpy(f).cuda()
+    gf, ga, gc = q.qr_backward(res["frame"], fdev, None, res["ids"], res["weights"],
+                               res["counts"], gmap)
+    # the same loss and gradients from the fused call (512 FP32 channels: fused route)
+    loss2, gmap2, gf2, ga2, gc2 = q.qr_cosine_backward(res["frame"], fdev, None, res["ids"],
+                                                       res["weights"], res["counts"], res["out"],
+                                                       tgt, mask=mask)
     torch.cuda.synchronize()
     Lref, gref = oracle.cosine_loss(ref.out_q, ref2.out_dense, use)
     assert abs(loss.item() - Lref) <= 1e-4 * max(1.0, abs(Lref)), (loss.item(), Lref)
+    assert abs(loss2.item() - Lref) <= 1e-4 * max(1.0, abs(Lref)), (loss2.item(), Lref)
     rf, ra, rc = oracle.backward(pr, f, K, pix, gref, alpha_min=oracle.ALPHA_MIN_F32,
                                  alpha_max=oracle.ALPHA_MAX_F32)
-    _compare("feat", gf.cpu().numpy(), rf, 1e-4)
-    _compare("alpha", ga.cpu().numpy(), ra, 1e-3)
-    _compare("conic", gc.cpu().numpy(), rc, 1e-3)
+    for name, (a1, a2, r, tol) in {"feat": (gf, gf2, rf, 1e-4), "alpha": (ga, ga2, ra, 1e-3),
+                                   "conic": (gc, gc2, rc, 1e-3)}.items():
+        _compare(name, a1.cpu().numpy(), r, tol)
+        _compare(name + " fused", a2.cpu().numpy(), r, tol)
+
+
+@pytest.mark.parametrize("kind,C", [("f32", 64),     # 16 float4 per row: the unfused route
+                                    ("f32", 128), ("bf16", 512), ("fp8", 512)])
+def test_cosine_backward_matches_separate_calls(kind, C):
+    """qr_cosine_backward = qr_cosine_loss then qr_backward, up to summation order."""
+    import torch
+    from paper_2512_20927_gb300 import qrender as q
+    g, f = H.small_room(n=20000, channels=C)
+    cam = scenes.room_camera(150, 110)
+    fdev = torch.from_numpy(f).cuda()
+    table = {"f32": fdev, "bf16": None, "fp8": None}[kind]
+    if kind == "bf16":
+        table = q.qr_quantize_bf16(fdev)
+    elif kind == "fp8":
+        table = q.qr_quantize_fp8(fdev)
+    feat_t, scale_t = table if isinstance(table, tuple) else (table, None)
+    res = q.render_frame(q.gaussians_to_device(g), table, cam, K=8)
+    rng = np.random.default_rng(3)
+    tgt = torch.from_numpy(rng.normal(size=(cam.width * cam.height, C)).astype(np.float32)).cuda()
+    loss, gmap = q.qr_cosine_loss(res["out"], tgt, res["counts"])
+    gf, ga, gc = q.qr_backward(res["frame"], feat_t, scale_t, res["ids"], res["weights"],
+                               res["counts"], gmap)
+    loss2, gmap2, gf2, ga2, gc2 = q.qr_cosine_backward(res["frame"], feat_t, scale_t, res["ids"],
+                                                       res["weights"], res["counts"], res["out"], tgt)
+    torch.cuda.synchronize()
+    assert abs(loss2.item() - loss.item()) <= 1e-6 * max(1.0, abs(loss.item()))
+    _compare("grad map", gmap2.cpu().numpy(), gmap.cpu().numpy().astype(np.float64), 1e-5)
+    _compare("feat", gf2.cpu().numpy(), gf.cpu().numpy().astype(np.float64), 1e-5)
+    _compare("alpha", ga2.cpu().numpy(), ga.cpu().numpy().astype(np.float64), 1e-4)
+    _compare("conic", gc2.cpu().numpy(), gc.cpu().numpy().astype(np.float64), 1e-4)
+    assert (res["counts"] > 0).any()

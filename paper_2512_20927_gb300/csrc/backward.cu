@@ -14,18 +14,21 @@
 //   1. bwd_pixel: one warp per pixel recomputes its quantile Gaussians' alpha'
 //      with the forward's exact evaluation, forms s_j with warp-wide dot
 //      products (16-byte feature loads, BF16/FP8 decoded in registers) and
-//      writes per-entry (dalpha, dA00, dA01, dA11);
+//      writes per-entry (dalpha, dA00, dA01, dA11); with the cosine loss
+//      fused, it first forms the pixel's dL/dF itself;
 //   2. bwd_tile_partials: one CTA per screen tile sorts the tile's (Gaussian,
 //      entry) keys once (in registers), stages each entry's pixel and weight
 //      and, 64 channels at a time, the tile's rows of g in shared memory, and
-//      lets each warp reduce one distinct Gaussian's w * g rows in entry order
-//      into a partial row, stored at a fixed slot of that tile's intersection
-//      range;
-//   3. a stable radix sort of the slot keys by Gaussian id;
-//   4. bwd_reduce_runs + bwd_reduce: a two-level sum of each Gaussian's
-//      partials in tile order -- fixed 32-slot chunks first, then the chunk
-//      sums per Gaussian -- so a Gaussian selected in many tiles is not one
-//      long serial chain; unselected Gaussians keep zero rows.
+//      sums each distinct Gaussian's w * g rows in entry order into a partial
+//      row, stored at a fixed slot of that tile's intersection range (slots
+//      in ascending Gaussian id);
+//   3. bwd_selected + bwd_rows: each Gaussian that survived the projection
+//      owns a slot map (one entry per tile of its footprint rectangle, at its
+//      intersection offset) that step 2 fills for the tiles that selected it;
+//      the first tile to select a Gaussian lists it, and one CTA per listed
+//      Gaussian (bwd_rows; 1024 threads for large footprints) adds its
+//      partials in tile order (warps over channel blocks and fixed row
+//      subsets).  Rows of unselected Gaussians stay as cleared.
 #include <cstring>
 
 #include <cuda_bf16.h>
@@ -38,6 +41,7 @@ namespace qr {
 namespace {
 
 constexpr int T = 256;
+constexpr int kRowsSmall = 256;   // selected Gaussians' maps up to this many tiles: 256-thread row CTAs
 
 template <int DT> struct VecB;
 template <> struct VecB<QR_F32> { static constexpr int C = 4; static constexpr int E = 4; };
@@ -310,8 +314,11 @@ bwd_tile_partials(const uint2 *__restrict__ ranges, int W, int H, int tile_w, in
                   const uint8_t *__restrict__ cnt, const float4 *__restrict__ E4,
                   const float *__restrict__ grad_out, int C, int K, int CH,
                   float *__restrict__ partial, float4 *__restrict__ partial_s,
-                  uint32_t *__restrict__ pkey, const __grid_constant__ CUtensorMap gmap, int use_tma,
-                  int nbuf, int stage_e, uint32_t *__restrict__ counters) {
+                  const uint2 *__restrict__ rect, const uint32_t *__restrict__ tcount,
+                  const uint32_t *__restrict__ goff, uint32_t *__restrict__ slotmap, int64_t X,
+                  uint32_t *__restrict__ gflag, uint32_t *__restrict__ lists, int64_t N,
+                  const __grid_constant__ CUtensorMap gmap, int use_tma, int nbuf, int stage_e,
+                  uint32_t *__restrict__ counters) {
     constexpr bool K32 = sizeof(KT) == 4;
     constexpr int SHIFT = K32 ? 11 : 32;
     extern __shared__ __align__(16) unsigned char s_dyn[];
@@ -346,7 +353,6 @@ bwd_tile_partials(const uint2 *__restrict__ ranges, int W, int H, int tile_w, in
     block_inclusive_scan(uint32_t(m), s_w, tot);
     const int n = int(tot);
     if (n == 0) {
-        for (int u = threadIdx.x; u < int(r.y - r.x); u += T) pkey[r.x + u] = 0xFFFFFFFFu;
         return;
     }
     const int nchunks = (C + CH - 1) / CH;
@@ -404,8 +410,25 @@ bwd_tile_partials(const uint2 *__restrict__ ranges, int W, int H, int tile_w, in
     if (threadIdx.x == 0) s_nseg = carry;
     __syncthreads();
     const int nseg = int(s_nseg);
-    for (int u = threadIdx.x; u < int(r.y - r.x); u += T)
-        pkey[r.x + u] = u < nseg ? uint32_t(s_key[seg[u]] >> SHIFT) : 0xFFFFFFFFu;
+    // segment u's partial row goes to slot r.x + u (u < nseg <= r.y - r.x); the
+    // slot is recorded in the Gaussian's slot map at this tile's position in
+    // its footprint rectangle (row-major, so the map lists its slots in tile order)
+    for (int u = threadIdx.x; u < nseg; u += T) {
+        const uint32_t gid = uint32_t(s_key[seg[u]] >> SHIFT);
+        const uint2 rc = rect[gid];
+        const int tx0 = int(rc.x & 0xFFFFu), ty0 = int(rc.x >> 16);
+        const int tw = int(rc.y & 0xFFFFu) - tx0 + 1;
+        const int64_t i = int64_t(ty - ty0) * tw + (tx - tx0);
+        const int64_t at = int64_t(goff[gid]) + i;
+        if (tx >= tx0 && ty >= ty0 && i < int64_t(tcount[gid]) && at < X) slotmap[at] = r.x + uint32_t(u);
+        // the first tile to select the Gaussian lists it (the order of the
+        // lists does not matter: each entry is summed on its own)
+        if (atomicExch(&gflag[gid], 1u) == 0u) {
+            const bool big = tcount[gid] > uint32_t(kRowsSmall);
+            uint32_t *list = lists + (big ? N : 0);
+            list[atomicAdd(lists + 2 * N + (big ? 1 : 0), 1u)] = gid;
+        }
+    }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // per-entry (dalpha, dA) sums: lanes take entries b + lane, b + lane + 32, ...
     for (int u = warp; u < nseg; u += T / 32) {
@@ -552,140 +575,118 @@ bwd_tile_partials(const uint2 *__restrict__ ranges, int W, int H, int tile_w, in
     }
 }
 
-__global__ void __launch_bounds__(T)
-iota_kernel(uint32_t *v, const uint32_t *__restrict__ d_n) {
-    const uint32_t n = *d_n;
-    for (uint32_t i = blockIdx.x * T + threadIdx.x; i < n; i += gridDim.x * T) v[i] = i;
+// ------------------------------------------------------------------ 3. per Gaussian
+// Each Gaussian's first intersection index (the exclusive prefix of the tile
+// counts over Gaussians), from the projection's tile counts and the per-256
+// block bases the binning left in the frame -- the arithmetic of the binning's
+// own offsets, for every Gaussian.
+__global__ void __launch_bounds__(kProjectThreads)
+isect_offsets(const uint32_t *__restrict__ tcount, const uint32_t *__restrict__ tsum_base,
+              int64_t n, uint32_t *__restrict__ goff, uint32_t *__restrict__ d_nlist) {
+    __shared__ uint32_t s_w[32];
+    if (blockIdx.x == 0 && threadIdx.x < 2) d_nlist[threadIdx.x] = 0;   // the selected lists start empty
+    const int64_t g = int64_t(blockIdx.x) * kProjectThreads + threadIdx.x;
+    const uint32_t c = g < n ? tcount[g] : 0u;
+    uint32_t tot;
+    const uint32_t cinc = block_inclusive_scan(c, s_w, tot);
+    if (g < n) goff[g] = tsum_base[blockIdx.x] + cinc - c;
 }
 
-// ------------------------------------------------------------------ 3-4. per Gaussian
-__global__ void __launch_bounds__(T)
-gauss_ranges(const uint32_t *__restrict__ key, const uint32_t *__restrict__ d_n, int64_t N,
-             uint2 *__restrict__ gr) {
-    const uint32_t n = *d_n;
-    for (uint32_t i = blockIdx.x * T + threadIdx.x; i < n; i += gridDim.x * T) {
-        const uint32_t k = key[i];
-        if (int64_t(k) >= N) continue;
-        if (i == 0 || key[i - 1] != k) gr[k].x = i;
-        if (i + 1 == n || key[i + 1] != k) gr[k].y = i + 1;
-    }
-}
-
-// Level 1 of the per-Gaussian reduction: the gid-sorted slot array is cut
-// into fixed chunks of 32 positions; one warp per chunk sums each run of equal
-// gids inside the chunk (four rows in flight, lanes over channels) into the
-// run's first row.  A run is a whole Gaussian or the part of a long one that
-// falls in the chunk.
-constexpr int kRunChunk = 32;
-
-__global__ void __launch_bounds__(T)
-bwd_reduce_runs(const uint32_t *__restrict__ skey, const uint32_t *__restrict__ sval,
-                const uint32_t *__restrict__ d_n, int64_t N, int C, float *__restrict__ partial,
-                float4 *__restrict__ partial_s) {
-    const int lane = threadIdx.x & 31;
-    const uint32_t n = *d_n;
-    const int64_t warp0 = (int64_t(blockIdx.x) * T + threadIdx.x) >> 5;
-    const int64_t nw = (int64_t(gridDim.x) * T) >> 5;
-    const int64_t nchunk = (int64_t(n) + kRunChunk - 1) / kRunChunk;
-    for (int64_t ch = warp0; ch < nchunk; ch += nw) {
-        const uint32_t i0 = uint32_t(ch * kRunChunk);
-        const uint32_t i1 = min(n, i0 + uint32_t(kRunChunk));
-        // lane k holds position i0 + k: its key and slot
-        const uint32_t my_key = i0 + lane < i1 ? skey[i0 + lane] : 0xFFFFFFFFu;
-        const uint32_t my_slot = i0 + lane < i1 ? sval[i0 + lane] : 0u;
-        const int len = int(i1 - i0);
-        int a0 = 0;
-        while (a0 < len) {
-            const uint32_t k = __shfl_sync(0xffffffffu, my_key, a0);
-            if (int64_t(k) >= N) break;   // unused slots sort last
-            // run [a0, a1) of key k
-            const unsigned same = __ballot_sync(0xffffffffu, my_key == k && lane >= a0 && lane < len);
-            const int a1 = 32 - __clz(same);   // one past the last lane of the run (runs are contiguous)
-            const uint32_t head = __shfl_sync(0xffffffffu, my_slot, a0);
-            if (a1 - a0 > 1) {
-                // every lane runs the channel loop (the shuffles need the whole
-                // warp); lanes past the row's end only skip the loads and stores
-                for (int cb = 0; cb < C; cb += 128) {
-                    const int c = cb + lane * 4;
-                    const bool act = c < C;
-                    float4 acc = act ? *reinterpret_cast<const float4 *>(partial + int64_t(head) * C + c)
-                                     : make_float4(0.f, 0.f, 0.f, 0.f);
-                    int q = a0 + 1;
-                    for (; q + 4 <= a1; q += 4) {
-                        float4 v[4];
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            const uint32_t sl = __shfl_sync(0xffffffffu, my_slot, q + u);
-                            v[u] = act ? *reinterpret_cast<const float4 *>(partial + int64_t(sl) * C + c)
-                                       : make_float4(0.f, 0.f, 0.f, 0.f);
-                        }
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            acc.x += v[u].x; acc.y += v[u].y; acc.z += v[u].z; acc.w += v[u].w;
-                        }
-                    }
-                    for (; q < a1; ++q) {
-                        const uint32_t sl = __shfl_sync(0xffffffffu, my_slot, q);
-                        if (act) {
-                            const float4 v = *reinterpret_cast<const float4 *>(partial + int64_t(sl) * C + c);
-                            acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
+// A selected Gaussian's slot map -- one entry per tile of its footprint
+// rectangle (row-major, so in tile order), from its first intersection index
+// -- holds the slot of its partial row in every tile that selected it and
+// 0xFFFFFFFF elsewhere; the tile kernel lists the selected Gaussians, those
+// with more than kRowsSmall tiles apart.
+// One CTA of NT threads per listed Gaussian: it walks the map NT tiles at a
+// time, compacts the found slots in tile order into shared memory, and its
+// NW = NT / 32 warps add the rows: warp w takes the 128-channel block w % nb
+// (nb = C / 128 rounded up) and, when nb < NW, the rows i = w / nb (mod R),
+// R = NW / nb, in order, eight rows in flight; the R partial sums are added in
+// subset order at the end.  Warp 0 adds the (dalpha, dA) terms of the found
+// slots in tile order.  Channel blocks beyond NW are taken in further rounds.
+template <int NT>
+__global__ void __launch_bounds__(NT)
+bwd_rows(const uint32_t *__restrict__ list, const uint32_t *__restrict__ d_nlist,
+         const uint32_t *__restrict__ goff, const uint32_t *__restrict__ tcount,
+         const uint32_t *__restrict__ slotmap, int64_t X, const float *__restrict__ partial,
+         const float4 *__restrict__ partial_s, int C, float *__restrict__ grad_feat,
+         float *__restrict__ grad_alpha, float *__restrict__ grad_conic) {
+    constexpr unsigned FULL = 0xffffffffu;
+    constexpr int NW = NT / 32;
+    __shared__ uint32_t s_slot[NT];
+    __shared__ uint32_t s_w[32];
+    __shared__ float4 s_acc[NW][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nb = (C + 127) / 128;
+    const int R = nb < NW ? NW / nb : 1;          // row subsets per channel block
+    const uint32_t nlist = *d_nlist;
+    for (uint32_t wi = blockIdx.x; wi < nlist; wi += gridDim.x) {
+        const uint32_t g = list[wi];
+        const int64_t m0 = goff[g];
+        int64_t nt = tcount[g];
+        if (m0 + nt > X) nt = X > m0 ? X - m0 : 0;
+        float4 sacc = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int cg = 0; cg < nb; cg += NW) {            // rounds of channel blocks
+            const int blk = cg + (R > 1 ? warp % nb : warp);
+            const int sub = R > 1 ? warp / nb : 0;
+            const bool on = blk < nb && sub < R;
+            const int c0 = blk * 128 + lane * 4;
+            const bool act = on && c0 < C;
+            float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int64_t base = 0; base < nt; base += NT) {
+                const uint32_t slot = base + threadIdx.x < nt ? slotmap[m0 + base + threadIdx.x] : 0xFFFFFFFFu;
+                const uint32_t f = slot != 0xFFFFFFFFu ? 1u : 0u;
+                uint32_t nf;
+                const uint32_t pos = block_inclusive_scan(f, s_w, nf);
+                if (f) s_slot[pos - 1] = slot;
+                __syncthreads();
+                if (cg == 0 && warp == 0) {
+                    for (uint32_t i0 = 0; i0 < nf; i0 += 32) {
+                        const float4 mine = i0 + lane < nf ? partial_s[s_slot[i0 + lane]] : make_float4(0.f, 0.f, 0.f, 0.f);
+                        const int cnt = int(min(32u, nf - i0));
+                        for (int q = 0; q < cnt; ++q) {
+                            sacc.x += __shfl_sync(FULL, mine.x, q);
+                            sacc.y += __shfl_sync(FULL, mine.y, q);
+                            sacc.z += __shfl_sync(FULL, mine.z, q);
+                            sacc.w += __shfl_sync(FULL, mine.w, q);
                         }
                     }
-                    if (act) *reinterpret_cast<float4 *>(partial + int64_t(head) * C + c) = acc;
                 }
-                // the (dalpha, dA) terms: lane k of the run adds its slot's, fixed tree
-                float4 sv = (lane >= a0 && lane < a1) ? partial_s[my_slot] : make_float4(0.f, 0.f, 0.f, 0.f);
+                if (act) {
+                    // this subset's rows: sub, sub + R, sub + 2R, ... of the found list
+                    for (uint32_t i = uint32_t(sub); i < nf; i += 8u * uint32_t(R)) {
+                        float4 v[8];
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    sv.x += __shfl_xor_sync(0xffffffffu, sv.x, o);
-                    sv.y += __shfl_xor_sync(0xffffffffu, sv.y, o);
-                    sv.z += __shfl_xor_sync(0xffffffffu, sv.z, o);
-                    sv.w += __shfl_xor_sync(0xffffffffu, sv.w, o);
+                        for (int x = 0; x < 8; ++x) {
+                            const uint32_t ii = i + uint32_t(x * R);
+                            if (ii < nf) v[x] = *reinterpret_cast<const float4 *>(partial + int64_t(s_slot[ii]) * C + c0);
+                        }
+#pragma unroll
+                        for (int x = 0; x < 8; ++x)
+                            if (i + uint32_t(x * R) < nf) { acc.x += v[x].x; acc.y += v[x].y; acc.z += v[x].z; acc.w += v[x].w; }
+                    }
                 }
-                if (lane == 0) partial_s[head] = sv;
+                __syncthreads();   // s_slot is rewritten by the next step
             }
-            a0 = a1;
+            // the R subsets of each channel block, added in subset order
+            s_acc[warp][lane] = acc;
+            __syncthreads();
+            if (on && sub == 0 && c0 < C) {
+                float4 t = acc;
+                for (int q = 1; q < R; ++q) {
+                    const float4 o = s_acc[warp + q * nb][lane];
+                    t.x += o.x; t.y += o.y; t.z += o.z; t.w += o.w;
+                }
+                *reinterpret_cast<float4 *>(grad_feat + int64_t(g) * C + c0) = t;
+            }
+            __syncthreads();
         }
-    }
-}
-
-// Level 2: one warp per Gaussian with slots adds the heads of its runs (its
-// first position and every chunk start inside its range) in order and writes
-// its gradient row; Gaussians without slots keep the zeros the output was
-// cleared to.
-__global__ void __launch_bounds__(T)
-bwd_reduce(const uint2 *__restrict__ gr, const uint32_t *__restrict__ sval,
-           const float *__restrict__ partial, const float4 *__restrict__ partial_s, int64_t N,
-           int C, float *__restrict__ grad_feat, float *__restrict__ grad_alpha,
-           float *__restrict__ grad_conic) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warp0 = (int64_t(blockIdx.x) * T + threadIdx.x) >> 5;
-    const int64_t nw = (int64_t(gridDim.x) * T) >> 5;
-    for (int64_t u = warp0; u < N; u += nw) {
-        const uint2 r = gr[u];
-        if (r.y <= r.x) continue;
-        float *out = grad_feat + u * int64_t(C);
-        // run heads: r.x, then every multiple of the chunk size inside (r.x, r.y)
-        const uint32_t first_chunk = r.x / kRunChunk + 1;
-        for (int c = lane * 4; c < C; c += 128) {
-            float4 acc = *reinterpret_cast<const float4 *>(partial + int64_t(sval[r.x]) * C + c);
-            for (uint32_t h = first_chunk * kRunChunk; h < r.y; h += kRunChunk) {
-                const float4 v = *reinterpret_cast<const float4 *>(partial + int64_t(sval[h]) * C + c);
-                acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
-            }
-            *reinterpret_cast<float4 *>(out + c) = acc;
-        }
-        if (lane == 0) {
-            float4 sacc = partial_s[sval[r.x]];
-            for (uint32_t h = first_chunk * kRunChunk; h < r.y; h += kRunChunk) {
-                const float4 v = partial_s[sval[h]];
-                sacc.x += v.x; sacc.y += v.y; sacc.z += v.z; sacc.w += v.w;
-            }
-            if (grad_alpha) grad_alpha[u] = sacc.x;
+        if (threadIdx.x == 0) {
+            if (grad_alpha) grad_alpha[g] = sacc.x;
             if (grad_conic) {
-                grad_conic[3 * u] = sacc.y;
-                grad_conic[3 * u + 1] = sacc.z;
-                grad_conic[3 * u + 2] = sacc.w;
+                grad_conic[3 * int64_t(g)] = sacc.y;
+                grad_conic[3 * int64_t(g) + 1] = sacc.z;
+                grad_conic[3 * int64_t(g) + 2] = sacc.w;
             }
         }
     }
@@ -701,24 +702,20 @@ int sms_now() {
 inline size_t up256(size_t x) { return (x + 255) / 256 * 256; }
 
 struct BwdLayout {
-    size_t e, partial, partial_s, key0, key1, val0, val1, hist, digitsum, granges, total;
+    size_t e, partial, partial_s, goff, slotmap, gflag, lists, total;
 };
 
 BwdLayout bwd_layout(const qr_frame &f, int C) {
     const size_t P = size_t(num_pixels(f)), K = size_t(f.params.K), X = size_t(f.max_isect);
-    const size_t N = size_t(f.n);
     BwdLayout L;
     size_t o = 0;
     L.e = o; o = up256(o + P * K * 16);
     L.partial = o; o = up256(o + X * size_t(C) * 4);
     L.partial_s = o; o = up256(o + X * 16);
-    L.key0 = o; o = up256(o + X * 4);
-    L.key1 = o; o = up256(o + X * 4);
-    L.val0 = o; o = up256(o + X * 4);
-    L.val1 = o; o = up256(o + X * 4);
-    L.hist = o; o = up256(o + size_t(1 << kRadixBitsMax) * kSortMaxBlocks * 4);
-    L.digitsum = o; o = up256(o + size_t(1 << kRadixBitsMax) * 4);
-    L.granges = o; o = up256(o + N * 8 + 8);
+    L.goff = o; o = up256(o + size_t(f.n) * 4);   // first intersection index per Gaussian
+    L.slotmap = o; o = up256(o + X * 4);          // per intersection: partial slot or none
+    L.gflag = o; o = up256(o + size_t(f.n) * 4);       // Gaussian listed yet
+    L.lists = o; o = up256(o + size_t(f.n) * 8 + 8);   // selected: small list, big list, counts
     L.total = o;
     return L;
 }
@@ -779,21 +776,18 @@ cudaError_t backward_impl(const qr_frame &f, const void *feat, const float *scal
     float4 *E = reinterpret_cast<float4 *>(b + L.e);
     float *partial = reinterpret_cast<float *>(b + L.partial);
     float4 *partial_s = reinterpret_cast<float4 *>(b + L.partial_s);
-    uint32_t *key0 = reinterpret_cast<uint32_t *>(b + L.key0);
-    uint32_t *key1 = reinterpret_cast<uint32_t *>(b + L.key1);
-    uint32_t *val0 = reinterpret_cast<uint32_t *>(b + L.val0);
-    uint32_t *val1 = reinterpret_cast<uint32_t *>(b + L.val1);
-    uint32_t *hist = reinterpret_cast<uint32_t *>(b + L.hist);
-    uint32_t *digitsum = reinterpret_cast<uint32_t *>(b + L.digitsum);
-    uint2 *gr = reinterpret_cast<uint2 *>(b + L.granges);
+    uint32_t *goff = reinterpret_cast<uint32_t *>(b + L.goff);
+    uint32_t *slotmap = reinterpret_cast<uint32_t *>(b + L.slotmap);
+    uint32_t *gflag = reinterpret_cast<uint32_t *>(b + L.gflag);
+    uint32_t *lists = reinterpret_cast<uint32_t *>(b + L.lists);
     uint32_t *counters = slot<uint32_t>(f, S_COUNTERS);
     const int tiles = num_tiles(f);
     const int K = f.params.K;
-    cudaError_t e = cudaMemsetAsync(gr, 0, size_t(f.n) * 8 + 8, s);
+    cudaError_t e = cudaMemsetAsync(slotmap, 0xFF, size_t(f.max_isect) * 4, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(gflag, 0, size_t(f.n) * 4, s);
     if (e != cudaSuccess) return e;
-    if (grad_alpha) e = cudaMemsetAsync(grad_alpha, 0, size_t(f.n) * 4, s);
-    if (e == cudaSuccess && grad_conic) e = cudaMemsetAsync(grad_conic, 0, size_t(f.n) * 12, s);
-    if (e != cudaSuccess) return e;
+    isect_offsets<<<unsigned((f.n + kProjectThreads - 1) / kProjectThreads), kProjectThreads, 0, s>>>(
+        slot<uint32_t>(f, S_TCOUNT), slot<uint32_t>(f, S_BSUM), f.n, goff, lists + 2 * f.n);
     float *g = const_cast<float *>(grad_out);   // written only by the fused loss pass
     switch (dt) {
         case QR_F32: launch_bwd_pixel<QR_F32>(f, feat, scale, C, ids, w, cnt, g, E, loss, s); break;
@@ -844,8 +838,11 @@ cudaError_t backward_impl(const qr_frame &f, const void *feat, const float *scal
         if (ee != cudaSuccess) return ee;
         kern<<<unsigned(tiles), T, smem, s>>>(slot<uint2>(f, S_RANGES), f.camera.width,
                                                f.camera.height, f.params.tile_w, f.tiles_x, ids, w,
-                                               cnt, E, grad_out, C, K, CH, partial, partial_s, key0,
-                                               gmap, use_tma, nbuf, stage_e, counters);
+                                               cnt, E, grad_out, C, K, CH, partial, partial_s,
+                                               slot<uint2>(f, S_RECT), slot<uint32_t>(f, S_TCOUNT),
+                                               goff, slotmap, f.max_isect, gflag, lists, f.n,
+                                               gmap, use_tma, nbuf,
+                                               stage_e, counters);
         return cudaSuccess;
     };
     if (k32) {
@@ -858,28 +855,20 @@ cudaError_t backward_impl(const qr_frame &f, const void *feat, const float *scal
                    : tp(bwd_tile_partials<0, unsigned long long>);
     }
     if (e != cudaSuccess) return e;
-    // stable sort of the slots by Gaussian id (ids < n; unused slots carry 0xFFFFFFFF)
-    const uint32_t *d_x = counters + CNT_SORT_N;
-    iota_kernel<<<sms_now() * 4, T, 0, s>>>(val0, d_x);
-    int in_b = 0;
-    e = radix_sort_pairs(key0, val0, key1, val1, d_x, f.max_isect, 0,
-                         tile_bits_for(int(f.n + 1 > 2 ? f.n + 1 : 2)), hist, digitsum,
-                         f.sort_blocks, &in_b, s);
-    if (e != cudaSuccess) return e;
-    const uint32_t *skey = in_b ? key1 : key0;
-    const uint32_t *sval = in_b ? val1 : val0;
-    gauss_ranges<<<sms_now() * 4, T, 0, s>>>(skey, d_x, f.n, gr);
-    // gradient rows of Gaussians that no pixel selected are zero
+    // rows of Gaussians that no tile selected are zero; the others get their
+    // partials added in tile order
     e = cudaMemsetAsync(grad_feat, 0, size_t(f.n) * size_t(C) * 4, s);
+    if (e == cudaSuccess && grad_alpha) e = cudaMemsetAsync(grad_alpha, 0, size_t(f.n) * 4, s);
+    if (e == cudaSuccess && grad_conic) e = cudaMemsetAsync(grad_conic, 0, size_t(f.n) * 12, s);
     if (e != cudaSuccess) return e;
-    bwd_reduce_runs<<<sms_now() * 8, T, 0, s>>>(skey, sval, d_x, f.n, C, partial, partial_s);
-    int64_t blocks = (f.n * 32 + T - 1) / T;
-    const int64_t cap = int64_t(sms_now()) * 16;
-    if (blocks > cap) blocks = cap;
-    if (blocks < 1) blocks = 1;
-    bwd_reduce<<<unsigned(blocks), T, 0, s>>>(gr, sval, partial, partial_s, f.n, C, grad_feat,
-                                              grad_alpha, grad_conic);
-    count_launch(6);
+    const uint32_t *tcount = slot<uint32_t>(f, S_TCOUNT);
+    bwd_rows<256><<<unsigned(sms_now() * 8), 256, 0, s>>>(
+        lists, lists + 2 * f.n, goff, tcount, slotmap, f.max_isect, partial, partial_s, C,
+        grad_feat, grad_alpha, grad_conic);
+    bwd_rows<1024><<<unsigned(sms_now() * 2), 1024, 0, s>>>(
+        lists + f.n, lists + 2 * f.n + 1, goff, tcount, slotmap, f.max_isect, partial, partial_s,
+        C, grad_feat, grad_alpha, grad_conic);
+    count_launch(5);
     return cudaGetLastError();
 }
 

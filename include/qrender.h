@@ -94,7 +94,7 @@ typedef struct {
     qr_camera camera;
     qr_params params;
     int32_t tiles_x, tiles_y;  /* screen tiles                            */
-    int32_t sort_blocks;       /* private                                 */
+    int32_t sort_blocks;       /* reserved (zero)                         */
     int32_t isect_buf;         /* private                                 */
     void *ws;                  /* device workspace                        */
     size_t ws_bytes;

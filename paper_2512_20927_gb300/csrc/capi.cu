@@ -145,7 +145,7 @@ qr_status qr_frame_init(qr_frame *frame, int64_t n, const qr_camera *camera,
     f.params = *params;
     f.tiles_x = (camera->width + params->tile_w - 1) / params->tile_w;
     f.tiles_y = (camera->height + params->tile_h - 1) / params->tile_h;
-    f.sort_blocks = sort_blocks_for(max_isect);
+    f.sort_blocks = 0;   // reserved
     f.isect_buf = 0;
     f.ws = ws;
     f.ws_bytes = ws_bytes;

@@ -33,11 +33,6 @@ constexpr int kDiffCopies = 8;
 constexpr int kEmitChunk = 1024;
 static_assert(S_END <= QR_FRAME_SLOTS, "too many workspace slots");
 
-constexpr int kSortThreads = 256;
-constexpr int kSortItems = 8;                       // items per thread per tile
-constexpr int kSortTile = kSortThreads * kSortItems; // 2048
-constexpr int kSortMaxBlocks = 304;                 // 2 per SM on a 152-SM GB300
-constexpr int kRadixBitsMax = 8;
 constexpr int kKMax = 32;
 
 // Launch counter (all TUs add to it).
@@ -133,17 +128,7 @@ bool relevance_supported(int Q, int C);
 cudaError_t launch_relevance(const float *map, const uint16_t *q, int Q, int64_t P, int C,
                              float *out, int *status, cudaStream_t s);
 
-// Generic pieces of the sort, reused by later stages.
-// Stable LSD radix sort of (key, val) pairs; count read from the device.
-// Sorts bits [bit_lo, bit_hi) of the keys; returns through *out_keys/*out_vals
-// which of the two buffers holds the result (0 = buffers "a", 1 = "b").
-cudaError_t radix_sort_pairs(uint32_t *keys_a, uint32_t *vals_a, uint32_t *keys_b,
-                             uint32_t *vals_b, const uint32_t *d_count, int64_t capacity,
-                             int bit_lo, int bit_hi, uint32_t *hist, uint32_t *digitsum,
-                             int blocks, int *result_in_b, cudaStream_t s);
 
-int sort_blocks_for(int64_t capacity);
-int tile_bits_for(int tiles);
 
 // ---------------------------------------------------------------- block scans
 // Inclusive scan of one value per thread across the CTA (blockDim.x a

@@ -387,12 +387,6 @@ tile_sort(const uint2 *__restrict__ ranges, unsigned long long *__restrict__ key
 
 }  // namespace
 
-int tile_bits_for(int tiles) {
-    int b = 1;
-    while ((1 << b) < tiles) ++b;
-    return b;
-}
-
 cudaError_t launch_sort(const qr_frame &f, cudaStream_t s) {
     uint32_t *counters = slot<uint32_t>(f, S_COUNTERS);
     const int tiles = num_tiles(f);

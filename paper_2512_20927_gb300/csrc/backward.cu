@@ -277,6 +277,14 @@ __device__ __forceinline__ void fma2v(float2 &acc, float w, float2 g) {
         : "+f"(acc.x), "+f"(acc.y) : "f"(w), "f"(g.x), "f"(g.y));
 }
 
+// acc += w * g for four channels: two packed FP32x2 FMAs
+__device__ __forceinline__ void fma4v(float4 &acc, float w, float4 g) {
+    float2 lo = make_float2(acc.x, acc.y), hi = make_float2(acc.z, acc.w);
+    fma2v(lo, w, make_float2(g.x, g.y));
+    fma2v(hi, w, make_float2(g.z, g.w));
+    acc = make_float4(lo.x, lo.y, hi.x, hi.y);
+}
+
 // ------------------------------------------------------------------ 2. per tile
 __device__ __forceinline__ void bitonic64(unsigned long long *s, int npow2) {
     for (int k = 2; k <= npow2; k <<= 1)
@@ -326,8 +334,9 @@ bwd_tile_partials(const uint2 *__restrict__ ranges, int W, int H, int tile_w, in
     __shared__ uint32_t s_nseg;
     __shared__ __align__(8) uint64_t s_bar[2];
     __shared__ int s_ok;
-    __shared__ float2 s_piece[(T / 32) * 2 * 32];   // per warp: continued piece, begun piece
-    __shared__ int s_first[T / 32], s_last[T / 32];
+    // per chunk parity, per warp: the continued and the begun piece (64 channels each)
+    __shared__ __align__(16) float4 s_piece[2][(T / 32) * 2 * 16];
+    __shared__ int s_first[2][T / 32], s_last[2][T / 32];
     int npow2 = 1;
     while (npow2 < T * K) npow2 <<= 1;
     // 1024-byte aligned base (the launch adds 1 KB of slack for it), formed as an
@@ -455,8 +464,8 @@ bwd_tile_partials(const uint2 *__restrict__ ranges, int W, int H, int tile_w, in
         }
         if (lane == 0) partial_s[int64_t(r.x) + u] = sacc;
     }
-    // the w * g sums, CH channels at a time (lane owns channels 2 lane, 2 lane + 1 of 64)
-    const int cpl = CH / 32;   // channels per lane: 1 or 2
+    // the w * g sums, CH (32 or 64) channels at a time
+    const int grp = lane >> 3, gl = lane & 7;   // 8-lane group, lane in the group
     constexpr int NWARP = T / 32;
     const int r0 = int(int64_t(n) * warp / NWARP), r1 = int(int64_t(n) * (warp + 1) / NWARP);
     int u_lo = 0;   // the segment holding entry r0: the last u with seg[u] <= r0
@@ -489,81 +498,101 @@ bwd_tile_partials(const uint2 *__restrict__ ranges, int W, int H, int tile_w, in
         }
         // balanced walk: warp w sums entries [w n / 8, (w + 1) n / 8); a segment
         // that crosses a warp boundary is split into pieces, the piece holding
-        // its start is completed below with the next warps' pieces, in order
-        auto walk = [&](int b, int e) {
-            float2 acc = make_float2(0.f, 0.f);
-            int i = b;
-            if (cpl == 2) {
-                for (; i + 8 <= e; i += 8) {
-                    uint2 en[8];
-                    float2 gv[8];
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) en[q] = s_ent[i + q];
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) gv[q] = reinterpret_cast<const float2 *>(gbuf + en[q].x * CH)[lane];
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) fma2v(acc, __uint_as_float(en[q].y), gv[q]);
+        // its start is completed below with the next warps' pieces, in order.
+        // The warp's four 8-lane groups take every fourth entry of a piece
+        // (group q: entries b + q, b + q + 4, ...); lane j of a group holds
+        // channels 4j .. 4j + 3 (a) and, for 64-channel chunks, 32 + 4j ..
+        // 32 + 4j + 3 (b) of the chunk.  The group sums are added as
+        // (q0 + q1) + (q2 + q3) at the end of the piece.
+        auto walk = [&](int b, int e, float4 &a, float4 &bb) {
+            a = make_float4(0.f, 0.f, 0.f, 0.f);
+            bb = make_float4(0.f, 0.f, 0.f, 0.f);
+            int i = b + grp;
+            for (; i + 4 < e; i += 8) {
+                const uint2 e0 = s_ent[i], e1 = s_ent[i + 4];
+                const float4 *g0 = reinterpret_cast<const float4 *>(gbuf + e0.x * CH);
+                const float4 *g1 = reinterpret_cast<const float4 *>(gbuf + e1.x * CH);
+                const float4 x0 = g0[gl], x1 = g1[gl];
+                const float w0 = __uint_as_float(e0.y), w1 = __uint_as_float(e1.y);
+                fma4v(a, w0, x0);
+                fma4v(a, w1, x1);
+                if (CH == 64) {
+                    const float4 y0 = g0[8 + gl], y1 = g1[8 + gl];
+                    fma4v(bb, w0, y0);
+                    fma4v(bb, w1, y1);
                 }
             }
-            for (; i < e; ++i) {
-                const uint2 en = s_ent[i];
-                const float2 gv = cpl == 2 ? reinterpret_cast<const float2 *>(gbuf + en.x * CH)[lane]
-                                           : make_float2(gbuf[en.x * CH + lane], 0.f);
-                fma2v(acc, __uint_as_float(en.y), gv);
+            if (i < e) {
+                const uint2 e0 = s_ent[i];
+                const float4 *g0 = reinterpret_cast<const float4 *>(gbuf + e0.x * CH);
+                const float w0 = __uint_as_float(e0.y);
+                fma4v(a, w0, g0[gl]);
+                if (CH == 64) fma4v(bb, w0, g0[8 + gl]);
             }
-            return acc;
+#pragma unroll
+            for (int o = 8; o <= 16; o <<= 1) {
+                a.x += __shfl_xor_sync(0xffffffffu, a.x, o); a.y += __shfl_xor_sync(0xffffffffu, a.y, o);
+                a.z += __shfl_xor_sync(0xffffffffu, a.z, o); a.w += __shfl_xor_sync(0xffffffffu, a.w, o);
+                if (CH == 64) {
+                    bb.x += __shfl_xor_sync(0xffffffffu, bb.x, o); bb.y += __shfl_xor_sync(0xffffffffu, bb.y, o);
+                    bb.z += __shfl_xor_sync(0xffffffffu, bb.z, o); bb.w += __shfl_xor_sync(0xffffffffu, bb.w, o);
+                }
+            }
         };
-        auto store = [&](int u, float2 acc) {
+        // group 0 stores the piece's 32 or 64 channels
+        auto store = [&](int u, const float4 &a, const float4 &bb) {
+            if (grp != 0) return;
             float *dst = partial + (int64_t(r.x) + u) * C + c0;
-            if (cpl == 2) {
-                if (c0 + 2 * lane + 1 < C) reinterpret_cast<float2 *>(dst)[lane] = acc;
-                else if (c0 + 2 * lane < C) dst[2 * lane] = acc.x;
-            } else if (c0 + lane < C) {
-                dst[lane] = acc.x;
-            }
+            if (c0 + 4 * gl < C) *reinterpret_cast<float4 *>(dst + 4 * gl) = a;
+            if (CH == 64 && c0 + 32 + 4 * gl < C) *reinterpret_cast<float4 *>(dst + 32 + 4 * gl) = bb;
         };
+        float4 *pc = s_piece[c & 1];   // [warp][first, last][16 float4]
+        int *sf = s_first[c & 1], *sla = s_last[c & 1];
         int first_u = -1, last_u = -1;
         if (r0 < r1) {
             for (int u = u_lo; u < nseg && int(seg[u]) < r1; ++u) {
                 const int sb = int(seg[u]), se = (u + 1 < nseg) ? int(seg[u + 1]) : n;
-                const float2 acc = walk(max(sb, r0), min(se, r1));
-                if (sb < r0) {            // continues a segment begun by an earlier warp
-                    s_piece[(warp * 2) * 32 + lane] = acc;
-                    first_u = u;
-                } else if (se > r1) {     // begins a segment that later warps continue
-                    s_piece[(warp * 2 + 1) * 32 + lane] = acc;
-                    last_u = u;
+                float4 a, bb;
+                walk(max(sb, r0), min(se, r1), a, bb);
+                if (sb < r0 || se > r1) {
+                    // continues a segment begun by an earlier warp (slot 0), or
+                    // begins one that later warps continue (slot 1)
+                    const int sl = sb < r0 ? 0 : 1;
+                    if (grp == 0) {
+                        pc[(warp * 2 + sl) * 16 + gl] = a;
+                        pc[(warp * 2 + sl) * 16 + 8 + gl] = bb;
+                    }
+                    if (sl == 0) first_u = u; else last_u = u;
                 } else {
-                    store(u, acc);
+                    store(u, a, bb);
                 }
             }
         }
         if (lane == 0) {
-            s_first[warp] = first_u;
-            s_last[warp] = last_u;
+            sf[warp] = first_u;
+            sla[warp] = last_u;
         }
-        __syncthreads();
-        if (s_last[warp] >= 0) {
-            const int u = s_last[warp];
-            float2 acc = s_piece[(warp * 2 + 1) * 32 + lane];
+        __syncthreads();   // the chunk's g is consumed and the pieces are visible
+        if (use_tma && threadIdx.x == 0 && c + nbuf < nchunks) {
+            // refill the buffer while the pieces are combined (the pieces use
+            // the other half of the piece buffer in the next chunk)
+            const int buf = nbuf == 2 ? (c & 1) : 0;
+            tma_expect_tx(&s_bar[buf], chunk_bytes);
+            tma_load_3d(s_g + size_t(buf) * T * CH, &gmap, (c + nbuf) * CH, tx * tile_w, ty * tile_h,
+                        &s_bar[buf]);
+        }
+        if (sla[warp] >= 0) {
+            const int u = sla[warp];
+            float4 a = pc[(warp * 2 + 1) * 16 + gl], bb = pc[(warp * 2 + 1) * 16 + 8 + gl];
             for (int w2 = warp + 1; w2 < NWARP; ++w2) {
                 const int a2 = int(int64_t(n) * w2 / NWARP), b2 = int(int64_t(n) * (w2 + 1) / NWARP);
                 if (a2 >= b2) continue;        // an empty range holds no piece
-                if (s_first[w2] != u) break;
-                const float2 v = s_piece[(w2 * 2) * 32 + lane];
-                acc.x += v.x;
-                acc.y += v.y;
+                if (sf[w2] != u) break;
+                const float4 v = pc[(w2 * 2) * 16 + gl], vb = pc[(w2 * 2) * 16 + 8 + gl];
+                a.x += v.x; a.y += v.y; a.z += v.z; a.w += v.w;
+                bb.x += vb.x; bb.y += vb.y; bb.z += vb.z; bb.w += vb.w;
             }
-            store(u, acc);
-        }
-        if (use_tma) {
-            __syncthreads();   // every warp is done with this buffer: refill it
-            if (threadIdx.x == 0 && c + nbuf < nchunks) {
-                const int buf = nbuf == 2 ? (c & 1) : 0;
-                tma_expect_tx(&s_bar[buf], chunk_bytes);
-                tma_load_3d(s_g + size_t(buf) * T * CH, &gmap, (c + nbuf) * CH, tx * tile_w, ty * tile_h,
-                            &s_bar[buf]);
-            }
+            store(u, a, bb);
         }
     }
     if (c_fail >= 0 && threadIdx.x == 0) {
@@ -801,7 +830,7 @@ cudaError_t backward_impl(const qr_frame &f, const void *feat, const float *scal
     }
     // per-tile partials; for K <= 8 the tile's rows of g are staged by TMA
     // (3-D boxes {64 channels, tile_w pixels, tile_h rows} of the [H][W][C]
-    // gradient, double-buffered) when the driver provides a tensor-map encoder
+    // gradient) when the driver provides a tensor-map encoder
     int npow2 = 1;
     while (npow2 < 256 * K) npow2 <<= 1;
     const int CH = K <= 8 ? 64 : 32;
@@ -819,15 +848,14 @@ cudaError_t backward_impl(const qr_frame &f, const void *feat, const float *scal
                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
             use_tma = 1;
     }
-    // One CTA per tile.  With TMA staging and K <= 8 the CTA holds one g chunk
-    // (64 channels x 256 pixels, 64 KB) and reads the E terms from global
-    // memory, so two CTAs share an SM and one's sort and gathers overlap the
-    // other's walk; otherwise one CTA per SM stages the E terms and
-    // double-buffers g.
+    // One CTA per tile.  With TMA staging the CTA holds one g chunk (64
+    // channels x 256 pixels, 64 KB) and reads the E terms from global memory,
+    // so two CTAs share an SM and one's sort, gathers and staging waits
+    // overlap the other's walk.
     const bool k32 = K <= 8 && f.n < (int64_t(1) << 21);
     const size_t key_bytes = k32 ? 4 : 8;
-    const int nbuf = use_tma && K <= 8 ? 1 : use_tma ? 2 : 1;
-    const int stage_e = (K <= 8 && nbuf == 2) ? 1 : 0;
+    const int nbuf = 1;
+    const int stage_e = 0;
     const size_t g_off = (size_t(npow2) * key_bytes + size_t(256 * K) * (12 + (stage_e ? 16 : 0)) + 1023) &
                          ~size_t(1023);
     const size_t smem = 1024 + g_off + size_t(nbuf) * 256 * CH * 4;

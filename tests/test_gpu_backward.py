@@ -63,6 +63,34 @@ def test_backward_tiny_matches_oracle():
     print("tiny backward rel errors", e)
 
 
+@pytest.mark.parametrize("C", [1040, 2056])
+def test_backward_wide_rows(C):
+    """Rows wider than one CTA's warps cover at once (C / 128 blocks > 8, the
+    last one partial) and widths the blend does not serve: the backward alone,
+    on the forward's selection."""
+    import torch
+    from paper_2512_20927_gb300 import qrender as q
+    g, _ = scenes.tiny_scene(n=1500)
+    cam = scenes.tiny_camera(64, 48)
+    K = 8
+    rng = np.random.default_rng(11)
+    f = rng.normal(size=(g.n, C)).astype(np.float32)
+    res = q.render_frame(q.gaussians_to_device(g), None, cam, K=K)
+    pr, pix, ref = H.run_oracle(g, f, cam, K)
+    tie = (ref.tie & compare.Q_TIE_BITS) != 0
+    gout = rng.normal(size=(cam.width * cam.height, C))
+    gout[tie] = 0.0
+    gf, ga, gc = q.qr_backward(res["frame"], torch.from_numpy(f).cuda(), None, res["ids"],
+                               res["weights"], res["counts"],
+                               torch.from_numpy(gout.astype(np.float32)).cuda())
+    torch.cuda.synchronize()
+    rf, ra, rc = oracle.backward(pr, f, K, pix, gout.astype(np.float32).astype(np.float64),
+                                 alpha_min=oracle.ALPHA_MIN_F32, alpha_max=oracle.ALPHA_MAX_F32)
+    _compare("feat", gf.cpu().numpy(), rf, 2e-5)
+    _compare("alpha", ga.cpu().numpy(), ra, 2e-4)
+    _compare("conic", gc.cpu().numpy(), rc, 2e-4)
+
+
 @pytest.mark.parametrize("K", [4, 16])
 def test_backward_room_matches_oracle(K):
     g, f = H.small_room(n=20000, channels=64)

@@ -107,6 +107,9 @@ bwd_pixel(const float4 *__restrict__ rec_m, const float4 *__restrict__ rec_w,
     const float inv_n = LOSS ? cos_inv_count(loss.out2) : 0.f;
     for (int64_t p = warp0; p < P; p += nw) {
         const int m = cnt[p];
+        // the pixel's entries, loaded before (and independently of) its rows
+        const int id = lane < m ? ids[p * K + lane] : 0;
+        const float wj = lane < m ? wts[p * K + lane] : 0.f;
         float gr[VPL > 0 ? VPL : 1][CPV];
         float *g = grad_out + p * int64_t(C);
         if (LOSS) {
@@ -154,8 +157,6 @@ bwd_pixel(const float4 *__restrict__ rec_m, const float4 *__restrict__ rec_w,
         }
         if (m == 0) continue;
         const float ux = float(p % W) + 0.5f, uy = float(p / W) + 0.5f;
-        const int id = lane < m ? ids[p * K + lane] : 0;
-        const float wj = lane < m ? wts[p * K + lane] : 0.f;
         // s_j = g . f_j for every quantile Gaussian j (lane j keeps s_j): the
         // lane's slice of g is held in registers, four rows are loaded at once
         // and their four partial dots reduced together

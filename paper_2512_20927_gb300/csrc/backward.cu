@@ -306,14 +306,14 @@ __device__ __forceinline__ void bitonic64(unsigned long long *s, int npow2) {
 // K <= 8, else 64-bit (gid << 32 | local) -- are sorted once (E = 1..8 per
 // thread in registers when K <= 8, else a shared-memory network), so the
 // entries of each distinct Gaussian form a segment in (pixel, entry) order.
-// Each entry's pixel, weight and per-entry (dalpha, dA) terms are then
-// gathered into shared memory in sorted order with independent loads; per
-// CH-channel chunk, the tile's rows of g are staged in shared memory (by TMA,
-// double-buffered, when a tensor map is given) and one warp per segment sums
-// w * g[pixel] over the segment (eight entries in flight) into that segment's
-// partial row, stored at slot range.x + segment of the tile's intersection
-// range.  The (dalpha, dA) terms are summed per segment by the warp's lanes in
-// a fixed order.
+// Each entry's pixel and weight are then gathered into shared memory in
+// sorted order with independent loads; the (dalpha, dA) terms are summed per
+// segment by a warp's lanes in a fixed order.  Per CH-channel chunk, the
+// tile's rows of g are staged in shared memory (by TMA when a tensor map is
+// given, the next chunk's copy issued as soon as the walk has read the
+// current one) and the warps walk equal shares of the entries (see below),
+// each segment's w * g[pixel] sum going to its partial row at slot range.x +
+// segment of the tile's intersection range.
 constexpr unsigned kTmaSpin = 1u << 26;   // polls before a staging wait gives up
 
 template <int E, typename KT>
@@ -326,14 +326,14 @@ bwd_tile_partials(const uint2 *__restrict__ ranges, int W, int H, int tile_w, in
                   const uint2 *__restrict__ rect, const uint32_t *__restrict__ tcount,
                   const uint32_t *__restrict__ goff, uint32_t *__restrict__ slotmap, int64_t X,
                   uint32_t *__restrict__ gflag, uint32_t *__restrict__ lists, int64_t N,
-                  const __grid_constant__ CUtensorMap gmap, int use_tma, int nbuf, int stage_e,
+                  const __grid_constant__ CUtensorMap gmap, int use_tma,
                   uint32_t *__restrict__ counters) {
     constexpr bool K32 = sizeof(KT) == 4;
     constexpr int SHIFT = K32 ? 11 : 32;
     extern __shared__ __align__(16) unsigned char s_dyn[];
     __shared__ uint32_t s_w[32];
     __shared__ uint32_t s_nseg;
-    __shared__ __align__(8) uint64_t s_bar[2];
+    __shared__ __align__(8) uint64_t s_bar[1];
     __shared__ int s_ok;
     // per chunk parity, per warp: the continued and the begun piece (64 channels each)
     __shared__ __align__(16) float4 s_piece[2][(T / 32) * 2 * 16];
@@ -347,10 +347,8 @@ bwd_tile_partials(const uint2 *__restrict__ ranges, int W, int H, int tile_w, in
     KT *s_key = reinterpret_cast<KT *>(base);                                    // npow2
     uint32_t *seg = reinterpret_cast<uint32_t *>(s_key + npow2);                 // T*K
     uint2 *s_ent = reinterpret_cast<uint2 *>(seg + T * K);                       // T*K (pixel, w)
-    float4 *s_e4 = reinterpret_cast<float4 *>(s_ent + T * K);                    // T*K if stage_e
-    const size_t g_off = (size_t(npow2) * sizeof(KT) + size_t(T * K) * (12 + (stage_e ? 16 : 0)) +
-                          1023) & ~size_t(1023);
-    float *s_g = reinterpret_cast<float *>(base + g_off);                       // [2][T*CH]
+    const size_t g_off = (size_t(npow2) * sizeof(KT) + size_t(T * K) * 12 + 1023) & ~size_t(1023);
+    float *s_g = reinterpret_cast<float *>(base + g_off);                       // [T*CH]
     const int tile = blockIdx.x;
     const int tx = tile % tiles_x, ty = tile / tiles_x;
     const int tile_h = T / tile_w;
@@ -368,14 +366,11 @@ bwd_tile_partials(const uint2 *__restrict__ ranges, int W, int H, int tile_w, in
     const int nchunks = (C + CH - 1) / CH;
     const uint32_t chunk_bytes = uint32_t(T) * uint32_t(CH) * 4u;
     if (use_tma && threadIdx.x == 0) {
-        // the first nbuf (1 or 2) chunks of g fly while the keys are sorted
+        // the first chunk of g flies while the keys are sorted
         tma_mbar_init(&s_bar[0], 1);
-        tma_mbar_init(&s_bar[1], 1);
         tma_fence_init();
-        for (int b = 0; b < nbuf && b < nchunks; ++b) {
-            tma_expect_tx(&s_bar[b], chunk_bytes);
-            tma_load_3d(s_g + size_t(b) * T * CH, &gmap, b * CH, tx * tile_w, ty * tile_h, &s_bar[b]);
-        }
+        tma_expect_tx(&s_bar[0], chunk_bytes);
+        tma_load_3d(s_g, &gmap, 0, tx * tile_w, ty * tile_h, &s_bar[0]);
     }
     auto key_of = [&](int j) -> KT {
         return j < m ? (KT(uint32_t(ids[p * K + j])) << SHIFT) | KT(uint32_t(threadIdx.x * K + j))
@@ -397,14 +392,13 @@ bwd_tile_partials(const uint2 *__restrict__ ranges, int W, int H, int tile_w, in
     }
     __syncthreads();
     constexpr KT LOCAL_MASK = K32 ? KT(0x7FF) : KT(0xFFFFFFFFu);
-    // each entry's (local pixel, weight) and E terms in sorted order: independent loads
+    // each entry's (local pixel, weight) in sorted order: independent loads
 #pragma unroll 4
     for (int i = threadIdx.x; i < n; i += T) {
         const uint32_t loc = uint32_t(s_key[i] & LOCAL_MASK);
         const int pix = int(loc) / K, j = int(loc) - pix * K;
         const int64_t pp = int64_t(ty * tile_h + pix / tile_w) * W + tx * tile_w + pix % tile_w;
         s_ent[i] = make_uint2(uint32_t(pix), __float_as_uint(wts[pp * K + j]));
-        if (stage_e) s_e4[i] = E4[pp * K + j];
     }
     if (threadIdx.x == 0) s_nseg = 0;
     // segment starts
@@ -445,15 +439,10 @@ bwd_tile_partials(const uint2 *__restrict__ ranges, int W, int H, int tile_w, in
         const int b = int(seg[u]), e = (u + 1 < nseg) ? int(seg[u + 1]) : n;
         float4 sacc = make_float4(0.f, 0.f, 0.f, 0.f);
         for (int i = b + lane; i < e; i += 32) {
-            float4 ee;
-            if (stage_e) {
-                ee = s_e4[i];
-            } else {
-                const uint32_t loc = uint32_t(s_key[i] & LOCAL_MASK);
-                const int pix = int(loc) / K, j = int(loc) - pix * K;
-                const int64_t pp = int64_t(ty * tile_h + pix / tile_w) * W + tx * tile_w + pix % tile_w;
-                ee = E4[pp * K + j];
-            }
+            const uint32_t loc = uint32_t(s_key[i] & LOCAL_MASK);
+            const int pix = int(loc) / K, j = int(loc) - pix * K;
+            const int64_t pp = int64_t(ty * tile_h + pix / tile_w) * W + tx * tile_w + pix % tile_w;
+            const float4 ee = E4[pp * K + j];
             sacc.x += ee.x; sacc.y += ee.y; sacc.z += ee.z; sacc.w += ee.w;
         }
 #pragma unroll
@@ -479,12 +468,9 @@ bwd_tile_partials(const uint2 *__restrict__ ranges, int W, int H, int tile_w, in
         const int c0 = c * CH;
         const float *gbuf = s_g;
         if (use_tma) {
-            const int buf = nbuf == 2 ? (c & 1) : 0;
-            const uint32_t parity = uint32_t(nbuf == 2 ? c >> 1 : c) & 1u;
-            if (threadIdx.x == 0) s_ok = tma_mbar_wait(&s_bar[buf], parity, kTmaSpin) ? 1 : 0;
+            if (threadIdx.x == 0) s_ok = tma_mbar_wait(&s_bar[0], uint32_t(c) & 1u, kTmaSpin) ? 1 : 0;
             __syncthreads();
             if (!s_ok) { c_fail = c; break; }
-            gbuf = s_g + size_t(buf) * T * CH;
         } else {
             __syncthreads();   // the previous chunk is consumed
             for (int i = threadIdx.x; i < T * (CH / 4); i += T) {
@@ -574,13 +560,11 @@ bwd_tile_partials(const uint2 *__restrict__ ranges, int W, int H, int tile_w, in
             sla[warp] = last_u;
         }
         __syncthreads();   // the chunk's g is consumed and the pieces are visible
-        if (use_tma && threadIdx.x == 0 && c + nbuf < nchunks) {
+        if (use_tma && threadIdx.x == 0 && c + 1 < nchunks) {
             // refill the buffer while the pieces are combined (the pieces use
             // the other half of the piece buffer in the next chunk)
-            const int buf = nbuf == 2 ? (c & 1) : 0;
-            tma_expect_tx(&s_bar[buf], chunk_bytes);
-            tma_load_3d(s_g + size_t(buf) * T * CH, &gmap, (c + nbuf) * CH, tx * tile_w, ty * tile_h,
-                        &s_bar[buf]);
+            tma_expect_tx(&s_bar[0], chunk_bytes);
+            tma_load_3d(s_g, &gmap, (c + 1) * CH, tx * tile_w, ty * tile_h, &s_bar[0]);
         }
         if (sla[warp] >= 0) {
             const int u = sla[warp];
@@ -598,10 +582,9 @@ bwd_tile_partials(const uint2 *__restrict__ ranges, int W, int H, int tile_w, in
     }
     if (c_fail >= 0 && threadIdx.x == 0) {
         // a staging copy did not arrive: report it, and let the copies still in
-        // flight (chunks c_fail .. c_fail + nbuf - 1) land before the CTA exits
+        // flight (chunk c_fail) land before the CTA exits
         atomicExch(&counters[CNT_STATUS], uint32_t(QR_ERR_DEVICE_TIMEOUT));
-        for (int cc = c_fail; cc < c_fail + nbuf && cc < nchunks; ++cc)
-            tma_mbar_wait(&s_bar[nbuf == 2 ? (cc & 1) : 0], uint32_t(nbuf == 2 ? cc >> 1 : cc) & 1u, kTmaSpin);
+        tma_mbar_wait(&s_bar[0], uint32_t(c_fail) & 1u, kTmaSpin);
     }
 }
 
@@ -855,11 +838,8 @@ cudaError_t backward_impl(const qr_frame &f, const void *feat, const float *scal
     // overlap the other's walk.
     const bool k32 = K <= 8 && f.n < (int64_t(1) << 21);
     const size_t key_bytes = k32 ? 4 : 8;
-    const int nbuf = 1;
-    const int stage_e = 0;
-    const size_t g_off = (size_t(npow2) * key_bytes + size_t(256 * K) * (12 + (stage_e ? 16 : 0)) + 1023) &
-                         ~size_t(1023);
-    const size_t smem = 1024 + g_off + size_t(nbuf) * 256 * CH * 4;
+    const size_t g_off = (size_t(npow2) * key_bytes + size_t(256 * K) * 12 + 1023) & ~size_t(1023);
+    const size_t smem = 1024 + g_off + size_t(256) * CH * 4;
     auto tp = [&](auto kern) {
         cudaError_t ee = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
         if (ee != cudaSuccess) return ee;
@@ -870,8 +850,7 @@ cudaError_t backward_impl(const qr_frame &f, const void *feat, const float *scal
                                                cnt, E, grad_out, C, K, CH, partial, partial_s,
                                                slot<uint2>(f, S_RECT), slot<uint32_t>(f, S_TCOUNT),
                                                goff, slotmap, f.max_isect, gflag, lists, f.n,
-                                               gmap, use_tma, nbuf,
-                                               stage_e, counters);
+                                               gmap, use_tma, counters);
         return cudaSuccess;
     };
     if (k32) {

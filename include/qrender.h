@@ -328,13 +328,16 @@ qr_status qr_cosine_backward(const qr_frame *frame, const void *feat, const floa
 
 /* Open-vocabulary relevance (Sec. 5 scores features against text embeddings by
  * cosine similarity): out[p][q] = sum_c map[p][c] * Q[q][c] on the tensor
- * cores (tcgen05, BF16 inputs, FP32 accumulation in TMEM).  feature_map
- * [P][C] float32 (rounded to BF16 on the fly), queries_bf16 [Q][C] (unit
- * vectors give cosine similarity against unit-normalised features),
- * out [P][Q] float32.  Q in {16, 32, 64, 128}; C a multiple of 64 with the
- * queries fitting in shared memory (Q * C * 2 bytes <= ~190 KB).  status: a
- * device int32 the kernel sets to QR_ERR_DEVICE_TIMEOUT if a bounded wait
- * gives up (it is never cleared by the library). */
+ * cores (tcgen05, FP32 accumulation in TMEM).  Where the queries fit in shared
+ * memory as FP32 (Q * C * 4 bytes plus four 16 KB map stages <= 227 KB) the
+ * map is streamed by TMA and multiplied as TF32 (at least 10 mantissa bits);
+ * otherwise it is rounded to BF16 on the fly.  feature_map [P][C] float32,
+ * queries_bf16 [Q][C] (unit vectors give cosine similarity against
+ * unit-normalised features), out [P][Q] float32.  Q in {16, 32, 64, 128}; C a
+ * multiple of 64 with the BF16 queries fitting in shared memory (Q * C * 2
+ * bytes <= ~190 KB).  status: a device int32 the kernel sets to
+ * QR_ERR_DEVICE_TIMEOUT if a bounded wait gives up (it is never cleared by the
+ * library). */
 qr_status qr_relevance(const float *feature_map, const uint16_t *queries_bf16, int32_t Q, int32_t C,
                        int64_t P, float *out, int32_t *status, qr_stream stream);
 

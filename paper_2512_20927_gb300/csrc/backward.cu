@@ -41,7 +41,7 @@ namespace qr {
 namespace {
 
 constexpr int T = 256;
-constexpr int kRowsSmall = 256;   // selected Gaussians' maps up to this many tiles: 256-thread row CTAs
+constexpr int kRowsSmall = 64;    // selected Gaussians' maps up to this many tiles: 256-thread row CTAs
 
 template <int DT> struct VecB;
 template <> struct VecB<QR_F32> { static constexpr int C = 4; static constexpr int E = 4; };

@@ -30,6 +30,7 @@
 //      partials in tile order (warps over channel blocks and fixed row
 //      subsets).  Rows of unselected Gaussians stay as cleared.
 #include <cstring>
+#include <mutex>
 
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
@@ -714,6 +715,22 @@ int sms_now() {
 
 inline size_t up256(size_t x) { return (x + 255) / 256 * 256; }
 
+// A non-blocking stream per device on which the backward clears its outputs
+// while the tile kernel runs (forked from and joined back to the caller's
+// stream with events, so the pattern is also valid under graph capture).
+cudaStream_t side_stream() {
+    constexpr int kMaxDev = 64;
+    static cudaStream_t streams[kMaxDev];
+    static std::once_flag once[kMaxDev];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return nullptr;
+    std::call_once(once[dev], [dev] {
+        if (cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking) != cudaSuccess)
+            streams[dev] = nullptr;
+    });
+    return streams[dev];
+}
+
 struct BwdLayout {
     size_t e, partial, partial_s, goff, slotmap, gflag, lists, total;
 };
@@ -812,6 +829,42 @@ cudaError_t backward_impl(const qr_frame &f, const void *feat, const float *scal
         if (e == cudaSuccess) e = launch_cos_final(loss->term, num_pixels(f), loss->out2, s);
         if (e != cudaSuccess) return e;
     }
+    // rows of Gaussians that no tile selects are zero: clear the outputs on the
+    // side stream, overlapping the tile kernel (which is not bandwidth-bound),
+    // and join before the rows are written; without a side stream, in order
+    cudaStream_t side = side_stream();
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    if (side && (cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+                 cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming) != cudaSuccess)) {
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        ev_fork = nullptr;
+        side = nullptr;
+    }
+    cudaStream_t zs = s;
+    if (side) {
+        e = cudaEventRecord(ev_fork, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(side, ev_fork, 0);
+        if (e != cudaSuccess) {
+            cudaEventDestroy(ev_fork);
+            cudaEventDestroy(ev_join);
+            return e;
+        }
+        zs = side;
+    }
+    e = cudaMemsetAsync(grad_feat, 0, size_t(f.n) * size_t(C) * 4, zs);
+    if (e == cudaSuccess && grad_alpha) e = cudaMemsetAsync(grad_alpha, 0, size_t(f.n) * 4, zs);
+    if (e == cudaSuccess && grad_conic) e = cudaMemsetAsync(grad_conic, 0, size_t(f.n) * 12, zs);
+    // the side stream joins the caller's stream again (also on an error path)
+    auto join = [&](cudaError_t err) {
+        if (!side) return err;
+        cudaError_t ej = cudaEventRecord(ev_join, side);
+        if (ej == cudaSuccess) ej = cudaStreamWaitEvent(s, ev_join, 0);
+        cudaEventDestroy(ev_fork);
+        cudaEventDestroy(ev_join);
+        side = nullptr;
+        return err != cudaSuccess ? err : ej;
+    };
+    if (e != cudaSuccess) return join(e);
     // per-tile partials; for K <= 8 the tile's rows of g are staged by TMA
     // (3-D boxes {64 channels, tile_w pixels, tile_h rows} of the [H][W][C]
     // gradient) when the driver provides a tensor-map encoder
@@ -862,13 +915,9 @@ cudaError_t backward_impl(const qr_frame &f, const void *feat, const float *scal
           : K <= 4 ? tp(bwd_tile_partials<4, unsigned long long>) : K <= 8 ? tp(bwd_tile_partials<8, unsigned long long>)
                    : tp(bwd_tile_partials<0, unsigned long long>);
     }
+    e = join(e);
     if (e != cudaSuccess) return e;
-    // rows of Gaussians that no tile selected are zero; the others get their
-    // partials added in tile order
-    e = cudaMemsetAsync(grad_feat, 0, size_t(f.n) * size_t(C) * 4, s);
-    if (e == cudaSuccess && grad_alpha) e = cudaMemsetAsync(grad_alpha, 0, size_t(f.n) * 4, s);
-    if (e == cudaSuccess && grad_conic) e = cudaMemsetAsync(grad_conic, 0, size_t(f.n) * 12, s);
-    if (e != cudaSuccess) return e;
+    // the selected Gaussians' rows in tile order, over the cleared outputs
     const uint32_t *tcount = slot<uint32_t>(f, S_TCOUNT);
     bwd_rows<256><<<unsigned(sms_now() * 8), 256, 0, s>>>(
         lists, lists + 2 * f.n, goff, tcount, slotmap, f.max_isect, partial, partial_s, C,

@@ -114,6 +114,7 @@ blend_kernel(const uint4 *__restrict__ feat, const float *__restrict__ scale, in
              const int32_t *__restrict__ ids, const float *__restrict__ wts,
              const uint8_t *__restrict__ cnt, int64_t P, int K, int W, int H,
              float4 *__restrict__ out) {
+    pdl_wait();   // the predecessor's outputs are complete and visible
     constexpr int CPV = Vec<DT>::C;          // channels per vector
     constexpr int PPW = 32 / LPP;            // pixels per warp
     constexpr int ROWV = LPP * VPL;          // vectors per row
@@ -202,6 +203,7 @@ blend_group_kernel(const uint4 *__restrict__ feat, const float *__restrict__ sca
                    int64_t n_gauss, const int32_t *__restrict__ ids,
                    const float *__restrict__ wts, const uint8_t *__restrict__ cnt, int64_t P,
                    int K, int W, int H, float4 *__restrict__ out) {
+    pdl_wait();   // the predecessor's outputs are complete and visible
     constexpr int CPV = Vec<DT>::C;
     constexpr int ROWV = 32 * VPL;
     constexpr unsigned FULL = 0xffffffffu;
@@ -301,14 +303,14 @@ cudaError_t run_group(const void *feat, const float *scale, int64_t n_gauss, con
     const unsigned blocks = unsigned((items + 255) / 256);
     const uint4 *f = static_cast<const uint4 *>(feat);
     float4 *o = reinterpret_cast<float4 *>(out);
-    if (K <= 8)
-        blend_group_kernel<DT, VPL, 4><<<blocks, kThreads, 0, s>>>(f, scale, n_gauss, ids, w, cnt, P, K, W, H, o);
-    else if (K <= 16)
-        blend_group_kernel<DT, VPL, 2><<<blocks, kThreads, 0, s>>>(f, scale, n_gauss, ids, w, cnt, P, K, W, H, o);
-    else
-        blend_group_kernel<DT, VPL, 1><<<blocks, kThreads, 0, s>>>(f, scale, n_gauss, ids, w, cnt, P, K, W, H, o);
+    auto go = [&](auto kern) {
+        return pdl_launch(kern, dim3(blocks), dim3(kThreads), 0, s, f, scale, n_gauss, ids, w, cnt, P,
+                          K, W, H, o);
+    };
+    const cudaError_t e = K <= 8 ? go(blend_group_kernel<DT, VPL, 4>)
+                        : K <= 16 ? go(blend_group_kernel<DT, VPL, 2>) : go(blend_group_kernel<DT, VPL, 1>);
     count_launch();
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 template <int DT, int LPP, int VPL>
@@ -317,11 +319,11 @@ cudaError_t run(const void *feat, const float *scale, int64_t n_gauss, const int
                 cudaStream_t s) {
     const int64_t items = (W > 0) ? int64_t((W + 15) >> 4) * ((H + 15) >> 4) * 256 : P;
     const int64_t blocks = (items + 255) / 256;
-    blend_kernel<DT, LPP, VPL><<<unsigned(blocks), kThreads, 0, s>>>(
-        static_cast<const uint4 *>(feat), scale, n_gauss, ids, w, cnt, P, K, W, H,
-        reinterpret_cast<float4 *>(out));
+    const cudaError_t e = pdl_launch(blend_kernel<DT, LPP, VPL>, dim3(unsigned(blocks)), dim3(kThreads),
+                                     0, s, static_cast<const uint4 *>(feat), scale, n_gauss, ids, w,
+                                     cnt, P, K, W, H, reinterpret_cast<float4 *>(out));
     count_launch();
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 template <int DT>

@@ -49,6 +49,7 @@ project_cull(int64_t n, const float *__restrict__ mean, const float *__restrict_
              uint32_t *__restrict__ dkey, uint32_t *__restrict__ cand,
              uint32_t *__restrict__ vis_count, uint32_t *__restrict__ tile_sum,
              int *__restrict__ diff, int64_t ndiff, uint32_t *__restrict__ counters) {
+    pdl_wait();   // the predecessor's outputs are complete and visible
     const int64_t g = int64_t(blockIdx.x) * kThreads + threadIdx.x;
     if (blockIdx.x == 0 && threadIdx.x == 0) counters[CNT_N] = uint32_t(n);
     // clear what the exact stage accumulates into (one word per 256 ids, the
@@ -116,6 +117,7 @@ project_exact(const float *__restrict__ mean, const float *__restrict__ log_scal
               uint32_t *__restrict__ dkey, uint32_t *__restrict__ vis_count,
               uint32_t *__restrict__ tile_sum, int tiles_x, int tiles_y, int *__restrict__ diff,
               const uint32_t *__restrict__ counters) {
+    pdl_wait();   // the predecessor's outputs are complete and visible
     const uint32_t ncand = counters[CNT_CAND];
     // this CTA's copy of the difference array of per-tile counts
     int *dcopy = diff + size_t(blockIdx.x % kDiffCopies) * size_t(tiles_x + 1) * size_t(tiles_y + 1);
@@ -275,17 +277,18 @@ cudaError_t launch_project(const qr_frame &f, const float *mean, const float *lo
     uint32_t *cand = slot<uint32_t>(f, S_KID);
     uint2 *rect = slot<uint2>(f, S_RECT);
     uint32_t *tcount = slot<uint32_t>(f, S_TCOUNT), *dkey = slot<uint32_t>(f, S_GKEY);
-    project_cull<<<blocks, kThreads, 0, s>>>(n, mean, log_scale, opacity, cam, f.params.dilation,
-                                             f.params.alpha_min, rect, tcount, dkey, cand, vis, tsum,
-                                             diff, ndiff, counters);
+    e = pdl_launch(project_cull, dim3(blocks), dim3(kThreads), 0, s, n, mean,
+                               log_scale, opacity, cam, f.params.dilation, f.params.alpha_min,
+                               rect, tcount, dkey, cand, vis, tsum, diff, ndiff, counters);
+    if (e != cudaSuccess) return e;
     const unsigned grid = blocks < unsigned(sms) * 4u ? blocks : unsigned(sms) * 4u;
-    project_exact<<<grid, kThreads, 0, s>>>(
-        mean, log_scale, quat, opacity, cam, f.params.dilation, f.params.alpha_min,
-        f.params.tile_w, f.params.tile_h, cand, slot<float4>(f, S_REC_M), slot<float4>(f, S_REC_C),
-        slot<float>(f, S_REC_A), slot<float>(f, S_REC_H), rect, tcount, dkey, vis, tsum, f.tiles_x,
-        f.tiles_y, diff, counters);
+    e = pdl_launch(project_exact, dim3(grid), dim3(kThreads), 0, s, mean, log_scale, quat,
+                   opacity, cam, f.params.dilation, f.params.alpha_min, f.params.tile_w,
+                   f.params.tile_h, cand, slot<float4>(f, S_REC_M), slot<float4>(f, S_REC_C),
+                   slot<float>(f, S_REC_A), slot<float>(f, S_REC_H), rect, tcount, dkey, vis,
+                   tsum, f.tiles_x, f.tiles_y, diff, counters);
     count_launch(2);
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace qr

@@ -8,6 +8,29 @@
 
 namespace qr {
 
+// Programmatic dependent launch: a kernel launched by pdl_launch may be
+// scheduled while its predecessor on the stream is still finishing, so its
+// launch overlaps the predecessor's last blocks; its first statement is
+// pdl_wait(), which returns once the predecessor has completed and its writes
+// are visible (a no-op for a kernel launched without the attribute).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t pdl_launch(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // ---------------------------------------------------------------- status word
 // counters[0]: device status (a qr_status value, 0 = OK)
 // counters[1]: number of tile-Gaussian intersections the frame needs

@@ -71,6 +71,7 @@ select_kernel(const float4 *__restrict__ rec_m, const float4 *__restrict__ rec_w
               const uint32_t *__restrict__ isect_gid, const uint2 *__restrict__ ranges, int W,
               int H, int tile_w, int tiles_x, int K, float alpha_min, float alpha_max,
               int32_t *__restrict__ ids, float *__restrict__ wout, uint8_t *__restrict__ cnt) {
+    pdl_wait();   // the predecessor's outputs are complete and visible
     __shared__ float4 s_m[kBatch];
     __shared__ float4 s_c[kBatch];
     __shared__ float s_a[kBatch];
@@ -244,13 +245,14 @@ cudaError_t launch_select(const qr_frame &f, int32_t *ids, float *w, uint8_t *cn
                                              int(dyn));
         if (e != cudaSuccess) return e;
     }
-    select_kernel<<<tiles, kThreads, dyn, s>>>(
-        slot<float4>(f, S_REC_M), slot<float4>(f, S_REC_C), slot<float>(f, S_REC_A), slot<float>(f, S_REC_H),
-        slot<uint32_t>(f, S_IGID),
-        slot<uint2>(f, S_RANGES), f.camera.width, f.camera.height, f.params.tile_w, f.tiles_x, K,
-        f.params.alpha_min, f.params.alpha_max, ids, w, cnt);
+    cudaError_t e = pdl_launch(
+        select_kernel, dim3(tiles), dim3(kThreads), dyn, s, (const float4 *)slot<float4>(f, S_REC_M),
+        (const float4 *)slot<float4>(f, S_REC_C), (const float *)slot<float>(f, S_REC_A),
+        (const float *)slot<float>(f, S_REC_H), (const uint32_t *)slot<uint32_t>(f, S_IGID),
+        (const uint2 *)slot<uint2>(f, S_RANGES), f.camera.width, f.camera.height, f.params.tile_w,
+        f.tiles_x, K, f.params.alpha_min, f.params.alpha_max, ids, w, cnt);
     count_launch();
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace qr

@@ -53,6 +53,7 @@ __global__ void __launch_bounds__(kProjectThreads)
 offsets_apply(const uint32_t *__restrict__ tcount, const uint32_t *__restrict__ kept_base,
               const uint32_t *__restrict__ tsum_base, int64_t n, uint32_t *__restrict__ kid,
               uint32_t *__restrict__ koff, uint32_t *__restrict__ chunk_owner, uint32_t nchunk) {
+    pdl_wait();   // the predecessor's outputs are complete and visible
     __shared__ uint32_t s_w[32];
     const int64_t g = int64_t(blockIdx.x) * kProjectThreads + threadIdx.x;
     const uint32_t c = g < n ? tcount[g] : 0u;
@@ -124,6 +125,7 @@ __global__ void __launch_bounds__(1024)
 bin_scan(uint32_t *kept, uint32_t *tsum, int nblk, uint32_t *counters, uint32_t capacity,
          const int *__restrict__ diff, uint32_t *tcnt, int tiles_x, int tiles_y, uint2 *ranges,
          int in_smem) {
+    pdl_wait();   // the predecessor's outputs are complete and visible
     extern __shared__ uint32_t s_cnt[];
     __shared__ uint32_t s_w[64];
     // both per-block scans in one pass, each thread owning `per` consecutive blocks
@@ -218,6 +220,7 @@ expand_scatter(const uint32_t *__restrict__ koff, const uint32_t *__restrict__ k
                const uint32_t *__restrict__ chunk_owner, const uint32_t *__restrict__ counters,
                int tiles_x, int tiles, const uint2 *__restrict__ ranges,
                uint32_t *__restrict__ cursor, unsigned long long *__restrict__ keys) {
+    pdl_wait();   // the predecessor's outputs are complete and visible
     __shared__ ExpandSmem sm;
     extern __shared__ uint32_t s_agg[];   // AGG: [tiles] counts, [tiles] run bases
     const uint32_t X = counters[CNT_SORT_N];
@@ -343,6 +346,7 @@ __device__ __forceinline__ void merge_cta(const unsigned long long *A, int na,
 __global__ void __launch_bounds__(T)
 tile_sort(const uint2 *__restrict__ ranges, unsigned long long *__restrict__ keys,
           unsigned long long *__restrict__ scratch, uint32_t *__restrict__ igid) {
+    pdl_wait();   // the predecessor's outputs are complete and visible
     extern __shared__ unsigned long long s_k[];   // TS_CAP keys
     const uint2 r = ranges[blockIdx.x];
     const int n = int(r.y - r.x);
@@ -416,30 +420,35 @@ cudaError_t launch_sort(const qr_frame &f, cudaStream_t s) {
     e = cudaFuncSetAttribute(bin_scan, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              int(sizeof(uint32_t) * kScanSmemTiles));
     if (e != cudaSuccess) return e;
-    bin_scan<<<1, 1024, scan_bytes, s>>>(kept, tsum, nblk, counters, uint32_t(f.max_isect), diff,
-                                         tcnt, f.tiles_x, f.tiles_y, ranges, scan_smem);
+    e = pdl_launch(bin_scan, dim3(1), dim3(1024), scan_bytes, s, kept, tsum, nblk, counters,
+                   uint32_t(f.max_isect), diff, tcnt, f.tiles_x, f.tiles_y, ranges, scan_smem);
+    if (e != cudaSuccess) return e;
     uint32_t *chunk_owner = slot<uint32_t>(f, S_CHUNK);
     const uint32_t nchunk = uint32_t(f.max_isect / EMIT_CHUNK + 1);
-    offsets_apply<<<nblk, kProjectThreads, 0, s>>>(slot<uint32_t>(f, S_TCOUNT), kept, tsum, f.n,
-                                                   kid, koff, chunk_owner, nchunk);
+    e = pdl_launch(offsets_apply, dim3(nblk), dim3(kProjectThreads), 0, s,
+                   (const uint32_t *)slot<uint32_t>(f, S_TCOUNT), (const uint32_t *)kept,
+                   (const uint32_t *)tsum, f.n, kid, koff, chunk_owner, nchunk);
+    if (e != cudaSuccess) return e;
     auto *keys = slot<unsigned long long>(f, S_KEYS64);
     if (tiles <= kAggTiles) {
         const size_t agg = sizeof(uint32_t) * 2 * size_t(tiles);
         e = cudaFuncSetAttribute(expand_scatter<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  int(sizeof(uint32_t) * 2 * kAggTiles));
         if (e != cudaSuccess) return e;
-        expand_scatter<true><<<sms * 4, T, agg, s>>>(koff, kid, rect, slot<uint32_t>(f, S_GKEY),
-                                                     chunk_owner, counters, f.tiles_x, tiles,
-                                                     ranges, tcnt, keys);
+        e = pdl_launch(expand_scatter<true>, dim3(sms * 4), dim3(T), agg, s, (const uint32_t *)koff,
+                       (const uint32_t *)kid, rect, (const uint32_t *)slot<uint32_t>(f, S_GKEY),
+                       (const uint32_t *)chunk_owner, counters, f.tiles_x, tiles, ranges, tcnt, keys);
     } else {
-        expand_scatter<false><<<sms * 6, T, 0, s>>>(koff, kid, rect, slot<uint32_t>(f, S_GKEY),
-                                                    chunk_owner, counters, f.tiles_x, tiles,
-                                                    ranges, tcnt, keys);
+        e = pdl_launch(expand_scatter<false>, dim3(sms * 6), dim3(T), 0, s, (const uint32_t *)koff,
+                       (const uint32_t *)kid, rect, (const uint32_t *)slot<uint32_t>(f, S_GKEY),
+                       (const uint32_t *)chunk_owner, counters, f.tiles_x, tiles, ranges, tcnt, keys);
     }
-    tile_sort<<<tiles, T, TS_CAP * sizeof(unsigned long long), s>>>(
-        ranges, keys, slot<unsigned long long>(f, S_SCRATCH64), slot<uint32_t>(f, S_IGID));
+    if (e != cudaSuccess) return e;
+    e = pdl_launch(tile_sort, dim3(tiles), dim3(T), TS_CAP * sizeof(unsigned long long), s,
+                   (const uint2 *)ranges, keys, slot<unsigned long long>(f, S_SCRATCH64),
+                   slot<uint32_t>(f, S_IGID));
     count_launch(4);
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace qr

@@ -233,3 +233,37 @@ def test_cosine_backward_matches_separate_calls(kind, C):
     _compare("alpha", ga2.cpu().numpy(), ga.cpu().numpy().astype(np.float64), 1e-4)
     _compare("conic", gc2.cpu().numpy(), gc.cpu().numpy().astype(np.float64), 1e-4)
     assert (res["counts"] > 0).any()
+
+
+def test_cosine_backward_is_deterministic_and_graph_capturable():
+    """Two eager runs give bit-identical gradients (no floating-point atomics
+    anywhere), and a CUDA-graph replay of the same call -- whose output
+    clearing runs on a forked side stream -- gives the same bits again."""
+    import torch
+    from paper_2512_20927_gb300 import qrender as q
+    g, f = H.small_room(n=20000, channels=128)
+    cam = scenes.room_camera(150, 110)
+    fdev = torch.from_numpy(f).cuda()
+    res = q.render_frame(q.gaussians_to_device(g), fdev, cam, K=8)
+    rng = np.random.default_rng(21)
+    tgt = torch.from_numpy(rng.normal(size=(cam.width * cam.height, 128)).astype(np.float32)).cuda()
+    args = (res["frame"], fdev, None, res["ids"], res["weights"], res["counts"], res["out"], tgt)
+    a = [t.clone() for t in q.qr_cosine_backward(*args)]
+    b = [t.clone() for t in q.qr_cosine_backward(*args)]
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        q.qr_cosine_backward(*args)
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        outs = q.qr_cosine_backward(*args)
+    for t in outs:
+        t.fill_(-1.0)
+    graph.replay()
+    torch.cuda.synchronize()
+    for x, y in zip(a, outs):
+        assert torch.equal(x, y)

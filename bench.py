@@ -336,16 +336,17 @@ def run_gpu(args, ws, rank, local):
 
     # ---- end to end through the host-buffer C-ABI call: every step uploads the
     # Gaussians and the feature table from pinned host memory, renders, and
-    # downloads the map.  Consecutive steps alternate between two streams (with
-    # their own frame and device buffers), so one step's upload overlaps the
-    # previous step's download on the full-duplex host link.
+    # downloads the map.  Consecutive steps rotate over NB streams (each with
+    # its own frame and device buffers), so one step's upload overlaps earlier
+    # steps' downloads on the full-duplex host link.
     e2e = None
     e2e_ms = None
     try:
         nin, nout = q.qr_render_host_bytes(N_GAUSS, WIDTH, HEIGHT, K, C, q.QR_F32)
-        frames = (fr, frame_for(K)[0])
-        dins = [torch.empty(nin + 256, dtype=torch.uint8, device=dev) for _ in range(2)]
-        douts = [torch.empty(nout + 256, dtype=torch.uint8, device=dev) for _ in range(2)]
+        NB = 3
+        frames = [fr] + [frame_for(K)[0] for _ in range(NB - 1)]
+        dins = [torch.empty(nin + 256, dtype=torch.uint8, device=dev) for _ in range(NB)]
+        douts = [torch.empty(nout + 256, dtype=torch.uint8, device=dev) for _ in range(NB)]
 
         class _Aligned:
             def __init__(self, t):
@@ -355,8 +356,8 @@ def run_gpu(args, ws, rank, local):
                 return self.p
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).pin_memory()  # noqa: E731
         hm, hl, hq, ho, hf = (pin(g.mean), pin(g.log_scale), pin(g.quat), pin(g.opacity), pin(feat))
-        houts = [torch.empty((P, C), dtype=torch.float32).pin_memory() for _ in range(2)]
-        side = [torch.cuda.Stream(device=dev) for _ in range(2)]
+        houts = [torch.empty((P, C), dtype=torch.float32).pin_memory() for _ in range(NB)]
+        side = [torch.cuda.Stream(device=dev) for _ in range(NB)]
 
         def e2e_run(nsteps):
             e0 = torch.cuda.Event(enable_timing=True)
@@ -365,7 +366,7 @@ def run_gpu(args, ws, rank, local):
             for s in side:
                 s.wait_event(e0)
             for i in range(nsteps):
-                b = i % 2
+                b = i % NB
                 q.qr_render_host(frames[b], hm, hl, hq, ho, hf, None, q.QR_F32, C,
                                  _Aligned(dins[b]), _Aligned(douts[b]), houts[b], stream=side[b])
             for s in side:
@@ -380,7 +381,7 @@ def run_gpu(args, ws, rank, local):
         e2e_ms = e2e_run(ne) / ne
         # the public call renders in screen-tile pixel order; the device-resident
         # steps above use row order, which sums a pixel's rows in another order
-        np.testing.assert_allclose(houts[(ne - 1) % 2][:64].numpy(), out[:64].cpu().numpy(),
+        np.testing.assert_allclose(houts[(ne - 1) % NB][:64].numpy(), out[:64].cpu().numpy(),
                                    rtol=1e-5, atol=1e-7)
     except Exception as exc:  # noqa: BLE001
         print(f"# e2e failed: {exc}", file=sys.stderr)

@@ -107,3 +107,40 @@ def test_blend_rejects_bad_arguments_before_launch(lib):
 def test_render_host_sizes(lib):
     nin, nout = q.qr_render_host_bytes(100, 32, 16, 8, 16, q.QR_F32)
     assert nin >= 100 * 11 * 4 + 100 * 16 * 4 and nout >= 32 * 16 * (8 * 8 + 1 + 16 * 4)
+
+
+def test_cosine_backward_rejects_bad_arguments_before_launch(lib):
+    """qr_cosine_backward checks its pointers, alignment and workspace size on
+    the host, and its workspace is the backward's plus one float per pixel."""
+    L = q.load()
+    P = ctypes.c_void_p
+    rc, f = _frame(n=1000, K=8, cap=4096)
+    assert rc == q.QR_OK
+    fp = ctypes.byref(f)
+    C = 64
+    wb = L.qr_backward_workspace_bytes(fp, C)
+    wc = L.qr_cosine_backward_workspace_bytes(fp, C)
+    pixels = f.camera.width * f.camera.height
+    assert wb > 0 and wc >= wb + 4 * pixels and wc - wb < 4 * pixels + 256
+    assert L.qr_cosine_backward_workspace_bytes(fp, 6) == 0     # C not a multiple of 4
+    good = P(1 << 20)
+    launches = L.qr_launch_count()
+
+    def call(**kw):
+        a = dict(feat=good, scale=None, dt=q.QR_F32, C=C, ids=good, w=good, cnt=good, F=good,
+                 t=good, mask=good, loss=good, gmap=good, gf=good, ga=None, gc=None, ws=good,
+                 wsb=wc)
+        a.update(kw)
+        return L.qr_cosine_backward(fp, a["feat"], a["scale"], a["dt"], a["C"], a["ids"], a["w"],
+                                    a["cnt"], a["F"], a["t"], a["mask"], a["loss"], a["gmap"],
+                                    a["gf"], a["ga"], a["gc"], a["ws"], a["wsb"], None)
+    assert call(F=None) == q.QR_ERR_INVALID_ARG
+    assert call(mask=None) == q.QR_ERR_INVALID_ARG
+    assert call(loss=None) == q.QR_ERR_INVALID_ARG
+    assert call(gmap=None) == q.QR_ERR_INVALID_ARG
+    assert call(t=P((1 << 20) + 4)) == q.QR_ERR_ALIGNMENT
+    assert call(gmap=P((1 << 20) + 8)) == q.QR_ERR_ALIGNMENT
+    assert call(ws=P((1 << 20) + 16)) == q.QR_ERR_ALIGNMENT
+    assert call(wsb=wc - 1) == q.QR_ERR_INVALID_ARG
+    assert call(dt=q.QR_FP8E4M3) == q.QR_ERR_INVALID_ARG             # FP8 without scales
+    assert L.qr_launch_count() == launches

@@ -283,7 +283,11 @@ qr_status qr_render_batch(const void *ws, int32_t n_views, uint32_t total_tiles,
  * selected), grad_opacity [n] and grad_conic [n][3] (both nullable).  The sum
  * over pixels is deterministic: per-tile partials reduced in a fixed order, no
  * floating-point atomics.  ws: qr_backward_workspace_bytes(frame, C) bytes,
- * 256-byte aligned (about max_isect * C * 4 bytes of partial rows). */
+ * 256-byte aligned (about max_isect * C * 4 bytes of partial rows).  The
+ * outputs are cleared on a library-owned stream of the current device that is
+ * forked from `stream` (event record, wait) and joined back to it within the
+ * call, so the call stays ordered on `stream` and can be captured in a CUDA
+ * graph. */
 size_t qr_backward_workspace_bytes(const qr_frame *frame, int32_t C);
 qr_status qr_backward(const qr_frame *frame, const void *feat, const float *feat_scale,
                       qr_dtype dtype, int32_t C, const int32_t *ids, const float *weights,

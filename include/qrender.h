@@ -303,7 +303,7 @@ qr_status qr_backward(const qr_frame *frame, const void *feat, const float *feat
  * grad [P][C] receives dL/dF (zero on pixels without quantile Gaussians);
  * scratch [P] floats (overwritten).  Deterministic reduction: the covered
  * pixels are counted with integer atomics and the per-pixel terms are summed
- * over fixed ranges whose sums are added in range order. */
+ * over fixed ranges whose sums are added in a fixed order. */
 qr_status qr_cosine_loss(const float *feature_map, const float *target, const uint8_t *counts,
                          int64_t P, int32_t C, float *loss_out, float *grad, float *scratch,
                          qr_stream stream);

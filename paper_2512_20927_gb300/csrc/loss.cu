@@ -5,7 +5,7 @@
 // first (integer atomics, so the count does not depend on their order), one
 // pass writes every pixel's term and its gradient row already scaled by 1/n,
 // and the terms are summed over fixed contiguous ranges, one per CTA, whose
-// sums the last CTA to finish adds in range order.  out[0] and out[1] hold
+// sums the last CTA to finish adds in a fixed order.  out[0] and out[1] hold
 // the ticket and the count as integers until that CTA writes (L, 1/n).
 #include "qr_internal.cuh"
 
@@ -125,7 +125,8 @@ __device__ __forceinline__ void two_sum_acc(float &s, float &c, float x) {
 // combined in double).  With one CTA it writes L directly; otherwise it
 // stores its sum, as the two 32-bit halves of a double, over the first two
 // terms of its range (every range holds at least 8192), which no other CTA
-// reads, and the last CTA to take a ticket adds the sums in range order.
+// reads, and the last CTA to take a ticket adds the sums in a fixed order
+// (lane l of its first warp the sums l, l + 32, ..., then a butterfly).
 __global__ void __launch_bounds__(1024)
 cos_final(float *__restrict__ term, int64_t P, int64_t range, float *__restrict__ out) {
     __shared__ double s_sum[32];
@@ -170,13 +171,17 @@ cos_final(float *__restrict__ term, int64_t P, int64_t range, float *__restrict_
         s_ticket = atomicAdd(reinterpret_cast<unsigned int *>(out), 1u);
     }
     __syncthreads();
-    if (s_ticket != gridDim.x - 1 || threadIdx.x != 0) return;
+    if (s_ticket != gridDim.x - 1 || threadIdx.x >= 32) return;
     __threadfence();
+    // the last CTA's first warp: lane l adds the range sums l, l + 32, ... in
+    // order, then the lanes' sums meet in a fixed butterfly
     double total = 0.0;
-    for (unsigned b = 0; b < gridDim.x; ++b) {
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += 32) {
         const volatile unsigned *slot = reinterpret_cast<const volatile unsigned *>(term + int64_t(b) * range);
         total += __hiloint2double(int(slot[1]), int(slot[0]));
     }
+    for (int o = 16; o > 0; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
+    if (threadIdx.x != 0) return;
     const unsigned nn = *reinterpret_cast<const volatile unsigned int *>(out + 1);
     const double n = nn > 0 ? double(nn) : 1.0;
     out[0] = float(total / n);

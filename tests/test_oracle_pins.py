@@ -472,3 +472,52 @@ def test_fp8_rows_round_trip_error_bound():
     # normal range: relative 2^-4; subnormal range: absolute 2^-10 * scale
     bound = np.maximum(np.abs(f) * 2.0 ** -4, 2.0 ** -10 * scale[:, None]) * 1.0001
     assert (err <= bound).all()
+
+
+def test_cosine_loss_through_the_render_matches_finite_differences():
+    """The composition the fused loss + backward computes: the cosine loss of
+    the rendered map, differentiated through Algorithm 1 into the features and
+    the opacities, against central differences of the whole FP64 pipeline."""
+    rng = np.random.default_rng(12)
+    gs = scenes.room_gaussians(rng, 20000)
+    cam = scenes.room_camera(24, 24)
+    pr_all = oracle.project(gs, cam.as_array())
+    near = np.nonzero(pr_all.valid & (np.abs(pr_all.mean2d[:, 0] - 12) < 16) &
+                      (np.abs(pr_all.mean2d[:, 1] - 12) < 16))[0][:150]
+    sub = scenes.Gaussians(gs.mean[near], gs.log_scale[near], gs.quat[near], gs.opacity[near])
+    pr = oracle.project(sub, cam.as_array())
+    C, K = 5, 4
+    f = rng.normal(size=(len(near), C))
+    pix = oracle.all_pixels(24, 24)
+    tgt = rng.normal(size=(len(pix), C))
+
+    def loss(p, feat):
+        r = oracle.render(p, feat, K, pix, want_dense=False)
+        L, gmap = oracle.cosine_loss(r.out_q, tgt, r.cnt > 0)
+        return L, gmap, r
+
+    L0, gmap, r0 = loss(pr, f)
+    gf, ga, _ = oracle.backward(pr, f, K, pix, gmap)
+    for i in rng.choice(len(near), 8, replace=False):
+        for c in (0, 3):
+            fp, fm = f.copy(), f.copy()
+            fp[i, c] += 1e-5
+            fm[i, c] -= 1e-5
+            fd = (loss(pr, fp)[0] - loss(pr, fm)[0]) / 2e-5
+            assert abs(gf[i, c] - fd) <= 1e-6 * max(1.0, abs(fd)), (i, c, gf[i, c], fd)
+    checked = 0
+    for i in np.argsort(-np.abs(ga))[:12]:
+        h = 1e-7 * abs(pr.alpha[i])
+        vals, same = [], True
+        for s in (+1, -1):
+            p2 = oracle.Projected(pr.mean2d, pr.conic, pr.cov2d, pr.depth, pr.alpha.copy(), pr.valid)
+            p2.alpha[i] += s * h
+            L, _, r = loss(p2, f)
+            vals.append(L)
+            same &= np.array_equal(r.ids, r0.ids)
+        if not same:
+            continue  # the perturbation moved a selection boundary
+        fd = (vals[0] - vals[1]) / (2 * h)
+        assert abs(ga[i] - fd) <= 1e-4 * max(abs(fd), 1e-3 * np.abs(ga).max()), (i, ga[i], fd)
+        checked += 1
+    assert checked >= 6

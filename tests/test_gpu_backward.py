@@ -203,9 +203,10 @@ def test_differentiation_config_sampled_pixels():
         _compare(name + " fused", a2.cpu().numpy(), r, tol)
 
 
-@pytest.mark.parametrize("kind,C", [("f32", 64),     # 16 float4 per row: the unfused route
-                                    ("f32", 128), ("bf16", 512), ("fp8", 512)])
-def test_cosine_backward_matches_separate_calls(kind, C):
+@pytest.mark.parametrize("kind,C,K", [("f32", 64, 8),     # 16 float4 per row: the unfused route
+                                      ("f32", 128, 8), ("bf16", 512, 8), ("fp8", 512, 8),
+                                      ("bf16", 512, 16)])  # 64-bit tile keys, staged without TMA
+def test_cosine_backward_matches_separate_calls(kind, C, K):
     """qr_cosine_backward = qr_cosine_loss then qr_backward, up to summation order."""
     import torch
     from paper_2512_20927_gb300 import qrender as q
@@ -218,7 +219,7 @@ def test_cosine_backward_matches_separate_calls(kind, C):
     elif kind == "fp8":
         table = q.qr_quantize_fp8(fdev)
     feat_t, scale_t = table if isinstance(table, tuple) else (table, None)
-    res = q.render_frame(q.gaussians_to_device(g), table, cam, K=8)
+    res = q.render_frame(q.gaussians_to_device(g), table, cam, K=K)
     rng = np.random.default_rng(3)
     tgt = torch.from_numpy(rng.normal(size=(cam.width * cam.height, C)).astype(np.float32)).cuda()
     loss, gmap = q.qr_cosine_loss(res["out"], tgt, res["counts"])

@@ -73,7 +73,9 @@ def _declare(L):
                             + [_P] * 11 + [_I, _P, _P])
     L.or_render.restype = _I
     L.or_backward.argtypes = [_I64, _P, _P, _P, _P, _P, _P, _I, _I, _D, _D, _I64, _P, _P,
-                              _P, _P, _P]
+                              _P, _P, _P, _P, _P, _P]
+    L.or_classify_candidates.argtypes = [_I64, _P, _P, _P, _P, _I, _D, _D, _D, _D, _P, _P]
+    L.or_classify_candidates.restype = _I
     L.or_backward.restype = _I
     L.or_qrender_list.argtypes = [_I64, _P, _I, _P, _P, _P, _P]
     L.or_qrender_list.restype = _I
@@ -238,8 +240,15 @@ def render(proj: Projected, feat, K: int, pixels, T_min: float = 1e-4,
 
 
 def backward(proj: Projected, feat, K: int, pixels, grad_out,
-             alpha_min: float = ALPHA_MIN, alpha_max: float = ALPHA_MAX):
-    """Gradients of Algorithm 1 w.r.t. features, opacity and conic (selection held fixed)."""
+             alpha_min: float = ALPHA_MIN, alpha_max: float = ALPHA_MAX,
+             with_scales: bool = False):
+    """Gradients of Algorithm 1 w.r.t. features, opacity and conic (selection held fixed).
+
+    Returns (grad_feat [n,C], grad_alpha [n], grad_conic [n,3]); with
+    ``with_scales`` also (scale_feat [n], scale_alpha [n], scale_conic [n,3]):
+    per Gaussian, the sum over pixels of the magnitudes of the terms its
+    gradient adds up (|w| max|g| for a feature row), the yardstick of the
+    rounding error of that sum."""
     n = proj.mean2d.shape[0]
     f = _c(feat, np.float64)
     C = f.shape[1]
@@ -248,12 +257,41 @@ def backward(proj: Projected, feat, K: int, pixels, grad_out,
     gf = np.zeros((n, C))
     ga = np.zeros(n)
     gc = np.zeros((n, 3))
+    sf = np.zeros(n) if with_scales else None
+    sa = np.zeros(n) if with_scales else None
+    sc = np.zeros((n, 3)) if with_scales else None
     rc = lib().or_backward(n, _ptr(proj.mean2d), _ptr(proj.conic), _ptr(proj.depth),
                            _ptr(proj.alpha), _ptr(proj.valid), _ptr(f), C, K, alpha_min,
                            alpha_max, pix.shape[0], _ptr(pix), _ptr(g), _ptr(gf), _ptr(ga),
-                           _ptr(gc))
+                           _ptr(gc), _ptr(sf), _ptr(sa), _ptr(sc))
     assert rc == 0, rc
+    if with_scales:
+        return gf, ga, gc, sf, sa, sc
     return gf, ga, gc
+
+
+def classify_candidates(depth, ids, g, qabs, K: int, T_min: float = 0.0,
+                        alpha_min: float = ALPHA_MIN, alpha_max: float = ALPHA_MAX,
+                        tie_eps: float = DEFAULT_TIE_EPS):
+    """Near-tie flags of one pixel given its candidates (test hook of the classifier).
+
+    depth, ids, g (= alpha * G, unclamped) and qabs (the conditioning
+    magnitude of q) describe the Gaussians evaluated at the pixel, in any
+    order.  Returns (flags, entries Algorithm 1 visited, entries the dense
+    walk blended); flag bits as in ``compare``: 1 / 2 / 4 for Algorithm 1's
+    boundary, alpha_min border and equal-depth checks, 8 / 16 / 64 / 128 for
+    the dense walk's T_min, boundary, border and equal-depth checks."""
+    d = _c(depth, np.float64)
+    i = _c(ids, np.int64)
+    gg = _c(g, np.float64)
+    qa = _c(qabs, np.float64)
+    npro = np.zeros(1, np.int64)
+    nused = np.zeros(1, np.int64)
+    flags = lib().or_classify_candidates(d.shape[0], _ptr(d), _ptr(i), _ptr(gg), _ptr(qa), K,
+                                         alpha_min, alpha_max, T_min, tie_eps, _ptr(npro),
+                                         _ptr(nused))
+    assert flags >= 0, flags
+    return int(flags), int(npro[0]), int(nused[0])
 
 
 # --------------------------------------------------------------------------

@@ -273,10 +273,56 @@ static int grow(void **p, int64_t *cap, int64_t need, size_t elem)
     return 0;
 }
 
+/*
+ * Relative FP32 error bound of alpha * G at one (pixel, Gaussian) pair that the
+ * near-tie classifier allows: tie_eps (1 + qabs) + 4u, with qabs the
+ * conditioning magnitude of q (see classify_ties).
+ */
+static double alpha_rel_err(double tie_eps, double qabs)
+{
+    return tie_eps * (1.0 + qabs) + 4.0 * ldexp(1.0, -24);
+}
+
+/* Add one candidate (a Gaussian evaluated at the pixel) to the pixel's list
+ * state: it is a member of I(p) when alpha' = min(alpha_max, g) >= alpha_min;
+ * its depth is also recorded as a border depth when g lies within the FP32
+ * error of alpha_min (for the tie check).  Returns 0 on success. */
+static int add_candidate(const render_job_t *J, scratch_t *S, double depth, int64_t id, double g,
+                         double G, double dx, double dy, double qabs)
+{
+    double rel = alpha_rel_err(J->tie_eps, qabs);
+    /* alpha*G within the FP32 error of alpha_min: |ln(g / alpha_min)| <= 4 rel */
+    if (J->tie && g > 0.0 && fabs(log(g / J->alpha_min)) <= 4.0 * rel) {
+        if (grow((void **)&S->border, &S->bcap, S->blen + 1, sizeof(double))) return -1;
+        S->border[S->blen++] = depth;
+    }
+    double a = g < J->alpha_max ? g : J->alpha_max;   /* alpha' = min(alpha_max, alpha G) */
+    if (a < J->alpha_min) return 0;
+    if (grow((void **)&S->m, &S->cap, S->len + 1, sizeof(member_t))) return -1;
+    member_t *mm = &S->m[S->len++];
+    mm->depth = depth; mm->id = id; mm->g = g; mm->G = G;
+    mm->a = a;
+    mm->dx = dx; mm->dy = dy; mm->qabs = qabs;
+    return 0;
+}
+
+/* Order the members by (depth, id) (Sec. 3, the ordered sequence) and lay out
+ * their alpha' values front to back.  Returns 0 on success. */
+static int finish_list(scratch_t *S)
+{
+    qsort(S->m, (size_t)S->len, sizeof(member_t), member_cmp);
+    if (grow((void **)&S->a, &S->acap, S->len + 1, sizeof(double))) return -1;
+    S->w = (double *)realloc(S->w, (size_t)S->acap * sizeof(double));
+    S->wd = (double *)realloc(S->wd, (size_t)S->acap * sizeof(double));
+    S->sel = (int32_t *)realloc(S->sel, (size_t)S->acap * sizeof(int32_t));
+    if (!S->w || !S->wd || !S->sel) return -1;
+    for (int64_t j = 0; j < S->len; ++j) S->a[j] = S->m[j].a;
+    return 0;
+}
+
 /* Build the depth-ordered list I(p) of one pixel.  Returns 0 on success. */
 static int build_list(const render_job_t *J, scratch_t *S, int px, int py)
 {
-    const double u = ldexp(1.0, -24);
     double ux = px + 0.5, uy = py + 0.5;
     S->len = 0; S->blen = 0;
     for (int64_t i = 0; i < J->n; ++i) {
@@ -290,28 +336,9 @@ static int build_list(const render_job_t *J, scratch_t *S, int px, int py)
          * conic's principal axes: |d| sqrt(lambda_max(A)) sqrt(q) + q */
         double lmax = 0.5 * (A00 + A11) + sqrt(0.25 * (A00 - A11) * (A00 - A11) + A01 * A01);
         double qabs = sqrt(dx * dx + dy * dy) * sqrt(lmax > 0.0 ? lmax : 0.0) * sqrt(q > 0.0 ? q : 0.0) + fabs(q);
-        double rel = J->tie_eps * (1.0 + qabs) + 4.0 * u;
-        /* alpha*G within the FP32 error of alpha_min: |ln(g / alpha_min)| <= 4 rel */
-        if (J->tie && g > 0.0 && fabs(log(g / J->alpha_min)) <= 4.0 * rel) {
-            if (grow((void **)&S->border, &S->bcap, S->blen + 1, sizeof(double))) return -1;
-            S->border[S->blen++] = J->depth[i];
-        }
-        double a = g < J->alpha_max ? g : J->alpha_max;   /* alpha' = min(alpha_max, alpha G) */
-        if (a < J->alpha_min) continue;
-        if (grow((void **)&S->m, &S->cap, S->len + 1, sizeof(member_t))) return -1;
-        member_t *mm = &S->m[S->len++];
-        mm->depth = J->depth[i]; mm->id = i; mm->g = g; mm->G = G;
-        mm->a = a;
-        mm->dx = dx; mm->dy = dy; mm->qabs = qabs;
+        if (add_candidate(J, S, J->depth[i], i, g, G, dx, dy, qabs)) return -1;
     }
-    qsort(S->m, (size_t)S->len, sizeof(member_t), member_cmp);
-    if (grow((void **)&S->a, &S->acap, S->len + 1, sizeof(double))) return -1;
-    S->w = (double *)realloc(S->w, (size_t)S->acap * sizeof(double));
-    S->wd = (double *)realloc(S->wd, (size_t)S->acap * sizeof(double));
-    S->sel = (int32_t *)realloc(S->sel, (size_t)S->acap * sizeof(int32_t));
-    if (!S->w || !S->wd || !S->sel) return -1;
-    for (int64_t j = 0; j < S->len; ++j) S->a[j] = S->m[j].a;
-    return 0;
+    return finish_list(S);
 }
 
 /*
@@ -326,8 +353,10 @@ static int build_list(const render_job_t *J, scratch_t *S, int px, int py)
  * Bits for Algorithm 1: 1 = a visited test transmittance within that error of
  * a segment boundary; 2 = a Gaussian up to the stopping point with alpha*G
  * within error of alpha_min; 4 = two visited list entries whose depths are
- * within FP32 resolution.  The same three checks up to the dense blend's
- * stopping point give 16, 64 and 128, and 8 marks its T_min decision.
+ * within FP32 resolution.  For the dense blend, up to its stopping point:
+ * 8 = a test transmittance within error of T_min, 64 = the alpha_min border,
+ * 128 = equal depths (16 is unused).  An alpha' clamped at alpha_max counts
+ * as exact only where alpha*G exceeds alpha_max by more than its error.
  */
 static int classify_ties(const render_job_t *J, const scratch_t *S, int64_t nproc_q,
                          int64_t nused_dense)
@@ -339,8 +368,11 @@ static int classify_ties(const render_job_t *J, const scratch_t *S, int64_t npro
     int64_t last_d = nused_dense < S->len ? nused_dense : S->len - 1;
     for (int64_t i = 0; i < S->len; ++i) {
         const member_t *m = &S->m[i];
-        double rel = J->tie_eps * (1.0 + m->qabs) + 4.0 * u;
-        double ea = (m->g >= J->alpha_max) ? 1e-6 : rel * m->a / (1.0 - m->a);
+        double rel = alpha_rel_err(J->tie_eps, m->qabs);
+        /* the clamp alpha' = alpha_max is exact only when alpha*G clears it by
+         * more than its error; within that error the FP32 clamp may fall
+         * either way and 1 - alpha' carries the error of an unclamped value */
+        double ea = (m->g * (1.0 - rel) >= J->alpha_max) ? 0.0 : rel * m->a / (1.0 - m->a);
         E += ea + 2.0 * u;
         double Tt = T * (1.0 - m->a);
         if (i <= last_q)
@@ -365,6 +397,47 @@ static int classify_ties(const render_job_t *J, const scratch_t *S, int64_t npro
         if (S->border[b] <= zq * (1.0 + 4.0 * u)) flags |= 2;
         if (S->border[b] <= zd * (1.0 + 4.0 * u)) flags |= 64;
     }
+    return flags;
+}
+
+/*
+ * The near-tie classification of one pixel from its candidates, for tests
+ * that pin the classifier on hand-built lists.  Candidate c is a Gaussian
+ * evaluated at the pixel: camera depth[c], index id[c], g[c] = alpha * G
+ * (unclamped) and the conditioning magnitude qabs[c] of its q.  The list I is
+ * built exactly as for a rendered pixel (membership, border depths, order),
+ * Algorithm 1 and the dense walk run on it, and the classifier's flags are
+ * returned; n_proc / n_used (nullable) receive the entries Algorithm 1
+ * visited and the entries the dense walk blended.  Returns -1 on bad
+ * arguments or memory exhaustion.
+ */
+int or_classify_candidates(int64_t n, const double *depth, const int64_t *id, const double *g,
+                           const double *qabs, int K, double alpha_min, double alpha_max,
+                           double T_min, double tie_eps, int64_t *n_proc, int64_t *n_used)
+{
+    if (n < 0 || K < 1 || !depth || !id || !g || !qabs) return -1;
+    render_job_t J;
+    memset(&J, 0, sizeof(J));
+    int32_t tie_dummy = 0;
+    J.K = K; J.alpha_min = alpha_min; J.alpha_max = alpha_max; J.T_min = T_min;
+    J.tie_eps = tie_eps; J.tie = &tie_dummy;
+    scratch_t S;
+    memset(&S, 0, sizeof(S));
+    int flags = -1;
+    for (int64_t c = 0; c < n; ++c)
+        if (add_candidate(&J, &S, depth[c], id[c], g[c], 1.0, 0.0, 0.0, qabs[c])) goto done;
+    if (finish_list(&S)) goto done;
+    {
+        double Tq = 1.0, Tf = 1.0;
+        int64_t nproc = 0;
+        or_qrender_list(S.len, S.a, K, S.sel, S.w, &Tq, &nproc);
+        int64_t nused = or_dense_list(S.len, S.a, T_min, S.wd, &Tf);
+        if (n_proc) *n_proc = nproc;
+        if (n_used) *n_used = nused;
+        flags = classify_ties(&J, &S, nproc, nused);
+    }
+done:
+    free(S.m); free(S.border); free(S.a); free(S.w); free(S.wd); free(S.sel);
     return flags;
 }
 
@@ -520,12 +593,18 @@ int or_render(int64_t n, const double *mean2d, const double *conic, const double
  * non-selected Gaussians receive zero gradient.  Accumulation is serial and
  * in pixel order.  grad_feat [n][C], grad_alpha [n], grad_conic [n][3] are
  * accumulated into (the caller zeroes them).
+ * The optional scale_feat [n], scale_alpha [n] and scale_conic [n][3]
+ * accumulate the magnitudes of the same per-pixel terms (|w_j| max_c |g_c|,
+ * |dL/dalpha| and |dL/dA| of each pixel): the size a Gaussian's gradient
+ * could reach without cancellation, against which a rounding error in its
+ * sum is measured.
  */
 int or_backward(int64_t n, const double *mean2d, const double *conic, const double *depth,
                 const double *alpha, const int32_t *valid, const double *feat, int C,
                 int K, double alpha_min, double alpha_max,
                 int64_t npix, const int32_t *pix, const double *grad_out,
-                double *grad_feat, double *grad_alpha, double *grad_conic)
+                double *grad_feat, double *grad_alpha, double *grad_conic,
+                double *scale_feat, double *scale_alpha, double *scale_conic)
 {
     if (n < 0 || npix < 0 || K < 1 || C < 1 || !feat || !grad_out) return OR_ERR_ARG;
     render_job_t J;
@@ -570,17 +649,28 @@ int or_backward(int64_t n, const double *mean2d, const double *conic, const doub
             double wj = sa[j] * sP[j] / D;
             double *gf = grad_feat + mm->id * C;
             for (int c = 0; c < C; ++c) gf[c] += wj * g[c];
+            if (scale_feat) {
+                double gmax = 0.0;
+                for (int c = 0; c < C; ++c) gmax = fabs(g[c]) > gmax ? fabs(g[c]) : gmax;
+                scale_feat[mm->id] += fabs(wj) * gmax;
+            }
             double tail = 0.0;
             for (int l = j + 1; l < m; ++l) tail += sa[l] * sP[l] * ss[l];
             double da = (sP[j] * ss[j] - tail / (1.0 - sa[j])) / D
                         - gF * sP[m] / ((1.0 - sa[j]) * D);
             if (mm->g < alpha_max) {
                 if (grad_alpha) grad_alpha[mm->id] += da * mm->G;
+                if (scale_alpha) scale_alpha[mm->id] += fabs(da * mm->G);
+                double h = -0.5 * sa[j] * da;
                 if (grad_conic) {
-                    double h = -0.5 * sa[j] * da;
                     grad_conic[3 * mm->id] += h * mm->dx * mm->dx;
                     grad_conic[3 * mm->id + 1] += h * 2.0 * mm->dx * mm->dy;
                     grad_conic[3 * mm->id + 2] += h * mm->dy * mm->dy;
+                }
+                if (scale_conic) {
+                    scale_conic[3 * mm->id] += fabs(h * mm->dx * mm->dx);
+                    scale_conic[3 * mm->id + 1] += fabs(h * 2.0 * mm->dx * mm->dy);
+                    scale_conic[3 * mm->id + 2] += fabs(h * mm->dy * mm->dy);
                 }
             }
         }

@@ -88,6 +88,7 @@ class ClockSampler:
         self.path = os.path.join("/tmp", f"qr_clocks_{os.getpid()}.csv")
 
     def __enter__(self):
+        self.fh = None
         try:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
@@ -111,10 +112,13 @@ class ClockSampler:
                 self.proc.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
+        if self.fh is not None:
             self.fh.close()
+            self.fh = None
 
     def summary(self):
-        if self.proc is None or not os.path.exists(self.path):
+        """Clock summary of the samples taken; removes the sample file."""
+        if not os.path.exists(self.path):
             return None
         rows = []
         with open(self.path) as fh:
@@ -122,6 +126,9 @@ class ClockSampler:
                 parts = [p.strip() for p in line.split(",")]
                 if len(parts) >= 9:
                     rows.append(parts)
+        os.remove(self.path)
+        if self.proc is None:
+            return None
         if not rows:
             return None
         sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]

@@ -299,7 +299,8 @@ qr_status qr_backward(const qr_frame *frame, const void *feat, const float *feat
  * Eq. 2 on CLIP targets, which are not available): L = mean over pixels with
  * counts > 0 of 1 - cos(F_p, t_p), cos = F.t / (max(|F|, 1e-8) max(|t|, 1e-8)).
  * feature_map, target [P][C]; loss_out [2] device floats receive (L, 1/n)
- * (they hold integer counters while the call runs on the stream);
+ * (they hold integer counters while the call runs on the stream; (0, 1) for
+ * P = 0);
  * grad [P][C] receives dL/dF (zero on pixels without quantile Gaussians);
  * scratch [P] floats (overwritten).  Deterministic reduction: the covered
  * pixels are counted with integer atomics and the per-pixel terms are summed
@@ -377,10 +378,12 @@ qr_status qr_quantize_fp8(const float *in, int64_t rows, int32_t C, uint8_t *cod
  * by qr_frame_status on *frame_out, which describes the static workspace
  * until the next call; frame_out may be NULL).
  * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  All calls share the one array: calls that
- * overlap on the GPU race.  A call allocates nothing: no cudaMalloc, no
- * cudaFree, no allocating library routine. */
+ * (cudaGetSymbolAddress, with that device current) and keeps it for the rest
+ * of the process; make that first call before any stream capture, and do not
+ * reset the device (cudaDeviceReset) after it, which would leave the kept
+ * address stale.  All calls share the one array: calls that overlap on the
+ * GPU race.  A call allocates nothing: no cudaMalloc, no cudaFree, no
+ * allocating library routine. */
 qr_status qr_render_noalloc(const float *mean, const float *log_scale, const float *quat,
                             const float *opacity, int64_t n, const qr_camera *camera,
                             const qr_params *params, const void *feat, const float *feat_scale,

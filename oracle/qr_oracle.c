@@ -594,10 +594,12 @@ int or_render(int64_t n, const double *mean2d, const double *conic, const double
  * in pixel order.  grad_feat [n][C], grad_alpha [n], grad_conic [n][3] are
  * accumulated into (the caller zeroes them).
  * The optional scale_feat [n], scale_alpha [n] and scale_conic [n][3]
- * accumulate the magnitudes of the same per-pixel terms (|w_j| max_c |g_c|,
- * |dL/dalpha| and |dL/dA| of each pixel): the size a Gaussian's gradient
- * could reach without cancellation, against which a rounding error in its
- * sum is measured.
+ * accumulate, per Gaussian, the magnitudes of the parts its gradient is summed
+ * from: |w_j| max_c |g_c| for a feature row, and for dL/da_j the same formula
+ * with every part taken by magnitude (s_l -> sum_c |g_c f_lc|, g.F ->
+ * sum_c |g_c| sum_l w_l |f_lc|) -- the size the sum could reach without
+ * cancellation, against which the rounding error of a computed gradient is
+ * measured.
  */
 int or_backward(int64_t n, const double *mean2d, const double *conic, const double *depth,
                 const double *alpha, const int32_t *valid, const double *feat, int C,
@@ -615,13 +617,16 @@ int or_backward(int64_t n, const double *mean2d, const double *conic, const doub
     scratch_t S;
     memset(&S, 0, sizeof(S));
     int64_t *sid = NULL; double *sa = NULL, *sP = NULL, *ss = NULL, *F = NULL;
+    double *sabs = NULL, *Fabs = NULL;
     int rc = OR_OK;
     sid = (int64_t *)malloc(sizeof(int64_t) * (size_t)K);
     sa = (double *)malloc(sizeof(double) * (size_t)K);
     sP = (double *)malloc(sizeof(double) * (size_t)(K + 1));
     ss = (double *)malloc(sizeof(double) * (size_t)K);
+    sabs = (double *)malloc(sizeof(double) * (size_t)K);
     F = (double *)malloc(sizeof(double) * (size_t)C);
-    if (!sid || !sa || !sP || !ss || !F) { rc = OR_ERR_NOMEM; goto done; }
+    Fabs = (double *)malloc(sizeof(double) * (size_t)C);
+    if (!sid || !sa || !sP || !ss || !sabs || !F || !Fabs) { rc = OR_ERR_NOMEM; goto done; }
     for (int64_t p = 0; p < npix; ++p) {
         int px = pix[2 * p], py = pix[2 * p + 1];
         if (build_list(&J, &S, px, py)) { rc = OR_ERR_NOMEM; goto done; }
@@ -635,15 +640,21 @@ int or_backward(int64_t n, const double *mean2d, const double *conic, const doub
         for (j = 0; j < m; ++j) sP[j + 1] = sP[j] * (1.0 - sa[j]);
         double D = 1.0 - sP[m];
         const double *g = grad_out + p * C;
-        for (int c = 0; c < C; ++c) F[c] = 0.0;
+        for (int c = 0; c < C; ++c) { F[c] = 0.0; Fabs[c] = 0.0; }
         for (j = 0; j < m; ++j) {
             const double *f = feat + S.m[sid[j]].id * C;
-            double sj = 0.0;
-            for (int c = 0; c < C; ++c) { sj += g[c] * f[c]; F[c] += sa[j] * sP[j] * f[c] / D; }
+            double sj = 0.0, sjabs = 0.0;
+            for (int c = 0; c < C; ++c) {
+                sj += g[c] * f[c];
+                sjabs += fabs(g[c] * f[c]);
+                F[c] += sa[j] * sP[j] * f[c] / D;
+                Fabs[c] += sa[j] * sP[j] * fabs(f[c]) / D;
+            }
             ss[j] = sj;
+            sabs[j] = sjabs;
         }
-        double gF = 0.0;
-        for (int c = 0; c < C; ++c) gF += g[c] * F[c];
+        double gF = 0.0, gFabs = 0.0;
+        for (int c = 0; c < C; ++c) { gF += g[c] * F[c]; gFabs += fabs(g[c]) * Fabs[c]; }
         for (j = 0; j < m; ++j) {
             const member_t *mm = &S.m[sid[j]];
             double wj = sa[j] * sP[j] / D;
@@ -654,30 +665,35 @@ int or_backward(int64_t n, const double *mean2d, const double *conic, const doub
                 for (int c = 0; c < C; ++c) gmax = fabs(g[c]) > gmax ? fabs(g[c]) : gmax;
                 scale_feat[mm->id] += fabs(wj) * gmax;
             }
-            double tail = 0.0;
-            for (int l = j + 1; l < m; ++l) tail += sa[l] * sP[l] * ss[l];
+            double tail = 0.0, tailabs = 0.0;
+            for (int l = j + 1; l < m; ++l) {
+                tail += sa[l] * sP[l] * ss[l];
+                tailabs += sa[l] * sP[l] * sabs[l];
+            }
             double da = (sP[j] * ss[j] - tail / (1.0 - sa[j])) / D
                         - gF * sP[m] / ((1.0 - sa[j]) * D);
+            double damag = (sP[j] * sabs[j] + tailabs / (1.0 - sa[j])) / D
+                           + gFabs * sP[m] / ((1.0 - sa[j]) * D);
             if (mm->g < alpha_max) {
                 if (grad_alpha) grad_alpha[mm->id] += da * mm->G;
-                if (scale_alpha) scale_alpha[mm->id] += fabs(da * mm->G);
-                double h = -0.5 * sa[j] * da;
+                if (scale_alpha) scale_alpha[mm->id] += damag * mm->G;
+                double h = -0.5 * sa[j] * da, hmag = 0.5 * sa[j] * damag;
                 if (grad_conic) {
                     grad_conic[3 * mm->id] += h * mm->dx * mm->dx;
                     grad_conic[3 * mm->id + 1] += h * 2.0 * mm->dx * mm->dy;
                     grad_conic[3 * mm->id + 2] += h * mm->dy * mm->dy;
                 }
                 if (scale_conic) {
-                    scale_conic[3 * mm->id] += fabs(h * mm->dx * mm->dx);
-                    scale_conic[3 * mm->id + 1] += fabs(h * 2.0 * mm->dx * mm->dy);
-                    scale_conic[3 * mm->id + 2] += fabs(h * mm->dy * mm->dy);
+                    scale_conic[3 * mm->id] += hmag * mm->dx * mm->dx;
+                    scale_conic[3 * mm->id + 1] += hmag * 2.0 * fabs(mm->dx * mm->dy);
+                    scale_conic[3 * mm->id + 2] += hmag * mm->dy * mm->dy;
                 }
             }
         }
     }
 done:
     free(S.m); free(S.border); free(S.a); free(S.w); free(S.wd); free(S.sel);
-    free(sid); free(sa); free(sP); free(ss); free(F);
+    free(sid); free(sa); free(sP); free(ss); free(sabs); free(F); free(Fabs);
     return rc;
 }
 

@@ -81,6 +81,9 @@ size_t layout(int64_t n, int W, int H, const qr_params *p, int64_t cap, size_t *
 
 qr_status from_cuda(cudaError_t e) { return e == cudaSuccess ? QR_OK : QR_ERR_CUDA; }
 
+// (L, 1/n) of a loss over no pixels: L = 0, n floored at 1.
+const float kEmptyLoss[2] = {0.0f, 1.0f};
+
 bool frame_ok(const qr_frame *f) {
     return f && f->ws && params_ok(&f->params) && dims_ok(f->n, f->camera.width, f->camera.height, f->max_isect);
 }
@@ -362,8 +365,10 @@ qr_status qr_cosine_backward(const qr_frame *frame, const void *feat, const floa
         return QR_ERR_ALIGNMENT;
     if (ws_bytes < backward_cos_workspace_bytes(*frame, C)) return QR_ERR_INVALID_ARG;
     const int64_t P = num_pixels(*frame);
-    if (P == 0) return QR_OK;
     const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (P == 0)
+        return from_cuda(cudaMemcpyAsync(loss_out, kEmptyLoss, sizeof(kEmptyLoss),
+                                         cudaMemcpyHostToDevice, s));
     CosLossArgs loss;
     loss.F = feature_map;
     loss.tgt = target;
@@ -383,7 +388,10 @@ qr_status qr_cosine_loss(const float *feature_map, const float *target, const ui
                          qr_stream stream) {
     if (!feature_map || !target || !counts || !loss_out || !grad || !scratch || P < 0 || C < 1)
         return QR_ERR_INVALID_ARG;
-    if (P == 0) return QR_OK;
+    if (P == 0)
+        return from_cuda(cudaMemcpyAsync(loss_out, kEmptyLoss, sizeof(kEmptyLoss),
+                                         cudaMemcpyHostToDevice,
+                                         reinterpret_cast<cudaStream_t>(stream)));
     return from_cuda(launch_cosine_loss(feature_map, target, counts, P, C, scratch, loss_out, grad,
                                         reinterpret_cast<cudaStream_t>(stream)));
 }

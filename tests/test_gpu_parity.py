@@ -169,7 +169,10 @@ def test_large_tile_lists_use_the_merge_path():
         np.testing.assert_array_equal(order, np.arange(b - a))
     pix = H.sample_pixels(48, 48, 200, seed=3)
     pr, pix, ref = H.run_oracle(g, f, cam, 8, pixels=pix)
-    H.check_frame(gpu, ref, pix, cam.width, f, FEAT_TOL, DENSE_TOL, max_tie_frac=0.6,
+    # 30,000 Gaussians within 1 m of depth: the FP32 depth keys of neighbours
+    # in a pixel's list collide often, and the oracle flags 90 of these 204
+    # pixels (44 %; deterministic for this seed)
+    H.check_frame(gpu, ref, pix, cam.width, f, FEAT_TOL, DENSE_TOL, max_tie_frac=0.46,
                   label="big tiles")
 
 
@@ -213,7 +216,8 @@ def test_tile_sort_size_classes(n, lo, hi):
         np.testing.assert_array_equal(order, np.arange(b - a))
     pix = H.sample_pixels(48, 48, 120, seed=5)
     pr, pix, ref = H.run_oracle(g, f, cam, 8, pixels=pix)
-    H.check_frame(gpu, ref, pix, cam.width, f, FEAT_TOL, DENSE_TOL, max_tie_frac=0.6,
+    # the oracle flags at most 6 of these 124 pixels (4.8 %, n = 1800)
+    H.check_frame(gpu, ref, pix, cam.width, f, FEAT_TOL, DENSE_TOL, max_tie_frac=0.05,
                   label=f"slab {n}")
 
 

@@ -388,6 +388,36 @@ def test_backward_matches_finite_differences():
     assert checked >= 40
 
 
+def test_backward_scales_bound_the_gradients():
+    """The per-Gaussian yardsticks of the backward (sums of the magnitudes of
+    each gradient's parts) bound the gradients, and equal them where nothing
+    can cancel: with non-negative features and upstream gradient, the feature
+    yardstick is sum_p |w| max|g| >= |dL/df| and for a single selected
+    Gaussian per pixel the opacity yardstick equals |dL/dalpha| summed over
+    pixels of one sign."""
+    rng = np.random.default_rng(12)
+    g, f = scenes.tiny_scene(seed=4, n=300, channels=8)
+    cam = scenes.tiny_camera(48, 48)
+    pr = oracle.project(g, cam.as_array())
+    pix = oracle.all_pixels(48, 48)
+    gout = rng.normal(size=(len(pix), 8))
+    gf, ga, gc, sf, sa, sc = oracle.backward(pr, f, 8, pix, gout, with_scales=True)
+    assert (np.abs(gf).max(axis=1) <= sf * (1 + 1e-12) + 1e-300).all()
+    assert (np.abs(ga) <= sa * (1 + 1e-12) + 1e-300).all()
+    assert (np.abs(gc) <= sc * (1 + 1e-12) + 1e-300).all()
+    assert ((sf > 0) == (np.abs(gf).max(axis=1) > 0)).all()
+    # no cancellation: positive features and gradients, feature yardstick tight
+    fpos, gpos = np.abs(f), np.ones_like(gout)
+    gf, ga, gc, sf, sa, sc = oracle.backward(pr, fpos, 8, pix, gpos, with_scales=True)
+    np.testing.assert_allclose(np.abs(gf).max(axis=1), sf, rtol=1e-12, atol=1e-300)
+    # K = 1 keeps one Gaussian per pixel with normalised weight 1: F = f_j and
+    # dL/da_j = 0 exactly (the normalisation removes a_j), while the yardstick
+    # of its cancelling parts stays positive
+    gf, ga, gc, sf, sa, sc = oracle.backward(pr, fpos, 1, pix, gpos, with_scales=True)
+    sel = sf > 0
+    assert (np.abs(ga[sel]) <= 1e-12 * sa[sel]).all() and (sa[sel] > 0).all()
+
+
 def test_cosine_loss_gradient_matches_finite_differences():
     rng = np.random.default_rng(10)
     F = rng.normal(size=(20, 7))

@@ -76,6 +76,16 @@ def _declare(L):
                               _P, _P, _P, _P, _P, _P]
     L.or_classify_candidates.argtypes = [_I64, _P, _P, _P, _P, _I, _D, _D, _D, _D, _P, _P]
     L.or_classify_candidates.restype = _I
+    L.or_topk_list.argtypes = [_I64, _P, _I, _D, _P, _P, _P]
+    L.or_topk_list.restype = _I
+    L.or_stratified_list.argtypes = [_I64, _P, _I, _D, _P, _P, _P, _P, _P, _P]
+    L.or_stratified_list.restype = _I
+    L.or_render_rule.argtypes = ([_I64, _P, _P, _P, _P, _P, _P, _I, _I, _I, _D, _D, _D, _D, _I64,
+                                  _P, _I] + [_P] * 9)
+    L.or_render_rule.restype = _I
+    L.or_classify_rule_candidates.argtypes = [_I64, _P, _P, _P, _P, _I, _I, _D, _D, _D, _D, _P,
+                                              _P]
+    L.or_classify_rule_candidates.restype = _I
     L.or_backward.restype = _I
     L.or_qrender_list.argtypes = [_I64, _P, _I, _P, _P, _P, _P]
     L.or_qrender_list.restype = _I
@@ -174,6 +184,102 @@ def dense_list(a, T_min: float = 0.0):
     tf = np.zeros(1)
     used = lib().or_dense_list(a.shape[0], _ptr(a), T_min, _ptr(w), _ptr(tf))
     return w, float(tf[0]), int(used)
+
+
+RULE_TOPK = 1
+RULE_STRATIFIED = 2
+
+
+def topk_list(a, K: int, T_min: float = 0.0):
+    """Top-K on one list (Sec. 4.2's comparison renderer): the K largest Eq. 1
+    weights of the dense walk.  Returns (kept mask, their Eq. 1 weights,
+    entries blended by the walk)."""
+    a = _c(a, np.float64)
+    n = a.shape[0]
+    sel = np.zeros(n, np.int32)
+    w = np.zeros(n)
+    nused = np.zeros(1, np.int64)
+    m = lib().or_topk_list(n, _ptr(a), K, T_min, _ptr(sel), _ptr(w), _ptr(nused))
+    assert m >= 0
+    return sel.astype(bool), w, int(nused[0])
+
+
+def stratified_list(a, K: int, T_min: float = 0.0):
+    """Stratified-K on one list (App. E).  Returns (kept mask, unnormalised
+    weights, T^Q, entries visited by pass 2, boundaries tau [K], (mu, sigma, n))."""
+    a = _c(a, np.float64)
+    n = a.shape[0]
+    sel = np.zeros(n, np.int32)
+    w = np.zeros(n)
+    tq = np.zeros(1)
+    npro = np.zeros(1, np.int64)
+    tau = np.zeros(K)
+    st = np.zeros(3)
+    m = lib().or_stratified_list(n, _ptr(a), K, T_min, _ptr(sel), _ptr(w), _ptr(tq), _ptr(npro),
+                                 _ptr(tau), _ptr(st))
+    assert m >= 0
+    return sel.astype(bool), w, float(tq[0]), int(npro[0]), tau, (st[0], st[1], int(st[2]))
+
+
+def classify_rule_candidates(depth, ids, g, qabs, rule: int, K: int, T_min: float = 0.0,
+                             alpha_min: float = ALPHA_MIN, alpha_max: float = ALPHA_MAX,
+                             tie_eps: float = DEFAULT_TIE_EPS):
+    """Near-tie flags of one pixel under top-K / Stratified-K, from its
+    candidates (see classify_candidates).  Returns (flags, kept ids in depth
+    order, boundaries tau [K] (stratified))."""
+    d = _c(depth, np.float64)
+    i = _c(ids, np.int64)
+    gg = _c(g, np.float64)
+    qa = _c(qabs, np.float64)
+    kept = np.zeros(K, np.int64)
+    tau = np.zeros(K)
+    flags = lib().or_classify_rule_candidates(d.shape[0], _ptr(d), _ptr(i), _ptr(gg), _ptr(qa),
+                                              rule, K, alpha_min, alpha_max, T_min, tie_eps,
+                                              _ptr(kept), _ptr(tau))
+    assert flags >= 0, flags
+    return int(flags), kept[kept >= 0], tau
+
+
+@dataclass
+class RuleRendered:
+    out: np.ndarray | None
+    ids: np.ndarray
+    wq: np.ndarray
+    cnt: np.ndarray
+    n_members: np.ndarray
+    n_proc: np.ndarray
+    tie: np.ndarray
+    scale: np.ndarray | None
+    tau: np.ndarray | None
+
+
+def render_rule(proj: Projected, feat, rule: int, K: int, pixels, T_min: float = 1e-4,
+                alpha_min: float = ALPHA_MIN, alpha_max: float = ALPHA_MAX,
+                tie_eps: float = DEFAULT_TIE_EPS, threads: int | None = None) -> RuleRendered:
+    """Brute-force render of the listed pixels with the top-K (RULE_TOPK) or
+    Stratified-K (RULE_STRATIFIED) select rule in place of Algorithm 1, FP64."""
+    n = proj.mean2d.shape[0]
+    pix = _c(pixels, np.int32)
+    m = pix.shape[0]
+    f = None if feat is None else _c(feat, np.float64)
+    C = 0 if f is None else f.shape[1]
+    threads = threads or max(1, os.cpu_count() or 1)
+    out = np.zeros((m, C)) if f is not None else None
+    sc = np.zeros(m) if f is not None else None
+    ids = np.zeros((m, K), np.int32)
+    wq = np.zeros((m, K))
+    cnt = np.zeros(m, np.int32)
+    nmem = np.zeros(m, np.int32)
+    npro = np.zeros(m, np.int32)
+    tie = np.zeros(m, np.int32)
+    tau = np.zeros((m, K)) if rule == RULE_STRATIFIED else None
+    rc = lib().or_render_rule(n, _ptr(proj.mean2d), _ptr(proj.conic), _ptr(proj.depth),
+                              _ptr(proj.alpha), _ptr(proj.valid), _ptr(f), C, rule, K, alpha_min,
+                              alpha_max, T_min, tie_eps, m, _ptr(pix), threads, _ptr(out),
+                              _ptr(ids), _ptr(wq), _ptr(cnt), _ptr(nmem), _ptr(npro), _ptr(tie),
+                              _ptr(sc), _ptr(tau))
+    assert rc == 0, rc
+    return RuleRendered(out, ids, wq, cnt, nmem, npro, tie, sc, tau)
 
 
 # --------------------------------------------------------------------------

@@ -15,6 +15,7 @@ import numpy as np
 
 Q_TIE_BITS = 1 | 2 | 4
 DENSE_TIE_BITS = 8 | 16 | 64 | 128
+RULE_TIE_BITS = 1 | 2 | 4 | 8        # top-K and Stratified-K (or_render_rule)
 
 
 def blend(ids, weights, counts, feat) -> np.ndarray:

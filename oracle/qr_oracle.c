@@ -217,6 +217,142 @@ int64_t or_dense_list(int64_t n, const double *a, double T_min, double *w, doubl
 }
 
 /* ------------------------------------------------------------------------ */
+/* Top-K: the comparison renderer of Sec. 4.2 and Table 1 (complexity table). */
+/* ------------------------------------------------------------------------ */
+/*
+ * The paper's top-K renderer sorts the Gaussians of a ray by weight and keeps
+ * the K largest.  Reading: the weights are Eq. 1's w_i = T_i alpha'_i over the
+ * list I (the dense walk, with its T_min stop), equal weights keep the
+ * earlier entry, and the kept Gaussians are blended with their Eq. 1 weights
+ * normalised by their sum (as Algorithm 1 normalises by 1 - T^Q).
+ * Streaming selection along the walk: at most K kept entries; once K are
+ * kept, a strictly larger weight replaces the smallest kept one (the latest
+ * of equal ones).  sel[i] = 1 for the kept entries and w[i] their Eq. 1
+ * weights (0 elsewhere); *n_used receives the entries the walk blended.
+ * Returns the number kept, or -1 when out of memory.
+ */
+int or_topk_list(int64_t n, const double *a, int K, double T_min, int32_t *sel, double *w,
+                 int64_t *n_used)
+{
+    int64_t *kept = (int64_t *)malloc(sizeof(int64_t) * (size_t)(K > 0 ? K : 1));
+    if (!kept) return -1;
+    double T = 1.0;
+    int m = 0;
+    int64_t i;
+    for (i = 0; i < n; ++i) { sel[i] = 0; w[i] = 0.0; }
+    for (i = 0; i < n; ++i) {
+        double Ttest = T * (1.0 - a[i]);
+        if (T_min > 0.0 && Ttest < T_min) break;
+        w[i] = T * a[i];
+        if (m < K) {
+            kept[m++] = i;
+        } else {
+            int s = 0;
+            for (int j = 1; j < K; ++j)
+                if (w[kept[j]] < w[kept[s]] || (w[kept[j]] == w[kept[s]] && kept[j] > kept[s])) s = j;
+            if (w[i] > w[kept[s]]) kept[s] = i;
+        }
+        T = Ttest;
+    }
+    if (n_used) *n_used = i;
+    for (int j = 0; j < m; ++j) sel[kept[j]] = 1;
+    for (int64_t l = 0; l < n; ++l)
+        if (!sel[l]) w[l] = 0.0;
+    free(kept);
+    return m;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Stratified-K: the two-pass adaptive variant of App. E.                     */
+/* ------------------------------------------------------------------------ */
+/* Standard normal CDF, Phi(z) = erfc(-z / sqrt 2) / 2. */
+static double normal_cdf(double z) { return 0.5 * erfc(-z / sqrt(2.0)); }
+
+/* Phi^{-1}(p) for p in (0, 1) by bisection on Phi (slow, to full precision). */
+static double normal_inv(double p)
+{
+    double lo = -40.0, hi = 40.0;
+    for (int it = 0; it < 400 && hi - lo > 1e-15 * (1.0 + fabs(lo)); ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (normal_cdf(mid) < p) lo = mid; else hi = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+/*
+ * App. E, "Stratified-sampling": pass 1 walks the list as Eq. 1 does (T_min
+ * stop) and takes the mean mu and the standard deviation sigma of the
+ * transmittances T_1..T_n after each blended Gaussian.  Reading of the
+ * appendix: the K boundaries are spaced uniformly in the probability of
+ * N(mu, sigma^2) over the transmittance interval [0, 1] and mapped back,
+ *     u_lo = Phi(-mu / sigma),  u_hi = Phi((1 - mu) / sigma),
+ *     tau_k = mu + sigma Phi^{-1}(u_lo + (u_hi - u_lo)(1 - k/(K+1))),  k = 1..K,
+ * so they crowd where the transmittances do; with fewer than two blended
+ * Gaussians (sigma = 0) they are Algorithm 1's 1 - k/(K+1).  Pass 2 is
+ * Algorithm 1 with tau_k in place of 1 - k/(K+1): a Gaussian whose test
+ * transmittance falls below the next boundary is kept with weight T^Q alpha',
+ * and the walk stops once the test transmittance falls below tau_K.
+ * Outputs as or_qrender_list; tau (nullable) receives tau_1..tau_K and
+ * stats (nullable) (mu, sigma, n).  Returns the number kept, -1 without memory.
+ */
+int or_stratified_list(int64_t n, const double *a, int K, double T_min, int32_t *sel, double *w,
+                       double *TQ, int64_t *n_proc, double *tau, double *stats)
+{
+    double *Tv = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double *th = (double *)malloc(sizeof(double) * (size_t)(K + 1));
+    if (!Tv || !th) { free(Tv); free(th); return -1; }
+    /* pass 1: the transmittances of the dense walk */
+    double T = 1.0;
+    int64_t nb = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        double Ttest = T * (1.0 - a[i]);
+        if (T_min > 0.0 && Ttest < T_min) break;
+        T = Ttest;
+        Tv[nb++] = T;
+    }
+    double mu = 0.0, var = 0.0;
+    for (int64_t i = 0; i < nb; ++i) mu += Tv[i];
+    mu = nb > 0 ? mu / (double)nb : 0.0;
+    for (int64_t i = 0; i < nb; ++i) var += (Tv[i] - mu) * (Tv[i] - mu);
+    var = nb > 0 ? var / (double)nb : 0.0;
+    double sigma = sqrt(var);
+    for (int k = 1; k <= K; ++k) {
+        double c = 1.0 - (double)k / (double)(K + 1);
+        if (nb >= 2 && sigma > 0.0) {
+            double ulo = normal_cdf(-mu / sigma), uhi = normal_cdf((1.0 - mu) / sigma);
+            th[k] = mu + sigma * normal_inv(ulo + (uhi - ulo) * c);
+        } else {
+            th[k] = c;
+        }
+        if (tau) tau[k - 1] = th[k];
+    }
+    if (stats) { stats[0] = mu; stats[1] = sigma; stats[2] = (double)nb; }
+    /* pass 2: Algorithm 1 with the boundaries tau_k */
+    double Tq = 1.0;
+    int k = 0, m = 0;
+    int64_t i;
+    T = 1.0;
+    for (i = 0; i < n; ++i) { sel[i] = 0; w[i] = 0.0; }
+    for (i = 0; i < n; ++i) {
+        double Ttest = T * (1.0 - a[i]);
+        if (k < K && Ttest < th[k + 1]) {
+            k = k + 1;
+            w[i] = Tq * a[i];
+            sel[i] = 1;
+            ++m;
+            Tq = Tq * (1.0 - a[i]);
+            while (k < K && Ttest < th[k + 1]) k = k + 1;
+        }
+        if (Ttest < th[K]) { ++i; break; }
+        T = Ttest;
+    }
+    if (TQ) *TQ = Tq;
+    if (n_proc) *n_proc = i;
+    free(Tv); free(th);
+    return m;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Per-pixel renderer (brute force over all Gaussians).                      */
 /* ------------------------------------------------------------------------ */
 typedef struct {
@@ -252,6 +388,8 @@ typedef struct {
     double *out_dense; double *t_final; int32_t *n_members; int32_t *n_proc; int32_t *tie;
     int32_t *members; int max_members;   /* optional: I(p) in depth order, -1 padded */
     double *scale_q, *scale_dense;       /* optional: sum_j |w_j| max|f_j| (error denominators) */
+    int rule;                            /* or_render_rule: RULE_TOPK or RULE_STRATIFIED */
+    double *tau_out;                     /* or_render_rule: [npix][K] boundaries (stratified) */
     /* threading */
     int tid, nthreads; int status;
 } render_job_t;
@@ -441,6 +579,201 @@ done:
     return flags;
 }
 
+#define RULE_TOPK 1
+#define RULE_STRATIFIED 2
+
+/*
+ * Near-tie classification for the two select rules of or_render_rule, with
+ * the error model of classify_ties.  Bits: 2 = an alpha_min border entry, 4 =
+ * equal depths, 8 = the T_min decision, all up to the last entry either walk
+ * visits; 1 = the rule's own decision:
+ *   top-K: the K-th and (K+1)-th largest weights w = T alpha' within their
+ *     FP32 errors (relative E_T + rel(alpha') + u each);
+ *   stratified: a visited test transmittance of pass 2 within its error plus
+ *     the error of the boundary tau_k.  The boundary is computed in FP32 from
+ *     mu and sigma of pass 1's transmittances (whose errors E_n T_n give
+ *     d mu <= mean E_n T_n, d var <= 2 mean |T_n - mu| E_n T_n), with the
+ *     normal CDF and its inverse within a few units in the last place:
+ *     d tau_k <= d mu + |z_k| d sigma + sigma d z_k + 2u |tau_k|,
+ *     d z_k = 16u |z_k| + 64u / phi(z_k).
+ */
+static int classify_rule_ties(const render_job_t *J, const scratch_t *S, int rule, int64_t nproc,
+                              int64_t nused, const double *tau, const double *stats)
+{
+    const double u = ldexp(1.0, -24);
+    int flags = 0, K = J->K;
+    int64_t last_d = nused < S->len ? nused : S->len - 1;
+    int64_t last_q = nproc - 1;
+    int64_t last = last_d > last_q ? last_d : last_q;
+    double T = 1.0, E = 0.0;
+    double *wv = NULL, *we = NULL;
+    if (rule == RULE_TOPK) {
+        wv = (double *)malloc(sizeof(double) * (size_t)(S->len + 1));
+        we = (double *)malloc(sizeof(double) * (size_t)(S->len + 1));
+        if (!wv || !we) { free(wv); free(we); return 255; }
+    }
+    /* pass-1 statistics errors (stratified) */
+    double dmu = 0.0, dvar = 0.0;
+    double mu = stats ? stats[0] : 0.0, sigma = stats ? stats[1] : 0.0;
+    int64_t nb = stats ? (int64_t)stats[2] : 0;
+    for (int64_t i = 0; i < S->len; ++i) {
+        const member_t *m = &S->m[i];
+        double rel = alpha_rel_err(J->tie_eps, m->qabs);
+        int exact = m->g * (1.0 - rel) >= J->alpha_max;
+        double ea = exact ? 0.0 : rel * m->a / (1.0 - m->a);
+        double Tt = T * (1.0 - m->a);
+        if (rule == RULE_TOPK && i < nused) {
+            wv[i] = T * m->a;
+            we[i] = E + (exact ? 0.0 : rel) + u;      /* relative error of fl32(T a) */
+        }
+        E += ea + 2.0 * u;
+        if (i < nused && J->T_min > 0.0 && fabs(Tt - J->T_min) <= (2.0 * E + 2.0 * u) * J->T_min)
+            flags |= 8;
+        if (i < nused && i < nb) {
+            dmu += E * Tt;
+            dvar += 2.0 * fabs(Tt - mu) * E * Tt;
+        }
+        T = Tt;
+    }
+    if (rule == RULE_STRATIFIED && nb >= 2 && sigma > 0.0) {
+        dmu /= (double)nb;
+        double dsigma = dvar / (double)nb / (2.0 * sigma) + 2.0 * u * sigma;
+        T = 1.0; E = 0.0;
+        for (int64_t i = 0; i <= last_q && i < S->len; ++i) {
+            const member_t *m = &S->m[i];
+            double rel = alpha_rel_err(J->tie_eps, m->qabs);
+            double ea = (m->g * (1.0 - rel) >= J->alpha_max) ? 0.0 : rel * m->a / (1.0 - m->a);
+            E += ea + 2.0 * u;
+            double Tt = T * (1.0 - m->a);
+            for (int k = 0; k < K; ++k) {
+                double z = (tau[k] - mu) / sigma;
+                double phi = exp(-0.5 * z * z) / sqrt(2.0 * 3.14159265358979323846);
+                double dz = 16.0 * u * fabs(z) + 64.0 * u / phi;
+                double dtau = dmu + fabs(z) * dsigma + sigma * dz + 2.0 * u * fabs(tau[k]);
+                if (fabs(Tt - tau[k]) <= (2.0 * E + 2.0 * u) * tau[k] + 2.0 * dtau) flags |= 1;
+            }
+            T = Tt;
+        }
+    } else if (rule == RULE_STRATIFIED) {
+        /* uniform boundaries: the checks of classify_ties */
+        T = 1.0; E = 0.0;
+        for (int64_t i = 0; i <= last_q && i < S->len; ++i) {
+            const member_t *m = &S->m[i];
+            double rel = alpha_rel_err(J->tie_eps, m->qabs);
+            double ea = (m->g * (1.0 - rel) >= J->alpha_max) ? 0.0 : rel * m->a / (1.0 - m->a);
+            E += ea + 2.0 * u;
+            double Tt = T * (1.0 - m->a);
+            for (int k = 0; k < K; ++k)
+                if (fabs(Tt - tau[k]) <= (2.0 * E + 2.0 * u) * tau[k]) flags |= 1;
+            T = Tt;
+        }
+    }
+    if (rule == RULE_TOPK && nused > K) {
+        /* the K-th and (K+1)-th largest weights: sort (weight desc, position asc) */
+        int64_t *ord = (int64_t *)malloc(sizeof(int64_t) * (size_t)nused);
+        if (!ord) { free(wv); free(we); return 255; }
+        for (int64_t i = 0; i < nused; ++i) ord[i] = i;
+        for (int64_t i = 1; i < nused; ++i) {          /* insertion sort: small lists */
+            int64_t v = ord[i], j = i;
+            while (j > 0 && (wv[ord[j - 1]] < wv[v] || (wv[ord[j - 1]] == wv[v] && ord[j - 1] > v))) {
+                ord[j] = ord[j - 1];
+                --j;
+            }
+            ord[j] = v;
+        }
+        int64_t p = ord[K - 1], q = ord[K];
+        if (fabs(wv[p] - wv[q]) <= 2.0 * (we[p] * wv[p] + we[q] * wv[q])) flags |= 1;
+        free(ord);
+    }
+    free(wv); free(we);
+    for (int64_t i = 0; i + 1 < S->len && i <= last; ++i)
+        if (fabs(S->m[i + 1].depth - S->m[i].depth) <= 4.0 * u * fabs(S->m[i].depth)) flags |= 4;
+    double zl = (last >= 0 && last < S->len - 1) ? S->m[last].depth : INFINITY;
+    for (int64_t b = 0; b < S->blen; ++b)
+        if (S->border[b] <= zl * (1.0 + 4.0 * u)) flags |= 2;
+    return flags;
+}
+
+/* One pixel under a select rule of or_render_rule. */
+static int render_rule_pixel(render_job_t *J, scratch_t *S, int64_t p)
+{
+    const int K = J->K, C = J->C;
+    double Tq = 1.0, stats[3] = {0.0, 0.0, 0.0};
+    int64_t nproc = 0, nused = 0;
+    double *tau = (double *)malloc(sizeof(double) * (size_t)K);
+    if (!tau) return -1;
+    int m;
+    double D;
+    if (J->rule == RULE_TOPK) {
+        m = or_topk_list(S->len, S->a, K, J->T_min, S->sel, S->w, &nused);
+        nproc = nused;
+        D = 0.0;                             /* normalisation: divide by the kept sum */
+        for (int64_t i = 0; i < S->len; ++i) D += S->w[i];
+        Tq = 1.0 - D;
+    } else {
+        m = or_stratified_list(S->len, S->a, K, J->T_min, S->sel, S->w, &Tq, &nproc, tau, stats);
+        double Tf = 1.0;
+        nused = or_dense_list(S->len, S->a, J->T_min, S->wd, &Tf);
+        if (J->tau_out)
+            for (int k = 0; k < K; ++k) J->tau_out[p * K + k] = tau[k];
+    }
+    if (m < 0) { free(tau); return -1; }
+    if (J->rule != RULE_TOPK) D = 1.0 - Tq;
+    if (J->cnt) J->cnt[p] = m;
+    if (J->n_proc) J->n_proc[p] = (int32_t)nproc;
+    if (J->tq) J->tq[p] = Tq;
+    int j = 0;
+    for (int64_t i = 0; i < S->len && j < K; ++i)
+        if (S->sel[i]) {
+            if (J->ids) J->ids[p * K + j] = (int32_t)S->m[i].id;
+            if (J->wq) J->wq[p * K + j] = S->w[i] / D;
+            ++j;
+        }
+    for (; j < K; ++j) {
+        if (J->ids) J->ids[p * K + j] = -1;
+        if (J->wq) J->wq[p * K + j] = 0.0;
+    }
+    if (J->out_q && J->feat) {
+        double *o = J->out_q + p * C;
+        double sc = 0.0;
+        for (int c = 0; c < C; ++c) o[c] = 0.0;
+        if (m > 0)
+            for (int64_t i = 0; i < S->len; ++i)
+                if (S->sel[i]) {
+                    const double *f = J->feat + S->m[i].id * C;
+                    double mx = 0.0;
+                    for (int c = 0; c < C; ++c) {
+                        o[c] += S->w[i] / D * f[c];
+                        mx = fabs(f[c]) > mx ? fabs(f[c]) : mx;
+                    }
+                    sc += fabs(S->w[i] / D) * mx;
+                }
+        if (J->scale_q) J->scale_q[p] = sc;
+    }
+    if (J->tie)
+        J->tie[p] = classify_rule_ties(J, S, J->rule, nproc, nused, tau,
+                                       J->rule == RULE_STRATIFIED ? stats : NULL);
+    free(tau);
+    return 0;
+}
+
+static void *render_rule_worker(void *arg)
+{
+    render_job_t *J = (render_job_t *)arg;
+    scratch_t S;
+    memset(&S, 0, sizeof(S));
+    for (int64_t p = J->tid; p < J->npix; p += J->nthreads) {
+        int px = J->pix[2 * p], py = J->pix[2 * p + 1];
+        if (build_list(J, &S, px, py) || render_rule_pixel(J, &S, p)) {
+            J->status = OR_ERR_NOMEM;
+            break;
+        }
+        if (J->n_members) J->n_members[p] = (int32_t)S.len;
+    }
+    free(S.m); free(S.border); free(S.a); free(S.w); free(S.wd); free(S.sel);
+    return NULL;
+}
+
 static void *render_worker(void *arg)
 {
     render_job_t *J = (render_job_t *)arg;
@@ -567,6 +900,90 @@ int or_render(int64_t n, const double *mean2d, const double *conic, const double
         if (t > 0) pthread_create(&th[t], NULL, render_worker, &jobs[t]);
     }
     render_worker(&jobs[0]);
+    int st = jobs[0].status;
+    for (int t = 1; t < nthreads; ++t) {
+        pthread_join(th[t], NULL);
+        if (jobs[t].status) st = jobs[t].status;
+    }
+    free(jobs); free(th);
+    return st;
+}
+
+/*
+ * The near-tie classification of one pixel under a select rule of
+ * or_render_rule, from its candidates as in or_classify_candidates.  Returns
+ * the flags (or -1); kept [K] (nullable) receives the kept ids in depth order
+ * (-1 padded) and tau [K] (nullable) the stratified boundaries.
+ */
+int or_classify_rule_candidates(int64_t n, const double *depth, const int64_t *id, const double *g,
+                                const double *qabs, int rule, int K, double alpha_min,
+                                double alpha_max, double T_min, double tie_eps, int64_t *kept,
+                                double *tau)
+{
+    if (n < 0 || K < 1 || !depth || !id || !g || !qabs ||
+        (rule != RULE_TOPK && rule != RULE_STRATIFIED))
+        return -1;
+    render_job_t J;
+    memset(&J, 0, sizeof(J));
+    int32_t tie = 0, cnt = 0;
+    int32_t *ids = (int32_t *)malloc(sizeof(int32_t) * (size_t)K);
+    double *tv = (double *)malloc(sizeof(double) * (size_t)K);
+    J.K = K; J.alpha_min = alpha_min; J.alpha_max = alpha_max; J.T_min = T_min;
+    J.tie_eps = tie_eps; J.tie = &tie; J.cnt = &cnt; J.ids = ids; J.tau_out = tv; J.rule = rule;
+    scratch_t S;
+    memset(&S, 0, sizeof(S));
+    int flags = -1;
+    if (!ids || !tv) goto done;
+    for (int64_t c = 0; c < n; ++c)
+        if (add_candidate(&J, &S, depth[c], id[c], g[c], 1.0, 0.0, 0.0, qabs[c])) goto done;
+    if (finish_list(&S) || render_rule_pixel(&J, &S, 0)) goto done;
+    flags = tie;
+    for (int k = 0; k < K; ++k) {
+        if (kept) kept[k] = ids[k];
+        if (tau) tau[k] = tv[k];
+    }
+done:
+    free(S.m); free(S.border); free(S.a); free(S.w); free(S.wd); free(S.sel);
+    free(ids); free(tv);
+    return flags;
+}
+
+/*
+ * Render the listed pixels with another select rule in place of Algorithm 1:
+ * rule 1 = top-K (or_topk_list), rule 2 = Stratified-K (or_stratified_list).
+ * Outputs as or_render's Q-Render outputs (nullable): out [npix][C] (the kept
+ * Gaussians' features with the rule's normalised weights), ids / wq [npix][K]
+ * (depth order, -1 / 0 padded), cnt, n_members, n_proc (entries visited),
+ * tie (classify_rule_ties), scale [npix] (sum |w| max|f|), tau [npix][K]
+ * (stratified boundaries).
+ */
+int or_render_rule(int64_t n, const double *mean2d, const double *conic, const double *depth,
+                   const double *alpha, const int32_t *valid, const double *feat, int C, int rule,
+                   int K, double alpha_min, double alpha_max, double T_min, double tie_eps,
+                   int64_t npix, const int32_t *pix, int nthreads, double *out, int32_t *ids,
+                   double *wq, int32_t *cnt, int32_t *n_members, int32_t *n_proc, int32_t *tie,
+                   double *scale, double *tau)
+{
+    if (n < 0 || npix < 0 || K < 1 || nthreads < 1 || C < 0 ||
+        (rule != RULE_TOPK && rule != RULE_STRATIFIED))
+        return OR_ERR_ARG;
+    render_job_t base;
+    memset(&base, 0, sizeof(base));
+    base.n = n; base.mean2d = mean2d; base.conic = conic; base.depth = depth;
+    base.alpha = alpha; base.valid = valid; base.feat = feat; base.C = C;
+    base.K = K; base.alpha_min = alpha_min; base.alpha_max = alpha_max; base.T_min = T_min;
+    base.tie_eps = tie_eps; base.npix = npix; base.pix = pix;
+    base.out_q = out; base.ids = ids; base.wq = wq; base.cnt = cnt;
+    base.n_members = n_members; base.n_proc = n_proc; base.tie = tie; base.scale_q = scale;
+    base.rule = rule; base.tau_out = tau; base.nthreads = nthreads;
+    render_job_t *jobs = (render_job_t *)calloc((size_t)nthreads, sizeof(render_job_t));
+    pthread_t *th = (pthread_t *)calloc((size_t)nthreads, sizeof(pthread_t));
+    if (!jobs || !th) { free(jobs); free(th); return OR_ERR_NOMEM; }
+    for (int t = 0; t < nthreads; ++t) {
+        jobs[t] = base; jobs[t].tid = t;
+        if (t > 0) pthread_create(&th[t], NULL, render_rule_worker, &jobs[t]);
+    }
+    render_rule_worker(&jobs[0]);
     int st = jobs[0].status;
     for (int t = 1; t < nthreads; ++t) {
         pthread_join(th[t], NULL);

@@ -627,7 +627,8 @@ static int classify_rule_ties(const render_job_t *J, const scratch_t *S, int rul
             we[i] = E + (exact ? 0.0 : rel) + u;      /* relative error of fl32(T a) */
         }
         E += ea + 2.0 * u;
-        if (i < nused && J->T_min > 0.0 && fabs(Tt - J->T_min) <= (2.0 * E + 2.0 * u) * J->T_min)
+        /* the T_min decision, up to and including the entry that stopped the walk */
+        if (i <= last_d && J->T_min > 0.0 && fabs(Tt - J->T_min) <= (2.0 * E + 2.0 * u) * J->T_min)
             flags |= 8;
         if (i < nused && i < nb) {
             dmu += E * Tt;

@@ -182,6 +182,31 @@ qr_status qr_sort(qr_frame *frame, qr_stream stream);
 qr_status qr_select(const qr_frame *frame, int32_t *ids, float *weights, uint8_t *counts,
                     qr_stream stream);
 
+/* The select rules the paper weighs Algorithm 1 against, with the outputs of
+ * qr_select (ids [P][K] in depth order, -1 padded; weights [P][K]
+ * normalised, zero padded; counts [P]), so qr_blend renders any of them.
+ *   QR_RULE_QUANTILE:   Algorithm 1 (the same kernel as qr_select).
+ *   QR_RULE_TOPK:       top-K, the renderer of Sec. 4.2 and the complexity
+ *                       table (O(N log K + KC)): the K largest Eq. 1 weights
+ *                       w = T alpha' along the dense walk (alpha' rules and
+ *                       T_min stop of qr_dense), equal weights keeping the
+ *                       earlier entry; weights divided by the kept sum.
+ *   QR_RULE_STRATIFIED: Stratified-K, App. E: pass 1 takes the mean mu and
+ *                       standard deviation sigma of the dense walk's
+ *                       transmittances; the boundaries
+ *                       tau_k = mu + sigma Phi^-1(u_lo + (u_hi - u_lo)(1 - k/(K+1))),
+ *                       u_lo = Phi(-mu/sigma), u_hi = Phi((1 - mu)/sigma),
+ *                       are equally spaced in the probability of
+ *                       N(mu, sigma^2) over [0, 1] (Algorithm 1's
+ *                       1 - k/(K+1) with fewer than two blended Gaussians);
+ *                       pass 2 is Algorithm 1 with tau_k in place of
+ *                       1 - k/(K+1), weights T^Q alpha' / (1 - T^Q).
+ * tau [P][K] float32 (nullable; stratified only) receives each pixel's
+ * boundaries.  K <= 32 (frame params). */
+typedef enum { QR_RULE_QUANTILE = 0, QR_RULE_TOPK = 1, QR_RULE_STRATIFIED = 2 } qr_rule;
+qr_status qr_select_rule(const qr_frame *frame, qr_rule rule, int32_t *ids, float *weights,
+                         uint8_t *counts, float *tau, qr_stream stream);
+
 /* Algorithm 1, blend half ("alpha-blending on quantile Gaussians" +
  * normalisation): out[p] = sum_{j < counts[p]} weights[p][j] * feat[ids[p][j]]
  * with FP32 accumulation.  feat is [n_gauss][C] of dtype; feat_scale [n_gauss]

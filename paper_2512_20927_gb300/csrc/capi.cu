@@ -202,6 +202,17 @@ qr_status qr_select(const qr_frame *frame, int32_t *ids, float *weights, uint8_t
     return from_cuda(launch_select(*frame, ids, weights, counts, reinterpret_cast<cudaStream_t>(stream)));
 }
 
+qr_status qr_select_rule(const qr_frame *frame, qr_rule rule, int32_t *ids, float *weights,
+                         uint8_t *counts, float *tau, qr_stream stream) {
+    if (!frame_ok(frame) || !ids || !weights || !counts) return QR_ERR_INVALID_ARG;
+    if (rule != QR_RULE_QUANTILE && rule != QR_RULE_TOPK && rule != QR_RULE_STRATIFIED)
+        return QR_ERR_INVALID_ARG;
+    const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (rule == QR_RULE_QUANTILE) return from_cuda(launch_select(*frame, ids, weights, counts, s));
+    return from_cuda(launch_select_rule(*frame, int(rule), ids, weights, counts,
+                                        rule == QR_RULE_STRATIFIED ? tau : nullptr, s));
+}
+
 static qr_status check_feat(const void *feat, const float *feat_scale, qr_dtype dtype, int32_t C) {
     if (!feat || C <= 0) return QR_ERR_INVALID_ARG;
     if (dtype != QR_F32 && dtype != QR_BF16 && dtype != QR_FP8E4M3) return QR_ERR_INVALID_ARG;

@@ -83,6 +83,9 @@ cudaError_t launch_select(const qr_frame &f, int32_t *ids, float *w, uint8_t *cn
                           cudaStream_t s);
 cudaError_t launch_dense(const qr_frame &f, const void *feat, const float *scale, qr_dtype dt,
                          int C, float *out, float *T_final, cudaStream_t s);
+// rule: 1 = top-K, 2 = Stratified-K (qr_rule); tau [P][K] nullable (stratified boundaries)
+cudaError_t launch_select_rule(const qr_frame &f, int rule, int32_t *ids, float *w, uint8_t *cnt,
+                               float *tau, cudaStream_t s);
 
 size_t backward_workspace_bytes(const qr_frame &f, int C);
 cudaError_t launch_backward(const qr_frame &f, const void *feat, const float *scale, qr_dtype dt,

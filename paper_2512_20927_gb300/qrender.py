@@ -22,6 +22,7 @@ LIB_PATH = os.path.join(_HERE, "libqrender.so")
 QR_OK, QR_ERR_INVALID_ARG, QR_ERR_ALIGNMENT, QR_ERR_CAPACITY, QR_ERR_CUDA, \
     QR_ERR_DEVICE_TIMEOUT, QR_ERR_NOT_SUPPORTED = range(7)
 QR_F32, QR_BF16, QR_FP8E4M3 = 0, 1, 2
+QR_RULE_QUANTILE, QR_RULE_TOPK, QR_RULE_STRATIFIED = 0, 1, 2
 FRAME_SLOTS = 24
 
 
@@ -84,6 +85,7 @@ SIGNATURES = {
     "qr_project": (_S, [ctypes.POINTER(qr_frame), _P, _P, _P, _P, _P]),
     "qr_sort": (_S, [ctypes.POINTER(qr_frame), _P]),
     "qr_select": (_S, [ctypes.POINTER(qr_frame), _P, _P, _P, _P]),
+    "qr_select_rule": (_S, [ctypes.POINTER(qr_frame), _S, _P, _P, _P, _P, _P]),
     "qr_blend": (_S, [_P, _P, _S, _I32, _I64, _P, _P, _P, _I64, _I32, _I32, _P, _P]),
     "qr_dense": (_S, [ctypes.POINTER(qr_frame), _P, _P, _S, _I32, _P, _P, _P]),
     "qr_render": (_S, [ctypes.POINTER(qr_frame), _P, _P, _P, _P, _P, _P, _S, _I32, _P, _P, _P,
@@ -267,6 +269,12 @@ def qr_select(fr: Frame, ids, weights, counts, stream=None):
                             _stream(stream)), "qr_select")
 
 
+def qr_select_rule(fr: Frame, rule, ids, weights, counts, tau=None, stream=None):
+    """Top-K / Stratified-K / Algorithm 1 selection into qr_select's outputs."""
+    _check(load().qr_select_rule(ctypes.byref(fr.frame), int(rule), _ptr(ids), _ptr(weights),
+                                 _ptr(counts), _ptr(tau), _stream(stream)), "qr_select_rule")
+
+
 def qr_blend(feat, feat_scale, ids, weights, counts, out, width=0, stream=None):
     P, K = ids.shape
     C = feat.shape[1]
@@ -445,10 +453,12 @@ def gaussians_to_device(g, device="cuda"):
                  for a in (g.mean, g.log_scale, g.quat, g.opacity))
 
 
-def render_frame(gdev, feat, cam, K=8, max_isect=None, params=None, stream=None, dense=False):
-    """Project, sort, select and blend one frame; grows the intersection
-    capacity and retries when the device reports an overflow.  Returns a dict
-    of device tensors (ids, weights, counts, out[, dense, T_final]) and the frame."""
+def render_frame(gdev, feat, cam, K=8, max_isect=None, params=None, stream=None, dense=False,
+                 rule=QR_RULE_QUANTILE):
+    """Project, sort, select (Algorithm 1, or another qr_rule) and blend one
+    frame; grows the intersection capacity and retries when the device reports
+    an overflow.  Returns a dict of device tensors (ids, weights, counts,
+    out[, dense, T_final][, tau]) and the frame."""
     torch = _torch()
     mean = gdev[0]
     n = mean.shape[0]
@@ -469,8 +479,15 @@ def render_frame(gdev, feat, cam, K=8, max_isect=None, params=None, stream=None,
             continue
         _check(code, "qr_sort")
         break
-    qr_select(fr, ids, w, cnt, stream=stream)
     res = {"ids": ids, "weights": w, "counts": cnt, "n_isect": nis, "frame": fr}
+    if rule == QR_RULE_QUANTILE:
+        qr_select(fr, ids, w, cnt, stream=stream)
+    else:
+        tau = (torch.empty((P, params.K), dtype=torch.float32, device=mean.device)
+               if rule == QR_RULE_STRATIFIED else None)
+        qr_select_rule(fr, rule, ids, w, cnt, tau, stream=stream)
+        if tau is not None:
+            res["tau"] = tau
     if feat is not None:
         f, fs = feat if isinstance(feat, tuple) else (feat, None)
         C = f.shape[1]

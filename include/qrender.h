@@ -354,6 +354,40 @@ qr_status qr_cosine_backward(const qr_frame *frame, const void *feat, const floa
                              float *grad_feat, float *grad_opacity, float *grad_conic, void *ws,
                              size_t ws_bytes, qr_stream stream);
 
+/* The training loss of the paper, Eq. 2 (Sec. 4.3): every pixel p of a mask
+ * (patch) i = mask_id[p] is pulled towards that mask's CLIP embedding t_i and
+ * away from the other masks' embeddings,
+ *   L_p = -log( exp(s_i) / sum_{j != i} exp(s_j) ),  s_j = cos(F_p, t_j)
+ *       = F.t_j / (max(|F|, 1e-8) max(|t_j|, 1e-8))
+ * (the denominator over the other masks j != i, as Eq. 2 prints it), and
+ * L = mean of L_p over the pixels with mask_id >= 0 (their count floored at
+ * 1).  feature_map [P][C] float32 (the rendered map), targets [M][C] float32
+ * (one embedding per mask, any length), mask_id [P] int32 (-1: pixel not in
+ * the loss); loss_out [2] device floats -> (L, 1/n) (integer counters while
+ * the call runs on the stream); grad [P][C] -> dL/dF (zero rows outside the
+ * masks).  2 <= M <= 64; C a multiple of 128 up to 512.  ws: 256-byte
+ * aligned, qr_contrastive_workspace_bytes(P, M, C) bytes (unit targets and
+ * per-pixel terms).  Deterministic: the terms are summed over fixed ranges
+ * added in a fixed order.  QR_ERR_NOT_SUPPORTED for other M or C. */
+size_t qr_contrastive_workspace_bytes(int64_t P, int32_t M, int32_t C);
+qr_status qr_contrastive_loss(const float *feature_map, const float *targets, int32_t M,
+                              int32_t C, const int32_t *mask_id, int64_t P, float *loss_out,
+                              float *grad, void *ws, size_t ws_bytes, qr_stream stream);
+
+/* qr_contrastive_loss followed on the stream by qr_backward with its dL/dF
+ * (grad_map) as the upstream gradient: one call from the rendered map and
+ * the masks' embeddings to the gradients of the features, opacities and
+ * conics.  Arguments as in the two calls; ws:
+ * qr_contrastive_backward_workspace_bytes(frame, M, C) bytes. */
+size_t qr_contrastive_backward_workspace_bytes(const qr_frame *frame, int32_t M, int32_t C);
+qr_status qr_contrastive_backward(const qr_frame *frame, const void *feat, const float *feat_scale,
+                                  qr_dtype dtype, int32_t C, const int32_t *ids,
+                                  const float *weights, const uint8_t *counts,
+                                  const float *feature_map, const float *targets, int32_t M,
+                                  const int32_t *mask_id, float *loss_out, float *grad_map,
+                                  float *grad_feat, float *grad_opacity, float *grad_conic,
+                                  void *ws, size_t ws_bytes, qr_stream stream);
+
 /* ---------------------------------------------------------------- relevance */
 
 /* Open-vocabulary relevance (Sec. 5 scores features against text embeddings by
@@ -370,6 +404,24 @@ qr_status qr_cosine_backward(const qr_frame *frame, const void *feat, const floa
  * library). */
 qr_status qr_relevance(const float *feature_map, const uint16_t *queries_bf16, int32_t Q, int32_t C,
                        int64_t P, float *out, int32_t *status, qr_stream stream);
+
+/* The blend of Algorithm 1 fused with the relevance product (Sec. 5 scores
+ * rendered features against text embeddings): out[p][q] = sum_c F_p[c] Q[q][c]
+ * with F_p = sum_{j < counts[p]} weights[p][j] feat[ids[p][j]] (qr_blend's
+ * map), without writing the [P][C] map.  Blocks of 128 pixels (16 x 8 on
+ * screen when width > 0, consecutive pixels when width = 0) are blended 32
+ * channels at a time into shared memory in FP32 and multiplied on the tensor
+ * cores as TF32 (at least 10 mantissa bits of F; the BF16 queries are exact),
+ * FP32 accumulation in TMEM.  feat / feat_scale / dtype / ids / weights /
+ * counts / P / K / width as in qr_blend; queries_bf16 [Q][C]; out [P][Q]
+ * float32.  Q in {16, 32, 64}; C a multiple of 32 with the FP32 queries
+ * fitting in shared memory (Q * C * 4 bytes plus 48 KB).  status as in
+ * qr_relevance (QR_ERR_DEVICE_TIMEOUT if a bounded wait gives up). */
+qr_status qr_blend_relevance(const void *feat, const float *feat_scale, qr_dtype dtype, int32_t C,
+                             int64_t n_gauss, const int32_t *ids, const float *weights,
+                             const uint8_t *counts, int64_t P, int32_t K, int32_t width,
+                             const uint16_t *queries_bf16, int32_t Q, float *out, int32_t *status,
+                             qr_stream stream);
 
 /* ---------------------------------------------------------------- feature storage */
 

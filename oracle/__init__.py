@@ -469,6 +469,45 @@ def cosine_loss(F, target, mask, eps: float = 1e-8):
     return L, g
 
 
+def contrastive_loss(F, targets, mask_id, eps: float = 1e-8):
+    """Eq. 2 (Sec. 4.3) on a rendered map, FP64.
+
+    Pixel p belongs to mask (patch) i = mask_id[p] with target embedding
+    t_i = targets[i]; pixels with mask_id < 0 are not in the loss.  With
+    s_j = cos(F_p, t_j) = F.t_j / (max(|F|,eps) max(|t_j|,eps)), the pixel's
+    term is  -log( exp(s_i) / sum_{j != i} exp(s_j) )  (the denominator sums
+    over the other masks, as Eq. 2 prints it), and L is the mean over the
+    pixels in the loss (their count floored at 1).  Returns (L, dL/dF [P,C]):
+    dL_p/dF = (1/n) sum_j c_j ds_j/dF with c_i = -1, c_j = softmax_{j != i}(s)_j,
+    ds_j/dF = t_j / (nf nt_j) - s_j F / nf^2 (the second term vanishes where
+    |F| <= eps, nf = max(|F|, eps) being constant there)."""
+    F = np.asarray(F, np.float64)
+    T = np.asarray(targets, np.float64)
+    mid = np.asarray(mask_id, np.int64)
+    on = mid >= 0
+    n = max(int(on.sum()), 1)
+    nf_raw = np.linalg.norm(F, axis=1)
+    nf = np.maximum(nf_raw, eps)
+    nt = np.maximum(np.linalg.norm(T, axis=1), eps)
+    S = (F @ T.T) / (nf[:, None] * nt[None, :])          # [P, M] cosine similarities
+    M = T.shape[0]
+    L = 0.0
+    g = np.zeros_like(F)
+    for p in np.nonzero(on)[0]:
+        i = mid[p]
+        others = np.arange(M) != i
+        e = np.exp(S[p, others])
+        L += -S[p, i] + np.log(e.sum())
+        c = np.zeros(M)
+        c[others] = e / e.sum()
+        c[i] = -1.0
+        grad = (c / nt) @ T / nf[p]
+        if nf_raw[p] > eps:
+            grad -= (c @ S[p]) * F[p] / nf[p] ** 2
+        g[p] = grad / n
+    return L / n, g
+
+
 def relevance(feature_map, queries) -> np.ndarray:
     """Open-vocabulary relevance (Sec. 5): map [P,C] times queries^T [C,Q] in FP64."""
     return np.asarray(feature_map, np.float64) @ np.asarray(queries, np.float64).T

@@ -407,6 +407,82 @@ qr_status qr_cosine_loss(const float *feature_map, const float *target, const ui
                                         reinterpret_cast<cudaStream_t>(stream)));
 }
 
+size_t qr_contrastive_workspace_bytes(int64_t P, int32_t M, int32_t C) {
+    if (P < 0 || !contrastive_supported(M, C)) return 0;
+    return contrastive_workspace_bytes(P, M, C);
+}
+
+qr_status qr_contrastive_loss(const float *feature_map, const float *targets, int32_t M,
+                              int32_t C, const int32_t *mask_id, int64_t P, float *loss_out,
+                              float *grad, void *ws, size_t ws_bytes, qr_stream stream) {
+    if (!feature_map || !targets || !mask_id || !loss_out || !grad || !ws || P < 0)
+        return QR_ERR_INVALID_ARG;
+    if (!contrastive_supported(M, C)) return QR_ERR_NOT_SUPPORTED;
+    if (!aligned16(feature_map) || !aligned16(targets) || !aligned16(grad) ||
+        (reinterpret_cast<uintptr_t>(ws) & (kAlign - 1)))
+        return QR_ERR_ALIGNMENT;
+    if (ws_bytes < contrastive_workspace_bytes(P, M, C)) return QR_ERR_INVALID_ARG;
+    const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (P == 0)
+        return from_cuda(cudaMemcpyAsync(loss_out, kEmptyLoss, sizeof(kEmptyLoss),
+                                         cudaMemcpyHostToDevice, s));
+    return from_cuda(launch_contrastive_loss(feature_map, targets, M, C, mask_id, P, loss_out,
+                                             grad, ws, s));
+}
+
+size_t qr_contrastive_backward_workspace_bytes(const qr_frame *frame, int32_t M, int32_t C) {
+    if (!frame_ok(frame) || C < 4 || C % 4 || !contrastive_supported(M, C)) return 0;
+    return align_up(backward_workspace_bytes(*frame, C)) +
+           contrastive_workspace_bytes(num_pixels(*frame), M, C);
+}
+
+qr_status qr_contrastive_backward(const qr_frame *frame, const void *feat, const float *feat_scale,
+                                  qr_dtype dtype, int32_t C, const int32_t *ids,
+                                  const float *weights, const uint8_t *counts,
+                                  const float *feature_map, const float *targets, int32_t M,
+                                  const int32_t *mask_id, float *loss_out, float *grad_map,
+                                  float *grad_feat, float *grad_opacity, float *grad_conic,
+                                  void *ws, size_t ws_bytes, qr_stream stream) {
+    if (!frame_ok(frame) || !ids || !weights || !counts || !feature_map || !targets || !mask_id ||
+        !loss_out || !grad_map || !grad_feat || !ws)
+        return QR_ERR_INVALID_ARG;
+    qr_status st = check_feat(feat, feat_scale, dtype, C);
+    if (st != QR_OK) return st;
+    if (!contrastive_supported(M, C)) return QR_ERR_NOT_SUPPORTED;
+    if (!aligned16(feature_map) || !aligned16(targets) || !aligned16(grad_map) ||
+        !aligned16(grad_feat) || (reinterpret_cast<uintptr_t>(ws) & (kAlign - 1)))
+        return QR_ERR_ALIGNMENT;
+    const size_t bw = align_up(backward_workspace_bytes(*frame, C));
+    const int64_t P = num_pixels(*frame);
+    if (ws_bytes < bw + contrastive_workspace_bytes(P, M, C)) return QR_ERR_INVALID_ARG;
+    const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = launch_contrastive_loss(feature_map, targets, M, C, mask_id, P, loss_out,
+                                            grad_map, static_cast<char *>(ws) + bw, s);
+    if (e != cudaSuccess) return QR_ERR_CUDA;
+    if (frame->n == 0) return QR_OK;
+    return from_cuda(launch_backward(*frame, feat, feat_scale, dtype, C, ids, weights, counts,
+                                     grad_map, grad_feat, grad_opacity, grad_conic, ws, s));
+}
+
+qr_status qr_blend_relevance(const void *feat, const float *feat_scale, qr_dtype dtype, int32_t C,
+                             int64_t n_gauss, const int32_t *ids, const float *weights,
+                             const uint8_t *counts, int64_t P, int32_t K, int32_t width,
+                             const uint16_t *queries_bf16, int32_t Q, float *out, int32_t *status,
+                             qr_stream stream) {
+    qr_status st = check_feat(feat, feat_scale, dtype, C);
+    if (st != QR_OK) return st;
+    if (!ids || !weights || !counts || !queries_bf16 || !out || !status || P < 0 || n_gauss < 1 ||
+        width < 0 || (width > 0 && P % width != 0))
+        return QR_ERR_INVALID_ARG;
+    if (!blend_relevance_supported(dtype, Q, C, K)) return QR_ERR_NOT_SUPPORTED;
+    if (!aligned16(queries_bf16) || !aligned16(out)) return QR_ERR_ALIGNMENT;
+    if (P == 0) return QR_OK;
+    const int H = width > 0 ? int(P / width) : 0;
+    return from_cuda(launch_blend_relevance(feat, feat_scale, dtype, C, n_gauss, ids, weights,
+                                            counts, P, K, width, H, queries_bf16, Q, out, status,
+                                            reinterpret_cast<cudaStream_t>(stream)));
+}
+
 qr_status qr_relevance(const float *feature_map, const uint16_t *queries_bf16, int32_t Q, int32_t C,
                        int64_t P, float *out, int32_t *status, qr_stream stream) {
     if (!feature_map || !queries_bf16 || !out || !status || P < 0) return QR_ERR_INVALID_ARG;

@@ -150,7 +150,21 @@ cudaError_t launch_batch(const void *ws, int n_views, uint32_t total_items, qr_d
                          int K, int group, int ctas_per_sm, cudaStream_t s);
 cudaError_t prepare_batch(const qr_view *views, int n_views, void *ws, uint32_t *total_items,
                           cudaStream_t s, BatchView *host_scratch);
+// Eq. 2 contrastive loss (contrastive.cu): out2 -> (L, 1/n), grad [P][C] -> dL/dF;
+// ws: contrastive_workspace_bytes (unit targets, per-pixel terms)
+bool contrastive_supported(int M, int C);
+size_t contrastive_workspace_bytes(int64_t P, int M, int C);
+cudaError_t launch_contrastive_loss(const float *F, const float *tgt, int M, int C,
+                                    const int32_t *mask_id, int64_t P, float *out2, float *grad,
+                                    void *ws, cudaStream_t s);
 bool relevance_supported(int Q, int C);
+// blend of qr_blend fused with the relevance product (the map is never written)
+bool blend_relevance_supported(qr_dtype dt, int Q, int C, int K);
+cudaError_t launch_blend_relevance(const void *feat, const float *scale, qr_dtype dt, int C,
+                                   int64_t n_gauss, const int32_t *ids, const float *w,
+                                   const uint8_t *cnt, int64_t P, int K, int W, int H,
+                                   const uint16_t *q, int Q, float *out, int *status,
+                                   cudaStream_t s);
 cudaError_t launch_relevance(const float *map, const uint16_t *q, int Q, int64_t P, int C,
                              float *out, int *status, cudaStream_t s);
 

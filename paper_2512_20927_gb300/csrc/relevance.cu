@@ -24,6 +24,7 @@
 // and MMAs, frees its TMEM and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include "qr_internal.cuh"
 #include "tma.cuh"
@@ -454,6 +455,280 @@ relevance_tma_kernel(const __grid_constant__ CUtensorMap tmap, const uint16_t *_
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(TMEM_COLS) : "memory");
 }
 
+// ------------------------------------------------------------ fused blend + relevance
+// R[p][q] = sum_c (sum_j w_pj f_{id_pj}[c]) Q[q][c] without writing the map:
+// persistent CTAs of 13 warps (one per SM).  Producer warps 5-12 blend the
+// pixels of a 16 x 8 screen block (128 pixels = the 128 TMEM lanes), 32
+// channels at a time, straight into a 128-byte-swizzled K-major FP32 stage of
+// a 3-deep ring (the layout a TMA box {32, 128} would write), four pixels
+// per warp-step with 8 lanes per pixel on 16-byte row slices; the entries of
+// the block are staged once per block.  Rows shared by the block's pixels are
+// re-read from L1 while all producers work on the same 32-channel slice.
+// Warp 4 issues kind::tf32 UMMAs of each stage against the resident queries
+// into one of two TMEM accumulators; warps 0-3 drain the other accumulator
+// into R rows.  Same bounded waits, abort flag and drain as the TMA kernel.
+constexpr int FB_THREADS = 416;
+constexpr int FB_STAGES = 3;
+constexpr int FB_PRODUCERS = 8;
+
+__device__ __forceinline__ int64_t fb_pixel(int64_t t, int r, int W, int H, int64_t P) {
+    if (W <= 0) {
+        const int64_t p = t * 128 + r;
+        return p < P ? p : -1;
+    }
+    const int tiles_x = (W + 15) >> 4;
+    const int tx = int(t % tiles_x), ty = int(t / tiles_x);
+    const int x = tx * 16 + (r & 15), y = ty * 8 + (r >> 4);
+    return (x < W && y < H) ? int64_t(y) * W + x : -1;
+}
+
+__device__ __forceinline__ void named_sync_producers() {
+    asm volatile("bar.sync 1, %0;" :: "n"(FB_PRODUCERS * 32) : "memory");
+}
+
+// 4 channels of a row slice, widened to FP32
+template <int DT>
+__device__ __forceinline__ float4 fb_load4(const unsigned char *__restrict__ feat, size_t row_bytes,
+                                           int id, int c) {
+    const unsigned char *ptr = feat + size_t(id) * row_bytes;
+    if (DT == QR_F32) {
+        return __ldg(reinterpret_cast<const float4 *>(ptr + size_t(c) * 4));
+    } else if (DT == QR_BF16) {
+        const uint2 u = __ldg(reinterpret_cast<const uint2 *>(ptr + size_t(c) * 2));
+        return make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xFFFF0000u),
+                           __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xFFFF0000u));
+    } else {
+        const uint32_t u = __ldg(reinterpret_cast<const uint32_t *>(ptr + size_t(c)));
+        const __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2(__nv_fp8x2_storage_t(u & 0xFFFFu), __NV_E4M3);
+        const __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2(__nv_fp8x2_storage_t(u >> 16), __NV_E4M3);
+        const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&lo));
+        const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&hi));
+        return make_float4(a.x, a.y, b.x, b.y);
+    }
+}
+
+template <int DT, int QN>
+__global__ void __launch_bounds__(FB_THREADS, 1)
+blend_relevance_kernel(const unsigned char *__restrict__ feat, const float *__restrict__ fscale,
+                       int64_t n_gauss, int C, const int32_t *__restrict__ ids,
+                       const float *__restrict__ wts, const uint8_t *__restrict__ cnt, int64_t P,
+                       int K, int W, int H, const uint16_t *__restrict__ queries,
+                       float *__restrict__ out, int *__restrict__ status) {
+    constexpr uint32_t TMEM_COLS = 2 * QN < 32 ? 32 : 2 * QN;
+    constexpr int ESZ = DT == QR_F32 ? 4 : DT == QR_BF16 ? 2 : 1;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *base = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const int nsl = C / 32;
+    unsigned char *sA = base;                                        // FB_STAGES x 16 KB
+    unsigned char *sB = sA + FB_STAGES * A_TILE;                     // nsl x QN x 128 B
+    int32_t *s_id = reinterpret_cast<int32_t *>(sB + size_t(nsl) * QN * 128);   // [128][K]
+    float *s_w = reinterpret_cast<float *>(s_id + 128 * K);                       // [128][K]
+    uint64_t *full = reinterpret_cast<uint64_t *>(s_w + 128 * K);
+    uint64_t *empty = full + FB_STAGES;
+    uint64_t *tfull = empty + FB_STAGES;
+    uint64_t *tempty = tfull + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tempty + 2);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    uint32_t *s_count = reinterpret_cast<uint32_t *>(tmem_slot + 2);   // [0] MMA stages issued
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    for (int i = threadIdx.x; i < QN * C; i += FB_THREADS) {
+        const int n = i / C, c = i - n * C;
+        const int sl = c >> 5, cc = c & 31;
+        const float v = __uint_as_float(uint32_t(queries[size_t(n) * C + c]) << 16);
+        *reinterpret_cast<float *>(sB + size_t(sl) * QN * 128 + n * 128 +
+                                   (((cc >> 2) ^ (n & 7)) << 4) + (cc & 3) * 4) = v;
+    }
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < FB_STAGES; ++st) {
+            mbar_init(&full[st], FB_PRODUCERS);
+            mbar_init(&empty[st], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&tfull[a], 1);
+            mbar_init(&tempty[a], 4);
+        }
+        *abort_flag = 0;
+        s_count[0] = 0u;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 4) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_u32(tmem_slot)), "r"(TMEM_COLS) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const int64_t tiles = (W > 0) ? int64_t((W + 15) >> 4) * ((H + 7) >> 3) : (P + 127) / 128;
+    const size_t row_bytes = size_t(C) * ESZ;
+
+    if (warp >= 5) {
+        // producers: blend 128 pixels x 32 channels per stage
+        const int pw = warp - 5, ptid = threadIdx.x - 5 * 32;
+        const int g = lane >> 3, c4 = lane & 7;
+        uint32_t it = 0;
+        bool ok = true;
+        // every producer warp runs the same number of blocks and named barriers,
+        // also after an abort (it then skips the waits and the work), so no
+        // warp can be left waiting at a barrier
+        for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+            named_sync_producers();            // the previous block's entries are no longer read
+            for (int e = ptid; e < 128 * K && ok; e += FB_PRODUCERS * 32) {
+                const int r = e / K, j = e - r * K;
+                const int64_t p = fb_pixel(t, r, W, H, P);
+                int id = -1;
+                float w = 0.f;
+                if (p >= 0 && j < int(cnt[p])) {
+                    id = ids[p * K + j];
+                    w = wts[p * K + j];
+                    // an id out of range contributes nothing (as in the blend)
+                    if (uint64_t(int64_t(id)) >= uint64_t(n_gauss)) { id = 0; w = 0.f; }
+                    else if (DT == QR_FP8E4M3) w *= fscale[id];
+                }
+                s_id[e] = id;
+                s_w[e] = w;
+            }
+            named_sync_producers();
+            for (int sl = 0; sl < nsl && ok; ++sl) {
+                const int st = int(it % FB_STAGES);
+                int wok = 1;
+                if (lane == 0) wok = lane_wait(&empty[st], ((it / FB_STAGES) & 1u) ^ 1u, abort_flag) ? 1 : 0;
+                wok = __shfl_sync(0xffffffffu, wok, 0);
+                if (!wok) { ok = false; break; }
+                unsigned char *stage = sA + st * A_TILE;
+                const int c = sl * 32 + c4 * 4;
+#pragma unroll
+                for (int pass = 0; pass < 4; ++pass) {
+                    const int r = pw * 16 + pass * 4 + g;
+                    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+                    for (int j = 0; j < K; ++j) {
+                        const int id = s_id[r * K + j];
+                        if (id < 0) break;            // entries are a prefix of the pixel's K
+                        const float w = s_w[r * K + j];
+                        const float4 f = fb_load4<DT>(feat, row_bytes, id, c);
+                        acc.x = fmaf(w, f.x, acc.x);
+                        acc.y = fmaf(w, f.y, acc.y);
+                        acc.z = fmaf(w, f.z, acc.z);
+                        acc.w = fmaf(w, f.w, acc.w);
+                    }
+                    *reinterpret_cast<float4 *>(stage + swz(r, c4)) = acc;
+                }
+                fence_async_smem();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&full[st]);
+                ++it;
+            }
+        }
+    } else if (warp == 4 && lane == 0) {
+        // MMA issuer
+        constexpr uint32_t idesc = make_idesc_tf32(128, QN);
+        uint32_t it = 0, tl = 0;
+        bool ok = true;
+        for (int64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++tl) {
+            const uint32_t acc = tl & 1u;
+            if (!lane_wait(&tempty[acc], ((tl >> 1) & 1u) ^ 1u, abort_flag)) break;
+            tc_fence_after();
+            for (int sl = 0; sl < nsl; ++sl) {
+                const int st = int(it % FB_STAGES);
+                if (!lane_wait(&full[st], (it / FB_STAGES) & 1u, abort_flag)) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t a0 = smem_u32(sA + st * A_TILE);
+                const uint32_t b0 = smem_u32(sB + size_t(sl) * QN * 128);
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    umma_tf32(tmem + acc * QN, make_desc(a0 + k * 32), make_desc(b0 + k * 32), idesc,
+                              (sl > 0 || k > 0) ? 1u : 0u);
+                umma_commit(&empty[st]);
+                ++it;
+            }
+            if (ok) umma_commit(&tfull[acc]);
+        }
+        s_count[0] = it;
+    } else if (warp < 4) {
+        // epilogue: warp q reads TMEM lanes 32 q .. (block rows 32 q .. 32 q + 31)
+        const int q = warp;
+        uint32_t tl = 0;
+        for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x, ++tl) {
+            const uint32_t acc = tl & 1u;
+            int ok = 1;
+            if (lane == 0) ok = lane_wait(&tfull[acc], (tl >> 1) & 1u, abort_flag) ? 1 : 0;
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) break;
+            tc_fence_after();
+            const int64_t p = fb_pixel(t, q * 32 + lane, W, H, P);
+            const uint32_t taddr = tmem + (uint32_t(q * 32) << 16) + acc * QN;
+#pragma unroll
+            for (int c = 0; c < QN; c += 16) {
+                float v[16];
+                tmem_ld16(taddr + uint32_t(c), v);
+                if (p >= 0) {
+                    float4 *o = reinterpret_cast<float4 *>(out + p * QN + c);
+                    o[0] = make_float4(v[0], v[1], v[2], v[3]);
+                    o[1] = make_float4(v[4], v[5], v[6], v[7]);
+                    o[2] = make_float4(v[8], v[9], v[10], v[11]);
+                    o[3] = make_float4(v[12], v[13], v[14], v[15]);
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[acc]);
+        }
+    }
+    __syncthreads();
+    if (*abort_flag) {
+        if (threadIdx.x == 0) atomicExch(status, int(QR_ERR_DEVICE_TIMEOUT));
+        // the MMAs of the last issued stage must have finished reading shared memory
+        if (warp == 4 && lane == 0 && s_count[0] > 0) {
+            const uint32_t last = s_count[0] - 1;
+            mbar_wait(&empty[last % FB_STAGES], (last / FB_STAGES) & 1u);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 4)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(TMEM_COLS) : "memory");
+}
+
+size_t fb_smem_bytes(int Q, int C, int K) {
+    return 1024 + size_t(FB_STAGES) * A_TILE + size_t(C) * Q * 4 + size_t(128) * K * 8 + 256;
+}
+
+template <int DT, int QN>
+cudaError_t run_fused(const void *feat, const float *scale, int64_t n_gauss, int C,
+                      const int32_t *ids, const float *w, const uint8_t *cnt, int64_t P, int K,
+                      int W, int H, const uint16_t *q, float *out, int *status, cudaStream_t s) {
+    const size_t smem = fb_smem_bytes(QN, C, K);
+    cudaError_t e = cudaFuncSetAttribute(blend_relevance_kernel<DT, QN>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t tiles = (W > 0) ? int64_t((W + 15) >> 4) * ((H + 7) >> 3) : (P + 127) / 128;
+    const int grid = int(tiles < sms ? tiles : sms);
+    blend_relevance_kernel<DT, QN><<<grid, FB_THREADS, smem, s>>>(
+        static_cast<const unsigned char *>(feat), scale, n_gauss, C, ids, w, cnt, P, K, W, H, q,
+        out, status);
+    count_launch();
+    return cudaGetLastError();
+}
+
+template <int DT>
+cudaError_t fused_q(const void *feat, const float *scale, int64_t n_gauss, int C, const int32_t *ids,
+                    const float *w, const uint8_t *cnt, int64_t P, int K, int W, int H,
+                    const uint16_t *q, int Q, float *out, int *status, cudaStream_t s) {
+    switch (Q) {
+        case 16: return run_fused<DT, 16>(feat, scale, n_gauss, C, ids, w, cnt, P, K, W, H, q, out, status, s);
+        case 32: return run_fused<DT, 32>(feat, scale, n_gauss, C, ids, w, cnt, P, K, W, H, q, out, status, s);
+        case 64: return run_fused<DT, 64>(feat, scale, n_gauss, C, ids, w, cnt, P, K, W, H, q, out, status, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
 size_t tma_smem_bytes(int Q, int C) {
     return 1024 + size_t(STAGES) * A_TILE + size_t(C) * Q * 4 + 256;
 }
@@ -505,6 +780,26 @@ cudaError_t run(const float *map, const uint16_t *q, int64_t P, int C, float *ou
 }
 
 }  // namespace
+
+bool blend_relevance_supported(qr_dtype dt, int Q, int C, int K) {
+    const int cpv = dt == QR_F32 ? 4 : dt == QR_BF16 ? 8 : 16;
+    if (C < 32 || C % 32 || C % cpv || K < 1 || K > kKMax) return false;
+    if (!(Q == 16 || Q == 32 || Q == 64)) return false;
+    return fb_smem_bytes(Q, C, K) <= 227 * 1024;
+}
+
+cudaError_t launch_blend_relevance(const void *feat, const float *scale, qr_dtype dt, int C,
+                                   int64_t n_gauss, const int32_t *ids, const float *w,
+                                   const uint8_t *cnt, int64_t P, int K, int W, int H,
+                                   const uint16_t *q, int Q, float *out, int *status,
+                                   cudaStream_t s) {
+    switch (dt) {
+        case QR_F32: return fused_q<QR_F32>(feat, scale, n_gauss, C, ids, w, cnt, P, K, W, H, q, Q, out, status, s);
+        case QR_BF16: return fused_q<QR_BF16>(feat, scale, n_gauss, C, ids, w, cnt, P, K, W, H, q, Q, out, status, s);
+        case QR_FP8E4M3: return fused_q<QR_FP8E4M3>(feat, scale, n_gauss, C, ids, w, cnt, P, K, W, H, q, Q, out, status, s);
+    }
+    return cudaErrorInvalidValue;
+}
 
 bool relevance_supported(int Q, int C) {
     if (C < BK || C % BK) return false;

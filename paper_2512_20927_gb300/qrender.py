@@ -104,6 +104,14 @@ SIGNATURES = {
     "qr_cosine_backward": (_S, [ctypes.POINTER(qr_frame), _P, _P, _S, _I32, _P, _P, _P, _P, _P,
                                 _P, _P, _P, _P, _P, _P, _P, ctypes.c_size_t, _P]),
     "qr_relevance": (_S, [_P, _P, _I32, _I32, _I64, _P, _P, _P]),
+    "qr_blend_relevance": (_S, [_P, _P, _S, _I32, _I64, _P, _P, _P, _I64, _I32, _I32, _P, _I32,
+                                _P, _P, _P]),
+    "qr_contrastive_workspace_bytes": (ctypes.c_size_t, [_I64, _I32, _I32]),
+    "qr_contrastive_loss": (_S, [_P, _P, _I32, _I32, _P, _I64, _P, _P, _P, ctypes.c_size_t, _P]),
+    "qr_contrastive_backward_workspace_bytes": (ctypes.c_size_t,
+                                                [ctypes.POINTER(qr_frame), _I32, _I32]),
+    "qr_contrastive_backward": (_S, [ctypes.POINTER(qr_frame), _P, _P, _S, _I32, _P, _P, _P, _P,
+                                     _P, _I32, _P, _P, _P, _P, _P, _P, _P, ctypes.c_size_t, _P]),
     "qr_batch_workspace_bytes": (ctypes.c_size_t, [_I32]),
     "qr_batch_prepare": (_S, [ctypes.POINTER(qr_view), _I32, _P, ctypes.c_size_t,
                               ctypes.POINTER(ctypes.c_uint32), _P]),
@@ -406,6 +414,60 @@ def qr_cosine_loss(feature_map, target, counts, stream=None):
     return out2[0], grad
 
 
+def _aligned_ws(nbytes, dev):
+    torch = _torch()
+    ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
+    return ws, ctypes.c_void_p((ws.data_ptr() + 255) // 256 * 256)
+
+
+def qr_contrastive_loss(feature_map, targets, mask_id, stream=None):
+    """Eq. 2 loss of a [P, C] map against [M, C] mask embeddings, mask_id [P]
+    int32 (-1: not in the loss).  Returns (loss scalar tensor, dL/dF [P, C])."""
+    torch = _torch()
+    P, C = feature_map.shape
+    M = targets.shape[0]
+    dev = feature_map.device
+    nbytes = int(load().qr_contrastive_workspace_bytes(P, M, C))
+    if nbytes == 0:
+        raise QRError(QR_ERR_NOT_SUPPORTED, "qr_contrastive_workspace_bytes")
+    ws, wsp = _aligned_ws(nbytes, dev)
+    out2 = torch.empty(2, dtype=torch.float32, device=dev)
+    grad = torch.empty((P, C), dtype=torch.float32, device=dev)
+    _check(load().qr_contrastive_loss(_ptr(feature_map.contiguous()), _ptr(targets.contiguous()),
+                                      M, C, _ptr(mask_id), P, _ptr(out2), _ptr(grad), wsp, nbytes,
+                                      _stream(stream)), "qr_contrastive_loss")
+    return out2[0], grad
+
+
+def qr_contrastive_backward(fr: Frame, feat, feat_scale, ids, weights, counts, feature_map,
+                            targets, mask_id, want_conic=True, stream=None):
+    """Eq. 2 loss of the rendered map and the backward of the forward of `fr`
+    under it.  Returns (loss scalar tensor, dL/dF [P, C], grad_feat [n, C],
+    grad_opacity [n], grad_conic [n, 3] or None)."""
+    torch = _torch()
+    n = int(fr.frame.n)
+    C = feat.shape[1]
+    M = targets.shape[0]
+    dev = feature_map.device
+    P = feature_map.shape[0]
+    nbytes = int(load().qr_contrastive_backward_workspace_bytes(ctypes.byref(fr.frame), M, C))
+    if nbytes == 0:
+        raise QRError(QR_ERR_NOT_SUPPORTED, "qr_contrastive_backward_workspace_bytes")
+    ws, wsp = _aligned_ws(nbytes, dev)
+    out2 = torch.empty(2, dtype=torch.float32, device=dev)
+    gmap = torch.empty((P, C), dtype=torch.float32, device=dev)
+    gf = torch.empty((n, C), dtype=torch.float32, device=dev)
+    ga = torch.empty(n, dtype=torch.float32, device=dev)
+    gc = torch.empty((n, 3), dtype=torch.float32, device=dev) if want_conic else None
+    _check(load().qr_contrastive_backward(ctypes.byref(fr.frame), _ptr(feat), _ptr(feat_scale),
+                                          _dtype_code(feat), C, _ptr(ids), _ptr(weights),
+                                          _ptr(counts), _ptr(feature_map.contiguous()),
+                                          _ptr(targets.contiguous()), M, _ptr(mask_id),
+                                          _ptr(out2), _ptr(gmap), _ptr(gf), _ptr(ga), _ptr(gc),
+                                          wsp, nbytes, _stream(stream)), "qr_contrastive_backward")
+    return out2[0], gmap, gf, ga, gc
+
+
 def qr_relevance(feature_map, queries_bf16, stream=None):
     """Relevance scores [P, Q] float32 of a [P, C] float32 map against [Q, C] BF16 queries.
 
@@ -418,6 +480,23 @@ def qr_relevance(feature_map, queries_bf16, stream=None):
     status = torch.zeros(1, dtype=torch.int32, device=feature_map.device)
     _check(load().qr_relevance(_ptr(feature_map), _ptr(queries_bf16), Q, C, P, _ptr(out),
                                _ptr(status), _stream(stream)), "qr_relevance")
+    return out, status
+
+
+def qr_blend_relevance(feat, feat_scale, ids, weights, counts, queries_bf16, width=0,
+                       stream=None):
+    """Relevance scores [P, Q] of the blend of (ids, weights, counts) against
+    [Q, C] BF16 queries without writing the map.  Returns (scores, status)."""
+    torch = _torch()
+    P, K = ids.shape
+    C = feat.shape[1]
+    Q = queries_bf16.shape[0]
+    out = torch.empty((P, Q), dtype=torch.float32, device=ids.device)
+    status = torch.zeros(1, dtype=torch.int32, device=ids.device)
+    _check(load().qr_blend_relevance(_ptr(feat), _ptr(feat_scale), _dtype_code(feat), C,
+                                     feat.shape[0], _ptr(ids), _ptr(weights), _ptr(counts), P, K,
+                                     width, _ptr(queries_bf16), Q, _ptr(out), _ptr(status),
+                                     _stream(stream)), "qr_blend_relevance")
     return out, status
 
 

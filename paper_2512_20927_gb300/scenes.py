@@ -218,3 +218,58 @@ def random_selection(seed: int, pixels: int, k: int, n: int, sparsity: float = 0
     s = x.sum(axis=1, keepdims=True)
     w = np.where(s > 0, x / np.where(s > 0, s, 1.0), 0.0).astype(np.float32)
     return ids, w, cnt.astype(np.uint8)
+
+
+def patch_masks(width: int, height: int, m: int, seed: int = 0, unlabeled: float = 0.1) -> np.ndarray:
+    """Synthetic image patches (the masks of Sec. 4.3): a Voronoi partition of
+    the image into m regions around random sites; a fraction `unlabeled` of
+    the pixels (random) belongs to no patch (-1).  Returns mask_id [H*W] int32."""
+    rng = np.random.default_rng(seed)
+    sites = np.stack([rng.uniform(0, width, m), rng.uniform(0, height, m)], 1)
+    ys, xs = np.mgrid[0:height, 0:width]
+    px, py = xs.ravel() + 0.5, ys.ravel() + 0.5
+    best = np.full(px.size, np.inf)
+    mid = np.zeros(px.size, np.int32)
+    for j in range(m):
+        d2 = (px - sites[j, 0]) ** 2 + (py - sites[j, 1]) ** 2
+        closer = d2 < best
+        best[closer] = d2[closer]
+        mid[closer] = j
+    mid[rng.uniform(size=mid.size) < unlabeled] = -1
+    return mid
+
+
+def patch_targets(m: int, channels: int = 512, seed: int = 3) -> np.ndarray:
+    """One CLIP-like embedding per patch: m unit vectors normalise(N(0, I))."""
+    return unit_queries(seed, m, channels)
+
+
+def object_scene(seed: int = 0, n: int = 500_000, channels: int = 512):
+    """An object-centric scene (the object workloads of the paper's LeRF /
+    MipNeRF360 scenes, stood in for by a synthetic object): 70 % of the
+    Gaussians within 1 cm of a unit sphere's surface, 30 % uniform inside it,
+    log-scales N(-4.5, 0.5), opacity sigmoid(N(0.5, 1.5)), C-D unit features.
+    Seen from outside (object_camera), every pixel's Gaussians come from its
+    own patch of the surface, so a frame gathers many distinct feature rows."""
+    rng = np.random.default_rng(seed)
+    n_s = int(round(0.7 * n))
+    d = rng.normal(size=(n_s, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    surf = d * (1.0 + rng.uniform(-0.01, 0.01, size=(n_s, 1)))
+    v = rng.normal(size=(n - n_s, 3))
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    inner = v * rng.uniform(0.0, 1.0, size=(n - n_s, 1)) ** (1.0 / 3.0)
+    mean = np.concatenate([surf, inner])[rng.permutation(n)].astype(np.float32)
+    log_scale = rng.normal(-4.5, 0.5, size=(n, 3)).astype(np.float32)
+    quat = _unit_quats(rng, n)
+    opacity = _sigmoid(rng.normal(0.5, 1.5, size=n)).astype(np.float32)
+    feat = unit_features(rng, n, channels)
+    return Gaussians(mean, log_scale, quat, opacity), feat
+
+
+def object_camera(width: int = 640, height: int = 480, distance: float = 2.6,
+                  hfov_deg: float = 60.0) -> Camera:
+    """Camera at `distance` from the object's centre on -y, looking at it, +z up."""
+    f = hfov_focal(width, hfov_deg)
+    return look_camera((0.0, -distance, 0.3), (0.0, distance, -0.3), (0.0, 0.0, 1.0), width,
+                       height, f, f)

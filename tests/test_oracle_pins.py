@@ -551,3 +551,45 @@ def test_cosine_loss_through_the_render_matches_finite_differences():
         assert abs(ga[i] - fd) <= 1e-4 * max(abs(fd), 1e-3 * np.abs(ga).max()), (i, ga[i], fd)
         checked += 1
     assert checked >= 6
+
+
+# ---------------------------------------------------------------- contrastive loss (Eq. 2)
+def test_contrastive_loss_gradient_matches_finite_differences():
+    rng = np.random.default_rng(31)
+    P, C, M = 40, 12, 5
+    F = rng.normal(size=(P, C))
+    F[3] = 0.0                                   # |F| <= eps: constant normaliser
+    T = rng.normal(size=(M, C))
+    mid = rng.integers(-1, M, P)
+    L, g = oracle.contrastive_loss(F, T, mid)
+    h = 1e-6
+    for p in (0, 1, 2, 5, 7, 11):
+        for c in (0, 4, 11):
+            Fp, Fm = F.copy(), F.copy()
+            Fp[p, c] += h
+            Fm[p, c] -= h
+            fd = (oracle.contrastive_loss(Fp, T, mid)[0] - oracle.contrastive_loss(Fm, T, mid)[0]) / (2 * h)
+            assert abs(fd - g[p, c]) <= 1e-6 * max(1.0, abs(fd)), (p, c, fd, g[p, c])
+    # pixels outside every mask neither count nor get a gradient
+    assert (g[mid < 0] == 0).all()
+
+
+def test_contrastive_loss_scale_invariance_and_two_masks():
+    """Cosine similarity ignores the length of F: L(cF) = L(F) and
+    F . dL/dF_p = 0 on every pixel.  With two masks the denominator of Eq. 2
+    holds the other mask alone, so the pixel's term is s_other - s_own."""
+    rng = np.random.default_rng(32)
+    P, C = 30, 9
+    F = rng.normal(size=(P, C))
+    T = rng.normal(size=(4, C))
+    mid = rng.integers(0, 4, P)
+    L, g = oracle.contrastive_loss(F, T, mid)
+    L2, _ = oracle.contrastive_loss(3.7 * F, T, mid)
+    assert abs(L - L2) <= 1e-13
+    np.testing.assert_allclose((F * g).sum(axis=1), 0.0, atol=1e-15)
+    T2 = T[:2]
+    mid2 = rng.integers(0, 2, P)
+    L, _ = oracle.contrastive_loss(F, T2, mid2)
+    cosv = (F @ T2.T) / (np.linalg.norm(F, axis=1)[:, None] * np.linalg.norm(T2, axis=1)[None, :])
+    want = np.mean([cosv[p, 1 - mid2[p]] - cosv[p, mid2[p]] for p in range(P)])
+    assert abs(L - want) <= 1e-13

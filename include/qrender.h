@@ -228,6 +228,14 @@ qr_status qr_blend(const void *feat, const float *feat_scale, qr_dtype dtype, in
 qr_status qr_dense(const qr_frame *frame, const void *feat, const float *feat_scale,
                    qr_dtype dtype, int32_t C, float *out, float *T_final, qr_stream stream);
 
+/* qr_dense that also counts its work, for measurement: counts [2] device
+ * uint64 (zeroed by the call) receive the blended (pixel, Gaussian) pairs --
+ * each C multiply-adds of useful work -- and the multiply-adds the kernel
+ * executed (rows of 128, 256 or 512 channels; both stay 0 for other widths). */
+qr_status qr_dense_work(const qr_frame *frame, const void *feat, const float *feat_scale,
+                        qr_dtype dtype, int32_t C, float *out, float *T_final, uint64_t *counts,
+                        qr_stream stream);
+
 /* The whole Q-Render forward of one frame: qr_project, qr_sort, qr_select and
  * qr_blend in order on one stream.  ids/weights/counts are kept for a later
  * backward. */
@@ -409,14 +417,16 @@ qr_status qr_relevance(const float *feature_map, const uint16_t *queries_bf16, i
  * rendered features against text embeddings): out[p][q] = sum_c F_p[c] Q[q][c]
  * with F_p = sum_{j < counts[p]} weights[p][j] feat[ids[p][j]] (qr_blend's
  * map), without writing the [P][C] map.  Blocks of 128 pixels (16 x 8 on
- * screen when width > 0, consecutive pixels when width = 0) are blended 32
- * channels at a time into shared memory in FP32 and multiplied on the tensor
- * cores as TF32 (at least 10 mantissa bits of F; the BF16 queries are exact),
- * FP32 accumulation in TMEM.  feat / feat_scale / dtype / ids / weights /
- * counts / P / K / width as in qr_blend; queries_bf16 [Q][C]; out [P][Q]
- * float32.  Q in {16, 32, 64}; C a multiple of 32 with the FP32 queries
- * fitting in shared memory (Q * C * 4 bytes plus 48 KB).  status as in
- * qr_relevance (QR_ERR_DEVICE_TIMEOUT if a bounded wait gives up). */
+ * screen when width > 0, consecutive pixels when width = 0) are blended 128
+ * channels at a time into shared memory with FP32 accumulation, rounded to
+ * BF16 and multiplied on the tensor cores against the BF16 queries with FP32
+ * accumulation in TMEM, so out is within 2^-8 sum_c |F_c q_c| of the exact
+ * product (like qr_relevance's BF16 kernel).  feat / feat_scale / dtype /
+ * ids / weights / counts / P / K / width as in qr_blend (K <= 8);
+ * queries_bf16 [Q][C]; out [P][Q] float32.  Q in {16, 32, 64, 128}; C a
+ * multiple of 128 with the queries fitting in shared memory (Q * C * 2 bytes
+ * plus 90 KB); QR_ERR_NOT_SUPPORTED otherwise.  status as in qr_relevance
+ * (QR_ERR_DEVICE_TIMEOUT if a bounded wait gives up). */
 qr_status qr_blend_relevance(const void *feat, const float *feat_scale, qr_dtype dtype, int32_t C,
                              int64_t n_gauss, const int32_t *ids, const float *weights,
                              const uint8_t *counts, int64_t P, int32_t K, int32_t width,

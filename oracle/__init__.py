@@ -70,7 +70,7 @@ def _declare(L):
     L.or_project.argtypes = [_I64, _P, _P, _P, _P, _D, _P, _P, _P, _P, _P]
     L.or_project.restype = _I
     L.or_render.argtypes = ([_I64, _P, _P, _P, _P, _P, _P, _I, _I, _D, _D, _D, _D, _I64, _P, _I]
-                            + [_P] * 11 + [_I, _P, _P])
+                            + [_P] * 11 + [_I, _P, _P, _P])
     L.or_render.restype = _I
     L.or_backward.argtypes = [_I64, _P, _P, _P, _P, _P, _P, _I, _I, _D, _D, _I64, _P, _P,
                               _P, _P, _P, _P, _P, _P]
@@ -300,6 +300,7 @@ class Rendered:
     members: np.ndarray | None = None
     scale_q: np.ndarray | None = None
     scale_dense: np.ndarray | None = None
+    n_dense: np.ndarray | None = None
 
 
 def all_pixels(width: int, height: int) -> np.ndarray:
@@ -335,14 +336,15 @@ def render(proj: Projected, feat, K: int, pixels, T_min: float = 1e-4,
     mem = np.zeros((m, max_members), np.int32) if max_members > 0 else None
     sq = np.zeros(m) if out_q is not None else None
     sd = np.zeros(m) if out_d is not None else None
+    nd = np.zeros(m, np.int32)
     rc = lib().or_render(n, _ptr(proj.mean2d), _ptr(proj.conic), _ptr(proj.depth),
                          _ptr(proj.alpha), _ptr(proj.valid), _ptr(f), C, K, alpha_min,
                          alpha_max, T_min, tie_eps, m, _ptr(pix), threads,
                          _ptr(out_q), _ptr(ids), _ptr(wq), _ptr(cnt), _ptr(tq), _ptr(out_d),
                          _ptr(tf), _ptr(nmem), _ptr(npro), _ptr(tie), _ptr(mem), max_members,
-                         _ptr(sq), _ptr(sd))
+                         _ptr(sq), _ptr(sd), _ptr(nd))
     assert rc == 0, rc
-    return Rendered(out_q, ids, wq, cnt, tq, out_d, tf, nmem, npro, tie, mem, sq, sd)
+    return Rendered(out_q, ids, wq, cnt, tq, out_d, tf, nmem, npro, tie, mem, sq, sd, nd)
 
 
 def backward(proj: Projected, feat, K: int, pixels, grad_out,

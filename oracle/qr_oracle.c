@@ -388,6 +388,7 @@ typedef struct {
     double *out_dense; double *t_final; int32_t *n_members; int32_t *n_proc; int32_t *tie;
     int32_t *members; int max_members;   /* optional: I(p) in depth order, -1 padded */
     double *scale_q, *scale_dense;       /* optional: sum_j |w_j| max|f_j| (error denominators) */
+    int32_t *n_dense;                    /* optional: entries the dense walk blended */
     int rule;                            /* or_render_rule: RULE_TOPK or RULE_STRATIFIED */
     double *tau_out;                     /* or_render_rule: [npix][K] boundaries (stratified) */
     /* threading */
@@ -833,7 +834,7 @@ static void *render_worker(void *arg)
         }
         /* Eq. 1 */
         int64_t nused = S.len;
-        if (J->out_dense || J->t_final || J->tie) {
+        if (J->out_dense || J->t_final || J->tie || J->n_dense) {
             double Tf = 1.0;
             nused = or_dense_list(S.len, S.a, J->T_min, S.wd, &Tf);
             if (J->t_final) J->t_final[p] = Tf;
@@ -854,6 +855,7 @@ static void *render_worker(void *arg)
                 if (J->scale_dense) J->scale_dense[p] = sc;
             }
         }
+        if (J->n_dense) J->n_dense[p] = (int32_t)nused;
         if (J->tie) J->tie[p] = classify_ties(J, &S, nproc, nused);
     }
     free(S.m); free(S.border); free(S.a); free(S.w); free(S.wd); free(S.sel);
@@ -869,7 +871,8 @@ static void *render_worker(void *arg)
  * n_proc = entries visited by Algorithm 1, tie = near-tie flags, members
  * [npix][max_members] = the first max_members entries of I(p) (-1 padded),
  * scale_q / scale_dense [npix] = sum over blended Gaussians of
- * |weight| * max_c |f_c| (the denominators of the parity error metric).
+ * |weight| * max_c |f_c| (the denominators of the parity error metric),
+ * n_dense [npix] = entries the dense walk blended.
  */
 int or_render(int64_t n, const double *mean2d, const double *conic, const double *depth,
               const double *alpha, const int32_t *valid, const double *feat, int C,
@@ -878,7 +881,7 @@ int or_render(int64_t n, const double *mean2d, const double *conic, const double
               double *out_q, int32_t *ids, double *wq, int32_t *cnt, double *tq,
               double *out_dense, double *t_final, int32_t *n_members, int32_t *n_proc,
               int32_t *tie, int32_t *members, int max_members, double *scale_q,
-              double *scale_dense)
+              double *scale_dense, int32_t *n_dense)
 {
     if (n < 0 || npix < 0 || K < 1 || nthreads < 1 || (C < 0)) return OR_ERR_ARG;
     render_job_t base;
@@ -891,7 +894,7 @@ int or_render(int64_t n, const double *mean2d, const double *conic, const double
     base.out_dense = out_dense; base.t_final = t_final; base.n_members = n_members;
     base.n_proc = n_proc; base.tie = tie;
     base.members = members; base.max_members = members ? max_members : 0;
-    base.scale_q = scale_q; base.scale_dense = scale_dense;
+    base.scale_q = scale_q; base.scale_dense = scale_dense; base.n_dense = n_dense;
     base.nthreads = nthreads;
     render_job_t *jobs = (render_job_t *)calloc((size_t)nthreads, sizeof(render_job_t));
     pthread_t *th = (pthread_t *)calloc((size_t)nthreads, sizeof(pthread_t));

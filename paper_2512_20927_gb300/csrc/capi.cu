@@ -250,6 +250,21 @@ qr_status qr_dense(const qr_frame *frame, const void *feat, const float *feat_sc
                                   reinterpret_cast<cudaStream_t>(stream)));
 }
 
+qr_status qr_dense_work(const qr_frame *frame, const void *feat, const float *feat_scale,
+                        qr_dtype dtype, int32_t C, float *out, float *T_final, uint64_t *counts,
+                        qr_stream stream) {
+    if (!frame_ok(frame) || !out || !counts) return QR_ERR_INVALID_ARG;
+    qr_status st = check_feat(feat, feat_scale, dtype, C);
+    if (st != QR_OK) return st;
+    if (!aligned16(out)) return QR_ERR_ALIGNMENT;
+    if (!dense_supported(dtype, C)) return QR_ERR_NOT_SUPPORTED;
+    const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(counts, 0, 2 * sizeof(uint64_t), s);
+    if (e != cudaSuccess) return QR_ERR_CUDA;
+    return from_cuda(launch_dense(*frame, feat, feat_scale, dtype, C, out, T_final, s,
+                                  reinterpret_cast<unsigned long long *>(counts)));
+}
+
 qr_status qr_render(qr_frame *frame, const float *mean, const float *log_scale,
                     const float *quat, const float *opacity, const void *feat,
                     const float *feat_scale, qr_dtype dtype, int32_t C, int32_t *ids,

@@ -194,6 +194,253 @@ dense_kernel(const float4 *__restrict__ rec_m, const float4 *__restrict__ rec_w,
     if (T_final && blockIdx.y == 0 && inside) T_final[int64_t(py) * W + px] = T;
 }
 
+// ------------------------------------------------------------------ sub-tile kernel
+// One CTA (512 threads) renders a 64-pixel sub-tile of a screen tile (16x4,
+// 8x8 or 32x2) over all C channels (C = 64 CH, CH = 2, 4 or 8), so each
+// pixel's alpha' / T walk runs once.  Per batch of 64 list entries:
+//   1. the records are staged and two warps cull them against the sub-tile's
+//      box of pixel centres (the conservative test of the selection);
+//   2. 64 threads walk their pixel over the survivors in list order (the
+//      same scalar FP32 recurrence as dense_kernel) and write w = T alpha'
+//      into W[survivor][pixel];
+//   3. survivors with a nonzero weight anywhere in the sub-tile are kept, in
+//      list order, and only their feature rows are staged (FP32, decoded);
+//   4. warps 2g and 2g+1 accumulate pixel group g (a 4x2 block of 8 pixels)
+//      over all channels: per kept entry 8 weights and CH features per
+//      thread, 8 CH FMAs; an entry whose 8 weights are all zero is skipped
+//      by the whole warp.
+// Zero weights add nothing (fmaf(0, f, acc) == acc), so the result equals
+// dense_kernel's bit for bit.  stats (nullable): [0] += blended (pixel,
+// Gaussian) pairs, [1] += executed (8-pixel group, entry) pairs.
+constexpr int S_THREADS = 512;
+constexpr int S_PIX = 64;
+constexpr int S_BATCH = 64;
+
+template <int DT, int CH>
+__global__ void __launch_bounds__(S_THREADS, 1)
+dense_sub_kernel(const float4 *__restrict__ rec_m, const float4 *__restrict__ rec_w,
+                 const float *__restrict__ rec_a, const float *__restrict__ rec_h,
+                 const uint32_t *__restrict__ isect_gid, const uint2 *__restrict__ ranges,
+                 const unsigned char *__restrict__ feat, const float *__restrict__ fscale, int C,
+                 int W, int H, int tile_w, int tiles_x, float alpha_min, float alpha_max,
+                 float T_min, float *__restrict__ out, float *__restrict__ T_final,
+                 unsigned long long *__restrict__ stats) {
+    constexpr int CPV = Cpv<DT>::v;
+    constexpr int ESZ = DT == QR_F32 ? 4 : DT == QR_BF16 ? 2 : 1;
+    constexpr unsigned FULL = 0xffffffffu;
+    __shared__ float4 s_m[S_BATCH];
+    __shared__ float4 s_c[S_BATCH];
+    __shared__ float s_a[S_BATCH];
+    __shared__ float s_h[S_BATCH];
+    __shared__ uint32_t s_g[S_BATCH];
+    __shared__ int s_surv[S_BATCH];       // survivor -> staged entry
+    __shared__ int s_used[S_BATCH];       // kept -> survivor
+    __shared__ int s_ns, s_nu, s_cnt0;
+    __shared__ float s_box[4];
+    __shared__ __align__(16) float s_W[S_BATCH][S_PIX];
+    extern __shared__ __align__(16) float s_F[];     // [S_BATCH][C]
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tile = blockIdx.x >> 2, sub = blockIdx.x & 3;
+    const int tx = tile % tiles_x, ty = tile / tiles_x;
+    const int tile_h = 256 / tile_w, sub_h = S_PIX / tile_w;
+    const int gx_n = tile_w / 4;                       // pixel groups across
+    // pixel slot ps = 8 g + i  ->  (lx, ly) in the sub-tile
+    auto slot_xy = [&](int ps, int &x, int &y) {       // groups of 4 x 2 pixels
+        const int g = ps >> 3, i = ps & 7;
+        x = tx * tile_w + (g % gx_n) * 4 + (i & 3);
+        y = ty * tile_h + sub * sub_h + (g / gx_n) * 2 + (i >> 2);
+    };
+    const uint2 range = ranges[tile];
+    // the walker's pixel
+    int px = 0, py = 0;
+    if (tid < S_PIX) slot_xy(tid, px, py);
+    const bool walker = tid < S_PIX;
+    const bool inside = walker && px < W && py < H;
+    const float ux = float(px) + 0.5f, uy = float(py) + 0.5f;
+    if (tid < 32) {
+        // the sub-tile's box of pixel centres (clipped to the image)
+        float bx0 = 1e30f, bx1 = -1e30f, by0 = 1e30f, by1 = -1e30f;
+        for (int ps = lane; ps < S_PIX; ps += 32) {
+            int x, y;
+            slot_xy(ps, x, y);
+            const float cx = float(x) + 0.5f, cy = float(y) + 0.5f;
+            bx0 = fminf(bx0, cx); bx1 = fmaxf(bx1, cx); by0 = fminf(by0, cy); by1 = fmaxf(by1, cy);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            bx0 = fminf(bx0, __shfl_xor_sync(FULL, bx0, o));
+            bx1 = fmaxf(bx1, __shfl_xor_sync(FULL, bx1, o));
+            by0 = fminf(by0, __shfl_xor_sync(FULL, by0, o));
+            by1 = fmaxf(by1, __shfl_xor_sync(FULL, by1, o));
+        }
+        if (lane == 0) { s_box[0] = bx0; s_box[1] = bx1; s_box[2] = by0; s_box[3] = by1; }
+    }
+    // accumulation roles: two warps per 8-pixel group; thread t of the group
+    // owns the channel pairs 2 t + 128 k (k < CH / 2), so a warp's shared-memory
+    // reads and global writes are consecutive 8-byte pairs
+    const int g = warp >> 1;
+    const int c0 = (tid & 63) * 2;
+    float acc[8][CH];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int c = 0; c < CH; ++c) acc[i][c] = 0.f;
+    float T = 1.0f;
+    bool done = !inside;
+    unsigned long long n_blend = 0, n_exec = 0;
+    const size_t row_bytes = size_t(C) * ESZ;
+    __syncthreads();
+
+    for (uint32_t b = range.x; b < range.y; b += S_BATCH) {
+        if (__syncthreads_count(done || !walker) == S_THREADS) break;
+        const int nb = int(min(uint32_t(S_BATCH), range.y - b));
+        // 1. stage and cull
+        if (tid < S_BATCH) {
+            bool pass = false;
+            if (tid < nb) {
+                const uint32_t gid = isect_gid[b + tid];
+                const float4 mm = rec_m[gid], cc = rec_w[gid];
+                const float hh = rec_h[gid];
+                s_g[tid] = gid;
+                s_m[tid] = mm;
+                s_c[tid] = cc;
+                s_a[tid] = rec_a[gid];
+                s_h[tid] = hh;
+                pass = !(box_min_half_q(mm, cc, s_box[0], s_box[1], s_box[2], s_box[3]) * 0.999f >
+                         hh + 1e-3f);
+            }
+            const unsigned bal = __ballot_sync(FULL, pass);
+            const int pos = __popc(bal & ((1u << lane) - 1u));
+            // warp 1's survivors follow warp 0's
+            if (warp == 0 && lane == 0) s_cnt0 = __popc(bal);
+            asm volatile("bar.sync 2, 64;" ::: "memory");
+            const int base = warp == 0 ? 0 : s_cnt0;
+            if (pass) s_surv[base + pos] = tid;
+            if (warp == 1 && lane == 0) s_ns = s_cnt0 + __popc(bal);
+        }
+        __syncthreads();
+        const int ns = s_ns;
+        // 2. the walk: W[survivor][pixel slot]
+        if (walker) {
+            for (int sv = 0; sv < ns; ++sv) {
+                const int j = s_surv[sv];
+                float w = 0.f;
+                if (!done) {
+                    const PixelTerm pt = eval_half_q(ux, uy, s_m[j], s_c[j]);
+                    const float a = pt.half_q > s_h[j] ? 0.f : eval_alpha(s_a[j], pt.half_q, alpha_max);
+                    if (a >= alpha_min) {
+                        const float Tt = T * (1.0f - a);
+                        if (T_min > 0.f && Tt < T_min) {
+                            done = true;
+                        } else {
+                            w = T * a;
+                            T = Tt;
+                            ++n_blend;
+                        }
+                    }
+                }
+                s_W[sv][tid] = w;
+            }
+        }
+        __syncthreads();
+        // 3. survivors with a nonzero weight, in list order
+        if (warp == 0) {
+            int nu = 0;
+            for (int s0 = 0; s0 < ns; s0 += 32) {
+                const int sv = s0 + lane;
+                bool used = false;
+                if (sv < ns) {
+                    const float4 *wr = reinterpret_cast<const float4 *>(s_W[sv]);
+#pragma unroll
+                    for (int q = 0; q < S_PIX / 4; ++q) {
+                        const float4 t = wr[q];
+                        used |= (t.x != 0.f) | (t.y != 0.f) | (t.z != 0.f) | (t.w != 0.f);
+                    }
+                }
+                const unsigned bal = __ballot_sync(FULL, used);
+                if (used) s_used[nu + __popc(bal & ((1u << lane) - 1u))] = sv;
+                nu += __popc(bal);
+            }
+            if (lane == 0) s_nu = nu;
+        }
+        __syncthreads();
+        const int nu = s_nu;
+        // 4. stage the kept rows (decoded to FP32)
+        {
+            const int vpr = C / CPV;                   // 16-byte vectors per row
+            for (int i = tid; i < nu * vpr; i += S_THREADS) {
+                const int u = i / vpr, v = i - u * vpr;
+                const uint32_t gid = s_g[s_surv[s_used[u]]];
+                const uint4 x = __ldg(reinterpret_cast<const uint4 *>(feat + size_t(gid) * row_bytes +
+                                                                       size_t(v) * 16));
+                float tmp[CPV];
+                widen16<DT>(x, DT == QR_FP8E4M3 ? fscale[gid] : 1.f, tmp);
+#pragma unroll
+                for (int q = 0; q < CPV; q += 4)
+                    *reinterpret_cast<float4 *>(s_F + size_t(u) * C + v * CPV + q) =
+                        make_float4(tmp[q], tmp[q + 1], tmp[q + 2], tmp[q + 3]);
+            }
+        }
+        __syncthreads();
+        // 5. accumulate: warp-uniform skip of entries with no weight in the group
+        for (int u = 0; u < nu; ++u) {
+            const float4 *wr = reinterpret_cast<const float4 *>(&s_W[s_used[u]][g * 8]);
+            const float4 wa = wr[0], wb = wr[1];
+            const float wv[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+            const bool any = (wa.x != 0.f) | (wa.y != 0.f) | (wa.z != 0.f) | (wa.w != 0.f) |
+                             (wb.x != 0.f) | (wb.y != 0.f) | (wb.z != 0.f) | (wb.w != 0.f);
+            if (!any) continue;
+            ++n_exec;
+            float fv[CH];
+#pragma unroll
+            for (int k = 0; k < CH / 2; ++k) {
+                const float2 t = *reinterpret_cast<const float2 *>(s_F + size_t(u) * C + 128 * k + c0);
+                fv[2 * k] = t.x;
+                fv[2 * k + 1] = t.y;
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int c = 0; c < CH; ++c) acc[i][c] = fmaf(wv[i], fv[c], acc[i][c]);
+        }
+    }
+    // write the sub-tile
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        int x, y;
+        slot_xy(g * 8 + i, x, y);
+        if (x < W && y < H) {
+            float *o = out + (int64_t(y) * W + x) * C + c0;
+#pragma unroll
+            for (int k = 0; k < CH / 2; ++k)
+                *reinterpret_cast<float2 *>(o + 128 * k) = make_float2(acc[i][2 * k], acc[i][2 * k + 1]);
+        }
+    }
+    if (T_final && inside) T_final[int64_t(py) * W + px] = T;
+    if (stats) {
+        // executed FMAs (a warp's entries x 32 lanes x 8 pixels x CH) and blended pairs
+        if (lane == 0) atomicAdd(&stats[1], n_exec * 32ull * 8ull * CH);
+        if (walker) atomicAdd(&stats[0], n_blend);
+    }
+}
+
+template <int DT, int CH>
+cudaError_t run_sub(const qr_frame &f, const void *feat, const float *scale, int C, float *out,
+                    float *T_final, unsigned long long *stats, cudaStream_t s) {
+    const size_t dyn = size_t(S_BATCH) * C * 4;
+    cudaError_t e = cudaFuncSetAttribute(dense_sub_kernel<DT, CH>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(dyn));
+    if (e != cudaSuccess) return e;
+    dense_sub_kernel<DT, CH><<<unsigned(num_tiles(f)) * 4, S_THREADS, dyn, s>>>(
+        slot<float4>(f, S_REC_M), slot<float4>(f, S_REC_C), slot<float>(f, S_REC_A),
+        slot<float>(f, S_REC_H), slot<uint32_t>(f, S_IGID), slot<uint2>(f, S_RANGES),
+        static_cast<const unsigned char *>(feat), scale, C, f.camera.width, f.camera.height,
+        f.params.tile_w, f.tiles_x, f.params.alpha_min, f.params.alpha_max, f.params.T_min, out,
+        T_final, stats);
+    count_launch();
+    return cudaGetLastError();
+}
+
 template <int DT, int CC, int PX, int CH>
 cudaError_t run(const qr_frame &f, const void *feat, const float *scale, int C, float *out,
                 float *T_final, cudaStream_t s) {
@@ -210,8 +457,12 @@ cudaError_t run(const qr_frame &f, const void *feat, const float *scale, int C, 
 
 template <int DT>
 cudaError_t dispatch(const qr_frame &f, const void *feat, const float *scale, int C, float *out,
-                     float *T_final, cudaStream_t s) {
+                     float *T_final, unsigned long long *stats, cudaStream_t s) {
     constexpr int cpv = Cpv<DT>::v;
+    // wide rows: the sub-tile kernel (one walk per pixel, culled and skipped entries)
+    if (C == 512) return run_sub<DT, 8>(f, feat, scale, C, out, T_final, stats, s);
+    if (C == 256) return run_sub<DT, 4>(f, feat, scale, C, out, T_final, stats, s);
+    if (C == 128 && cpv <= 8) return run_sub<DT, 2>(f, feat, scale, C, out, T_final, stats, s);
     if (C % 64 == 0) return run<DT, 64, 8, 8>(f, feat, scale, C, out, T_final, s);
     if (C % 32 == 0) return run<DT, 32, 8, 4>(f, feat, scale, C, out, T_final, s);
     if (C % 16 == 0) return run<DT, 16, 4, 4>(f, feat, scale, C, out, T_final, s);
@@ -230,12 +481,13 @@ bool dense_supported(qr_dtype dt, int C) {
 }
 
 cudaError_t launch_dense(const qr_frame &f, const void *feat, const float *scale, qr_dtype dt,
-                         int C, float *out, float *T_final, cudaStream_t s) {
+                         int C, float *out, float *T_final, cudaStream_t s,
+                         unsigned long long *stats) {
     if (num_tiles(f) == 0) return cudaSuccess;
     switch (dt) {
-        case QR_F32: return dispatch<QR_F32>(f, feat, scale, C, out, T_final, s);
-        case QR_BF16: return dispatch<QR_BF16>(f, feat, scale, C, out, T_final, s);
-        case QR_FP8E4M3: return dispatch<QR_FP8E4M3>(f, feat, scale, C, out, T_final, s);
+        case QR_F32: return dispatch<QR_F32>(f, feat, scale, C, out, T_final, stats, s);
+        case QR_BF16: return dispatch<QR_BF16>(f, feat, scale, C, out, T_final, stats, s);
+        case QR_FP8E4M3: return dispatch<QR_FP8E4M3>(f, feat, scale, C, out, T_final, stats, s);
     }
     return cudaErrorInvalidValue;
 }

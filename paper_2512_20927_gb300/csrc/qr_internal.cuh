@@ -81,8 +81,11 @@ cudaError_t launch_project(const qr_frame &f, const float *mean, const float *lo
 cudaError_t launch_sort(const qr_frame &f, cudaStream_t s);
 cudaError_t launch_select(const qr_frame &f, int32_t *ids, float *w, uint8_t *cnt,
                           cudaStream_t s);
+// stats (nullable, wide rows only): [0] += blended (pixel, Gaussian) pairs,
+// [1] += executed (8-pixel group, entry) pairs of the accumulation
 cudaError_t launch_dense(const qr_frame &f, const void *feat, const float *scale, qr_dtype dt,
-                         int C, float *out, float *T_final, cudaStream_t s);
+                         int C, float *out, float *T_final, cudaStream_t s,
+                         unsigned long long *stats = nullptr);
 // rule: 1 = top-K, 2 = Stratified-K (qr_rule); tau [P][K] nullable (stratified boundaries)
 cudaError_t launch_select_rule(const qr_frame &f, int rule, int32_t *ids, float *w, uint8_t *cnt,
                                float *tau, cudaStream_t s);

@@ -456,20 +456,33 @@ relevance_tma_kernel(const __grid_constant__ CUtensorMap tmap, const uint16_t *_
 }
 
 // ------------------------------------------------------------ fused blend + relevance
-// R[p][q] = sum_c (sum_j w_pj f_{id_pj}[c]) Q[q][c] without writing the map:
-// persistent CTAs of 13 warps (one per SM).  Producer warps 5-12 blend the
-// pixels of a 16 x 8 screen block (128 pixels = the 128 TMEM lanes), 32
-// channels at a time, straight into a 128-byte-swizzled K-major FP32 stage of
-// a 3-deep ring (the layout a TMA box {32, 128} would write), four pixels
-// per warp-step with 8 lanes per pixel on 16-byte row slices; the entries of
-// the block are staged once per block.  Rows shared by the block's pixels are
-// re-read from L1 while all producers work on the same 32-channel slice.
-// Warp 4 issues kind::tf32 UMMAs of each stage against the resident queries
-// into one of two TMEM accumulators; warps 0-3 drain the other accumulator
-// into R rows.  Same bounded waits, abort flag and drain as the TMA kernel.
-constexpr int FB_THREADS = 416;
-constexpr int FB_STAGES = 3;
-constexpr int FB_PRODUCERS = 8;
+// R[p][q] = sum_c (sum_j w_pj f_{id_pj}[c]) Q[q][c] without writing the map.
+// Persistent CTAs of 13 warps, one per SM; a block is 16 x 8 screen pixels
+// (the 128 TMEM lanes), in 2 x 2 pixel groups.
+//   * Producer warps 5-20 own two groups each.  Per block, a warp reads its
+//     groups' entries once (lane m K + j = entry j of pixel m, so K <= 8),
+//     merges equal ids with __match_any_sync and keeps, per group, the list of
+//     distinct rows and each row's four pixel weights in shared memory.  Then,
+//     128 channels at a time, it reads each distinct row once (one warp-wide
+//     512-byte load), accumulates the four pixels in FP32 in entry order per
+//     pixel (eight rows in flight), rounds them to BF16 and writes them into
+//     a 128-byte-swizzled K-major stage (two 64-channel slices) of a ring
+//     (2 stages: a deeper ring costs L1 capacity the row reads need) -- the
+//     layout the fallback relevance kernel stages.
+//   * Warp 4 issues kind::f16 UMMAs (BF16 x BF16, FP32 accumulation) of each
+//     stage against the resident BF16 queries into one of two TMEM
+//     accumulators; warps 0-3 drain the other accumulator into R.
+// Each producer warp reads only its own groups' tables, so the producers
+// share nothing but the ring.  Long waits back off with __nanosleep so the
+// waiting warps leave issue slots to the producers.  Same bounded waits,
+// abort flag and drain as the other kernels.
+constexpr int FB_PRODUCERS = 16;
+constexpr int FB_THREADS = (5 + FB_PRODUCERS) * 32;   // 4 epilogue warps, 1 MMA warp, producers
+constexpr int FB_MAX_STAGES = 2;
+constexpr int FB_GPW = 32 / FB_PRODUCERS;             // 2 x 2 groups per producer warp
+constexpr int FB_ROWS = 8;                            // row loads in flight per lane
+constexpr int FB_CHUNK = 128;                        // channels per stage
+constexpr int FB_STAGE_BYTES = 128 * FB_CHUNK * 2;    // 32 KB (two 64-channel BF16 slices)
 
 __device__ __forceinline__ int64_t fb_pixel(int64_t t, int r, int W, int H, int64_t P) {
     if (W <= 0) {
@@ -482,11 +495,30 @@ __device__ __forceinline__ int64_t fb_pixel(int64_t t, int r, int W, int H, int6
     return (x < W && y < H) ? int64_t(y) * W + x : -1;
 }
 
-__device__ __forceinline__ void named_sync_producers() {
-    asm volatile("bar.sync 1, %0;" :: "n"(FB_PRODUCERS * 32) : "memory");
+// block row (TMEM lane) of pixel m of 2 x 2 group gi (8 groups across, 4 down)
+__device__ __forceinline__ int fb_row(int gi, int m) {
+    return (2 * (gi >> 3) + (m >> 1)) * 16 + 2 * (gi & 7) + (m & 1);
 }
 
-// 4 channels of a row slice, widened to FP32
+// Bounded wait with backoff; false on timeout (sets the abort flag).
+__device__ __forceinline__ bool lane_wait_sleep(uint64_t *bar, uint32_t parity,
+                                                volatile int *abort_flag) {
+    if (*abort_flag) return false;
+    const uint32_t a = smem_u32(bar);
+    for (unsigned i = 0; i < kSpinLimit / 16; ++i) {
+        uint32_t done;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(done) : "r"(a), "r"(parity) : "memory");
+        if (done) return true;
+        __nanosleep(64);
+    }
+    *abort_flag = 1;
+    return false;
+}
+
+// 4 channels of a row at channel c, widened to FP32 (the lane's share of a
+// 128-channel chunk)
 template <int DT>
 __device__ __forceinline__ float4 fb_load4(const unsigned char *__restrict__ feat, size_t row_bytes,
                                            int id, int c) {
@@ -513,32 +545,34 @@ blend_relevance_kernel(const unsigned char *__restrict__ feat, const float *__re
                        int64_t n_gauss, int C, const int32_t *__restrict__ ids,
                        const float *__restrict__ wts, const uint8_t *__restrict__ cnt, int64_t P,
                        int K, int W, int H, const uint16_t *__restrict__ queries,
-                       float *__restrict__ out, int *__restrict__ status) {
+                       float *__restrict__ out, int *__restrict__ status, int FB_STAGES) {
     constexpr uint32_t TMEM_COLS = 2 * QN < 32 ? 32 : 2 * QN;
     constexpr int ESZ = DT == QR_F32 ? 4 : DT == QR_BF16 ? 2 : 1;
+    constexpr unsigned FULL = 0xffffffffu;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *base = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    const int nsl = C / 32;
-    unsigned char *sA = base;                                        // FB_STAGES x 16 KB
-    unsigned char *sB = sA + FB_STAGES * A_TILE;                     // nsl x QN x 128 B
-    int32_t *s_id = reinterpret_cast<int32_t *>(sB + size_t(nsl) * QN * 128);   // [128][K]
-    float *s_w = reinterpret_cast<float *>(s_id + 128 * K);                       // [128][K]
-    uint64_t *full = reinterpret_cast<uint64_t *>(s_w + 128 * K);
-    uint64_t *empty = full + FB_STAGES;
-    uint64_t *tfull = empty + FB_STAGES;
+    const int nchunk = C / FB_CHUNK;
+    const int nslices = C / BK;                                      // 64-channel query slices
+    unsigned char *sA = base;                                        // FB_STAGES x 32 KB
+    unsigned char *sB = sA + FB_STAGES * FB_STAGE_BYTES;             // nslices x QN x 128 B
+    int32_t *t_id = reinterpret_cast<int32_t *>(sB + size_t(nslices) * QN * 128);   // [32 groups][32]
+    float4 *t_w = reinterpret_cast<float4 *>(t_id + 32 * 32);                         // [32][32] weights of the 4 pixels
+    int32_t *t_n = reinterpret_cast<int32_t *>(t_w + 32 * 32);                        // [32] distinct rows per group
+    uint64_t *full = reinterpret_cast<uint64_t *>(t_n + 32);
+    uint64_t *empty = full + FB_MAX_STAGES;
+    uint64_t *tfull = empty + FB_MAX_STAGES;
     uint64_t *tempty = tfull + 2;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tempty + 2);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
     uint32_t *s_count = reinterpret_cast<uint32_t *>(tmem_slot + 2);   // [0] MMA stages issued
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-    for (int i = threadIdx.x; i < QN * C; i += FB_THREADS) {
-        const int n = i / C, c = i - n * C;
-        const int sl = c >> 5, cc = c & 31;
-        const float v = __uint_as_float(uint32_t(queries[size_t(n) * C + c]) << 16);
-        *reinterpret_cast<float *>(sB + size_t(sl) * QN * 128 + n * 128 +
-                                   (((cc >> 2) ^ (n & 7)) << 4) + (cc & 3) * 4) = v;
+    // queries -> swizzled K-major BF16 slices of 64 channels (16-byte chunks copied as they are)
+    for (int i = threadIdx.x; i < nslices * QN * 8; i += FB_THREADS) {
+        const int sl = i / (QN * 8), rem = i % (QN * 8), n = rem >> 3, c = rem & 7;
+        const uint4 v = *reinterpret_cast<const uint4 *>(queries + size_t(n) * C + sl * BK + c * 8);
+        *reinterpret_cast<uint4 *>(sB + size_t(sl) * QN * 128 + swz(n, c)) = v;
     }
     if (threadIdx.x == 0) {
         for (int st = 0; st < FB_STAGES; ++st) {
@@ -567,55 +601,92 @@ blend_relevance_kernel(const unsigned char *__restrict__ feat, const float *__re
     const size_t row_bytes = size_t(C) * ESZ;
 
     if (warp >= 5) {
-        // producers: blend 128 pixels x 32 channels per stage
-        const int pw = warp - 5, ptid = threadIdx.x - 5 * 32;
-        const int g = lane >> 3, c4 = lane & 7;
+        const int pw = warp - 5;
+        const int m = lane / K, j = lane - m * K;      // entry j of group pixel m (m < 4)
         uint32_t it = 0;
         bool ok = true;
-        // every producer warp runs the same number of blocks and named barriers,
-        // also after an abort (it then skips the waits and the work), so no
-        // warp can be left waiting at a barrier
         for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
-            named_sync_producers();            // the previous block's entries are no longer read
-            for (int e = ptid; e < 128 * K && ok; e += FB_PRODUCERS * 32) {
-                const int r = e / K, j = e - r * K;
-                const int64_t p = fb_pixel(t, r, W, H, P);
+            // the distinct rows of this warp's groups and their pixel weights
+#pragma unroll
+            for (int q4 = 0; q4 < FB_GPW; ++q4) {
+                if (!ok) break;
+                const int gi = pw + FB_PRODUCERS * q4;
                 int id = -1;
                 float w = 0.f;
-                if (p >= 0 && j < int(cnt[p])) {
-                    id = ids[p * K + j];
-                    w = wts[p * K + j];
-                    // an id out of range contributes nothing (as in the blend)
-                    if (uint64_t(int64_t(id)) >= uint64_t(n_gauss)) { id = 0; w = 0.f; }
-                    else if (DT == QR_FP8E4M3) w *= fscale[id];
+                if (m < 4) {
+                    const int64_t p = fb_pixel(t, fb_row(gi, m), W, H, P);
+                    if (p >= 0 && j < int(cnt[p])) {
+                        id = ids[p * K + j];
+                        w = wts[p * K + j];
+                        if (uint64_t(int64_t(id)) >= uint64_t(n_gauss)) { id = -1; w = 0.f; }
+                        else if (DT == QR_FP8E4M3) w *= fscale[id];
+                    }
                 }
-                s_id[e] = id;
-                s_w[e] = w;
+                const unsigned peers = __match_any_sync(FULL, id);
+                const int leader = __ffs(peers) - 1;
+                const unsigned leaders = __ballot_sync(FULL, id >= 0 && lane == leader);
+                const int slot = __popc(leaders & ((1u << leader) - 1u));
+                float4 *tw = t_w + gi * 32;
+                tw[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+                __syncwarp();
+                if (id >= 0) {
+                    // a pixel listing an id twice gets the sum of its weights
+                    float *wrow = reinterpret_cast<float *>(&tw[slot]);
+                    atomicAdd(wrow + m, w);
+                    if (lane == leader) t_id[gi * 32 + slot] = id;
+                }
+                if (lane == 0) t_n[gi] = __popc(leaders);
+                __syncwarp();
             }
-            named_sync_producers();
-            for (int sl = 0; sl < nsl && ok; ++sl) {
+            for (int ch = 0; ch < nchunk && ok; ++ch) {
                 const int st = int(it % FB_STAGES);
                 int wok = 1;
-                if (lane == 0) wok = lane_wait(&empty[st], ((it / FB_STAGES) & 1u) ^ 1u, abort_flag) ? 1 : 0;
-                wok = __shfl_sync(0xffffffffu, wok, 0);
+                if (lane == 0) wok = lane_wait_sleep(&empty[st], ((it / FB_STAGES) & 1u) ^ 1u, abort_flag) ? 1 : 0;
+                wok = __shfl_sync(FULL, wok, 0);
                 if (!wok) { ok = false; break; }
-                unsigned char *stage = sA + st * A_TILE;
-                const int c = sl * 32 + c4 * 4;
+                unsigned char *stage = sA + st * FB_STAGE_BYTES;
+                const int c = ch * FB_CHUNK + lane * 4;
+                for (int q4 = 0; q4 < FB_GPW; ++q4) {
+                    const int gi = pw + FB_PRODUCERS * q4;
+                    const int nr = t_n[gi];
+                    const int32_t *tid = t_id + gi * 32;
+                    const float4 *tw = t_w + gi * 32;
+                    float4 acc[4];
 #pragma unroll
-                for (int pass = 0; pass < 4; ++pass) {
-                    const int r = pw * 16 + pass * 4 + g;
-                    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-                    for (int j = 0; j < K; ++j) {
-                        const int id = s_id[r * K + j];
-                        if (id < 0) break;            // entries are a prefix of the pixel's K
-                        const float w = s_w[r * K + j];
-                        const float4 f = fb_load4<DT>(feat, row_bytes, id, c);
-                        acc.x = fmaf(w, f.x, acc.x);
-                        acc.y = fmaf(w, f.y, acc.y);
-                        acc.z = fmaf(w, f.z, acc.z);
-                        acc.w = fmaf(w, f.w, acc.w);
+                    for (int mm = 0; mm < 4; ++mm) acc[mm] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    for (int r0 = 0; r0 < nr; r0 += FB_ROWS) {
+                        float4 f[FB_ROWS];
+#pragma unroll
+                        for (int u = 0; u < FB_ROWS; ++u)
+                            f[u] = r0 + u < nr ? fb_load4<DT>(feat, row_bytes, tid[r0 + u], c)
+                                               : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                        for (int u = 0; u < FB_ROWS; ++u) {
+                            if (r0 + u >= nr) break;
+                            const float4 wg = tw[r0 + u];
+                            const float wv[4] = {wg.x, wg.y, wg.z, wg.w};
+#pragma unroll
+                            for (int mm = 0; mm < 4; ++mm) {
+                                acc[mm].x = fmaf(wv[mm], f[u].x, acc[mm].x);
+                                acc[mm].y = fmaf(wv[mm], f[u].y, acc[mm].y);
+                                acc[mm].z = fmaf(wv[mm], f[u].z, acc[mm].z);
+                                acc[mm].w = fmaf(wv[mm], f[u].w, acc[mm].w);
+                            }
+                        }
                     }
-                    *reinterpret_cast<float4 *>(stage + swz(r, c4)) = acc;
+                    // BF16 into the stage: channel 4 lane of the chunk lies in
+                    // 64-channel slice lane / 16, 16-byte chunk (lane % 16) / 2
+#pragma unroll
+                    for (int mm = 0; mm < 4; ++mm) {
+                        const int r = fb_row(gi, mm);
+                        const __nv_bfloat162 lo = __floats2bfloat162_rn(acc[mm].x, acc[mm].y);
+                        const __nv_bfloat162 hi = __floats2bfloat162_rn(acc[mm].z, acc[mm].w);
+                        uint2 packed;
+                        packed.x = *reinterpret_cast<const uint32_t *>(&lo);
+                        packed.y = *reinterpret_cast<const uint32_t *>(&hi);
+                        *reinterpret_cast<uint2 *>(stage + (lane >> 4) * (128 * 128) +
+                                                   swz(r, (lane & 15) >> 1) + (lane & 1) * 8) = packed;
+                    }
                 }
                 fence_async_smem();
                 __syncwarp();
@@ -624,24 +695,27 @@ blend_relevance_kernel(const unsigned char *__restrict__ feat, const float *__re
             }
         }
     } else if (warp == 4 && lane == 0) {
-        // MMA issuer
-        constexpr uint32_t idesc = make_idesc_tf32(128, QN);
+        // MMA issuer: per stage two 64-channel slices, four K = 16 steps each
+        constexpr uint32_t idesc = make_idesc(128, QN);
         uint32_t it = 0, tl = 0;
         bool ok = true;
         for (int64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++tl) {
             const uint32_t acc = tl & 1u;
-            if (!lane_wait(&tempty[acc], ((tl >> 1) & 1u) ^ 1u, abort_flag)) break;
+            if (!lane_wait_sleep(&tempty[acc], ((tl >> 1) & 1u) ^ 1u, abort_flag)) break;
             tc_fence_after();
-            for (int sl = 0; sl < nsl; ++sl) {
+            for (int ch = 0; ch < nchunk; ++ch) {
                 const int st = int(it % FB_STAGES);
-                if (!lane_wait(&full[st], (it / FB_STAGES) & 1u, abort_flag)) { ok = false; break; }
+                if (!lane_wait_sleep(&full[st], (it / FB_STAGES) & 1u, abort_flag)) { ok = false; break; }
                 tc_fence_after();
-                const uint32_t a0 = smem_u32(sA + st * A_TILE);
-                const uint32_t b0 = smem_u32(sB + size_t(sl) * QN * 128);
 #pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    umma_tf32(tmem + acc * QN, make_desc(a0 + k * 32), make_desc(b0 + k * 32), idesc,
-                              (sl > 0 || k > 0) ? 1u : 0u);
+                for (int h = 0; h < 2; ++h) {
+                    const uint32_t a0 = smem_u32(sA + st * FB_STAGE_BYTES + h * (128 * 128));
+                    const uint32_t b0 = smem_u32(sB + size_t(2 * ch + h) * QN * 128);
+#pragma unroll
+                    for (int k = 0; k < BK / 16; ++k)
+                        umma_bf16(tmem + acc * QN, make_desc(a0 + k * 32), make_desc(b0 + k * 32),
+                                  idesc, (ch > 0 || h > 0 || k > 0) ? 1u : 0u);
+                }
                 umma_commit(&empty[st]);
                 ++it;
             }
@@ -655,8 +729,8 @@ blend_relevance_kernel(const unsigned char *__restrict__ feat, const float *__re
         for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x, ++tl) {
             const uint32_t acc = tl & 1u;
             int ok = 1;
-            if (lane == 0) ok = lane_wait(&tfull[acc], (tl >> 1) & 1u, abort_flag) ? 1 : 0;
-            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (lane == 0) ok = lane_wait_sleep(&tfull[acc], (tl >> 1) & 1u, abort_flag) ? 1 : 0;
+            ok = __shfl_sync(FULL, ok, 0);
             if (!ok) break;
             tc_fence_after();
             const int64_t p = fb_pixel(t, q * 32 + lane, W, H, P);
@@ -693,8 +767,19 @@ blend_relevance_kernel(const unsigned char *__restrict__ feat, const float *__re
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(TMEM_COLS) : "memory");
 }
 
-size_t fb_smem_bytes(int Q, int C, int K) {
-    return 1024 + size_t(FB_STAGES) * A_TILE + size_t(C) * Q * 4 + size_t(128) * K * 8 + 256;
+size_t fb_smem_with(int stages, int Q, int C) {
+    return 1024 + size_t(stages) * FB_STAGE_BYTES + size_t(C / BK) * Q * 128 +
+           size_t(32) * 32 * (4 + 16) + 32 * 4 + 256;
+}
+// the deepest ring (4, 3 or 2 stages) that fits next to the queries
+int fb_stages(int Q, int C) {
+    for (int st = FB_MAX_STAGES; st >= 2; --st)
+        if (fb_smem_with(st, Q, C) <= 227 * 1024) return st;
+    return 0;
+}
+size_t fb_smem_bytes(int Q, int C, int) {
+    const int st = fb_stages(Q, C);
+    return st ? fb_smem_with(st, Q, C) : ~size_t(0);
 }
 
 template <int DT, int QN>
@@ -712,7 +797,7 @@ cudaError_t run_fused(const void *feat, const float *scale, int64_t n_gauss, int
     const int grid = int(tiles < sms ? tiles : sms);
     blend_relevance_kernel<DT, QN><<<grid, FB_THREADS, smem, s>>>(
         static_cast<const unsigned char *>(feat), scale, n_gauss, C, ids, w, cnt, P, K, W, H, q,
-        out, status);
+        out, status, fb_stages(QN, C));
     count_launch();
     return cudaGetLastError();
 }
@@ -725,6 +810,7 @@ cudaError_t fused_q(const void *feat, const float *scale, int64_t n_gauss, int C
         case 16: return run_fused<DT, 16>(feat, scale, n_gauss, C, ids, w, cnt, P, K, W, H, q, out, status, s);
         case 32: return run_fused<DT, 32>(feat, scale, n_gauss, C, ids, w, cnt, P, K, W, H, q, out, status, s);
         case 64: return run_fused<DT, 64>(feat, scale, n_gauss, C, ids, w, cnt, P, K, W, H, q, out, status, s);
+        case 128: return run_fused<DT, 128>(feat, scale, n_gauss, C, ids, w, cnt, P, K, W, H, q, out, status, s);
     }
     return cudaErrorInvalidValue;
 }
@@ -782,9 +868,9 @@ cudaError_t run(const float *map, const uint16_t *q, int64_t P, int C, float *ou
 }  // namespace
 
 bool blend_relevance_supported(qr_dtype dt, int Q, int C, int K) {
-    const int cpv = dt == QR_F32 ? 4 : dt == QR_BF16 ? 8 : 16;
-    if (C < 32 || C % 32 || C % cpv || K < 1 || K > kKMax) return false;
-    if (!(Q == 16 || Q == 32 || Q == 64)) return false;
+    if (C < FB_CHUNK || C % FB_CHUNK || K < 1 || K > 8) return false;
+    if (!(Q == 16 || Q == 32 || Q == 64 || Q == 128)) return false;
+    (void)dt;
     return fb_smem_bytes(Q, C, K) <= 227 * 1024;
 }
 

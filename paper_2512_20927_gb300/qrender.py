@@ -88,6 +88,7 @@ SIGNATURES = {
     "qr_select_rule": (_S, [ctypes.POINTER(qr_frame), _S, _P, _P, _P, _P, _P]),
     "qr_blend": (_S, [_P, _P, _S, _I32, _I64, _P, _P, _P, _I64, _I32, _I32, _P, _P]),
     "qr_dense": (_S, [ctypes.POINTER(qr_frame), _P, _P, _S, _I32, _P, _P, _P]),
+    "qr_dense_work": (_S, [ctypes.POINTER(qr_frame), _P, _P, _S, _I32, _P, _P, _P, _P]),
     "qr_render": (_S, [ctypes.POINTER(qr_frame), _P, _P, _P, _P, _P, _P, _S, _I32, _P, _P, _P,
                        _P, _P]),
     "qr_render_host_bytes": (_S, [_I64, _I32, _I32, _I32, _I32, _S,
@@ -295,6 +296,17 @@ def qr_dense(fr: Frame, feat, feat_scale, out, T_final=None, stream=None):
     _check(load().qr_dense(ctypes.byref(fr.frame), _ptr(feat), _ptr(feat_scale),
                            _dtype_code(feat), feat.shape[1], _ptr(out), _ptr(T_final),
                            _stream(stream)), "qr_dense")
+
+
+def qr_dense_work(fr: Frame, feat, feat_scale, out, T_final=None, stream=None):
+    """qr_dense counting its work: returns a device int64 tensor [blended
+    (pixel, Gaussian) pairs, executed multiply-adds]."""
+    torch = _torch()
+    counts = torch.zeros(2, dtype=torch.int64, device=out.device)
+    _check(load().qr_dense_work(ctypes.byref(fr.frame), _ptr(feat), _ptr(feat_scale),
+                                _dtype_code(feat), feat.shape[1], _ptr(out), _ptr(T_final),
+                                _ptr(counts), _stream(stream)), "qr_dense_work")
+    return counts
 
 
 def qr_render(fr: Frame, mean, log_scale, quat, opacity, feat, feat_scale, ids, weights, counts,

@@ -1,10 +1,10 @@
 """The blend fused with the relevance product (qr_blend_relevance) against its
 definition in FP64: R = (sum_j w_pj f_{id_pj}) Q^T, through the C ABI.
 
-The map is blended in FP32 and multiplied as TF32 (at least 10 mantissa bits),
-so |R - R_64| <= 2^-10 sum_c |F|_c |q|_c + (FP32 blend rounding), with
-|F|_c = sum_j |w_j| |f_j,c|: the test uses 2^-10 of that magnitude product
-plus 1e-6.
+The map is blended in FP32, rounded to BF16 and multiplied on the tensor
+cores with FP32 accumulation, so |R - R_64| <= 2^-8 sum_c |F|_c |q|_c, with
+|F|_c = sum_j |w_j| |f_j,c| (which also covers the FP32 blend rounding): the
+test uses 2^-8 of that magnitude product plus 1e-6.
 """
 import numpy as np
 import pytest
@@ -31,7 +31,7 @@ def _check(got, ids, w, cnt, fdec, qbits):
     mag = Fmag @ np.abs(qd).T
     err = np.abs(np.asarray(got, np.float64) - exact)
     worst = float((err / (mag + 1e-30)).max())
-    assert (err <= 2.0 ** -10 * mag + 1e-6).all(), worst
+    assert (err <= 2.0 ** -8 * mag + 1e-6).all(), worst
     return worst
 
 
@@ -46,9 +46,9 @@ def _table(kind, f, q, torch):
     return codes, scale, oracle.fp8_dequantize_rows(c, s)
 
 
-@pytest.mark.parametrize("kind,C,Q,K", [("f32", 512, 64, 8), ("f32", 64, 16, 4), ("f32", 256, 32, 16),
+@pytest.mark.parametrize("kind,C,Q,K", [("f32", 512, 64, 8), ("f32", 128, 16, 4), ("f32", 256, 32, 8),
                                         ("bf16", 512, 64, 8), ("fp8", 512, 64, 8),
-                                        ("f32", 96, 64, 32)])
+                                        ("f32", 384, 128, 1), ("bf16", 1024, 64, 3)])
 def test_fused_matches_definition_consecutive_pixels(kind, C, Q, K):
     import torch
     from paper_2512_20927_gb300 import qrender as q
@@ -87,3 +87,22 @@ def test_fused_on_a_rendered_frame_matches_the_two_step_path():
     _check(fused.cpu().numpy(), ids, w, cnt, f.astype(np.float64), qn)
     _check(two.cpu().numpy(), ids, w, cnt, f.astype(np.float64), qn)
     assert (fused[torch.from_numpy(cnt == 0).cuda()] == 0).all()
+
+
+def test_fused_rejects_what_it_does_not_serve():
+    import torch
+    from paper_2512_20927_gb300 import qrender as q
+    f = torch.zeros((100, 96), device="cuda")
+    ids = torch.zeros((10, 8), dtype=torch.int32, device="cuda")
+    w = torch.zeros((10, 8), device="cuda")
+    cnt = torch.zeros(10, dtype=torch.uint8, device="cuda")
+    qb = torch.zeros((64, 96), dtype=torch.int16, device="cuda")
+    with pytest.raises(q.QRError) as e:
+        q.qr_blend_relevance(f, None, ids, w, cnt, qb)          # C = 96: not a multiple of 128
+    assert e.value.code == q.QR_ERR_NOT_SUPPORTED
+    ids16 = torch.zeros((10, 16), dtype=torch.int32, device="cuda")
+    with pytest.raises(q.QRError) as e:
+        q.qr_blend_relevance(torch.zeros((100, 128), device="cuda"), None, ids16,
+                             torch.zeros((10, 16), device="cuda"), cnt,
+                             torch.zeros((64, 128), dtype=torch.int16, device="cuda"))
+    assert e.value.code == q.QR_ERR_NOT_SUPPORTED             # K = 16 > 8

@@ -373,3 +373,45 @@ def test_launch_counter_advances():
     g, f = scenes.tiny_scene(n=200)
     H.run_gpu(g, f, scenes.tiny_camera(32, 32), K=4)
     assert q.qr_launch_count() > before
+
+
+@pytest.mark.parametrize("C,kind,tile", [(512, "f32", (16, 16)), (256, "f32", (8, 32)),
+                                         (128, "bf16", (32, 8)), (512, "fp8", (16, 16))])
+def test_dense_subtile_kernel(C, kind, tile):
+    """The sub-tile dense kernel (rows of 128-512 channels; 16x4, 8x8 or 32x2
+    sub-tiles, one walk per pixel, culled and skipped entries) against the
+    oracle's Eq. 1, and its work counter against the oracle's walk lengths."""
+    import torch
+    from paper_2512_20927_gb300 import qrender as q
+    g, f = H.small_room(n=20000, channels=C)
+    cam = scenes.room_camera(150, 110)
+    fdev = torch.from_numpy(f).cuda()
+    table, scale, fdec = fdev, None, f
+    if kind == "bf16":
+        table = q.qr_quantize_bf16(fdev)
+        fdec = oracle.bf16_decode(oracle.bf16_encode(f))
+    elif kind == "fp8":
+        table, scale = q.qr_quantize_fp8(fdev)
+        c8, s8 = oracle.fp8_quantize_rows(f)
+        fdec = oracle.fp8_dequantize_rows(c8, s8)
+    params = q.default_params(8, tile_w=tile[0], tile_h=tile[1])
+    res = q.render_frame(q.gaussians_to_device(g), None, cam, K=8, params=params)
+    fr = res["frame"]
+    P = cam.width * cam.height
+    out = torch.empty((P, C), device="cuda")
+    tf = torch.empty(P, device="cuda")
+    counts = q.qr_dense_work(fr, table, scale, out, tf)
+    torch.cuda.synchronize()
+    pr, pix, ref = H.run_oracle(g, fdec, cam, 8)
+    dtie = (ref.tie & compare.DENSE_TIE_BITS) != 0
+    err = compare.feature_error(out.cpu().numpy(), ref.out_dense, ref.scale_dense)[~dtie]
+    assert err.max() <= DENSE_TOL, err.max()
+    tf_err = np.abs(tf.cpu().numpy() - ref.t_final)[~dtie]
+    assert tf_err.max() <= 1e-5, tf_err.max()
+    blended, executed = (int(x) for x in counts.cpu().numpy())
+    want = int(ref.n_dense.sum())
+    slack = int(ref.n_dense[dtie].sum()) + int(dtie.sum())
+    assert abs(blended - want) <= slack, (blended, want, slack)
+    assert executed >= blended * C
+    print(f"dense sub-tile C={C} {kind} tile {tile}: err {err.max():.2e}, blended {blended} "
+          f"(oracle {want}), executed/useful FMA {executed / max(blended * C, 1):.2f}")

@@ -409,7 +409,7 @@ qr_status qr_contrastive_backward(const qr_frame *frame, const void *feat, const
  * multiple of 64 with the BF16 queries fitting in shared memory (Q * C * 2
  * bytes <= ~190 KB).  status: a device int32 the kernel sets to
  * QR_ERR_DEVICE_TIMEOUT if a bounded wait gives up (it is never cleared by the
- * library). */
+ * library; see qr_set_wait_limit). */
 qr_status qr_relevance(const float *feature_map, const uint16_t *queries_bf16, int32_t Q, int32_t C,
                        int64_t P, float *out, int32_t *status, qr_stream stream);
 
@@ -481,6 +481,17 @@ qr_status qr_render_noalloc(const float *mean, const float *log_scale, const flo
 
 /* Number of kernels this library has launched since it was loaded. */
 uint64_t qr_launch_count(void);
+
+/* Test hook for the device-side error path.  The relevance kernels
+ * (qr_relevance's TMA kernel, qr_blend_relevance) bound each of their waits
+ * on a producer, the tensor cores or the epilogue to a number of polls
+ * (2^26 by default, seconds); when one runs out the CTA stops every role,
+ * waits (with the default bound) for its own copies and MMAs in flight,
+ * frees its tensor memory and writes QR_ERR_DEVICE_TIMEOUT to the call's
+ * status word.  qr_set_wait_limit(polls) sets that bound for the launches
+ * that follow (0 restores the default), so a test can make a wait run out
+ * without anything hanging.  Not for production use; not thread-safe. */
+void qr_set_wait_limit(uint32_t polls);
 
 #ifdef __cplusplus
 }

@@ -465,7 +465,9 @@ static int build_list(const render_job_t *J, scratch_t *S, int px, int py)
     double ux = px + 0.5, uy = py + 0.5;
     S->len = 0; S->blen = 0;
     for (int64_t i = 0; i < J->n; ++i) {
-        if (!J->valid[i]) continue;
+        /* a Gaussian with a non-finite parameter contributes nothing (the
+         * projection marks non-finite geometry invalid; the opacity here) */
+        if (!J->valid[i] || !isfinite(J->alpha[i])) continue;
         double dx = ux - J->mean2d[2 * i], dy = uy - J->mean2d[2 * i + 1];
         double A00 = J->conic[3 * i], A01 = J->conic[3 * i + 1], A11 = J->conic[3 * i + 2];
         double q = A00 * dx * dx + 2.0 * A01 * dx * dy + A11 * dy * dy;

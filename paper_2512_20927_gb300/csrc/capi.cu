@@ -549,4 +549,6 @@ qr_status qr_render_batch(const void *ws, int32_t n_views, uint32_t total_tiles,
 
 uint64_t qr_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
+void qr_set_wait_limit(uint32_t polls) { set_wait_limit(polls); }
+
 }  // extern "C"

@@ -65,7 +65,8 @@ project_cull(int64_t n, const float *__restrict__ mean, const float *__restrict_
         const float mx = mean[3 * g], my = mean[3 * g + 1], mz = mean[3 * g + 2];
         const float alpha = opacity[g];
         const float cz = fmaf(cam.R[6], mx, fmaf(cam.R[7], my, fmaf(cam.R[8], mz, cam.t[2])));
-        if (alpha >= alpha_min && cz > cam.znear - 1e-3f) {
+        // a Gaussian with a non-finite opacity is culled (NaN fails the first test)
+        if (alpha >= alpha_min && alpha <= 3.402823466e38f && cz > cam.znear - 1e-3f) {
             const float cx_ = fmaf(cam.R[0], mx, fmaf(cam.R[1], my, fmaf(cam.R[2], mz, cam.t[0])));
             const float cy_ = fmaf(cam.R[3], mx, fmaf(cam.R[4], my, fmaf(cam.R[5], mz, cam.t[1])));
             const float zz = fmaxf(cz, 0.5f * cam.znear);

@@ -161,6 +161,7 @@ cudaError_t launch_contrastive_loss(const float *F, const float *tgt, int M, int
                                     const int32_t *mask_id, int64_t P, float *out2, float *grad,
                                     void *ws, cudaStream_t s);
 bool relevance_supported(int Q, int C);
+void set_wait_limit(unsigned polls);
 // blend of qr_blend fused with the relevance product (the map is never written)
 bool blend_relevance_supported(qr_dtype dt, int Q, int C, int K);
 cudaError_t launch_blend_relevance(const void *feat, const float *scale, qr_dtype dt, int C,

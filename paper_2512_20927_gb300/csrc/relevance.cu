@@ -187,13 +187,27 @@ __host__ __device__ constexpr uint32_t make_idesc_tf32(int M, int N) {
     return (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t(N >> 3) << 17) | (uint32_t(M >> 4) << 24);
 }
 
-// Bounded wait by one thread; on timeout raises the CTA's abort flag.
-__device__ __forceinline__ bool lane_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
+// Bounded wait by one thread (at most `spin` polls); on timeout raises the
+// CTA's abort flag.
+__device__ __forceinline__ bool lane_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
+                                          unsigned spin = kSpinLimit) {
     if (*abort_flag) return false;
-    if (mbar_wait(bar, parity)) return true;
+    const uint32_t a = smem_u32(bar);
+    for (unsigned i = 0; i < spin; ++i) {
+        uint32_t done;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(done) : "r"(a), "r"(parity) : "memory");
+        if (done) return true;
+    }
     *abort_flag = 1;
     return false;
 }
+
+// Polls allowed to the first-level waits of the relevance kernels (those
+// that set the abort flag); the drains after an abort keep kSpinLimit.
+// Changed only through qr_set_wait_limit (a test hook).
+unsigned g_wait_limit = kSpinLimit;
 
 template <int QN>
 __global__ void __launch_bounds__(NT, 2)
@@ -315,7 +329,8 @@ constexpr int A_TILE = 128 * 32 * 4;  // 128 pixels x 32 channels FP32 = 16 KB
 template <int QN>
 __global__ void __launch_bounds__(TT, 1)
 relevance_tma_kernel(const __grid_constant__ CUtensorMap tmap, const uint16_t *__restrict__ queries,
-                     int64_t P, int C, float *__restrict__ out, int *__restrict__ status) {
+                     int64_t P, int C, float *__restrict__ out, int *__restrict__ status,
+                     unsigned spin) {
     constexpr uint32_t TMEM_COLS = 2 * QN < 32 ? 32 : 2 * QN;   // two accumulators
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *base = reinterpret_cast<unsigned char *>(
@@ -374,7 +389,7 @@ relevance_tma_kernel(const __grid_constant__ CUtensorMap tmap, const uint16_t *_
         for (int64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x)
             for (int sl = 0; sl < nsl; ++sl) {
                 const int st = int(it % STAGES);
-                if (!lane_wait(&empty[st], ((it / STAGES) & 1u) ^ 1u, abort_flag)) { ok = false; break; }
+                if (!lane_wait(&empty[st], ((it / STAGES) & 1u) ^ 1u, abort_flag, spin)) { ok = false; break; }
                 mbar_expect_tx(&full[st], A_TILE);
                 tma_load_2d(smem_u32(sA + st * A_TILE), &tmap, sl * 32, int(t * 128), &full[st]);
                 ++it;
@@ -387,11 +402,11 @@ relevance_tma_kernel(const __grid_constant__ CUtensorMap tmap, const uint16_t *_
         bool ok = true;
         for (int64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++tl) {
             const uint32_t acc = tl & 1u;
-            if (!lane_wait(&tempty[acc], ((tl >> 1) & 1u) ^ 1u, abort_flag)) break;
+            if (!lane_wait(&tempty[acc], ((tl >> 1) & 1u) ^ 1u, abort_flag, spin)) break;
             tc_fence_after();
             for (int sl = 0; sl < nsl; ++sl) {
                 const int st = int(it % STAGES);
-                if (!lane_wait(&full[st], (it / STAGES) & 1u, abort_flag)) { ok = false; break; }
+                if (!lane_wait(&full[st], (it / STAGES) & 1u, abort_flag, spin)) { ok = false; break; }
                 tc_fence_after();
                 const uint32_t a0 = smem_u32(sA + st * A_TILE);
                 const uint32_t b0 = smem_u32(sB + size_t(sl) * QN * 128);
@@ -412,7 +427,7 @@ relevance_tma_kernel(const __grid_constant__ CUtensorMap tmap, const uint16_t *_
         for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x, ++tl) {
             const uint32_t acc = tl & 1u;
             int ok = 1;
-            if (lane == 0) ok = lane_wait(&tfull[acc], (tl >> 1) & 1u, abort_flag) ? 1 : 0;
+            if (lane == 0) ok = lane_wait(&tfull[acc], (tl >> 1) & 1u, abort_flag, spin) ? 1 : 0;
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) break;
             tc_fence_after();
@@ -502,10 +517,10 @@ __device__ __forceinline__ int fb_row(int gi, int m) {
 
 // Bounded wait with backoff; false on timeout (sets the abort flag).
 __device__ __forceinline__ bool lane_wait_sleep(uint64_t *bar, uint32_t parity,
-                                                volatile int *abort_flag) {
+                                                volatile int *abort_flag, unsigned spin) {
     if (*abort_flag) return false;
     const uint32_t a = smem_u32(bar);
-    for (unsigned i = 0; i < kSpinLimit / 16; ++i) {
+    for (unsigned i = 0; i < spin / 16 + 1; ++i) {
         uint32_t done;
         asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
                      " selp.u32 %0, 1, 0, p;\n}\n"
@@ -545,7 +560,8 @@ blend_relevance_kernel(const unsigned char *__restrict__ feat, const float *__re
                        int64_t n_gauss, int C, const int32_t *__restrict__ ids,
                        const float *__restrict__ wts, const uint8_t *__restrict__ cnt, int64_t P,
                        int K, int W, int H, const uint16_t *__restrict__ queries,
-                       float *__restrict__ out, int *__restrict__ status, int FB_STAGES) {
+                       float *__restrict__ out, int *__restrict__ status, int FB_STAGES,
+                       unsigned spin) {
     constexpr uint32_t TMEM_COLS = 2 * QN < 32 ? 32 : 2 * QN;
     constexpr int ESZ = DT == QR_F32 ? 4 : DT == QR_BF16 ? 2 : 1;
     constexpr unsigned FULL = 0xffffffffu;
@@ -641,7 +657,7 @@ blend_relevance_kernel(const unsigned char *__restrict__ feat, const float *__re
             for (int ch = 0; ch < nchunk && ok; ++ch) {
                 const int st = int(it % FB_STAGES);
                 int wok = 1;
-                if (lane == 0) wok = lane_wait_sleep(&empty[st], ((it / FB_STAGES) & 1u) ^ 1u, abort_flag) ? 1 : 0;
+                if (lane == 0) wok = lane_wait_sleep(&empty[st], ((it / FB_STAGES) & 1u) ^ 1u, abort_flag, spin) ? 1 : 0;
                 wok = __shfl_sync(FULL, wok, 0);
                 if (!wok) { ok = false; break; }
                 unsigned char *stage = sA + st * FB_STAGE_BYTES;
@@ -701,11 +717,11 @@ blend_relevance_kernel(const unsigned char *__restrict__ feat, const float *__re
         bool ok = true;
         for (int64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++tl) {
             const uint32_t acc = tl & 1u;
-            if (!lane_wait_sleep(&tempty[acc], ((tl >> 1) & 1u) ^ 1u, abort_flag)) break;
+            if (!lane_wait_sleep(&tempty[acc], ((tl >> 1) & 1u) ^ 1u, abort_flag, spin)) break;
             tc_fence_after();
             for (int ch = 0; ch < nchunk; ++ch) {
                 const int st = int(it % FB_STAGES);
-                if (!lane_wait_sleep(&full[st], (it / FB_STAGES) & 1u, abort_flag)) { ok = false; break; }
+                if (!lane_wait_sleep(&full[st], (it / FB_STAGES) & 1u, abort_flag, spin)) { ok = false; break; }
                 tc_fence_after();
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
@@ -729,7 +745,7 @@ blend_relevance_kernel(const unsigned char *__restrict__ feat, const float *__re
         for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x, ++tl) {
             const uint32_t acc = tl & 1u;
             int ok = 1;
-            if (lane == 0) ok = lane_wait_sleep(&tfull[acc], (tl >> 1) & 1u, abort_flag) ? 1 : 0;
+            if (lane == 0) ok = lane_wait_sleep(&tfull[acc], (tl >> 1) & 1u, abort_flag, spin) ? 1 : 0;
             ok = __shfl_sync(FULL, ok, 0);
             if (!ok) break;
             tc_fence_after();
@@ -797,7 +813,7 @@ cudaError_t run_fused(const void *feat, const float *scale, int64_t n_gauss, int
     const int grid = int(tiles < sms ? tiles : sms);
     blend_relevance_kernel<DT, QN><<<grid, FB_THREADS, smem, s>>>(
         static_cast<const unsigned char *>(feat), scale, n_gauss, C, ids, w, cnt, P, K, W, H, q,
-        out, status, fb_stages(QN, C));
+        out, status, fb_stages(QN, C), g_wait_limit);
     count_launch();
     return cudaGetLastError();
 }
@@ -842,7 +858,7 @@ cudaError_t run_tma(const float *map, const uint16_t *q, int64_t P, int C, float
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t tiles = (P + 127) / 128;
     const int grid = int(tiles < sms ? tiles : sms);
-    relevance_tma_kernel<QN><<<grid, TT, smem, s>>>(tm, q, P, C, out, status);
+    relevance_tma_kernel<QN><<<grid, TT, smem, s>>>(tm, q, P, C, out, status, g_wait_limit);
     count_launch();
     return cudaGetLastError();
 }
@@ -866,6 +882,8 @@ cudaError_t run(const float *map, const uint16_t *q, int64_t P, int C, float *ou
 }
 
 }  // namespace
+
+void set_wait_limit(unsigned polls) { g_wait_limit = polls ? polls : kSpinLimit; }
 
 bool blend_relevance_supported(qr_dtype dt, int Q, int C, int K) {
     if (C < FB_CHUNK || C % FB_CHUNK || K < 1 || K > 8) return false;

@@ -97,6 +97,7 @@ SIGNATURES = {
     "qr_render_host": (_S, [ctypes.POINTER(qr_frame), _P, _P, _P, _P, _P, _P, _S, _I32, _P, _P,
                             _P, _P]),
     "qr_launch_count": (ctypes.c_uint64, []),
+    "qr_set_wait_limit": (None, [ctypes.c_uint32]),
     "qr_backward_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(qr_frame), _I32]),
     "qr_backward": (_S, [ctypes.POINTER(qr_frame), _P, _P, _S, _I32, _P, _P, _P, _P, _P, _P, _P,
                          _P, ctypes.c_size_t, _P]),
@@ -534,6 +535,11 @@ def qr_quantize_fp8(x, stream=None):
 
 def qr_launch_count() -> int:
     return int(load().qr_launch_count())
+
+
+def qr_set_wait_limit(polls: int):
+    """Test hook: bound the relevance kernels' waits to `polls` polls (0 = default)."""
+    load().qr_set_wait_limit(int(polls))
 
 
 # ---------------------------------------------------------------- convenience

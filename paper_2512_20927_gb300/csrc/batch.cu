@@ -87,6 +87,33 @@ __device__ __forceinline__ void dec_fma(const uint4 v, float w, float *acc) {
     }
 }
 
+// A 16-byte vector widened to FP32 once (exact for BF16 and E4M3); the group
+// loop then FMAs it into each pixel that lists the row.
+template <int DT>
+__device__ __forceinline__ void dec_vec(const uint4 v, float *o) {
+    if constexpr (DT == QR_F32) {
+        o[0] = __uint_as_float(v.x); o[1] = __uint_as_float(v.y);
+        o[2] = __uint_as_float(v.z); o[3] = __uint_as_float(v.w);
+    } else if constexpr (DT == QR_BF16) {
+        const uint32_t u[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            o[2 * i] = __uint_as_float(u[i] << 16);
+            o[2 * i + 1] = __uint_as_float(u[i] & 0xFFFF0000u);
+        }
+    } else {
+        const uint32_t u[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2(__nv_fp8x2_storage_t(u[i] & 0xFFFFu), __NV_E4M3);
+            const __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2(__nv_fp8x2_storage_t(u[i] >> 16), __NV_E4M3);
+            const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&lo));
+            const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&hi));
+            o[4 * i] = a.x; o[4 * i + 1] = a.y; o[4 * i + 2] = b.x; o[4 * i + 3] = b.y;
+        }
+    }
+}
+
 __device__ __forceinline__ uint4 ldg_nc(const uint4 *p) {
     uint4 r;
     asm volatile("ld.global.nc.v4.u32 {%0,%1,%2,%3}, [%4];"
@@ -303,11 +330,17 @@ batch_kernel(const BatchView *__restrict__ views, int n_views, uint32_t total_it
                     float wg[G];
 #pragma unroll
                     for (int g = 0; g < G; ++g) wg[g] = s_tw[warp][r0 + u][g];
+                    float fv[VPL][CPV];
+#pragma unroll
+                    for (int vv = 0; vv < VPL; ++vv) dec_vec<DT>(r[u][vv], fv[vv]);
 #pragma unroll
                     for (int g = 0; g < G; ++g)
                         if (wg[g] != 0.f) {
 #pragma unroll
-                            for (int vv = 0; vv < VPL; ++vv) dec_fma<DT>(r[u][vv], wg[g], acc[g][vv]);
+                            for (int vv = 0; vv < VPL; ++vv)
+#pragma unroll
+                                for (int q = 0; q < CPV; q += 2)
+                                    fma2b(acc[g][vv] + q, wg[g], fv[vv][q], fv[vv][q + 1]);
                         }
                 }
             }

@@ -83,6 +83,40 @@ __device__ __forceinline__ void decode_fma<QR_FP8E4M3>(const uint4 v, float w, f
     fp8x4_fma(v.w, w, acc + 12);
 }
 
+// A 16-byte vector widened to FP32 once (exact for BF16 and E4M3), so that a
+// row shared by several pixels is decoded once and FMA'd into each of them.
+template <int DT>
+__device__ __forceinline__ void decode_vec(const uint4 v, float *o) {
+    if constexpr (DT == QR_F32) {
+        o[0] = __uint_as_float(v.x); o[1] = __uint_as_float(v.y);
+        o[2] = __uint_as_float(v.z); o[3] = __uint_as_float(v.w);
+    } else if constexpr (DT == QR_BF16) {
+        const uint32_t u[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            o[2 * i] = __uint_as_float(u[i] << 16);
+            o[2 * i + 1] = __uint_as_float(u[i] & 0xFFFF0000u);
+        }
+    } else {
+        const uint32_t u[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2(__nv_fp8x2_storage_t(u[i] & 0xFFFFu), __NV_E4M3);
+            const __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2(__nv_fp8x2_storage_t(u[i] >> 16), __NV_E4M3);
+            const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&lo));
+            const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&hi));
+            o[4 * i] = a.x; o[4 * i + 1] = a.y; o[4 * i + 2] = b.x; o[4 * i + 3] = b.y;
+        }
+    }
+}
+
+// acc[0..N) += w * f[0..N) in packed pairs (each half rounds like fmaf)
+template <int N>
+__device__ __forceinline__ void fma_vec(const float *f, float w, float *acc) {
+#pragma unroll
+    for (int i = 0; i < N; i += 2) fma2(acc + i, w, f[i], f[i + 1]);
+}
+
 __device__ __forceinline__ uint4 ld_row(const uint4 *p) {
     uint4 r;
     asm volatile("ld.global.nc.v4.u32 {%0,%1,%2,%3}, [%4];"
@@ -268,11 +302,14 @@ blend_group_kernel(const uint4 *__restrict__ feat, const float *__restrict__ sca
                 float wg[G];
 #pragma unroll
                 for (int g = 0; g < G; ++g) wg[g] = s_w[warp][r0 + u][g];
+                float fv[VPL][CPV];
+#pragma unroll
+                for (int v = 0; v < VPL; ++v) decode_vec<DT>(r[u][v], fv[v]);
 #pragma unroll
                 for (int g = 0; g < G; ++g)
                     if (wg[g] != 0.f) {
 #pragma unroll
-                        for (int v = 0; v < VPL; ++v) decode_fma<DT>(r[u][v], wg[g], acc[g][v]);
+                        for (int v = 0; v < VPL; ++v) fma_vec<CPV>(fv[v], wg[g], acc[g][v]);
                     }
             }
         }

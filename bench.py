@@ -858,6 +858,55 @@ def profile_relevance(local, reps=13):
             "status": int(st.item())}
 
 
+def profile_mode(local, mode, steps):
+    """Workload set up once, then `steps` eager launches of one part of it, for
+    ncu captures: indoor / object (a whole Q-Render frame: project, sort,
+    select, blend), blend, fused (blend + relevance in one kernel), eq2 (the
+    Eq. 2 loss and its gradient, 32 patches), rules (top-K then Stratified-K
+    selection), dense (Eq. 1) -- on the 500k indoor room (object: the object
+    scene), 640x480, 512-D FP32, K = 8."""
+    import torch
+    from paper_2512_20927_gb300 import qrender as q
+    from paper_2512_20927_gb300 import scenes
+    dev = torch.device("cuda", local)
+    if mode == "object":
+        g, feat = scenes.object_scene(seed=0, n=N_GAUSS, channels=C)
+        cam = scenes.object_camera(WIDTH, HEIGHT)
+    else:
+        g, feat = scenes.room_scene(seed=0, n=N_GAUSS, channels=C)
+        cam = scenes.room_camera(WIDTH, HEIGHT)
+    gd = tuple(t.to(dev) for t in q.gaussians_to_device(g, device="cpu"))
+    fd = torch.from_numpy(feat).to(dev)
+    del feat
+    r = q.render_frame(gd, fd, cam, K=K)
+    fr, ids, w, cnt, o = r["frame"], r["ids"], r["weights"], r["counts"], r["out"]
+    qb = q.qr_quantize_bf16(torch.from_numpy(scenes.unit_queries(7, 64, C)).to(dev)).view(torch.int16)
+    mid = torch.from_numpy(scenes.patch_masks(WIDTH, HEIGHT, 32, seed=2)).to(dev)
+    tg = torch.from_numpy(scenes.patch_targets(32, C, seed=5)).to(dev)
+    dout = torch.empty_like(o)
+    tf = torch.empty(fr.pixels, device=dev)
+    torch.cuda.synchronize()
+    for _ in range(steps):
+        if mode in ("indoor", "object"):
+            q.qr_project(fr, *gd)
+            q.qr_sort(fr)
+            q.qr_select(fr, ids, w, cnt)
+            q.qr_blend(fd, None, ids, w, cnt, o)
+        elif mode == "blend":
+            q.qr_blend(fd, None, ids, w, cnt, o)
+        elif mode == "fused":
+            q.qr_blend_relevance(fd, None, ids, w, cnt, qb, width=fr.width)
+        elif mode == "eq2":
+            q.qr_contrastive_loss(o, tg, mid)
+        elif mode == "rules":
+            q.qr_select_rule(fr, q.QR_RULE_TOPK, ids, w, cnt)
+            q.qr_select_rule(fr, q.QR_RULE_STRATIFIED, ids, w, cnt)
+        elif mode == "dense":
+            q.qr_dense(fr, fd, None, dout, tf)
+    torch.cuda.synchronize()
+    return {"profile": mode, "steps": steps}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -872,6 +921,9 @@ def main():
                     help="only run eager training steps of the differentiation workload (for ncu)")
     ap.add_argument("--profile-relevance", action="store_true",
                     help="only run the relevance GEMM on a 1.07 GB map (for ncu captures)")
+    ap.add_argument("--profile-mode", default=None,
+                    choices=["indoor", "object", "blend", "fused", "eq2", "rules", "dense"],
+                    help="set up one workload and run --steps eager launches of one part (for ncu)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the many-view and training-step measurements")
     args = ap.parse_args()
@@ -916,6 +968,11 @@ def main():
                     "d2h_bytes_per_step": 0}}))
         return
 
+    if args.profile_mode:
+        import torch
+        torch.cuda.set_device(local)
+        print(json.dumps(profile_mode(local, args.profile_mode, args.steps)))
+        return
     if args.profile_relevance or args.profile_train:
         import torch
         torch.cuda.set_device(local)

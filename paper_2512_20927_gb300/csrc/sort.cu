@@ -24,12 +24,13 @@
 //      its tile's bucket at an atomically claimed position (counted per tile
 //      in shared memory first, one global atomic per touched tile, when the
 //      grid has at most 4096 tiles);
-//   5. tile_sort: one CTA per tile sorts its bucket (bitonic network over the
-//      unique 64-bit keys) and writes the ids: buckets of up to 2048 keys in
-//      registers (register swaps, warp shuffles, shared memory only for the
-//      cross-warp strides), up to 8192 in shared memory; a larger bucket is
-//      sorted in chunks and merged in global memory by the same CTA (merge
-//      path), so no size is refused.
+//   5. tile_sort / tile_sort_big: one CTA per tile sorts its bucket (bitonic
+//      network over the unique 64-bit keys) and writes the ids: buckets of up
+//      to 2048 keys in registers (register swaps, warp shuffles, shared memory
+//      only for the cross-warp strides) in tile_sort; larger ones in
+//      tile_sort_big, up to 8192 keys still in registers (32 per thread), up
+//      to 8192 otherwise in shared memory, beyond that in chunks merged in
+//      global memory by the same CTA (merge path), so no size is refused.
 // Keys are unique, so the order inside a bucket before step 5 does not matter
 // and the result is deterministic.  No CTA waits for another.  Counts live in
 // device memory, so the stage can be captured in a CUDA graph.
@@ -343,23 +344,43 @@ __device__ __forceinline__ void merge_cta(const unsigned long long *A, int na,
     }
 }
 
+// Buckets of up to 8 T keys (registers, up to 8 per thread); larger ones
+// are left to tile_sort_big, whose register needs would lower this kernel's
+// occupancy for every tile.
 __global__ void __launch_bounds__(T)
 tile_sort(const uint2 *__restrict__ ranges, unsigned long long *__restrict__ keys,
-          unsigned long long *__restrict__ scratch, uint32_t *__restrict__ igid) {
+          uint32_t *__restrict__ igid) {
     pdl_wait();   // the predecessor's outputs are complete and visible
-    extern __shared__ unsigned long long s_k[];   // TS_CAP keys
+    __shared__ unsigned long long s_k[8 * T];
     const uint2 r = ranges[blockIdx.x];
     const int n = int(r.y - r.x);
-    if (n == 0) return;
+    if (n == 0 || n > 8 * T) return;
     unsigned long long *src = keys + r.x;
     if (n <= 2 * T) {
         if (n <= T) sort_registers<1>(src, n, s_k, igid + r.x);
         else sort_registers<2>(src, n, s_k, igid + r.x);
         return;
     }
-    if (n <= 8 * T) {
-        if (n <= 4 * T) sort_registers<4>(src, n, s_k, igid + r.x);
-        else sort_registers<8>(src, n, s_k, igid + r.x);
+    if (n <= 4 * T) sort_registers<4>(src, n, s_k, igid + r.x);
+    else sort_registers<8>(src, n, s_k, igid + r.x);
+}
+
+// Buckets of more than 8 T keys (a CTA per tile; the others return at once):
+// up to 32 keys per thread in registers (strides below 32 E in registers and
+// shuffles, only the widest through shared memory), up to TS_CAP keys in a
+// shared-memory network, beyond that sorted chunks merged in global memory.
+__global__ void __launch_bounds__(T)
+tile_sort_big(const uint2 *__restrict__ ranges, unsigned long long *__restrict__ keys,
+              unsigned long long *__restrict__ scratch, uint32_t *__restrict__ igid) {
+    pdl_wait();   // the predecessor's outputs are complete and visible
+    extern __shared__ unsigned long long s_k[];   // TS_CAP keys
+    const uint2 r = ranges[blockIdx.x];
+    const int n = int(r.y - r.x);
+    if (n <= 8 * T) return;
+    unsigned long long *src = keys + r.x;
+    if (n <= 32 * T) {
+        if (n <= 16 * T) sort_registers<16>(src, n, s_k, igid + r.x);
+        else sort_registers<32>(src, n, s_k, igid + r.x);
         return;
     }
     if (n <= TS_CAP) {
@@ -403,7 +424,7 @@ cudaError_t launch_sort(const qr_frame &f, cudaStream_t s) {
         if (e == cudaSuccess) e = cudaMemsetAsync(ranges, 0, sizeof(uint2) * size_t(tiles), s);
         return e;
     }
-    e = cudaFuncSetAttribute(tile_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(tile_sort_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              int(TS_CAP * sizeof(unsigned long long)));
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 152;
@@ -444,10 +465,13 @@ cudaError_t launch_sort(const qr_frame &f, cudaStream_t s) {
                        (const uint32_t *)chunk_owner, counters, f.tiles_x, tiles, ranges, tcnt, keys);
     }
     if (e != cudaSuccess) return e;
-    e = pdl_launch(tile_sort, dim3(tiles), dim3(T), TS_CAP * sizeof(unsigned long long), s,
+    e = pdl_launch(tile_sort, dim3(tiles), dim3(T), 0, s, (const uint2 *)ranges, keys,
+                   slot<uint32_t>(f, S_IGID));
+    if (e != cudaSuccess) return e;
+    e = pdl_launch(tile_sort_big, dim3(tiles), dim3(T), TS_CAP * sizeof(unsigned long long), s,
                    (const uint2 *)ranges, keys, slot<unsigned long long>(f, S_SCRATCH64),
                    slot<uint32_t>(f, S_IGID));
-    count_launch(4);
+    count_launch(5);
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 

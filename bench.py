@@ -689,6 +689,97 @@ def run_train_eq2(local, steps=10, masks=32):
                     "BF16 512-D, 640x480, K=8"}
 
 
+def run_config_table(local, headline, precision, budget_s=4.0):
+    """The configuration table: GPU and FP64-oracle frames/s of Q-Render (K = 8)
+    and dense Eq. 1 for the tiny, indoor and precision configurations, and the
+    blend's fraction of the measured HBM bandwidth.  Oracle: tiny frames are
+    rendered whole; indoor and precision frames are extrapolated from a
+    random pixel sample (each about budget_s seconds of host time)."""
+    import torch
+    import oracle
+    from paper_2512_20927_gb300 import qrender as q
+    from paper_2512_20927_gb300 import scenes
+    dev = torch.device("cuda", local)
+    hbm, _ = _peaks()
+    cores = os.cpu_count() or 1
+
+    def oracle_fps(g, feat, cam, dense, whole):
+        pr = oracle.project(g, cam.as_array())
+        P = cam.width * cam.height
+        rng = np.random.default_rng(1)
+        kw = dict(want_q=not dense, want_dense=dense, threads=cores,
+                  alpha_min=oracle.ALPHA_MIN_F32, alpha_max=oracle.ALPHA_MAX_F32)
+        if whole:
+            pix = oracle.all_pixels(cam.width, cam.height)
+        else:
+            pix = np.stack([rng.integers(0, cam.width, 2 * cores),
+                            rng.integers(0, cam.height, 2 * cores)], 1).astype(np.int32)
+            t0 = time.perf_counter()
+            oracle.render(pr, feat, K, pix, **kw)
+            per = (time.perf_counter() - t0) / len(pix)
+            n = int(max(cores, min(P, budget_s / max(per, 1e-9))))
+            pix = np.stack([rng.integers(0, cam.width, n), rng.integers(0, cam.height, n)], 1).astype(np.int32)
+        t0 = time.perf_counter()
+        oracle.render(pr, feat, K, pix, **kw)
+        return 1.0 / ((time.perf_counter() - t0) * P / len(pix))
+
+    rows = {}
+    # tiny: 2,000 Gaussians, 128x128, 16-D
+    g, f = scenes.tiny_scene()
+    cam = scenes.tiny_camera()
+    gd = q.gaussians_to_device(g, device=dev)
+    fd = torch.from_numpy(f).to(dev)
+    r = q.render_frame(gd, fd, cam, K=K, dense=True)
+    fr, ids, w, cnt, o = r["frame"], r["ids"], r["weights"], r["counts"], r["out"]
+
+    def qf():
+        q.qr_project(fr, *gd)
+        q.qr_sort(fr)
+        q.qr_select(fr, ids, w, cnt)
+        q.qr_blend(fd, None, ids, w, cnt, o)
+
+    def df():
+        q.qr_project(fr, *gd)
+        q.qr_sort(fr)
+        q.qr_dense(fr, fd, None, r["dense"], r["T_final"])
+    rows["tiny"] = {"gpu_q_fps": round(1000.0 / _time_ms(qf, 50), 1),
+                    "gpu_dense_fps": round(1000.0 / _time_ms(df, 50), 1),
+                    "oracle_q_fps": round(oracle_fps(g, f, cam, False, True), 3),
+                    "oracle_dense_fps": round(oracle_fps(g, f, cam, True, True), 3),
+                    "oracle_frames": "whole 128x128 frames"}
+    # indoor: the headline frame
+    g, f = scenes.room_scene(seed=0, n=N_GAUSS, channels=C)
+    cam = scenes.room_camera(WIDTH, HEIGHT)
+    rows["indoor"] = {"gpu_q_fps": headline["per_k_fps"], "gpu_dense_fps": headline["dense_fps"],
+                      "oracle_q_fps": round(oracle_fps(g, f, cam, False, False), 5),
+                      "oracle_dense_fps": round(oracle_fps(g, f, cam, True, False), 5),
+                      "blend_frac_of_hbm": headline["roofline"]["frac"],
+                      "oracle_frames": "extrapolated from a random pixel sample"}
+    del g, f
+    # precision: 1M room, 1296x968
+    g, f = scenes.room_scene(seed=0, n=1_000_000, channels=C)
+    cam = scenes.room_camera(1296, 968)
+    prow = {"oracle_q_fps": round(oracle_fps(g, f, cam, False, False), 6),
+            "oracle_dense_fps": round(oracle_fps(g, f, cam, True, False), 6),
+            "oracle_frames": "extrapolated from a random pixel sample"}
+    if isinstance(precision, dict):
+        for dt in ("f32", "bf16", "fp8"):
+            if isinstance(precision.get(dt), dict):
+                prow[f"gpu_q_fps_{dt}"] = precision[dt].get("fps")
+                prow[f"blend_frac_of_hbm_{dt}"] = precision[dt].get("blend_frac_of_hbm")
+    gd = q.gaussians_to_device(g, device=dev)
+    fd = torch.from_numpy(f).to(dev)
+    del f
+    r = q.render_frame(gd, fd, cam, K=K, dense=True)
+    fr = r["frame"]
+    prow["gpu_dense_fps_f32"] = round(1000.0 / _time_ms(
+        lambda: (q.qr_project(fr, *gd), q.qr_sort(fr), q.qr_dense(fr, fd, None, r["dense"], r["T_final"])),
+        5), 2)
+    rows["precision"] = prow
+    rows["oracle_cores"] = cores
+    return rows
+
+
 def run_batched(local, steps=3):
     """Many-view workload: 4 rooms (200k, 500k, 1M, 2M Gaussians), 32 views from
     320x240 to 1296x968, 512-D BF16 features, K = 8, autotuned tile shape and
@@ -1023,6 +1114,8 @@ def main():
                       ("batched", lambda: run_batched(local)),
                       ("train_step", lambda: run_train_step(local)),
                       ("train_step_eq2", lambda: run_train_eq2(local)))
+            extras = extras + (("config_table",
+                                lambda: run_config_table(local, line, line.get("precision"))),)
             for key, fn in extras:
                 try:
                     line[key] = fn()

@@ -955,11 +955,31 @@ def profile_mode(local, mode, steps):
     select, blend), blend, fused (blend + relevance in one kernel), eq2 (the
     Eq. 2 loss and its gradient, 32 patches), rules (top-K then Stratified-K
     selection), dense (Eq. 1) -- on the 500k indoor room (object: the object
-    scene), 640x480, 512-D FP32, K = 8."""
+    scene), 640x480, 512-D FP32, K = 8; batch: the many-view launch on a small
+    batch (see below)."""
     import torch
     from paper_2512_20927_gb300 import qrender as q
     from paper_2512_20927_gb300 import scenes
     dev = torch.device("cuda", local)
+    if mode == "batch":
+        # a small many-view batch (2 rooms of 200k and 500k Gaussians, 4 views of
+        # 640x480, BF16 512-D, K = 8, 16x16 tiles, pixel pairs): the fused
+        # select + blend launch alone
+        from paper_2512_20927_gb300.batch import Batch, Scene
+        sc = []
+        for seed, n in enumerate((200_000, 500_000)):
+            g, f = scenes.room_scene(seed=seed, n=n, channels=C)
+            gd = tuple(t.to(dev) for t in q.gaussians_to_device(g, device="cpu"))
+            sc.append(Scene(gd, q.qr_quantize_bf16(torch.from_numpy(f).to(dev))))
+            del f
+        views = [(i % 2, scenes.room_camera(WIDTH, HEIGHT, yaw=0.8 * i)) for i in range(4)]
+        b = Batch(sc, views, K=K, tile=(16, 16), group=2)
+        b.project_sort()
+        torch.cuda.synchronize()
+        for _ in range(steps):
+            b.select_blend()
+        torch.cuda.synchronize()
+        return {"profile": mode, "steps": steps, "pixels": int(b.offsets[-1])}
     if mode == "object":
         g, feat = scenes.object_scene(seed=0, n=N_GAUSS, channels=C)
         cam = scenes.object_camera(WIDTH, HEIGHT)
@@ -1013,7 +1033,7 @@ def main():
     ap.add_argument("--profile-relevance", action="store_true",
                     help="only run the relevance GEMM on a 1.07 GB map (for ncu captures)")
     ap.add_argument("--profile-mode", default=None,
-                    choices=["indoor", "object", "blend", "fused", "eq2", "rules", "dense"],
+                    choices=["indoor", "object", "blend", "fused", "eq2", "rules", "dense", "batch"],
                     help="set up one workload and run --steps eager launches of one part (for ncu)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the many-view and training-step measurements")

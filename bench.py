@@ -539,7 +539,7 @@ def run_fused_relevance(ctx, hbm_peak, steps=20):
     Qn = 64
     qbits = q.qr_quantize_bf16(torch.from_numpy(scenes.unit_queries(7, Qn, C)).to(fdev.device))
     qbits = qbits.view(torch.int16)
-    two = _time_ms(lambda: (q.qr_blend(fdev, None, ids, w, cnt, out, width=fr.width),
+    two = _time_ms(lambda: (q.qr_blend(fdev, None, ids, w, cnt, out),
                             q.qr_relevance(out, qbits)), steps)
     fused = _time_ms(lambda: q.qr_blend_relevance(fdev, None, ids, w, cnt, qbits, width=fr.width),
                      steps)
@@ -577,9 +577,9 @@ def run_object(local, hbm_peak, steps=20):
         q.qr_project(fr, *gdev)
         q.qr_sort(fr)
         q.qr_select(fr, ids, w, cnt)
-        q.qr_blend(fdev, None, ids, w, cnt, out, width=fr.width)
+        q.qr_blend(fdev, None, ids, w, cnt, out)
     ms = _time_ms(frame, steps)
-    blend_ms = _time_ms(lambda: q.qr_blend(fdev, None, ids, w, cnt, out, width=fr.width), steps)
+    blend_ms = _time_ms(lambda: q.qr_blend(fdev, None, ids, w, cnt, out), steps)
     alg = U * C * 4 + P * K * 8 + P + P * C * 4
     return {"workload": "object-centric FP32: 500k Gaussians (70 % within 1 cm of a unit sphere, "
                         "30 % inside), 640x480 from 2.6 m, 512-D, Q-Render K=8",
@@ -629,9 +629,9 @@ def run_precision(local, hbm_peak, steps=10, sample_px=160):
             q.qr_project(fr, *gdev)
             q.qr_sort(fr)
             q.qr_select(fr, ids, w, cnt)
-            q.qr_blend(table, sc, ids, w, cnt, o, width=fr.width)
+            q.qr_blend(table, sc, ids, w, cnt, o)
         ms = _time_ms(frame, steps)
-        bms = _time_ms(lambda: q.qr_blend(table, sc, ids, w, cnt, o, width=fr.width), steps)
+        bms = _time_ms(lambda: q.qr_blend(table, sc, ids, w, cnt, o), steps)
         U = int(torch.unique(ids[ids >= 0]).numel())
         alg = U * (C * bf + (4 if name == "fp8" else 0)) + P * K * 8 + P + P * C * 4
         got = o.cpu().numpy()[idx]
@@ -813,10 +813,19 @@ def run_batched(local, steps=3):
     rel_ms = r0.elapsed_time(r1) / 3
     rel_bytes = pixels * C * 4 + pixels * 64 * 4
     rel_flops = 2.0 * pixels * C * 64
+    # the persistent select + blend launch alone: bytes written (the FP32 map,
+    # ids, weights, counts); the feature rows it reads are not counted
+    sb_ms = _time_ms(best.select_blend, 5)
+    sb_bytes = pixels * C * 4 + pixels * K * 8 + pixels
+    hbm = _peaks()[0]
     return {"views": len(views), "pixels": pixels, "ms_per_batch": round(ms, 3),
             "views_per_s": round(len(views) * 1000.0 / ms, 2),
             "mpixels_per_s": round(pixels / ms / 1000.0, 1),
-            "autotune_ms": timings, "chosen": {"tile": list(best.tile), "group": best.group},
+            "autotune_ms": timings,
+            "chosen": {"tile": list(best.tile), "group": best.group, "chunks": best.chunks},
+            "select_blend": {"ms": round(sb_ms, 4), "GB_per_s": round(sb_bytes / sb_ms / 1e6, 1),
+                             "frac_of_hbm": round(sb_bytes / sb_ms / 1e6 / hbm, 4),
+                             "bytes": sb_bytes, "bytes_counted": "map + ids + weights + counts written"},
             "relevance": {"ms": round(rel_ms, 4), "GB_per_s": round(rel_bytes / rel_ms / 1e6, 1),
                           "TFLOP_per_s": round(rel_flops / rel_ms / 1e9, 1)}}
 
@@ -954,7 +963,9 @@ def profile_mode(local, mode, steps):
     ncu captures: indoor / object (a whole Q-Render frame: project, sort,
     select, blend), blend, fused (blend + relevance in one kernel), eq2 (the
     Eq. 2 loss and its gradient, 32 patches), rules (top-K then Stratified-K
-    selection), dense (Eq. 1) -- on the 500k indoor room (object: the object
+    selection), dense (Eq. 1), blend_bf16 / blend_fp8 (the blend from a BF16
+    table / FP8 E4M3 codes with per-Gaussian scales, tile-ordered pixel
+    groups) -- on the 500k indoor room (object: the object
     scene), 640x480, 512-D FP32, K = 8; batch: the many-view launch on a small
     batch (see below)."""
     import torch
@@ -963,7 +974,8 @@ def profile_mode(local, mode, steps):
     dev = torch.device("cuda", local)
     if mode == "batch":
         # a small many-view batch (2 rooms of 200k and 500k Gaussians, 4 views of
-        # 640x480, BF16 512-D, K = 8, 16x16 tiles, pixel pairs): the fused
+        # 640x480, BF16 512-D, K = 8, 16x16 tiles, built-in pixel groups and
+        # channel chunks): the fused
         # select + blend launch alone
         from paper_2512_20927_gb300.batch import Batch, Scene
         sc = []
@@ -973,7 +985,7 @@ def profile_mode(local, mode, steps):
             sc.append(Scene(gd, q.qr_quantize_bf16(torch.from_numpy(f).to(dev))))
             del f
         views = [(i % 2, scenes.room_camera(WIDTH, HEIGHT, yaw=0.8 * i)) for i in range(4)]
-        b = Batch(sc, views, K=K, tile=(16, 16), group=2)
+        b = Batch(sc, views, K=K, tile=(16, 16))
         b.project_sort()
         torch.cuda.synchronize()
         for _ in range(steps):
@@ -996,6 +1008,11 @@ def profile_mode(local, mode, steps):
     tg = torch.from_numpy(scenes.patch_targets(32, C, seed=5)).to(dev)
     dout = torch.empty_like(o)
     tf = torch.empty(fr.pixels, device=dev)
+    tab, tsc = fd, None
+    if mode == "blend_bf16":
+        tab = q.qr_quantize_bf16(fd)
+    elif mode == "blend_fp8":
+        tab, tsc = q.qr_quantize_fp8(fd)
     torch.cuda.synchronize()
     for _ in range(steps):
         if mode in ("indoor", "object"):
@@ -1005,6 +1022,8 @@ def profile_mode(local, mode, steps):
             q.qr_blend(fd, None, ids, w, cnt, o)
         elif mode == "blend":
             q.qr_blend(fd, None, ids, w, cnt, o)
+        elif mode in ("blend_bf16", "blend_fp8"):
+            q.qr_blend(tab, tsc, ids, w, cnt, o)
         elif mode == "fused":
             q.qr_blend_relevance(fd, None, ids, w, cnt, qb, width=fr.width)
         elif mode == "eq2":
@@ -1033,7 +1052,8 @@ def main():
     ap.add_argument("--profile-relevance", action="store_true",
                     help="only run the relevance GEMM on a 1.07 GB map (for ncu captures)")
     ap.add_argument("--profile-mode", default=None,
-                    choices=["indoor", "object", "blend", "fused", "eq2", "rules", "dense", "batch"],
+                    choices=["indoor", "object", "blend", "blend_bf16", "blend_fp8", "fused", "eq2",
+                             "rules", "dense", "batch"],
                     help="set up one workload and run --steps eager launches of one part (for ncu)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the many-view and training-step measurements")

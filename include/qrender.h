@@ -214,8 +214,9 @@ qr_status qr_select_rule(const qr_frame *frame, qr_rule rule, int32_t *ids, floa
  * Pixels with counts 0 get zeros.  ids must lie in [0, n_gauss).
  * width > 0 declares the P pixels a row-major image of that width: pixels are
  * then visited in 16x16 screen tiles with 2x2 groups sharing feature rows;
- * width = 0 groups consecutive pixels.  Only the summation order (and speed)
- * depends on it. */
+ * width = 0 groups consecutive pixels, whose output rows then form one
+ * contiguous run per group (the faster order on GB300, and the one qr_render
+ * uses).  Only the summation order (and speed) depends on it. */
 qr_status qr_blend(const void *feat, const float *feat_scale, qr_dtype dtype, int32_t C,
                    int64_t n_gauss, const int32_t *ids, const float *weights,
                    const uint8_t *counts, int64_t P, int32_t K, int32_t width, float *out,
@@ -286,15 +287,22 @@ qr_status qr_batch_prepare(const qr_view *views, int32_t n_views, void *ws, size
                            uint32_t *total_tiles, qr_stream stream);
 
 /* Algorithm 1 (selection and blend) for every tile of every prepared view in
- * one persistent launch: CTAs take (view, tile) items from a device counter,
- * select each pixel's quantile Gaussians into shared memory and blend them
- * there (same arithmetic as qr_select + qr_blend; ids/weights/counts are also
- * written).  dtype and C are shared by the batch; group = pixels per warp in
- * the blend (4, 2 or 1; 0 = largest allowed by K), ctas_per_sm caps the
- * resident CTAs per SM (0 = occupancy limit).  Capturable in a CUDA graph. */
+ * one persistent launch: CTAs take (view, tile) items from a device counter;
+ * in each CTA four warps select a tile's quantile Gaussians into one of two
+ * shared-memory buffers while the other warps blend the previously selected
+ * tile from the other buffer (same selection arithmetic as qr_select, the
+ * same per-channel sums as qr_blend with width > 0; ids/weights/counts are
+ * also written).  dtype and C are shared by the batch (rows of 32, 64 or 128
+ * sixteen-byte vectors: e.g. 512-D F32 / BF16 / FP8); group = pixels per
+ * warp in the blend (4, 2 or 1; 0 = largest allowed by K); chunks = channel
+ * slices per feature row for groups of 4, taken by different blend warps
+ * (1, 2 or 4 dividing the row's vectors per lane; 0 = the built-in choice);
+ * ctas_per_sm caps the resident CTAs per SM (0 = occupancy limit).  Results
+ * do not depend on group size or chunks beyond the summation order of a
+ * pixel's rows (chunks: not at all).  Capturable in a CUDA graph. */
 qr_status qr_render_batch(const void *ws, int32_t n_views, uint32_t total_tiles, qr_dtype dtype,
-                          int32_t C, int32_t K, int32_t group, int32_t ctas_per_sm,
-                          qr_stream stream);
+                          int32_t C, int32_t K, int32_t group, int32_t chunks,
+                          int32_t ctas_per_sm, qr_stream stream);
 
 /* ---------------------------------------------------------------- backward */
 
@@ -492,6 +500,16 @@ uint64_t qr_launch_count(void);
  * that follow (0 restores the default), so a test can make a wait run out
  * without anything hanging.  Not for production use; not thread-safe. */
 void qr_set_wait_limit(uint32_t polls);
+
+/* Tuning: the blend of rows of 2 or 4 sixteen-byte vectors per lane
+ * (e.g. 512-D BF16 / F32 rows) with K <= 8 splits each feature row into
+ * `chunks` channel slices taken by different warps (1, 2 or 4; 0 restores the
+ * built-in choice: at most 16 accumulators per pixel and lane).  More chunks
+ * mean fewer registers per thread and more warps per SM.  The sums and their
+ * order per channel do not change, so results are bit-identical for every
+ * setting.  Applies to qr_blend and qr_render launched afterwards; returns
+ * QR_ERR_INVALID_ARG for other values.  Not thread-safe. */
+qr_status qr_set_blend_chunks(int32_t chunks);
 
 #ifdef __cplusplus
 }

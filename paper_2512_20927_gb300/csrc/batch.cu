@@ -5,26 +5,28 @@
 //
 // GB300 design: a grid of (SMs x resident CTAs) persistent CTAs pulls
 // (view, tile) work items from one atomic counter, so views of very different
-// sizes balance without a host round trip.  For each tile:
-//   1. selection (thread per pixel): the tile's depth-ordered list is staged
-//      through shared memory 256 entries at a time; each warp culls the
-//      staged entries against its box of pixel centres and walks only the
-//      survivors, four per step, with the same alpha' evaluation and the same
-//      Algorithm 1 rule as qr_select; the kept ids and normalised weights
-//      stay in shared memory and are also written out (coalesced tile-row
+// sizes balance without a host round trip.  Each CTA is warp-specialised and
+// double-buffered, so the latency-bound selection of one tile overlaps the
+// bandwidth-bound blend of the previous one:
+//   1. selection (warps 0-3, select_tile.cuh, the same code as qr_select):
+//      the tile's depth-ordered list is staged through shared memory, culled
+//      per warp against the warp's box of pixel centres and walked two pixels
+//      per thread; the kept ids and normalised weights go to one of two
+//      shared-memory buffers and are also written out (coalesced tile-row
 //      runs) for a backward pass;
-//   2. blend (warp per 2x2 / 2x1 pixel group, like qr_blend): equal ids of the
-//      group are merged with __match_any_sync, the group's weights of each
-//      distinct row are gathered into a per-warp shared-memory table, each
-//      distinct feature row is read once with 16-byte loads and accumulated
-//      into every pixel of the group, and the rows of the map are written
-//      with streaming stores.
-// Per-view descriptors live in device memory (qr_batch_prepare), the counter
-// is cleared by a memset on the stream, so the launch can sit in a CUDA graph.
+//   2. blend (8 warps, warp per 2x2 / 2x1 pixel group and channel chunk, like
+//      qr_blend): equal ids of the group are merged with __match_any_sync, the
+//      group's weights of each distinct row are gathered into a per-warp
+//      table, each distinct feature row (or its chunk) is read once with
+//      16-byte loads and accumulated into every pixel of the group, and the
+//      rows of the map are written with streaming stores.
+// Hand-over between the roles uses named barriers (below).  Per-view
+// descriptors live in device memory (qr_batch_prepare), the counter is
+// cleared by a memset on the stream, so the launch can sit in a CUDA graph.
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
-#include "qr_internal.cuh"
+#include "select_tile.cuh"
 
 namespace qr {
 
@@ -126,136 +128,111 @@ __device__ __forceinline__ void st_cs(float4 *p, float4 v) {
                  :: "l"(p), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w) : "memory");
 }
 
-// Dynamic shared memory: s_ids [256][K|1] int32, s_w [256][K|1] float.
-template <int DT, int VPL, int G>
-__global__ void __launch_bounds__(T)
+// ------------------------------------------------------------------ the kernel
+// Warp roles of a CTA: warps 0..3 select (select_tile, 128 threads, two pixels
+// each), warps 4..4+NBW-1 blend.  Two shared-memory buffers hold a tile's
+// kept ids, normalised weights and counts; the selection fills one while the
+// blend warps read the other.  Hand-over uses hardware named barriers:
+//   FULL[b]  (ids 2, 3): selection arrives once buffer b holds tile n (or the
+//                        end marker), blend warps wait;
+//   EMPTY[b] (ids 4, 5): blend warps arrive once done with buffer b, the
+//                        selection waits before refilling it (from its third
+//                        tile on) and once more after the end marker for the
+//                        last tile's arrival, so every arrival is matched;
+//   id 1:                the selection threads among themselves.
+// Every thread of both roles runs the same number of barrier phases on each
+// id, so no phase is left open and no wait can be missed.
+constexpr int kNBW = 8;                               // blend warps
+constexpr int kBT = kSelThreads + 32 * kNBW;          // threads per CTA
+constexpr int kItemEnd = -1;
+
+// Barrier ids are immediates (2 + b or 4 + b picked by a branch on b), so
+// the kernel uses barriers 0..5 only.
+template <int ID>
+__device__ __forceinline__ void bar_sync_id() {
+    asm volatile("bar.sync %0, %1;" ::"n"(ID), "n"(kBT) : "memory");
+}
+template <int ID>
+__device__ __forceinline__ void bar_arrive_id() {
+    asm volatile("bar.arrive %0, %1;" ::"n"(ID), "n"(kBT) : "memory");
+}
+__device__ __forceinline__ void full_sync(int b) { if (b) bar_sync_id<3>(); else bar_sync_id<2>(); }
+__device__ __forceinline__ void full_arrive(int b) { if (b) bar_arrive_id<3>(); else bar_arrive_id<2>(); }
+__device__ __forceinline__ void empty_sync(int b) { if (b) bar_sync_id<5>(); else bar_sync_id<4>(); }
+__device__ __forceinline__ void empty_arrive(int b) { if (b) bar_arrive_id<5>(); else bar_arrive_id<4>(); }
+
+__device__ __forceinline__ int find_view(const BatchView *views, int n_views, uint32_t item) {
+    int lo = 0, hi = n_views;   // last view with tile_base <= item
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (views[mid].tile_base <= item) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// Dynamic shared memory: ids [2][256][KSB] int32, weights [2][256][KSB] float.
+template <int DT, int VPL, int G, int NCH>
+__global__ void __launch_bounds__(kBT, DT == QR_FP8E4M3 ? 1 : 2)
 batch_kernel(const BatchView *__restrict__ views, int n_views, uint32_t total_items,
-             uint32_t *__restrict__ counter) {
-    constexpr int CPV = VecT<DT>::C;
-    constexpr int ROWV = 32 * VPL;
-    constexpr unsigned FULL = 0xffffffffu;
-    __shared__ float4 s_m[T];
-    __shared__ float4 s_c[T];
-    __shared__ float s_a[T];
-    __shared__ float s_h[T];
-    __shared__ uint32_t s_g[T];
-    __shared__ uint32_t s_item;
-    __shared__ uint8_t s_cnt[T];
-    __shared__ __align__(16) float s_tw[T / 32][32][G];   // per-warp row-weight table
-    __shared__ int s_tid[T / 32][32];
-    extern __shared__ unsigned char s_dyn[];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+             uint32_t *__restrict__ counter, int KSB) {
+    __shared__ SelStage st;
+    __shared__ float s_D[kSelPix];
+    __shared__ uint8_t s_cnt[2][kSelPix];
+    __shared__ int s_item[2];
+    __shared__ __align__(16) float s_tw[kNBW][32][G];   // per blend warp: row-weight table
+    __shared__ int s_tid[kNBW][32];
+    extern __shared__ __align__(16) unsigned char s_dyn[];
+    int32_t *s_ids0 = reinterpret_cast<int32_t *>(s_dyn);
+    float *s_w0 = reinterpret_cast<float *>(s_dyn) + 2 * kSelPix * KSB;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-    for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1u);
-        __syncthreads();
-        const uint32_t item = s_item;
-        __syncthreads();
-        if (item >= total_items) break;
-        int v = 0;
-        for (int lo = 0, hi = n_views; hi - lo > 1;) {      // last view with tile_base <= item
-            const int mid = (lo + hi) >> 1;
-            if (views[mid].tile_base <= item) lo = mid; else hi = mid;
-            v = lo;
-        }
-        const BatchView &V = views[v];
-        const int K = V.K;
-        const int KS = K | 1;   // odd stride: per-pixel slots fall in distinct banks
-        int32_t *s_ids = reinterpret_cast<int32_t *>(s_dyn);          // [256][KS]
-        float *s_w = reinterpret_cast<float *>(s_dyn) + KS * T;       // [256][KS]
-        const int tile = int(item - V.tile_base);
-        const int tx = tile % V.tiles_x, ty = tile / V.tiles_x;
-        const int tile_w = V.tile_w, tile_h = T / tile_w;
-
-        // ---------------- 1. selection (thread per pixel)
-        {
-            constexpr unsigned FULL = 0xffffffffu;
-            const int lane = threadIdx.x & 31;
-            const int lx = int(threadIdx.x) % tile_w, ly = int(threadIdx.x) / tile_w;
-            const int px = tx * tile_w + lx, py = ty * tile_h + ly;
-            const bool inside = px < V.W && py < V.H;
-            const float ux = float(px) + 0.5f, uy = float(py) + 0.5f;
-            const uint2 range = V.ranges[tile];
-            const float tau_stop = __fdiv_rn(1.0f, float(K + 1));
-            Walk wk{1.0f, 1.0f, __fdiv_rn(float(K), float(K + 1)), 0, 0, !inside};
-            // the warp's box of pixel centres
-            float bx0 = ux, bx1 = ux, by0 = uy, by1 = uy;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                bx0 = fminf(bx0, __shfl_xor_sync(FULL, bx0, o));
-                bx1 = fmaxf(bx1, __shfl_xor_sync(FULL, bx1, o));
-                by0 = fminf(by0, __shfl_xor_sync(FULL, by0, o));
-                by1 = fmaxf(by1, __shfl_xor_sync(FULL, by1, o));
+    if (warp < kSelThreads / 32) {
+        // ------------------------------------------------ selection role
+        using Bar = NamedBarrier<1, kSelThreads>;
+        for (int n = 0;; ++n) {
+            const int b = n & 1;
+            if (n >= 2) empty_sync(b);   // the blend warps are done with buffer b
+            if (threadIdx.x == 0) {
+                const uint32_t it = atomicAdd(counter, 1u);
+                s_item[b] = it < total_items ? int(it) : kItemEnd;
             }
-            uint32_t gnext = range.x + threadIdx.x < range.y ? V.igid[range.x + threadIdx.x] : 0u;
-            for (uint32_t b = range.x; b < range.y; b += T) {
-                if (__syncthreads_count(wk.done) == T) break;
-                if (b + threadIdx.x < range.y) {
-                    s_g[threadIdx.x] = gnext;
-                    s_m[threadIdx.x] = V.rec_m[gnext];
-                    s_c[threadIdx.x] = V.rec_w[gnext];
-                    s_a[threadIdx.x] = V.rec_a[gnext];
-                    s_h[threadIdx.x] = V.rec_h[gnext];
-                }
-                __syncthreads();
-                {
-                    const uint32_t idx = b + T + threadIdx.x;
-                    gnext = idx < range.y ? V.igid[idx] : 0u;
-                }
-                const int nb = int(min(uint32_t(T), range.y - b));
-                for (int c0 = 0; c0 < nb; c0 += 32) {
-                    if (__all_sync(FULL, wk.done)) break;
-                    // per-warp culling against the box, as in qr_select
-                    const int jl = c0 + lane;
-                    bool pass = false;
-                    if (jl < nb)
-                        pass = !(box_min_half_q(s_m[jl], s_c[jl], bx0, bx1, by0, by1) * 0.999f > s_h[jl] + 1e-3f);
-                    unsigned todo = __ballot_sync(FULL, pass);
-                    while (todo) {
-                        int jj[4];
-                        bool valid[4];
+            Bar::sync();
+            const int item = s_item[b];
+            if (item == kItemEnd) {
+                full_arrive(b);
+                if (n >= 1) empty_sync(b ^ 1);   // the last tile's arrival
+                break;
+            }
+            const BatchView &V = views[find_view(views, n_views, uint32_t(item))];
+            const int K = V.K;
+            int32_t *s_ids = s_ids0 + b * kSelPix * KSB;
+            float *s_w = s_w0 + b * kSelPix * KSB;
+            const int tile = item - int(V.tile_base);
+            const int tx = tile % V.tiles_x, ty = tile / V.tiles_x;
+            const int tile_w = V.tile_w, tile_h = kSelPix / tile_w;
+            select_tile<Bar>(V.rec_m, V.rec_w, V.rec_a, V.rec_h, V.igid, V.ranges[tile], V.W, V.H,
+                             tile_w, tx, ty, K, V.alpha_min, V.alpha_max, st, s_ids, s_w, s_D,
+                             s_cnt[b]);
+            // normalise this thread's two pixels in place (Algorithm 1's 1 / (1 - T^Q))
+            {
+                const int lx = threadIdx.x % tile_w, ly = 2 * (threadIdx.x / tile_w);
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            valid[u] = todo != 0u;
-                            jj[u] = valid[u] ? c0 + __ffs(todo) - 1 : jj[0];
-                            todo &= todo - 1u;
-                        }
-                        float hq[4];
-                        unsigned reach = 0;
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            hq[u] = eval_half_q(ux, uy, s_m[jj[u]], s_c[jj[u]]).half_q;
-                            reach |= unsigned(valid[u] && !(hq[u] > s_h[jj[u]])) << u;
-                        }
-                        if (wk.done || !reach) continue;
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            if (wk.done || !((reach >> u) & 1u)) continue;
-                            const float a = eval_alpha(s_a[jj[u]], hq[u], V.alpha_max);
-                            if (a < V.alpha_min) continue;
-                            const float Tt = wk.T * (1.0f - a);
-                            if (Tt < wk.thr || Tt < tau_stop)
-                                walk_event(wk, Tt, a, tau_stop, K, s_g[jj[u]], threadIdx.x, KS, s_ids, s_w);
-                            else
-                                wk.T = Tt;
-                        }
-                        if (wk.done) break;
+                for (int r = 0; r < 2; ++r) {
+                    const int sl = (ly + r) * tile_w + lx;
+                    const int c = s_cnt[b][sl];
+                    const float D = s_D[sl];
+                    for (int j = 0; j < K; ++j) {
+                        const bool has = j < c;
+                        s_w[sl * KSB + j] = has ? __fdiv_rn(s_w[sl * KSB + j], D) : 0.0f;
+                        if (!has) s_ids[sl * KSB + j] = -1;
                     }
                 }
             }
-            // normalise this pixel's weights (Algorithm 1's 1 / (1 - T^Q)) in place
-            const float D = 1.0f - wk.TQ;
-            for (int j = 0; j < K; ++j) {
-                const bool has = j < wk.m;
-                s_w[threadIdx.x * KS + j] = has ? __fdiv_rn(s_w[threadIdx.x * KS + j], D) : 0.0f;
-                if (!has) s_ids[threadIdx.x * KS + j] = -1;
-            }
-            s_cnt[threadIdx.x] = uint8_t(wk.m);
-            __syncthreads();
+            Bar::sync();
             // coalesced output for a backward pass: each tile row is tile_w * K
             // consecutive ids and weights in the view
             const int rowlen = tile_w * K;
-            for (int rem = threadIdx.x; rem < rowlen; rem += T) {
+            for (int rem = threadIdx.x; rem < rowlen; rem += kSelThreads) {
                 const int cx = rem / K, j = rem - cx * K;
                 const int gx = tx * tile_w + cx;
                 if (gx >= V.W) continue;
@@ -264,18 +241,43 @@ batch_kernel(const BatchView *__restrict__ views, int n_views, uint32_t total_it
                     if (gy >= V.H) break;
                     const int sl = row * tile_w + cx;
                     const int64_t o = (int64_t(gy) * V.W + gx) * K + j;
-                    V.ids[o] = s_ids[sl * KS + j];
-                    V.w[o] = s_w[sl * KS + j];
+                    V.ids[o] = s_ids[sl * KSB + j];
+                    V.w[o] = s_w[sl * KSB + j];
                 }
             }
-            if (inside) V.cnt[int64_t(py) * V.W + px] = s_cnt[threadIdx.x];
+            for (int e = threadIdx.x; e < kSelPix; e += kSelThreads) {
+                const int gx = tx * tile_w + e % tile_w, gy = ty * tile_h + e / tile_w;
+                if (gx < V.W && gy < V.H) V.cnt[int64_t(gy) * V.W + gx] = s_cnt[b][e];
+            }
+            full_arrive(b);
         }
-        __syncthreads();
-
-        // ---------------- 2. blend (warp per pixel group, rows shared in registers)
-                const int half_w = tile_w / 2;
-        for (int gi = warp; gi < T / G; gi += T / 32) {
-            const int mm = lane / K, j = lane - mm * K;
+        return;
+    }
+    // ---------------------------------------------------- blend role
+    constexpr int CPV = VecT<DT>::C;
+    constexpr int CV = 32 * VPL;                 // vectors of a channel chunk
+    constexpr int ROWV = CV * NCH;               // vectors of a row
+    constexpr int U = VPL >= 2 ? 2 : 4;          // rows in flight
+    constexpr unsigned FULL = 0xffffffffu;
+    constexpr int NITEMS = (kSelPix / G) * NCH;
+    const int bw = warp - kSelThreads / 32;
+    for (int n = 0;; ++n) {
+        const int b = n & 1;
+        full_sync(b);   // buffer b holds a selected tile (or the end marker)
+        const int item = s_item[b];
+        if (item == kItemEnd) break;
+        const BatchView &V = views[find_view(views, n_views, uint32_t(item))];
+        const int K = V.K;
+        const int32_t *s_ids = s_ids0 + b * kSelPix * KSB;
+        const float *s_w = s_w0 + b * kSelPix * KSB;
+        const int tile = item - int(V.tile_base);
+        const int tx = tile % V.tiles_x, ty = tile / V.tiles_x;
+        const int tile_w = V.tile_w, tile_h = kSelPix / tile_w;
+        const int half_w = tile_w / 2;
+        const uint4 *feat = reinterpret_cast<const uint4 *>(V.feat);
+        const int mm = lane / K, j = lane - mm * K;
+        for (int it = bw; it < NITEMS; it += kNBW) {
+            const int gi = it / NCH, ch = it - gi * NCH;
             int lx, ly;
             if (G == 4) { lx = 2 * (gi % half_w) + (mm & 1); ly = 2 * (gi / half_w) + (mm >> 1); }
             else if (G == 2) { lx = 2 * (gi % half_w) + mm; ly = gi / half_w; }
@@ -287,9 +289,8 @@ batch_kernel(const BatchView *__restrict__ views, int n_views, uint32_t total_it
             int id = -1;
             float w = 0.f;
             if (p >= 0) {
-                id = s_ids[loc * KS + j];
-                w = s_w[loc * KS + j];
-                if (id >= 0 && DT == QR_FP8E4M3) w *= V.fscale[id];
+                id = s_ids[loc * KSB + j];
+                w = s_w[loc * KSB + j];
             }
             const unsigned peers = __match_any_sync(FULL, id);
             const int leader = __ffs(peers) - 1;
@@ -298,49 +299,53 @@ batch_kernel(const BatchView *__restrict__ views, int n_views, uint32_t total_it
             // the G weights of each distinct row, gathered once (a pixel that
             // lists an id twice gets the sum)
 #pragma unroll
-            for (int g = 0; g < G; ++g) s_tw[warp][lane][g] = 0.f;
+            for (int g = 0; g < G; ++g) s_tw[bw][lane][g] = 0.f;
             __syncwarp();
             if (id >= 0) {
                 const int slot = __popc(leaders & ((1u << leader) - 1u));
-                atomicAdd(&s_tw[warp][slot][mm], w);
-                if (lane == leader) s_tid[warp][slot] = id;
+                atomicAdd(&s_tw[bw][slot][mm], w);
+                if (lane == leader) s_tid[bw][slot] = id;
             }
             __syncwarp();
             float acc[G][VPL][CPV];
 #pragma unroll
             for (int g = 0; g < G; ++g)
 #pragma unroll
-                for (int vv = 0; vv < VPL; ++vv)
+                for (int v = 0; v < VPL; ++v)
 #pragma unroll
-                    for (int q = 0; q < CPV; ++q) acc[g][vv][q] = 0.f;
-            const uint4 *feat = reinterpret_cast<const uint4 *>(V.feat);
-            for (int r0 = 0; r0 < nrows; r0 += 2) {
-                uint4 r[2][VPL];
+                    for (int q = 0; q < CPV; ++q) acc[g][v][q] = 0.f;
+            const uint4 *fch = feat + ch * CV + lane;
+            for (int r0 = 0; r0 < nrows; r0 += U) {
+                uint4 r[U][VPL];
+                float sc[U];
 #pragma unroll
-                for (int u = 0; u < 2; ++u) {
+                for (int u = 0; u < U; ++u) {
                     const bool ok = r0 + u < nrows;
-                    const uint4 *row = feat + int64_t(ok ? s_tid[warp][r0 + u] : 0) * ROWV + lane;
+                    const int rid = ok ? s_tid[bw][r0 + u] : 0;
+                    const uint4 *row = fch + int64_t(rid) * ROWV;
 #pragma unroll
-                    for (int vv = 0; vv < VPL; ++vv)
-                        r[u][vv] = ok ? ldg_nc(row + 32 * vv) : make_uint4(0, 0, 0, 0);
+                    for (int v = 0; v < VPL; ++v)
+                        r[u][v] = ok ? ldg_nc(row + 32 * v) : make_uint4(0, 0, 0, 0);
+                    if (DT == QR_FP8E4M3) sc[u] = ok ? V.fscale[rid] : 0.f;
                 }
 #pragma unroll
-                for (int u = 0; u < 2; ++u) {
+                for (int u = 0; u < U; ++u) {
                     if (r0 + u >= nrows) break;
                     float wg[G];
 #pragma unroll
-                    for (int g = 0; g < G; ++g) wg[g] = s_tw[warp][r0 + u][g];
+                    for (int g = 0; g < G; ++g)
+                        wg[g] = DT == QR_FP8E4M3 ? s_tw[bw][r0 + u][g] * sc[u] : s_tw[bw][r0 + u][g];
                     float fv[VPL][CPV];
 #pragma unroll
-                    for (int vv = 0; vv < VPL; ++vv) dec_vec<DT>(r[u][vv], fv[vv]);
+                    for (int v = 0; v < VPL; ++v) dec_vec<DT>(r[u][v], fv[v]);
 #pragma unroll
                     for (int g = 0; g < G; ++g)
                         if (wg[g] != 0.f) {
 #pragma unroll
-                            for (int vv = 0; vv < VPL; ++vv)
+                            for (int v = 0; v < VPL; ++v)
 #pragma unroll
                                 for (int q = 0; q < CPV; q += 2)
-                                    fma2b(acc[g][vv] + q, wg[g], fv[vv][q], fv[vv][q + 1]);
+                                    fma2b(acc[g][v] + q, wg[g], fv[v][q], fv[v][q + 1]);
                         }
                 }
             }
@@ -348,49 +353,72 @@ batch_kernel(const BatchView *__restrict__ views, int n_views, uint32_t total_it
             for (int g = 0; g < G; ++g) {
                 const int64_t pg = __shfl_sync(FULL, p, g * K < 32 ? g * K : 0);
                 if (pg >= 0) {
-                    float4 *o = reinterpret_cast<float4 *>(V.out) + pg * (int64_t(ROWV) * CPV / 4);
+                    float4 *o = reinterpret_cast<float4 *>(V.out) + pg * (int64_t(ROWV) * CPV / 4) +
+                                ch * (CV * CPV / 4);
 #pragma unroll
-                    for (int vv = 0; vv < VPL; ++vv)
+                    for (int v = 0; v < VPL; ++v)
 #pragma unroll
                         for (int q = 0; q < CPV / 4; ++q)
-                            st_cs(o + int64_t(lane + 32 * vv) * (CPV / 4) + q,
-                                  make_float4(acc[g][vv][4 * q], acc[g][vv][4 * q + 1],
-                                              acc[g][vv][4 * q + 2], acc[g][vv][4 * q + 3]));
+                            st_cs(o + int64_t(lane + 32 * v) * (CPV / 4) + q,
+                                  make_float4(acc[g][v][4 * q], acc[g][v][4 * q + 1],
+                                              acc[g][v][4 * q + 2], acc[g][v][4 * q + 3]));
                 }
             }
-            __syncwarp();   // the table is rewritten by the next group
+            __syncwarp();   // the table is rewritten by the next item
         }
-        __syncthreads();
+        empty_arrive(b);   // buffer b may be refilled
     }
 }
 
-template <int DT, int VPL, int G>
+template <int DT, int VT, int G, int NCH>
 cudaError_t run_batch(const BatchView *dviews, int n_views, uint32_t total, uint32_t *counter,
                       int K, int ctas_per_sm, cudaStream_t s) {
-    const size_t dyn = size_t(K | 1) * T * 8;
-    cudaError_t e = cudaFuncSetAttribute(batch_kernel<DT, VPL, G>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(dyn));
+    auto kern = batch_kernel<DT, VT / NCH, G, NCH>;
+    const int KSB = K | 1;
+    const size_t dyn = size_t(KSB) * kSelPix * 2 * 8;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(dyn));
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     int occ = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel<DT, VPL, G>, T, dyn);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kBT, dyn);
     if (ctas_per_sm > 0 && ctas_per_sm < occ) occ = ctas_per_sm;
     if (occ < 1) occ = 1;
     const uint32_t grid = uint32_t(sms) * uint32_t(occ);
-    batch_kernel<DT, VPL, G><<<grid < total ? grid : total, T, dyn, s>>>(dviews, n_views, total, counter);
+    kern<<<grid < total ? grid : total, kBT, dyn, s>>>(dviews, n_views, total, counter, KSB);
     count_launch();
     return cudaGetLastError();
 }
 
-template <int DT, int VPL>
-cudaError_t pick_g(const BatchView *d, int n, uint32_t total, uint32_t *counter, int K, int group,
-                   int ctas, cudaStream_t s) {
+// Channel chunks per row by default: at most 8 accumulators per pixel and
+// lane (two F32 vectors or one BF16 / FP8 vector), so the blend warps fit the
+// register budget of two CTAs per SM.
+template <int DT, int VT>
+constexpr int batch_default_chunks() {
+    constexpr int lim = DT == QR_F32 ? 2 : 1;
+    return VT <= lim ? 1 : VT / lim;
+}
+
+// VT 16-byte vectors per lane over the whole row (1, 2 or 4).  group picks
+// the pixel-group size (0 = largest allowed by K), chunks the channel chunks
+// per row for groups of 4 (0 = default; 1, 2, 4 where they divide VT).
+template <int DT, int VT>
+cudaError_t pick(const BatchView *d, int n, uint32_t total, uint32_t *counter, int K, int group,
+                 int chunks, int ctas, cudaStream_t s) {
+    constexpr int DEF = batch_default_chunks<DT, VT>();
     const int g = group > 0 ? group : (K <= 8 ? 4 : K <= 16 ? 2 : 1);
-    if (g == 4 && K <= 8) return run_batch<DT, VPL, 4>(d, n, total, counter, K, ctas, s);
-    if (g >= 2 && K <= 16) return run_batch<DT, VPL, 2>(d, n, total, counter, K, ctas, s);
-    return run_batch<DT, VPL, 1>(d, n, total, counter, K, ctas, s);
+    if (g == 4 && K <= 8) {
+        const int c = chunks > 0 ? chunks : DEF;
+        if (c == 1) return run_batch<DT, VT, 4, 1>(d, n, total, counter, K, ctas, s);
+        if constexpr (VT % 2 == 0)
+            if (c == 2) return run_batch<DT, VT, 4, 2>(d, n, total, counter, K, ctas, s);
+        if constexpr (VT % 4 == 0)
+            if (c == 4) return run_batch<DT, VT, 4, 4>(d, n, total, counter, K, ctas, s);
+        return cudaErrorInvalidValue;
+    }
+    if (g >= 2 && K <= 16) return run_batch<DT, VT, 2, DEF>(d, n, total, counter, K, ctas, s);
+    return run_batch<DT, VT, 1, DEF>(d, n, total, counter, K, ctas, s);
 }
 
 }  // namespace
@@ -405,27 +433,26 @@ bool batch_supported(qr_dtype dt, int C) {
 size_t batch_desc_bytes(int n_views) { return (size_t(n_views) * sizeof(BatchView) + 255) / 256 * 256 + 256; }
 
 cudaError_t launch_batch(const void *ws, int n_views, uint32_t total_items, qr_dtype dt, int C,
-                         int K, int group, int ctas_per_sm, cudaStream_t s) {
+                         int K, int group, int chunks, int ctas_per_sm, cudaStream_t s) {
     const BatchView *d = static_cast<const BatchView *>(ws);
     uint32_t *counter = reinterpret_cast<uint32_t *>(static_cast<char *>(const_cast<void *>(ws)) +
                                                      batch_desc_bytes(n_views) - 256);
     cudaError_t e = cudaMemsetAsync(counter, 0, 4, s);
     if (e != cudaSuccess) return e;
-    const int rowv = C / (dt == QR_F32 ? 4 : dt == QR_BF16 ? 8 : 16);
-    const int vpl = rowv / 32;
+    const int vt = C / (dt == QR_F32 ? 4 : dt == QR_BF16 ? 8 : 16) / 32;
     switch (dt) {
         case QR_F32:
-            if (vpl == 4) return pick_g<QR_F32, 4>(d, n_views, total_items, counter, K, group, ctas_per_sm, s);
-            if (vpl == 2) return pick_g<QR_F32, 2>(d, n_views, total_items, counter, K, group, ctas_per_sm, s);
-            return pick_g<QR_F32, 1>(d, n_views, total_items, counter, K, group, ctas_per_sm, s);
+            if (vt == 4) return pick<QR_F32, 4>(d, n_views, total_items, counter, K, group, chunks, ctas_per_sm, s);
+            if (vt == 2) return pick<QR_F32, 2>(d, n_views, total_items, counter, K, group, chunks, ctas_per_sm, s);
+            return pick<QR_F32, 1>(d, n_views, total_items, counter, K, group, chunks, ctas_per_sm, s);
         case QR_BF16:
-            if (vpl == 4) return pick_g<QR_BF16, 4>(d, n_views, total_items, counter, K, group, ctas_per_sm, s);
-            if (vpl == 2) return pick_g<QR_BF16, 2>(d, n_views, total_items, counter, K, group, ctas_per_sm, s);
-            return pick_g<QR_BF16, 1>(d, n_views, total_items, counter, K, group, ctas_per_sm, s);
+            if (vt == 4) return pick<QR_BF16, 4>(d, n_views, total_items, counter, K, group, chunks, ctas_per_sm, s);
+            if (vt == 2) return pick<QR_BF16, 2>(d, n_views, total_items, counter, K, group, chunks, ctas_per_sm, s);
+            return pick<QR_BF16, 1>(d, n_views, total_items, counter, K, group, chunks, ctas_per_sm, s);
         case QR_FP8E4M3:
-            if (vpl == 4) return pick_g<QR_FP8E4M3, 4>(d, n_views, total_items, counter, K, group, ctas_per_sm, s);
-            if (vpl == 2) return pick_g<QR_FP8E4M3, 2>(d, n_views, total_items, counter, K, group, ctas_per_sm, s);
-            return pick_g<QR_FP8E4M3, 1>(d, n_views, total_items, counter, K, group, ctas_per_sm, s);
+            if (vt == 4) return pick<QR_FP8E4M3, 4>(d, n_views, total_items, counter, K, group, chunks, ctas_per_sm, s);
+            if (vt == 2) return pick<QR_FP8E4M3, 2>(d, n_views, total_items, counter, K, group, chunks, ctas_per_sm, s);
+            return pick<QR_FP8E4M3, 1>(d, n_views, total_items, counter, K, group, chunks, ctas_per_sm, s);
     }
     return cudaErrorInvalidValue;
 }

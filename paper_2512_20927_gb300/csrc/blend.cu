@@ -231,7 +231,17 @@ __device__ __forceinline__ int64_t group_pixel(int64_t chunk0, int gi, int m, in
 // table (slot = rank of the row's leader lane, one float per pixel; a pixel
 // that lists an id twice gets the sum), so the row loop reads them with one
 // broadcast load instead of a chain of shuffles.
-template <int DT, int VPL, int G>
+//
+// Latency hiding: a work item is (pixel group, channel chunk); NCH > 1 splits
+// each row into NCH chunks of 32 VPL vectors taken by different warps (fewer
+// accumulators per thread, more warps per SM).  The next item's counts, ids
+// and weights are loaded (three independent loads) before the current item's
+// rows, U = max(2, 8 / VPL) rows are in flight per step, and FP8 rows load
+// their per-Gaussian scale beside the row and apply it to the row's weights,
+// so no load waits on another's result.  An FP8 row's weight for a pixel is
+// (the pixel's weight for it) * scale, rounded once: a selection lists a
+// Gaussian at most once per pixel.
+template <int DT, int VPL, int G, int NCH>
 __global__ void __launch_bounds__(kThreads)
 blend_group_kernel(const uint4 *__restrict__ feat, const float *__restrict__ scale,
                    int64_t n_gauss, const int32_t *__restrict__ ids,
@@ -239,33 +249,42 @@ blend_group_kernel(const uint4 *__restrict__ feat, const float *__restrict__ sca
                    int K, int W, int H, float4 *__restrict__ out) {
     pdl_wait();   // the predecessor's outputs are complete and visible
     constexpr int CPV = Vec<DT>::C;
-    constexpr int ROWV = 32 * VPL;
+    constexpr int CV = 32 * VPL;             // vectors of a chunk
+    constexpr int ROWV = CV * NCH;           // vectors of a row
+    constexpr int U = VPL >= 4 ? 2 : 8 / VPL;
     constexpr unsigned FULL = 0xffffffffu;
     constexpr int NW = kThreads / 32;
+    constexpr int NITEMS = (256 / G) * NCH;
     __shared__ __align__(16) float s_w[NW][32][G];
     __shared__ int s_id[NW][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t items = (W > 0) ? int64_t((W + 15) >> 4) * ((H + 15) >> 4) * 256 : P;
     const int64_t chunk0 = int64_t(blockIdx.x) * 256;
     const int m = lane / K, j = lane - m * K;
-    auto entry = [&](int wi, int64_t &p, int &id, float &w) {
+    auto fetch = [&](int gi, int64_t &p, int &idr, float &wr, int &c) {
         p = -1;
-        if (m < G) p = (W > 0) ? group_pixel<G>(chunk0, wi, m, W, H, items)
-                               : (chunk0 + wi * G + m < items ? chunk0 + wi * G + m : -1);
-        id = -1;
-        w = 0.f;
-        if (p >= 0 && j < int(cnt[p])) {
-            id = ids[p * K + j];
-            w = wts[p * K + j];
-            if (uint64_t(int64_t(id)) >= uint64_t(n_gauss)) { id = -1; w = 0.f; }
-            else if (DT == QR_FP8E4M3) w *= scale[id];
+        if (m < G) p = (W > 0) ? group_pixel<G>(chunk0, gi, m, W, H, items)
+                               : (chunk0 + gi * G + m < items ? chunk0 + gi * G + m : -1);
+        idr = -1;
+        wr = 0.f;
+        c = 0;
+        if (p >= 0) {
+            c = int(cnt[p]);
+            idr = ids[p * K + j];
+            wr = wts[p * K + j];
         }
     };
     int64_t p;
-    int id;
-    float w;
-    entry(warp, p, id, w);
-    for (int wi = warp; wi < 256 / G; wi += NW) {
+    int idr, c;
+    float wr;
+    fetch(warp / NCH, p, idr, wr, c);
+    for (int it = warp; it < NITEMS; it += NW) {
+        const int ch = it % NCH;
+        const bool ok = p >= 0 && j < c && uint64_t(int64_t(idr)) < uint64_t(n_gauss);
+        const int id = ok ? idr : -1;
+        const float w = ok ? wr : 0.f;
+        const int64_t pc = p;
+        if (it + NW < NITEMS) fetch((it + NW) / NCH, p, idr, wr, c);
         const unsigned peers = __match_any_sync(FULL, id);
         const int leader = __ffs(peers) - 1;
         const unsigned leaders = __ballot_sync(FULL, id >= 0 && lane == leader);
@@ -286,22 +305,27 @@ blend_group_kernel(const uint4 *__restrict__ feat, const float *__restrict__ sca
             for (int v = 0; v < VPL; ++v)
 #pragma unroll
                 for (int q = 0; q < CPV; ++q) acc[g][v][q] = 0.f;
-        for (int r0 = 0; r0 < nrows; r0 += 2) {
-            uint4 r[2][VPL];
+        const uint4 *fch = feat + ch * CV + lane;
+        for (int r0 = 0; r0 < nrows; r0 += U) {
+            uint4 r[U][VPL];
+            float sc[U];
 #pragma unroll
-            for (int u = 0; u < 2; ++u) {
+            for (int u = 0; u < U; ++u) {
                 const bool ok = r0 + u < nrows;
-                const uint4 *row = feat + int64_t(ok ? s_id[warp][r0 + u] : 0) * ROWV + lane;
+                const int rid = ok ? s_id[warp][r0 + u] : 0;
+                const uint4 *row = fch + int64_t(rid) * ROWV;
 #pragma unroll
                 for (int v = 0; v < VPL; ++v)
                     r[u][v] = ok ? ld_row(row + 32 * v) : make_uint4(0, 0, 0, 0);
+                if (DT == QR_FP8E4M3) sc[u] = ok ? scale[rid] : 0.f;
             }
 #pragma unroll
-            for (int u = 0; u < 2; ++u) {
+            for (int u = 0; u < U; ++u) {
                 if (r0 + u >= nrows) break;
                 float wg[G];
 #pragma unroll
-                for (int g = 0; g < G; ++g) wg[g] = s_w[warp][r0 + u][g];
+                for (int g = 0; g < G; ++g)
+                    wg[g] = DT == QR_FP8E4M3 ? s_w[warp][r0 + u][g] * sc[u] : s_w[warp][r0 + u][g];
                 float fv[VPL][CPV];
 #pragma unroll
                 for (int v = 0; v < VPL; ++v) decode_vec<DT>(r[u][v], fv[v]);
@@ -315,9 +339,9 @@ blend_group_kernel(const uint4 *__restrict__ feat, const float *__restrict__ sca
         }
 #pragma unroll
         for (int g = 0; g < G; ++g) {
-            const int64_t pg = __shfl_sync(FULL, p, g * K < 32 ? g * K : 0);
+            const int64_t pg = __shfl_sync(FULL, pc, g * K < 32 ? g * K : 0);
             if (pg >= 0) {
-                float4 *o = out + pg * (int64_t(ROWV) * CPV / 4);
+                float4 *o = out + pg * (int64_t(ROWV) * CPV / 4) + ch * (CV * CPV / 4);
 #pragma unroll
                 for (int v = 0; v < VPL; ++v)
 #pragma unroll
@@ -327,25 +351,60 @@ blend_group_kernel(const uint4 *__restrict__ feat, const float *__restrict__ sca
                                               acc[g][v][4 * q + 2], acc[g][v][4 * q + 3]));
             }
         }
-        __syncwarp();   // the table is rewritten by the next group
-        if (wi + NW < 256 / G) entry(wi + NW, p, id, w);
+        __syncwarp();   // the table is rewritten by the next item
     }
 }
 
-template <int DT, int VPL>
+// Channel chunks a row is split into by default: a chunk keeps at most 16
+// accumulators per pixel (4 F32, 2 BF16 or 1 FP8 vector per lane).
+template <int DT, int VT>
+constexpr int default_chunks() {
+    constexpr int lim = DT == QR_F32 ? 4 : DT == QR_BF16 ? 2 : 1;
+    return VT <= lim ? 1 : (VT % lim == 0 ? VT / lim : VT);
+}
+
+int g_blend_chunks = 0;   // qr_set_blend_chunks: 0 = default_chunks
+
+template <int DT, int VT, int G, int NCH>
+cudaError_t go_group(const void *feat, const float *scale, int64_t n_gauss, const int32_t *ids,
+                     const float *w, const uint8_t *cnt, int64_t P, int K, int W, int H,
+                     float *out, cudaStream_t s) {
+    const int64_t items = (W > 0) ? int64_t((W + 15) >> 4) * ((H + 15) >> 4) * 256 : P;
+    const unsigned blocks = unsigned((items + 255) / 256);
+    return pdl_launch(blend_group_kernel<DT, VT / NCH, G, NCH>, dim3(blocks), dim3(kThreads), 0, s,
+                      static_cast<const uint4 *>(feat), scale, n_gauss, ids, w, cnt, P, K, W, H,
+                      reinterpret_cast<float4 *>(out));
+}
+
+// VT 16-byte vectors per lane over the whole row.  With K <= 8 (pixel groups
+// of 4) and rows of 2 or 4 vectors per lane the chunk count can be chosen
+// (qr_set_blend_chunks); the results are the same for every choice.
+template <int DT, int VT>
 cudaError_t run_group(const void *feat, const float *scale, int64_t n_gauss, const int32_t *ids,
                       const float *w, const uint8_t *cnt, int64_t P, int K, int W, int H,
                       float *out, cudaStream_t s) {
-    const int64_t items = (W > 0) ? int64_t((W + 15) >> 4) * ((H + 15) >> 4) * 256 : P;
-    const unsigned blocks = unsigned((items + 255) / 256);
-    const uint4 *f = static_cast<const uint4 *>(feat);
-    float4 *o = reinterpret_cast<float4 *>(out);
-    auto go = [&](auto kern) {
-        return pdl_launch(kern, dim3(blocks), dim3(kThreads), 0, s, f, scale, n_gauss, ids, w, cnt, P,
-                          K, W, H, o);
-    };
-    const cudaError_t e = K <= 8 ? go(blend_group_kernel<DT, VPL, 4>)
-                        : K <= 16 ? go(blend_group_kernel<DT, VPL, 2>) : go(blend_group_kernel<DT, VPL, 1>);
+    constexpr int DEF = default_chunks<DT, VT>();
+    cudaError_t e;
+    if (K <= 8) {
+        const int want = g_blend_chunks > 0 ? g_blend_chunks : DEF;
+        if constexpr (VT == 2 || VT == 4) {
+            if (want == 1 && DEF != 1)
+                e = go_group<DT, VT, 4, 1>(feat, scale, n_gauss, ids, w, cnt, P, K, W, H, out, s);
+            else if (want == 2 && DEF != 2)
+                e = go_group<DT, VT, 4, 2>(feat, scale, n_gauss, ids, w, cnt, P, K, W, H, out, s);
+            else if (VT == 4 && want == 4 && DEF != 4)
+                e = go_group<DT, VT, 4, (VT == 4 ? 4 : 1)>(feat, scale, n_gauss, ids, w, cnt, P, K, W,
+                                                           H, out, s);
+            else
+                e = go_group<DT, VT, 4, DEF>(feat, scale, n_gauss, ids, w, cnt, P, K, W, H, out, s);
+        } else {
+            e = go_group<DT, VT, 4, DEF>(feat, scale, n_gauss, ids, w, cnt, P, K, W, H, out, s);
+        }
+    } else if (K <= 16) {
+        e = go_group<DT, VT, 2, DEF>(feat, scale, n_gauss, ids, w, cnt, P, K, W, H, out, s);
+    } else {
+        e = go_group<DT, VT, 1, DEF>(feat, scale, n_gauss, ids, w, cnt, P, K, W, H, out, s);
+    }
     count_launch();
     return e != cudaSuccess ? e : cudaGetLastError();
 }
@@ -384,6 +443,12 @@ cudaError_t dispatch(const void *feat, const float *scale, int64_t n_gauss, int 
 }
 
 }  // namespace
+
+bool set_blend_chunks(int chunks) {
+    if (chunks != 0 && chunks != 1 && chunks != 2 && chunks != 4) return false;
+    g_blend_chunks = chunks;
+    return true;
+}
 
 // Row widths the blend kernel is built for (16-byte vectors per row).
 bool blend_supported(qr_dtype dt, int C) {

@@ -38,7 +38,7 @@ inline cudaError_t pdl_launch(void (*kern)(KArgs...), dim3 grid, dim3 block, siz
 // counters[3]: number of Gaussians n
 // counters[4]: number of intersections actually emitted (0 on overflow)
 enum { CNT_STATUS = 0, CNT_ISECT = 1, CNT_VISIBLE = 2, CNT_N = 3, CNT_SORT_N = 4, CNT_CAND = 5,
-       CNT_WORDS = 8 };
+       CNT_BIG = 6, CNT_WORDS = 8 };
 
 // Workspace slots (byte offsets in qr_frame::off).
 enum Slot {
@@ -150,7 +150,7 @@ bool batch_supported(qr_dtype dt, int C);
 size_t batch_desc_bytes(int n_views);
 size_t batch_view_size();
 cudaError_t launch_batch(const void *ws, int n_views, uint32_t total_items, qr_dtype dt, int C,
-                         int K, int group, int ctas_per_sm, cudaStream_t s);
+                         int K, int group, int chunks, int ctas_per_sm, cudaStream_t s);
 cudaError_t prepare_batch(const qr_view *views, int n_views, void *ws, uint32_t *total_items,
                           cudaStream_t s, BatchView *host_scratch);
 // Eq. 2 contrastive loss (contrastive.cu): out2 -> (L, 1/n), grad [P][C] -> dL/dF;
@@ -162,6 +162,7 @@ cudaError_t launch_contrastive_loss(const float *F, const float *tgt, int M, int
                                     void *ws, cudaStream_t s);
 bool relevance_supported(int Q, int C);
 void set_wait_limit(unsigned polls);
+bool set_blend_chunks(int chunks);
 // blend of qr_blend fused with the relevance product (the map is never written)
 bool blend_relevance_supported(qr_dtype dt, int Q, int C, int K);
 cudaError_t launch_blend_relevance(const void *feat, const float *scale, qr_dtype dt, int C,

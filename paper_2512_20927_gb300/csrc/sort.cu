@@ -24,13 +24,14 @@
 //      its tile's bucket at an atomically claimed position (counted per tile
 //      in shared memory first, one global atomic per touched tile, when the
 //      grid has at most 4096 tiles);
-//   5. tile_sort / tile_sort_big: one CTA per tile sorts its bucket (bitonic
-//      network over the unique 64-bit keys) and writes the ids: buckets of up
-//      to 2048 keys in registers (register swaps, warp shuffles, shared memory
-//      only for the cross-warp strides) in tile_sort; larger ones in
-//      tile_sort_big, up to 8192 keys still in registers (32 per thread), up
-//      to 8192 otherwise in shared memory, beyond that in chunks merged in
-//      global memory by the same CTA (merge path), so no size is refused.
+//   5. tile_sort: one CTA per tile sorts a bucket of up to 2048 keys
+//      (bitonic network over the unique 64-bit keys in registers: register
+//      swaps, warp shuffles, shared memory only for the cross-warp strides)
+//      and writes the ids; a larger bucket goes to a list, which
+//      tile_sort_big's persistent CTAs of 1024 threads work through: up to
+//      8192 keys merge-sorted in shared memory (runs of 8 in registers, then
+//      merge-path rounds between two buffers), beyond that in 8192-key chunks merged in
+//      global memory by the same CTA, so no size is refused.
 // Keys are unique, so the order inside a bucket before step 5 does not matter
 // and the result is deterministic.  No CTA waits for another.  Counts live in
 // device memory, so the stage can be captured in a CUDA graph.
@@ -41,7 +42,8 @@ namespace {
 
 constexpr int T = 256;
 constexpr int EMIT_CHUNK = kEmitChunk;
-constexpr int TS_CAP = 8192;             // keys a tile sorts in shared memory (64 KB)
+constexpr int TB = 1024;                 // threads of the big-bucket sort
+constexpr int BIG_CAP = 8192;            // keys a big bucket sorts in shared memory (2 x 64 KB)
 constexpr int kScanSmemTiles = 48 * 1024; // tile counts bin_scan integrates in shared memory
 constexpr int kAggTiles = 4096;           // tile grids whose bucket claims are aggregated per CTA
 
@@ -153,6 +155,7 @@ bin_scan(uint32_t *kept, uint32_t *tsum, int nblk, uint32_t *counters, uint32_t 
     const uint32_t isect = tot.y;
     const bool over = isect > capacity;
     if (threadIdx.x == 0) {
+        counters[CNT_BIG] = 0u;
         counters[CNT_VISIBLE] = tot.x;
         counters[CNT_ISECT] = isect;
         if (over) counters[CNT_STATUS] = QR_ERR_CAPACITY;
@@ -280,21 +283,6 @@ expand_scatter(const uint32_t *__restrict__ koff, const uint32_t *__restrict__ k
 }
 
 // ------------------------------------------------------------------ per-tile sort
-__device__ __forceinline__ void bitonic_smem(unsigned long long *s, int npow2) {
-    for (int k = 2; k <= npow2; k <<= 1)
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = threadIdx.x; i < npow2; i += T) {
-                const int ixj = i ^ j;
-                if (ixj > i) {
-                    const unsigned long long a = s[i], b = s[ixj];
-                    const bool up = (i & k) == 0;
-                    if ((a > b) == up) { s[i] = b; s[ixj] = a; }
-                }
-            }
-            __syncthreads();
-        }
-}
-
 // A bucket of up to 256*E keys, loaded E per thread in blocked order and
 // padded with ~0, sorted by the register bitonic network, ids written out.
 template <int E>
@@ -310,23 +298,14 @@ __device__ void sort_registers(const unsigned long long *__restrict__ src, int n
         if (base + e < n) dst[base + e] = uint32_t(v[e]);
 }
 
-// Sort m <= TS_CAP keys in place in global memory through shared memory.
-__device__ __forceinline__ void sort_chunk(unsigned long long *s, unsigned long long *g, int m) {
-    int npow2 = 1;
-    while (npow2 < m) npow2 <<= 1;
-    for (int i = threadIdx.x; i < npow2; i += T) s[i] = i < m ? g[i] : ~0ull;
-    __syncthreads();
-    bitonic_smem(s, npow2);
-    for (int i = threadIdx.x; i < m; i += T) g[i] = s[i];
-    __syncthreads();
-}
-
-// Merge sorted A[0,na) and B[0,nb) into C with the whole CTA (merge path).
+// Merge sorted A[0,na) and B[0,nb) into C with the whole CTA of NT threads
+// (merge path).
+template <int NT>
 __device__ __forceinline__ void merge_cta(const unsigned long long *A, int na,
                                           const unsigned long long *B, int nb,
                                           unsigned long long *C) {
     const int total = na + nb;
-    const int per = (total + T - 1) / T;
+    const int per = (total + NT - 1) / NT;
     const int d0 = min(total, int(threadIdx.x) * per), d1 = min(total, d0 + per);
     auto split = [&](int d) {
         int lo = max(0, d - nb), hi = min(d, na);
@@ -344,17 +323,22 @@ __device__ __forceinline__ void merge_cta(const unsigned long long *A, int na,
     }
 }
 
-// Buckets of up to 8 T keys (registers, up to 8 per thread); larger ones
-// are left to tile_sort_big, whose register needs would lower this kernel's
-// occupancy for every tile.
+// Buckets of up to 8 T keys (registers, up to 8 per thread).  A larger
+// bucket is appended to the list of big buckets that tile_sort_big works
+// through, so its register and shared-memory needs do not lower this
+// kernel's occupancy for every tile.
 __global__ void __launch_bounds__(T)
 tile_sort(const uint2 *__restrict__ ranges, unsigned long long *__restrict__ keys,
-          uint32_t *__restrict__ igid) {
+          uint32_t *__restrict__ igid, uint32_t *__restrict__ big, uint32_t *__restrict__ counters) {
     pdl_wait();   // the predecessor's outputs are complete and visible
     __shared__ unsigned long long s_k[8 * T];
     const uint2 r = ranges[blockIdx.x];
     const int n = int(r.y - r.x);
-    if (n == 0 || n > 8 * T) return;
+    if (n > 8 * T) {
+        if (threadIdx.x == 0) big[atomicAdd(&counters[CNT_BIG], 1u)] = blockIdx.x;
+        return;
+    }
+    if (n == 0) return;
     unsigned long long *src = keys + r.x;
     if (n <= 2 * T) {
         if (n <= T) sort_registers<1>(src, n, s_k, igid + r.x);
@@ -365,49 +349,128 @@ tile_sort(const uint2 *__restrict__ ranges, unsigned long long *__restrict__ key
     else sort_registers<8>(src, n, s_k, igid + r.x);
 }
 
-// Buckets of more than 8 T keys (a CTA per tile; the others return at once):
-// up to 32 keys per thread in registers (strides below 32 E in registers and
-// shuffles, only the widest through shared memory), up to TS_CAP keys in a
-// shared-memory network, beyond that sorted chunks merged in global memory.
-__global__ void __launch_bounds__(T)
-tile_sort_big(const uint2 *__restrict__ ranges, unsigned long long *__restrict__ keys,
-              unsigned long long *__restrict__ scratch, uint32_t *__restrict__ igid) {
-    pdl_wait();   // the predecessor's outputs are complete and visible
-    extern __shared__ unsigned long long s_k[];   // TS_CAP keys
-    const uint2 r = ranges[blockIdx.x];
-    const int n = int(r.y - r.x);
-    if (n <= 8 * T) return;
-    unsigned long long *src = keys + r.x;
-    if (n <= 32 * T) {
-        if (n <= 16 * T) sort_registers<16>(src, n, s_k, igid + r.x);
-        else sort_registers<32>(src, n, s_k, igid + r.x);
-        return;
+// ------------------------------------------------------------------ big buckets
+// Eight keys in registers sorted by Batcher's odd-even merge network (19
+// compare-exchanges).
+__device__ __forceinline__ void cx(unsigned long long &a, unsigned long long &b) {
+    const unsigned long long lo = a < b ? a : b, hi = a < b ? b : a;
+    a = lo;
+    b = hi;
+}
+__device__ __forceinline__ void sort8(unsigned long long (&v)[8]) {
+    cx(v[0], v[1]); cx(v[2], v[3]); cx(v[4], v[5]); cx(v[6], v[7]);
+    cx(v[0], v[2]); cx(v[1], v[3]); cx(v[4], v[6]); cx(v[5], v[7]);
+    cx(v[1], v[2]); cx(v[5], v[6]);
+    cx(v[0], v[4]); cx(v[1], v[5]); cx(v[2], v[6]); cx(v[3], v[7]);
+    cx(v[2], v[4]); cx(v[3], v[5]);
+    cx(v[1], v[2]); cx(v[3], v[4]); cx(v[5], v[6]);
+}
+
+// Sort n <= TB * E unique keys in shared memory: runs of 8 sorted in
+// registers, then merge rounds of doubling run length L between the two
+// buffers s and t.  In a round thread i produces outputs [iE, iE + E) of its
+// pair of runs (2L is a multiple of E, so the range never crosses pairs): a
+// merge-path binary search gives its start in each run and the E outputs are
+// merged straight into the other buffer.  Returns the buffer holding the
+// sorted keys.
+template <int E>
+__device__ unsigned long long *sort_smem(unsigned long long *s, unsigned long long *t, int n) {
+    for (int r0 = int(threadIdx.x) * 8; r0 < n; r0 += TB * 8) {
+        unsigned long long v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = r0 + e < n ? s[r0 + e] : ~0ull;
+        sort8(v);
+#pragma unroll
+        for (int e = 0; e < 8; ++e)
+            if (r0 + e < n) s[r0 + e] = v[e];
     }
-    if (n <= TS_CAP) {
-        int npow2 = 1;
-        while (npow2 < n) npow2 <<= 1;
-        for (int i = threadIdx.x; i < npow2; i += T) s_k[i] = i < n ? src[i] : ~0ull;
-        __syncthreads();
-        bitonic_smem(s_k, npow2);
-        for (int i = threadIdx.x; i < n; i += T) igid[r.x + i] = uint32_t(s_k[i]);
-        return;
-    }
-    // a bucket beyond shared memory: sorted chunks, then merge rounds
-    // ping-ponging between the key buffer and the scratch buffer
-    for (int c0 = 0; c0 < n; c0 += TS_CAP) sort_chunk(s_k, src + c0, min(TS_CAP, n - c0));
-    unsigned long long *dst = scratch + r.x;
-    for (int w = TS_CAP; w < n; w <<= 1) {
-        for (int a0 = 0; a0 < n; a0 += 2 * w) {
-            const int na = min(w, n - a0);
-            const int nb = min(w, n - a0 - na);
-            merge_cta(src + a0, na, src + a0 + na, nb, dst + a0);
+    __syncthreads();
+    const int d0 = int(threadIdx.x) * E;
+    const int m = max(0, min(E, n - d0));
+    for (int L = 8; L < n; L <<= 1) {
+        if (m > 0) {
+            const int ps = d0 & ~(2 * L - 1);
+            const int na = min(L, n - ps);
+            const int nb = max(0, min(L, n - ps - na));
+            const unsigned long long *a = s + ps, *b = a + na;
+            const int diag = d0 - ps;
+            int lo = max(0, diag - nb), hi = min(diag, na);
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (a[mid] < b[diag - 1 - mid]) lo = mid + 1; else hi = mid;
+            }
+            int i = lo, j = diag - lo;
+            for (int e = 0; e < m; ++e) {
+                const bool take_a = j >= nb || (i < na && a[i] < b[j]);
+                t[d0 + e] = take_a ? a[i] : b[j];
+                i += take_a ? 1 : 0;
+                j += take_a ? 0 : 1;
+            }
         }
         __syncthreads();
-        unsigned long long *t = src;
-        src = dst;
-        dst = t;
+        unsigned long long *x = s;
+        s = t;
+        t = x;
     }
-    for (int i = threadIdx.x; i < n; i += T) igid[r.x + i] = uint32_t(src[i]);
+    return s;
+}
+
+__device__ __forceinline__ unsigned long long *sort_smem_any(unsigned long long *s,
+                                                             unsigned long long *t, int n) {
+    if (n <= TB * 2) return sort_smem<2>(s, t, n);
+    if (n <= TB * 4) return sort_smem<4>(s, t, n);
+    return sort_smem<8>(s, t, n);
+}
+
+// The buckets of more than 8 T keys, listed by tile_sort: persistent CTAs of
+// TB threads (one per SM: 128 KB of shared memory) take them in turn.  Up to
+// BIG_CAP keys are sorted in shared memory; a larger bucket is sorted in
+// BIG_CAP chunks whose sorted runs are merged in global memory by the same
+// CTA (merge path, ping-ponging between the key buffer and the scratch
+// buffer), so no size is refused.
+__global__ void __launch_bounds__(TB, 1)
+tile_sort_big(const uint2 *__restrict__ ranges, unsigned long long *__restrict__ keys,
+              unsigned long long *__restrict__ scratch, uint32_t *__restrict__ igid,
+              const uint32_t *__restrict__ big, const uint32_t *__restrict__ counters) {
+    pdl_wait();   // the predecessor's outputs are complete and visible
+    extern __shared__ unsigned long long s_k[];   // 2 x BIG_CAP keys
+    unsigned long long *s_t = s_k + BIG_CAP;
+    const uint32_t nbig = counters[CNT_BIG];
+    for (uint32_t bi = blockIdx.x; bi < nbig; bi += gridDim.x) {
+        const uint2 r = ranges[big[bi]];
+        const int n = int(r.y - r.x);
+        unsigned long long *src = keys + r.x;
+        if (n <= BIG_CAP) {
+            for (int i = threadIdx.x; i < n; i += TB) s_k[i] = src[i];
+            __syncthreads();
+            const unsigned long long *o = sort_smem_any(s_k, s_t, n);
+            for (int i = threadIdx.x; i < n; i += TB) igid[r.x + i] = uint32_t(o[i]);
+            __syncthreads();
+            continue;
+        }
+        for (int c0 = 0; c0 < n; c0 += BIG_CAP) {
+            const int m = min(BIG_CAP, n - c0);
+            for (int i = threadIdx.x; i < m; i += TB) s_k[i] = src[c0 + i];
+            __syncthreads();
+            const unsigned long long *o = sort_smem_any(s_k, s_t, m);
+            for (int i = threadIdx.x; i < m; i += TB) src[c0 + i] = o[i];
+            __syncthreads();
+        }
+        unsigned long long *a = src, *dst = scratch + r.x;
+        for (int w = BIG_CAP; w < n; w <<= 1) {
+            for (int a0 = 0; a0 < n; a0 += 2 * w) {
+                const int na = min(w, n - a0);
+                const int nb = min(w, n - a0 - na);
+                merge_cta<TB>(a + a0, na, a + a0 + na, nb, dst + a0);
+            }
+            __syncthreads();
+            unsigned long long *t = a;
+            a = dst;
+            dst = t;
+        }
+        for (int i = threadIdx.x; i < n; i += TB) igid[r.x + i] = uint32_t(a[i]);
+        __syncthreads();
+    }
 }
 
 }  // namespace
@@ -425,7 +488,7 @@ cudaError_t launch_sort(const qr_frame &f, cudaStream_t s) {
         return e;
     }
     e = cudaFuncSetAttribute(tile_sort_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             int(TS_CAP * sizeof(unsigned long long)));
+                             int(2 * BIG_CAP * sizeof(unsigned long long)));
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
@@ -465,12 +528,15 @@ cudaError_t launch_sort(const qr_frame &f, cudaStream_t s) {
                        (const uint32_t *)chunk_owner, counters, f.tiles_x, tiles, ranges, tcnt, keys);
     }
     if (e != cudaSuccess) return e;
+    // the per-tile cursors are dead once the keys are scattered: their slot
+    // holds the list of big buckets
     e = pdl_launch(tile_sort, dim3(tiles), dim3(T), 0, s, (const uint2 *)ranges, keys,
-                   slot<uint32_t>(f, S_IGID));
+                   slot<uint32_t>(f, S_IGID), tcnt, counters);
     if (e != cudaSuccess) return e;
-    e = pdl_launch(tile_sort_big, dim3(tiles), dim3(T), TS_CAP * sizeof(unsigned long long), s,
+    e = pdl_launch(tile_sort_big, dim3(unsigned(min(tiles, sms))), dim3(TB),
+                   2 * BIG_CAP * sizeof(unsigned long long), s,
                    (const uint2 *)ranges, keys, slot<unsigned long long>(f, S_SCRATCH64),
-                   slot<uint32_t>(f, S_IGID));
+                   slot<uint32_t>(f, S_IGID), (const uint32_t *)tcnt, (const uint32_t *)counters);
     count_launch(5);
     return e != cudaSuccess ? e : cudaGetLastError();
 }

@@ -98,6 +98,7 @@ SIGNATURES = {
                             _P, _P]),
     "qr_launch_count": (ctypes.c_uint64, []),
     "qr_set_wait_limit": (None, [ctypes.c_uint32]),
+    "qr_set_blend_chunks": (_S, [_I32]),
     "qr_backward_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(qr_frame), _I32]),
     "qr_backward": (_S, [ctypes.POINTER(qr_frame), _P, _P, _S, _I32, _P, _P, _P, _P, _P, _P, _P,
                          _P, ctypes.c_size_t, _P]),
@@ -117,7 +118,7 @@ SIGNATURES = {
     "qr_batch_workspace_bytes": (ctypes.c_size_t, [_I32]),
     "qr_batch_prepare": (_S, [ctypes.POINTER(qr_view), _I32, _P, ctypes.c_size_t,
                               ctypes.POINTER(ctypes.c_uint32), _P]),
-    "qr_render_batch": (_S, [_P, _I32, ctypes.c_uint32, _S, _I32, _I32, _I32, _I32, _P]),
+    "qr_render_batch": (_S, [_P, _I32, ctypes.c_uint32, _S, _I32, _I32, _I32, _I32, _I32, _P]),
     "qr_quantize_bf16": (_S, [_P, _I64, _P, _P]),
     "qr_quantize_fp8": (_S, [_P, _I64, _I32, _P, _P, _P]),
     "qr_render_noalloc": (_S, [_P, _P, _P, _P, _I64, ctypes.POINTER(qr_camera),
@@ -542,6 +543,11 @@ def qr_set_wait_limit(polls: int):
     load().qr_set_wait_limit(int(polls))
 
 
+def qr_set_blend_chunks(chunks: int):
+    """Tuning: channel chunks per feature row in the wide-row blend (0 = built-in)."""
+    _check(load().qr_set_blend_chunks(int(chunks)), "qr_set_blend_chunks")
+
+
 # ---------------------------------------------------------------- convenience
 def gaussians_to_device(g, device="cuda"):
     """Upload a scenes.Gaussians to the GPU as contiguous float32 tensors."""
@@ -589,7 +595,7 @@ def render_frame(gdev, feat, cam, K=8, max_isect=None, params=None, stream=None,
         f, fs = feat if isinstance(feat, tuple) else (feat, None)
         C = f.shape[1]
         out = torch.empty((P, C), dtype=torch.float32, device=mean.device)
-        qr_blend(f, fs, ids, w, cnt, out, width=fr.width, stream=stream)
+        qr_blend(f, fs, ids, w, cnt, out, stream=stream)
         res["out"] = out
         if dense:
             dout = torch.empty((P, C), dtype=torch.float32, device=mean.device)

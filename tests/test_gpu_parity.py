@@ -415,3 +415,41 @@ def test_dense_subtile_kernel(C, kind, tile):
     assert executed >= blended * C
     print(f"dense sub-tile C={C} {kind} tile {tile}: err {err.max():.2e}, blended {blended} "
           f"(oracle {want}), executed/useful FMA {executed / max(blended * C, 1):.2f}")
+
+
+@pytest.mark.parametrize("dtype,C", [("f32", 512), ("bf16", 512), ("bf16", 1024), ("fp8", 1024),
+                                     ("fp8", 512)])
+def test_blend_channel_chunks_bit_identical(dtype, C):
+    """Splitting the rows into channel chunks across warps changes neither the
+    terms nor their order per channel: every chunk count gives the same bits,
+    in both pixel orders, with ragged P and counts (0 .. K)."""
+    import torch
+    from paper_2512_20927_gb300 import qrender as q
+    rng = np.random.default_rng(C + len(dtype))
+    n, W, H_, K = 4000, 53, 37, 8
+    P = W * H_
+    f = torch.from_numpy(rng.normal(size=(n, C)).astype(np.float32)).cuda()
+    table, sc = f, None
+    if dtype == "bf16":
+        table = q.qr_quantize_bf16(f)
+    elif dtype == "fp8":
+        table, sc = q.qr_quantize_fp8(f)
+    ids, w, cnt = scenes.random_selection(seed=C, pixels=P, k=K, n=n)
+    dev = lambda a: torch.from_numpy(a).cuda()  # noqa: E731
+    ids, w, cnt = dev(ids), dev(w), dev(cnt)
+    try:
+        for width in (0, W):
+            outs = []
+            for chunks in (0, 1, 2, 4):
+                q.qr_set_blend_chunks(chunks)
+                o = torch.full((P, C), float("nan"), dtype=torch.float32, device="cuda")
+                q.qr_blend(table, sc, ids, w, cnt, o, width=width)
+                outs.append(o)
+            torch.cuda.synchronize()
+            for o in outs[1:]:
+                assert torch.equal(o, outs[0]), (width, dtype, C)
+            assert not torch.isnan(outs[0]).any()
+    finally:
+        q.qr_set_blend_chunks(0)
+    with pytest.raises(q.QRError):
+        q.qr_set_blend_chunks(3)

@@ -822,7 +822,8 @@ def run_batched(local, steps=3):
             "views_per_s": round(len(views) * 1000.0 / ms, 2),
             "mpixels_per_s": round(pixels / ms / 1000.0, 1),
             "autotune_ms": timings,
-            "chosen": {"tile": list(best.tile), "group": best.group, "chunks": best.chunks},
+            "chosen": {"tile": list(best.tile), "group": best.group, "chunks": best.chunks,
+                       "blend_warps": best.blend_warps or 8},
             "select_blend": {"ms": round(sb_ms, 4), "GB_per_s": round(sb_bytes / sb_ms / 1e6, 1),
                              "frac_of_hbm": round(sb_bytes / sb_ms / 1e6 / hbm, 4),
                              "bytes": sb_bytes, "bytes_counted": "map + ids + weights + counts written"},

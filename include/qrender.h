@@ -297,12 +297,14 @@ qr_status qr_batch_prepare(const qr_view *views, int32_t n_views, void *ws, size
  * warp in the blend (4, 2 or 1; 0 = largest allowed by K); chunks = channel
  * slices per feature row for groups of 4, taken by different blend warps
  * (1, 2 or 4 dividing the row's vectors per lane; 0 = the built-in choice);
- * ctas_per_sm caps the resident CTAs per SM (0 = occupancy limit).  Results
- * do not depend on group size or chunks beyond the summation order of a
- * pixel's rows (chunks: not at all).  Capturable in a CUDA graph. */
+ * blend_warps = blend warps per CTA beside the four selection warps (4 or 8;
+ * 0 = 8); ctas_per_sm caps the resident CTAs per SM (0 = occupancy limit).
+ * Results do not depend on group size or chunks beyond the summation order
+ * of a pixel's rows (chunks, blend_warps: not at all).  Capturable in a CUDA
+ * graph. */
 qr_status qr_render_batch(const void *ws, int32_t n_views, uint32_t total_tiles, qr_dtype dtype,
                           int32_t C, int32_t K, int32_t group, int32_t chunks,
-                          int32_t ctas_per_sm, qr_stream stream);
+                          int32_t blend_warps, int32_t ctas_per_sm, qr_stream stream);
 
 /* ---------------------------------------------------------------- backward */
 

@@ -48,6 +48,7 @@ class Batch:
     tile: tuple = (16, 16)
     group: int = 0
     chunks: int = 0               # channel chunks per feature row in the blend (0 = built-in)
+    blend_warps: int = 0          # blend warps per CTA beside 4 selection warps (0 = 8)
     ctas_per_sm: int = 0
     queries: object = None        # [Q, C] BF16 bit patterns (int16 tensor) or None
     streams: int = 4              # side streams the per-view projection and binning use
@@ -140,8 +141,8 @@ class Batch:
     def select_blend(self, stream=None):
         q._check(q.load().qr_render_batch(ctypes.c_void_p(self.ws_ptr), len(self.views),
                                           self.total_tiles, self.dtype, self.C, self.K,
-                                          self.group, self.chunks, self.ctas_per_sm,
-                                          q._stream(stream)),
+                                          self.group, self.chunks, self.blend_warps,
+                                          self.ctas_per_sm, q._stream(stream)),
                  "qr_render_batch")
 
     def relevance(self, stream=None):
@@ -207,9 +208,11 @@ def time_batch(batch: Batch, steps: int = 5, warmup: int = 2) -> float:
     return e0.elapsed_time(e1) / steps
 
 
-# (tile shape, pixel group, channel chunks per row): 0 = the built-in choice
-DEFAULT_CANDIDATES = (((16, 16), 0, 0), ((16, 16), 0, 1), ((16, 16), 0, 2), ((16, 16), 0, 4),
-                      ((8, 32), 0, 0), ((16, 16), 2, 0), ((8, 32), 2, 0))
+# (tile shape, pixel group, channel chunks per row, blend warps per CTA):
+# 0 = the built-in choice
+DEFAULT_CANDIDATES = (((16, 16), 0, 0, 0), ((16, 16), 0, 0, 4), ((16, 16), 0, 1, 0),
+                      ((16, 16), 0, 2, 0), ((16, 16), 0, 4, 0), ((16, 16), 0, 2, 4),
+                      ((8, 32), 0, 0, 0), ((16, 16), 2, 0, 0), ((8, 32), 2, 0, 0))
 
 
 def _vectors_per_lane(C: int, dtype: int) -> int:
@@ -217,20 +220,21 @@ def _vectors_per_lane(C: int, dtype: int) -> int:
 
 
 def autotune(scenes, views, K=8, queries=None, candidates=DEFAULT_CANDIDATES, steps=3):
-    """Try each (tile shape, pixel group, channel chunks) on the batch, return
+    """Try each (tile shape, pixel group, channel chunks, blend warps) on the batch, return
     (best Batch, timings); combinations the row width or K rule out are skipped."""
     timings = {}
     best, best_ms = None, float("inf")
     C = int(scenes[0].feat.shape[1])
     vt = _vectors_per_lane(C, q._dtype_code(scenes[0].feat))
-    for tile, group, chunks in candidates:
+    for tile, group, chunks, bw in candidates:
         if group and group * K > 32:
             continue
         if chunks and (vt % chunks or (group or (4 if K <= 8 else 2)) != 4):
             continue
-        b = Batch(scenes, views, K=K, tile=tile, group=group, chunks=chunks, queries=queries)
+        b = Batch(scenes, views, K=K, tile=tile, group=group, chunks=chunks, blend_warps=bw,
+                  queries=queries)
         ms = time_batch(b, steps=steps)
-        timings[f"{tile[0]}x{tile[1]}/g{group or 'auto'}/c{chunks or 'auto'}"] = round(ms, 4)
+        timings[f"{tile[0]}x{tile[1]}/g{group or 'auto'}/c{chunks or 'auto'}/w{bw or 8}"] = round(ms, 4)
         if ms < best_ms:
             if best is not None:
                 best.graph = None

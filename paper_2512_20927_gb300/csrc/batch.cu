@@ -130,7 +130,7 @@ __device__ __forceinline__ void st_cs(float4 *p, float4 v) {
 
 // ------------------------------------------------------------------ the kernel
 // Warp roles of a CTA: warps 0..3 select (select_tile, 128 threads, two pixels
-// each), warps 4..4+NBW-1 blend.  Two shared-memory buffers hold a tile's
+// each), warps 4..4+nbw-1 blend (nbw = 4 or 8, from the launch's block size).  Two shared-memory buffers hold a tile's
 // kept ids, normalised weights and counts; the selection fills one while the
 // blend warps read the other.  Hand-over uses hardware named barriers:
 //   FULL[b]  (ids 2, 3): selection arrives once buffer b holds tile n (or the
@@ -142,24 +142,24 @@ __device__ __forceinline__ void st_cs(float4 *p, float4 v) {
 //   id 1:                the selection threads among themselves.
 // Every thread of both roles runs the same number of barrier phases on each
 // id, so no phase is left open and no wait can be missed.
-constexpr int kNBW = 8;                               // blend warps
-constexpr int kBT = kSelThreads + 32 * kNBW;          // threads per CTA
+constexpr int kNBW = 8;                               // blend warps at most
+constexpr int kBT = kSelThreads + 32 * kNBW;          // threads per CTA at most
 constexpr int kItemEnd = -1;
 
 // Barrier ids are immediates (2 + b or 4 + b picked by a branch on b), so
-// the kernel uses barriers 0..5 only.
+// the kernel uses barriers 0..5 only; nt = the CTA's thread count.
 template <int ID>
-__device__ __forceinline__ void bar_sync_id() {
-    asm volatile("bar.sync %0, %1;" ::"n"(ID), "n"(kBT) : "memory");
+__device__ __forceinline__ void bar_sync_id(int nt) {
+    asm volatile("bar.sync %0, %1;" ::"n"(ID), "r"(nt) : "memory");
 }
 template <int ID>
-__device__ __forceinline__ void bar_arrive_id() {
-    asm volatile("bar.arrive %0, %1;" ::"n"(ID), "n"(kBT) : "memory");
+__device__ __forceinline__ void bar_arrive_id(int nt) {
+    asm volatile("bar.arrive %0, %1;" ::"n"(ID), "r"(nt) : "memory");
 }
-__device__ __forceinline__ void full_sync(int b) { if (b) bar_sync_id<3>(); else bar_sync_id<2>(); }
-__device__ __forceinline__ void full_arrive(int b) { if (b) bar_arrive_id<3>(); else bar_arrive_id<2>(); }
-__device__ __forceinline__ void empty_sync(int b) { if (b) bar_sync_id<5>(); else bar_sync_id<4>(); }
-__device__ __forceinline__ void empty_arrive(int b) { if (b) bar_arrive_id<5>(); else bar_arrive_id<4>(); }
+__device__ __forceinline__ void full_sync(int b, int nt) { if (b) bar_sync_id<3>(nt); else bar_sync_id<2>(nt); }
+__device__ __forceinline__ void full_arrive(int b, int nt) { if (b) bar_arrive_id<3>(nt); else bar_arrive_id<2>(nt); }
+__device__ __forceinline__ void empty_sync(int b, int nt) { if (b) bar_sync_id<5>(nt); else bar_sync_id<4>(nt); }
+__device__ __forceinline__ void empty_arrive(int b, int nt) { if (b) bar_arrive_id<5>(nt); else bar_arrive_id<4>(nt); }
 
 __device__ __forceinline__ int find_view(const BatchView *views, int n_views, uint32_t item) {
     int lo = 0, hi = n_views;   // last view with tile_base <= item
@@ -185,13 +185,14 @@ batch_kernel(const BatchView *__restrict__ views, int n_views, uint32_t total_it
     int32_t *s_ids0 = reinterpret_cast<int32_t *>(s_dyn);
     float *s_w0 = reinterpret_cast<float *>(s_dyn) + 2 * kSelPix * KSB;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nt = int(blockDim.x), nbw = nt / 32 - kSelThreads / 32;
 
     if (warp < kSelThreads / 32) {
         // ------------------------------------------------ selection role
         using Bar = NamedBarrier<1, kSelThreads>;
         for (int n = 0;; ++n) {
             const int b = n & 1;
-            if (n >= 2) empty_sync(b);   // the blend warps are done with buffer b
+            if (n >= 2) empty_sync(b, nt);   // the blend warps are done with buffer b
             if (threadIdx.x == 0) {
                 const uint32_t it = atomicAdd(counter, 1u);
                 s_item[b] = it < total_items ? int(it) : kItemEnd;
@@ -199,8 +200,8 @@ batch_kernel(const BatchView *__restrict__ views, int n_views, uint32_t total_it
             Bar::sync();
             const int item = s_item[b];
             if (item == kItemEnd) {
-                full_arrive(b);
-                if (n >= 1) empty_sync(b ^ 1);   // the last tile's arrival
+                full_arrive(b, nt);
+                if (n >= 1) empty_sync(b ^ 1, nt);   // the last tile's arrival
                 break;
             }
             const BatchView &V = views[find_view(views, n_views, uint32_t(item))];
@@ -249,7 +250,7 @@ batch_kernel(const BatchView *__restrict__ views, int n_views, uint32_t total_it
                 const int gx = tx * tile_w + e % tile_w, gy = ty * tile_h + e / tile_w;
                 if (gx < V.W && gy < V.H) V.cnt[int64_t(gy) * V.W + gx] = s_cnt[b][e];
             }
-            full_arrive(b);
+            full_arrive(b, nt);
         }
         return;
     }
@@ -263,7 +264,7 @@ batch_kernel(const BatchView *__restrict__ views, int n_views, uint32_t total_it
     const int bw = warp - kSelThreads / 32;
     for (int n = 0;; ++n) {
         const int b = n & 1;
-        full_sync(b);   // buffer b holds a selected tile (or the end marker)
+        full_sync(b, nt);   // buffer b holds a selected tile (or the end marker)
         const int item = s_item[b];
         if (item == kItemEnd) break;
         const BatchView &V = views[find_view(views, n_views, uint32_t(item))];
@@ -276,7 +277,7 @@ batch_kernel(const BatchView *__restrict__ views, int n_views, uint32_t total_it
         const int half_w = tile_w / 2;
         const uint4 *feat = reinterpret_cast<const uint4 *>(V.feat);
         const int mm = lane / K, j = lane - mm * K;
-        for (int it = bw; it < NITEMS; it += kNBW) {
+        for (int it = bw; it < NITEMS; it += nbw) {
             const int gi = it / NCH, ch = it - gi * NCH;
             int lx, ly;
             if (G == 4) { lx = 2 * (gi % half_w) + (mm & 1); ly = 2 * (gi / half_w) + (mm >> 1); }
@@ -366,15 +367,16 @@ batch_kernel(const BatchView *__restrict__ views, int n_views, uint32_t total_it
             }
             __syncwarp();   // the table is rewritten by the next item
         }
-        empty_arrive(b);   // buffer b may be refilled
+        empty_arrive(b, nt);   // buffer b may be refilled
     }
 }
 
 template <int DT, int VT, int G, int NCH>
 cudaError_t run_batch(const BatchView *dviews, int n_views, uint32_t total, uint32_t *counter,
-                      int K, int ctas_per_sm, cudaStream_t s) {
+                      int K, int nbw, int ctas_per_sm, cudaStream_t s) {
     auto kern = batch_kernel<DT, VT / NCH, G, NCH>;
     const int KSB = K | 1;
+    const int nt = kSelThreads + 32 * nbw;
     const size_t dyn = size_t(KSB) * kSelPix * 2 * 8;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(dyn));
     if (e != cudaSuccess) return e;
@@ -382,11 +384,11 @@ cudaError_t run_batch(const BatchView *dviews, int n_views, uint32_t total, uint
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     int occ = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kBT, dyn);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, nt, dyn);
     if (ctas_per_sm > 0 && ctas_per_sm < occ) occ = ctas_per_sm;
     if (occ < 1) occ = 1;
     const uint32_t grid = uint32_t(sms) * uint32_t(occ);
-    kern<<<grid < total ? grid : total, kBT, dyn, s>>>(dviews, n_views, total, counter, KSB);
+    kern<<<grid < total ? grid : total, nt, dyn, s>>>(dviews, n_views, total, counter, KSB);
     count_launch();
     return cudaGetLastError();
 }
@@ -405,20 +407,20 @@ constexpr int batch_default_chunks() {
 // per row for groups of 4 (0 = default; 1, 2, 4 where they divide VT).
 template <int DT, int VT>
 cudaError_t pick(const BatchView *d, int n, uint32_t total, uint32_t *counter, int K, int group,
-                 int chunks, int ctas, cudaStream_t s) {
+                 int chunks, int nbw, int ctas, cudaStream_t s) {
     constexpr int DEF = batch_default_chunks<DT, VT>();
     const int g = group > 0 ? group : (K <= 8 ? 4 : K <= 16 ? 2 : 1);
     if (g == 4 && K <= 8) {
         const int c = chunks > 0 ? chunks : DEF;
-        if (c == 1) return run_batch<DT, VT, 4, 1>(d, n, total, counter, K, ctas, s);
+        if (c == 1) return run_batch<DT, VT, 4, 1>(d, n, total, counter, K, nbw, ctas, s);
         if constexpr (VT % 2 == 0)
-            if (c == 2) return run_batch<DT, VT, 4, 2>(d, n, total, counter, K, ctas, s);
+            if (c == 2) return run_batch<DT, VT, 4, 2>(d, n, total, counter, K, nbw, ctas, s);
         if constexpr (VT % 4 == 0)
-            if (c == 4) return run_batch<DT, VT, 4, 4>(d, n, total, counter, K, ctas, s);
+            if (c == 4) return run_batch<DT, VT, 4, 4>(d, n, total, counter, K, nbw, ctas, s);
         return cudaErrorInvalidValue;
     }
-    if (g >= 2 && K <= 16) return run_batch<DT, VT, 2, DEF>(d, n, total, counter, K, ctas, s);
-    return run_batch<DT, VT, 1, DEF>(d, n, total, counter, K, ctas, s);
+    if (g >= 2 && K <= 16) return run_batch<DT, VT, 2, DEF>(d, n, total, counter, K, nbw, ctas, s);
+    return run_batch<DT, VT, 1, DEF>(d, n, total, counter, K, nbw, ctas, s);
 }
 
 }  // namespace
@@ -433,7 +435,9 @@ bool batch_supported(qr_dtype dt, int C) {
 size_t batch_desc_bytes(int n_views) { return (size_t(n_views) * sizeof(BatchView) + 255) / 256 * 256 + 256; }
 
 cudaError_t launch_batch(const void *ws, int n_views, uint32_t total_items, qr_dtype dt, int C,
-                         int K, int group, int chunks, int ctas_per_sm, cudaStream_t s) {
+                         int K, int group, int chunks, int blend_warps, int ctas_per_sm,
+                         cudaStream_t s) {
+    const int nbw = blend_warps > 0 ? blend_warps : kNBW;
     const BatchView *d = static_cast<const BatchView *>(ws);
     uint32_t *counter = reinterpret_cast<uint32_t *>(static_cast<char *>(const_cast<void *>(ws)) +
                                                      batch_desc_bytes(n_views) - 256);
@@ -442,17 +446,17 @@ cudaError_t launch_batch(const void *ws, int n_views, uint32_t total_items, qr_d
     const int vt = C / (dt == QR_F32 ? 4 : dt == QR_BF16 ? 8 : 16) / 32;
     switch (dt) {
         case QR_F32:
-            if (vt == 4) return pick<QR_F32, 4>(d, n_views, total_items, counter, K, group, chunks, ctas_per_sm, s);
-            if (vt == 2) return pick<QR_F32, 2>(d, n_views, total_items, counter, K, group, chunks, ctas_per_sm, s);
-            return pick<QR_F32, 1>(d, n_views, total_items, counter, K, group, chunks, ctas_per_sm, s);
+            if (vt == 4) return pick<QR_F32, 4>(d, n_views, total_items, counter, K, group, chunks, nbw, ctas_per_sm, s);
+            if (vt == 2) return pick<QR_F32, 2>(d, n_views, total_items, counter, K, group, chunks, nbw, ctas_per_sm, s);
+            return pick<QR_F32, 1>(d, n_views, total_items, counter, K, group, chunks, nbw, ctas_per_sm, s);
         case QR_BF16:
-            if (vt == 4) return pick<QR_BF16, 4>(d, n_views, total_items, counter, K, group, chunks, ctas_per_sm, s);
-            if (vt == 2) return pick<QR_BF16, 2>(d, n_views, total_items, counter, K, group, chunks, ctas_per_sm, s);
-            return pick<QR_BF16, 1>(d, n_views, total_items, counter, K, group, chunks, ctas_per_sm, s);
+            if (vt == 4) return pick<QR_BF16, 4>(d, n_views, total_items, counter, K, group, chunks, nbw, ctas_per_sm, s);
+            if (vt == 2) return pick<QR_BF16, 2>(d, n_views, total_items, counter, K, group, chunks, nbw, ctas_per_sm, s);
+            return pick<QR_BF16, 1>(d, n_views, total_items, counter, K, group, chunks, nbw, ctas_per_sm, s);
         case QR_FP8E4M3:
-            if (vt == 4) return pick<QR_FP8E4M3, 4>(d, n_views, total_items, counter, K, group, chunks, ctas_per_sm, s);
-            if (vt == 2) return pick<QR_FP8E4M3, 2>(d, n_views, total_items, counter, K, group, chunks, ctas_per_sm, s);
-            return pick<QR_FP8E4M3, 1>(d, n_views, total_items, counter, K, group, chunks, ctas_per_sm, s);
+            if (vt == 4) return pick<QR_FP8E4M3, 4>(d, n_views, total_items, counter, K, group, chunks, nbw, ctas_per_sm, s);
+            if (vt == 2) return pick<QR_FP8E4M3, 2>(d, n_views, total_items, counter, K, group, chunks, nbw, ctas_per_sm, s);
+            return pick<QR_FP8E4M3, 1>(d, n_views, total_items, counter, K, group, chunks, nbw, ctas_per_sm, s);
     }
     return cudaErrorInvalidValue;
 }

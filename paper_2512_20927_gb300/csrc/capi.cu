@@ -535,18 +535,19 @@ qr_status qr_batch_prepare(const qr_view *views, int32_t n_views, void *ws, size
 }
 
 qr_status qr_render_batch(const void *ws, int32_t n_views, uint32_t total_tiles, qr_dtype dtype,
-                          int32_t C, int32_t K, int32_t group, int32_t chunks, int32_t ctas_per_sm,
-                          qr_stream stream) {
+                          int32_t C, int32_t K, int32_t group, int32_t chunks,
+                          int32_t blend_warps, int32_t ctas_per_sm, qr_stream stream) {
     if (!ws || n_views < 1 || K < 1 || K > kKMax || group < 0 || group > 4 || ctas_per_sm < 0)
         return QR_ERR_INVALID_ARG;
     if (dtype != QR_F32 && dtype != QR_BF16 && dtype != QR_FP8E4M3) return QR_ERR_INVALID_ARG;
     if (!batch_supported(dtype, C)) return QR_ERR_NOT_SUPPORTED;
     if (chunks != 0 && chunks != 1 && chunks != 2 && chunks != 4) return QR_ERR_INVALID_ARG;
+    if (blend_warps != 0 && blend_warps != 4 && blend_warps != 8) return QR_ERR_INVALID_ARG;
     if (chunks > 0 && (C / (dtype == QR_F32 ? 4 : dtype == QR_BF16 ? 8 : 16) / 32) % chunks != 0)
         return QR_ERR_INVALID_ARG;
     if (total_tiles == 0) return QR_OK;
-    return from_cuda(launch_batch(ws, n_views, total_tiles, dtype, C, K, group, chunks, ctas_per_sm,
-                                  reinterpret_cast<cudaStream_t>(stream)));
+    return from_cuda(launch_batch(ws, n_views, total_tiles, dtype, C, K, group, chunks, blend_warps,
+                                  ctas_per_sm, reinterpret_cast<cudaStream_t>(stream)));
 }
 
 uint64_t qr_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }

@@ -150,7 +150,8 @@ bool batch_supported(qr_dtype dt, int C);
 size_t batch_desc_bytes(int n_views);
 size_t batch_view_size();
 cudaError_t launch_batch(const void *ws, int n_views, uint32_t total_items, qr_dtype dt, int C,
-                         int K, int group, int chunks, int ctas_per_sm, cudaStream_t s);
+                         int K, int group, int chunks, int blend_warps, int ctas_per_sm,
+                         cudaStream_t s);
 cudaError_t prepare_batch(const qr_view *views, int n_views, void *ws, uint32_t *total_items,
                           cudaStream_t s, BatchView *host_scratch);
 // Eq. 2 contrastive loss (contrastive.cu): out2 -> (L, 1/n), grad [P][C] -> dL/dF;

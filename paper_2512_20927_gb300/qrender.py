@@ -118,7 +118,8 @@ SIGNATURES = {
     "qr_batch_workspace_bytes": (ctypes.c_size_t, [_I32]),
     "qr_batch_prepare": (_S, [ctypes.POINTER(qr_view), _I32, _P, ctypes.c_size_t,
                               ctypes.POINTER(ctypes.c_uint32), _P]),
-    "qr_render_batch": (_S, [_P, _I32, ctypes.c_uint32, _S, _I32, _I32, _I32, _I32, _I32, _P]),
+    "qr_render_batch": (_S, [_P, _I32, ctypes.c_uint32, _S, _I32, _I32, _I32, _I32, _I32, _I32,
+                             _P]),
     "qr_quantize_bf16": (_S, [_P, _I64, _P, _P]),
     "qr_quantize_fp8": (_S, [_P, _I64, _I32, _P, _P, _P]),
     "qr_render_noalloc": (_S, [_P, _P, _P, _P, _I64, ctypes.POINTER(qr_camera),

@@ -122,3 +122,36 @@ def test_many_view_workload_against_oracle():
         ref_rel = oracle.relevance(ref.out_q, oracle.bf16_decode(qbits.cpu().numpy().view(np.uint16)))
         mag = np.abs(ref.out_q) @ np.abs(oracle.bf16_decode(qbits.cpu().numpy().view(np.uint16))).T
         assert (np.abs(got - ref_rel) <= 2.0 ** -7 * mag + 1e-5).all()
+
+
+@pytest.mark.parametrize("dtype,channels", [("f32", 512), ("bf16", 512), ("bf16", 256)])
+def test_batch_chunks_and_blend_warps_bit_identical(dtype, channels):
+    """The autotuner's channel-chunk and blend-warp axes change who computes
+    which channels, not the sums: every setting gives the same bits (ids,
+    weights, counts and map) as the default, and the default's map equals the
+    tile-ordered qr_blend of its own selection."""
+    import torch
+    from paper_2512_20927_gb300 import qrender as q
+    from paper_2512_20927_gb300.batch import Batch
+    sc, views, b0 = _small_batch((16, 16), channels=channels, dtype=dtype)
+    b0.step()
+    torch.cuda.synchronize()
+    ref = [b0.view_slice(i) for i in range(len(views))]
+    vt = channels // (4 if dtype == "f32" else 8) // 32
+    settings = [(c, w) for c in (1, 2, 4) for w in (0, 4) if vt % c == 0] + [(0, 4)]
+    for chunks, bw in settings:
+        b = Batch(b0.scenes, views, K=8, chunks=chunks, blend_warps=bw)
+        b.step()
+        torch.cuda.synchronize()
+        codes, _ = b.status()
+        assert all(c == q.QR_OK for c in codes)
+        for i in range(len(views)):
+            got = b.view_slice(i)
+            for k in ("ids", "weights", "counts", "out"):
+                assert torch.equal(got[k], ref[i][k]), (chunks, bw, i, k)
+    for i, (si, cam) in enumerate(views):
+        tab = sc[si][2].table
+        tiled = torch.empty_like(ref[i]["out"])
+        q.qr_blend(tab, None, ref[i]["ids"], ref[i]["weights"], ref[i]["counts"], tiled,
+                   width=cam.width)
+        assert torch.equal(tiled, ref[i]["out"]), i

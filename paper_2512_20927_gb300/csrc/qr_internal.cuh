@@ -42,14 +42,15 @@ enum { CNT_STATUS = 0, CNT_ISECT = 1, CNT_VISIBLE = 2, CNT_N = 3, CNT_SORT_N = 4
 
 // Workspace slots (byte offsets in qr_frame::off).
 enum Slot {
-    S_COUNTERS = 0, S_REC_M, S_REC_C, S_REC_A, S_REC_H, S_RECT, S_TCOUNT, S_GKEY,
-    S_VISCNT, S_BSUM, S_KID, S_OFF, S_TCNT, S_RANGES, S_KEYS64, S_SCRATCH64, S_IGID, S_DIFF,
+    S_COUNTERS = 0, S_DIFF, S_REC_M, S_REC_C, S_REC_A, S_REC_H, S_RECT, S_TCOUNT, S_GKEY,
+    S_VISCNT, S_BSUM, S_KID, S_OFF, S_TCNT, S_RANGES, S_KEYS64, S_SCRATCH64, S_IGID,
     S_CHUNK,
     S_END
 };
 constexpr int kProjectThreads = 256;
 // Copies of the 2-D difference array of per-tile counts; CTA b adds into copy
-// b % kDiffCopies, which spreads the atomics on its hot corners.
+// b % kDiffCopies, which spreads the atomics on its hot corners.  S_DIFF
+// follows S_COUNTERS so that one memset clears both.
 constexpr int kDiffCopies = 8;
 // Output slots per expansion chunk (the binning records the owner of each
 // chunk's first slot).
@@ -357,32 +358,36 @@ __device__ __forceinline__ uint32_t shfl_xor_key(uint32_t x, int m) {
     return __shfl_xor_sync(0xffffffffu, x, m);
 }
 
+// The smaller of (a, b) when take_min, else the larger.
+template <typename KT>
+__device__ __forceinline__ KT key_pick(KT a, KT b, bool take_min) {
+    return ((a < b) == take_min) ? a : b;
+}
+
+// Position i = base + e of a thread's keys differs from base only below bit
+// log2(E) (base is a multiple of E), so for strides j >= E and blocks k > j
+// the direction of a compare-exchange is the same for all E keys of a thread
+// and is computed once per stage.
 template <int E, int NTH, typename KT>
 __device__ void bitonic_regs(KT (&v)[E], KT *s) {
     constexpr int N = NTH * E;
     const int base = threadIdx.x * E;
     for (int k = 2; k <= N; k <<= 1) {
+        const bool up = (base & k) == 0;
         for (int j = k >> 1; j >= 32 * E; j >>= 1) {
 #pragma unroll
             for (int e = 0; e < E; ++e) s[base + e] = v[e];
             __syncthreads();
+            const bool take_min = ((base & j) == 0) == up;
+            const KT *partner = s + (base ^ j);
 #pragma unroll
-            for (int e = 0; e < E; ++e) {
-                const int i = base + e;
-                const KT y = s[i ^ j];
-                const bool take_min = ((i & j) == 0) == ((i & k) == 0);
-                v[e] = take_min ? (v[e] < y ? v[e] : y) : (v[e] < y ? y : v[e]);
-            }
+            for (int e = 0; e < E; ++e) v[e] = key_pick(v[e], partner[e], take_min);
             __syncthreads();
         }
         for (int j = min(k >> 1, 16 * E); j >= E; j >>= 1) {
+            const bool take_min = ((base & j) == 0) == up;
 #pragma unroll
-            for (int e = 0; e < E; ++e) {
-                const int i = base + e;
-                const KT y = shfl_xor_key(v[e], j / E);
-                const bool take_min = ((i & j) == 0) == ((i & k) == 0);
-                v[e] = take_min ? (v[e] < y ? v[e] : y) : (v[e] < y ? y : v[e]);
-            }
+            for (int e = 0; e < E; ++e) v[e] = key_pick(v[e], shfl_xor_key(v[e], j / E), take_min);
         }
 #pragma unroll
         for (int J = E / 2; J > 0; J >>= 1) {
@@ -390,9 +395,9 @@ __device__ void bitonic_regs(KT (&v)[E], KT *s) {
 #pragma unroll
             for (int e = 0; e < E; ++e) {
                 if ((e ^ J) > e) {
-                    const bool up = ((base + e) & k) == 0;
+                    const bool u = k >= E ? up : ((e & k) == 0);
                     const KT a = v[e], b = v[e ^ J];
-                    if ((a > b) == up) { v[e] = b; v[e ^ J] = a; }
+                    if ((a > b) == u) { v[e] = b; v[e ^ J] = a; }
                 }
             }
         }

@@ -90,6 +90,24 @@ struct PixLoss {
     const float *out2;
 };
 
+// Four partial sums per lane reduced over the warp with 7 shuffles instead of
+// 20: two halving levels (lane bits 4 and 3 pick which sums a lane keeps),
+// then a plain butterfly over bits 2..0.  Lane l ends with the full sum of
+// value 2 ((l >> 4) & 1) + ((l >> 3) & 1); red4_lane(u) is a lane holding u.
+__device__ __forceinline__ float reduce4(float (&v)[4], int lane) {
+    constexpr unsigned FULL = 0xffffffffu;
+    const bool u16 = (lane & 16) != 0, u8 = (lane & 8) != 0;
+    const float k0 = u16 ? v[2] : v[0], k1 = u16 ? v[3] : v[1];
+    const float s0 = u16 ? v[0] : v[2], s1 = u16 ? v[1] : v[3];
+    const float w0 = k0 + __shfl_xor_sync(FULL, s0, 16);
+    const float w1 = k1 + __shfl_xor_sync(FULL, s1, 16);
+    float x = (u8 ? w1 : w0) + __shfl_xor_sync(FULL, u8 ? w0 : w1, 8);
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
+    return x;
+}
+__device__ __forceinline__ int red4_lane(int u) { return ((u >> 1) << 4) | ((u & 1) << 3); }
+
 template <int DT, int VPL, bool LOSS>
 __global__ void __launch_bounds__(T)
 bwd_pixel(const float4 *__restrict__ rec_m, const float4 *__restrict__ rec_w,
@@ -138,10 +156,12 @@ bwd_pixel(const float4 *__restrict__ rec_m, const float4 *__restrict__ rec_w,
                     ff = fmaf(gr[t][q], gr[t][q], ff);
                     tt = fmaf(tr[t][q], tr[t][q], tt);
                 }
-            for (int o = 16; o > 0; o >>= 1) {
-                dot += __shfl_xor_sync(FULL, dot, o);
-                ff += __shfl_xor_sync(FULL, ff, o);
-                tt += __shfl_xor_sync(FULL, tt, o);
+            {
+                float v4[4] = {dot, ff, tt, 0.f};
+                const float x = reduce4(v4, lane);
+                dot = __shfl_sync(FULL, x, red4_lane(0));
+                ff = __shfl_sync(FULL, x, red4_lane(1));
+                tt = __shfl_sync(FULL, x, red4_lane(2));
             }
             const CosCoeffs cc = cos_coeffs(dot, ff, tt, 1e-8f);
             if (lane == 0) loss.term[p] = on ? 1.f - cc.cs : 0.f;
@@ -199,13 +219,11 @@ bwd_pixel(const float4 *__restrict__ rec_m, const float4 *__restrict__ rec_w,
                         for (int q = 0; q < CPV; ++q) part[u] = fmaf(fv[q], gr[t][q], part[u]);
                     }
                 }
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) part[u] += __shfl_xor_sync(FULL, part[u], o);
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    if (j0 + u < m && lane == j0 + u) s_mine = part[u] * sc4[u];
+                // lane j0 + u takes row u's dot from a lane that holds it
+                const float x = reduce4(part, lane);
+                const int u = lane - j0;
+                const float su = __shfl_sync(FULL, x, red4_lane(u & 3));
+                if (u >= 0 && u < 4 && lane < m) s_mine = su * sc4[u & 3];
             }
         } else {
             for (int j = 0; j < m; ++j) {
@@ -311,8 +329,8 @@ __device__ __forceinline__ void bitonic64(unsigned long long *s, int npow2) {
 // sorted order with independent loads; the (dalpha, dA) terms are summed per
 // segment by a warp's lanes in a fixed order.  Per CH-channel chunk, the
 // tile's rows of g are staged in shared memory (by TMA when a tensor map is
-// given, the next chunk's copy issued as soon as the walk has read the
-// current one) and the warps walk equal shares of the entries (see below),
+// given, into two buffers: chunk c + 1 lands while chunk c is walked, and a
+// buffer is refilled with chunk c + 2 as soon as the walk has read it) and the warps walk equal shares of the entries (see below),
 // each segment's w * g[pixel] sum going to its partial row at slot range.x +
 // segment of the tile's intersection range.
 constexpr unsigned kTmaSpin = 1u << 26;   // polls before a staging wait gives up
@@ -334,7 +352,7 @@ bwd_tile_partials(const uint2 *__restrict__ ranges, int W, int H, int tile_w, in
     extern __shared__ __align__(16) unsigned char s_dyn[];
     __shared__ uint32_t s_w[32];
     __shared__ uint32_t s_nseg;
-    __shared__ __align__(8) uint64_t s_bar[1];
+    __shared__ __align__(8) uint64_t s_bar[2];
     __shared__ int s_ok;
     // per chunk parity, per warp: the continued and the begun piece (64 channels each)
     __shared__ __align__(16) float4 s_piece[2][(T / 32) * 2 * 16];
@@ -367,11 +385,17 @@ bwd_tile_partials(const uint2 *__restrict__ ranges, int W, int H, int tile_w, in
     const int nchunks = (C + CH - 1) / CH;
     const uint32_t chunk_bytes = uint32_t(T) * uint32_t(CH) * 4u;
     if (use_tma && threadIdx.x == 0) {
-        // the first chunk of g flies while the keys are sorted
+        // the first two chunks of g fly while the keys are sorted (two
+        // buffers: chunk c lands in buffer c & 1)
         tma_mbar_init(&s_bar[0], 1);
+        tma_mbar_init(&s_bar[1], 1);
         tma_fence_init();
         tma_expect_tx(&s_bar[0], chunk_bytes);
         tma_load_3d(s_g, &gmap, 0, tx * tile_w, ty * tile_h, &s_bar[0]);
+        if (nchunks > 1) {
+            tma_expect_tx(&s_bar[1], chunk_bytes);
+            tma_load_3d(s_g + T * CH, &gmap, CH, tx * tile_w, ty * tile_h, &s_bar[1]);
+        }
     }
     auto key_of = [&](int j) -> KT {
         return j < m ? (KT(uint32_t(ids[p * K + j])) << SHIFT) | KT(uint32_t(threadIdx.x * K + j))
@@ -469,7 +493,9 @@ bwd_tile_partials(const uint2 *__restrict__ ranges, int W, int H, int tile_w, in
         const int c0 = c * CH;
         const float *gbuf = s_g;
         if (use_tma) {
-            if (threadIdx.x == 0) s_ok = tma_mbar_wait(&s_bar[0], uint32_t(c) & 1u, kTmaSpin) ? 1 : 0;
+            gbuf = s_g + (c & 1) * (T * CH);
+            if (threadIdx.x == 0)
+                s_ok = tma_mbar_wait(&s_bar[c & 1], uint32_t(c >> 1) & 1u, kTmaSpin) ? 1 : 0;
             __syncthreads();
             if (!s_ok) { c_fail = c; break; }
         } else {
@@ -561,11 +587,13 @@ bwd_tile_partials(const uint2 *__restrict__ ranges, int W, int H, int tile_w, in
             sla[warp] = last_u;
         }
         __syncthreads();   // the chunk's g is consumed and the pieces are visible
-        if (use_tma && threadIdx.x == 0 && c + 1 < nchunks) {
-            // refill the buffer while the pieces are combined (the pieces use
-            // the other half of the piece buffer in the next chunk)
-            tma_expect_tx(&s_bar[0], chunk_bytes);
-            tma_load_3d(s_g, &gmap, (c + 1) * CH, tx * tile_w, ty * tile_h, &s_bar[0]);
+        if (use_tma && threadIdx.x == 0 && c + 2 < nchunks) {
+            // refill the consumed buffer with chunk c + 2 while the pieces are
+            // combined and chunk c + 1 is walked (the pieces use the other
+            // half of the piece buffer in the next chunk)
+            tma_expect_tx(&s_bar[c & 1], chunk_bytes);
+            tma_load_3d(s_g + (c & 1) * (T * CH), &gmap, (c + 2) * CH, tx * tile_w, ty * tile_h,
+                        &s_bar[c & 1]);
         }
         if (sla[warp] >= 0) {
             const int u = sla[warp];
@@ -583,9 +611,11 @@ bwd_tile_partials(const uint2 *__restrict__ ranges, int W, int H, int tile_w, in
     }
     if (c_fail >= 0 && threadIdx.x == 0) {
         // a staging copy did not arrive: report it, and let the copies still in
-        // flight (chunk c_fail) land before the CTA exits
+        // flight (chunks c_fail and c_fail + 1) land before the CTA exits
         atomicExch(&counters[CNT_STATUS], uint32_t(QR_ERR_DEVICE_TIMEOUT));
-        tma_mbar_wait(&s_bar[0], uint32_t(c_fail) & 1u, kTmaSpin);
+        tma_mbar_wait(&s_bar[c_fail & 1], uint32_t(c_fail >> 1) & 1u, kTmaSpin);
+        if (c_fail + 1 < nchunks)
+            tma_mbar_wait(&s_bar[(c_fail + 1) & 1], uint32_t((c_fail + 1) >> 1) & 1u, kTmaSpin);
     }
 }
 
@@ -866,11 +896,14 @@ cudaError_t backward_impl(const qr_frame &f, const void *feat, const float *scal
     };
     if (e != cudaSuccess) return join(e);
     // per-tile partials; for K <= 8 the tile's rows of g are staged by TMA
-    // (3-D boxes {64 channels, tile_w pixels, tile_h rows} of the [H][W][C]
+    // (3-D boxes {32 channels, tile_w pixels, tile_h rows} of the [H][W][C]
     // gradient) when the driver provides a tensor-map encoder
     int npow2 = 1;
     while (npow2 < 256 * K) npow2 <<= 1;
-    const int CH = K <= 8 ? 64 : 32;
+    // TMA staging: 32-channel chunks in two buffers (chunk c + 1 lands while
+    // chunk c is walked); without it one 64- (K <= 8) or 32-channel buffer
+    // filled by the threads
+    constexpr int kTmaCH = 32;
     CUtensorMap gmap;
     std::memset(&gmap, 0, sizeof(gmap));
     int use_tma = 0;
@@ -878,21 +911,22 @@ cudaError_t backward_impl(const qr_frame &f, const void *feat, const float *scal
         EncodeTiled enc = tensor_map_encoder();
         const cuuint64_t dims[3] = {cuuint64_t(C), cuuint64_t(f.camera.width), cuuint64_t(f.camera.height)};
         const cuuint64_t strides[2] = {cuuint64_t(C) * 4, cuuint64_t(C) * 4 * cuuint64_t(f.camera.width)};
-        const cuuint32_t box[3] = {cuuint32_t(CH), cuuint32_t(f.params.tile_w), cuuint32_t(f.params.tile_h)};
+        const cuuint32_t box[3] = {cuuint32_t(kTmaCH), cuuint32_t(f.params.tile_w), cuuint32_t(f.params.tile_h)};
         const cuuint32_t estr[3] = {1, 1, 1};
         if (enc && enc(&gmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(grad_out), dims,
                        strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
             use_tma = 1;
     }
-    // One CTA per tile.  With TMA staging the CTA holds one g chunk (64
-    // channels x 256 pixels, 64 KB) and reads the E terms from global memory,
+    // One CTA per tile.  With TMA staging the CTA holds two g chunks (32
+    // channels x 256 pixels, 32 KB each) and reads the E terms from global memory,
     // so two CTAs share an SM and one's sort, gathers and staging waits
     // overlap the other's walk.
     const bool k32 = K <= 8 && f.n < (int64_t(1) << 21);
     const size_t key_bytes = k32 ? 4 : 8;
     const size_t g_off = (size_t(npow2) * key_bytes + size_t(256 * K) * 12 + 1023) & ~size_t(1023);
-    const size_t smem = 1024 + g_off + size_t(256) * CH * 4;
+    const int CH = use_tma ? kTmaCH : (K <= 8 ? 64 : 32);
+    const size_t smem = 1024 + g_off + size_t(use_tma ? 2 : 1) * 256 * CH * 4;
     auto tp = [&](auto kern) {
         cudaError_t ee = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
         if (ee != cudaSuccess) return ee;

@@ -329,8 +329,8 @@ __device__ __forceinline__ void bitonic64(unsigned long long *s, int npow2) {
 // sorted order with independent loads; the (dalpha, dA) terms are summed per
 // segment by a warp's lanes in a fixed order.  Per CH-channel chunk, the
 // tile's rows of g are staged in shared memory (by TMA when a tensor map is
-// given, into two buffers: chunk c + 1 lands while chunk c is walked, and a
-// buffer is refilled with chunk c + 2 as soon as the walk has read it) and the warps walk equal shares of the entries (see below),
+// given, the next chunk's copy issued as soon as the walk has read the
+// current one) and the warps walk equal shares of the entries (see below),
 // each segment's w * g[pixel] sum going to its partial row at slot range.x +
 // segment of the tile's intersection range.
 constexpr unsigned kTmaSpin = 1u << 26;   // polls before a staging wait gives up
@@ -352,7 +352,7 @@ bwd_tile_partials(const uint2 *__restrict__ ranges, int W, int H, int tile_w, in
     extern __shared__ __align__(16) unsigned char s_dyn[];
     __shared__ uint32_t s_w[32];
     __shared__ uint32_t s_nseg;
-    __shared__ __align__(8) uint64_t s_bar[2];
+    __shared__ __align__(8) uint64_t s_bar[1];
     __shared__ int s_ok;
     // per chunk parity, per warp: the continued and the begun piece (64 channels each)
     __shared__ __align__(16) float4 s_piece[2][(T / 32) * 2 * 16];
@@ -385,17 +385,11 @@ bwd_tile_partials(const uint2 *__restrict__ ranges, int W, int H, int tile_w, in
     const int nchunks = (C + CH - 1) / CH;
     const uint32_t chunk_bytes = uint32_t(T) * uint32_t(CH) * 4u;
     if (use_tma && threadIdx.x == 0) {
-        // the first two chunks of g fly while the keys are sorted (two
-        // buffers: chunk c lands in buffer c & 1)
+        // the first chunk of g flies while the keys are sorted
         tma_mbar_init(&s_bar[0], 1);
-        tma_mbar_init(&s_bar[1], 1);
         tma_fence_init();
         tma_expect_tx(&s_bar[0], chunk_bytes);
         tma_load_3d(s_g, &gmap, 0, tx * tile_w, ty * tile_h, &s_bar[0]);
-        if (nchunks > 1) {
-            tma_expect_tx(&s_bar[1], chunk_bytes);
-            tma_load_3d(s_g + T * CH, &gmap, CH, tx * tile_w, ty * tile_h, &s_bar[1]);
-        }
     }
     auto key_of = [&](int j) -> KT {
         return j < m ? (KT(uint32_t(ids[p * K + j])) << SHIFT) | KT(uint32_t(threadIdx.x * K + j))
@@ -493,9 +487,7 @@ bwd_tile_partials(const uint2 *__restrict__ ranges, int W, int H, int tile_w, in
         const int c0 = c * CH;
         const float *gbuf = s_g;
         if (use_tma) {
-            gbuf = s_g + (c & 1) * (T * CH);
-            if (threadIdx.x == 0)
-                s_ok = tma_mbar_wait(&s_bar[c & 1], uint32_t(c >> 1) & 1u, kTmaSpin) ? 1 : 0;
+            if (threadIdx.x == 0) s_ok = tma_mbar_wait(&s_bar[0], uint32_t(c) & 1u, kTmaSpin) ? 1 : 0;
             __syncthreads();
             if (!s_ok) { c_fail = c; break; }
         } else {
@@ -587,13 +579,11 @@ bwd_tile_partials(const uint2 *__restrict__ ranges, int W, int H, int tile_w, in
             sla[warp] = last_u;
         }
         __syncthreads();   // the chunk's g is consumed and the pieces are visible
-        if (use_tma && threadIdx.x == 0 && c + 2 < nchunks) {
-            // refill the consumed buffer with chunk c + 2 while the pieces are
-            // combined and chunk c + 1 is walked (the pieces use the other
-            // half of the piece buffer in the next chunk)
-            tma_expect_tx(&s_bar[c & 1], chunk_bytes);
-            tma_load_3d(s_g + (c & 1) * (T * CH), &gmap, (c + 2) * CH, tx * tile_w, ty * tile_h,
-                        &s_bar[c & 1]);
+        if (use_tma && threadIdx.x == 0 && c + 1 < nchunks) {
+            // refill the buffer while the pieces are combined (the pieces use
+            // the other half of the piece buffer in the next chunk)
+            tma_expect_tx(&s_bar[0], chunk_bytes);
+            tma_load_3d(s_g, &gmap, (c + 1) * CH, tx * tile_w, ty * tile_h, &s_bar[0]);
         }
         if (sla[warp] >= 0) {
             const int u = sla[warp];
@@ -611,11 +601,9 @@ bwd_tile_partials(const uint2 *__restrict__ ranges, int W, int H, int tile_w, in
     }
     if (c_fail >= 0 && threadIdx.x == 0) {
         // a staging copy did not arrive: report it, and let the copies still in
-        // flight (chunks c_fail and c_fail + 1) land before the CTA exits
+        // flight (chunk c_fail) land before the CTA exits
         atomicExch(&counters[CNT_STATUS], uint32_t(QR_ERR_DEVICE_TIMEOUT));
-        tma_mbar_wait(&s_bar[c_fail & 1], uint32_t(c_fail >> 1) & 1u, kTmaSpin);
-        if (c_fail + 1 < nchunks)
-            tma_mbar_wait(&s_bar[(c_fail + 1) & 1], uint32_t((c_fail + 1) >> 1) & 1u, kTmaSpin);
+        tma_mbar_wait(&s_bar[0], uint32_t(c_fail) & 1u, kTmaSpin);
     }
 }
 
@@ -896,14 +884,11 @@ cudaError_t backward_impl(const qr_frame &f, const void *feat, const float *scal
     };
     if (e != cudaSuccess) return join(e);
     // per-tile partials; for K <= 8 the tile's rows of g are staged by TMA
-    // (3-D boxes {32 channels, tile_w pixels, tile_h rows} of the [H][W][C]
+    // (3-D boxes {64 channels, tile_w pixels, tile_h rows} of the [H][W][C]
     // gradient) when the driver provides a tensor-map encoder
     int npow2 = 1;
     while (npow2 < 256 * K) npow2 <<= 1;
-    // TMA staging: 32-channel chunks in two buffers (chunk c + 1 lands while
-    // chunk c is walked); without it one 64- (K <= 8) or 32-channel buffer
-    // filled by the threads
-    constexpr int kTmaCH = 32;
+    const int CH = K <= 8 ? 64 : 32;
     CUtensorMap gmap;
     std::memset(&gmap, 0, sizeof(gmap));
     int use_tma = 0;
@@ -911,22 +896,21 @@ cudaError_t backward_impl(const qr_frame &f, const void *feat, const float *scal
         EncodeTiled enc = tensor_map_encoder();
         const cuuint64_t dims[3] = {cuuint64_t(C), cuuint64_t(f.camera.width), cuuint64_t(f.camera.height)};
         const cuuint64_t strides[2] = {cuuint64_t(C) * 4, cuuint64_t(C) * 4 * cuuint64_t(f.camera.width)};
-        const cuuint32_t box[3] = {cuuint32_t(kTmaCH), cuuint32_t(f.params.tile_w), cuuint32_t(f.params.tile_h)};
+        const cuuint32_t box[3] = {cuuint32_t(CH), cuuint32_t(f.params.tile_w), cuuint32_t(f.params.tile_h)};
         const cuuint32_t estr[3] = {1, 1, 1};
         if (enc && enc(&gmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(grad_out), dims,
                        strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
             use_tma = 1;
     }
-    // One CTA per tile.  With TMA staging the CTA holds two g chunks (32
-    // channels x 256 pixels, 32 KB each) and reads the E terms from global memory,
+    // One CTA per tile.  With TMA staging the CTA holds one g chunk (64
+    // channels x 256 pixels, 64 KB) and reads the E terms from global memory,
     // so two CTAs share an SM and one's sort, gathers and staging waits
     // overlap the other's walk.
     const bool k32 = K <= 8 && f.n < (int64_t(1) << 21);
     const size_t key_bytes = k32 ? 4 : 8;
     const size_t g_off = (size_t(npow2) * key_bytes + size_t(256 * K) * 12 + 1023) & ~size_t(1023);
-    const int CH = use_tma ? kTmaCH : (K <= 8 ? 64 : 32);
-    const size_t smem = 1024 + g_off + size_t(use_tma ? 2 : 1) * 256 * CH * 4;
+    const size_t smem = 1024 + g_off + size_t(256) * CH * 4;
     auto tp = [&](auto kern) {
         cudaError_t ee = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
         if (ee != cudaSuccess) return ee;

@@ -296,7 +296,8 @@ qr_status qr_batch_prepare(const qr_view *views, int32_t n_views, void *ws, size
  * sixteen-byte vectors: e.g. 512-D F32 / BF16 / FP8); group = pixels per
  * warp in the blend (4, 2 or 1; 0 = largest allowed by K); chunks = channel
  * slices per feature row for groups of 4, taken by different blend warps
- * (1, 2 or 4 dividing the row's vectors per lane; 0 = the built-in choice);
+ * (1, 2 or 4 dividing C / 128 and leaving at most 512 channels per slice;
+ * 0 = the built-in choice);
  * blend_warps = blend warps per CTA beside the four selection warps (4 or 8;
  * 0 = 8); ctas_per_sm caps the resident CTAs per SM (0 = occupancy limit).
  * Results do not depend on group size or chunks beyond the summation order
@@ -503,9 +504,9 @@ uint64_t qr_launch_count(void);
  * without anything hanging.  Not for production use; not thread-safe. */
 void qr_set_wait_limit(uint32_t polls);
 
-/* Tuning: the blend of rows of 2 or 4 sixteen-byte vectors per lane
- * (e.g. 512-D BF16 / F32 rows) with K <= 8 splits each feature row into
- * `chunks` channel slices taken by different warps (1, 2 or 4; 0 restores the
+/* Tuning: the blend of 512-D rows (any dtype) with K <= 8 splits each
+ * feature row into `chunks` channel slices taken by different warps (1, 2 or
+ * 4; 0 restores the built-in choice, one slice; wider rows always use the
  * built-in choice: at most 16 accumulators per pixel and lane).  More chunks
  * mean fewer registers per thread and more warps per SM.  The sums and their
  * order per channel do not change, so results are bit-identical for every

@@ -215,8 +215,8 @@ DEFAULT_CANDIDATES = (((16, 16), 0, 0, 0), ((16, 16), 0, 0, 4), ((16, 16), 0, 1,
                       ((8, 32), 0, 0, 0), ((16, 16), 2, 0, 0), ((8, 32), 2, 0, 0))
 
 
-def _vectors_per_lane(C: int, dtype: int) -> int:
-    return C // {q.QR_F32: 4, q.QR_BF16: 8}.get(dtype, 16) // 32
+def _quads_per_lane(C: int) -> int:
+    return C // 128
 
 
 def autotune(scenes, views, K=8, queries=None, candidates=DEFAULT_CANDIDATES, steps=3):
@@ -225,11 +225,11 @@ def autotune(scenes, views, K=8, queries=None, candidates=DEFAULT_CANDIDATES, st
     timings = {}
     best, best_ms = None, float("inf")
     C = int(scenes[0].feat.shape[1])
-    vt = _vectors_per_lane(C, q._dtype_code(scenes[0].feat))
+    qt = _quads_per_lane(C)
     for tile, group, chunks, bw in candidates:
         if group and group * K > 32:
             continue
-        if chunks and (vt % chunks or (group or (4 if K <= 8 else 2)) != 4):
+        if chunks and (qt % chunks or qt // chunks > 4 or (group or (4 if K <= 8 else 2)) != 4):
             continue
         b = Batch(scenes, views, K=K, tile=tile, group=group, chunks=chunks, blend_warps=bw,
                   queries=queries)

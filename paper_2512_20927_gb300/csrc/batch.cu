@@ -23,9 +23,12 @@
 // Hand-over between the roles uses named barriers (below).  Per-view
 // descriptors live in device memory (qr_batch_prepare), the counter is
 // cleared by a memset on the stream, so the launch can sit in a CUDA graph.
+#include <type_traits>
+
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
+#include "quad.cuh"
 #include "select_tile.cuh"
 
 namespace qr {
@@ -171,7 +174,8 @@ __device__ __forceinline__ int find_view(const BatchView *views, int n_views, ui
 }
 
 // Dynamic shared memory: ids [2][256][KSB] int32, weights [2][256][KSB] float.
-template <int DT, int VPL, int G, int NCH>
+// QPL quads (4 channels) per lane per channel chunk, NCH chunks per row.
+template <int DT, int QPL, int G, int NCH>
 __global__ void __launch_bounds__(kBT, DT == QR_FP8E4M3 ? 1 : 2)
 batch_kernel(const BatchView *__restrict__ views, int n_views, uint32_t total_items,
              uint32_t *__restrict__ counter, int KSB) {
@@ -255,10 +259,10 @@ batch_kernel(const BatchView *__restrict__ views, int n_views, uint32_t total_it
         return;
     }
     // ---------------------------------------------------- blend role
-    constexpr int CPV = VecT<DT>::C;
-    constexpr int CV = 32 * VPL;                 // vectors of a channel chunk
-    constexpr int ROWV = CV * NCH;               // vectors of a row
-    constexpr int U = VPL >= 2 ? 2 : 4;          // rows in flight
+    constexpr int QB = Quad<DT>::B;
+    constexpr int CQ = 32 * QPL;                 // quads of a channel chunk
+    constexpr int ROWQ = CQ * NCH;               // quads of a row (C / 4)
+    constexpr int U = QPL * QB >= 32 ? 2 : 4;    // rows in flight
     constexpr unsigned FULL = 0xffffffffu;
     constexpr int NITEMS = (kSelPix / G) * NCH;
     const int bw = warp - kSelThreads / 32;
@@ -275,7 +279,7 @@ batch_kernel(const BatchView *__restrict__ views, int n_views, uint32_t total_it
         const int tx = tile % V.tiles_x, ty = tile / V.tiles_x;
         const int tile_w = V.tile_w, tile_h = kSelPix / tile_w;
         const int half_w = tile_w / 2;
-        const uint4 *feat = reinterpret_cast<const uint4 *>(V.feat);
+        const unsigned char *feat = V.feat;
         const int mm = lane / K, j = lane - mm * K;
         for (int it = bw; it < NITEMS; it += nbw) {
             const int gi = it / NCH, ch = it - gi * NCH;
@@ -308,25 +312,25 @@ batch_kernel(const BatchView *__restrict__ views, int n_views, uint32_t total_it
                 if (lane == leader) s_tid[bw][slot] = id;
             }
             __syncwarp();
-            float acc[G][VPL][CPV];
+            float acc[G][QPL][4];
 #pragma unroll
             for (int g = 0; g < G; ++g)
 #pragma unroll
-                for (int v = 0; v < VPL; ++v)
+                for (int v = 0; v < QPL; ++v)
 #pragma unroll
-                    for (int q = 0; q < CPV; ++q) acc[g][v][q] = 0.f;
-            const uint4 *fch = feat + ch * CV + lane;
+                    for (int q = 0; q < 4; ++q) acc[g][v][q] = 0.f;
+            const unsigned char *fch = feat + size_t(ch * CQ + lane) * QB;
             for (int r0 = 0; r0 < nrows; r0 += U) {
-                uint4 r[U][VPL];
+                typename Quad<DT>::T r[U][QPL];
                 float sc[U];
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     const bool ok = r0 + u < nrows;
                     const int rid = ok ? s_tid[bw][r0 + u] : 0;
-                    const uint4 *row = fch + int64_t(rid) * ROWV;
+                    const unsigned char *row = fch + size_t(rid) * (size_t(ROWQ) * QB);
 #pragma unroll
-                    for (int v = 0; v < VPL; ++v)
-                        r[u][v] = ok ? ldg_nc(row + 32 * v) : make_uint4(0, 0, 0, 0);
+                    for (int v = 0; v < QPL; ++v)
+                        r[u][v] = ok ? ld_quad<DT>(row + size_t(32 * v) * QB) : zero_quad<DT>();
                     if (DT == QR_FP8E4M3) sc[u] = ok ? V.fscale[rid] : 0.f;
                 }
 #pragma unroll
@@ -336,17 +340,17 @@ batch_kernel(const BatchView *__restrict__ views, int n_views, uint32_t total_it
 #pragma unroll
                     for (int g = 0; g < G; ++g)
                         wg[g] = DT == QR_FP8E4M3 ? s_tw[bw][r0 + u][g] * sc[u] : s_tw[bw][r0 + u][g];
-                    float fv[VPL][CPV];
+                    float fv[QPL][4];
 #pragma unroll
-                    for (int v = 0; v < VPL; ++v) dec_vec<DT>(r[u][v], fv[v]);
+                    for (int v = 0; v < QPL; ++v) dec_quad<DT>(r[u][v], fv[v]);
 #pragma unroll
                     for (int g = 0; g < G; ++g)
                         if (wg[g] != 0.f) {
 #pragma unroll
-                            for (int v = 0; v < VPL; ++v)
-#pragma unroll
-                                for (int q = 0; q < CPV; q += 2)
-                                    fma2b(acc[g][v] + q, wg[g], fv[v][q], fv[v][q + 1]);
+                            for (int v = 0; v < QPL; ++v) {
+                                fma2b(acc[g][v] + 0, wg[g], fv[v][0], fv[v][1]);
+                                fma2b(acc[g][v] + 2, wg[g], fv[v][2], fv[v][3]);
+                            }
                         }
                 }
             }
@@ -354,15 +358,11 @@ batch_kernel(const BatchView *__restrict__ views, int n_views, uint32_t total_it
             for (int g = 0; g < G; ++g) {
                 const int64_t pg = __shfl_sync(FULL, p, g * K < 32 ? g * K : 0);
                 if (pg >= 0) {
-                    float4 *o = reinterpret_cast<float4 *>(V.out) + pg * (int64_t(ROWV) * CPV / 4) +
-                                ch * (CV * CPV / 4);
+                    float4 *o = reinterpret_cast<float4 *>(V.out) + pg * int64_t(ROWQ) + ch * CQ + lane;
 #pragma unroll
-                    for (int v = 0; v < VPL; ++v)
-#pragma unroll
-                        for (int q = 0; q < CPV / 4; ++q)
-                            st_cs(o + int64_t(lane + 32 * v) * (CPV / 4) + q,
-                                  make_float4(acc[g][v][4 * q], acc[g][v][4 * q + 1],
-                                              acc[g][v][4 * q + 2], acc[g][v][4 * q + 3]));
+                    for (int v = 0; v < QPL; ++v)
+                        st_cs(o + 32 * v, make_float4(acc[g][v][0], acc[g][v][1], acc[g][v][2],
+                                                      acc[g][v][3]));
                 }
             }
             __syncwarp();   // the table is rewritten by the next item
@@ -371,10 +371,10 @@ batch_kernel(const BatchView *__restrict__ views, int n_views, uint32_t total_it
     }
 }
 
-template <int DT, int VT, int G, int NCH>
+template <int DT, int QT, int G, int NCH>
 cudaError_t run_batch(const BatchView *dviews, int n_views, uint32_t total, uint32_t *counter,
                       int K, int nbw, int ctas_per_sm, cudaStream_t s) {
-    auto kern = batch_kernel<DT, VT / NCH, G, NCH>;
+    auto kern = batch_kernel<DT, QT / NCH, G, NCH>;
     const int KSB = K | 1;
     const int nt = kSelThreads + 32 * nbw;
     const size_t dyn = size_t(KSB) * kSelPix * 2 * 8;
@@ -393,34 +393,36 @@ cudaError_t run_batch(const BatchView *dviews, int n_views, uint32_t total, uint
     return cudaGetLastError();
 }
 
-// Channel chunks per row by default: at most 8 accumulators per pixel and
-// lane (two F32 vectors or one BF16 / FP8 vector), so the blend warps fit the
-// register budget of two CTAs per SM.
-template <int DT, int VT>
+// Channel chunks per row by default: at most 2 quads (8 accumulators) per
+// pixel and lane, so the blend warps fit the register budget of two CTAs
+// per SM.
+template <int QT>
 constexpr int batch_default_chunks() {
-    constexpr int lim = DT == QR_F32 ? 2 : 1;
-    return VT <= lim ? 1 : VT / lim;
+    return QT <= 2 ? 1 : QT / 2;
 }
 
-// VT 16-byte vectors per lane over the whole row (1, 2 or 4).  group picks
-// the pixel-group size (0 = largest allowed by K), chunks the channel chunks
-// per row for groups of 4 (0 = default; 1, 2, 4 where they divide VT).
-template <int DT, int VT>
+// QT = C / 128 quads per lane over the whole row (1 .. 16).  group picks the
+// pixel-group size (0 = largest allowed by K), chunks the channel chunks per
+// row for groups of 4 (0 = default; 1, 2, 4 where they divide QT and leave at
+// most 4 quads per lane).
+template <int DT, int QT>
 cudaError_t pick(const BatchView *d, int n, uint32_t total, uint32_t *counter, int K, int group,
                  int chunks, int nbw, int ctas, cudaStream_t s) {
-    constexpr int DEF = batch_default_chunks<DT, VT>();
+    constexpr int DEF = batch_default_chunks<QT>();
     const int g = group > 0 ? group : (K <= 8 ? 4 : K <= 16 ? 2 : 1);
     if (g == 4 && K <= 8) {
         const int c = chunks > 0 ? chunks : DEF;
-        if (c == 1) return run_batch<DT, VT, 4, 1>(d, n, total, counter, K, nbw, ctas, s);
-        if constexpr (VT % 2 == 0)
-            if (c == 2) return run_batch<DT, VT, 4, 2>(d, n, total, counter, K, nbw, ctas, s);
-        if constexpr (VT % 4 == 0)
-            if (c == 4) return run_batch<DT, VT, 4, 4>(d, n, total, counter, K, nbw, ctas, s);
-        return cudaErrorInvalidValue;
+        if constexpr (QT <= 4)
+            if (c == 1) return run_batch<DT, QT, 4, 1>(d, n, total, counter, K, nbw, ctas, s);
+        if constexpr (QT % 2 == 0 && QT <= 8)
+            if (c == 2) return run_batch<DT, QT, 4, 2>(d, n, total, counter, K, nbw, ctas, s);
+        if constexpr (QT % 4 == 0 && QT <= 16)
+            if (c == 4) return run_batch<DT, QT, 4, 4>(d, n, total, counter, K, nbw, ctas, s);
+        if (chunks > 0) return cudaErrorInvalidValue;
+        return run_batch<DT, QT, 4, DEF>(d, n, total, counter, K, nbw, ctas, s);
     }
-    if (g >= 2 && K <= 16) return run_batch<DT, VT, 2, DEF>(d, n, total, counter, K, nbw, ctas, s);
-    return run_batch<DT, VT, 1, DEF>(d, n, total, counter, K, nbw, ctas, s);
+    if (g >= 2 && K <= 16) return run_batch<DT, QT, 2, DEF>(d, n, total, counter, K, nbw, ctas, s);
+    return run_batch<DT, QT, 1, DEF>(d, n, total, counter, K, nbw, ctas, s);
 }
 
 }  // namespace
@@ -430,6 +432,11 @@ bool batch_supported(qr_dtype dt, int C) {
     if (C <= 0 || C % cpv) return false;
     const int rowv = C / cpv;
     return rowv == 32 || rowv == 64 || rowv == 128;
+}
+
+bool batch_chunks_ok(int C, int chunks) {
+    const int qt = C / 128;
+    return chunks == 0 || (qt % chunks == 0 && qt / chunks <= 4);
 }
 
 size_t batch_desc_bytes(int n_views) { return (size_t(n_views) * sizeof(BatchView) + 255) / 256 * 256 + 256; }
@@ -443,20 +450,22 @@ cudaError_t launch_batch(const void *ws, int n_views, uint32_t total_items, qr_d
                                                      batch_desc_bytes(n_views) - 256);
     cudaError_t e = cudaMemsetAsync(counter, 0, 4, s);
     if (e != cudaSuccess) return e;
-    const int vt = C / (dt == QR_F32 ? 4 : dt == QR_BF16 ? 8 : 16) / 32;
+    const int qt = C / 128;   // quads per lane over the whole row
+    auto by_qt = [&](auto dtc) -> cudaError_t {
+        constexpr int DT = decltype(dtc)::value;
+        switch (qt) {
+            case 1: return pick<DT, 1>(d, n_views, total_items, counter, K, group, chunks, nbw, ctas_per_sm, s);
+            case 2: return pick<DT, 2>(d, n_views, total_items, counter, K, group, chunks, nbw, ctas_per_sm, s);
+            case 4: return pick<DT, 4>(d, n_views, total_items, counter, K, group, chunks, nbw, ctas_per_sm, s);
+            case 8: return pick<DT, 8>(d, n_views, total_items, counter, K, group, chunks, nbw, ctas_per_sm, s);
+            case 16: return pick<DT, 16>(d, n_views, total_items, counter, K, group, chunks, nbw, ctas_per_sm, s);
+        }
+        return cudaErrorInvalidValue;
+    };
     switch (dt) {
-        case QR_F32:
-            if (vt == 4) return pick<QR_F32, 4>(d, n_views, total_items, counter, K, group, chunks, nbw, ctas_per_sm, s);
-            if (vt == 2) return pick<QR_F32, 2>(d, n_views, total_items, counter, K, group, chunks, nbw, ctas_per_sm, s);
-            return pick<QR_F32, 1>(d, n_views, total_items, counter, K, group, chunks, nbw, ctas_per_sm, s);
-        case QR_BF16:
-            if (vt == 4) return pick<QR_BF16, 4>(d, n_views, total_items, counter, K, group, chunks, nbw, ctas_per_sm, s);
-            if (vt == 2) return pick<QR_BF16, 2>(d, n_views, total_items, counter, K, group, chunks, nbw, ctas_per_sm, s);
-            return pick<QR_BF16, 1>(d, n_views, total_items, counter, K, group, chunks, nbw, ctas_per_sm, s);
-        case QR_FP8E4M3:
-            if (vt == 4) return pick<QR_FP8E4M3, 4>(d, n_views, total_items, counter, K, group, chunks, nbw, ctas_per_sm, s);
-            if (vt == 2) return pick<QR_FP8E4M3, 2>(d, n_views, total_items, counter, K, group, chunks, nbw, ctas_per_sm, s);
-            return pick<QR_FP8E4M3, 1>(d, n_views, total_items, counter, K, group, chunks, nbw, ctas_per_sm, s);
+        case QR_F32: return by_qt(std::integral_constant<int, QR_F32>());
+        case QR_BF16: return by_qt(std::integral_constant<int, QR_BF16>());
+        case QR_FP8E4M3: return by_qt(std::integral_constant<int, QR_FP8E4M3>());
     }
     return cudaErrorInvalidValue;
 }

@@ -25,6 +25,7 @@
 #include <cuda_fp8.h>
 
 #include "qr_internal.cuh"
+#include "quad.cuh"
 
 namespace qr {
 namespace {
@@ -232,26 +233,26 @@ __device__ __forceinline__ int64_t group_pixel(int64_t chunk0, int gi, int m, in
 // that lists an id twice gets the sum), so the row loop reads them with one
 // broadcast load instead of a chain of shuffles.
 //
-// Latency hiding: a work item is (pixel group, channel chunk); NCH > 1 splits
-// each row into NCH chunks of 32 VPL vectors taken by different warps (fewer
-// accumulators per thread, more warps per SM).  The next item's counts, ids
-// and weights are loaded (three independent loads) before the current item's
-// rows, U = max(2, 8 / VPL) rows are in flight per step, and FP8 rows load
-// their per-Gaussian scale beside the row and apply it to the row's weights,
-// so no load waits on another's result.  An FP8 row's weight for a pixel is
-// (the pixel's weight for it) * scale, rounded once: a selection lists a
-// Gaussian at most once per pixel.
-template <int DT, int VPL, int G, int NCH>
+// Rows are handled in quads (above): QPL quads per lane per channel chunk, NCH
+// chunks per row (a work item is a (pixel group, chunk) pair; NCH > 1 means
+// fewer accumulators per thread and more warps per item).  The next item's
+// counts, ids and weights are loaded (three independent loads) before the
+// current item's rows, U rows are in flight per step (64-128 bytes per lane),
+// and FP8 rows load their per-Gaussian scale beside the row and apply it to
+// the row's weights, so no load waits on another's result.  An FP8 row's
+// weight for a pixel is (the pixel's weight for it) * scale, rounded once: a
+// selection lists a Gaussian at most once per pixel.
+template <int DT, int QPL, int G, int NCH>
 __global__ void __launch_bounds__(kThreads)
-blend_group_kernel(const uint4 *__restrict__ feat, const float *__restrict__ scale,
+blend_group_kernel(const unsigned char *__restrict__ feat, const float *__restrict__ scale,
                    int64_t n_gauss, const int32_t *__restrict__ ids,
                    const float *__restrict__ wts, const uint8_t *__restrict__ cnt, int64_t P,
                    int K, int W, int H, float4 *__restrict__ out) {
     pdl_wait();   // the predecessor's outputs are complete and visible
-    constexpr int CPV = Vec<DT>::C;
-    constexpr int CV = 32 * VPL;             // vectors of a chunk
-    constexpr int ROWV = CV * NCH;           // vectors of a row
-    constexpr int U = VPL >= 4 ? 2 : 8 / VPL;
+    constexpr int QB = Quad<DT>::B;
+    constexpr int CQ = 32 * QPL;             // quads of a chunk
+    constexpr int ROWQ = CQ * NCH;           // quads of a row (C / 4)
+    constexpr int U = (QPL * QB >= 64) ? 2 : (QPL * QB >= 32 ? 128 / (QPL * QB) : 4);
     constexpr unsigned FULL = 0xffffffffu;
     constexpr int NW = kThreads / 32;
     constexpr int NITEMS = (256 / G) * NCH;
@@ -298,25 +299,25 @@ blend_group_kernel(const uint4 *__restrict__ feat, const float *__restrict__ sca
             if (lane == leader) s_id[warp][slot] = id;
         }
         __syncwarp();
-        float acc[G][VPL][CPV];
+        float acc[G][QPL][4];
 #pragma unroll
         for (int g = 0; g < G; ++g)
 #pragma unroll
-            for (int v = 0; v < VPL; ++v)
+            for (int v = 0; v < QPL; ++v)
 #pragma unroll
-                for (int q = 0; q < CPV; ++q) acc[g][v][q] = 0.f;
-        const uint4 *fch = feat + ch * CV + lane;
+                for (int q = 0; q < 4; ++q) acc[g][v][q] = 0.f;
+        const unsigned char *fch = feat + size_t(ch * CQ + lane) * QB;
         for (int r0 = 0; r0 < nrows; r0 += U) {
-            uint4 r[U][VPL];
+            typename Quad<DT>::T r[U][QPL];
             float sc[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 const bool ok = r0 + u < nrows;
                 const int rid = ok ? s_id[warp][r0 + u] : 0;
-                const uint4 *row = fch + int64_t(rid) * ROWV;
+                const unsigned char *row = fch + size_t(rid) * (size_t(ROWQ) * QB);
 #pragma unroll
-                for (int v = 0; v < VPL; ++v)
-                    r[u][v] = ok ? ld_row(row + 32 * v) : make_uint4(0, 0, 0, 0);
+                for (int v = 0; v < QPL; ++v)
+                    r[u][v] = ok ? ld_quad<DT>(row + size_t(32 * v) * QB) : zero_quad<DT>();
                 if (DT == QR_FP8E4M3) sc[u] = ok ? scale[rid] : 0.f;
             }
 #pragma unroll
@@ -326,14 +327,14 @@ blend_group_kernel(const uint4 *__restrict__ feat, const float *__restrict__ sca
 #pragma unroll
                 for (int g = 0; g < G; ++g)
                     wg[g] = DT == QR_FP8E4M3 ? s_w[warp][r0 + u][g] * sc[u] : s_w[warp][r0 + u][g];
-                float fv[VPL][CPV];
+                float fv[QPL][4];
 #pragma unroll
-                for (int v = 0; v < VPL; ++v) decode_vec<DT>(r[u][v], fv[v]);
+                for (int v = 0; v < QPL; ++v) dec_quad<DT>(r[u][v], fv[v]);
 #pragma unroll
                 for (int g = 0; g < G; ++g)
                     if (wg[g] != 0.f) {
 #pragma unroll
-                        for (int v = 0; v < VPL; ++v) fma_vec<CPV>(fv[v], wg[g], acc[g][v]);
+                        for (int v = 0; v < QPL; ++v) fma_vec<4>(fv[v], wg[g], acc[g][v]);
                     }
             }
         }
@@ -341,69 +342,63 @@ blend_group_kernel(const uint4 *__restrict__ feat, const float *__restrict__ sca
         for (int g = 0; g < G; ++g) {
             const int64_t pg = __shfl_sync(FULL, pc, g * K < 32 ? g * K : 0);
             if (pg >= 0) {
-                float4 *o = out + pg * (int64_t(ROWV) * CPV / 4) + ch * (CV * CPV / 4);
+                float4 *o = out + pg * int64_t(ROWQ) + ch * CQ + lane;
 #pragma unroll
-                for (int v = 0; v < VPL; ++v)
-#pragma unroll
-                    for (int q = 0; q < CPV / 4; ++q)
-                        st_stream(o + int64_t(lane + 32 * v) * (CPV / 4) + q,
-                                  make_float4(acc[g][v][4 * q], acc[g][v][4 * q + 1],
-                                              acc[g][v][4 * q + 2], acc[g][v][4 * q + 3]));
+                for (int v = 0; v < QPL; ++v)
+                    st_stream(o + 32 * v, make_float4(acc[g][v][0], acc[g][v][1], acc[g][v][2],
+                                                      acc[g][v][3]));
             }
         }
         __syncwarp();   // the table is rewritten by the next item
     }
 }
 
-// Channel chunks a row is split into by default: a chunk keeps at most 16
-// accumulators per pixel (4 F32, 2 BF16 or 1 FP8 vector per lane).
-template <int DT, int VT>
+// Channel chunks a row of QT quads per lane is split into by default: the
+// fewest that keep at most 4 quads (16 accumulators per pixel) per lane.
+template <int QT>
 constexpr int default_chunks() {
-    constexpr int lim = DT == QR_F32 ? 4 : DT == QR_BF16 ? 2 : 1;
-    return VT <= lim ? 1 : (VT % lim == 0 ? VT / lim : VT);
+    return QT <= 4 ? 1 : QT % 4 == 0 ? QT / 4 : QT % 3 == 0 ? QT / 3 : QT / 2;
 }
 
 int g_blend_chunks = 0;   // qr_set_blend_chunks: 0 = default_chunks
 
-template <int DT, int VT, int G, int NCH>
+template <int DT, int QT, int G, int NCH>
 cudaError_t go_group(const void *feat, const float *scale, int64_t n_gauss, const int32_t *ids,
                      const float *w, const uint8_t *cnt, int64_t P, int K, int W, int H,
                      float *out, cudaStream_t s) {
     const int64_t items = (W > 0) ? int64_t((W + 15) >> 4) * ((H + 15) >> 4) * 256 : P;
     const unsigned blocks = unsigned((items + 255) / 256);
-    return pdl_launch(blend_group_kernel<DT, VT / NCH, G, NCH>, dim3(blocks), dim3(kThreads), 0, s,
-                      static_cast<const uint4 *>(feat), scale, n_gauss, ids, w, cnt, P, K, W, H,
-                      reinterpret_cast<float4 *>(out));
+    return pdl_launch(blend_group_kernel<DT, QT / NCH, G, NCH>, dim3(blocks), dim3(kThreads), 0, s,
+                      static_cast<const unsigned char *>(feat), scale, n_gauss, ids, w, cnt, P, K,
+                      W, H, reinterpret_cast<float4 *>(out));
 }
 
-// VT 16-byte vectors per lane over the whole row.  With K <= 8 (pixel groups
-// of 4) and rows of 2 or 4 vectors per lane the chunk count can be chosen
-// (qr_set_blend_chunks); the results are the same for every choice.
-template <int DT, int VT>
+// QT = C / 128 quads per lane over the whole row (e.g. 4 for 512-D rows of
+// any dtype).  With K <= 8 (pixel groups of 4) and QT = 4 the chunk count can
+// be chosen (qr_set_blend_chunks: 1, 2 or 4); the results are the same for
+// every choice.
+template <int DT, int QT>
 cudaError_t run_group(const void *feat, const float *scale, int64_t n_gauss, const int32_t *ids,
                       const float *w, const uint8_t *cnt, int64_t P, int K, int W, int H,
                       float *out, cudaStream_t s) {
-    constexpr int DEF = default_chunks<DT, VT>();
+    constexpr int DEF = default_chunks<QT>();
     cudaError_t e;
     if (K <= 8) {
         const int want = g_blend_chunks > 0 ? g_blend_chunks : DEF;
-        if constexpr (VT == 2 || VT == 4) {
-            if (want == 1 && DEF != 1)
-                e = go_group<DT, VT, 4, 1>(feat, scale, n_gauss, ids, w, cnt, P, K, W, H, out, s);
-            else if (want == 2 && DEF != 2)
-                e = go_group<DT, VT, 4, 2>(feat, scale, n_gauss, ids, w, cnt, P, K, W, H, out, s);
-            else if (VT == 4 && want == 4 && DEF != 4)
-                e = go_group<DT, VT, 4, (VT == 4 ? 4 : 1)>(feat, scale, n_gauss, ids, w, cnt, P, K, W,
-                                                           H, out, s);
+        if constexpr (QT == 4) {
+            if (want == 2)
+                e = go_group<DT, QT, 4, 2>(feat, scale, n_gauss, ids, w, cnt, P, K, W, H, out, s);
+            else if (want == 4)
+                e = go_group<DT, QT, 4, 4>(feat, scale, n_gauss, ids, w, cnt, P, K, W, H, out, s);
             else
-                e = go_group<DT, VT, 4, DEF>(feat, scale, n_gauss, ids, w, cnt, P, K, W, H, out, s);
+                e = go_group<DT, QT, 4, 1>(feat, scale, n_gauss, ids, w, cnt, P, K, W, H, out, s);
         } else {
-            e = go_group<DT, VT, 4, DEF>(feat, scale, n_gauss, ids, w, cnt, P, K, W, H, out, s);
+            e = go_group<DT, QT, 4, DEF>(feat, scale, n_gauss, ids, w, cnt, P, K, W, H, out, s);
         }
     } else if (K <= 16) {
-        e = go_group<DT, VT, 2, DEF>(feat, scale, n_gauss, ids, w, cnt, P, K, W, H, out, s);
+        e = go_group<DT, QT, 2, DEF>(feat, scale, n_gauss, ids, w, cnt, P, K, W, H, out, s);
     } else {
-        e = go_group<DT, VT, 1, DEF>(feat, scale, n_gauss, ids, w, cnt, P, K, W, H, out, s);
+        e = go_group<DT, QT, 1, DEF>(feat, scale, n_gauss, ids, w, cnt, P, K, W, H, out, s);
     }
     count_launch();
     return e != cudaSuccess ? e : cudaGetLastError();
@@ -427,16 +422,18 @@ cudaError_t dispatch(const void *feat, const float *scale, int64_t n_gauss, int 
                      const int32_t *ids, const float *w, const uint8_t *cnt, int64_t P, int K,
                      int W, int H, float *out, cudaStream_t s) {
     const int rowv = C / Vec<DT>::C;  // 16-byte vectors per row
+    constexpr int CPV4 = Vec<DT>::C / 4;  // quads per 16-byte vector
     switch (rowv) {
         case 1: return run<DT, 1, 1>(feat, scale, n_gauss, ids, w, cnt, P, K, W, H, out, s);
         case 2: return run<DT, 2, 1>(feat, scale, n_gauss, ids, w, cnt, P, K, W, H, out, s);
         case 4: return run<DT, 4, 1>(feat, scale, n_gauss, ids, w, cnt, P, K, W, H, out, s);
         case 8: return run<DT, 8, 1>(feat, scale, n_gauss, ids, w, cnt, P, K, W, H, out, s);
         case 16: return run<DT, 16, 1>(feat, scale, n_gauss, ids, w, cnt, P, K, W, H, out, s);
-        case 32: return run_group<DT, 1>(feat, scale, n_gauss, ids, w, cnt, P, K, W, H, out, s);
-        case 64: return run_group<DT, 2>(feat, scale, n_gauss, ids, w, cnt, P, K, W, H, out, s);
-        case 96: return run_group<DT, 3>(feat, scale, n_gauss, ids, w, cnt, P, K, W, H, out, s);
-        case 128: return run_group<DT, 4>(feat, scale, n_gauss, ids, w, cnt, P, K, W, H, out, s);
+        // wide rows: QT = C / 128 quads per lane
+        case 32: return run_group<DT, CPV4 * 1>(feat, scale, n_gauss, ids, w, cnt, P, K, W, H, out, s);
+        case 64: return run_group<DT, CPV4 * 2>(feat, scale, n_gauss, ids, w, cnt, P, K, W, H, out, s);
+        case 96: return run_group<DT, CPV4 * 3>(feat, scale, n_gauss, ids, w, cnt, P, K, W, H, out, s);
+        case 128: return run_group<DT, CPV4 * 4>(feat, scale, n_gauss, ids, w, cnt, P, K, W, H, out, s);
         case 256: return run<DT, 32, 8>(feat, scale, n_gauss, ids, w, cnt, P, K, W, H, out, s);
         default: return cudaErrorInvalidValue;
     }

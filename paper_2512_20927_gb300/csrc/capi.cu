@@ -543,8 +543,7 @@ qr_status qr_render_batch(const void *ws, int32_t n_views, uint32_t total_tiles,
     if (!batch_supported(dtype, C)) return QR_ERR_NOT_SUPPORTED;
     if (chunks != 0 && chunks != 1 && chunks != 2 && chunks != 4) return QR_ERR_INVALID_ARG;
     if (blend_warps != 0 && blend_warps != 4 && blend_warps != 8) return QR_ERR_INVALID_ARG;
-    if (chunks > 0 && (C / (dtype == QR_F32 ? 4 : dtype == QR_BF16 ? 8 : 16) / 32) % chunks != 0)
-        return QR_ERR_INVALID_ARG;
+    if (!batch_chunks_ok(C, chunks)) return QR_ERR_INVALID_ARG;
     if (total_tiles == 0) return QR_OK;
     return from_cuda(launch_batch(ws, n_views, total_tiles, dtype, C, K, group, chunks, blend_warps,
                                   ctas_per_sm, reinterpret_cast<cudaStream_t>(stream)));

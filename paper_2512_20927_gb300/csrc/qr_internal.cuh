@@ -148,6 +148,7 @@ __device__ __forceinline__ CosCoeffs cos_coeffs(float dot, float ff, float tt, f
 
 struct BatchView;
 bool batch_supported(qr_dtype dt, int C);
+bool batch_chunks_ok(int C, int chunks);
 size_t batch_desc_bytes(int n_views);
 size_t batch_view_size();
 cudaError_t launch_batch(const void *ws, int n_views, uint32_t total_items, qr_dtype dt, int C,

@@ -137,8 +137,8 @@ def test_batch_chunks_and_blend_warps_bit_identical(dtype, channels):
     b0.step()
     torch.cuda.synchronize()
     ref = [b0.view_slice(i) for i in range(len(views))]
-    vt = channels // (4 if dtype == "f32" else 8) // 32
-    settings = [(c, w) for c in (1, 2, 4) for w in (0, 4) if vt % c == 0] + [(0, 4)]
+    qt = channels // 128   # quads (4 channels) per lane over a row
+    settings = [(c, w) for c in (1, 2, 4) for w in (0, 4) if qt % c == 0 and qt // c <= 4] + [(0, 4)]
     for chunks, bw in settings:
         b = Batch(b0.scenes, views, K=8, chunks=chunks, blend_warps=bw)
         b.step()

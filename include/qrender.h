@@ -514,16 +514,6 @@ void qr_set_wait_limit(uint32_t polls);
  * QR_ERR_INVALID_ARG for other values.  Not thread-safe. */
 qr_status qr_set_blend_chunks(int32_t chunks);
 
-/* Tuning: with one channel chunk (above), the 512-D blend with K <= 8 can
- * stage feature rows through a per-lane ring in shared memory filled by
- * asynchronous copies (bytes_per_lane = 256 or 512 bytes of rows in flight
- * per lane; 0 restores register staging, the default).  Each lane copies and
- * reads back only its own channels, so no cross-thread synchronisation is
- * involved.  Results are bit-identical for every setting.  Applies to
- * qr_blend and qr_render launched afterwards; QR_ERR_INVALID_ARG for other
- * values.  Not thread-safe. */
-qr_status qr_set_blend_ring(int32_t bytes_per_lane);
-
 #ifdef __cplusplus
 }
 #endif

@@ -242,7 +242,7 @@ __device__ __forceinline__ int64_t group_pixel(int64_t chunk0, int gi, int m, in
 // the row's weights, so no load waits on another's result.  An FP8 row's
 // weight for a pixel is (the pixel's weight for it) * scale, rounded once: a
 // selection lists a Gaussian at most once per pixel.
-template <int DT, int QPL, int G, int NCH, int RING>
+template <int DT, int QPL, int G, int NCH>
 __global__ void __launch_bounds__(kThreads)
 blend_group_kernel(const unsigned char *__restrict__ feat, const float *__restrict__ scale,
                    int64_t n_gauss, const int32_t *__restrict__ ids,
@@ -258,7 +258,6 @@ blend_group_kernel(const unsigned char *__restrict__ feat, const float *__restri
     constexpr int NITEMS = (256 / G) * NCH;
     __shared__ __align__(16) float s_w[NW][32][G];
     __shared__ int s_id[NW][32];
-    extern __shared__ __align__(16) unsigned char s_ring[];   // RING > 0: per-lane row rings
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t items = (W > 0) ? int64_t((W + 15) >> 4) * ((H + 15) >> 4) * 256 : P;
     const int64_t chunk0 = int64_t(blockIdx.x) * 256;
@@ -308,72 +307,29 @@ blend_group_kernel(const unsigned char *__restrict__ feat, const float *__restri
 #pragma unroll
                 for (int q = 0; q < 4; ++q) acc[g][v][q] = 0.f;
         const unsigned char *fch = feat + size_t(ch * CQ + lane) * QB;
-        if constexpr (RING == 0) {
-            for (int r0 = 0; r0 < nrows; r0 += U) {
-                typename Quad<DT>::T r[U][QPL];
-                float sc[U];
+        for (int r0 = 0; r0 < nrows; r0 += U) {
+            typename Quad<DT>::T r[U][QPL];
+            float sc[U];
 #pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const bool ok = r0 + u < nrows;
-                    const int rid = ok ? s_id[warp][r0 + u] : 0;
-                    const unsigned char *row = fch + size_t(rid) * (size_t(ROWQ) * QB);
-#pragma unroll
-                    for (int v = 0; v < QPL; ++v)
-                        r[u][v] = ok ? ld_quad<DT>(row + size_t(32 * v) * QB) : zero_quad<DT>();
-                    if (DT == QR_FP8E4M3) sc[u] = ok ? scale[rid] : 0.f;
-                }
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    if (r0 + u >= nrows) break;
-                    float wg[G];
-#pragma unroll
-                    for (int g = 0; g < G; ++g)
-                        wg[g] = DT == QR_FP8E4M3 ? s_w[warp][r0 + u][g] * sc[u] : s_w[warp][r0 + u][g];
-                    float fv[QPL][4];
-#pragma unroll
-                    for (int v = 0; v < QPL; ++v) dec_quad<DT>(r[u][v], fv[v]);
-#pragma unroll
-                    for (int g = 0; g < G; ++g)
-                        if (wg[g] != 0.f) {
-#pragma unroll
-                            for (int v = 0; v < QPL; ++v) fma_vec<4>(fv[v], wg[g], acc[g][v]);
-                        }
-                }
-            }
-        } else {
-            // rows staged through this lane's ring of RING slots in shared
-            // memory by cp.async (each lane copies and later reads only its
-            // own quads, so a wait_group is the only synchronisation): RING
-            // rows in flight without holding them in registers
-            unsigned char *ring = s_ring + (size_t(warp) * 32 + lane) * (RING * QPL * QB + 4 * RING);
-            const uint32_t ring_s = uint32_t(__cvta_generic_to_shared(ring));
-            for (int r = 0; r < nrows + RING - 1; ++r) {
-                if (r < nrows) {
-                    const int rid = s_id[warp][r];
-                    const unsigned char *row = fch + size_t(rid) * (size_t(ROWQ) * QB);
-                    const uint32_t slot = ring_s + uint32_t((r % RING) * QPL * QB);
-#pragma unroll
-                    for (int v = 0; v < QPL; ++v)
-                        cp_async<QB>(slot + uint32_t(v * QB), row + size_t(32 * v) * QB);
-                    if (DT == QR_FP8E4M3)
-                        cp_async<4>(ring_s + uint32_t(RING * QPL * QB + 4 * (r % RING)), scale + rid);
-                }
-                cp_async_commit();
-                const int rr = r - (RING - 1);
-                if (rr < 0) continue;
-                cp_async_wait<RING - 1>();   // row rr (an older group) has landed
-                const unsigned char *slot = ring + (rr % RING) * QPL * QB;
-                float wg[G];
-                const float sc = DT == QR_FP8E4M3
-                                     ? *reinterpret_cast<const float *>(ring + RING * QPL * QB + 4 * (rr % RING))
-                                     : 1.f;
-#pragma unroll
-                for (int g = 0; g < G; ++g)
-                    wg[g] = DT == QR_FP8E4M3 ? s_w[warp][rr][g] * sc : s_w[warp][rr][g];
-                float fv[QPL][4];
+            for (int u = 0; u < U; ++u) {
+                const bool ok = r0 + u < nrows;
+                const int rid = ok ? s_id[warp][r0 + u] : 0;
+                const unsigned char *row = fch + size_t(rid) * (size_t(ROWQ) * QB);
 #pragma unroll
                 for (int v = 0; v < QPL; ++v)
-                    dec_quad<DT>(*reinterpret_cast<const typename Quad<DT>::T *>(slot + v * QB), fv[v]);
+                    r[u][v] = ok ? ld_quad<DT>(row + size_t(32 * v) * QB) : zero_quad<DT>();
+                if (DT == QR_FP8E4M3) sc[u] = ok ? scale[rid] : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (r0 + u >= nrows) break;
+                float wg[G];
+#pragma unroll
+                for (int g = 0; g < G; ++g)
+                    wg[g] = DT == QR_FP8E4M3 ? s_w[warp][r0 + u][g] * sc[u] : s_w[warp][r0 + u][g];
+                float fv[QPL][4];
+#pragma unroll
+                for (int v = 0; v < QPL; ++v) dec_quad<DT>(r[u][v], fv[v]);
 #pragma unroll
                 for (int g = 0; g < G; ++g)
                     if (wg[g] != 0.f) {
@@ -405,22 +361,14 @@ constexpr int default_chunks() {
 }
 
 int g_blend_chunks = 0;   // qr_set_blend_chunks: 0 = default_chunks
-int g_blend_ring = 0;     // qr_set_blend_ring: bytes of row ring per lane (0 = registers)
 
-template <int DT, int QT, int G, int NCH, int RING = 0>
+template <int DT, int QT, int G, int NCH>
 cudaError_t go_group(const void *feat, const float *scale, int64_t n_gauss, const int32_t *ids,
                      const float *w, const uint8_t *cnt, int64_t P, int K, int W, int H,
                      float *out, cudaStream_t s) {
     const int64_t items = (W > 0) ? int64_t((W + 15) >> 4) * ((H + 15) >> 4) * 256 : P;
     const unsigned blocks = unsigned((items + 255) / 256);
-    constexpr int QPL = QT / NCH;
-    auto kern = blend_group_kernel<DT, QPL, G, NCH, RING>;
-    const size_t dyn = RING > 0 ? size_t(kThreads) * (RING * QPL * Quad<DT>::B + 4 * RING) : 0;
-    if (dyn > 0) {
-        const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(dyn));
-        if (e != cudaSuccess) return e;
-    }
-    return pdl_launch(kern, dim3(blocks), dim3(kThreads), dyn, s,
+    return pdl_launch(blend_group_kernel<DT, QT / NCH, G, NCH>, dim3(blocks), dim3(kThreads), 0, s,
                       static_cast<const unsigned char *>(feat), scale, n_gauss, ids, w, cnt, P, K,
                       W, H, reinterpret_cast<float4 *>(out));
 }
@@ -437,13 +385,8 @@ cudaError_t run_group(const void *feat, const float *scale, int64_t n_gauss, con
     cudaError_t e;
     if (K <= 8) {
         const int want = g_blend_chunks > 0 ? g_blend_chunks : DEF;
-        constexpr int QB = Quad<DT>::B;
         if constexpr (QT == 4) {
-            if (want == 1 && g_blend_ring == 256)
-                e = go_group<DT, QT, 4, 1, 256 / (4 * QB)>(feat, scale, n_gauss, ids, w, cnt, P, K, W, H, out, s);
-            else if (want == 1 && g_blend_ring == 512)
-                e = go_group<DT, QT, 4, 1, 512 / (4 * QB)>(feat, scale, n_gauss, ids, w, cnt, P, K, W, H, out, s);
-            else if (want == 2)
+            if (want == 2)
                 e = go_group<DT, QT, 4, 2>(feat, scale, n_gauss, ids, w, cnt, P, K, W, H, out, s);
             else if (want == 4)
                 e = go_group<DT, QT, 4, 4>(feat, scale, n_gauss, ids, w, cnt, P, K, W, H, out, s);
@@ -497,12 +440,6 @@ cudaError_t dispatch(const void *feat, const float *scale, int64_t n_gauss, int 
 }
 
 }  // namespace
-
-bool set_blend_ring(int bytes) {
-    if (bytes != 0 && bytes != 256 && bytes != 512) return false;
-    g_blend_ring = bytes;
-    return true;
-}
 
 bool set_blend_chunks(int chunks) {
     if (chunks != 0 && chunks != 1 && chunks != 2 && chunks != 4) return false;

@@ -557,8 +557,4 @@ qr_status qr_set_blend_chunks(int32_t chunks) {
     return set_blend_chunks(chunks) ? QR_OK : QR_ERR_INVALID_ARG;
 }
 
-qr_status qr_set_blend_ring(int32_t bytes_per_lane) {
-    return set_blend_ring(bytes_per_lane) ? QR_OK : QR_ERR_INVALID_ARG;
-}
-
 }  // extern "C"

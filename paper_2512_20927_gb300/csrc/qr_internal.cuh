@@ -166,7 +166,6 @@ cudaError_t launch_contrastive_loss(const float *F, const float *tgt, int M, int
 bool relevance_supported(int Q, int C);
 void set_wait_limit(unsigned polls);
 bool set_blend_chunks(int chunks);
-bool set_blend_ring(int bytes);
 // blend of qr_blend fused with the relevance product (the map is never written)
 bool blend_relevance_supported(qr_dtype dt, int Q, int C, int K);
 cudaError_t launch_blend_relevance(const void *feat, const float *scale, qr_dtype dt, int C,

@@ -60,16 +60,4 @@ __device__ __forceinline__ void dec_quad(const typename Quad<DT>::T v, float *o)
     }
 }
 
-// Asynchronous copy of N (4, 8 or 16) bytes from global to shared memory
-// through L1 (cp.async.ca); completion is per thread, by commit and wait
-// groups (no polling).
-template <int N>
-__device__ __forceinline__ void cp_async(uint32_t smem_dst, const void *gsrc) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_dst), "l"(gsrc), "n"(N)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-
 }  // namespace qr

@@ -99,7 +99,6 @@ SIGNATURES = {
     "qr_launch_count": (ctypes.c_uint64, []),
     "qr_set_wait_limit": (None, [ctypes.c_uint32]),
     "qr_set_blend_chunks": (_S, [_I32]),
-    "qr_set_blend_ring": (_S, [_I32]),
     "qr_backward_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(qr_frame), _I32]),
     "qr_backward": (_S, [ctypes.POINTER(qr_frame), _P, _P, _S, _I32, _P, _P, _P, _P, _P, _P, _P,
                          _P, ctypes.c_size_t, _P]),
@@ -548,11 +547,6 @@ def qr_set_wait_limit(polls: int):
 def qr_set_blend_chunks(chunks: int):
     """Tuning: channel chunks per feature row in the wide-row blend (0 = built-in)."""
     _check(load().qr_set_blend_chunks(int(chunks)), "qr_set_blend_chunks")
-
-
-def qr_set_blend_ring(bytes_per_lane: int):
-    """Tuning: per-lane shared-memory row ring of the 512-D blend (0 = register staging)."""
-    _check(load().qr_set_blend_ring(int(bytes_per_lane)), "qr_set_blend_ring")
 
 
 # ---------------------------------------------------------------- convenience

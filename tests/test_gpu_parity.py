@@ -420,10 +420,9 @@ def test_dense_subtile_kernel(C, kind, tile):
 @pytest.mark.parametrize("dtype,C", [("f32", 512), ("bf16", 512), ("bf16", 1024), ("fp8", 1024),
                                      ("fp8", 512)])
 def test_blend_channel_chunks_bit_identical(dtype, C):
-    """Splitting the rows into channel chunks across warps, or staging them
-    through a shared-memory ring, changes neither the terms nor their order
-    per channel: every setting gives the same bits, in both pixel orders, with
-    ragged P and counts (0 .. K)."""
+    """Splitting the rows into channel chunks across warps changes neither the
+    terms nor their order per channel: every chunk count gives the same bits,
+    in both pixel orders, with ragged P and counts (0 .. K)."""
     import torch
     from paper_2512_20927_gb300 import qrender as q
     rng = np.random.default_rng(C + len(dtype))
@@ -441,9 +440,8 @@ def test_blend_channel_chunks_bit_identical(dtype, C):
     try:
         for width in (0, W):
             outs = []
-            for chunks, ring in ((0, 0), (1, 0), (2, 0), (4, 0), (0, 256), (0, 512), (2, 512)):
+            for chunks in (0, 1, 2, 4):
                 q.qr_set_blend_chunks(chunks)
-                q.qr_set_blend_ring(ring)
                 o = torch.full((P, C), float("nan"), dtype=torch.float32, device="cuda")
                 q.qr_blend(table, sc, ids, w, cnt, o, width=width)
                 outs.append(o)
@@ -453,8 +451,5 @@ def test_blend_channel_chunks_bit_identical(dtype, C):
             assert not torch.isnan(outs[0]).any()
     finally:
         q.qr_set_blend_chunks(0)
-        q.qr_set_blend_ring(0)
     with pytest.raises(q.QRError):
         q.qr_set_blend_chunks(3)
-    with pytest.raises(q.QRError):
-        q.qr_set_blend_ring(100)

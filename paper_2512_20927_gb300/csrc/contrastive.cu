@@ -227,6 +227,250 @@ eq2_terms(const float *__restrict__ F, const float *__restrict__ tn, int M, int 
     }
 }
 
+// ------------------------------------------------------------------ tensor cores
+// The two contractions on the tensor cores (mma.sync m16n8k8, TF32 operands,
+// FP32 accumulation), each FP32 operand split as x = hi + lo with hi, lo
+// TF32 (round to nearest) and three products lo*hi + hi*lo + hi*hi per step:
+// the dropped lo*lo term and the rounding of lo leave about 2^-22 of |x||y|
+// per product, FP32-class accuracy.
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ void split_tf32(float x, uint32_t &hi, uint32_t &lo) {
+    hi = to_tf32(x);
+    lo = to_tf32(x - __uint_as_float(hi));
+}
+__device__ __forceinline__ void mma_tf32(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2,
+                                         uint32_t a3, uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+// d += A B with A = ah + al, B = bh + bl (the small products first)
+__device__ __forceinline__ void mma3(float (&d)[4], const uint32_t (&ah)[4], const uint32_t (&al)[4],
+                                     uint32_t bh0, uint32_t bh1, uint32_t bl0, uint32_t bl1) {
+    mma_tf32(d, al[0], al[1], al[2], al[3], bh0, bh1);
+    mma_tf32(d, ah[0], ah[1], ah[2], ah[3], bl0, bl1);
+    mma_tf32(d, ah[0], ah[1], ah[2], ah[3], bh0, bh1);
+}
+
+// eq2_mma: M <= 16 MT targets.  One CTA per SM holds the unit targets split
+// into TF32 hi / lo parts in shared memory ([16 MT][C + 16] each; the row pad
+// makes the fragment loads conflict-free); each warp takes 64 pixels at a
+// time (eight 8-pixel n-tiles; g = lane / 4, t = lane % 4):
+//   1. S^T = T^ F^T (M = targets, N = pixels, K = channels): per 16
+//      channels a lane loads one float4 of each of its eight pixel rows (the
+//      K order inside the 16 is permuted so that A and B fragments are float4
+//      loads; the sums are the same) and accumulates |F|^2;
+//   2. per pixel, from the accumulator layout (lane (g, t) holds targets g,
+//      g + 8 of each 16 for pixels 2t, 2t + 1 of each n-tile): s_j, the
+//      softmax over the other masks, the loss term and c_j, with reductions
+//      over the eight lanes that share t;
+//   3. G = C T^ (M = pixels, N = channels, K = targets): the c_j fragments
+//      are gathered by shuffles, T^ fragments read from shared memory, and
+//      each 16 x 8 result, (G / nf - (sum_j c_j s_j) F / nf^2) / n, is
+//      written with the F values it needs re-read (they were read moments
+//      before and come from L2).
+template <int MT>
+__global__ void __launch_bounds__(kThreads, 1)
+eq2_mma(const float *__restrict__ F, const float *__restrict__ tn, int M, int C,
+        const int32_t *__restrict__ mask_id, int64_t P, float eps, float *__restrict__ term,
+        float *__restrict__ grad, const float *__restrict__ out2) {
+    constexpr unsigned FULL = 0xffffffffu;
+    constexpr int NW = kThreads / 32;
+    constexpr int NT = 8;                  // 8-pixel n-tiles per warp
+    constexpr int NPX = 8 * NT;            // pixels per warp block
+    constexpr int MR = 16 * MT;            // target rows held
+    extern __shared__ __align__(16) float s_t[];
+    const int S = C + 16;
+    float *s_hi = s_t, *s_lo = s_t + MR * S;
+    __shared__ float s_a1[NW][NPX], s_a2[NW][NPX];
+    for (int i = threadIdx.x; i < MR * C; i += kThreads) {
+        const int j = i / C, c = i - j * C;
+        const float x = j < M ? tn[int64_t(j) * C + c] : 0.f;
+        uint32_t h, l;
+        split_tf32(x, h, l);
+        s_hi[j * S + c] = __uint_as_float(h);
+        s_lo[j * S + c] = __uint_as_float(l);
+    }
+    __syncthreads();
+    const float inv_n = cos_inv_count(out2);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    const int64_t blocks = (P + NPX - 1) / NPX;
+    for (int64_t blk = int64_t(blockIdx.x) * NW + warp; blk < blocks; blk += int64_t(gridDim.x) * NW) {
+        const int64_t p0 = blk * NPX;
+        // ---------------- 1. similarities
+        float acc[MT][NT][4];
+        float ff[NT];
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) {
+            ff[nt] = 0.f;
+#pragma unroll
+            for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[mt][nt][q] = 0.f;
+        }
+        for (int cg = 0; cg < C; cg += 16) {
+            float4 fq[NT];
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt) {
+                const int64_t px = p0 + nt * 8 + g;
+                fq[nt] = px < P ? __ldg(reinterpret_cast<const float4 *>(F + px * C + cg + 4 * t))
+                                : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            // A fragments of every m-tile (rows g and g + 8, channels cg + 4t ..):
+            // k-step 0 takes .x (slot t) and .y (slot t + 4), k-step 1 .z and .w
+            uint32_t ah[MT][2][4], al[MT][2][4];
+#pragma unroll
+            for (int mt = 0; mt < MT; ++mt) {
+                const float4 h0 = *reinterpret_cast<const float4 *>(s_hi + (16 * mt + g) * S + cg + 4 * t);
+                const float4 h1 = *reinterpret_cast<const float4 *>(s_hi + (16 * mt + g + 8) * S + cg + 4 * t);
+                const float4 l0 = *reinterpret_cast<const float4 *>(s_lo + (16 * mt + g) * S + cg + 4 * t);
+                const float4 l1 = *reinterpret_cast<const float4 *>(s_lo + (16 * mt + g + 8) * S + cg + 4 * t);
+                ah[mt][0][0] = __float_as_uint(h0.x); ah[mt][0][1] = __float_as_uint(h1.x);
+                ah[mt][0][2] = __float_as_uint(h0.y); ah[mt][0][3] = __float_as_uint(h1.y);
+                ah[mt][1][0] = __float_as_uint(h0.z); ah[mt][1][1] = __float_as_uint(h1.z);
+                ah[mt][1][2] = __float_as_uint(h0.w); ah[mt][1][3] = __float_as_uint(h1.w);
+                al[mt][0][0] = __float_as_uint(l0.x); al[mt][0][1] = __float_as_uint(l1.x);
+                al[mt][0][2] = __float_as_uint(l0.y); al[mt][0][3] = __float_as_uint(l1.y);
+                al[mt][1][0] = __float_as_uint(l0.z); al[mt][1][1] = __float_as_uint(l1.z);
+                al[mt][1][2] = __float_as_uint(l0.w); al[mt][1][3] = __float_as_uint(l1.w);
+            }
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt) {
+                const float4 x = fq[nt];
+                ff[nt] = fmaf(x.x, x.x, fmaf(x.y, x.y, fmaf(x.z, x.z, fmaf(x.w, x.w, ff[nt]))));
+                uint32_t bh[4], bl[4];
+                split_tf32(x.x, bh[0], bl[0]);
+                split_tf32(x.y, bh[1], bl[1]);
+                split_tf32(x.z, bh[2], bl[2]);
+                split_tf32(x.w, bh[3], bl[3]);
+#pragma unroll
+                for (int mt = 0; mt < MT; ++mt) {
+                    mma3(acc[mt][nt], ah[mt][0], al[mt][0], bh[0], bh[1], bl[0], bl[1]);
+                    mma3(acc[mt][nt], ah[mt][1], al[mt][1], bh[2], bh[3], bl[2], bl[3]);
+                }
+            }
+        }
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) {
+            ff[nt] += __shfl_xor_sync(FULL, ff[nt], 1);
+            ff[nt] += __shfl_xor_sync(FULL, ff[nt], 2);
+        }
+        // ---------------- 2. softmax over the other masks, loss terms, c_j
+        // lane (g, t) holds, for pixel nt*8 + 2t + b, targets 16 mt + g + 8 h
+        // in acc[mt][nt][2 h + b]; the eight lanes sharing t hold all targets
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) {
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                const int pl = nt * 8 + 2 * t + b;
+                const int64_t px = p0 + pl;
+                const float nfr = sqrtf(__shfl_sync(FULL, ff[nt], (2 * t + b) * 4));
+                const float nf = fmaxf(nfr, eps);
+                const int i = px < P ? mask_id[px] : -1;
+                float e[MT][2], sv[MT][2];
+                float Z = 0.f, si = 0.f;
+#pragma unroll
+                for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int j = 16 * mt + g + 8 * h;
+                        sv[mt][h] = acc[mt][nt][2 * h + b] / nf;
+                        e[mt][h] = (j < M && j != i) ? expf(sv[mt][h]) : 0.f;
+                        Z += e[mt][h];
+                        if (j == i) si += sv[mt][h];
+                    }
+#pragma unroll
+                for (int o = 4; o < 32; o <<= 1) {
+                    Z += __shfl_xor_sync(FULL, Z, o);
+                    si += __shfl_xor_sync(FULL, si, o);
+                }
+                float cs = 0.f;
+#pragma unroll
+                for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int j = 16 * mt + g + 8 * h;
+                        const float c = j >= M ? 0.f : (j == i ? -1.f : e[mt][h] / Z);
+                        cs = fmaf(c, sv[mt][h], cs);
+                        acc[mt][nt][2 * h + b] = i >= 0 ? c * inv_n : 0.f;
+                    }
+#pragma unroll
+                for (int o = 4; o < 32; o <<= 1) cs += __shfl_xor_sync(FULL, cs, o);
+                if (g == 0) {
+                    if (px < P) term[px] = i >= 0 ? logf(Z) - si : 0.f;
+                    s_a1[warp][pl] = i >= 0 ? 1.0f / nf : 0.f;
+                    s_a2[warp][pl] = (i >= 0 && nfr > eps) ? cs * inv_n / (nf * nf) : 0.f;
+                }
+            }
+        }
+        __syncwarp();
+        // ---------------- 3. gradient rows, 16 pixels x 8 channels at a time
+#pragma unroll
+        for (int m2 = 0; m2 < NT / 2; ++m2) {
+            const int n0 = 2 * m2, n1 = 2 * m2 + 1;     // n-tiles of rows g and g + 8
+            uint32_t ch[2 * MT][4], cl[2 * MT][4];
+#pragma unroll
+            for (int kk = 0; kk < 2 * MT; ++kk) {
+                const int mt = kk >> 1, h = kk & 1;
+                const int sa = t * 4 + (g >> 1), sb = (t + 4) * 4 + (g >> 1);
+                float v[4];
+                {
+                    const float x0 = __shfl_sync(FULL, acc[mt][n0][2 * h], sa);
+                    const float x1 = __shfl_sync(FULL, acc[mt][n0][2 * h + 1], sa);
+                    v[0] = (g & 1) ? x1 : x0;                       // (pixel g, target 8kk + t)
+                    const float y0 = __shfl_sync(FULL, acc[mt][n1][2 * h], sa);
+                    const float y1 = __shfl_sync(FULL, acc[mt][n1][2 * h + 1], sa);
+                    v[1] = (g & 1) ? y1 : y0;                       // (pixel g + 8, target 8kk + t)
+                    const float z0 = __shfl_sync(FULL, acc[mt][n0][2 * h], sb);
+                    const float z1 = __shfl_sync(FULL, acc[mt][n0][2 * h + 1], sb);
+                    v[2] = (g & 1) ? z1 : z0;                       // (pixel g, target 8kk + t + 4)
+                    const float w0 = __shfl_sync(FULL, acc[mt][n1][2 * h], sb);
+                    const float w1 = __shfl_sync(FULL, acc[mt][n1][2 * h + 1], sb);
+                    v[3] = (g & 1) ? w1 : w0;                       // (pixel g + 8, target 8kk + t + 4)
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) split_tf32(v[q], ch[kk][q], cl[kk][q]);
+            }
+            const int pa = 16 * m2 + g, pb = pa + 8;
+            const int64_t pxa = p0 + pa, pxb = p0 + pb;
+            const float a1a = s_a1[warp][pa], a2a = s_a2[warp][pa];
+            const float a1b = s_a1[warp][pb], a2b = s_a2[warp][pb];
+            for (int c0 = 0; c0 < C; c0 += 8) {
+                float d[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int kk = 0; kk < 2 * MT; ++kk) {
+                    const int r0 = (8 * kk + t) * S + c0 + g, r1 = r0 + 4 * S;
+                    mma3(d, ch[kk], cl[kk], __float_as_uint(s_hi[r0]), __float_as_uint(s_hi[r1]),
+                         __float_as_uint(s_lo[r0]), __float_as_uint(s_lo[r1]));
+                }
+                const int cc = c0 + 2 * t;
+                if (pxa < P) {
+                    const float2 f = a1a > 0.f ? __ldg(reinterpret_cast<const float2 *>(F + pxa * C + cc))
+                                               : make_float2(0.f, 0.f);
+                    __stcg(reinterpret_cast<float2 *>(grad + pxa * C + cc),
+                           a1a > 0.f ? make_float2(fmaf(d[0], a1a, -a2a * f.x), fmaf(d[1], a1a, -a2a * f.y))
+                                     : make_float2(0.f, 0.f));
+                }
+                if (pxb < P) {
+                    const float2 f = a1b > 0.f ? __ldg(reinterpret_cast<const float2 *>(F + pxb * C + cc))
+                                               : make_float2(0.f, 0.f);
+                    __stcg(reinterpret_cast<float2 *>(grad + pxb * C + cc),
+                           a1b > 0.f ? make_float2(fmaf(d[2], a1b, -a2b * f.x), fmaf(d[3], a1b, -a2b * f.y))
+                                     : make_float2(0.f, 0.f));
+                }
+            }
+        }
+        __syncwarp();   // s_a1 / s_a2 are rewritten by the next block
+    }
+}
+
 int sm_count_now() {
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
@@ -256,18 +500,24 @@ cudaError_t launch_contrastive_loss(const float *F, const float *tgt, int M, int
     if (e != cudaSuccess) return e;
     eq2_norm<<<(M * 32 + 255) / 256, 256, 0, s>>>(tgt, M, C, 1e-8f, tn);
     eq2_count<<<unsigned(sms), 1024, 0, s>>>(mask_id, P, out2);
-    const size_t dyn = size_t(M) * C * 4;
-    auto go = [&](auto kern) -> cudaError_t {
+    auto go = [&](auto kern, size_t dyn) -> cudaError_t {
         cudaError_t ee = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(dyn));
         if (ee != cudaSuccess) return ee;
         kern<<<unsigned(sms), kThreads, dyn, s>>>(F, tn, M, C, mask_id, P, 1e-8f, term, grad, out2);
         return cudaGetLastError();
     };
-    switch (C / 128) {
-        case 1: e = go(eq2_terms<1>); break;
-        case 2: e = go(eq2_terms<2>); break;
-        case 3: e = go(eq2_terms<3>); break;
-        default: e = go(eq2_terms<4>); break;
+    if (M <= 32) {
+        // tensor cores: the unit targets split into TF32 hi / lo rows of C + 16
+        const size_t dyn2 = size_t(2) * (M <= 16 ? 16 : 32) * size_t(C + 16) * 4;
+        e = M <= 16 ? go(eq2_mma<1>, dyn2) : go(eq2_mma<2>, dyn2);
+    } else {
+        const size_t dyn = size_t(M) * C * 4;
+        switch (C / 128) {
+            case 1: e = go(eq2_terms<1>, dyn); break;
+            case 2: e = go(eq2_terms<2>, dyn); break;
+            case 3: e = go(eq2_terms<3>, dyn); break;
+            default: e = go(eq2_terms<4>, dyn); break;
+        }
     }
     count_launch(3);
     if (e != cudaSuccess) return e;

@@ -263,7 +263,8 @@ __device__ __forceinline__ void mma3(float (&d)[4], const uint32_t (&ah)[4], con
 // makes the fragment loads conflict-free); each warp takes 64 pixels at a
 // time (eight 8-pixel n-tiles; g = lane / 4, t = lane % 4):
 //   1. S^T = T^ F^T (M = targets, N = pixels, K = channels): per 16
-//      channels a lane loads one float4 of each of its eight pixel rows (the
+//      channels a lane loads one float4 of each of its two pixel rows, the
+//      next 16 channels' loads in flight meanwhile (the
 //      K order inside the 16 is permuted so that A and B fragments are float4
 //      loads; the sums are the same) and accumulates |F|^2;
 //   2. per pixel, from the accumulator layout (lane (g, t) holds targets g,
@@ -273,23 +274,25 @@ __device__ __forceinline__ void mma3(float (&d)[4], const uint32_t (&ah)[4], con
 //   3. G = C T^ (M = pixels, N = channels, K = targets): the c_j fragments
 //      are gathered by shuffles, T^ fragments read from shared memory, and
 //      each 16 x 8 result, (G / nf - (sum_j c_j s_j) F / nf^2) / n, is
-//      written with the F values it needs re-read (they were read moments
-//      before and come from L2).
+//      written (streaming stores) with the F values it needs re-read (they
+//      were read moments before and come from L2).
+constexpr int kMmaThreads = 512;
+
 template <int MT>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kMmaThreads, 1)
 eq2_mma(const float *__restrict__ F, const float *__restrict__ tn, int M, int C,
         const int32_t *__restrict__ mask_id, int64_t P, float eps, float *__restrict__ term,
         float *__restrict__ grad, const float *__restrict__ out2) {
     constexpr unsigned FULL = 0xffffffffu;
-    constexpr int NW = kThreads / 32;
-    constexpr int NT = 8;                  // 8-pixel n-tiles per warp
+    constexpr int NW = kMmaThreads / 32;
+    constexpr int NT = 2;                  // 8-pixel n-tiles per warp
     constexpr int NPX = 8 * NT;            // pixels per warp block
     constexpr int MR = 16 * MT;            // target rows held
     extern __shared__ __align__(16) float s_t[];
     const int S = C + 16;
     float *s_hi = s_t, *s_lo = s_t + MR * S;
     __shared__ float s_a1[NW][NPX], s_a2[NW][NPX];
-    for (int i = threadIdx.x; i < MR * C; i += kThreads) {
+    for (int i = threadIdx.x; i < MR * C; i += kMmaThreads) {
         const int j = i / C, c = i - j * C;
         const float x = j < M ? tn[int64_t(j) * C + c] : 0.f;
         uint32_t h, l;
@@ -315,14 +318,21 @@ eq2_mma(const float *__restrict__ F, const float *__restrict__ tn, int M, int C,
 #pragma unroll
                 for (int q = 0; q < 4; ++q) acc[mt][nt][q] = 0.f;
         }
-        for (int cg = 0; cg < C; cg += 16) {
-            float4 fq[NT];
+        // the next 16 channels' F values are loaded while the current ones are used
+        float4 fq[NT];
+        auto load_f = [&](int cg, float4 (&dst)[NT]) {
 #pragma unroll
             for (int nt = 0; nt < NT; ++nt) {
                 const int64_t px = p0 + nt * 8 + g;
-                fq[nt] = px < P ? __ldg(reinterpret_cast<const float4 *>(F + px * C + cg + 4 * t))
-                                : make_float4(0.f, 0.f, 0.f, 0.f);
+                dst[nt] = (px < P && cg < C)
+                              ? __ldg(reinterpret_cast<const float4 *>(F + px * C + cg + 4 * t))
+                              : make_float4(0.f, 0.f, 0.f, 0.f);
             }
+        };
+        load_f(0, fq);
+        for (int cg = 0; cg < C; cg += 16) {
+            float4 fn[NT];
+            load_f(cg + 16, fn);
             // A fragments of every m-tile (rows g and g + 8, channels cg + 4t ..):
             // k-step 0 takes .x (slot t) and .y (slot t + 4), k-step 1 .z and .w
             uint32_t ah[MT][2][4], al[MT][2][4];
@@ -356,6 +366,8 @@ eq2_mma(const float *__restrict__ F, const float *__restrict__ tn, int M, int C,
                     mma3(acc[mt][nt], ah[mt][1], al[mt][1], bh[2], bh[3], bl[2], bl[3]);
                 }
             }
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt) fq[nt] = fn[nt];
         }
 #pragma unroll
         for (int nt = 0; nt < NT; ++nt) {
@@ -454,14 +466,14 @@ eq2_mma(const float *__restrict__ F, const float *__restrict__ tn, int M, int C,
                 if (pxa < P) {
                     const float2 f = a1a > 0.f ? __ldg(reinterpret_cast<const float2 *>(F + pxa * C + cc))
                                                : make_float2(0.f, 0.f);
-                    __stcg(reinterpret_cast<float2 *>(grad + pxa * C + cc),
+                    __stcs(reinterpret_cast<float2 *>(grad + pxa * C + cc),
                            a1a > 0.f ? make_float2(fmaf(d[0], a1a, -a2a * f.x), fmaf(d[1], a1a, -a2a * f.y))
                                      : make_float2(0.f, 0.f));
                 }
                 if (pxb < P) {
                     const float2 f = a1b > 0.f ? __ldg(reinterpret_cast<const float2 *>(F + pxb * C + cc))
                                                : make_float2(0.f, 0.f);
-                    __stcg(reinterpret_cast<float2 *>(grad + pxb * C + cc),
+                    __stcs(reinterpret_cast<float2 *>(grad + pxb * C + cc),
                            a1b > 0.f ? make_float2(fmaf(d[2], a1b, -a2b * f.x), fmaf(d[3], a1b, -a2b * f.y))
                                      : make_float2(0.f, 0.f));
                 }
@@ -500,23 +512,23 @@ cudaError_t launch_contrastive_loss(const float *F, const float *tgt, int M, int
     if (e != cudaSuccess) return e;
     eq2_norm<<<(M * 32 + 255) / 256, 256, 0, s>>>(tgt, M, C, 1e-8f, tn);
     eq2_count<<<unsigned(sms), 1024, 0, s>>>(mask_id, P, out2);
-    auto go = [&](auto kern, size_t dyn) -> cudaError_t {
+    auto go = [&](auto kern, size_t dyn, int nthreads) -> cudaError_t {
         cudaError_t ee = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(dyn));
         if (ee != cudaSuccess) return ee;
-        kern<<<unsigned(sms), kThreads, dyn, s>>>(F, tn, M, C, mask_id, P, 1e-8f, term, grad, out2);
+        kern<<<unsigned(sms), nthreads, dyn, s>>>(F, tn, M, C, mask_id, P, 1e-8f, term, grad, out2);
         return cudaGetLastError();
     };
     if (M <= 32) {
         // tensor cores: the unit targets split into TF32 hi / lo rows of C + 16
         const size_t dyn2 = size_t(2) * (M <= 16 ? 16 : 32) * size_t(C + 16) * 4;
-        e = M <= 16 ? go(eq2_mma<1>, dyn2) : go(eq2_mma<2>, dyn2);
+        e = M <= 16 ? go(eq2_mma<1>, dyn2, kMmaThreads) : go(eq2_mma<2>, dyn2, kMmaThreads);
     } else {
         const size_t dyn = size_t(M) * C * 4;
         switch (C / 128) {
-            case 1: e = go(eq2_terms<1>, dyn); break;
-            case 2: e = go(eq2_terms<2>, dyn); break;
-            case 3: e = go(eq2_terms<3>, dyn); break;
-            default: e = go(eq2_terms<4>, dyn); break;
+            case 1: e = go(eq2_terms<1>, dyn, kThreads); break;
+            case 2: e = go(eq2_terms<2>, dyn, kThreads); break;
+            case 3: e = go(eq2_terms<3>, dyn, kThreads); break;
+            default: e = go(eq2_terms<4>, dyn, kThreads); break;
         }
     }
     count_launch(3);

@@ -264,7 +264,7 @@ __device__ __forceinline__ void mma3(float (&d)[4], const uint32_t (&ah)[4], con
 // time (eight 8-pixel n-tiles; g = lane / 4, t = lane % 4):
 //   1. S^T = T^ F^T (M = targets, N = pixels, K = channels): per 16
 //      channels a lane loads one float4 of each of its two pixel rows, the
-//      next 16 channels' loads in flight meanwhile (the
+//      next 32 channels' loads in flight meanwhile (the
 //      K order inside the 16 is permuted so that A and B fragments are float4
 //      loads; the sums are the same) and accumulates |F|^2;
 //   2. per pixel, from the accumulator layout (lane (g, t) holds targets g,
@@ -329,10 +329,12 @@ eq2_mma(const float *__restrict__ F, const float *__restrict__ tn, int M, int C,
                               : make_float4(0.f, 0.f, 0.f, 0.f);
             }
         };
+        float4 fn[NT];
         load_f(0, fq);
+        load_f(16, fn);
         for (int cg = 0; cg < C; cg += 16) {
-            float4 fn[NT];
-            load_f(cg + 16, fn);
+            float4 fn2[NT];
+            load_f(cg + 32, fn2);   // two groups of loads in flight ahead of the MMAs
             // A fragments of every m-tile (rows g and g + 8, channels cg + 4t ..):
             // k-step 0 takes .x (slot t) and .y (slot t + 4), k-step 1 .z and .w
             uint32_t ah[MT][2][4], al[MT][2][4];
@@ -367,7 +369,10 @@ eq2_mma(const float *__restrict__ F, const float *__restrict__ tn, int M, int C,
                 }
             }
 #pragma unroll
-            for (int nt = 0; nt < NT; ++nt) fq[nt] = fn[nt];
+            for (int nt = 0; nt < NT; ++nt) {
+                fq[nt] = fn[nt];
+                fn[nt] = fn2[nt];
+            }
         }
 #pragma unroll
         for (int nt = 0; nt < NT; ++nt) {
@@ -454,7 +459,14 @@ eq2_mma(const float *__restrict__ F, const float *__restrict__ tn, int M, int C,
             const int64_t pxa = p0 + pa, pxb = p0 + pb;
             const float a1a = s_a1[warp][pa], a2a = s_a2[warp][pa];
             const float a1b = s_a1[warp][pb], a2b = s_a2[warp][pb];
+            // F values of the F term, one 8-channel step ahead
+            auto load_f2 = [&](int64_t px, int c) {
+                return (px < P && c < C) ? __ldg(reinterpret_cast<const float2 *>(F + px * C + c))
+                                         : make_float2(0.f, 0.f);
+            };
+            float2 fa = load_f2(pxa, 2 * t), fb = load_f2(pxb, 2 * t);
             for (int c0 = 0; c0 < C; c0 += 8) {
+                const float2 fa_n = load_f2(pxa, c0 + 8 + 2 * t), fb_n = load_f2(pxb, c0 + 8 + 2 * t);
                 float d[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
                 for (int kk = 0; kk < 2 * MT; ++kk) {
@@ -463,20 +475,16 @@ eq2_mma(const float *__restrict__ F, const float *__restrict__ tn, int M, int C,
                          __float_as_uint(s_lo[r0]), __float_as_uint(s_lo[r1]));
                 }
                 const int cc = c0 + 2 * t;
-                if (pxa < P) {
-                    const float2 f = a1a > 0.f ? __ldg(reinterpret_cast<const float2 *>(F + pxa * C + cc))
-                                               : make_float2(0.f, 0.f);
+                if (pxa < P)
                     __stcs(reinterpret_cast<float2 *>(grad + pxa * C + cc),
-                           a1a > 0.f ? make_float2(fmaf(d[0], a1a, -a2a * f.x), fmaf(d[1], a1a, -a2a * f.y))
+                           a1a > 0.f ? make_float2(fmaf(d[0], a1a, -a2a * fa.x), fmaf(d[1], a1a, -a2a * fa.y))
                                      : make_float2(0.f, 0.f));
-                }
-                if (pxb < P) {
-                    const float2 f = a1b > 0.f ? __ldg(reinterpret_cast<const float2 *>(F + pxb * C + cc))
-                                               : make_float2(0.f, 0.f);
+                if (pxb < P)
                     __stcs(reinterpret_cast<float2 *>(grad + pxb * C + cc),
-                           a1b > 0.f ? make_float2(fmaf(d[2], a1b, -a2b * f.x), fmaf(d[3], a1b, -a2b * f.y))
+                           a1b > 0.f ? make_float2(fmaf(d[2], a1b, -a2b * fb.x), fmaf(d[3], a1b, -a2b * fb.y))
                                      : make_float2(0.f, 0.f));
-                }
+                fa = fa_n;
+                fb = fb_n;
             }
         }
         __syncwarp();   // s_a1 / s_a2 are rewritten by the next block

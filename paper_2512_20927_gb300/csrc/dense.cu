@@ -195,26 +195,53 @@ dense_kernel(const float4 *__restrict__ rec_m, const float4 *__restrict__ rec_w,
 }
 
 // ------------------------------------------------------------------ sub-tile kernel
-// One CTA (512 threads) renders a 64-pixel sub-tile of a screen tile (16x4,
-// 8x8 or 32x2) over all C channels (C = 64 CH, CH = 2, 4 or 8), so each
-// pixel's alpha' / T walk runs once.  Per batch of 64 list entries:
-//   1. the records are staged and two warps cull them against the sub-tile's
-//      box of pixel centres (the conservative test of the selection);
-//   2. 64 threads walk their pixel over the survivors in list order (the
-//      same scalar FP32 recurrence as dense_kernel) and write w = T alpha'
-//      into W[survivor][pixel];
-//   3. survivors with a nonzero weight anywhere in the sub-tile are kept, in
-//      list order, and only their feature rows are staged (FP32, decoded);
-//   4. warps 2g and 2g+1 accumulate pixel group g (a 4x2 block of 8 pixels)
-//      over all channels: per kept entry 8 weights and CH features per
-//      thread, 8 CH FMAs; an entry whose 8 weights are all zero is skipped
-//      by the whole warp.
-// Zero weights add nothing (fmaf(0, f, acc) == acc), so the result equals
-// dense_kernel's bit for bit.  stats (nullable): [0] += blended (pixel,
-// Gaussian) pairs, [1] += executed (8-pixel group, entry) pairs.
-constexpr int S_THREADS = 512;
+// One CTA renders a 64-pixel sub-tile of a screen tile (16x4, 8x8 or 32x2)
+// over all C channels (C = 64 CH, CH = 2, 4 or 8), so each pixel's alpha' / T
+// walk runs once.  The CTA is warp-specialised and double-buffered, so the
+// serial walk of one batch of list entries overlaps the accumulation of the
+// previous one:
+//   producers (warps 16, 17: one thread per pixel), per batch of 32 entries:
+//     1. cull the batch's records (loaded into registers while the previous
+//        batch was walked) against the sub-tile's box of pixel centres (the
+//        conservative test of the selection);
+//     2. walk every pixel over the survivors in list order (the scalar FP32
+//        recurrence of dense_kernel) and write w = T alpha' into W[slot];
+//     3. list, in list order, the survivors with a nonzero weight anywhere in
+//        the sub-tile (and their ids);
+//   consumers (warps 0-15: warps 2g and 2g+1 own pixel group g, a 4x2 block
+//   of 8 pixels): stage the kept entries' feature rows in shared memory
+//   (FP32 rows by 16-byte cp.async, BF16 / FP8 rows widened), then per kept
+//   entry 8 weights and CH features per thread, 8 CH FMAs; an entry whose 8
+//   weights are all zero is skipped by the warp.
+// Hand-over through hardware named barriers: FULL[slot] (producers arrive
+// once the slot is written, consumers wait) and EMPTY[slot] (consumers arrive
+// once the slot is read, producers wait before writing it again and, at the
+// end, for every slot still unread), so every barrier phase is matched.  A
+// slot whose kept count is -1 ends the consumers' loop.  Zero weights add
+// nothing (fmaf(0, f, acc) == acc), so the result equals dense_kernel's.
+// stats (nullable): [0] += blended (pixel, Gaussian) pairs, [1] += executed
+// multiply-adds.
+constexpr int S_CONS = 512;                  // consumer threads (16 warps)
+constexpr int S_PROD = 64;                   // producer threads (2 warps, one per pixel)
+constexpr int S_THREADS = S_CONS + S_PROD;
 constexpr int S_PIX = 64;
-constexpr int S_BATCH = 64;
+constexpr int S_BATCH = 32;
+// named barriers (0 is __syncthreads)
+constexpr int kBarFull = 1;                  // + slot
+constexpr int kBarEmpty = 3;                 // + slot
+constexpr int kBarProd = 5;
+constexpr int kBarCons = 6;
+
+__device__ __forceinline__ void nbar_sync(int id, int n) {
+    asm volatile("bar.sync %0, %1;" :: "r"(id), "r"(n) : "memory");
+}
+__device__ __forceinline__ void nbar_arrive(int id, int n) {
+    asm volatile("bar.arrive %0, %1;" :: "r"(id), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
+                 :: "r"(uint32_t(__cvta_generic_to_shared(smem))), "l"(gmem) : "memory");
+}
 
 template <int DT, int CH>
 __global__ void __launch_bounds__(S_THREADS, 1)
@@ -228,17 +255,22 @@ dense_sub_kernel(const float4 *__restrict__ rec_m, const float4 *__restrict__ re
     constexpr int CPV = Cpv<DT>::v;
     constexpr int ESZ = DT == QR_F32 ? 4 : DT == QR_BF16 ? 2 : 1;
     constexpr unsigned FULL = 0xffffffffu;
+    // producer state
     __shared__ float4 s_m[S_BATCH];
     __shared__ float4 s_c[S_BATCH];
     __shared__ float s_a[S_BATCH];
     __shared__ float s_h[S_BATCH];
     __shared__ uint32_t s_g[S_BATCH];
-    __shared__ int s_surv[S_BATCH];       // survivor -> staged entry
-    __shared__ int s_used[S_BATCH];       // kept -> survivor
-    __shared__ int s_ns, s_nu, s_cnt0;
+    __shared__ int s_surv[S_BATCH];          // survivor -> staged entry
+    __shared__ int s_ns;
+    __shared__ int s_done[2];
     __shared__ float s_box[4];
-    __shared__ __align__(16) float s_W[S_BATCH][S_PIX];
-    extern __shared__ __align__(16) float s_F[];     // [S_BATCH][C]
+    // double-buffered hand-over
+    __shared__ __align__(16) float s_W[2][S_BATCH][S_PIX];
+    __shared__ int s_used[2][S_BATCH];       // kept -> survivor
+    __shared__ uint32_t s_kg[2][S_BATCH];    // kept -> Gaussian id
+    __shared__ int s_nu[2];                  // kept entries, -1 = end
+    extern __shared__ __align__(16) float s_F[];     // [S_BATCH][C], the consumers' rows
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int tile = blockIdx.x >> 2, sub = blockIdx.x & 3;
@@ -252,13 +284,8 @@ dense_sub_kernel(const float4 *__restrict__ rec_m, const float4 *__restrict__ re
         y = ty * tile_h + sub * sub_h + (g / gx_n) * 2 + (i >> 2);
     };
     const uint2 range = ranges[tile];
-    // the walker's pixel
-    int px = 0, py = 0;
-    if (tid < S_PIX) slot_xy(tid, px, py);
-    const bool walker = tid < S_PIX;
-    const bool inside = walker && px < W && py < H;
-    const float ux = float(px) + 0.5f, uy = float(py) + 0.5f;
-    if (tid < 32) {
+    const bool producer = tid >= S_CONS;
+    if (tid >= S_CONS && tid < S_CONS + 32) {
         // the sub-tile's box of pixel centres (clipped to the image)
         float bx0 = 1e30f, bx1 = -1e30f, by0 = 1e30f, by1 = -1e30f;
         for (int ps = lane; ps < S_PIX; ps += 32) {
@@ -275,59 +302,76 @@ dense_sub_kernel(const float4 *__restrict__ rec_m, const float4 *__restrict__ re
         }
         if (lane == 0) { s_box[0] = bx0; s_box[1] = bx1; s_box[2] = by0; s_box[3] = by1; }
     }
-    // accumulation roles: two warps per 8-pixel group; thread t of the group
-    // owns the channel pairs 2 t + 128 k (k < CH / 2), so a warp's shared-memory
-    // reads and global writes are consecutive 8-byte pairs
-    const int g = warp >> 1;
-    const int c0 = (tid & 63) * 2;
-    float acc[8][CH];
-#pragma unroll
-    for (int i = 0; i < 8; ++i)
-#pragma unroll
-        for (int c = 0; c < CH; ++c) acc[i][c] = 0.f;
-    float T = 1.0f;
-    bool done = !inside;
-    unsigned long long n_blend = 0, n_exec = 0;
-    const size_t row_bytes = size_t(C) * ESZ;
     __syncthreads();
+    const size_t row_bytes = size_t(C) * ESZ;
 
-    for (uint32_t b = range.x; b < range.y; b += S_BATCH) {
-        if (__syncthreads_count(done || !walker) == S_THREADS) break;
-        const int nb = int(min(uint32_t(S_BATCH), range.y - b));
-        // 1. stage and cull
-        if (tid < S_BATCH) {
-            bool pass = false;
-            if (tid < nb) {
-                const uint32_t gid = isect_gid[b + tid];
-                const float4 mm = rec_m[gid], cc = rec_w[gid];
-                const float hh = rec_h[gid];
-                s_g[tid] = gid;
-                s_m[tid] = mm;
-                s_c[tid] = cc;
-                s_a[tid] = rec_a[gid];
-                s_h[tid] = hh;
-                pass = !(box_min_half_q(mm, cc, s_box[0], s_box[1], s_box[2], s_box[3]) * 0.999f >
-                         hh + 1e-3f);
+    if (producer) {
+        // ---------------------------------------------------------- producers
+        const int pt = tid - S_CONS, pw = pt >> 5;     // pixel slot, producer warp
+        int px, py;
+        slot_xy(pt, px, py);
+        const bool inside = px < W && py < H;
+        const float ux = float(px) + 0.5f, uy = float(py) + 0.5f;
+        float T = 1.0f;
+        bool done = !inside;
+        unsigned long long n_blend = 0;
+        bool pending[2] = {false, false};
+        int sl = 0;
+        // producer warp 0 holds the next batch's records in registers: their
+        // loads (the list ids, then the records) run while the current batch
+        // is walked
+        uint32_t n_gid = 0;
+        float4 n_m = make_float4(0.f, 0.f, 0.f, 0.f), n_c = n_m;
+        float n_a = 0.f, n_h = 0.f;
+        auto prefetch = [&](uint32_t bb) {
+            if (pw == 0 && bb < range.y && uint32_t(lane) < range.y - bb) {
+                n_gid = isect_gid[bb + lane];
+                n_m = rec_m[n_gid];
+                n_c = rec_w[n_gid];
+                n_a = rec_a[n_gid];
+                n_h = rec_h[n_gid];
             }
-            const unsigned bal = __ballot_sync(FULL, pass);
-            const int pos = __popc(bal & ((1u << lane) - 1u));
-            // warp 1's survivors follow warp 0's
-            if (warp == 0 && lane == 0) s_cnt0 = __popc(bal);
-            asm volatile("bar.sync 2, 64;" ::: "memory");
-            const int base = warp == 0 ? 0 : s_cnt0;
-            if (pass) s_surv[base + pos] = tid;
-            if (warp == 1 && lane == 0) s_ns = s_cnt0 + __popc(bal);
-        }
-        __syncthreads();
-        const int ns = s_ns;
-        // 2. the walk: W[survivor][pixel slot]
-        if (walker) {
+        };
+        prefetch(range.x);
+        for (uint32_t b = range.x;; b += S_BATCH) {
+            const unsigned dv = __ballot_sync(FULL, done);
+            if (lane == 0) s_done[pw] = dv == FULL;
+            nbar_sync(kBarProd, S_PROD);
+            const bool all_done = s_done[0] && s_done[1];
+            nbar_sync(kBarProd, S_PROD);               // s_done is read before it is rewritten
+            if (b >= range.y || all_done) break;
+            const int nb = int(min(uint32_t(S_BATCH), range.y - b));
+            // 1. stage and cull (producer warp 0, one entry per lane)
+            if (pw == 0) {
+                bool pass = false;
+                if (lane < nb) {
+                    s_g[lane] = n_gid;
+                    s_m[lane] = n_m;
+                    s_c[lane] = n_c;
+                    s_a[lane] = n_a;
+                    s_h[lane] = n_h;
+                    pass = !(box_min_half_q(n_m, n_c, s_box[0], s_box[1], s_box[2], s_box[3]) * 0.999f >
+                             n_h + 1e-3f);
+                }
+                const unsigned bal = __ballot_sync(FULL, pass);
+                if (pass) s_surv[__popc(bal & ((1u << lane) - 1u))] = lane;
+                if (lane == 0) s_ns = __popc(bal);
+                prefetch(b + S_BATCH);
+            }
+            if (pending[sl]) {                        // the consumers are done with this slot
+                nbar_sync(kBarEmpty + sl, S_THREADS);
+                pending[sl] = false;
+            }
+            nbar_sync(kBarProd, S_PROD);
+            const int ns = s_ns;
+            // 2. the walk: W[slot][survivor][pixel slot]
+            float(*Wt)[S_PIX] = s_W[sl];
             for (int sv = 0; sv < ns; ++sv) {
                 const int j = s_surv[sv];
                 float w = 0.f;
                 if (!done) {
-                    const PixelTerm pt = eval_half_q(ux, uy, s_m[j], s_c[j]);
-                    const float a = pt.half_q > s_h[j] ? 0.f : eval_alpha(s_a[j], pt.half_q, alpha_max);
+                    const PixelTerm ptm = eval_half_q(ux, uy, s_m[j], s_c[j]);
+                    const float a = ptm.half_q > s_h[j] ? 0.f : eval_alpha(s_a[j], ptm.half_q, alpha_max);
                     if (a >= alpha_min) {
                         const float Tt = T * (1.0f - a);
                         if (T_min > 0.f && Tt < T_min) {
@@ -339,18 +383,15 @@ dense_sub_kernel(const float4 *__restrict__ rec_m, const float4 *__restrict__ re
                         }
                     }
                 }
-                s_W[sv][tid] = w;
+                Wt[sv][pt] = w;
             }
-        }
-        __syncthreads();
-        // 3. survivors with a nonzero weight, in list order
-        if (warp == 0) {
-            int nu = 0;
-            for (int s0 = 0; s0 < ns; s0 += 32) {
-                const int sv = s0 + lane;
+            nbar_sync(kBarProd, S_PROD);
+            // 3. survivors with a nonzero weight, in list order, and their ids
+            // (producer warp 0)
+            if (pw == 0) {
                 bool used = false;
-                if (sv < ns) {
-                    const float4 *wr = reinterpret_cast<const float4 *>(s_W[sv]);
+                if (lane < ns) {
+                    const float4 *wr = reinterpret_cast<const float4 *>(Wt[lane]);
 #pragma unroll
                     for (int q = 0; q < S_PIX / 4; ++q) {
                         const float4 t = wr[q];
@@ -358,21 +399,58 @@ dense_sub_kernel(const float4 *__restrict__ rec_m, const float4 *__restrict__ re
                     }
                 }
                 const unsigned bal = __ballot_sync(FULL, used);
-                if (used) s_used[nu + __popc(bal & ((1u << lane) - 1u))] = sv;
-                nu += __popc(bal);
+                if (used) {
+                    const int u = __popc(bal & ((1u << lane) - 1u));
+                    s_used[sl][u] = lane;
+                    s_kg[sl][u] = s_g[s_surv[lane]];
+                }
+                if (lane == 0) s_nu[sl] = __popc(bal);
             }
-            if (lane == 0) s_nu = nu;
+            nbar_arrive(kBarFull + sl, S_THREADS);
+            pending[sl] = true;
+            sl ^= 1;
         }
-        __syncthreads();
-        const int nu = s_nu;
-        // 4. stage the kept rows (decoded to FP32)
-        {
-            const int vpr = C / CPV;                   // 16-byte vectors per row
-            for (int i = tid; i < nu * vpr; i += S_THREADS) {
-                const int u = i / vpr, v = i - u * vpr;
-                const uint32_t gid = s_g[s_surv[s_used[u]]];
-                const uint4 x = __ldg(reinterpret_cast<const uint4 *>(feat + size_t(gid) * row_bytes +
-                                                                       size_t(v) * 16));
+        // the end marker, then wait until every produced slot has been read
+        if (pending[sl]) {
+            nbar_sync(kBarEmpty + sl, S_THREADS);
+            pending[sl] = false;
+        }
+        if (pt == 0) s_nu[sl] = -1;
+        nbar_arrive(kBarFull + sl, S_THREADS);
+        sl ^= 1;
+        if (pending[sl]) nbar_sync(kBarEmpty + sl, S_THREADS);
+        if (T_final && inside) T_final[int64_t(py) * W + px] = T;
+        if (stats) atomicAdd(&stats[0], n_blend);
+        return;
+    }
+
+    // -------------------------------------------------------------- consumers
+    // thread t of a group's warp pair owns the channel pairs 2 t + 128 k
+    // (k < CH / 2), so a warp's shared-memory reads and global writes are
+    // consecutive 8-byte pairs
+    const int g = warp >> 1;
+    const int c0 = (tid & 63) * 2;
+    float acc[8][CH];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int c = 0; c < CH; ++c) acc[i][c] = 0.f;
+    unsigned long long n_exec = 0;
+    for (int sl = 0;; sl ^= 1) {
+        nbar_sync(kBarFull + sl, S_THREADS);
+        const int nu = s_nu[sl];
+        if (nu < 0) break;
+        // the kept rows into F (the consumers are all past the previous
+        // batch: the FULL barrier counts every one of them)
+        const int vpr = C / CPV;                       // 16-byte vectors per row
+        for (int i = tid; i < nu * vpr; i += S_CONS) {
+            const int u = i / vpr, v = i - u * vpr;
+            const uint32_t gid = s_kg[sl][u];
+            const unsigned char *src = feat + size_t(gid) * row_bytes + size_t(v) * 16;
+            if constexpr (DT == QR_F32) {
+                cp_async16(s_F + size_t(u) * C + v * CPV, src);
+            } else {
+                const uint4 x = __ldg(reinterpret_cast<const uint4 *>(src));
                 float tmp[CPV];
                 widen16<DT>(x, DT == QR_FP8E4M3 ? fscale[gid] : 1.f, tmp);
 #pragma unroll
@@ -381,20 +459,22 @@ dense_sub_kernel(const float4 *__restrict__ rec_m, const float4 *__restrict__ re
                         make_float4(tmp[q], tmp[q + 1], tmp[q + 2], tmp[q + 3]);
             }
         }
-        __syncthreads();
-        // 5. accumulate: warp-uniform skip of entries with no weight in the group
+        if constexpr (DT == QR_F32) asm volatile("cp.async.wait_all;" ::: "memory");
+        nbar_sync(kBarCons, S_CONS);
         for (int u = 0; u < nu; ++u) {
-            const float4 *wr = reinterpret_cast<const float4 *>(&s_W[s_used[u]][g * 8]);
+            const int sv = s_used[sl][u];
+            const float4 *wr = reinterpret_cast<const float4 *>(&s_W[sl][sv][g * 8]);
             const float4 wa = wr[0], wb = wr[1];
             const float wv[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
             const bool any = (wa.x != 0.f) | (wa.y != 0.f) | (wa.z != 0.f) | (wa.w != 0.f) |
                              (wb.x != 0.f) | (wb.y != 0.f) | (wb.z != 0.f) | (wb.w != 0.f);
             if (!any) continue;
             ++n_exec;
+            const float *Fr = s_F + size_t(u) * C;
             float fv[CH];
 #pragma unroll
             for (int k = 0; k < CH / 2; ++k) {
-                const float2 t = *reinterpret_cast<const float2 *>(s_F + size_t(u) * C + 128 * k + c0);
+                const float2 t = *reinterpret_cast<const float2 *>(Fr + 128 * k + c0);
                 fv[2 * k] = t.x;
                 fv[2 * k + 1] = t.y;
             }
@@ -403,6 +483,7 @@ dense_sub_kernel(const float4 *__restrict__ rec_m, const float4 *__restrict__ re
 #pragma unroll
                 for (int c = 0; c < CH; ++c) acc[i][c] = fmaf(wv[i], fv[c], acc[i][c]);
         }
+        nbar_arrive(kBarEmpty + sl, S_THREADS);
     }
     // write the sub-tile
 #pragma unroll
@@ -416,12 +497,8 @@ dense_sub_kernel(const float4 *__restrict__ rec_m, const float4 *__restrict__ re
                 *reinterpret_cast<float2 *>(o + 128 * k) = make_float2(acc[i][2 * k], acc[i][2 * k + 1]);
         }
     }
-    if (T_final && inside) T_final[int64_t(py) * W + px] = T;
-    if (stats) {
-        // executed FMAs (a warp's entries x 32 lanes x 8 pixels x CH) and blended pairs
-        if (lane == 0) atomicAdd(&stats[1], n_exec * 32ull * 8ull * CH);
-        if (walker) atomicAdd(&stats[0], n_blend);
-    }
+    // executed FMAs (a warp's entries x 32 lanes x 8 pixels x CH)
+    if (stats && lane == 0) atomicAdd(&stats[1], n_exec * 32ull * 8ull * CH);
 }
 
 template <int DT, int CH>

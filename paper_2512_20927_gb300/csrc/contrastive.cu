@@ -13,7 +13,11 @@
 //   * eq2_norm writes the unit targets t^ (one warp per target) and
 //     eq2_count counts the pixels in the loss (integer atomics), ahead of the
 //     pass that needs 1/n;
-//   * eq2_terms: one persistent CTA per SM holds all M unit targets in shared
+//   * up to 32 targets, eq2_mma: both
+//     contractions on the tensor cores as 3xTF32 mma.sync products (the
+//     operands split into TF32 hi and lo parts, hi*hi + hi*lo + lo*hi with
+//     FP32 accumulation, which keeps FP32 accuracy), described at the kernel;
+//   * otherwise eq2_terms: one persistent CTA per SM holds all M unit targets in shared
 //     memory (M x C FP32); each warp takes four pixels at a time with their
 //     feature rows in registers (a lane owns 4 x C/128 channels of each), so
 //     every target slice read from shared memory feeds four pixels.  Partial
@@ -23,8 +27,9 @@
 //     gradient rows are accumulated from the same shared targets and written
 //     once, already scaled by 1/n, with the pixel's loss term;
 //   * the terms are summed by the cosine loss's deterministic range sums.
-// FP32 throughout (exp and log with the accurate expf / logf), so the loss
-// and its gradient meet an FP64 reference to a few units of FP32 rounding.
+// FP32 arithmetic (exp and log with the accurate expf / logf; the 3xTF32
+// products carry about FP32 precision), so the loss and its gradient meet an
+// FP64 reference to a few units of FP32 rounding.
 #include "qr_internal.cuh"
 
 namespace qr {
@@ -260,8 +265,8 @@ __device__ __forceinline__ void mma3(float (&d)[4], const uint32_t (&ah)[4], con
 
 // eq2_mma: M <= 16 MT targets.  One CTA per SM holds the unit targets split
 // into TF32 hi / lo parts in shared memory ([16 MT][C + 16] each; the row pad
-// makes the fragment loads conflict-free); each warp takes 64 pixels at a
-// time (eight 8-pixel n-tiles; g = lane / 4, t = lane % 4):
+// makes the fragment loads conflict-free); each warp takes 16 pixels at a
+// time (two 8-pixel n-tiles; g = lane / 4, t = lane % 4):
 //   1. S^T = T^ F^T (M = targets, N = pixels, K = channels): per 16
 //      channels a lane loads one float4 of each of its two pixel rows, the
 //      next 32 channels' loads in flight meanwhile (the

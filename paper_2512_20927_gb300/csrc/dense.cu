@@ -7,7 +7,10 @@
 //
 // GB300 design: every pixel of a tile walks the same list, so the blend is a
 // dense product W (pixels x batch) * F (batch x channels) per batch of 32
-// list entries.  One CTA owns a screen tile and a 16/32/64-channel slice:
+// list entries.  Rows of 128, 256 or 512 channels go to dense_sub_kernel
+// (below: one CTA per 64-pixel sub-tile over all channels, warp-specialised
+// walk and accumulation).  Other widths use dense_kernel, where one CTA owns
+// a screen tile and a 16/32/64-channel slice:
 //   1. the batch's Gaussian records and feature-row slices are staged in
 //      shared memory (coalesced 16-byte loads; BF16/FP8 widened here),
 //   2. each thread walks its own pixel over the batch (scalar FP32, the exact

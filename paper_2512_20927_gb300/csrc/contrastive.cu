@@ -31,6 +31,7 @@
 // products carry about FP32 precision), so the loss and its gradient meet an
 // FP64 reference to a few units of FP32 rounding.
 #include "qr_internal.cuh"
+#include "mma_tf32.cuh"
 
 namespace qr {
 namespace {
@@ -233,35 +234,8 @@ eq2_terms(const float *__restrict__ F, const float *__restrict__ tn, int M, int 
 }
 
 // ------------------------------------------------------------------ tensor cores
-// The two contractions on the tensor cores (mma.sync m16n8k8, TF32 operands,
-// FP32 accumulation), each FP32 operand split as x = hi + lo with hi, lo
-// TF32 (round to nearest) and three products lo*hi + hi*lo + hi*hi per step:
-// the dropped lo*lo term and the rounding of lo leave about 2^-22 of |x||y|
-// per product, FP32-class accuracy.
-__device__ __forceinline__ uint32_t to_tf32(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return r;
-}
-__device__ __forceinline__ void split_tf32(float x, uint32_t &hi, uint32_t &lo) {
-    hi = to_tf32(x);
-    lo = to_tf32(x - __uint_as_float(hi));
-}
-__device__ __forceinline__ void mma_tf32(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2,
-                                         uint32_t a3, uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-        "{%8,%9}, {%0,%1,%2,%3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-// d += A B with A = ah + al, B = bh + bl (the small products first)
-__device__ __forceinline__ void mma3(float (&d)[4], const uint32_t (&ah)[4], const uint32_t (&al)[4],
-                                     uint32_t bh0, uint32_t bh1, uint32_t bl0, uint32_t bl1) {
-    mma_tf32(d, al[0], al[1], al[2], al[3], bh0, bh1);
-    mma_tf32(d, ah[0], ah[1], ah[2], ah[3], bl0, bl1);
-    mma_tf32(d, ah[0], ah[1], ah[2], ah[3], bh0, bh1);
-}
+// The two contractions on the tensor cores in the 3xTF32 form of
+// mma_tf32.cuh (mma.sync m16n8k8, FP32-class accuracy).
 
 // eq2_mma: M <= 16 MT targets.  One CTA per SM holds the unit targets split
 // into TF32 hi / lo parts in shared memory ([16 MT][C + 16] each; the row pad

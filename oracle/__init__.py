@@ -80,6 +80,8 @@ def _declare(L):
     L.or_topk_list.restype = _I
     L.or_stratified_list.argtypes = [_I64, _P, _I, _D, _P, _P, _P, _P, _P, _P]
     L.or_stratified_list.restype = _I
+    L.or_riemann_list.argtypes = [_I64, _P, _I, _P, _P, _P]
+    L.or_riemann_list.restype = _I
     L.or_render_rule.argtypes = ([_I64, _P, _P, _P, _P, _P, _P, _I, _I, _I, _D, _D, _D, _D, _I64,
                                   _P, _I] + [_P] * 9)
     L.or_render_rule.restype = _I
@@ -188,6 +190,7 @@ def dense_list(a, T_min: float = 0.0):
 
 RULE_TOPK = 1
 RULE_STRATIFIED = 2
+RULE_RIEMANN = 3
 
 
 def topk_list(a, K: int, T_min: float = 0.0):
@@ -219,6 +222,21 @@ def stratified_list(a, K: int, T_min: float = 0.0):
                                  _ptr(tau), _ptr(st))
     assert m >= 0
     return sel.astype(bool), w, float(tq[0]), int(npro[0]), tau, (st[0], st[1], int(st[2]))
+
+
+def riemann_list(a, K: int):
+    """Algorithm 1's selection with App. C's right-Riemann weights on one list:
+    each quantile Gaussian weighs the number of segment boundaries its test
+    transmittance crosses.  Returns (kept mask, crossing counts, entries
+    visited)."""
+    a = _c(a, np.float64)
+    n = a.shape[0]
+    sel = np.zeros(n, np.int32)
+    w = np.zeros(n)
+    npro = np.zeros(1, np.int64)
+    m = lib().or_riemann_list(n, _ptr(a), K, _ptr(sel), _ptr(w), _ptr(npro))
+    assert m >= 0
+    return sel.astype(bool), w, int(npro[0])
 
 
 def classify_rule_candidates(depth, ids, g, qabs, rule: int, K: int, T_min: float = 0.0,
@@ -256,8 +274,9 @@ class RuleRendered:
 def render_rule(proj: Projected, feat, rule: int, K: int, pixels, T_min: float = 1e-4,
                 alpha_min: float = ALPHA_MIN, alpha_max: float = ALPHA_MAX,
                 tie_eps: float = DEFAULT_TIE_EPS, threads: int | None = None) -> RuleRendered:
-    """Brute-force render of the listed pixels with the top-K (RULE_TOPK) or
-    Stratified-K (RULE_STRATIFIED) select rule in place of Algorithm 1, FP64."""
+    """Brute-force render of the listed pixels with the top-K (RULE_TOPK),
+    Stratified-K (RULE_STRATIFIED) or App. C Riemann-weight (RULE_RIEMANN)
+    select rule in place of Algorithm 1's weights, FP64."""
     n = proj.mean2d.shape[0]
     pix = _c(pixels, np.int32)
     m = pix.shape[0]

@@ -196,6 +196,42 @@ int or_qselect_closed_form(int64_t n, const double *a, int K, int32_t *sel)
 }
 
 /*
+ * App. C reads Algorithm 1 as a right Riemann sum over the transmittance
+ * domain split into K + 1 equal segments: each boundary 1 - k/(K+1) that the
+ * accumulated transmittance crosses contributes the feature of the Gaussian
+ * at which it is crossed, with the segment width 1/(K+1).  Reading (the
+ * optional weight form of the select rules): the same walk and selection as
+ * or_qrender_list; a quantile Gaussian's weight is the number of boundaries
+ * its test transmittance crosses, and the render divides by the number
+ * crossed in all, so the weights sum to 1 like Algorithm 1's normalised ones.
+ * sel[i] = 1 for the quantile Gaussians, w[i] their crossing counts; *n_proc
+ * as or_qrender_list.  Returns the number of quantile Gaussians.
+ */
+int or_riemann_list(int64_t n, const double *a, int K, int32_t *sel, double *w, int64_t *n_proc)
+{
+    double T = 1.0;
+    int k = 0, m = 0;
+    int64_t i;
+    for (i = 0; i < n; ++i) { sel[i] = 0; w[i] = 0.0; }
+    for (i = 0; i < n; ++i) {
+        double Ttest = T * (1.0 - a[i]);
+        if (Ttest < 1.0 - (double)(k + 1) / (double)(K + 1)) {
+            int k0 = k;
+            k = k + 1;
+            while (Ttest < 1.0 - (double)(k + 1) / (double)(K + 1)) k = k + 1;
+            if (k > K) k = K;              /* the K boundaries 1 - j/(K+1), j = 1..K */
+            w[i] = (double)(k - k0);
+            sel[i] = 1;
+            ++m;
+        }
+        if (Ttest < 1.0 / (double)(K + 1)) { ++i; break; }
+        T = Ttest;
+    }
+    if (n_proc) *n_proc = i;
+    return m;
+}
+
+/*
  * Eq. 1 on one list: w_i = T_i alpha'_i with T_i the transmittance before i.
  * With T_min > 0 the walk stops before the Gaussian whose test transmittance
  * would fall below T_min.  Returns the number of blended Gaussians.
@@ -389,7 +425,7 @@ typedef struct {
     int32_t *members; int max_members;   /* optional: I(p) in depth order, -1 padded */
     double *scale_q, *scale_dense;       /* optional: sum_j |w_j| max|f_j| (error denominators) */
     int32_t *n_dense;                    /* optional: entries the dense walk blended */
-    int rule;                            /* or_render_rule: RULE_TOPK or RULE_STRATIFIED */
+    int rule;                            /* or_render_rule: RULE_TOPK, RULE_STRATIFIED, RULE_RIEMANN */
     double *tau_out;                     /* or_render_rule: [npix][K] boundaries (stratified) */
     /* threading */
     int tid, nthreads; int status;
@@ -584,6 +620,7 @@ done:
 
 #define RULE_TOPK 1
 #define RULE_STRATIFIED 2
+#define RULE_RIEMANN 3
 
 /*
  * Near-tie classification for the two select rules of or_render_rule, with
@@ -658,8 +695,8 @@ static int classify_rule_ties(const render_job_t *J, const scratch_t *S, int rul
             }
             T = Tt;
         }
-    } else if (rule == RULE_STRATIFIED) {
-        /* uniform boundaries: the checks of classify_ties */
+    } else if (rule == RULE_STRATIFIED || rule == RULE_RIEMANN) {
+        /* uniform boundaries (Algorithm 1's): the checks of classify_ties */
         T = 1.0; E = 0.0;
         for (int64_t i = 0; i <= last_q && i < S->len; ++i) {
             const member_t *m = &S->m[i];
@@ -714,6 +751,13 @@ static int render_rule_pixel(render_job_t *J, scratch_t *S, int64_t p)
         D = 0.0;                             /* normalisation: divide by the kept sum */
         for (int64_t i = 0; i < S->len; ++i) D += S->w[i];
         Tq = 1.0 - D;
+    } else if (J->rule == RULE_RIEMANN) {
+        m = or_riemann_list(S->len, S->a, K, S->sel, S->w, &nproc);
+        nused = nproc;
+        D = 0.0;                             /* the boundaries crossed in all */
+        for (int64_t i = 0; i < S->len; ++i) D += S->w[i];
+        Tq = 1.0 - D / (double)(K + 1);
+        for (int k = 1; k <= K; ++k) tau[k - 1] = 1.0 - (double)k / (double)(K + 1);
     } else {
         m = or_stratified_list(S->len, S->a, K, J->T_min, S->sel, S->w, &Tq, &nproc, tau, stats);
         double Tf = 1.0;
@@ -722,7 +766,7 @@ static int render_rule_pixel(render_job_t *J, scratch_t *S, int64_t p)
             for (int k = 0; k < K; ++k) J->tau_out[p * K + k] = tau[k];
     }
     if (m < 0) { free(tau); return -1; }
-    if (J->rule != RULE_TOPK) D = 1.0 - Tq;
+    if (J->rule == RULE_STRATIFIED) D = 1.0 - Tq;
     if (J->cnt) J->cnt[p] = m;
     if (J->n_proc) J->n_proc[p] = (int32_t)nproc;
     if (J->tq) J->tq[p] = Tq;
@@ -927,7 +971,7 @@ int or_classify_rule_candidates(int64_t n, const double *depth, const int64_t *i
                                 double *tau)
 {
     if (n < 0 || K < 1 || !depth || !id || !g || !qabs ||
-        (rule != RULE_TOPK && rule != RULE_STRATIFIED))
+        (rule != RULE_TOPK && rule != RULE_STRATIFIED && rule != RULE_RIEMANN))
         return -1;
     render_job_t J;
     memset(&J, 0, sizeof(J));
@@ -956,7 +1000,9 @@ done:
 
 /*
  * Render the listed pixels with another select rule in place of Algorithm 1:
- * rule 1 = top-K (or_topk_list), rule 2 = Stratified-K (or_stratified_list).
+ * rule 1 = top-K (or_topk_list), rule 2 = Stratified-K (or_stratified_list),
+ * rule 3 = Algorithm 1's selection with the Riemann weights of App. C
+ * (or_riemann_list).
  * Outputs as or_render's Q-Render outputs (nullable): out [npix][C] (the kept
  * Gaussians' features with the rule's normalised weights), ids / wq [npix][K]
  * (depth order, -1 / 0 padded), cnt, n_members, n_proc (entries visited),
@@ -971,7 +1017,7 @@ int or_render_rule(int64_t n, const double *mean2d, const double *conic, const d
                    double *scale, double *tau)
 {
     if (n < 0 || npix < 0 || K < 1 || nthreads < 1 || C < 0 ||
-        (rule != RULE_TOPK && rule != RULE_STRATIFIED))
+        (rule != RULE_TOPK && rule != RULE_STRATIFIED && rule != RULE_RIEMANN))
         return OR_ERR_ARG;
     render_job_t base;
     memset(&base, 0, sizeof(base));

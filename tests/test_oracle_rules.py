@@ -190,3 +190,73 @@ def test_stratified_render_invariants():
         np.testing.assert_allclose(rr.out[p], rr.wq[p, :c] @ f[rr.ids[p, :c]].astype(np.float64),
                                    rtol=1e-12, atol=1e-12)
         assert (np.diff(rr.tau[p]) <= 0).all()
+
+
+# ----------------------------------------------------------------------- Riemann weights
+@pytest.mark.parametrize("K", [1, 2, 4, 8, 16, 32])
+def test_riemann_selection_is_algorithm_1_and_weights_count_crossings(K):
+    """App. C's right Riemann sum: the selection is Algorithm 1's, and each
+    kept Gaussian weighs the number of boundaries 1 - j/(K+1) that the
+    transmittance crosses at it -- written here with numpy's cumprod and a
+    direct count, independently of the oracle's walk."""
+    rng = np.random.default_rng(90 + K)
+    bounds = 1.0 - np.arange(1, K + 1) / (K + 1)
+    for trial in range(300):
+        n = int(rng.integers(0, 60))
+        a = _random_alphas(rng, n)
+        sel, w, nproc = oracle.riemann_list(a, K)
+        s1, _, _, np1 = oracle.qrender_list(a, K)
+        np.testing.assert_array_equal(sel, s1)
+        assert nproc == np1
+        T = np.concatenate([[1.0], np.cumprod(1.0 - a)])
+        crossed = lambda t: int((t < bounds).sum())  # noqa: E731
+        want = np.zeros(n)
+        for i in range(nproc):
+            want[i] = crossed(T[i + 1]) - crossed(T[i])
+        np.testing.assert_array_equal(w[sel], want[sel])
+        assert (w[~sel] == 0).all()
+        # every boundary crossed before the walk stops is counted once
+        assert w.sum() == crossed(T[nproc]) if nproc else w.sum() == 0
+        if nproc < n or (n and T[n] < 1.0 / (K + 1)):
+            assert w.sum() == K
+
+
+def test_riemann_special_cases():
+    # K = 1: one boundary, one kept Gaussian with weight 1 (Algorithm 1's as well)
+    a = np.array([0.2, 0.3, 0.5, 0.9])
+    sel, w, _ = oracle.riemann_list(a, 1)
+    assert sel.sum() == 1 and w[sel][0] == 1.0
+    # one Gaussian crossing every boundary at once takes all K counts
+    sel, w, nproc = oracle.riemann_list(np.array([0.95, 0.5]), 8)
+    assert sel.tolist() == [True, False] and w[0] == 8.0 and nproc == 1
+    # equal steps of one segment each: uniform weights
+    K = 4
+    T = 1.0 - (np.arange(1, K + 1) + 0.5) / (K + 1)       # one boundary between steps
+    a = 1.0 - T / np.concatenate([[1.0], T[:-1]])
+    sel, w, _ = oracle.riemann_list(a, K)
+    assert sel.all() and (w == 1.0).all()
+
+
+def test_riemann_render_invariants():
+    """Rendered with the rule: weights k_j / sum k, summing to 1, rational with
+    the boundaries crossed as denominator; ids equal Algorithm 1's."""
+    g, f = scenes.tiny_scene(seed=6, n=600, channels=4)
+    cam = scenes.tiny_camera(48, 48)
+    pr = oracle.project(g, cam.as_array())
+    pix = oracle.all_pixels(48, 48)
+    K = 8
+    rr = oracle.render_rule(pr, f, oracle.RULE_RIEMANN, K, pix, T_min=0.0)
+    ref = oracle.render(pr, f, K, pix, T_min=0.0)
+    np.testing.assert_array_equal(rr.ids, ref.ids)
+    np.testing.assert_array_equal(rr.cnt, ref.cnt)
+    assert (rr.cnt > 0).sum() > 200
+    for p in np.nonzero(rr.cnt > 0)[0]:
+        c = rr.cnt[p]
+        ws = rr.wq[p, :c]
+        assert abs(ws.sum() - 1.0) <= 1e-12
+        # some total D <= K of crossed boundaries makes every weight a whole count >= 1
+        ok = [D for D in range(1, K + 1)
+              if np.allclose(ws * D, np.round(ws * D), atol=1e-9) and (np.round(ws * D) >= 1).all()]
+        assert ok, ws
+        np.testing.assert_allclose(rr.out[p], ws @ f[rr.ids[p, :c]].astype(np.float64),
+                                   rtol=1e-12, atol=1e-12)

@@ -505,13 +505,15 @@ def _time_ms(fn, steps, warmup=2):
 
 def run_rules(ctx, steps=20):
     """The paper's other select rules on the headline frame: top-K (Sec. 4.2,
-    complexity table) and Stratified-K (App. E), each a whole frame (project,
-    sort, the rule's selection, blend), K = 8, beside Algorithm 1 and dense."""
+    complexity table), Stratified-K (App. E) and Algorithm 1 with App. C's
+    Riemann weights, each a whole frame (project, sort, the rule's selection,
+    blend), K = 8, beside Algorithm 1 and dense."""
     from paper_2512_20927_gb300 import qrender as q
     fr, gdev, fdev, ids, w, cnt, out = (ctx[k] for k in ("fr", "gdev", "fdev", "ids", "w", "cnt",
                                                           "out"))
     res = {}
-    for name, rule in (("topk", q.QR_RULE_TOPK), ("stratified", q.QR_RULE_STRATIFIED)):
+    for name, rule in (("topk", q.QR_RULE_TOPK), ("stratified", q.QR_RULE_STRATIFIED),
+                       ("riemann", q.QR_RULE_RIEMANN)):
         def frame():
             q.qr_project(fr, *gdev)
             q.qr_sort(fr)

@@ -182,7 +182,8 @@ qr_status qr_sort(qr_frame *frame, qr_stream stream);
 qr_status qr_select(const qr_frame *frame, int32_t *ids, float *weights, uint8_t *counts,
                     qr_stream stream);
 
-/* The select rules the paper weighs Algorithm 1 against, with the outputs of
+/* The select rules the paper weighs Algorithm 1 against, and App. C's weight
+ * form of Algorithm 1, with the outputs of
  * qr_select (ids [P][K] in depth order, -1 padded; weights [P][K]
  * normalised, zero padded; counts [P]), so qr_blend renders any of them.
  *   QR_RULE_QUANTILE:   Algorithm 1 (the same kernel as qr_select).
@@ -201,9 +202,19 @@ qr_status qr_select(const qr_frame *frame, int32_t *ids, float *weights, uint8_t
  *                       1 - k/(K+1) with fewer than two blended Gaussians);
  *                       pass 2 is Algorithm 1 with tau_k in place of
  *                       1 - k/(K+1), weights T^Q alpha' / (1 - T^Q).
+ *   QR_RULE_RIEMANN:    App. C's right-Riemann reading of Algorithm 1:
+ *                       qr_select's ids and counts; each quantile
+ *                       Gaussian weighs the number of boundaries
+ *                       1 - k/(K+1) its test transmittance crosses,
+ *                       divided by the number crossed in all.
  * tau [P][K] float32 (nullable; stratified only) receives each pixel's
  * boundaries.  K <= 32 (frame params). */
-typedef enum { QR_RULE_QUANTILE = 0, QR_RULE_TOPK = 1, QR_RULE_STRATIFIED = 2 } qr_rule;
+typedef enum {
+    QR_RULE_QUANTILE = 0,
+    QR_RULE_TOPK = 1,
+    QR_RULE_STRATIFIED = 2,
+    QR_RULE_RIEMANN = 3
+} qr_rule;
 qr_status qr_select_rule(const qr_frame *frame, qr_rule rule, int32_t *ids, float *weights,
                          uint8_t *counts, float *tau, qr_stream stream);
 

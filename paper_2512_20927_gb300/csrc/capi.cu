@@ -205,7 +205,8 @@ qr_status qr_select(const qr_frame *frame, int32_t *ids, float *weights, uint8_t
 qr_status qr_select_rule(const qr_frame *frame, qr_rule rule, int32_t *ids, float *weights,
                          uint8_t *counts, float *tau, qr_stream stream) {
     if (!frame_ok(frame) || !ids || !weights || !counts) return QR_ERR_INVALID_ARG;
-    if (rule != QR_RULE_QUANTILE && rule != QR_RULE_TOPK && rule != QR_RULE_STRATIFIED)
+    if (rule != QR_RULE_QUANTILE && rule != QR_RULE_TOPK && rule != QR_RULE_STRATIFIED &&
+        rule != QR_RULE_RIEMANN)
         return QR_ERR_INVALID_ARG;
     const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if (rule == QR_RULE_QUANTILE) return from_cuda(launch_select(*frame, ids, weights, counts, s));

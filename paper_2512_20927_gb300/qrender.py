@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(_HERE, "libqrender.so")
 QR_OK, QR_ERR_INVALID_ARG, QR_ERR_ALIGNMENT, QR_ERR_CAPACITY, QR_ERR_CUDA, \
     QR_ERR_DEVICE_TIMEOUT, QR_ERR_NOT_SUPPORTED = range(7)
 QR_F32, QR_BF16, QR_FP8E4M3 = 0, 1, 2
-QR_RULE_QUANTILE, QR_RULE_TOPK, QR_RULE_STRATIFIED = 0, 1, 2
+QR_RULE_QUANTILE, QR_RULE_TOPK, QR_RULE_STRATIFIED, QR_RULE_RIEMANN = 0, 1, 2, 3
 FRAME_SLOTS = 24
 
 
@@ -282,7 +282,8 @@ def qr_select(fr: Frame, ids, weights, counts, stream=None):
 
 
 def qr_select_rule(fr: Frame, rule, ids, weights, counts, tau=None, stream=None):
-    """Top-K / Stratified-K / Algorithm 1 selection into qr_select's outputs."""
+    """Top-K / Stratified-K / Riemann-weight / Algorithm 1 selection into
+    qr_select's outputs."""
     _check(load().qr_select_rule(ctypes.byref(fr.frame), int(rule), _ptr(ids), _ptr(weights),
                                  _ptr(counts), _ptr(tau), _stream(stream)), "qr_select_rule")
 

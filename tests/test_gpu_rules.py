@@ -1,5 +1,5 @@
-"""GPU parity of the top-K and Stratified-K select rules (qr_select_rule)
-against the FP64 oracle (or_render_rule), through the C ABI.
+"""GPU parity of the top-K, Stratified-K and Riemann-weight select rules
+(qr_select_rule) against the FP64 oracle (or_render_rule), through the C ABI.
 
 Same bar as Algorithm 1: kept ids and counts exact on every pixel the oracle
 does not flag (RULE_TIE_BITS: the rule's own decision, the alpha_min border,
@@ -66,8 +66,9 @@ def _run(g, f, cam, rule, K, pixels=None, params_kw=None, max_tie_frac=0.02, lab
     return rep
 
 
-RULES = [oracle.RULE_TOPK, oracle.RULE_STRATIFIED]
-NAMES = {oracle.RULE_TOPK: "topk", oracle.RULE_STRATIFIED: "stratified"}
+RULES = [oracle.RULE_TOPK, oracle.RULE_STRATIFIED, oracle.RULE_RIEMANN]
+NAMES = {oracle.RULE_TOPK: "topk", oracle.RULE_STRATIFIED: "stratified",
+         oracle.RULE_RIEMANN: "riemann"}
 
 
 @pytest.mark.parametrize("rule", RULES)
@@ -129,3 +130,34 @@ def test_empty_scene(rule):
                          rule=rule)
     torch.cuda.synchronize()
     assert (res["counts"] == 0).all() and (res["out"] == 0).all() and (res["ids"] == -1).all()
+
+
+@pytest.mark.parametrize("K", [1, 4, 8, 16, 32])
+def test_riemann_selection_is_algorithm_1(K):
+    """App. C changes Algorithm 1's weights only: on every pixel of a frame
+    the Riemann rule keeps qr_select's ids and counts bit for bit, its weights
+    sum to 1, and each is a crossing count c_j over the total D <= K."""
+    import torch
+    from paper_2512_20927_gb300 import qrender as q
+    g, f = H.small_room(n=20000, channels=16)
+    cam = scenes.room_camera(150, 110)
+    gdev = q.gaussians_to_device(g)
+    a = q.render_frame(gdev, None, cam, K=K)
+    b = q.render_frame(gdev, None, cam, K=K, rule=q.QR_RULE_RIEMANN)
+    torch.cuda.synchronize()
+    assert torch.equal(a["ids"], b["ids"]) and torch.equal(a["counts"], b["counts"])
+    w = b["weights"].cpu().numpy().astype(np.float64)
+    cnt = b["counts"].cpu().numpy().astype(np.int64)
+    kept = cnt > 0
+    assert kept.any()
+    assert np.abs(w[kept].sum(1) - 1.0).max() <= K * 2e-7
+    assert (w[~kept] == 0).all()
+    # some total D in counts..K makes every c_j = w_j D a positive integer
+    wk, ck = w[kept], cnt[kept]
+    found = np.zeros(len(wk), bool)
+    for D in range(1, K + 1):
+        c = wk * D
+        cj = np.rint(c)
+        ok = (np.abs(c - cj) <= 1e-5 * D).all(1) & ((cj >= 1) | (wk == 0)).all(1) & (ck <= D)
+        found |= ok
+    assert found.all()

@@ -206,16 +206,35 @@ def oracle_frames_per_s(g, feat, cam, budget_s: float, seed: int = 0, proj=None)
 
 def sample_parity(ids, counts, out, width, pix, ref):
     """Selections and features of the GPU frame on the oracle's sampled pixels:
-    near-tie pixels (oracle flags), mismatches off them (must be 0) and the
-    largest mixed relative feature error."""
+    near-tie pixels (oracle flags), per category (a test transmittance near a
+    segment boundary, alpha * G near alpha_min, equal neighbouring depths),
+    mismatches off them (must be 0) and the largest mixed relative feature
+    error."""
     from oracle import compare
     idx = pix[:, 1].astype(np.int64) * width + pix[:, 0]
     rep = compare.selection_report(ids[idx], np.zeros(ids[idx].shape), counts[idx], ref)
     same, tie = rep["same"], rep["tie"]
     err = compare.feature_error(out[idx], ref.out_q, ref.scale_q)
+    flags = np.asarray(ref.tie)
     return {"pixels": rep["pixels"], "near_tie_pixels": rep["tie_pixels"],
+            "near_tie_by_category": {"boundary": int(((flags & 1) != 0).sum()),
+                                     "alpha_min_border": int(((flags & 2) != 0).sum()),
+                                     "equal_depth": int(((flags & 4) != 0).sum())},
             "mismatch_nontie": rep["mismatch_nontie"],
             "feat_err_max": float(err[same].max()) if same.any() else None}
+
+
+def tile_distinct_rows(ids, width, tile_w, tile_h):
+    """U_tile: the sum over screen tiles of the distinct Gaussians selected in
+    the tile (each row read once per tile with perfect in-tile reuse), the
+    reuse diagnostic beside U (each row read once per frame)."""
+    import torch
+    P, K = ids.shape
+    pix = torch.arange(P, device=ids.device)
+    tiles_x = (width + tile_w - 1) // tile_w
+    tile = (pix // width // tile_h) * tiles_x + (pix % width) // tile_w
+    key = tile[:, None].to(torch.int64) * (1 << 32) + ids.to(torch.int64)
+    return int(torch.unique(key[ids >= 0]).numel())
 
 
 # --------------------------------------------------------------------------- GPU arm
@@ -242,6 +261,7 @@ def run_gpu(args, ws, rank, local):
     ids, w, cnt, out = res["ids"], res["weights"], res["counts"], res["out"]
     dout, tf = res["dense"], res["T_final"]
     U = int(torch.unique(ids[ids >= 0]).numel())
+    U_tile = tile_distinct_rows(ids, WIDTH, 16, 16)
     sel_per_px = float(cnt.float().mean().item())
 
     def q_frame():
@@ -481,7 +501,8 @@ def run_gpu(args, ws, rank, local):
                      "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
                      "frac": round(achieved / hbm_peak, 4), "peak_source": peak_src,
                      "traffic": traffic, "algorithmic_bytes": int(alg_bytes),
-                     "distinct_rows": U, "selected_per_px": round(sel_per_px, 3)},
+                     "distinct_rows": U, "distinct_rows_per_tile_sum": U_tile,
+                     "selected_per_px": round(sel_per_px, 3)},
         "_g": g, "_feat": feat, "_cam": cam,
     }
 
@@ -586,7 +607,9 @@ def run_object(local, hbm_peak, steps=20):
     return {"workload": "object-centric FP32: 500k Gaussians (70 % within 1 cm of a unit sphere, "
                         "30 % inside), 640x480 from 2.6 m, 512-D, Q-Render K=8",
             "fps": round(1000.0 / ms, 2), "ms": round(ms, 4), "blend_ms": round(blend_ms, 4),
-            "distinct_rows": U, "selected_per_px": round(float(cnt.float().mean().item()), 3),
+            "distinct_rows": U,
+            "distinct_rows_per_tile_sum": tile_distinct_rows(ids, fr.width, 16, 16),
+            "selected_per_px": round(float(cnt.float().mean().item()), 3),
             "n_isect": int(res["n_isect"]),
             "blend_roofline": {"achieved": round(alg / blend_ms / 1e6, 1), "peak": hbm_peak,
                                "unit": "GB/s", "frac": round(alg / blend_ms / 1e6 / hbm_peak, 4),

@@ -376,13 +376,15 @@ __device__ void bitonic_regs(KT (&v)[E], KT *s) {
     for (int k = 2; k <= N; k <<= 1) {
         const bool up = (base & k) == 0;
         for (int j = k >> 1; j >= 32 * E; j >>= 1) {
+            // exchange through s element-major (key e of thread t at e NTH + t):
+            // a warp's accesses are consecutive words, free of bank conflicts
 #pragma unroll
-            for (int e = 0; e < E; ++e) s[base + e] = v[e];
+            for (int e = 0; e < E; ++e) s[e * NTH + threadIdx.x] = v[e];
             __syncthreads();
             const bool take_min = ((base & j) == 0) == up;
-            const KT *partner = s + (base ^ j);
+            const KT *partner = s + (threadIdx.x ^ (j / E));
 #pragma unroll
-            for (int e = 0; e < E; ++e) v[e] = key_pick(v[e], partner[e], take_min);
+            for (int e = 0; e < E; ++e) v[e] = key_pick(v[e], partner[e * NTH], take_min);
             __syncthreads();
         }
         for (int j = min(k >> 1, 16 * E); j >= E; j >>= 1) {

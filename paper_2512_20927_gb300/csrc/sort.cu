@@ -43,7 +43,8 @@ namespace {
 constexpr int T = 256;
 constexpr int EMIT_CHUNK = kEmitChunk;
 constexpr int TB = 1024;                 // threads of the big-bucket sort
-constexpr int BIG_CAP = 8192;            // keys a big bucket sorts in shared memory (2 x 64 KB)
+constexpr int BIG_CAP = 8192;            // keys a big bucket sorts in shared memory (2 x 68 KB)
+constexpr int BIG_SLOTS = BIG_CAP + BIG_CAP / 16;   // with one pad word per 16 keys
 constexpr int kScanSmemTiles = 48 * 1024; // tile counts bin_scan integrates in shared memory
 constexpr int kAggTiles = 4096;           // tile grids whose bucket claims are aggregated per CTA
 
@@ -366,23 +367,28 @@ __device__ __forceinline__ void sort8(unsigned long long (&v)[8]) {
     cx(v[1], v[2]); cx(v[3], v[4]); cx(v[5], v[6]);
 }
 
-// Sort n <= TB * E unique keys in shared memory: runs of 8 sorted in
-// registers, then merge rounds of doubling run length L between the two
-// buffers s and t.  In a round thread i produces outputs [iE, iE + E) of its
-// pair of runs (2L is a multiple of E, so the range never crosses pairs): a
-// merge-path binary search gives its start in each run and the E outputs are
-// merged straight into the other buffer.  Returns the buffer holding the
+// Shared-memory slot of key i in a big-bucket buffer: one pad word after
+// every 16 keys.  Threads that own E consecutive keys (E = 2..16) then touch
+// 16 different bank pairs per half-warp instead of 16 / E.
+__device__ __forceinline__ int pad(int i) { return i + (i >> 4); }
+
+// Sort n <= TB * E unique keys in shared memory (padded slots): runs of 8
+// sorted in registers, then merge rounds of doubling run length L between the
+// two buffers s and t.  In a round thread i produces outputs [iE, iE + E) of
+// its pair of runs (2L is a multiple of E, so the range never crosses pairs):
+// a merge-path binary search gives its start in each run and the E outputs
+// are merged straight into the other buffer.  Returns the buffer holding the
 // sorted keys.
 template <int E>
 __device__ unsigned long long *sort_smem(unsigned long long *s, unsigned long long *t, int n) {
     for (int r0 = int(threadIdx.x) * 8; r0 < n; r0 += TB * 8) {
         unsigned long long v[8];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) v[e] = r0 + e < n ? s[r0 + e] : ~0ull;
+        for (int e = 0; e < 8; ++e) v[e] = r0 + e < n ? s[pad(r0 + e)] : ~0ull;
         sort8(v);
 #pragma unroll
         for (int e = 0; e < 8; ++e)
-            if (r0 + e < n) s[r0 + e] = v[e];
+            if (r0 + e < n) s[pad(r0 + e)] = v[e];
     }
     __syncthreads();
     const int d0 = int(threadIdx.x) * E;
@@ -392,17 +398,19 @@ __device__ unsigned long long *sort_smem(unsigned long long *s, unsigned long lo
             const int ps = d0 & ~(2 * L - 1);
             const int na = min(L, n - ps);
             const int nb = max(0, min(L, n - ps - na));
-            const unsigned long long *a = s + ps, *b = a + na;
+            const int pb = ps + na;   // run A is keys [ps, pb), run B [pb, pb + nb)
             const int diag = d0 - ps;
             int lo = max(0, diag - nb), hi = min(diag, na);
             while (lo < hi) {
                 const int mid = (lo + hi) >> 1;
-                if (a[mid] < b[diag - 1 - mid]) lo = mid + 1; else hi = mid;
+                if (s[pad(ps + mid)] < s[pad(pb + diag - 1 - mid)]) lo = mid + 1; else hi = mid;
             }
             int i = lo, j = diag - lo;
             for (int e = 0; e < m; ++e) {
-                const bool take_a = j >= nb || (i < na && a[i] < b[j]);
-                t[d0 + e] = take_a ? a[i] : b[j];
+                const unsigned long long ka = i < na ? s[pad(ps + i)] : ~0ull;
+                const unsigned long long kb = j < nb ? s[pad(pb + j)] : ~0ull;
+                const bool take_a = j >= nb || (i < na && ka < kb);
+                t[pad(d0 + e)] = take_a ? ka : kb;
                 i += take_a ? 1 : 0;
                 j += take_a ? 0 : 1;
             }
@@ -423,7 +431,7 @@ __device__ __forceinline__ unsigned long long *sort_smem_any(unsigned long long 
 }
 
 // The buckets of more than 8 T keys, listed by tile_sort: persistent CTAs of
-// TB threads (one per SM: 128 KB of shared memory) take them in turn.  Up to
+// TB threads (one per SM: 136 KB of shared memory) take them in turn.  Up to
 // BIG_CAP keys are merge-sorted in shared memory (faster here than the
 // register bitonic network over 1024 threads: 232 vs 365 us for the object
 // frame's sort stage); a larger bucket is sorted in BIG_CAP chunks whose
@@ -435,27 +443,27 @@ tile_sort_big(const uint2 *__restrict__ ranges, unsigned long long *__restrict__
               unsigned long long *__restrict__ scratch, uint32_t *__restrict__ igid,
               const uint32_t *__restrict__ big, const uint32_t *__restrict__ counters) {
     pdl_wait();   // the predecessor's outputs are complete and visible
-    extern __shared__ unsigned long long s_k[];   // 2 x BIG_CAP keys
-    unsigned long long *s_t = s_k + BIG_CAP;
+    extern __shared__ unsigned long long s_k[];   // 2 x BIG_SLOTS (padded slots)
+    unsigned long long *s_t = s_k + BIG_SLOTS;
     const uint32_t nbig = counters[CNT_BIG];
     for (uint32_t bi = blockIdx.x; bi < nbig; bi += gridDim.x) {
         const uint2 r = ranges[big[bi]];
         const int n = int(r.y - r.x);
         unsigned long long *src = keys + r.x;
         if (n <= BIG_CAP) {
-            for (int i = threadIdx.x; i < n; i += TB) s_k[i] = src[i];
+            for (int i = threadIdx.x; i < n; i += TB) s_k[pad(i)] = src[i];
             __syncthreads();
             const unsigned long long *o = sort_smem_any(s_k, s_t, n);
-            for (int i = threadIdx.x; i < n; i += TB) igid[r.x + i] = uint32_t(o[i]);
+            for (int i = threadIdx.x; i < n; i += TB) igid[r.x + i] = uint32_t(o[pad(i)]);
             __syncthreads();
             continue;
         }
         for (int c0 = 0; c0 < n; c0 += BIG_CAP) {
             const int m = min(BIG_CAP, n - c0);
-            for (int i = threadIdx.x; i < m; i += TB) s_k[i] = src[c0 + i];
+            for (int i = threadIdx.x; i < m; i += TB) s_k[pad(i)] = src[c0 + i];
             __syncthreads();
             const unsigned long long *o = sort_smem_any(s_k, s_t, m);
-            for (int i = threadIdx.x; i < m; i += TB) src[c0 + i] = o[i];
+            for (int i = threadIdx.x; i < m; i += TB) src[c0 + i] = o[pad(i)];
             __syncthreads();
         }
         unsigned long long *a = src, *dst = scratch + r.x;
@@ -490,7 +498,7 @@ cudaError_t launch_sort(const qr_frame &f, cudaStream_t s) {
         return e;
     }
     e = cudaFuncSetAttribute(tile_sort_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             int(2 * BIG_CAP * sizeof(unsigned long long)));
+                             int(2 * BIG_SLOTS * sizeof(unsigned long long)));
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
@@ -536,7 +544,7 @@ cudaError_t launch_sort(const qr_frame &f, cudaStream_t s) {
                    slot<uint32_t>(f, S_IGID), tcnt, counters);
     if (e != cudaSuccess) return e;
     e = pdl_launch(tile_sort_big, dim3(unsigned(min(tiles, sms))), dim3(TB),
-                   2 * BIG_CAP * sizeof(unsigned long long), s,
+                   2 * BIG_SLOTS * sizeof(unsigned long long), s,
                    (const uint2 *)ranges, keys, slot<unsigned long long>(f, S_SCRATCH64),
                    slot<uint32_t>(f, S_IGID), (const uint32_t *)tcnt, (const uint32_t *)counters);
     count_launch(5);

@@ -988,8 +988,8 @@ def profile_mode(local, mode, steps):
     """Workload set up once, then `steps` eager launches of one part of it, for
     ncu captures: indoor / object (a whole Q-Render frame: project, sort,
     select, blend), blend, fused (blend + relevance in one kernel), eq2 (the
-    Eq. 2 loss and its gradient, 32 patches), rules (top-K then Stratified-K
-    selection), dense (Eq. 1), blend_bf16 / blend_fp8 (the blend from a BF16
+    Eq. 2 loss and its gradient, 32 patches), rules (top-K, Stratified-K,
+    then Riemann-weight selection), dense (Eq. 1), blend_bf16 / blend_fp8 (the blend from a BF16
     table / FP8 E4M3 codes with per-Gaussian scales, tile-ordered pixel
     groups) -- on the 500k indoor room (object: the object
     scene), 640x480, 512-D FP32, K = 8; batch: the many-view launch on a small
@@ -1057,6 +1057,7 @@ def profile_mode(local, mode, steps):
         elif mode == "rules":
             q.qr_select_rule(fr, q.QR_RULE_TOPK, ids, w, cnt)
             q.qr_select_rule(fr, q.QR_RULE_STRATIFIED, ids, w, cnt)
+            q.qr_select_rule(fr, q.QR_RULE_RIEMANN, ids, w, cnt)
         elif mode == "dense":
             q.qr_dense(fr, fd, None, dout, tf)
     torch.cuda.synchronize()

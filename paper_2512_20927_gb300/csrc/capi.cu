@@ -199,7 +199,8 @@ qr_status qr_sort(qr_frame *frame, qr_stream stream) {
 qr_status qr_select(const qr_frame *frame, int32_t *ids, float *weights, uint8_t *counts,
                     qr_stream stream) {
     if (!frame_ok(frame) || !ids || !weights || !counts) return QR_ERR_INVALID_ARG;
-    return from_cuda(launch_select(*frame, ids, weights, counts, reinterpret_cast<cudaStream_t>(stream)));
+    return from_cuda(launch_select(*frame, ids, weights, counts, false,
+                                   reinterpret_cast<cudaStream_t>(stream)));
 }
 
 qr_status qr_select_rule(const qr_frame *frame, qr_rule rule, int32_t *ids, float *weights,
@@ -209,7 +210,8 @@ qr_status qr_select_rule(const qr_frame *frame, qr_rule rule, int32_t *ids, floa
         rule != QR_RULE_RIEMANN)
         return QR_ERR_INVALID_ARG;
     const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    if (rule == QR_RULE_QUANTILE) return from_cuda(launch_select(*frame, ids, weights, counts, s));
+    if (rule == QR_RULE_QUANTILE || rule == QR_RULE_RIEMANN)
+        return from_cuda(launch_select(*frame, ids, weights, counts, rule == QR_RULE_RIEMANN, s));
     return from_cuda(launch_select_rule(*frame, int(rule), ids, weights, counts,
                                         rule == QR_RULE_STRATIFIED ? tau : nullptr, s));
 }
@@ -279,7 +281,7 @@ qr_status qr_render(qr_frame *frame, const float *mean, const float *log_scale,
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e = launch_project(*frame, mean, log_scale, quat, opacity, s);
     if (e == cudaSuccess) e = launch_sort(*frame, s);
-    if (e == cudaSuccess) e = launch_select(*frame, ids, weights, counts, s);
+    if (e == cudaSuccess) e = launch_select(*frame, ids, weights, counts, false, s);
     if (e == cudaSuccess)
         e = launch_blend_tiled(feat, feat_scale, dtype, C, frame->n > 0 ? frame->n : 1, ids, weights,
                                counts, num_pixels(*frame), frame->params.K, 0, 0, out, s);

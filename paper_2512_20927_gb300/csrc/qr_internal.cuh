@@ -80,7 +80,7 @@ inline int32_t num_tiles(const qr_frame &f) { return f.tiles_x * f.tiles_y; }
 cudaError_t launch_project(const qr_frame &f, const float *mean, const float *log_scale,
                            const float *quat, const float *opacity, cudaStream_t s);
 cudaError_t launch_sort(const qr_frame &f, cudaStream_t s);
-cudaError_t launch_select(const qr_frame &f, int32_t *ids, float *w, uint8_t *cnt,
+cudaError_t launch_select(const qr_frame &f, int32_t *ids, float *w, uint8_t *cnt, bool riemann,
                           cudaStream_t s);
 // stats (nullable, wide rows only): [0] += blended (pixel, Gaussian) pairs,
 // [1] += executed (8-pixel group, entry) pairs of the accumulation
@@ -327,18 +327,23 @@ struct Walk {
 
 // The rarely taken end of an Algorithm 1 step, for a member entry (alpha' >=
 // alpha_min) whose T_test = Tt crosses the next quantile boundary or the stop
-// threshold: keep the Gaussian, advance k, stop.
+// threshold: keep the Gaussian, advance k, stop.  The kept weight is
+// T^Q alpha' (Algorithm 1), or with kCount the number of boundaries Tt
+// crosses (App. C's right-Riemann weights, one segment width per boundary).
+template <bool kCount = false>
 __device__ __forceinline__ void walk_event(Walk &w, float Tt, float a, float tau_stop, int K,
                                         uint32_t gid, int slot, int KS, int32_t *s_ids, float *s_w) {
     if (Tt < w.thr) {
+        const int k0 = w.k;
         s_ids[slot * KS + w.m] = int32_t(gid);
-        s_w[slot * KS + w.m] = w.TQ * a;
+        if constexpr (!kCount) s_w[slot * KS + w.m] = w.TQ * a;
         ++w.m;
         w.TQ = w.TQ * (1.0f - a);
         do {
             ++w.k;
             w.thr = (w.k < K) ? __fdiv_rn(float(K - w.k), float(K + 1)) : -1.0f;
         } while (Tt < w.thr);
+        if constexpr (kCount) s_w[slot * KS + w.m - 1] = float(w.k - k0);
     }
     if (Tt < tau_stop) w.done = true;
     else w.T = Tt;

@@ -1,6 +1,6 @@
-// The other select rules of the paper, behind the same outputs as the
+// The two other select rules of the paper, behind the same outputs as the
 // Algorithm 1 selection (ids [P][K] in depth order, normalised weights
-// [P][K], counts [P]), so the blend serves all of them:
+// [P][K], counts [P]), so the blend serves all three:
 //
 //   top-K (Sec. 4.2 and the complexity table, the renderer Q-Render is
 //   compared against): the K largest Eq. 1 weights w = T alpha' of the dense
@@ -14,12 +14,10 @@
 //   probability of N(mu, sigma^2) over the transmittance interval [0, 1]
 //   and mapped back (tau_k = mu + sigma Phi^-1(u_lo + (u_hi - u_lo)(1 -
 //   k/(K+1))), u_lo = Phi(-mu/sigma), u_hi = Phi((1-mu)/sigma)); pass 2 is
-//   Algorithm 1 with tau_k in place of 1 - k/(K+1);
+//   Algorithm 1 with tau_k in place of 1 - k/(K+1).
 //
-//   Riemann weights (App. C, Algorithm 1 read as a right Riemann sum over
-//   K + 1 equal transmittance segments): Algorithm 1's walk and selection,
-//   each quantile Gaussian weighted by the number of boundaries 1 - k/(K+1)
-//   its test transmittance crosses, divided by the number crossed in all.
+// (App. C's Riemann-weight form of Algorithm 1 keeps Algorithm 1's
+// selection, so it runs in the selection kernel itself, select.cu.)
 //
 // GB300 design: one CTA per screen tile, one thread per pixel (256).  The
 // tile's depth-ordered list is staged through shared memory 256 records at
@@ -37,9 +35,6 @@
 //     mu and sigma from them, and the boundaries with the FP32 normal CDF and
 //     its inverse (normcdff, normcdfinvf); the boundaries sit in shared memory
 //     for pass 2, which re-walks the list.
-//   * the Riemann form is pass 2 alone on Algorithm 1's boundaries, computed
-//     as the Algorithm 1 selection computes them, so its selection is that
-//     kernel's bit for bit.
 #include "qr_internal.cuh"
 
 namespace qr {
@@ -49,7 +44,7 @@ constexpr int kPix = 256;
 constexpr int kThreads = 256;
 constexpr int kBatch = 256;
 
-enum { kTopK = 1, kStratified = 2, kRiemann = 3 };
+enum { kTopK = 1, kStratified = 2 };
 
 struct Stage {
     float4 *m, *c;
@@ -122,7 +117,7 @@ rule_kernel(const float4 *__restrict__ rec_m, const float4 *__restrict__ rec_w,
     const int KS = K | 1;   // odd stride: a thread's slots fall in their own banks
     uint32_t *s_key = reinterpret_cast<uint32_t *>(s_dyn);                 // [256][KS]
     float *s_w = reinterpret_cast<float *>(s_dyn) + KS * kPix;             // [256][KS]
-    float *s_tau = reinterpret_cast<float *>(s_dyn) + 2 * KS * kPix;       // [256][KS] (stratified only)
+    float *s_tau = reinterpret_cast<float *>(s_dyn) + 2 * KS * kPix;       // [256][KS] (stratified)
     const Stage st{s_m, s_c, s_a, s_h};
 
     const int tile = blockIdx.x;
@@ -195,7 +190,7 @@ rule_kernel(const float4 *__restrict__ rec_m, const float4 *__restrict__ rec_w,
         }
         for (int j = 0; j < m; ++j) D = __fadd_rn(D, my_w[j]);
         for (int j = 0; j < m; ++j) my_key[j] = isect_gid[my_key[j]];
-    } else if (RULE == kStratified) {
+    } else {
         // ---- pass 1: transmittance statistics of the dense walk
         float T = 1.0f;
         df s1 = df_from(0.0f), s2 = df_from(0.0f);
@@ -230,35 +225,28 @@ rule_kernel(const float4 *__restrict__ rec_m, const float4 *__restrict__ rec_w,
         } else {
             for (int k = 1; k <= K; ++k) my_tau[k - 1] = __fdiv_rn(float(K + 1 - k), float(K + 1));
         }
-    }
-    if (RULE != kTopK) {
-        // ---- pass 2: Algorithm 1 with the boundaries tau_k (Riemann: the
-        // uniform ones, (K - k)/(K + 1) for index k as the selection forms them)
-        auto tau = [&](int k) -> float {
-            return RULE == kStratified ? my_tau[k] : __fdiv_rn(float(K - k), float(K + 1));
-        };
+        // ---- pass 2: Algorithm 1 with the boundaries tau_k
         float T2 = 1.0f, TQ = 1.0f;
         int k = 0;
-        const float tau_stop = tau(K - 1);
+        const float tau_stop = my_tau[K - 1];
         bool done2 = !inside;
         walk_list(rec_m, rec_w, rec_a, rec_h, isect_gid, range, st, ux, uy, bx0, bx1, by0, by1,
                   alpha_min, alpha_max, done2, [&](uint32_t pos, float a) -> bool {
                       const float Tt = __fmul_rn(T2, __fsub_rn(1.0f, a));
-                      if (k < K && Tt < tau(k)) {
-                          const int k0 = k;
+                      if (k < K && Tt < my_tau[k]) {
                           my_key[m] = isect_gid[pos];
-                          do {
-                              ++k;
-                          } while (k < K && Tt < tau(k));
-                          my_w[m] = RULE == kRiemann ? float(k - k0) : __fmul_rn(TQ, a);
+                          my_w[m] = __fmul_rn(TQ, a);
                           ++m;
                           TQ = __fmul_rn(TQ, __fsub_rn(1.0f, a));
+                          do {
+                              ++k;
+                          } while (k < K && Tt < my_tau[k]);
                       }
                       if (Tt < tau_stop) return true;
                       T2 = Tt;
                       return false;
                   });
-        D = RULE == kRiemann ? float(k) : __fsub_rn(1.0f, TQ);
+        D = __fsub_rn(1.0f, TQ);
     }
 
     // ---- outputs (a pixel outside the image writes nothing)
@@ -299,9 +287,7 @@ cudaError_t launch_select_rule(const qr_frame &f, int rule, int32_t *ids, float 
                           f.camera.height, f.params.tile_w, f.tiles_x, K, f.params.alpha_min,
                           f.params.alpha_max, f.params.T_min, ids, w, cnt, tau);
     };
-    const cudaError_t e = rule == kTopK         ? go(rule_kernel<kTopK>)
-                          : rule == kStratified ? go(rule_kernel<kStratified>)
-                                                : go(rule_kernel<kRiemann>);
+    const cudaError_t e = rule == kTopK ? go(rule_kernel<kTopK>) : go(rule_kernel<kStratified>);
     count_launch();
     return e != cudaSuccess ? e : cudaGetLastError();
 }

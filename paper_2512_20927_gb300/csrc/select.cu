@@ -10,7 +10,10 @@
 //       advance k past every boundary T_test is below;
 //   stop once T_test < 1/(K+1); otherwise T = T_test.
 // Outputs are the kept ids in depth order and the weights divided by
-// 1 - T^Q (the normalisation step folded into the weights).
+// 1 - T^Q (the normalisation step folded into the weights).  The same kernel
+// serves App. C's Riemann-weight form (QR_RULE_RIEMANN): the same selection,
+// each kept Gaussian weighted by the number of boundaries T_test crosses at
+// it, divided by the number crossed in all.
 //
 // GB300 design: one CTA of 128 threads per screen tile; the walk itself
 // (select_tile.cuh) stages the tile's list through shared memory, culls it
@@ -23,6 +26,8 @@
 namespace qr {
 namespace {
 
+// kCount: App. C's Riemann weights in place of Algorithm 1's (select_tile).
+template <bool kCount>
 __global__ void __launch_bounds__(kSelThreads, 8)
 select_kernel(const float4 *__restrict__ rec_m, const float4 *__restrict__ rec_w,
               const float *__restrict__ rec_a, const float *__restrict__ rec_h,
@@ -40,7 +45,7 @@ select_kernel(const float4 *__restrict__ rec_m, const float4 *__restrict__ rec_w
     const int tile = blockIdx.x;
     const int tx = tile % tiles_x, ty = tile / tiles_x;
     const int tile_h = kSelPix / tile_w;
-    select_tile<CtaBarrier>(rec_m, rec_w, rec_a, rec_h, isect_gid, ranges[tile], W, H, tile_w, tx,
+    select_tile<CtaBarrier, kCount>(rec_m, rec_w, rec_a, rec_h, isect_gid, ranges[tile], W, H, tile_w, tx,
                             ty, K, alpha_min, alpha_max, st, s_ids, s_w, s_D, s_cnt);
     __syncthreads();
     // coalesced output: each row of the tile is tile_w * K consecutive entries
@@ -68,23 +73,29 @@ select_kernel(const float4 *__restrict__ rec_m, const float4 *__restrict__ rec_w
 
 }  // namespace
 
-cudaError_t launch_select(const qr_frame &f, int32_t *ids, float *w, uint8_t *cnt,
+cudaError_t launch_select(const qr_frame &f, int32_t *ids, float *w, uint8_t *cnt, bool riemann,
                           cudaStream_t s) {
     const int tiles = num_tiles(f);
     if (tiles == 0) return cudaSuccess;
     const int K = f.params.K;
     const size_t dyn = size_t(K | 1) * kSelPix * 8;
-    if (dyn > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             int(dyn));
-        if (e != cudaSuccess) return e;
-    }
-    cudaError_t e = pdl_launch(
-        select_kernel, dim3(tiles), dim3(kSelThreads), dyn, s, (const float4 *)slot<float4>(f, S_REC_M),
-        (const float4 *)slot<float4>(f, S_REC_C), (const float *)slot<float>(f, S_REC_A),
-        (const float *)slot<float>(f, S_REC_H), (const uint32_t *)slot<uint32_t>(f, S_IGID),
-        (const uint2 *)slot<uint2>(f, S_RANGES), f.camera.width, f.camera.height, f.params.tile_w,
-        f.tiles_x, K, f.params.alpha_min, f.params.alpha_max, ids, w, cnt);
+    auto go = [&](auto kern) -> cudaError_t {
+        if (dyn > 48 * 1024) {
+            const cudaError_t e =
+                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(dyn));
+            if (e != cudaSuccess) return e;
+        }
+        return pdl_launch(kern, dim3(tiles), dim3(kSelThreads), dyn, s,
+                          (const float4 *)slot<float4>(f, S_REC_M),
+                          (const float4 *)slot<float4>(f, S_REC_C),
+                          (const float *)slot<float>(f, S_REC_A),
+                          (const float *)slot<float>(f, S_REC_H),
+                          (const uint32_t *)slot<uint32_t>(f, S_IGID),
+                          (const uint2 *)slot<uint2>(f, S_RANGES), f.camera.width,
+                          f.camera.height, f.params.tile_w, f.tiles_x, K, f.params.alpha_min,
+                          f.params.alpha_max, ids, w, cnt);
+    };
+    const cudaError_t e = riemann ? go(select_kernel<true>) : go(select_kernel<false>);
     count_launch();
     return e != cudaSuccess ? e : cudaGetLastError();
 }

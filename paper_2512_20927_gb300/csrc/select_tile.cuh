@@ -94,8 +94,11 @@ __device__ __forceinline__ float2 sel_fma2(float2 a, float2 b, float2 c) {
 // Walks tile (tx, ty) whose depth-ordered ids are isect_gid[range.x, range.y).
 // Called by threads 0..127 (all of them); ends with the per-pixel results in
 // s_ids / s_w / s_D / s_cnt, written by their owners (the caller joins the
-// threads with Bar::sync() before reading other pixels' slots).
-template <class Bar>
+// threads with Bar::sync() before reading other pixels' slots).  With
+// kCount the weights are boundary-crossing counts and s_D the number of
+// boundaries crossed in all (App. C's Riemann weights); the selection is the
+// same.
+template <class Bar, bool kCount = false>
 __device__ __forceinline__ void select_tile(const float4 *__restrict__ rec_m,
                                             const float4 *__restrict__ rec_w,
                                             const float *__restrict__ rec_a,
@@ -213,8 +216,8 @@ __device__ __forceinline__ void select_tile(const float4 *__restrict__ rec_m,
                     const bool e1 = t1 && (Tt.y < w1.thr || Tt.y < tau_stop);
                     if (e0 || e1) {
                         const uint32_t gid = st.g[jj[u]];
-                        if (e0) walk_event(w0, Tt.x, a0, tau_stop, K, gid, slot0, KS, s_ids, s_w);
-                        if (e1) walk_event(w1, Tt.y, a1, tau_stop, K, gid, slot1, KS, s_ids, s_w);
+                        if (e0) walk_event<kCount>(w0, Tt.x, a0, tau_stop, K, gid, slot0, KS, s_ids, s_w);
+                        if (e1) walk_event<kCount>(w1, Tt.y, a1, tau_stop, K, gid, slot1, KS, s_ids, s_w);
                     }
                     if (t0 && !e0) w0.T = Tt.x;
                     if (t1 && !e1) w1.T = Tt.y;
@@ -223,8 +226,8 @@ __device__ __forceinline__ void select_tile(const float4 *__restrict__ rec_m,
             }
         }
     }
-    s_D[slot0] = 1.0f - w0.TQ;
-    s_D[slot1] = 1.0f - w1.TQ;
+    s_D[slot0] = kCount ? float(w0.k) : 1.0f - w0.TQ;
+    s_D[slot1] = kCount ? float(w1.k) : 1.0f - w1.TQ;
     s_cnt[slot0] = uint8_t(w0.m);
     s_cnt[slot1] = uint8_t(w1.m);
 }

@@ -1,5 +1,6 @@
-"""Pins of the oracle's two other select rules: top-K (the comparison renderer
-of Sec. 4.2 and the complexity table) and Stratified-K (App. E).
+"""Pins of the oracle's other select rules: top-K (the comparison renderer of
+Sec. 4.2 and the complexity table), Stratified-K (App. E) and the
+Riemann-weight form of Algorithm 1 (App. C).
 
 Top-K is pinned against a full stable sort of the Eq. 1 weights (the oracle
 keeps a running set of K instead), against the dense blend when K covers the
@@ -8,7 +9,10 @@ properties, each checked with independent tools: pass 1's mean and standard
 deviation equal numpy's over the dense walk's transmittances (numpy cumprod),
 the boundaries are equally spaced in scipy's normal CDF over [0, 1], the
 selection equals the closed form "visited and the count of boundaries above T
-grows", and with fewer than two blended Gaussians it is Algorithm 1.
+grows", and with fewer than two blended Gaussians it is Algorithm 1.  The
+Riemann-weight form (App. C) is pinned to Algorithm 1's selection, to a numpy
+count of the boundaries crossed, to special cases, and to App. C's own error
+bound M / (2 (K + 1)) on a smooth integrand.
 """
 import numpy as np
 import pytest
@@ -260,3 +264,39 @@ def test_riemann_render_invariants():
         assert ok, ws
         np.testing.assert_allclose(rr.out[p], ws @ f[rr.ids[p, :c]].astype(np.float64),
                                    rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("K", [1, 2, 4, 8, 16, 32])
+def test_riemann_within_app_c_error_bound(K):
+    """App. C's theorem for the right-Riemann reading: with c(u) the feature
+    of the Gaussian covering transmittance u and |c'| <= M, one sample per
+    segment of width 1/(K+1), normalised by the width covered, lies within
+    M / (2 (K + 1)) of the mean of c over that width.  A list of many small
+    steps (each at most delta) carrying features g(u) = (sin 3u, cos 2u, u^2)
+    at the step's midpoint makes c a step approximation of g, so the oracle's
+    Riemann estimate must be within M / (2 (K + 1)) + M delta of the exact
+    mean of g over [u_D, 1] (closed-form antiderivatives), u_D the last
+    boundary crossed."""
+    n = 4000
+    T = np.concatenate([[1.0], 1.0 - (1.0 - 1e-3) * np.arange(1, n + 1) / n])
+    a = 1.0 - T[1:] / T[:-1]
+    mid = 0.5 * (T[1:] + T[:-1])
+    g = np.stack([np.sin(3 * mid), np.cos(2 * mid), mid ** 2], 1)
+    M = np.array([3.0, 2.0, 2.0])
+    delta = (1.0 - 1e-3) / n
+    sel, w, _ = oracle.riemann_list(a, K)
+    D = w.sum()
+    assert D == K                       # the walk ends below 1/(K+1) > 1e-3
+    R = (w[:, None] * g).sum(0) / D
+    lo = 1.0 - D / (K + 1)
+    G = lambda u: np.stack([-np.cos(3 * u) / 3, np.sin(2 * u) / 2, u ** 3 / 3], -1)
+    mean = (G(1.0) - G(lo)) / (1.0 - lo)
+    err = np.abs(R - mean)
+    assert (err <= M / (2 * (K + 1)) + M * delta + 1e-12).all(), (K, err)
+    # the bound is met with the sample at each segment's crossing, not with a
+    # sample one segment late (a misplaced crossing count breaks it at K >= 4)
+    if K >= 4:
+        idx = np.nonzero(sel)[0]
+        late = g[np.minimum(idx + int(1.0 / ((K + 1) * delta)), n - 1)]
+        R_late = (w[idx, None] * late).sum(0) / D
+        assert (np.abs(R_late - mean) > M / (2 * (K + 1)) * 0.5).any()

@@ -1,6 +1,8 @@
 """Host-side pieces of bench.py that need no GPU: the clock-sample summary
 (throttle reasons must be reported), the tie of the stored DRAM-traffic figure
-to the blend kernel's source, and the oracle arm's bounded per-step timing."""
+to the blend kernel's source, the oracle arm's bounded per-step timing, the
+per-tile distinct-row count U_tile and the near-tie categories of the parity
+sample."""
 import json
 import os
 
@@ -51,3 +53,38 @@ def test_oracle_arm_step_is_bounded_and_reuses_the_projection():
     fps2, _, _, secs2 = bench.oracle_frames_per_s(g, f, cam, 0.2, seed=1, proj=proj)
     assert fps2 > 0 and np.isfinite(secs2)
     assert bench.oracle_frames_per_s.last_proj[1] == proj[1]   # the projection time is reused
+
+
+def test_tile_distinct_rows_counts_each_tile_s_set_once():
+    torch = __import__("pytest").importorskip("torch")
+    rng = np.random.default_rng(3)
+    W, H, K = 37, 21, 5                      # ragged 16x16 tiles on both axes
+    ids = rng.integers(-1, 40, (W * H, K)).astype(np.int32)
+    got = bench.tile_distinct_rows(torch.from_numpy(ids), W, 16, 16)
+    seen = set()
+    for p in range(W * H):
+        y, x = divmod(p, W)
+        seen.update((y // 16, x // 16, int(v)) for v in ids[p] if v >= 0)
+    assert got == len(seen)
+    # one tile, every pixel listing the same rows: U_tile = U
+    same = np.tile(np.array([[3, 7, -1, -1, -1]], np.int32), (16 * 16, 1))
+    assert bench.tile_distinct_rows(torch.from_numpy(same), 16, 16, 16) == 2
+
+
+def test_parity_sample_reports_tie_categories():
+    class Ref:
+        pass
+    K, W = 2, 4
+    pix = np.array([[0, 0], [1, 0], [2, 0], [3, 0]], np.int32)
+    ref = Ref()
+    ref.ids = np.array([[5, -1], [6, 7], [8, -1], [1, 2]], np.int32)
+    ref.cnt = np.array([1, 2, 1, 2])
+    ref.tie = np.array([0, 1, 2 | 4, 1 | 8])     # bit 8 (dense T_min) is not Algorithm 1's
+    ref.wq = np.zeros((4, K))
+    ref.out_q = np.zeros((4, 3))
+    ref.scale_q = np.ones(4)
+    ids = ref.ids.copy()
+    ids[1] = [6, 9]                               # a mismatch on a flagged pixel only
+    rep = bench.sample_parity(ids, ref.cnt.astype(np.uint8), np.zeros((4, 3)), W, pix, ref)
+    assert rep["near_tie_pixels"] == 3 and rep["mismatch_nontie"] == 0
+    assert rep["near_tie_by_category"] == {"boundary": 2, "alpha_min_border": 1, "equal_depth": 1}

@@ -37,7 +37,7 @@ def test_two_gloo_ranks_reduce_to_the_slowest():
     import torch.multiprocessing as mp
     ws = 2
     port = _free_port()
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()   # no fork of a multi-threaded process
     out = mgr.dict()
     mp.spawn(_rank_main, args=(ws, port, out), nprocs=ws, join=True)
     assert out[0] == out[1] == [4.0, 7.0, 4.0]

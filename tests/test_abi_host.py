@@ -144,3 +144,28 @@ def test_cosine_backward_rejects_bad_arguments_before_launch(lib):
     assert call(wsb=wc - 1) == q.QR_ERR_INVALID_ARG
     assert call(dt=q.QR_FP8E4M3) == q.QR_ERR_INVALID_ARG             # FP8 without scales
     assert L.qr_launch_count() == launches
+
+
+def test_header_enumerators_match_the_binding():
+    """Every `QR_NAME = value` enumerator of the header has the same value in
+    the Python binding (status codes, dtypes, select rules)."""
+    src = open(os.path.join(ROOT, "include", "qrender.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    enums = {m.group(1): int(m.group(2), 0)
+             for m in re.finditer(r"\b(QR_[A-Z0-9_]+)\s*=\s*(-?(?:0x[0-9a-fA-F]+|\d+))", src)}
+    assert {"QR_RULE_QUANTILE", "QR_RULE_TOPK", "QR_RULE_STRATIFIED", "QR_RULE_RIEMANN",
+            "QR_OK", "QR_F32", "QR_BF16", "QR_FP8E4M3"} <= set(enums)
+    for name, value in enums.items():
+        assert hasattr(q, name), name
+        assert getattr(q, name) == value, (name, getattr(q, name), value)
+
+
+def test_select_rule_rejects_unknown_rules_before_launch(lib):
+    rc, f = _frame()
+    assert rc == q.QR_OK
+    good = ctypes.c_void_p(1 << 20)
+    for rule in (-1, 4, 99):
+        assert lib.qr_select_rule(ctypes.byref(f), rule, good, good, good, None, None) == \
+            q.QR_ERR_INVALID_ARG
+    assert lib.qr_select_rule(None, q.QR_RULE_RIEMANN, good, good, good, None, None) == \
+        q.QR_ERR_INVALID_ARG

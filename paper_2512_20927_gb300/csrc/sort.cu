@@ -415,7 +415,13 @@ __device__ unsigned long long *sort_smem(unsigned long long *s, unsigned long lo
                 j += take_a ? 0 : 1;
             }
         }
-        __syncthreads();
+        // Thread i writes keys [iE, iE + E) in every round, and the next round
+        // (run length 2L) reads only the aligned block of 4L keys holding its
+        // outputs.  While 4L <= 32 E that block is one warp's own outputs (and
+        // was read by that warp alone in this round), so the warp's barrier
+        // orders it; the last round's outputs are read by every thread.
+        if (4 * L <= 32 * E && 2 * L < n) __syncwarp();
+        else __syncthreads();
         unsigned long long *x = s;
         s = t;
         t = x;
